@@ -1,0 +1,97 @@
+"""Seeded synthetic metasurface workloads (inputs only, no solver arithmetic).
+
+Both the CUDA path and the FP64 oracle take their scenes from here.  The
+module draws lattices, radii and incidences; it computes nothing of the
+MLFMA-SMR method itself.
+
+All lengths are in vacuum wavelengths.  The particles are dielectric spheres
+(eps_r = 4, mu_r = 1) in vacuum on a square lattice of pitch 0.5; every
+sphere carries N_perp transverse and N_par longitudinal static modes.  The
+paper's own workloads (gold spheres, bricks, TiO2 nanofins meshed with an
+external mesher) need permittivity tables and meshes that are not available
+here; the radius-quantised sphere lattices below stand in for them with the
+same particle counts, the same 8-shape structure and the same unknown counts.
+"""
+import numpy as np
+
+PITCH = 0.5
+EPS_IN = 4.0
+RADII8 = np.linspace(0.08, 0.20, 8)
+
+
+def lattice(nx, ny, pitch=PITCH):
+    """Centred nx x ny lattice, row-major (x fastest); (p, 3) array."""
+    xs = (np.arange(nx) - (nx - 1) / 2.0) * pitch
+    ys = (np.arange(ny) - (ny - 1) / 2.0) * pitch
+    X, Y = np.meshgrid(xs, ys, indexing='xy')
+    return np.stack([X.ravel(), Y.ravel(), np.zeros(nx * ny)], axis=1)
+
+
+def incidence(theta_deg=0.0, phi_deg=0.0, pol='x'):
+    """Plane wave direction khat and the unit projection of x_hat or y_hat
+    onto the plane orthogonal to khat."""
+    t, f = np.radians(theta_deg), np.radians(phi_deg)
+    k = np.array([np.sin(t) * np.cos(f), np.sin(t) * np.sin(f), np.cos(t)])
+    e = np.array([1.0, 0.0, 0.0]) if pol == 'x' else np.array([0.0, 1.0, 0.0])
+    e = e - k * (k @ e)
+    return k, (e / np.linalg.norm(e)).astype(complex)
+
+
+def incidence_grid64():
+    """64 incidences: theta in linspace(0, 40 deg, 8), phi in {0,90,180,270},
+    x and y polarisations (duplicates at theta = 0 kept)."""
+    out = []
+    for t in np.linspace(0.0, 40.0, 8):
+        for f in (0.0, 90.0, 180.0, 270.0):
+            for pol in ('x', 'y'):
+                out.append(incidence(t, f, pol))
+    return out
+
+
+def metalens_bins(centres, focal, n_bins=8):
+    """Radius bin per site from the hyperbolic lens phase
+    phi = 2 pi (f - sqrt(f^2 + x^2 + y^2)) mod 2 pi, bin = floor(n phi / 2 pi)."""
+    x, y = centres[:, 0], centres[:, 1]
+    ph = np.mod(2 * np.pi * (focal - np.sqrt(focal ** 2 + x ** 2 + y ** 2)), 2 * np.pi)
+    return np.minimum((n_bins * ph / (2 * np.pi)).astype(int), n_bins - 1)
+
+
+def make(name, **kw):
+    """Workload dict: centres, shape_ids, shapes [(radius, n_perp, n_par)],
+    eps_in, pitch, incidences [(khat, pol)], label."""
+    if name == 'spheres8x8':
+        # 8x8 identical spheres r = 0.15, 12 + 12 modes per current: 3,072 unknowns
+        C = lattice(8, 8)
+        return dict(label='8x8 spheres r=0.15, 24 modes/current, 3072 unknowns',
+                    centres=C, shape_ids=np.zeros(64, dtype=np.int32),
+                    shapes=[(0.15, 12, 12)], eps_in=EPS_IN, pitch=PITCH,
+                    incidences=[incidence(0, 0, 'x')])
+    if name == 'random':
+        # n x n lattice, radius index uniform over 8 values from a seed
+        n = kw.get('n', 40)
+        seed = kw.get('seed', 21724)
+        modes = kw.get('modes', 16)
+        rng = np.random.default_rng(seed)
+        ids = rng.integers(0, 8, size=n * n).astype(np.int32)
+        inc = kw.get('incidences') or [incidence(0, 0, 'x')]
+        return dict(label=f'{n}x{n} random-radius spheres (8 radii), {2*modes} modes/current, '
+                          f'{n*n*4*modes} unknowns',
+                    centres=lattice(n, n), shape_ids=ids,
+                    shapes=[(r, modes, modes) for r in RADII8], eps_in=EPS_IN,
+                    pitch=PITCH, incidences=inc)
+    if name == 'metalens':
+        # n x n hyperbolic-phase lens, focal length f, radii quantised to 8 bins
+        n = kw.get('n', 200)
+        f = kw.get('focal', 50.0)
+        modes = kw.get('modes', 16)
+        C = lattice(n, n)
+        ids = metalens_bins(C, f).astype(np.int32)
+        return dict(label=f'{n}x{n} metalens f={f}, {2*modes} modes/current, {n*n*4*modes} unknowns',
+                    centres=C, shape_ids=ids,
+                    shapes=[(r, modes, modes) for r in RADII8], eps_in=EPS_IN,
+                    pitch=PITCH, incidences=[incidence(0, 0, 'x')], focal=f)
+    if name == 'ragged16':
+        # 16 arrays of n_i = round(10 + 50 i / 15) pillars per side, seeds 21726 + i
+        return [make('random', n=int(round(10 + 50 * i / 15)), seed=21726 + i,
+                     modes=kw.get('modes', 16)) for i in range(16)]
+    raise KeyError(name)

@@ -1,0 +1,331 @@
+"""Pins of the FP64 oracle against closed forms, textbook results and
+invariants (no GPU).  Each test names what it pins and why a plausible
+mistake in the oracle would fail it."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import mlfma as ml
+from oracle import pmchwt as pm
+from oracle.gmres import block_diag_precond, gmres
+from oracle.mie import mie_converged_order, mie_cross_sections
+from oracle.special import gauss_legendre, mode_list, real_ylm, sph_h2, sph_j
+from oracle.sphere import SphereShape, eval_modes, sphere_rule, static_eigenvalues
+
+
+def _lattice(n, pitch=0.5):
+    xs = (np.arange(n) - (n - 1) / 2) * pitch
+    return np.array([[x, y, 0.0] for y in xs for x in xs])
+
+
+# ------------------------------------------------------------- special functions
+def test_real_harmonics_orthonormal_and_gradient():
+    """Real Y_lm are orthonormal on the unit sphere (quadrature exact to 1e-14)
+    and the analytic surface gradient matches central finite differences."""
+    rule = sphere_rule(1.0, 12, 24)
+    modes = mode_list(15)
+    Y = np.array([real_ylm(l, m, k, rule['theta'], rule['phi'])[0] for (l, m, k) in modes])
+    G = (Y * rule['w']) @ Y.T
+    assert np.max(np.abs(G - np.eye(len(modes)))) < 1e-13
+    th, ph, h = 0.7, 1.3, 1e-6
+    for (l, m, k) in modes:
+        _, Yt, Yp = real_ylm(l, m, k, th, ph)
+        ft = (real_ylm(l, m, k, th + h, ph)[0] - real_ylm(l, m, k, th - h, ph)[0]) / (2 * h)
+        fp = (real_ylm(l, m, k, th, ph + h)[0] - real_ylm(l, m, k, th, ph - h)[0]) / (2 * h)
+        assert abs(Yt - ft) < 1e-8 and abs(Yp - fp / math.sin(th)) < 1e-8
+
+
+# ------------------------------------------------------------- static modes
+@pytest.mark.parametrize("a", [0.08, 0.15, 0.2])
+def test_sphere_modes_orthonormal_divergence(a):
+    """Static modes have unit L2 norm and are mutually orthogonal (Gram = I);
+    transverse modes are divergence-free and the longitudinal divergence obeys
+    Gauss: int psi . grad_S f = -int (div psi) f for f = c . r."""
+    sh = SphereShape(a, 16, 16)
+    rule = sphere_rule(a, 16, 32)
+    psi, div = eval_modes(sh, rule)
+    w = rule['w']
+    G = np.einsum('nqc,mqc,q->nm', psi, psi, w)
+    assert np.max(np.abs(G - np.eye(32))) < 1e-13
+    assert np.max(np.abs(np.einsum('nqc,qc->nq', psi, rule['r_hat']))) < 1e-14  # tangential
+    assert np.max(np.abs(div[:16])) == 0.0
+    c = np.array([0.3, -0.5, 0.8])
+    gradf = c[None, :] - rule['r_hat'] * (rule['r_hat'] @ c)[:, None]
+    f = rule['r'] @ c
+    lhs = np.einsum('nqc,qc,q->n', psi, gradf, w)
+    rhs = -np.einsum('nq,q,q->n', div, f, w)
+    assert np.max(np.abs(lhs - rhs)) < 1e-13
+
+
+def test_static_eigenvalue_order():
+    """Sec. III orders longitudinal modes by ascending and transverse modes by
+    descending static eigenvalue; the closed forms obey both."""
+    gp, gl = static_eigenvalues(SphereShape(0.15, 24, 24))
+    assert np.all(np.diff(gp) <= 0) and np.all(np.diff(gl) >= 0)
+
+
+def test_transverse_pattern_closed_form():
+    """Eq. 26 by quadrature equals the closed form for transverse modes,
+    psi_hat^perp_lm(k) = 4 pi a (-j)^l j_l(ka) (khat x grad_1 Y_lm)(khat)/sqrt(l(l+1))."""
+    a = 0.2
+    sc = pm.Scene([[0, 0, 0]], [0], [(a, 15, 15)], eps_in=4.0, n_theta=16, n_phi=32)
+    M = ml.MLFMA.__new__(ml.MLFMA)
+    M.scene, M.k = sc, sc.outer.k
+    M.grids = [ml.Grid(10)]
+    P = M._pattern(0)
+    g = M.grids[0]
+    th = np.arccos(g.khat[:, 2])
+    ph = np.mod(np.arctan2(g.khat[:, 1], g.khat[:, 0]), 2 * np.pi)
+    k = sc.outer.k
+    for n, (l, m, kind) in enumerate(mode_list(15)):
+        _, Yt, Yp = real_ylm(l, m, kind, th, ph)
+        c = 4 * np.pi * a * (-1j) ** l * sph_j(l, k * a) / math.sqrt(l * (l + 1))
+        assert np.max(np.abs(P[n, 0] - c * (-Yp))) < 1e-13
+        assert np.max(np.abs(P[n, 1] - c * Yt)) < 1e-13
+
+
+# ------------------------------------------------------------- self block vs Mie
+@pytest.mark.parametrize("lmax", [1, 2, 3])
+@pytest.mark.parametrize("a,eps", [(0.15, 4.0), (0.2, 4.0), (0.1, 2.25)])
+def test_single_sphere_matches_truncated_mie(lmax, a, eps):
+    """With full shells l <= lmax the closed-form self block (Eq. 16), the RHS
+    (Eqs. 18-19) and the far field reproduce the Mie series truncated at lmax
+    exactly: C_sca and C_ext to 1e-12.  A sign error in T, K, zeta or the RHS
+    breaks this."""
+    nm = lmax * (lmax + 2)
+    sc = pm.Scene([[0.1, -0.2, 0.05]], [0], [(a, nm, nm)], eps_in=eps, n_theta=20, n_phi=40)
+    x = np.linalg.solve(sc.self_block(0), pm.rhs(sc, [0, 0, 1], [1, 0, 0]))
+    cs = pm.scattering_cross_section(sc, x, 24)
+    ce = pm.extinction_cross_section(sc, x, [0, 0, 1], [1, 0, 0])
+    ms, me = mie_cross_sections(sc.outer.k, a, math.sqrt(eps), lmax)
+    assert abs(cs / ms - 1) < 1e-12 and abs(ce / me - 1) < 1e-12
+
+
+def test_single_sphere_converges_to_mie():
+    """l <= 4 (24 modes/current) against the converged Mie series: the
+    remaining error is the l >= 5 Mie terms, below 1e-6 at ka = 0.94."""
+    sc = pm.Scene([[0, 0, 0]], [0], [(0.15, 24, 24)], eps_in=4.0, n_theta=20, n_phi=40)
+    x = np.linalg.solve(sc.self_block(0), pm.rhs(sc, [0, 0, 1], [1, 0, 0]))
+    cs = pm.scattering_cross_section(sc, x, 24)
+    nconv = mie_converged_order(sc.outer.k * 0.15)
+    ms, _ = mie_cross_sections(sc.outer.k, 0.15, 2.0, nconv)
+    assert abs(cs / ms - 1) < 1e-6
+
+
+# ------------------------------------------------------------- off-diagonal blocks
+@pytest.fixture(scope="module")
+def small_dense():
+    sc = pm.Scene(_lattice(3), [0] * 9, [(0.15, 8, 8)], eps_in=4.0, n_theta=12, n_phi=24)
+    return sc, pm.dense_matrix(sc)
+
+
+def test_reciprocity(small_dense):
+    """Real modes make T and K symmetric under (mu,m) <-> (nu,n), so
+    Z^T = D Z D with D = diag(I, -I) per particle."""
+    sc, Z = small_dense
+    D = np.ones(Z.shape[0])
+    D.reshape(sc.p, 2, sc.n_psi)[:, 1, :] = -1
+    assert np.linalg.norm(Z.T - D[:, None] * Z * D[None, :]) / np.linalg.norm(Z) < 1e-14
+
+
+def test_optical_theorem_lossless_array(small_dense):
+    """For lossless particles C_ext (forward amplitude) = C_sca (integrated
+    far field): energy conservation of the whole coupled system."""
+    sc, Z = small_dense
+    for khat, pol in (([0, 0, 1], [1, 0, 0]), ([0.3, 0, 0.9539392014169456], [0, 1, 0])):
+        x = np.linalg.solve(Z, pm.rhs(sc, khat, pol))
+        cs = pm.scattering_cross_section(sc, x, 40)
+        ce = pm.extinction_cross_section(sc, x, khat, pol)
+        assert abs(ce / cs - 1) < 1e-10
+
+
+def test_optical_theorem_catches_planted_K_sign(monkeypatch):
+    """Plant a flipped K in the oracle's off-diagonal blocks: energy
+    conservation must fail by far more than its 1e-10 tolerance."""
+    orig = pm.exterior_TK
+
+    def flipped(*args):
+        T, K = orig(*args)
+        return T, -K
+    monkeypatch.setattr(pm, "exterior_TK", flipped)
+    sc = pm.Scene(_lattice(3), [0] * 9, [(0.15, 8, 8)], eps_in=4.0, n_theta=10, n_phi=20)
+    x = np.linalg.solve(pm.dense_matrix(sc), pm.rhs(sc, [0, 0, 1], [1, 0, 0]))
+    cs = pm.scattering_cross_section(sc, x, 40)
+    ce = pm.extinction_cross_section(sc, x, [0, 0, 1], [1, 0, 0])
+    assert abs(ce / cs - 1) > 1e-2
+
+
+def test_offdiag_quadrature_converged():
+    """Exterior blocks at 1 wavelength are converged in the surface rule."""
+    blocks = []
+    for n in (12, 20):
+        sc = pm.Scene([[0, 0, 0], [1.0, 0, 0]], [0, 0], [(0.2, 16, 16)], eps_in=4.0,
+                      n_theta=n, n_phi=2 * n)
+        blocks.append(pm.exterior_block(sc, 0, [0, 0, 0], 0, [1.0, 0, 0]))
+    assert np.linalg.norm(blocks[0] - blocks[1]) / np.linalg.norm(blocks[1]) < 1e-10
+
+
+def test_well_separated_spheres_decouple():
+    """Two spheres 40 wavelengths apart: each current tends to the isolated
+    sphere's (coupling ~ 1/(k d)); the relative change is below 1e-2."""
+    sh = [(0.15, 8, 8)]
+    one = pm.Scene([[0, 0, 0]], [0], sh, eps_in=4.0)
+    x1 = np.linalg.solve(one.self_block(0), pm.rhs(one, [0, 0, 1], [1, 0, 0]))
+    two = pm.Scene([[0, 0, 0], [40.0, 0, 0]], [0, 0], sh, eps_in=4.0)
+    x2 = np.linalg.solve(pm.dense_matrix(two), pm.rhs(two, [0, 0, 1], [1, 0, 0]))
+    assert np.linalg.norm(x2[:32] - x1) / np.linalg.norm(x1) < 1e-2
+
+
+# ------------------------------------------------------------- MLFMA pieces
+def _addition_error(L, Xn, dn=0.35):
+    k = 2 * np.pi
+    g = ml.Grid(L)
+    rng = np.random.default_rng(L)
+    errs = []
+    for _ in range(5):
+        X = rng.standard_normal(3)
+        X *= Xn / np.linalg.norm(X)
+        d = rng.standard_normal(3)
+        d *= dn / np.linalg.norm(d)
+        T = ml.translation_function(k, L, g.khat, X)
+        approx = np.sum(g.w * np.exp(-1j * k * (g.khat @ d)) * T)
+        R = np.linalg.norm(X + d)
+        exact = np.exp(-1j * k * R) / (4 * np.pi * R)
+        errs.append(abs(approx - exact) / abs(exact))
+    return max(errs)
+
+
+@pytest.mark.parametrize("L,tol", [(10, 1e-6), (14, 1e-10), (20, 1e-13)])
+def test_addition_theorem(L, tol):
+    """Eq. 22: sum_k w e^{-j k khat.d} T_L(khat, X) reproduces g(|X + d|)
+    for |d| < |X| (here |X| = 3, |d| = 0.35); the error falls with L."""
+    assert _addition_error(L, 3.0) < tol
+
+
+def test_addition_theorem_breaks_when_L_far_above_kX():
+    """Sec. IV warns that h_l diverges for small arguments: with L = 40 at
+    k|X| = 3 pi the truncated series loses every digit, which is why the
+    truncation per level follows kd rather than a fixed doubling."""
+    assert _addition_error(14, 1.5) < 1e-8
+    assert _addition_error(40, 1.5) > 1.0
+
+
+def test_interpolation_reproduces_cubics():
+    """4x4 Lagrange reproduces tensor cubics in (theta, phi) exactly away
+    from the poles and the phi seam."""
+    src, dst = ml.Grid(10), ml.Grid(17)
+    I = ml.interpolation_matrix(src, dst)
+    TH, PH = np.meshgrid(src.theta, src.phi, indexing='ij')
+    f = lambda t, p: (1 + 2 * t - t ** 2 + 0.3 * t ** 3) * (0.5 - p + 0.2 * p ** 2 - 0.01 * p ** 3)
+    out = I @ f(TH, PH).ravel()
+    Tt, Tp = np.meshgrid(dst.theta, dst.phi, indexing='ij')
+    exact = f(Tt, Tp).ravel()
+    dphi = 2 * np.pi / src.n_phi
+    ok = ((Tt > src.theta[1]) & (Tt < src.theta[-2]) & (Tp > 2 * dphi) & (Tp < 2 * np.pi - 3 * dphi)).ravel()
+    assert ok.sum() > 100
+    assert np.max(np.abs(out[ok] - exact[ok])) < 1e-12
+
+
+def test_interpolation_pole_reflection():
+    """A smooth tangential field (components of a constant Cartesian vector)
+    interpolates near the poles as well as elsewhere; dropping the sign
+    flip of the reflected taps would leave O(1) errors there."""
+    c = np.array([0.4, -0.7, 0.6])
+    errs = []
+    for (La, Lb) in ((10, 17), (20, 34)):
+        src, dst = ml.Grid(La), ml.Grid(Lb)
+        I = ml.interpolation_matrix(src, dst)
+        for basis_s, basis_d in ((src.that, dst.that), (src.phat, dst.phat)):
+            out = I @ (basis_s @ c)
+            errs.append(np.max(np.abs(out - basis_d @ c)))
+    assert errs[0] < 2e-3 and errs[1] < 2e-3
+    assert errs[2] < errs[0] / 8 and errs[3] < errs[1] / 8
+
+
+def test_anterpolation_is_weighted_adjoint():
+    """<I f, g>_{W_parent} = <f, A g>_{W_child} with A = W_c^{-1} I^T W_p."""
+    src, dst = ml.Grid(10), ml.Grid(17)
+    I = ml.interpolation_matrix(src, dst)
+    rng = np.random.default_rng(3)
+    f = rng.standard_normal(src.K) + 1j * rng.standard_normal(src.K)
+    g = rng.standard_normal(dst.K) + 1j * rng.standard_normal(dst.K)
+    lhs = np.sum(dst.w * (I @ f) * g)
+    rhs = np.sum(src.w * f * ((I.T @ (dst.w * g)) / src.w))
+    assert abs(lhs - rhs) < 1e-12 * abs(lhs)
+
+
+def test_single_level_fmm_blocks_match_dense():
+    """Eqs. 24-25 with Eq. 26 patterns and Eq. 23 at large L reproduce the
+    dense T and K of a pair two wavelengths apart to 1e-11 (L = 20, inside
+    the stable range L < ~1.6 k|X|): pins the k-space forms, their signs and
+    the (theta, phi) algebra of the receive step."""
+    sc = pm.Scene([[0, 0, 0], [2.0, 0.5, 0]], [0, 1], [(0.15, 8, 8), (0.2, 8, 8)], eps_in=4.0,
+                  n_theta=16, n_phi=32)
+    T0, K0 = pm.exterior_TK(sc, 0, sc.centres[0], 1, sc.centres[1])
+    M = ml.MLFMA.__new__(ml.MLFMA)
+    M.scene, M.k = sc, sc.outer.k
+    L = 20
+    M.grids = [ml.Grid(L)]
+    P0, P1 = M._pattern(0), M._pattern(1)
+    g = M.grids[0]
+    T = ml.translation_function(M.k, L, g.khat, sc.centres[0] - sc.centres[1])
+    wT = g.w * T
+    Tf = -1j * M.k * (np.einsum('mk,nk,k->mn', P0[:, 0], np.conj(P1[:, 0]), wT)
+                      + np.einsum('mk,nk,k->mn', P0[:, 1], np.conj(P1[:, 1]), wT))
+    Kf = -1j * M.k * (np.einsum('mk,nk,k->mn', P0[:, 0], np.conj(P1[:, 1]), wT)
+                      - np.einsum('mk,nk,k->mn', P0[:, 1], np.conj(P1[:, 0]), wT))
+    assert np.linalg.norm(Tf - T0) / np.linalg.norm(T0) < 1e-11
+    assert np.linalg.norm(Kf - K0) / np.linalg.norm(K0) < 1e-11
+
+
+@pytest.fixture(scope="module")
+def mixed5():
+    rng = np.random.default_rng(7)
+    ids = rng.integers(0, 2, size=25)
+    sc = pm.Scene(_lattice(5), ids, [(0.12, 8, 8), (0.18, 8, 8)], eps_in=4.0,
+                  n_theta=12, n_phi=24)
+    return sc, pm.dense_matrix(sc)
+
+
+def test_tree_covers_every_pair_once(mixed5):
+    """Near pairs plus interaction lists (mapped down to particles) cover
+    every ordered pair exactly once."""
+    sc, _ = mixed5
+    t = ml.Tree(sc.centres, 0.5)
+    count = np.zeros((sc.p, sc.p), dtype=int)
+    for (mu, nu) in t.near_pairs():
+        count[mu, nu] += 1
+    anc = [np.arange(sc.p)]
+    for s in range(t.n_levels - 1):
+        anc.append(t.levels[s]['parent'][anc[-1]])
+    for s, lev in enumerate(t.levels):
+        for (b, bb, _) in lev['il']:
+            count[np.ix_(anc[s] == b, anc[s] == bb)] += 1
+    assert np.all(count == 1)
+
+
+def test_mlfma_matches_dense(mixed5):
+    """MLFMA product vs the dense Galerkin product: FMM accuracy at L0 = 10,
+    improving as L0 grows."""
+    sc, Z = mixed5
+    rng = np.random.default_rng(0)
+    x = (rng.standard_normal(Z.shape[0]) + 1j * rng.standard_normal(Z.shape[0])) / math.sqrt(2)
+    y0 = Z @ x
+    e10 = np.linalg.norm(ml.MLFMA(sc, 0.5, L0=10).matvec(x) - y0) / np.linalg.norm(y0)
+    e16 = np.linalg.norm(ml.MLFMA(sc, 0.5, L0=16).matvec(x) - y0) / np.linalg.norm(y0)
+    assert e10 < 1e-3 and e16 < e10 / 3
+
+
+# ------------------------------------------------------------- GMRES
+def test_gmres_matches_direct_solve(mixed5):
+    """Block-diagonal right-preconditioned GMRES reaches the requested true
+    residual and agrees with the direct solution to that accuracy."""
+    sc, Z = mixed5
+    b = pm.rhs(sc, [0, 0, 1], [1, 0, 0])
+    x, info = gmres(lambda v: Z @ v, b, precond=block_diag_precond(sc), tol=1e-8)
+    assert info['resid_true'] <= 1e-8
+    xd = np.linalg.solve(Z, b)
+    assert np.linalg.norm(x - xd) / np.linalg.norm(xd) < 1e-6
+    x2, info2 = gmres(lambda v: Z @ v, b, precond=block_diag_precond(sc), tol=1e-8, restart=7)
+    assert info2['resid_true'] <= 1e-8
