@@ -1,0 +1,211 @@
+/*
+ * smr.h - C ABI of the GB300 MLFMA-SMR library (libsmr.so).
+ *
+ * Multilevel fast multipole matrix-vector product and GMRES solve of the
+ * PMCHWT system whose unknowns are static-mode coefficients of the electric
+ * and magnetic surface currents on each particle of a metasurface
+ * (Corsaro, Miano, Tamburrino, Ventre, Forestiere, arXiv 2407.21724).
+ *
+ * Conventions shared by every call
+ *  - Every call returns int: SMR_OK (0) or a negative SMR_E_* code; the
+ *    message of the last failure is smr_last_error(ctx).  No call aborts,
+ *    throws or exits.
+ *  - Lengths are in units of the vacuum wavelength times opts.wavelength
+ *    (wavelength = 1 means lengths in wavelengths).  Impedances are
+ *    normalised by the vacuum impedance.  Time dependence e^{j w t} (Sec. II).
+ *  - Complex numbers are interleaved (re, im) doubles (C99 double _Complex).
+ *  - Unknown vector layout x[mu][c][n][r]: particle mu (scene order), current
+ *    c (0 = electric J, 1 = magnetic M), mode n (N_perp transverse modes then
+ *    N_par longitudinal ones, Sec. III), right-hand side r (innermost, R of
+ *    them).  N = 2 N_psi p unknowns per right-hand side (Eq. 11).
+ *  - "device" pointers are CUDA global-memory pointers on ctx's device; the
+ *    caller owns them and keeps them alive until the call's work on `stream`
+ *    is complete.  "host" pointers are read or written before the call
+ *    returns.  `stream` is a cudaStream_t (NULL = legacy default stream).
+ *  - The library owns all memory it allocates (tables, level spectra,
+ *    Krylov basis) until smr_destroy.
+ *  - Sign conventions: T_mn = -j k <psi_m, G psi_n> and
+ *    K_mn = -<psi_m, psi_n x grad' g> (Eqs. 8, 9, T_far1 and Eq. 25 read
+ *    together), right-hand side [<psi, E_inc>; <psi, H_inc>] (Eqs. 18-19).
+ */
+#ifndef SMR_H
+#define SMR_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct smr_ctx smr_ctx;
+
+enum {
+  SMR_OK = 0,
+  SMR_E_INVALID_ARG = -1,   /* bad size, pointer, option or value            */
+  SMR_E_SHAPE = -2,         /* unknown shape id or inconsistent mode counts   */
+  SMR_E_OOM = -3,           /* device or host allocation failed              */
+  SMR_E_CUDA = -4,          /* a CUDA runtime call or kernel launch failed    */
+  SMR_E_NOT_CONVERGED = -5, /* solve hit maxit before the tolerance          */
+  SMR_E_BREAKDOWN = -6,     /* Arnoldi breakdown before convergence          */
+  SMR_E_NAN = -7,           /* NaN or Inf in a residual                      */
+  SMR_E_STATE = -9          /* call made before smr_set_scene, or similar    */
+};
+
+enum { SMR_PREC_FP64 = 0, SMR_PREC_FP32 = 1 };
+enum { SMR_LRULE_FORMULA = 0, SMR_LRULE_DOUBLE = 1 };
+enum { SMR_PRECOND_NONE = 0, SMR_PRECOND_BLOCKDIAG = 1 };
+
+/* Options of a context (smr_default_opts fills the defaults in brackets). */
+typedef struct {
+  int device;         /* CUDA device ordinal [0]                                 */
+  double wavelength;  /* vacuum wavelength in the caller's length unit [1.0]     */
+  double pitch;       /* finest group size = lattice spacing [0.5]: each particle
+                         is its own finest group (Sec. IV, Fig. 1a)              */
+  int L0;             /* truncation order at the finest level [10] (Sec. V)      */
+  int level_rule;     /* L above the finest level: SMR_LRULE_FORMULA uses
+                         L = kd + 1.8 d0^{2/3} (kd)^{1/3}, d = sqrt(2) x box size
+                         (Sec. IV); SMR_LRULE_DOUBLE uses L0 2^s (Sec. V)  [0]   */
+  double digits;      /* d0 of the truncation formula [3.0]                       */
+  int n_theta;        /* surface rule per particle: Gauss-Legendre nodes in
+                         cos(theta) [16]                                          */
+  int n_phi;          /* and uniform phi nodes [32]                               */
+} smr_opts;
+
+void smr_default_opts(smr_opts* opts);
+
+/* Create a context on opts->device.  *ctx is NULL on failure (the return code
+ * says why; no message object exists then). */
+int smr_create(smr_ctx** ctx, const smr_opts* opts);
+
+/* Free every device and host allocation of the context.  NULL is a no-op. */
+int smr_destroy(smr_ctx* ctx);
+
+/* Message of the last failing call on ctx ("" if none).  Owned by ctx. */
+const char* smr_last_error(const smr_ctx* ctx);
+
+/* Register a sphere of the given radius whose currents are expanded in its
+ * closed-form static modes (Sec. III, Eqs. 21-25: vector spherical harmonics
+ * grad_1 Y_lm / (a sqrt(l(l+1))) and r x that), n_perp transverse and n_par
+ * longitudinal ones, l ascending, real harmonics in the order m = 0, 1c, 1s,
+ * 2c, 2s, ...  All shapes of a context must share n_perp + n_par.
+ * *shape_id receives the new id (0, 1, ...).  Must precede smr_set_scene. */
+int smr_add_sphere(smr_ctx* ctx, double radius, int n_perp, int n_par, int* shape_id);
+
+/* Set the scene: p particles with host centres[p][3] and host shape_ids[p],
+ * inner medium (eps_in, mu_in) and background (eps_out, mu_out), each a
+ * complex relative value {re, im}.  Centres must lie one per cell of a square
+ * lattice of spacing opts.pitch in a plane z = const (the quadtree of Sec. IV).
+ * Builds the quadtree, interaction lists, k-space grids, and on the GPU in
+ * FP64: the patterns (Eq. 26), translation tables (Eq. 23) and near blocks
+ * (Eq. 16; exterior blocks by surface quadrature, self blocks in closed form),
+ * and the block-diagonal preconditioner (Sec. V, stage v).  Only real
+ * (lossless) permittivities and permeabilities are accepted.  May be called
+ * again to replace the scene. */
+int smr_set_scene(smr_ctx* ctx, int p, const double* centres, const int* shape_ids,
+                  const double eps_in[2], const double mu_in[2],
+                  const double eps_out[2], const double mu_out[2]);
+
+/* Sizes of the current scene. */
+typedef struct {
+  int p, n_psi, n_shapes, n_levels;
+  long long n_unknowns;     /* 2 n_psi p                                       */
+  int L[16], K[16], n_box[16], n_il[16];  /* per level s < n_levels          */
+  long long n_near_pairs;   /* particle pairs in the near SpMV (self included) */
+  int n_near_blocks;        /* distinct near blocks stored                     */
+  double device_bytes;      /* tables + one set of level spectra (R = 1)       */
+} smr_info_t;
+int smr_info(smr_ctx* ctx, smr_info_t* info);
+
+/* Right-hand sides of R unit plane waves E = pol exp(-j k khat . r),
+ * H = khat x E / zeta_out (Eqs. 5, 18, 19): host khat[R][3] (unit vectors),
+ * host pol[R][3] complex.  Writes device b[N][R] (layout above). */
+int smr_rhs_plane_waves(smr_ctx* ctx, int R, const double* khat, const double* pol,
+                        void* b, void* stream);
+
+/* The hot path: y = Z x for R right-hand sides at once (Sec. IV): near
+ * block-sparse product plus aggregation, interpolation, translation,
+ * anterpolation and receive.  precision SMR_PREC_FP64 computes every step in
+ * FP64; SMR_PREC_FP32 computes the steps in FP32 from FP32 copies of the
+ * FP64-generated tables (x and y stay FP64 complex).  device x, y [N][R]. */
+int smr_matvec(smr_ctx* ctx, int R, const void* x, void* y, int precision, void* stream);
+
+/* Same, split: y_near = near-field part, y_far = MLFMA far part (either may
+ * be NULL).  For per-stage parity checks. */
+int smr_matvec_parts(smr_ctx* ctx, int R, const void* x, void* y_near, void* y_far,
+                     int precision, void* stream);
+
+/* Same as smr_matvec with HOST x and y (pageable or pinned): copies in,
+ * multiplies, copies out on `stream`, and synchronises it before returning. */
+int smr_matvec_host(smr_ctx* ctx, int R, const double* x, double* y, int precision,
+                    void* stream);
+
+/* z = blockdiag(Z_s^-1) r over particles: the block-diagonal preconditioner
+ * of Sec. V (each block the inverse of the particle's self block).
+ * device r, z [N][R]; precision as in smr_matvec. */
+int smr_precond(smr_ctx* ctx, int R, const void* r, void* z, int precision, void* stream);
+
+typedef struct {
+  double tol;      /* true relative residual ||b - Z x|| / ||b|| target [1e-4] */
+  int maxit;       /* maximum inner iterations in total [2000]                 */
+  int restart;     /* Krylov dimension before restart; 0 = maxit [0]           */
+  int precond;     /* SMR_PRECOND_* [SMR_PRECOND_BLOCKDIAG]                    */
+  int precision;   /* SMR_PREC_FP64: plain GMRES on the FP64 product;
+                      SMR_PREC_FP32: iterative refinement, outer residual with
+                      the FP64 product, inner flexible GMRES on the FP32
+                      product, FP64 Arnoldi/Givens throughout [FP64]          */
+  int max_outer;   /* refinement steps for SMR_PREC_FP32 [8]                   */
+  int use_x0;      /* 1: x holds the initial guess on entry; 0: start at 0     */
+} smr_solve_opts;
+
+typedef struct {
+  int iters;            /* Arnoldi steps (one product each)                    */
+  int matvecs_fp64;     /* FP64 products incl. true-residual checks            */
+  int matvecs_fp32;     /* FP32 products                                       */
+  int outer;            /* refinement steps (SMR_PREC_FP32)                    */
+  double resid_true;    /* max over r of ||b - Z_64 x|| / ||b|| at exit        */
+  double seconds;       /* wall time of the call                               */
+} smr_solve_stats;
+
+void smr_default_solve_opts(smr_solve_opts* o);
+
+/* Solve Z x = b for R right-hand sides with right-preconditioned GMRES
+ * (Sec. V, stage v).  device b, x [N][R].  The R systems run in lockstep,
+ * one R-column product per Arnoldi step; each stops updating once its own
+ * true residual meets tol.  Returns SMR_E_NOT_CONVERGED (x still holds the
+ * last iterate) if maxit is reached first.  stats may be NULL. */
+int smr_solve(smr_ctx* ctx, int R, const void* b, void* x, const smr_solve_opts* opts,
+              smr_solve_stats* stats, void* stream);
+
+/* Scattered far-field amplitude F(rhat), E_s ~ F exp(-j k r)/r, at host unit
+ * directions dirs[n_dir][3] from device coefficients x[N][R]:
+ * F = (j k / 4 pi) [zeta (I - rr) J_hat - r x M_hat] with
+ * J_hat = int J exp(j k rhat . r') dS'.  Writes device F[n_dir][3][R]
+ * (Cartesian components). */
+int smr_far_field(smr_ctx* ctx, int R, const void* x, int n_dir, const double* dirs,
+                  void* F, void* stream);
+
+/* Scattered E and H at host points pts[n_pt][3] (outside every particle) by
+ * direct surface quadrature with the full Green's dyadic:
+ * E = -zeta L{J} + K{M}, H = -K{J} - L{M}/zeta.  Writes device
+ * EH[n_pt][6][R] (Ex, Ey, Ez, Hx, Hy, Hz). */
+int smr_near_field(smr_ctx* ctx, int R, const void* x, int n_pt, const double* pts,
+                   void* EH, void* stream);
+
+/* Debug and parity access (host outputs, layouts as the oracle's):
+ *  smr_copy_pattern: receiving patterns of a shape, [n_psi][2][K_0] complex
+ *    (theta and phi components of Eq. 26 on the level-0 grid);
+ *  smr_copy_translation: T_L(khat, X) of Eq. 23 at level s for the lattice
+ *    offset X = (dx, dy) x box size, [K_s] complex (FP64 table);
+ *  smr_copy_near_block: the stored near block for (shape_m, shape_n, dx, dy)
+ *    (dx = dy = 0: self block), [2 n_psi][2 n_psi] complex row-major;
+ *  smr_copy_level: level-s outgoing (kind 0) or incoming (kind 1) spectra of
+ *    the last product, [n_box][K_s][4][R] complex, in FP64. */
+int smr_copy_pattern(smr_ctx* ctx, int shape, double* out);
+int smr_copy_translation(smr_ctx* ctx, int level, int dx, int dy, double* out);
+int smr_copy_near_block(smr_ctx* ctx, int shape_m, int shape_n, int dx, int dy, double* out);
+int smr_copy_level(smr_ctx* ctx, int level, int kind, double* out, size_t n_doubles);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SMR_H */

@@ -1,0 +1,715 @@
+// C ABI of libsmr (declared in include/smr.h): context, scene setup and the
+// entry points.  Scene setup builds the quadtree of Sec. IV (each particle its
+// own finest group, parents = 2x2 children), the interaction lists, the
+// k-space grids of Sec. V, the 4x4 Lagrange interpolation taps and their
+// weighted adjoint, and then calls the FP64 table generators on the GPU.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <tuple>
+
+#include "smr_internal.h"
+
+using namespace smr;
+
+struct smr_ctx {
+  Ctx c;
+};
+
+namespace {
+
+const double PI = 3.14159265358979323846;
+
+int fail(Ctx* c, int code, const std::string& msg) {
+  c->err = msg;
+  return code;
+}
+
+template <typename T> void dfree(T*& p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+void free_scene(Ctx* c) {
+  for (auto& L : c->lev) {
+    dfree(L.d_khat); dfree(L.d_w); dfree(L.d_il_ptr); dfree(L.d_il_src); dfree(L.d_il_off);
+    dfree(L.d_T64); dfree(L.d_T32); dfree(L.d_parent); dfree(L.d_quad); dfree(L.d_ch_ptr);
+    dfree(L.d_ch_idx); dfree(L.d_ch_quad); dfree(L.d_th_src); dfree(L.d_th_refl); dfree(L.d_th_w64);
+    dfree(L.d_th_w32); dfree(L.d_ph_src); dfree(L.d_ph_w64); dfree(L.d_ph_w32); dfree(L.d_shift64);
+    dfree(L.d_shift32); dfree(L.d_ant_ptr); dfree(L.d_ant_idx); dfree(L.d_ant_w64); dfree(L.d_ant_w32);
+    if (L.d_out) cudaFree(L.d_out);
+    if (L.d_in) cudaFree(L.d_in);
+    L.d_out = L.d_in = nullptr;
+  }
+  c->lev.clear();
+  dfree(c->d_modes); dfree(c->d_rq); dfree(c->d_P64); dfree(c->d_P32); dfree(c->d_sid);
+  dfree(c->d_centres); dfree(c->d_dshift); dfree(c->d_nr_ptr); dfree(c->d_nr_col); dfree(c->d_nr_blk);
+  dfree(c->d_B64); dfree(c->d_B32); dfree(c->d_Pinv64); dfree(c->d_Pinv32); dfree(c->d_pc_ptr);
+  dfree(c->d_pc_col); dfree(c->d_pc_blk); dfree(c->d_tmp);
+  c->tmp_elems = 0;
+  c->spec_R = 0;
+  c->spec_prec = -1;
+  c->have_scene = false;
+}
+
+// truncation order at level s (see smr_opts.level_rule)
+int truncation(const Ctx* c, int s) {
+  if (s == 0) return c->opts.L0;
+  if (c->opts.level_rule == SMR_LRULE_DOUBLE) return c->opts.L0 << s;
+  double kd = c->k * std::sqrt(2.0) * c->opts.pitch * (double)(1 << s);
+  return (int)std::ceil(kd + 1.8 * std::pow(c->opts.digits, 2.0 / 3.0) * std::cbrt(kd));
+}
+
+void make_grid(Level& L) {
+  std::vector<double> x, w;
+  hm::gauss_legendre(L.L + 1, x, w);
+  L.nth = L.L + 1;
+  L.nph = 2 * L.L + 2;
+  L.K = L.nth * L.nph;
+  L.khat.resize(3 * (size_t)L.K);
+  L.w.resize(L.K);
+  for (int i = 0; i < L.nth; ++i) {
+    double th = std::acos(x[i]), st = std::sin(th), ct = std::cos(th);
+    for (int j = 0; j < L.nph; ++j) {
+      double ph = 2.0 * PI * j / L.nph;
+      int k = i * L.nph + j;
+      L.khat[3 * k] = st * std::cos(ph);
+      L.khat[3 * k + 1] = st * std::sin(ph);
+      L.khat[3 * k + 2] = ct;
+      L.w[k] = w[i] * 2.0 * PI / L.nph;
+    }
+  }
+}
+
+std::vector<double> grid_theta(const Level& L) {
+  std::vector<double> x, w, th(L.nth);
+  hm::gauss_legendre(L.nth, x, w);
+  for (int i = 0; i < L.nth; ++i) th[i] = std::acos(x[i]);
+  return th;
+}
+
+void lagrange4(const double* nodes, double t, double* out) {
+  for (int a = 0; a < 4; ++a) {
+    double v = 1.0;
+    for (int b = 0; b < 4; ++b)
+      if (b != a) v *= (t - nodes[b]) / (nodes[a] - nodes[b]);
+    out[a] = v;
+  }
+}
+
+// 4x4 Lagrange taps from the child grid C to the parent grid P; the stencil
+// in theta is reflected through the poles, (-theta, phi) = (theta, phi + pi),
+// where both spherical components change sign.
+int build_interp(Ctx* c, Level& C, const Level& P) {
+  std::vector<double> thc = grid_theta(C), thp = grid_theta(P);
+  int ntc = C.nth;
+  std::vector<int> tsrc(4 * P.nth), trefl(4 * P.nth), psrc(4 * P.nph);
+  std::vector<double> tw(4 * P.nth), pw(4 * P.nph);
+  for (int tp = 0; tp < P.nth; ++tp) {
+    double t = thp[tp];
+    int i0 = (int)(std::upper_bound(thc.begin(), thc.end(), t) - thc.begin()) - 1;
+    double nodes[4];
+    for (int a = 0; a < 4; ++a) {
+      int i = i0 - 1 + a;
+      if (i < 0) { nodes[a] = -thc[-1 - i]; tsrc[4 * tp + a] = -1 - i; trefl[4 * tp + a] = 1; }
+      else if (i >= ntc) {
+        nodes[a] = 2.0 * PI - thc[2 * ntc - 1 - i];
+        tsrc[4 * tp + a] = 2 * ntc - 1 - i;
+        trefl[4 * tp + a] = 1;
+      } else { nodes[a] = thc[i]; tsrc[4 * tp + a] = i; trefl[4 * tp + a] = 0; }
+    }
+    lagrange4(nodes, t, &tw[4 * tp]);
+  }
+  double dphi = 2.0 * PI / C.nph;
+  for (int jp = 0; jp < P.nph; ++jp) {
+    double f = 2.0 * PI * jp / P.nph;
+    int j0 = (int)std::floor(f / dphi);
+    double nodes[4];
+    for (int b = 0; b < 4; ++b) {
+      int j = j0 - 1 + b;
+      nodes[b] = j * dphi;
+      psrc[4 * jp + b] = ((j % C.nph) + C.nph) % C.nph;
+    }
+    lagrange4(nodes, f, &pw[4 * jp]);
+  }
+  std::vector<float> tw32(tw.begin(), tw.end()), pw32(pw.begin(), pw.end());
+  int rc;
+  if ((rc = upload(c, &C.d_th_src, tsrc)) || (rc = upload(c, &C.d_th_refl, trefl)) ||
+      (rc = upload(c, &C.d_th_w64, tw)) || (rc = upload(c, &C.d_th_w32, tw32)) ||
+      (rc = upload(c, &C.d_ph_src, psrc)) || (rc = upload(c, &C.d_ph_w64, pw)) ||
+      (rc = upload(c, &C.d_ph_w32, pw32)))
+    return rc;
+  // weighted adjoint A = W_c^{-1} I^T W_p as CSR over child points
+  std::vector<int> cnt(C.K + 1, 0);
+  int half = C.nph / 2;
+  auto child_of = [&](int tp, int jp, int a, int b) {
+    int row = tsrc[4 * tp + a];
+    int col = psrc[4 * jp + b];
+    if (trefl[4 * tp + a]) col = (col + half) % C.nph;
+    return row * C.nph + col;
+  };
+  for (int tp = 0; tp < P.nth; ++tp)
+    for (int jp = 0; jp < P.nph; ++jp)
+      for (int a = 0; a < 4; ++a)
+        for (int b = 0; b < 4; ++b) cnt[child_of(tp, jp, a, b) + 1]++;
+  for (int k = 0; k < C.K; ++k) cnt[k + 1] += cnt[k];
+  long long nnz = cnt[C.K];
+  std::vector<int> idx(nnz), fill(cnt.begin(), cnt.end() - 1);
+  std::vector<double> val(nnz);
+  for (int tp = 0; tp < P.nth; ++tp)
+    for (int jp = 0; jp < P.nph; ++jp) {
+      int kp = tp * P.nph + jp;
+      for (int a = 0; a < 4; ++a)
+        for (int b = 0; b < 4; ++b) {
+          int kc = child_of(tp, jp, a, b);
+          double sg = trefl[4 * tp + a] ? -1.0 : 1.0;
+          int e = fill[kc]++;
+          idx[e] = kp;
+          val[e] = sg * tw[4 * tp + a] * pw[4 * jp + b] * P.w[kp] / C.w[kc];
+        }
+    }
+  std::vector<float> val32(val.begin(), val.end());
+  C.ant_nnz = nnz;
+  if ((rc = upload(c, &C.d_ant_ptr, cnt)) || (rc = upload(c, &C.d_ant_idx, idx)) ||
+      (rc = upload(c, &C.d_ant_w64, val)) || (rc = upload(c, &C.d_ant_w32, val32)))
+    return rc;
+  // shift tables exp(j k khat_p . (c_child - c_parent)), child offset (+-1/2) x child box
+  std::vector<double2> sh(4 * (size_t)P.K);
+  std::vector<float2> sh32(4 * (size_t)P.K);
+  for (int q = 0; q < 4; ++q) {
+    double dx = ((q & 1) - 0.5) * C.box, dy = ((q >> 1) - 0.5) * C.box;
+    for (int k = 0; k < P.K; ++k) {
+      double ph = c->k * (P.khat[3 * k] * dx + P.khat[3 * k + 1] * dy);
+      sh[(size_t)q * P.K + k] = make_double2(std::cos(ph), std::sin(ph));
+      sh32[(size_t)q * P.K + k] = make_float2((float)std::cos(ph), (float)std::sin(ph));
+    }
+  }
+  if ((rc = upload(c, &C.d_shift64, sh)) || (rc = upload(c, &C.d_shift32, sh32))) return rc;
+  return SMR_OK;
+}
+
+int set_scene(Ctx* c, int p, const double* centres, const int* shape_ids, const double* eps_in,
+              const double* mu_in, const double* eps_out, const double* mu_out) {
+  if (p <= 0 || !centres || !shape_ids) return fail(c, SMR_E_INVALID_ARG, "p > 0 and host arrays required");
+  if (c->shapes.empty()) return fail(c, SMR_E_SHAPE, "no shapes registered");
+  if (eps_in[1] != 0 || mu_in[1] != 0 || eps_out[1] != 0 || mu_out[1] != 0 || eps_in[0] <= 0 ||
+      mu_in[0] <= 0 || eps_out[0] <= 0 || mu_out[0] <= 0)
+    return fail(c, SMR_E_INVALID_ARG, "only real positive permittivity/permeability are supported");
+  free_scene(c);
+  int npsi = c->shapes[0].n_psi();
+  for (auto& s : c->shapes)
+    if (s.n_psi() != npsi) return fail(c, SMR_E_SHAPE, "all shapes must share n_perp + n_par");
+  c->p = p;
+  c->npsi = npsi;
+  c->S = (int)c->shapes.size();
+  double lam = c->opts.wavelength;
+  c->k = 2.0 * PI / lam * std::sqrt(eps_out[0] * mu_out[0]);
+  c->zeta = std::sqrt(mu_out[0] / eps_out[0]);
+  c->k_in = 2.0 * PI / lam * std::sqrt(eps_in[0] * mu_in[0]);
+  c->zeta_in = std::sqrt(mu_in[0] / eps_in[0]);
+  c->centres.assign(centres, centres + 3 * (size_t)p);
+  c->sid.assign(shape_ids, shape_ids + p);
+  for (int i = 0; i < p; ++i)
+    if (c->sid[i] < 0 || c->sid[i] >= c->S) return fail(c, SMR_E_SHAPE, "shape id out of range");
+  double pitch = c->opts.pitch;
+  // lattice indices and finest-box offsets
+  double ox = 1e300, oy = 1e300, zs = 0;
+  for (int i = 0; i < p; ++i) {
+    ox = std::min(ox, centres[3 * i]);
+    oy = std::min(oy, centres[3 * i + 1]);
+    zs += centres[3 * i + 2];
+  }
+  c->origin[0] = ox;
+  c->origin[1] = oy;
+  c->z0 = zs / p;
+  c->pi.resize(p);
+  c->pj.resize(p);
+  std::map<std::pair<int, int>, int> idx0;
+  std::vector<double> dsh(3 * (size_t)p);
+  int anyd = 0;
+  for (int i = 0; i < p; ++i) {
+    double fx = (centres[3 * i] - ox) / pitch, fy = (centres[3 * i + 1] - oy) / pitch;
+    int ix = (int)std::lround(fx), iy = (int)std::lround(fy);
+    if (std::fabs(fx - ix) > 1e-6 || std::fabs(fy - iy) > 1e-6 ||
+        std::fabs(centres[3 * i + 2] - c->z0) > 1e-9 * pitch)
+      return fail(c, SMR_E_INVALID_ARG, "centres must lie on a square lattice of spacing opts.pitch in one plane");
+    if (!idx0.emplace(std::make_pair(ix, iy), i).second)
+      return fail(c, SMR_E_INVALID_ARG, "two particles share a lattice cell");
+    c->pi[i] = ix;
+    c->pj[i] = iy;
+    dsh[3 * i] = centres[3 * i] - (ox + ix * pitch);
+    dsh[3 * i + 1] = centres[3 * i + 1] - (oy + iy * pitch);
+    dsh[3 * i + 2] = centres[3 * i + 2] - c->z0;
+    if (dsh[3 * i] != 0 || dsh[3 * i + 1] != 0 || dsh[3 * i + 2] != 0) anyd = 1;
+  }
+  // check no sphere overlaps its neighbours on the lattice
+  for (auto& s : c->shapes)
+    if (2 * s.a >= pitch) return fail(c, SMR_E_INVALID_ARG, "sphere diameter must be below the pitch");
+  c->any_dshift = anyd;
+  // ---- levels
+  std::vector<int> bi(c->pi), bj(c->pj);
+  std::vector<Level> levs;
+  for (int s = 0;; ++s) {
+    Level L;
+    L.box = pitch * (double)(1 << s);
+    if (s == 0) {
+      L.bi = bi;
+      L.bj = bj;
+    } else {
+      std::vector<std::pair<int, int>> keys;
+      for (size_t t = 0; t < bi.size(); ++t) keys.push_back({bj[t], bi[t]});
+      std::sort(keys.begin(), keys.end());
+      keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
+      for (auto& kv : keys) { L.bi.push_back(kv.second); L.bj.push_back(kv.first); }
+    }
+    L.nbox = (int)L.bi.size();
+    std::map<std::pair<int, int>, int> index;
+    for (int b = 0; b < L.nbox; ++b) index[{L.bi[b], L.bj[b]}] = b;
+    L.centre.resize(3 * (size_t)L.nbox);
+    double half = ((double)(1 << s) - 1.0) / 2.0;
+    for (int b = 0; b < L.nbox; ++b) {
+      L.centre[3 * b] = ox + ((double)L.bi[b] * (1 << s) + half) * pitch;
+      L.centre[3 * b + 1] = oy + ((double)L.bj[b] * (1 << s) + half) * pitch;
+      L.centre[3 * b + 2] = c->z0;
+    }
+    // interaction list: parents adjacent (or equal), boxes not adjacent
+    std::map<std::pair<int, int>, int> offid;
+    L.il_ptr.assign(1, 0);
+    for (int b = 0; b < L.nbox; ++b) {
+      int ix = L.bi[b], iy = L.bj[b], px = ix >> 1, py = iy >> 1;
+      for (int qx = px - 1; qx <= px + 1; ++qx)
+        for (int qy = py - 1; qy <= py + 1; ++qy)
+          for (int cx = 2 * qx; cx <= 2 * qx + 1; ++cx)
+            for (int cy = 2 * qy; cy <= 2 * qy + 1; ++cy) {
+              if (std::max(std::abs(cx - ix), std::abs(cy - iy)) <= 1) continue;
+              auto it = index.find({cx, cy});
+              if (it == index.end()) continue;
+              std::pair<int, int> o(ix - cx, iy - cy);
+              auto f = offid.find(o);
+              int oid;
+              if (f == offid.end()) {
+                oid = (int)L.off_dx.size();
+                offid[o] = oid;
+                L.off_dx.push_back(o.first);
+                L.off_dy.push_back(o.second);
+              } else {
+                oid = f->second;
+              }
+              L.il_src.push_back(it->second);
+              L.il_off.push_back(oid);
+            }
+      L.il_ptr.push_back((int)L.il_src.size());
+    }
+    int minx = *std::min_element(L.bi.begin(), L.bi.end()), maxx = *std::max_element(L.bi.begin(), L.bi.end());
+    int miny = *std::min_element(L.bj.begin(), L.bj.end()), maxy = *std::max_element(L.bj.begin(), L.bj.end());
+    levs.push_back(std::move(L));
+    if (std::max(maxx - minx, maxy - miny) <= 1) break;
+    for (size_t t = 0; t < bi.size(); ++t) { bi[t] >>= 1; bj[t] >>= 1; }
+    if (s > 20) return fail(c, SMR_E_INVALID_ARG, "tree too deep");
+  }
+  while (levs.size() > 1 && levs.back().il_src.empty()) levs.pop_back();
+  c->nlev = (int)levs.size();
+  if (c->nlev > 16) return fail(c, SMR_E_INVALID_ARG, "more than 16 levels");
+  // parents / children
+  for (int s = 0; s + 1 < c->nlev; ++s) {
+    Level &C = levs[s], &P = levs[s + 1];
+    std::map<std::pair<int, int>, int> pidx;
+    for (int b = 0; b < P.nbox; ++b) pidx[{P.bi[b], P.bj[b]}] = b;
+    C.parent.resize(C.nbox);
+    C.quad.resize(C.nbox);
+    std::vector<std::vector<std::pair<int, int>>> ch(P.nbox);
+    for (int b = 0; b < C.nbox; ++b) {
+      int B = pidx[{C.bi[b] >> 1, C.bj[b] >> 1}];
+      C.parent[b] = B;
+      C.quad[b] = (C.bi[b] & 1) + 2 * (C.bj[b] & 1);
+      ch[B].push_back({b, C.quad[b]});
+    }
+    P.ch_ptr.assign(1, 0);
+    for (int B = 0; B < P.nbox; ++B) {
+      for (auto& e : ch[B]) { P.ch_idx.push_back(e.first); P.ch_quad.push_back(e.second); }
+      P.ch_ptr.push_back((int)P.ch_idx.size());
+    }
+  }
+  c->lev = std::move(levs);
+  for (int s = 0; s < c->nlev; ++s) {
+    Level& L = c->lev[s];
+    L.L = truncation(c, s);
+    make_grid(L);
+    int rc;
+    if ((rc = upload(c, &L.d_khat, L.khat)) || (rc = upload(c, &L.d_w, L.w)) ||
+        (rc = upload(c, &L.d_il_ptr, L.il_ptr)) || (rc = upload(c, &L.d_il_src, L.il_src)) ||
+        (rc = upload(c, &L.d_il_off, L.il_off)) || (rc = upload(c, &L.d_parent, L.parent)) ||
+        (rc = upload(c, &L.d_quad, L.quad)) || (rc = upload(c, &L.d_ch_ptr, L.ch_ptr)) ||
+        (rc = upload(c, &L.d_ch_idx, L.ch_idx)) || (rc = upload(c, &L.d_ch_quad, L.ch_quad)))
+      return rc;
+  }
+  for (int s = 0; s + 1 < c->nlev; ++s) {
+    int rc = build_interp(c, c->lev[s], c->lev[s + 1]);
+    if (rc) return rc;
+  }
+  // ---- near lists: self + 8 lattice neighbours; block keys (sm, sn, dx, dy)
+  c->blk_sm.clear(); c->blk_sn.clear(); c->blk_dx.clear(); c->blk_dy.clear();
+  for (int s = 0; s < c->S; ++s) {
+    c->blk_sm.push_back(s); c->blk_sn.push_back(s); c->blk_dx.push_back(0); c->blk_dy.push_back(0);
+  }
+  std::map<std::tuple<int, int, int, int>, int> bkey;
+  c->nr_ptr.assign(1, 0);
+  c->nr_col.clear();
+  c->nr_blk.clear();
+  for (int mu = 0; mu < p; ++mu) {
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dx = -1; dx <= 1; ++dx) {
+        auto it = idx0.find({c->pi[mu] + dx, c->pj[mu] + dy});
+        if (it == idx0.end()) continue;
+        int nu = it->second, b;
+        if (nu == mu) {
+          b = c->sid[mu];
+        } else {
+          auto key = std::make_tuple(c->sid[mu], c->sid[nu], -dx, -dy);
+          auto f = bkey.find(key);
+          if (f == bkey.end()) {
+            b = (int)c->blk_sm.size();
+            bkey[key] = b;
+            c->blk_sm.push_back(c->sid[mu]); c->blk_sn.push_back(c->sid[nu]);
+            c->blk_dx.push_back(-dx); c->blk_dy.push_back(-dy);
+          } else {
+            b = f->second;
+          }
+        }
+        c->nr_col.push_back(nu);
+        c->nr_blk.push_back(b);
+      }
+    c->nr_ptr.push_back((int)c->nr_col.size());
+  }
+  c->nblk = (int)c->blk_sm.size();
+  std::vector<int> pcp(p + 1), pcc(p), pcb(p);
+  for (int i = 0; i < p; ++i) { pcp[i] = i; pcc[i] = i; pcb[i] = c->sid[i]; }
+  pcp[p] = p;
+  std::vector<double> cen(c->centres);
+  int rc;
+  if ((rc = upload(c, &c->d_sid, c->sid)) || (rc = upload(c, &c->d_centres, cen)) ||
+      (rc = upload(c, &c->d_dshift, dsh)) || (rc = upload(c, &c->d_nr_ptr, c->nr_ptr)) ||
+      (rc = upload(c, &c->d_nr_col, c->nr_col)) || (rc = upload(c, &c->d_nr_blk, c->nr_blk)) ||
+      (rc = upload(c, &c->d_pc_ptr, pcp)) || (rc = upload(c, &c->d_pc_col, pcc)) ||
+      (rc = upload(c, &c->d_pc_blk, pcb)))
+    return rc;
+  if ((rc = build_modes(c)) || (rc = build_patterns(c)) || (rc = build_translations(c)) ||
+      (rc = build_near(c)))
+    return rc;
+  SMR_CUDA(c, cudaDeviceSynchronize());
+  c->have_scene = true;
+  return SMR_OK;
+}
+
+bool check_scene(Ctx* c) {
+  if (!c->have_scene) {
+    c->err = "no scene: call smr_set_scene first";
+    return false;
+  }
+  return true;
+}
+
+long long n_unknowns(const Ctx* c) { return 2LL * c->npsi * c->p; }
+
+int tmp_buffer(Ctx* c, size_t elems) {
+  if (c->tmp_elems >= elems) return SMR_OK;
+  dfree(c->d_tmp);
+  SMR_CUDA(c, cudaMalloc((void**)&c->d_tmp, elems * sizeof(double2)));
+  c->tmp_elems = elems;
+  return SMR_OK;
+}
+
+}  // namespace
+
+// ====================================================================== ABI
+extern "C" {
+
+void smr_default_opts(smr_opts* o) {
+  if (!o) return;
+  o->device = 0;
+  o->wavelength = 1.0;
+  o->pitch = 0.5;
+  o->L0 = 10;
+  o->level_rule = SMR_LRULE_FORMULA;
+  o->digits = 3.0;
+  o->n_theta = 16;
+  o->n_phi = 32;
+}
+
+void smr_default_solve_opts(smr_solve_opts* o) {
+  if (!o) return;
+  o->tol = 1e-4;
+  o->maxit = 2000;
+  o->restart = 0;
+  o->precond = SMR_PRECOND_BLOCKDIAG;
+  o->precision = SMR_PREC_FP64;
+  o->max_outer = 8;
+  o->use_x0 = 0;
+}
+
+int smr_create(smr_ctx** out, const smr_opts* opts) {
+  if (!out) return SMR_E_INVALID_ARG;
+  *out = nullptr;
+  smr_opts o;
+  smr_default_opts(&o);
+  if (opts) o = *opts;
+  if (o.L0 < 2 || o.pitch <= 0 || o.wavelength <= 0 || o.n_theta < 2 || o.n_phi < 4 || o.digits <= 0)
+    return SMR_E_INVALID_ARG;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || o.device < 0 || o.device >= ndev) return SMR_E_CUDA;
+  if (cudaSetDevice(o.device) != cudaSuccess) return SMR_E_CUDA;
+  smr_ctx* h = new (std::nothrow) smr_ctx();
+  if (!h) return SMR_E_OOM;
+  h->c.opts = o;
+  h->c.device = o.device;
+  *out = h;
+  return SMR_OK;
+}
+
+int smr_destroy(smr_ctx* h) {
+  if (!h) return SMR_OK;
+  cudaSetDevice(h->c.device);
+  free_scene(&h->c);
+  if (h->c.d_red) cudaFree(h->c.d_red);
+  if (h->c.h_red) cudaFreeHost(h->c.h_red);
+  delete h;
+  return SMR_OK;
+}
+
+const char* smr_last_error(const smr_ctx* h) { return h ? h->c.err.c_str() : "null context"; }
+
+int smr_add_sphere(smr_ctx* h, double radius, int n_perp, int n_par, int* shape_id) {
+  if (!h) return SMR_E_INVALID_ARG;
+  Ctx* c = &h->c;
+  if (!(radius > 0) || n_perp < 0 || n_par < 0 || n_perp + n_par < 1 || n_perp + n_par > 128)
+    return fail(c, SMR_E_INVALID_ARG, "radius > 0 and 1 <= n_perp + n_par <= 128 required");
+  c->shapes.push_back(Shape{radius, n_perp, n_par});
+  if (shape_id) *shape_id = (int)c->shapes.size() - 1;
+  return SMR_OK;
+}
+
+int smr_set_scene(smr_ctx* h, int p, const double* centres, const int* shape_ids, const double eps_in[2],
+                  const double mu_in[2], const double eps_out[2], const double mu_out[2]) {
+  if (!h || !eps_in || !mu_in || !eps_out || !mu_out) return SMR_E_INVALID_ARG;
+  Ctx* c = &h->c;
+  if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, SMR_E_CUDA, "cudaSetDevice");
+  int rc = set_scene(c, p, centres, shape_ids, eps_in, mu_in, eps_out, mu_out);
+  if (rc) {
+    std::string msg = c->err;
+    free_scene(c);
+    c->err = msg;
+  }
+  return rc;
+}
+
+int smr_info(smr_ctx* h, smr_info_t* info) {
+  if (!h || !info) return SMR_E_INVALID_ARG;
+  Ctx* c = &h->c;
+  if (!check_scene(c)) return SMR_E_STATE;
+  std::memset(info, 0, sizeof(*info));
+  info->p = c->p;
+  info->n_psi = c->npsi;
+  info->n_shapes = c->S;
+  info->n_levels = c->nlev;
+  info->n_unknowns = n_unknowns(c);
+  double bytes = 0;
+  for (int s = 0; s < c->nlev; ++s) {
+    const Level& L = c->lev[s];
+    info->L[s] = L.L;
+    info->K[s] = L.K;
+    info->n_box[s] = L.nbox;
+    info->n_il[s] = (int)L.il_src.size();
+    bytes += 2.0 * L.nbox * L.K * 4 * 16 + (double)L.off_dx.size() * L.K * 24 + L.ant_nnz * 16;
+  }
+  info->n_near_pairs = (long long)c->nr_col.size();
+  info->n_near_blocks = c->nblk;
+  bytes += (double)c->nblk * 4 * c->npsi * c->npsi * 24;
+  info->device_bytes = bytes;
+  return SMR_OK;
+}
+
+int smr_rhs_plane_waves(smr_ctx* h, int R, const double* khat, const double* pol, void* b, void* stream) {
+  if (!h || R <= 0 || !khat || !pol || !b) return SMR_E_INVALID_ARG;
+  Ctx* c = &h->c;
+  if (!check_scene(c)) return SMR_E_STATE;
+  cudaSetDevice(c->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<double> kh(khat, khat + 3 * (size_t)R);
+  std::vector<double2> pl(3 * (size_t)R);
+  for (int i = 0; i < 3 * R; ++i) pl[i] = make_double2(pol[2 * i], pol[2 * i + 1]);
+  double* d_k = nullptr;
+  double2* d_p = nullptr;
+  int rc;
+  if ((rc = upload(c, &d_k, kh)) || (rc = upload(c, &d_p, pl))) return rc;
+  rc = launch_rhs(c, R, d_k, d_p, (double2*)b, st);
+  cudaStreamSynchronize(st);
+  cudaFree(d_k);
+  cudaFree(d_p);
+  return rc;
+}
+
+int smr_matvec(smr_ctx* h, int R, const void* x, void* y, int precision, void* stream) {
+  if (!h || R <= 0 || R > 256 || !x || !y) return SMR_E_INVALID_ARG;
+  Ctx* c = &h->c;
+  if (!check_scene(c)) return SMR_E_STATE;
+  if (precision != SMR_PREC_FP64 && precision != SMR_PREC_FP32)
+    return fail(c, SMR_E_INVALID_ARG, "precision must be SMR_PREC_FP64 or SMR_PREC_FP32");
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc = run_near(c, R, precision, (const double2*)x, (double2*)y, st);
+  if (rc) return rc;
+  return run_far(c, R, precision, (const double2*)x, (double2*)y, true, st);
+}
+
+int smr_matvec_parts(smr_ctx* h, int R, const void* x, void* y_near, void* y_far, int precision,
+                     void* stream) {
+  if (!h || R <= 0 || R > 256 || !x) return SMR_E_INVALID_ARG;
+  Ctx* c = &h->c;
+  if (!check_scene(c)) return SMR_E_STATE;
+  if (precision != SMR_PREC_FP64 && precision != SMR_PREC_FP32)
+    return fail(c, SMR_E_INVALID_ARG, "precision must be SMR_PREC_FP64 or SMR_PREC_FP32");
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc = SMR_OK;
+  if (y_near) rc = run_near(c, R, precision, (const double2*)x, (double2*)y_near, st);
+  if (rc) return rc;
+  if (y_far) rc = run_far(c, R, precision, (const double2*)x, (double2*)y_far, false, st);
+  return rc;
+}
+
+int smr_matvec_host(smr_ctx* h, int R, const double* x, double* y, int precision, void* stream) {
+  if (!h || R <= 0 || R > 256 || !x || !y) return SMR_E_INVALID_ARG;
+  Ctx* c = &h->c;
+  if (!check_scene(c)) return SMR_E_STATE;
+  cudaStream_t st = (cudaStream_t)stream;
+  size_t n = (size_t)n_unknowns(c) * R;
+  int rc = tmp_buffer(c, 2 * n);
+  if (rc) return rc;
+  double2* dx = c->d_tmp;
+  double2* dy = c->d_tmp + n;
+  SMR_CUDA(c, cudaMemcpyAsync(dx, x, n * sizeof(double2), cudaMemcpyHostToDevice, st));
+  rc = smr_matvec(h, R, dx, dy, precision, stream);
+  if (rc) return rc;
+  SMR_CUDA(c, cudaMemcpyAsync(y, dy, n * sizeof(double2), cudaMemcpyDeviceToHost, st));
+  SMR_CUDA(c, cudaStreamSynchronize(st));
+  return SMR_OK;
+}
+
+int smr_precond(smr_ctx* h, int R, const void* r, void* z, int precision, void* stream) {
+  if (!h || R <= 0 || R > 256 || !r || !z) return SMR_E_INVALID_ARG;
+  Ctx* c = &h->c;
+  if (!check_scene(c)) return SMR_E_STATE;
+  return run_precond(c, R, precision, (const double2*)r, (double2*)z, (cudaStream_t)stream);
+}
+
+int smr_solve(smr_ctx* h, int R, const void* b, void* x, const smr_solve_opts* opts, smr_solve_stats* stats,
+              void* stream) {
+  if (!h || R <= 0 || R > 256 || !b || !x) return SMR_E_INVALID_ARG;
+  Ctx* c = &h->c;
+  if (!check_scene(c)) return SMR_E_STATE;
+  smr_solve_opts o;
+  smr_default_solve_opts(&o);
+  if (opts) o = *opts;
+  if (o.precision != SMR_PREC_FP64 && o.precision != SMR_PREC_FP32)
+    return fail(c, SMR_E_INVALID_ARG, "precision must be SMR_PREC_FP64 or SMR_PREC_FP32");
+  if (o.precond != SMR_PRECOND_NONE && o.precond != SMR_PRECOND_BLOCKDIAG)
+    return fail(c, SMR_E_INVALID_ARG, "unknown preconditioner");
+  return solve(c, R, (const double2*)b, (double2*)x, &o, stats, (cudaStream_t)stream);
+}
+
+int smr_far_field(smr_ctx* h, int R, const void* x, int n_dir, const double* dirs, void* F, void* stream) {
+  if (!h || R <= 0 || !x || n_dir <= 0 || !dirs || !F) return SMR_E_INVALID_ARG;
+  Ctx* c = &h->c;
+  if (!check_scene(c)) return SMR_E_STATE;
+  std::vector<double> d(dirs, dirs + 3 * (size_t)n_dir);
+  double* dd = nullptr;
+  int rc = upload(c, &dd, d);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  rc = launch_far_field(c, R, (const double2*)x, n_dir, dd, (double2*)F, st);
+  cudaStreamSynchronize(st);
+  cudaFree(dd);
+  return rc;
+}
+
+int smr_near_field(smr_ctx* h, int R, const void* x, int n_pt, const double* pts, void* EH, void* stream) {
+  if (!h || R <= 0 || !x || n_pt <= 0 || !pts || !EH) return SMR_E_INVALID_ARG;
+  Ctx* c = &h->c;
+  if (!check_scene(c)) return SMR_E_STATE;
+  std::vector<double> d(pts, pts + 3 * (size_t)n_pt);
+  double* dd = nullptr;
+  int rc = upload(c, &dd, d);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  rc = launch_near_field(c, R, (const double2*)x, n_pt, dd, (double2*)EH, st);
+  cudaStreamSynchronize(st);
+  cudaFree(dd);
+  return rc;
+}
+
+int smr_copy_pattern(smr_ctx* h, int shape, double* out) {
+  if (!h || !out) return SMR_E_INVALID_ARG;
+  Ctx* c = &h->c;
+  if (!check_scene(c)) return SMR_E_STATE;
+  if (shape < 0 || shape >= c->S) return fail(c, SMR_E_SHAPE, "shape id out of range");
+  size_t n = (size_t)c->npsi * 2 * c->lev[0].K;
+  SMR_CUDA(c, cudaMemcpy(out, c->d_P64 + (size_t)shape * n, n * sizeof(double2), cudaMemcpyDeviceToHost));
+  return SMR_OK;
+}
+
+int smr_copy_translation(smr_ctx* h, int level, int dx, int dy, double* out) {
+  if (!h || !out) return SMR_E_INVALID_ARG;
+  Ctx* c = &h->c;
+  if (!check_scene(c)) return SMR_E_STATE;
+  if (level < 0 || level >= c->nlev) return fail(c, SMR_E_INVALID_ARG, "level out of range");
+  Level& L = c->lev[level];
+  for (size_t o = 0; o < L.off_dx.size(); ++o)
+    if (L.off_dx[o] == dx && L.off_dy[o] == dy) {
+      SMR_CUDA(c, cudaMemcpy(out, L.d_T64 + o * L.K, L.K * sizeof(double2), cudaMemcpyDeviceToHost));
+      return SMR_OK;
+    }
+  return fail(c, SMR_E_INVALID_ARG, "offset not in this level's interaction lists");
+}
+
+int smr_copy_near_block(smr_ctx* h, int sm, int sn, int dx, int dy, double* out) {
+  if (!h || !out) return SMR_E_INVALID_ARG;
+  Ctx* c = &h->c;
+  if (!check_scene(c)) return SMR_E_STATE;
+  int n2 = 2 * c->npsi;
+  for (int b = 0; b < c->nblk; ++b)
+    if (c->blk_sm[b] == sm && c->blk_sn[b] == sn && c->blk_dx[b] == dx && c->blk_dy[b] == dy) {
+      std::vector<double2> t((size_t)n2 * n2);
+      SMR_CUDA(c, cudaMemcpy(t.data(), c->d_B64 + (size_t)b * n2 * n2, t.size() * sizeof(double2),
+                             cudaMemcpyDeviceToHost));
+      for (int i = 0; i < n2; ++i)
+        for (int j = 0; j < n2; ++j) {
+          out[2 * ((size_t)i * n2 + j)] = t[(size_t)j * n2 + i].x;
+          out[2 * ((size_t)i * n2 + j) + 1] = t[(size_t)j * n2 + i].y;
+        }
+      return SMR_OK;
+    }
+  return fail(c, SMR_E_INVALID_ARG, "no such near block in this scene");
+}
+
+int smr_copy_level(smr_ctx* h, int level, int kind, double* out, size_t n_doubles) {
+  if (!h || !out) return SMR_E_INVALID_ARG;
+  Ctx* c = &h->c;
+  if (!check_scene(c)) return SMR_E_STATE;
+  if (level < 0 || level >= c->nlev || (kind != 0 && kind != 1))
+    return fail(c, SMR_E_INVALID_ARG, "level or kind out of range");
+  if (c->spec_prec < 0) return fail(c, SMR_E_STATE, "no product has run yet");
+  Level& L = c->lev[level];
+  size_t elems = (size_t)L.nbox * L.K * 4 * c->spec_R;
+  if (n_doubles < 2 * elems) return fail(c, SMR_E_INVALID_ARG, "output buffer too small");
+  const void* src = kind == 0 ? L.d_out : L.d_in;
+  cudaDeviceSynchronize();
+  if (c->spec_prec == SMR_PREC_FP64) {
+    SMR_CUDA(c, cudaMemcpy(out, src, elems * sizeof(double2), cudaMemcpyDeviceToHost));
+  } else {
+    std::vector<float2> t(elems);
+    SMR_CUDA(c, cudaMemcpy(t.data(), src, elems * sizeof(float2), cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < elems; ++i) { out[2 * i] = t[i].x; out[2 * i + 1] = t[i].y; }
+  }
+  return SMR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,204 @@
+// Internal declarations of libsmr: context, per-level tables, kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <complex>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/smr.h"
+
+namespace smr {
+
+typedef std::complex<double> cd;
+
+// ------------------------------------------------------------------ host math
+namespace hm {
+// n-point Gauss-Legendre rule on [-1,1], nodes descending (theta ascending).
+void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w);
+// Real orthonormal Y_lm (m >= 0, kind 0 = cos, 1 = sin) and its surface
+// gradient components dY/dtheta, (1/sin theta) dY/dphi.
+void real_ylm(int l, int m, int kind, double theta, double phi, double* Y, double* Yt, double* Yp);
+// Spherical Bessel j_l, y_l for l = 0..L at real x > 0 (Miller downward for j,
+// upward for y).
+void sph_bessel(int L, double x, std::vector<double>& j, std::vector<double>& y);
+// Riccati psi_l(x) = x j_l, xi_l(x) = x h^(2)_l and derivatives.
+void riccati(int l, double x, double* psi, double* dpsi, cd* xi, cd* dxi);
+// In-place inverse of an n x n complex row-major matrix (partial pivoting).
+bool invert(int n, std::vector<cd>& a);
+// Modes of a sphere shell list: (l, m, kind) for the first n modes.
+void mode_list(int n, std::vector<int>& l, std::vector<int>& m, std::vector<int>& kind);
+}  // namespace hm
+
+// ------------------------------------------------------------------ data
+struct Shape {
+  double a;
+  int n_perp, n_par;
+  int n_psi() const { return n_perp + n_par; }
+};
+
+struct Level {
+  int L = 0, K = 0, nth = 0, nph = 0, nbox = 0;
+  double box = 0;
+  std::vector<double> khat, w;          // [K][3], [K]
+  std::vector<int> bi, bj;               // box integer coordinates
+  std::vector<double> centre;            // [nbox][3]
+  std::vector<int> il_ptr, il_src, il_off;  // interaction list CSR by target box
+  std::vector<int> off_dx, off_dy;       // unique offsets (box units)
+  std::vector<int> parent, quad;         // to level s+1
+  std::vector<int> ch_ptr, ch_idx, ch_quad;  // children at level s-1 (s >= 1)
+  // device
+  double* d_khat = nullptr;
+  double* d_w = nullptr;
+  int* d_il_ptr = nullptr;
+  int* d_il_src = nullptr;
+  int* d_il_off = nullptr;
+  double2* d_T64 = nullptr;              // [noff][K]
+  float2* d_T32 = nullptr;
+  int* d_parent = nullptr;
+  int* d_quad = nullptr;
+  int* d_ch_ptr = nullptr;
+  int* d_ch_idx = nullptr;
+  int* d_ch_quad = nullptr;
+  // interpolation from this level (child) to s+1 (parent) -- stored on the child
+  int* d_th_src = nullptr;               // [nth_p][4] source theta row
+  int* d_th_refl = nullptr;              // [nth_p][4] 1 if reflected through a pole
+  double* d_th_w64 = nullptr;            // [nth_p][4]
+  float* d_th_w32 = nullptr;
+  int* d_ph_src = nullptr;               // [nph_p][4]
+  double* d_ph_w64 = nullptr;
+  float* d_ph_w32 = nullptr;
+  double2* d_shift64 = nullptr;          // [4][K_p] exp(j k khat_p.(c_c - c_p))
+  float2* d_shift32 = nullptr;
+  int* d_ant_ptr = nullptr;              // [K+1] weighted adjoint CSR (rows = this grid)
+  int* d_ant_idx = nullptr;              // parent point index
+  double* d_ant_w64 = nullptr;
+  float* d_ant_w32 = nullptr;
+  long long ant_nnz = 0;
+  // spectra (allocated for the current R and precision)
+  void* d_out = nullptr;
+  void* d_in = nullptr;
+  size_t spec_bytes = 0;
+};
+
+struct Ctx {
+  smr_opts opts;
+  std::string err;
+  int device = 0;
+  std::vector<Shape> shapes;
+  bool have_scene = false;
+  // scene
+  int p = 0, npsi = 0, S = 0, nlev = 0;
+  double k = 0, zeta = 1, k_in = 0, zeta_in = 1;
+  std::vector<double> centres;          // [p][3]
+  std::vector<int> sid;                 // [p]
+  std::vector<int> pi, pj;              // lattice indices
+  double origin[2] = {0, 0}, z0 = 0;
+  std::vector<Level> lev;
+  // surface rule (shared by all shapes, scaled by radius)
+  int Q = 0;
+  std::vector<double> rule_th, rule_ph, rule_w1;  // unit-sphere rule
+  double* d_modes = nullptr;            // [S][npsi][Q][4]: psi xyz, div
+  double* d_rq = nullptr;               // [S][Q][4]: point xyz, weight
+  // patterns [S][npsi][2][K0]
+  double2* d_P64 = nullptr;
+  float2* d_P32 = nullptr;
+  // particles
+  int* d_sid = nullptr;
+  double* d_centres = nullptr;          // [p][3]
+  double* d_dshift = nullptr;           // [p][3] r_mu - c_box (finest level)
+  int any_dshift = 0;
+  // near SpMV: CSR by particle, block ids; blocks stored transposed [nb][2n][2n]
+  std::vector<int> nr_ptr, nr_col, nr_blk;
+  int* d_nr_ptr = nullptr;
+  int* d_nr_col = nullptr;
+  int* d_nr_blk = nullptr;
+  int nblk = 0;
+  std::vector<int> blk_sm, blk_sn, blk_dx, blk_dy;  // key of each block
+  double2* d_B64 = nullptr;
+  float2* d_B32 = nullptr;
+  // preconditioner: inverse self blocks, transposed [S][2n][2n]
+  double2* d_Pinv64 = nullptr;
+  float2* d_Pinv32 = nullptr;
+  int* d_pc_ptr = nullptr;              // identity CSR for the block kernel
+  int* d_pc_col = nullptr;
+  int* d_pc_blk = nullptr;
+  // work buffers
+  int spec_R = 0, spec_prec = -1;
+  double2* d_tmp = nullptr;             // [N][R] scratch for split products
+  size_t tmp_elems = 0;
+  // solver scratch
+  void* d_sol = nullptr;
+  size_t sol_bytes = 0;
+  double* d_red = nullptr;              // reduction partials
+  size_t red_bytes = 0;
+  double* h_red = nullptr;              // pinned host mirror
+};
+
+// ------------------------------------------------------------------ helpers
+#define SMR_CUDA(ctx, call)                                                        \
+  do {                                                                             \
+    cudaError_t e_ = (call);                                                       \
+    if (e_ != cudaSuccess) {                                                       \
+      (ctx)->err = std::string(#call) + ": " + cudaGetErrorString(e_);             \
+      return SMR_E_CUDA;                                                           \
+    }                                                                              \
+  } while (0)
+
+#define SMR_LAUNCH(ctx)                                                            \
+  do {                                                                             \
+    cudaError_t e_ = cudaGetLastError();                                           \
+    if (e_ != cudaSuccess) {                                                       \
+      (ctx)->err = std::string("kernel launch: ") + cudaGetErrorString(e_);        \
+      return SMR_E_CUDA;                                                           \
+    }                                                                              \
+  } while (0)
+
+template <typename T>
+int upload(Ctx* c, T** dst, const std::vector<T>& src) {
+  if (*dst) cudaFree(*dst);
+  *dst = nullptr;
+  if (src.empty()) return SMR_OK;
+  SMR_CUDA(c, cudaMalloc((void**)dst, src.size() * sizeof(T)));
+  SMR_CUDA(c, cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return SMR_OK;
+}
+
+// ------------------------------------------------------------------ setup (k_setup.cu)
+int build_modes(Ctx* c);          // d_modes, d_rq (host evaluation, upload)
+int build_patterns(Ctx* c);       // d_P64 / d_P32 on the GPU (FP64)
+int build_translations(Ctx* c);   // per level d_T64 / d_T32 on the GPU (FP64)
+int build_near(Ctx* c);           // d_B64 / d_B32 on the GPU (FP64) + self blocks
+int launch_rhs(Ctx* c, int R, const double* d_khat, const double2* d_pol, double2* b,
+               cudaStream_t st);
+int launch_far_field(Ctx* c, int R, const double2* x, int nd, const double* d_dirs,
+                     double2* F, cudaStream_t st);
+int launch_near_field(Ctx* c, int R, const double2* x, int npt, const double* d_pts,
+                      double2* EH, cudaStream_t st);
+
+// ------------------------------------------------------------------ hot path (k_mlfma.cu)
+int ensure_spectra(Ctx* c, int R, int prec);
+int run_near(Ctx* c, int R, int prec, const double2* x, double2* y, cudaStream_t st);
+int run_far(Ctx* c, int R, int prec, const double2* x, double2* y, bool accumulate,
+            cudaStream_t st);
+int run_precond(Ctx* c, int R, int prec, const double2* r, double2* z, cudaStream_t st);
+
+// ------------------------------------------------------------------ linear algebra (k_linalg.cu)
+// h[j*R + r] = sum_i conj(V_j[i][r]) w[i][r] for j < J (V_j = V + j*ldv), FP64.
+int multidot(Ctx* c, int J, long long n, int R, const double2* V, long long ldv,
+             const double2* w, double2* h_host, cudaStream_t st);
+// w[i][r] -= sum_j V_j[i][r] h[j][r]   (h on the device, [J][R])
+int multi_axpy(Ctx* c, int J, long long n, int R, const double2* V, long long ldv,
+               const double2* d_h, double2* w, double sign, cudaStream_t st);
+// norms[r] = ||v[:, r]||_2
+int col_norms(Ctx* c, long long n, int R, const double2* v, double* norms_host, cudaStream_t st);
+// y[i][r] = a[r] * x[i][r] + b[r] * y[i][r]  (a, b complex per column, device)
+int col_axpby(long long n, int R, const double2* d_a, const double2* x, const double2* d_b,
+              double2* y, cudaStream_t st);
+
+int solve(Ctx* c, int R, const double2* b, double2* x, const smr_solve_opts* o,
+          smr_solve_stats* stats, cudaStream_t st);
+
+}  // namespace smr

@@ -1,0 +1,289 @@
+"""Thin ctypes binding of libsmr.so (C ABI in include/smr.h).
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels.  Function names are the C names.  Device buffers are passed as
+torch tensors (complex128, CUDA, contiguous) or as raw integer pointers; the
+stream defaults to torch's current stream on the tensor's device.  A non-zero
+status raises ``SmrError`` with the library's message.  There is no fallback:
+if libsmr.so has not been built the first call raises.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIBPATH = os.path.join(_HERE, "libsmr.so")
+_lib = None
+
+SMR_PREC_FP64, SMR_PREC_FP32 = 0, 1
+SMR_LRULE_FORMULA, SMR_LRULE_DOUBLE = 0, 1
+SMR_PRECOND_NONE, SMR_PRECOND_BLOCKDIAG = 0, 1
+ERRORS = {-1: "INVALID_ARG", -2: "SHAPE", -3: "OOM", -4: "CUDA", -5: "NOT_CONVERGED",
+          -6: "BREAKDOWN", -7: "NAN", -9: "STATE"}
+
+
+class SmrError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"SMR_E_{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class smr_opts(C.Structure):
+    _fields_ = [("device", C.c_int), ("wavelength", C.c_double), ("pitch", C.c_double),
+                ("L0", C.c_int), ("level_rule", C.c_int), ("digits", C.c_double),
+                ("n_theta", C.c_int), ("n_phi", C.c_int)]
+
+
+class smr_info_t(C.Structure):
+    _fields_ = [("p", C.c_int), ("n_psi", C.c_int), ("n_shapes", C.c_int), ("n_levels", C.c_int),
+                ("n_unknowns", C.c_longlong), ("L", C.c_int * 16), ("K", C.c_int * 16),
+                ("n_box", C.c_int * 16), ("n_il", C.c_int * 16), ("n_near_pairs", C.c_longlong),
+                ("n_near_blocks", C.c_int), ("device_bytes", C.c_double)]
+
+
+class smr_solve_opts(C.Structure):
+    _fields_ = [("tol", C.c_double), ("maxit", C.c_int), ("restart", C.c_int), ("precond", C.c_int),
+                ("precision", C.c_int), ("max_outer", C.c_int), ("use_x0", C.c_int)]
+
+
+class smr_solve_stats(C.Structure):
+    _fields_ = [("iters", C.c_int), ("matvecs_fp64", C.c_int), ("matvecs_fp32", C.c_int),
+                ("outer", C.c_int), ("resid_true", C.c_double), ("seconds", C.c_double)]
+
+
+_P = C.c_void_p
+_D = C.POINTER(C.c_double)
+_SIGS = {
+    "smr_default_opts": (None, [C.POINTER(smr_opts)]),
+    "smr_default_solve_opts": (None, [C.POINTER(smr_solve_opts)]),
+    "smr_create": (C.c_int, [C.POINTER(_P), C.POINTER(smr_opts)]),
+    "smr_destroy": (C.c_int, [_P]),
+    "smr_last_error": (C.c_char_p, [_P]),
+    "smr_add_sphere": (C.c_int, [_P, C.c_double, C.c_int, C.c_int, C.POINTER(C.c_int)]),
+    "smr_set_scene": (C.c_int, [_P, C.c_int, _D, C.POINTER(C.c_int), _D, _D, _D, _D]),
+    "smr_info": (C.c_int, [_P, C.POINTER(smr_info_t)]),
+    "smr_rhs_plane_waves": (C.c_int, [_P, C.c_int, _D, _D, _P, _P]),
+    "smr_matvec": (C.c_int, [_P, C.c_int, _P, _P, C.c_int, _P]),
+    "smr_matvec_parts": (C.c_int, [_P, C.c_int, _P, _P, _P, C.c_int, _P]),
+    "smr_matvec_host": (C.c_int, [_P, C.c_int, _D, _D, C.c_int, _P]),
+    "smr_precond": (C.c_int, [_P, C.c_int, _P, _P, C.c_int, _P]),
+    "smr_solve": (C.c_int, [_P, C.c_int, _P, _P, C.POINTER(smr_solve_opts),
+                            C.POINTER(smr_solve_stats), _P]),
+    "smr_far_field": (C.c_int, [_P, C.c_int, _P, C.c_int, _D, _P, _P]),
+    "smr_near_field": (C.c_int, [_P, C.c_int, _P, C.c_int, _D, _P, _P]),
+    "smr_copy_pattern": (C.c_int, [_P, C.c_int, _D]),
+    "smr_copy_translation": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _D]),
+    "smr_copy_near_block": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_int, _D]),
+    "smr_copy_level": (C.c_int, [_P, C.c_int, C.c_int, _D, C.c_size_t]),
+}
+
+
+def exported_symbols():
+    """Names this binding expects the library to export."""
+    return sorted(_SIGS)
+
+
+def lib():
+    """Load libsmr.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_LIBPATH):
+            raise ImportError(f"{_LIBPATH} is missing: run __graft_entry__.build() first")
+        L = C.CDLL(_LIBPATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(ctx, rc):
+    if rc != 0:
+        msg = lib().smr_last_error(ctx).decode() if ctx else ""
+        raise SmrError(rc, msg)
+
+
+def _dptr(a):
+    return a.ctypes.data_as(_D)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    import torch
+    if not (t.is_cuda and t.is_contiguous() and t.dtype == torch.complex128):
+        raise ValueError("device buffers must be contiguous complex128 CUDA tensors")
+    return t.data_ptr()
+
+
+def _stream(stream, t=None):
+    if stream is None:
+        import torch
+        dev = t.device if t is not None and hasattr(t, "device") else None
+        return torch.cuda.current_stream(dev).cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _R(t, n):
+    if isinstance(t, int):
+        raise ValueError("pass R explicitly with raw pointers")
+    return t.numel() // n
+
+
+# ------------------------------------------------------------------ context
+def smr_default_opts(**kw):
+    o = smr_opts()
+    lib().smr_default_opts(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def smr_create(**kw):
+    """Create a context; keyword arguments override smr_default_opts."""
+    o = smr_default_opts(**kw)
+    h = _P()
+    rc = lib().smr_create(C.byref(h), C.byref(o))
+    if rc != 0:
+        raise SmrError(rc, "smr_create failed (device or options)")
+    return h
+
+
+def smr_destroy(ctx):
+    lib().smr_destroy(ctx)
+
+
+def smr_add_sphere(ctx, radius, n_perp, n_par):
+    sid = C.c_int()
+    _check(ctx, lib().smr_add_sphere(ctx, float(radius), int(n_perp), int(n_par), C.byref(sid)))
+    return sid.value
+
+
+def smr_set_scene(ctx, centres, shape_ids, eps_in, eps_out=1.0, mu_in=1.0, mu_out=1.0):
+    c = np.ascontiguousarray(centres, dtype=np.float64).reshape(-1, 3)
+    s = np.ascontiguousarray(shape_ids, dtype=np.int32).ravel()
+    cx = lambda v: np.array([np.real(v), np.imag(v)], dtype=np.float64)
+    ei, mi, eo, mo = cx(eps_in), cx(mu_in), cx(eps_out), cx(mu_out)
+    _check(ctx, lib().smr_set_scene(ctx, c.shape[0], _dptr(c), s.ctypes.data_as(C.POINTER(C.c_int)),
+                                    _dptr(ei), _dptr(mi), _dptr(eo), _dptr(mo)))
+
+
+def smr_info(ctx):
+    i = smr_info_t()
+    _check(ctx, lib().smr_info(ctx, C.byref(i)))
+    n = i.n_levels
+    return dict(p=i.p, n_psi=i.n_psi, n_shapes=i.n_shapes, n_levels=n, n_unknowns=i.n_unknowns,
+                L=list(i.L[:n]), K=list(i.K[:n]), n_box=list(i.n_box[:n]), n_il=list(i.n_il[:n]),
+                n_near_pairs=i.n_near_pairs, n_near_blocks=i.n_near_blocks,
+                device_bytes=i.device_bytes)
+
+
+def smr_rhs_plane_waves(ctx, khat, pol, b, stream=None):
+    kh = np.ascontiguousarray(khat, dtype=np.float64).reshape(-1, 3)
+    pl = np.ascontiguousarray(np.asarray(pol, dtype=np.complex128).reshape(-1, 3))
+    pv = pl.view(np.float64)
+    _check(ctx, lib().smr_rhs_plane_waves(ctx, kh.shape[0], _dptr(kh), _dptr(pv), _ptr(b),
+                                          _stream(stream, b)))
+
+
+def smr_matvec(ctx, x, y, precision=SMR_PREC_FP64, R=None, stream=None):
+    n = smr_info(ctx)["n_unknowns"] if R is None else None
+    R = R if R is not None else _R(x, n)
+    _check(ctx, lib().smr_matvec(ctx, R, _ptr(x), _ptr(y), precision, _stream(stream, x)))
+
+
+def smr_matvec_parts(ctx, x, y_near, y_far, precision=SMR_PREC_FP64, R=None, stream=None):
+    R = R if R is not None else _R(x, smr_info(ctx)["n_unknowns"])
+    _check(ctx, lib().smr_matvec_parts(ctx, R, _ptr(x), _ptr(y_near), _ptr(y_far), precision,
+                                       _stream(stream, x)))
+
+
+def smr_matvec_host(ctx, x, precision=SMR_PREC_FP64, stream=None):
+    """x: host complex128 array [N] or [N, R]; returns y (host)."""
+    xx = np.ascontiguousarray(x, dtype=np.complex128)
+    n = smr_info(ctx)["n_unknowns"]
+    R = xx.size // n
+    y = np.empty_like(xx)
+    _check(ctx, lib().smr_matvec_host(ctx, R, _dptr(xx.view(np.float64)), _dptr(y.view(np.float64)),
+                                      precision, _stream(stream)))
+    return y
+
+
+def smr_precond(ctx, r, z, precision=SMR_PREC_FP64, R=None, stream=None):
+    R = R if R is not None else _R(r, smr_info(ctx)["n_unknowns"])
+    _check(ctx, lib().smr_precond(ctx, R, _ptr(r), _ptr(z), precision, _stream(stream, r)))
+
+
+def smr_default_solve_opts(**kw):
+    o = smr_solve_opts()
+    lib().smr_default_solve_opts(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def smr_solve(ctx, b, x, R=None, stream=None, **kw):
+    """Returns (status, stats dict); SMR_E_NOT_CONVERGED is returned, not raised."""
+    R = R if R is not None else _R(b, smr_info(ctx)["n_unknowns"])
+    o = smr_default_solve_opts(**kw)
+    st = smr_solve_stats()
+    rc = lib().smr_solve(ctx, R, _ptr(b), _ptr(x), C.byref(o), C.byref(st), _stream(stream, b))
+    if rc not in (0, -5):
+        _check(ctx, rc)
+    return rc, dict(iters=st.iters, matvecs_fp64=st.matvecs_fp64, matvecs_fp32=st.matvecs_fp32,
+                    outer=st.outer, resid_true=st.resid_true, seconds=st.seconds)
+
+
+def smr_far_field(ctx, x, dirs, F, R=None, stream=None):
+    d = np.ascontiguousarray(dirs, dtype=np.float64).reshape(-1, 3)
+    R = R if R is not None else _R(x, smr_info(ctx)["n_unknowns"])
+    _check(ctx, lib().smr_far_field(ctx, R, _ptr(x), d.shape[0], _dptr(d), _ptr(F), _stream(stream, x)))
+
+
+def smr_near_field(ctx, x, pts, EH, R=None, stream=None):
+    d = np.ascontiguousarray(pts, dtype=np.float64).reshape(-1, 3)
+    R = R if R is not None else _R(x, smr_info(ctx)["n_unknowns"])
+    _check(ctx, lib().smr_near_field(ctx, R, _ptr(x), d.shape[0], _dptr(d), _ptr(EH), _stream(stream, x)))
+
+
+def smr_copy_pattern(ctx, shape):
+    i = smr_info(ctx)
+    out = np.empty((i["n_psi"], 2, i["K"][0]), dtype=np.complex128)
+    _check(ctx, lib().smr_copy_pattern(ctx, shape, _dptr(out.view(np.float64))))
+    return out
+
+
+def smr_copy_translation(ctx, level, dx, dy):
+    K = smr_info(ctx)["K"][level]
+    out = np.empty(K, dtype=np.complex128)
+    _check(ctx, lib().smr_copy_translation(ctx, level, dx, dy, _dptr(out.view(np.float64))))
+    return out
+
+
+def smr_copy_near_block(ctx, sm, sn, dx, dy):
+    n2 = 2 * smr_info(ctx)["n_psi"]
+    out = np.empty((n2, n2), dtype=np.complex128)
+    _check(ctx, lib().smr_copy_near_block(ctx, sm, sn, dx, dy, _dptr(out.view(np.float64))))
+    return out
+
+
+def smr_copy_level(ctx, level, kind, R=1):
+    i = smr_info(ctx)
+    out = np.empty((i["n_box"][level], i["K"][level], 4, R), dtype=np.complex128)
+    _check(ctx, lib().smr_copy_level(ctx, level, kind, _dptr(out.view(np.float64)), out.size * 2))
+    return out
+
+
+def scene_from_workload(w, **opts):
+    """Create a context and set the scene of a workload dict (workloads.make)."""
+    ctx = smr_create(pitch=w["pitch"], **opts)
+    for (a, npp, npl) in w["shapes"]:
+        smr_add_sphere(ctx, a, npp, npl)
+    smr_set_scene(ctx, w["centres"], w["shape_ids"], w["eps_in"])
+    return ctx

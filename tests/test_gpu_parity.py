@@ -1,0 +1,257 @@
+"""GPU FP64 path vs the FP64 oracle, element by element, through the C ABI.
+
+Bar (the product's stated target): relative error <= 1e-10 per product in
+FP64; tables and level spectra are compared element-wise at the same bar.
+The FP32 path is compared against the same oracle and its error is bounded
+by what single precision allows (<= 2e-5 relative per product here)."""
+import math
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from oracle import gmres as ogm
+from oracle import mlfma as oml
+from oracle import pmchwt as opm
+from paper_2407_21724_gb300 import smr, workloads
+
+TOL64 = 1e-10
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+def crandn(n, seed):
+    rng = np.random.default_rng(seed)
+    return (rng.standard_normal(n) + 1j * rng.standard_normal(n)) / math.sqrt(2)
+
+
+class Case:
+    def __init__(self, w, **opts):
+        self.w = w
+        self.ctx = smr.scene_from_workload(w, **opts)
+        self.info = smr.smr_info(self.ctx)
+        self.sc = opm.Scene(w["centres"], w["shape_ids"], w["shapes"], eps_in=w["eps_in"],
+                            n_theta=opts.get("n_theta", 16), n_phi=opts.get("n_phi", 32))
+        rule = "double" if opts.get("level_rule", 0) == 1 else "formula"
+        self.M = oml.MLFMA(self.sc, w["pitch"], L0=opts.get("L0", 10), rule=rule)
+
+    def gpu_matvec(self, x, prec=smr.SMR_PREC_FP64):
+        xd = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+        yd = torch.empty_like(xd)
+        smr.smr_matvec(self.ctx, xd, yd, prec, R=xd.numel() // self.info["n_unknowns"])
+        torch.cuda.synchronize()
+        return yd.cpu().numpy()
+
+
+@pytest.fixture(scope="module")
+def c1():
+    c = Case(workloads.make("spheres8x8"))
+    yield c
+    smr.smr_destroy(c.ctx)
+
+
+@pytest.fixture(scope="module")
+def rnd():
+    # 13 x 11 random radii, 8 shapes, 32 modes per current: several boxes per
+    # level, odd sizes (ragged tail at every level)
+    w = workloads.make("random", n=13, seed=5, modes=16)
+    keep = np.ones(len(w["centres"]), dtype=bool)
+    keep[[0, 17, 40, 101]] = False           # holes in the lattice
+    keep[-13:-2] = False                     # ragged last row
+    w["centres"], w["shape_ids"] = w["centres"][keep], w["shape_ids"][keep]
+    c = Case(w)
+    yield c
+    smr.smr_destroy(c.ctx)
+
+
+def test_tree_matches_oracle(c1, rnd):
+    for c in (c1, rnd):
+        t = c.M.tree
+        assert c.info["n_levels"] == t.n_levels
+        for s in range(t.n_levels):
+            assert c.info["n_box"][s] == len(t.levels[s]["ij"])
+            assert c.info["n_il"][s] == len(t.levels[s]["il"])
+            assert c.info["L"][s] == c.M.grids[s].L
+
+
+def test_patterns(c1, rnd):
+    for c in (c1, rnd):
+        for s in range(len(c.w["shapes"])):
+            P = smr.smr_copy_pattern(c.ctx, s)
+            assert rel(P, c.M.patterns[s]) < 1e-13
+
+
+def test_translation_tables(c1, rnd):
+    for c in (c1, rnd):
+        for s, tab in enumerate(c.M.T):
+            for (dx, dy), T0 in tab.items():
+                T = smr.smr_copy_translation(c.ctx, s, dx, dy)
+                assert np.max(np.abs(T - T0)) / np.max(np.abs(T0)) < 1e-12
+
+
+def test_near_blocks(c1, rnd):
+    for c in (c1, rnd):
+        seen = set()
+        for (mu, nu) in c.M.tree.near_pairs():
+            sm, sn = c.sc.shape_ids[mu], c.sc.shape_ids[nu]
+            d = tuple(int(v) for v in (c.M.tree.ij0[mu] - c.M.tree.ij0[nu]))
+            key = (sm, sn) + d
+            if key in seen:
+                continue
+            seen.add(key)
+            B = smr.smr_copy_near_block(c.ctx, int(sm), int(sn), *d)
+            assert rel(B, c.M.near_block(mu, nu)) < 1e-12, key
+
+
+def test_level_spectra(c1, rnd):
+    for c in (c1, rnd):
+        x = crandn(c.info["n_unknowns"], 11)
+        c.gpu_matvec(x)
+        outs = [c.M.aggregate(x)]
+        for s in range(c.M.tree.n_levels - 1):
+            outs.append(c.M.upward(s, outs[s]))
+        ins = [c.M.translate(s, outs[s]) for s in range(c.M.tree.n_levels)]
+        for s in range(c.M.tree.n_levels - 2, -1, -1):
+            ins[s] = ins[s] + c.M.downward(s, ins[s + 1])
+        for s in range(c.M.tree.n_levels):
+            go = smr.smr_copy_level(c.ctx, s, 0)[..., 0]
+            gi = smr.smr_copy_level(c.ctx, s, 1)[..., 0]
+            assert rel(go, outs[s]) < 1e-12, ("out", s)
+            assert rel(gi, ins[s]) < 1e-12, ("in", s)
+
+
+def test_matvec_fp64(c1, rnd):
+    for c in (c1, rnd):
+        for x in (crandn(c.info["n_unknowns"], 1), opm.rhs(c.sc, [0, 0, 1], [1, 0, 0])):
+            y0 = c.M.matvec(x)
+            assert rel(c.gpu_matvec(x), y0) < TOL64
+
+
+def test_matvec_parts(c1):
+    x = crandn(c1.info["n_unknowns"], 2)
+    xd = torch.from_numpy(x).cuda()
+    yn, yf = torch.empty_like(xd), torch.empty_like(xd)
+    smr.smr_matvec_parts(c1.ctx, xd, yn, yf, smr.SMR_PREC_FP64)
+    torch.cuda.synchronize()
+    assert rel(yn.cpu().numpy(), c1.M.near(x)) < TOL64
+    assert rel(yf.cpu().numpy(), c1.M.far(x)) < TOL64
+
+
+def test_matvec_fp32(c1, rnd):
+    for c in (c1, rnd):
+        x = crandn(c.info["n_unknowns"], 3)
+        err = rel(c.gpu_matvec(x, smr.SMR_PREC_FP32), c.M.matvec(x))
+        assert err < 2e-5
+
+
+def test_batched_columns_match_single(rnd):
+    n = rnd.info["n_unknowns"]
+    R = 5
+    X = np.stack([crandn(n, 20 + r) for r in range(R)], axis=1)
+    Y = rnd.gpu_matvec(X).reshape(n, R)
+    for r in range(R):
+        y1 = rnd.gpu_matvec(np.ascontiguousarray(X[:, r]))
+        assert np.array_equal(Y[:, r], y1)
+
+
+def test_matvec_host_buffers(c1):
+    x = crandn(c1.info["n_unknowns"], 4)
+    y = smr.smr_matvec_host(c1.ctx, x)
+    assert rel(y, c1.M.matvec(x)) < TOL64
+
+
+def test_rhs(c1, rnd):
+    for c in (c1, rnd):
+        for (kh, pol) in workloads.incidence_grid64()[::13]:
+            b = torch.empty(c.info["n_unknowns"], dtype=torch.complex128, device="cuda")
+            smr.smr_rhs_plane_waves(c.ctx, [kh], [pol], b)
+            torch.cuda.synchronize()
+            assert rel(b.cpu().numpy(), opm.rhs(c.sc, kh, pol)) < 1e-13
+
+
+def test_precond(c1):
+    x = crandn(c1.info["n_unknowns"], 6)
+    xd = torch.from_numpy(x).cuda()
+    zd = torch.empty_like(xd)
+    smr.smr_precond(c1.ctx, xd, zd)
+    torch.cuda.synchronize()
+    z0 = ogm.block_diag_precond(c1.sc)(x)
+    assert rel(zd.cpu().numpy(), z0) < 1e-12
+
+
+def test_single_particle_and_line():
+    for C in ([[0.0, 0.0, 0.0]], [[0.5 * i, 0.0, 0.0] for i in range(7)]):
+        w = dict(centres=np.array(C), shape_ids=np.zeros(len(C), dtype=np.int32),
+                 shapes=[(0.15, 8, 8)], eps_in=4.0, pitch=0.5)
+        c = Case(w)
+        x = crandn(c.info["n_unknowns"], 8)
+        assert rel(c.gpu_matvec(x), c.M.matvec(x)) < TOL64
+        smr.smr_destroy(c.ctx)
+
+
+def test_solve_fp64_and_mixed(c1):
+    b = opm.rhs(c1.sc, [0, 0, 1], [1, 0, 0])
+    bd = torch.from_numpy(b).cuda()
+    for prec in (smr.SMR_PREC_FP64, smr.SMR_PREC_FP32):
+        xd = torch.zeros_like(bd)
+        rc, st = smr.smr_solve(c1.ctx, bd, xd, tol=1e-4, precision=prec)
+        assert rc == 0
+        x = xd.cpu().numpy()
+        # the true residual of the FP64 oracle operator meets the tolerance
+        r = np.linalg.norm(b - c1.M.matvec(x)) / np.linalg.norm(b)
+        assert r <= 1.001e-4, (prec, r, st)
+    # same iterations as the oracle GMRES on the same operator (within 1)
+    x0, info = ogm.gmres(c1.M.matvec, b, precond=ogm.block_diag_precond(c1.sc), tol=1e-4)
+    xd = torch.zeros_like(bd)
+    rc, st = smr.smr_solve(c1.ctx, bd, xd, tol=1e-4, precision=smr.SMR_PREC_FP64)
+    assert abs(st["iters"] - info["iters"]) <= 1
+
+
+def test_far_field_and_cross_sections(c1):
+    b = opm.rhs(c1.sc, [0, 0, 1], [1, 0, 0])
+    x, _ = ogm.gmres(c1.M.matvec, b, precond=ogm.block_diag_precond(c1.sc), tol=1e-8)
+    rng = np.random.default_rng(9)
+    d = rng.standard_normal((40, 3))
+    d /= np.linalg.norm(d, axis=1)[:, None]
+    xd = torch.from_numpy(x).cuda()
+    F = torch.empty(40 * 3, dtype=torch.complex128, device="cuda")
+    smr.smr_far_field(c1.ctx, xd, d, F)
+    torch.cuda.synchronize()
+    assert rel(F.cpu().numpy().reshape(40, 3), opm.far_field(c1.sc, x, d)) < 1e-12
+
+
+def test_near_field(c1):
+    b = opm.rhs(c1.sc, [0, 0, 1], [1, 0, 0])
+    x = crandn(c1.info["n_unknowns"], 10) + b
+    pts = np.array([[0.0, 0.0, 2.0], [0.3, -0.2, 5.0], [3.0, 1.0, 0.4], [0.1, 0.1, 0.6]])
+    xd = torch.from_numpy(x).cuda()
+    EH = torch.empty(4 * 6, dtype=torch.complex128, device="cuda")
+    smr.smr_near_field(c1.ctx, xd, pts, EH)
+    torch.cuda.synchronize()
+    E0, H0 = opm.near_field(c1.sc, x, pts)
+    g = EH.cpu().numpy().reshape(4, 6)
+    assert rel(g[:, :3], E0) < 1e-12 and rel(g[:, 3:], H0) < 1e-12
+
+
+def test_invalid_arguments(c1):
+    with pytest.raises(smr.SmrError):
+        smr.smr_matvec(c1.ctx, 0, 0, R=1)
+    ctx = smr.smr_create()
+    with pytest.raises(smr.SmrError):
+        smr.smr_set_scene(ctx, [[0, 0, 0]], [0], 4.0)      # no shapes
+    smr.smr_add_sphere(ctx, 0.15, 4, 4)
+    with pytest.raises(smr.SmrError):
+        smr.smr_set_scene(ctx, [[0, 0, 0], [0.01, 0, 0]], [0, 0], 4.0)   # same cell
+    with pytest.raises(smr.SmrError):
+        smr.smr_set_scene(ctx, [[0, 0, 0]], [0], 4.0 + 0.1j)             # lossy
+    xd = torch.zeros(16, dtype=torch.complex128, device="cuda")
+    with pytest.raises(smr.SmrError):
+        smr.smr_matvec(ctx, xd, xd, R=1)                   # no scene
+    smr.smr_destroy(ctx)
