@@ -1,0 +1,353 @@
+"""Benchmark of the MLFMA-SMR product and GMRES solve on one GB300.
+
+Workload (default): the 200 x 200 hyperbolic metalens of 8 radius-quantised
+dielectric spheres (eps_r = 4, pitch 0.5 wavelength, f = 50 wavelengths),
+32 static modes per current: 2,560,000 complex unknowns, 7 interacting
+levels.  A step is one MLFMA-SMR product y = Z x (near block-sparse product,
+aggregation, interpolation, translation, anterpolation, receive) in the tuned
+precision (FP32 arithmetic from FP64-generated tables, FP64 in and out).
+The same line carries the plain-FP64 product rate and, measured after the
+timed steps, the GMRES time to a 1e-4 true relative residual for the tuned
+solver (FP64-outer iterative refinement over FP32-inner GMRES) and for plain
+FP64 GMRES.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+       [--workload metalens200|random40|spheres8x8] [--no-solve]
+For N > 1 launch with torch.distributed.run: every rank runs its own replica
+(weak scaling, no collective on the data path).
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+if "reference" in sys.argv:
+    # the oracle runs single-threaded: pin every BLAS pool before NumPy loads
+    for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[_v] = "1"
+
+WORKLOADS = {
+    "metalens200": ("metalens", dict(n=200, focal=50.0)),
+    "random40": ("random", dict(n=40, seed=21724)),
+    "spheres8x8": ("spheres8x8", {}),
+}
+METRIC = "MLFMA-SMR matvecs/s and GMRES time to 1e-4 residual, tuned vs plain FP64"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="metalens200", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-solve", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--sample", type=int, default=20, help="side of the oracle's sample sub-array")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ algorithmic work model
+def algorithmic_flops(centres, pitch, n_psi, L0=10):
+    """FMM work of one product (same per-unit counts as the library's
+    profile records): near 8 (2n)^2 per pair, aggregation 32 n per sample,
+    interpolation 72 x 4 per (child, parent direction), translation 32 per
+    (IL entry, direction), anterpolation 34 x 16 x 4 per (child, parent
+    direction) / 4, receive 48 n per sample."""
+    from oracle.mlfma import Tree, truncation
+    t = Tree(centres, pitch)
+    k = 2 * 3.141592653589793
+    K = [2 * (truncation(k, pitch, s, L0) + 1) ** 2 for s in range(t.n_levels)]
+    n2 = 2 * n_psi
+    p = len(centres)
+    fl = 8.0 * n2 * n2 * len(t.near_pairs())
+    fl += (32.0 + 48.0) * n_psi * p * K[0]
+    for s in range(t.n_levels):
+        fl += 32.0 * len(t.levels[s]["il"]) * K[s]
+    for s in range(t.n_levels - 1):
+        nc = len(t.levels[s]["ij"])
+        fl += nc * K[s + 1] * 4 * 72.0 + nc * 16.0 * K[s + 1] * 34.0
+    return fl
+
+
+def central_sample(w, side):
+    """The central side x side sub-array of a square workload."""
+    import numpy as np
+    C = w["centres"]
+    n = int(round(np.sqrt(len(C))))
+    i0 = (n - side) // 2
+    idx = np.array([(i0 + j) * n + i0 + i for j in range(side) for i in range(side)])
+    return C[idx], w["shape_ids"][idx]
+
+
+def oracle_sample_rate(w, side, steps, warmup):
+    """Time the FP64 oracle's MLFMA product on the central sub-array and scale
+    to full-workload products/s by the algorithmic flop ratio."""
+    import numpy as np
+    from oracle import mlfma as oml
+    from oracle import pmchwt as opm
+    Cs, ids = central_sample(w, side)
+    sc = opm.Scene(Cs, ids, w["shapes"], eps_in=w["eps_in"])
+    M = oml.MLFMA(sc, w["pitch"])
+    rng = np.random.default_rng(0)
+    x = rng.standard_normal(sc.n_unknowns) + 1j * rng.standard_normal(sc.n_unknowns)
+    times = []
+    for i in range(warmup + steps):
+        t0 = time.perf_counter()
+        M.matvec(x)
+        if i >= warmup:
+            times.append(time.perf_counter() - t0)
+    t = float(np.mean(times))
+    n_psi = w["shapes"][0][1] + w["shapes"][0][2]
+    ratio = algorithmic_flops(w["centres"], w["pitch"], n_psi) / algorithmic_flops(Cs, w["pitch"], n_psi)
+    return 1.0 / (t * ratio), t, ratio, len(Cs)
+
+
+# ------------------------------------------------------------------ reference arm (the oracle)
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_2407_21724_gb300 import workloads
+    name, kw = WORKLOADS[a.workload]
+    w = workloads.make(name, **kw)
+    rate, t, ratio, ps = oracle_sample_rate(w, min(a.sample, int(len(w["centres"]) ** 0.5)),
+                                            a.steps, a.warmup)
+    sample = (f"FP64 NumPy oracle MLFMA product on the central {int(ps ** 0.5)}x{int(ps ** 0.5)} "
+              f"sub-array ({ps} particles), {t:.3f} s per product, scaled by the algorithmic flop "
+              f"ratio {ratio:.1f} to the full workload")
+    line = dict(metric=METRIC, value=rate, unit="matvecs/s", n_gpus=a.gpus, steps=a.steps,
+                warmup=a.warmup, ms_per_step=1e3 / rate, higher_is_better=True, scaling="weak",
+                vs_baseline=None, dtype="f64", data="synthetic", impl="reference",
+                config=dict(workload=w["label"], rhs=1, l2="inputs larger than L2 (CPU run)"),
+                cpu_baseline=dict(value=rate, unit="matvecs/s", cores=1, kind="oracle", sample=sample),
+                e2e=dict(value=rate, unit="matvecs/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ our arm
+def clocks_start(path):
+    q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    try:
+        f = open(path, "w")
+        return subprocess.Popen(["nvidia-smi", "--query-gpu=" + q, "--format=csv,noheader,nounits",
+                                 "-lms", "100"], stdout=f, stderr=subprocess.DEVNULL), f
+    except (OSError, FileNotFoundError):
+        return None, None
+
+
+def clocks_stop(proc, f, path, dev):
+    import statistics
+    if proc is None:
+        return None
+    proc.terminate()
+    proc.wait()
+    f.close()
+    sm, mx, reasons = [], None, set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in open(path):
+        v = [s.strip() for s in line.split(",")]
+        if len(v) < 9 or v[0] != str(dev):
+            continue
+        try:
+            sm.append(float(v[1]))
+            mx = float(v[2])
+        except ValueError:
+            continue
+        for n, val in zip(names, v[5:9]):
+            if val.lower() == "active":
+                reasons.add(n)
+    if not sm:
+        return None
+    return dict(sm_mhz=statistics.median(sm), sm_max_mhz=mx, reasons=sorted(reasons), samples=len(sm))
+
+
+def traffic_for(kernel):
+    """DRAM bytes per launch of a kernel from the committed ncu summary, if
+    it was taken on the current source of that kernel (else None)."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    rec = json.load(open(p)).get(kernel)
+    if not rec:
+        return None
+    src = os.path.join(ROOT, "paper_2407_21724_gb300", "csrc", rec["source"])
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    return rec["dram_bytes_per_launch"] if h == rec["sha"] else None
+
+
+def run_ours(a):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_2407_21724_gb300 import smr, workloads
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    name, kw = WORKLOADS[a.workload]
+    w = workloads.make(name, **kw)
+    t0 = time.perf_counter()
+    ctx = smr.scene_from_workload(w, device=local)
+    setup_s = time.perf_counter() - t0
+    info = smr.smr_info(ctx)
+    n = info["n_unknowns"]
+    st = torch.cuda.current_stream(dev)
+    b = torch.empty(n, dtype=torch.complex128, device=dev)
+    kh, pol = w["incidences"][0]
+    smr.smr_rhs_plane_waves(ctx, [kh], [pol], b)
+    rng = np.random.default_rng(rank)
+    x = torch.from_numpy(rng.standard_normal(n) + 1j * rng.standard_normal(n)).to(dev)
+    y = torch.empty_like(x)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # 256 MB > 129 MB L2
+    P32 = smr.SMR_PREC_FP32
+
+    def timed(prec, steps, warmup):
+        for _ in range(warmup):
+            smr.smr_matvec(ctx, x, y, prec)
+        torch.cuda.synchronize(dev)
+        evs = []
+        for _ in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            smr.smr_matvec(ctx, x, y, prec)
+            e1.record(st)
+            evs.append((e0, e1))
+        torch.cuda.synchronize(dev)
+        return sum(e0.elapsed_time(e1) for e0, e1 in evs)
+
+    # ---- timed region: K tuned products
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    cproc, cf = clocks_start(os.path.join(ROOT, f".clocks_{rank}.csv")) if rank == 0 else (None, None)
+    ms_total = timed(P32, a.steps, max(3, a.warmup))
+    clocks = clocks_stop(cproc, cf, os.path.join(ROOT, f".clocks_{rank}.csv"), local) if rank == 0 else None
+    if cf is not None and os.path.exists(os.path.join(ROOT, f".clocks_{rank}.csv")):
+        os.remove(os.path.join(ROOT, f".clocks_{rank}.csv"))
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        t = torch.tensor([ms_total], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+        dist.barrier()
+    ms_step = ms_total / a.steps
+    value = world * a.steps / (ms_total / 1e3)
+
+    # ---- plain FP64 products (same protocol, fewer steps)
+    k64 = max(3, a.steps // 4)
+    ms64 = timed(smr.SMR_PREC_FP64, k64, 2) / k64
+
+    # ---- per-launch profile of the tuned product (CUDA events around every launch)
+    prof_runs = [smr.smr_profile_matvec(ctx, x, y, P32) for _ in range(max(3, a.steps // 4))]
+    nr = len(prof_runs)
+    names, launch = {}, {}
+    for run in prof_runs:
+        for rec in run:
+            for key, tab in ((rec["name"], names), ("%s:%d" % (rec["name"], rec["level"]), launch)):
+                d = tab.setdefault(key, dict(ms=0.0, bytes=0.0, flops=0.0, launches=0.0))
+                d["ms"] += rec["ms"] / nr
+                d["bytes"] += rec["bytes"] / nr
+                d["flops"] += rec["flops"] / nr
+                d["launches"] += 1.0 / nr
+    tot = sum(d["ms"] for d in names.values())
+    # dominant kernel launch: the (kernel, level) with the largest share of the step
+    top = max(launch, key=lambda k: launch[k]["ms"])
+    d = launch[top]
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    ach = d["bytes"] / d["ms"] / 1e6
+    roofline = dict(kernel=top, bound="hbm", achieved=ach, peak=hbm, unit="GB/s", frac=ach / hbm,
+                    traffic=traffic_for(top), algorithmic_bytes_per_launch=d["bytes"],
+                    launch_ms=d["ms"], share_of_step=d["ms"] / tot,
+                    peak_source="measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks
+                    else "fallback 6800 GB/s")
+    breakdown = {k: dict(ms=round(v["ms"], 4), share=round(v["ms"] / tot, 4), launches=round(v["launches"]),
+                         GBps=round(v["bytes"] / v["ms"] / 1e6, 1),
+                         TFLOPs=round(v["flops"] / v["ms"] / 1e9, 2)) for k, v in names.items()}
+    launches = len(prof_runs[0])
+
+    # ---- end to end through the C ABI with host buffers (copies timed)
+    xh = torch.from_numpy(rng.standard_normal(n) + 1j * rng.standard_normal(n)).pin_memory()
+    yh = torch.empty_like(xh).pin_memory()
+    xa, ya = xh.numpy(), yh.numpy()
+    lib = smr.lib()
+    import ctypes as C
+    D = C.POINTER(C.c_double)
+    px, py = xa.ctypes.data_as(D), ya.ctypes.data_as(D)
+    for _ in range(2):
+        lib.smr_matvec_host(ctx, 1, px, py, P32, st.cuda_stream)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    ke = max(3, a.steps // 2)
+    for _ in range(ke):
+        rc = lib.smr_matvec_host(ctx, 1, px, py, P32, st.cuda_stream)
+        assert rc == 0
+    e2e_s = (time.perf_counter() - t0) / ke
+
+    # ---- GMRES to 1e-4 (tuned and plain), after the timed region
+    gm = None
+    if not a.no_solve:
+        gm = {}
+        for label, prec in (("tuned_fp32_inner_fp64_outer", P32), ("plain_fp64", smr.SMR_PREC_FP64)):
+            xs = torch.zeros_like(b)
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            rc, stt = smr.smr_solve(ctx, b, xs, tol=1e-4, precision=prec, maxit=3000)
+            e1.record(st)
+            torch.cuda.synchronize(dev)
+            stt["solver_seconds"] = stt.pop("seconds")
+            gm[label] = dict(seconds=e0.elapsed_time(e1) / 1e3, converged=(rc == 0), **stt)
+        gm["speedup_tuned_vs_plain"] = (gm["plain_fp64"]["seconds"] /
+                                        gm["tuned_fp32_inner_fp64_outer"]["seconds"])
+
+    # ---- CPU oracle baseline on a bounded sample (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu:
+        env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+        cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "2",
+               "--warmup", "1", "--workload", a.workload, "--sample", str(a.sample)]
+        r = subprocess.run(cmd, capture_output=True, text=True, env=env)
+        for line in r.stdout.splitlines():
+            if line.startswith("{"):
+                cpu = json.loads(line)["cpu_baseline"]
+    smr.smr_destroy(ctx)
+    if rank == 0:
+        line = dict(metric=METRIC, value=value, unit="matvecs/s", n_gpus=world, steps=a.steps,
+                    warmup=a.warmup, ms_per_step=ms_step, higher_is_better=True, scaling="weak",
+                    vs_baseline=None, dtype="f32", data="synthetic",
+                    config=dict(workload=w["label"], rhs=1, precision="FP32 product, FP64 tables/IO",
+                                l2="L2 flushed (256 MB write) before every timed step",
+                                parallelism="replicas" if world > 1 else "single GPU",
+                                levels=info["n_levels"], L=info["L"], unknowns=n),
+                    fp64_matvecs_per_s=1e3 / ms64, fp64_ms_per_matvec=ms64,
+                    gmres=gm, setup_s=setup_s,
+                    e2e=dict(value=1.0 / e2e_s, unit="matvecs/s", h2d_bytes_per_step=16 * n,
+                             d2h_bytes_per_step=16 * n),
+                    gpu_launches=launches * a.steps, roofline=roofline, kernels=breakdown,
+                    clocks=clocks, cpu_baseline=cpu)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)

@@ -191,6 +191,23 @@ int smr_far_field(smr_ctx* ctx, int R, const void* x, int n_dir, const double* d
 int smr_near_field(smr_ctx* ctx, int R, const void* x, int n_pt, const double* pts,
                    void* EH, void* stream);
 
+/* One product with a per-launch breakdown.  For each kernel launch of
+ * smr_matvec, in launch order: its name, level (-1 if none), ALGORITHMIC
+ * bytes (every operand read once, every result written once; tables
+ * included) and flops of that launch, and its device time in ms from CUDA
+ * events recorded on `stream` around the launch.  Fills at most n_max
+ * entries of `out`, sets *n_out to the number of launches, and synchronises
+ * `stream`.  Same arguments otherwise as smr_matvec. */
+typedef struct {
+  char name[24];
+  int level;
+  double bytes;
+  double flops;
+  double ms;
+} smr_launch_t;
+int smr_profile_matvec(smr_ctx* ctx, int R, const void* x, void* y, int precision,
+                       smr_launch_t* out, int n_max, int* n_out, void* stream);
+
 /* Debug and parity access (host outputs, layouts as the oracle's):
  *  smr_copy_pattern: receiving patterns of a shape, [n_psi][2][K_0] complex
  *    (theta and phi components of Eq. 26 on the level-0 grid);

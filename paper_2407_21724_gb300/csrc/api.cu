@@ -646,6 +646,36 @@ int smr_near_field(smr_ctx* h, int R, const void* x, int n_pt, const double* pts
   return rc;
 }
 
+int smr_profile_matvec(smr_ctx* h, int R, const void* x, void* y, int precision, smr_launch_t* out,
+                       int n_max, int* n_out, void* stream) {
+  if (!h || R <= 0 || R > 256 || !x || !y || (n_max > 0 && !out)) return SMR_E_INVALID_ARG;
+  Ctx* c = &h->c;
+  if (!check_scene(c)) return SMR_E_STATE;
+  std::vector<ProfRec> recs;
+  c->prof = &recs;
+  int rc = smr_matvec(h, R, x, y, precision, stream);
+  c->prof = nullptr;
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  for (size_t i = 0; i < recs.size(); ++i) {
+    float ms = 0.f;
+    if (rc == SMR_OK && e == cudaSuccess) cudaEventElapsedTime(&ms, recs[i].a, recs[i].b);
+    if ((int)i < n_max) {
+      std::memset(&out[i], 0, sizeof(smr_launch_t));
+      std::strncpy(out[i].name, recs[i].name, sizeof(out[i].name) - 1);
+      out[i].level = recs[i].level;
+      out[i].bytes = recs[i].bytes;
+      out[i].flops = recs[i].flops;
+      out[i].ms = ms;
+    }
+    cudaEventDestroy(recs[i].a);
+    cudaEventDestroy(recs[i].b);
+  }
+  if (n_out) *n_out = (int)recs.size();
+  if (rc) return rc;
+  if (e != cudaSuccess) return fail(c, SMR_E_CUDA, cudaGetErrorString(e));
+  return SMR_OK;
+}
+
 int smr_copy_pattern(smr_ctx* h, int shape, double* out) {
   if (!h || !out) return SMR_E_INVALID_ARG;
   Ctx* c = &h->c;

@@ -348,17 +348,26 @@ static int far_impl(Ctx* c, int R, const double2* x, double2* y, bool accumulate
   int kc = kchunk(R);
   Level& L0 = c->lev[0];
   // aggregation
+  const double es = sizeof(V), R_ = R;
   {
     int nchunk = (L0.K + kc - 1) / kc;
+    pbeg(c, st, "aggregate", 0,
+         (double)c->p * 2 * c->npsi * R_ * 16 + (double)c->S * c->npsi * 2 * L0.K * es +
+             (double)c->p * L0.K * 4 * R_ * es,
+         32.0 * c->npsi * c->p * L0.K * R_);
     k_aggregate<T><<<(unsigned)(c->p * nchunk), 256, 0, st>>>(
         c->p, L0.K, c->npsi, R, kc, nchunk, x, (const V*)(f64 ? (void*)c->d_P64 : (void*)c->d_P32),
         c->d_sid, c->d_dshift, c->any_dshift, L0.d_khat, c->k, (V*)L0.d_out);
     SMR_LAUNCH(c);
+    pend(c, st);
   }
   // upward
   for (int s = 0; s + 1 < c->nlev; ++s) {
     Level &Lc = c->lev[s], &Lp = c->lev[s + 1];
     int nchunk = (Lp.K + kc - 1) / kc;
+    pbeg(c, st, "interpolate", s,
+         ((double)Lc.nbox * Lc.K + (double)Lp.nbox * Lp.K) * 4 * R_ * es + 4.0 * Lp.K * es,
+         (double)Lc.nbox * Lp.K * 4 * R_ * 72.0);
     k_interp<T><<<(unsigned)(Lp.nbox * nchunk), 256, 0, st>>>(
         Lp.nbox, Lp.K, Lp.nph, Lc.nph, Lc.K, R, kc, Lp.d_ch_ptr, Lp.d_ch_idx, Lp.d_ch_quad,
         Lc.d_th_src, Lc.d_th_refl, (const T*)(f64 ? (void*)Lc.d_th_w64 : (void*)Lc.d_th_w32),
@@ -366,26 +375,36 @@ static int far_impl(Ctx* c, int R, const double2* x, double2* y, bool accumulate
         (const V*)(f64 ? (void*)Lc.d_shift64 : (void*)Lc.d_shift32), (const V*)Lc.d_out,
         (V*)Lp.d_out);
     SMR_LAUNCH(c);
+    pend(c, st);
   }
   // translation at every level
   for (int s = 0; s < c->nlev; ++s) {
     Level& L = c->lev[s];
     int nchunk = (L.K + kc - 1) / kc;
+    pbeg(c, st, "translate", s,
+         2.0 * L.nbox * L.K * 4 * R_ * es + (double)L.off_dx.size() * L.K * es,
+         8.0 * L.il_src.size() * L.K * 4 * R_);
     k_translate<T><<<(unsigned)(L.nbox * nchunk), 256, 0, st>>>(
         L.nbox, L.K, R, kc, L.d_il_ptr, L.d_il_src, L.d_il_off,
         (const V*)(f64 ? (void*)L.d_T64 : (void*)L.d_T32), (const V*)L.d_out, (V*)L.d_in);
     SMR_LAUNCH(c);
+    pend(c, st);
   }
   // downward
   for (int s = c->nlev - 2; s >= 0; --s) {
     Level &Lc = c->lev[s], &Lp = c->lev[s + 1];
     int nchunk = (Lc.K + kc - 1) / kc;
+    pbeg(c, st, "anterpolate", s,
+         ((double)Lp.nbox * Lp.K + 2.0 * Lc.nbox * Lc.K) * 4 * R_ * es +
+             (double)Lc.ant_nnz * (4.0 + es / 2) + 4.0 * Lp.K * es,
+         (double)Lc.nbox * Lc.ant_nnz * (34.0 * R_));
     k_anterp<T><<<(unsigned)(Lc.nbox * nchunk), 256, 0, st>>>(
         Lc.nbox, Lc.K, Lp.K, R, kc, Lc.d_parent, Lc.d_quad, Lc.d_ant_ptr, Lc.d_ant_idx,
         (const T*)(f64 ? (void*)Lc.d_ant_w64 : (void*)Lc.d_ant_w32),
         (const V*)(f64 ? (void*)Lc.d_shift64 : (void*)Lc.d_shift32), (const V*)Lp.d_in,
         (V*)Lc.d_in);
     SMR_LAUNCH(c);
+    pend(c, st);
   }
   // receive
   {
@@ -394,11 +413,16 @@ static int far_impl(Ctx* c, int R, const double2* x, double2* y, bool accumulate
     int nrc = (R + rc - 1) / rc;
     size_t sm = (size_t)L0.K * 4 * rc * sizeof(V);
     cudaFuncSetAttribute(k_receive<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+    pbeg(c, st, "receive", 0,
+         (double)c->p * L0.K * 4 * R_ * es + (double)c->S * c->npsi * 2 * L0.K * es +
+             (accumulate ? 2.0 : 1.0) * c->p * 2 * c->npsi * R_ * 16,
+         48.0 * c->p * c->npsi * L0.K * R_);
     k_receive<T><<<(unsigned)(c->p * nrc), c->npsi * rc, sm, st>>>(
         c->p, L0.K, c->npsi, R, rc, nrc, (const V*)L0.d_in,
         (const V*)(f64 ? (void*)c->d_P64 : (void*)c->d_P32), c->d_sid, L0.d_w, c->d_dshift,
         c->any_dshift, L0.d_khat, c->k, c->zeta, y, accumulate ? 1 : 0);
     SMR_LAUNCH(c);
+    pend(c, st);
   }
   return SMR_OK;
 }
@@ -426,9 +450,14 @@ static int bs_impl(Ctx* c, int nrow, int R, const int* ptr, const int* col, cons
 }
 
 int run_near(Ctx* c, int R, int prec, const double2* x, double2* y, cudaStream_t st) {
-  if (prec == SMR_PREC_FP64)
-    return bs_impl<double>(c, c->p, R, c->d_nr_ptr, c->d_nr_col, c->d_nr_blk, c->d_B64, x, y, false, st);
-  return bs_impl<float>(c, c->p, R, c->d_nr_ptr, c->d_nr_col, c->d_nr_blk, c->d_B32, x, y, false, st);
+  double n2 = 2.0 * c->npsi, es = prec == SMR_PREC_FP64 ? 16 : 8;
+  pbeg(c, st, "near", -1, 2.0 * c->p * n2 * R * 16 + (double)c->nblk * n2 * n2 * es,
+       8.0 * n2 * n2 * c->nr_col.size() * R);
+  int rc = (prec == SMR_PREC_FP64)
+               ? bs_impl<double>(c, c->p, R, c->d_nr_ptr, c->d_nr_col, c->d_nr_blk, c->d_B64, x, y, false, st)
+               : bs_impl<float>(c, c->p, R, c->d_nr_ptr, c->d_nr_col, c->d_nr_blk, c->d_B32, x, y, false, st);
+  pend(c, st);
+  return rc;
 }
 
 int run_precond(Ctx* c, int R, int prec, const double2* r, double2* z, cudaStream_t st) {

@@ -83,8 +83,17 @@ struct Level {
   size_t spec_bytes = 0;
 };
 
+// one profiled launch: algorithmic bytes / flops and CUDA events around it
+struct ProfRec {
+  const char* name;
+  int level;
+  double bytes, flops;
+  cudaEvent_t a, b;
+};
+
 struct Ctx {
   smr_opts opts;
+  std::vector<ProfRec>* prof = nullptr;   // non-null while smr_profile_matvec runs
   std::string err;
   int device = 0;
   std::vector<Shape> shapes;
@@ -164,6 +173,18 @@ int upload(Ctx* c, T** dst, const std::vector<T>& src) {
   SMR_CUDA(c, cudaMalloc((void**)dst, src.size() * sizeof(T)));
   SMR_CUDA(c, cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice));
   return SMR_OK;
+}
+
+inline void pbeg(Ctx* c, cudaStream_t st, const char* name, int level, double bytes, double flops) {
+  if (!c->prof) return;
+  ProfRec r{name, level, bytes, flops, nullptr, nullptr};
+  cudaEventCreate(&r.a);
+  cudaEventCreate(&r.b);
+  cudaEventRecord(r.a, st);
+  c->prof->push_back(r);
+}
+inline void pend(Ctx* c, cudaStream_t st) {
+  if (c->prof) cudaEventRecord(c->prof->back().b, st);
 }
 
 // ------------------------------------------------------------------ setup (k_setup.cu)

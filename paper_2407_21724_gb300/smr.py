@@ -52,6 +52,11 @@ class smr_solve_stats(C.Structure):
                 ("outer", C.c_int), ("resid_true", C.c_double), ("seconds", C.c_double)]
 
 
+class smr_launch_t(C.Structure):
+    _fields_ = [("name", C.c_char * 24), ("level", C.c_int), ("bytes", C.c_double),
+                ("flops", C.c_double), ("ms", C.c_double)]
+
+
 _P = C.c_void_p
 _D = C.POINTER(C.c_double)
 _SIGS = {
@@ -72,6 +77,8 @@ _SIGS = {
                             C.POINTER(smr_solve_stats), _P]),
     "smr_far_field": (C.c_int, [_P, C.c_int, _P, C.c_int, _D, _P, _P]),
     "smr_near_field": (C.c_int, [_P, C.c_int, _P, C.c_int, _D, _P, _P]),
+    "smr_profile_matvec": (C.c_int, [_P, C.c_int, _P, _P, C.c_int, C.POINTER(smr_launch_t), C.c_int,
+                                     C.POINTER(C.c_int), _P]),
     "smr_copy_pattern": (C.c_int, [_P, C.c_int, _D]),
     "smr_copy_translation": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _D]),
     "smr_copy_near_block": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_int, _D]),
@@ -250,6 +257,17 @@ def smr_near_field(ctx, x, pts, EH, R=None, stream=None):
     d = np.ascontiguousarray(pts, dtype=np.float64).reshape(-1, 3)
     R = R if R is not None else _R(x, smr_info(ctx)["n_unknowns"])
     _check(ctx, lib().smr_near_field(ctx, R, _ptr(x), d.shape[0], _dptr(d), _ptr(EH), _stream(stream, x)))
+
+
+def smr_profile_matvec(ctx, x, y, precision=SMR_PREC_FP64, R=None, stream=None):
+    """One product with per-launch (name, level, bytes, flops, ms) records."""
+    R = R if R is not None else _R(x, smr_info(ctx)["n_unknowns"])
+    arr = (smr_launch_t * 256)()
+    n = C.c_int()
+    _check(ctx, lib().smr_profile_matvec(ctx, R, _ptr(x), _ptr(y), precision, arr, 256, C.byref(n),
+                                         _stream(stream, x)))
+    return [dict(name=arr[i].name.decode(), level=arr[i].level, bytes=arr[i].bytes,
+                 flops=arr[i].flops, ms=arr[i].ms) for i in range(min(n.value, 256))]
 
 
 def smr_copy_pattern(ctx, shape):
