@@ -222,6 +222,31 @@ int smr_copy_translation(smr_ctx* ctx, int level, int dx, int dy, double* out);
 int smr_copy_near_block(smr_ctx* ctx, int shape_m, int shape_n, int dx, int dy, double* out);
 int smr_copy_level(smr_ctx* ctx, int level, int kind, double* out, size_t n_doubles);
 
+/* Right-hand sides of R plane waves, like smr_rhs_plane_waves, but the call
+ * allocates and frees no device memory.  For callers that cannot call
+ * cudaMalloc: an application whose device memory is fully reserved by its own
+ * pool allocator (an allocation from inside the library could fail, or break
+ * that budget), or a latency-critical loop that cannot accept the implicit
+ * device synchronisation cudaMalloc and cudaFree may cause.
+ *  - khat: device [R][3] unit vectors; pol: device [R][3] complex; b: device
+ *    [N][R] output (layout above).  All three are caller-owned device buffers.
+ *  - The intermediate per-shape sums ([n_shapes][n_psi][2][R] complex128)
+ *    live in a fixed 4 MiB array in device global memory that every GPU which
+ *    loads libsmr holds until the process exits.  A call needing more
+ *    (n_shapes * n_psi * 2 * R * 16 bytes > 4 MiB, e.g. R > 128 with 8 shapes
+ *    of 32 modes) fails with SMR_E_INVALID_ARG and a message; split R.
+ *  - The first call on a device looks up that array's device address (with
+ *    the context's device made current) and caches it; make that first call
+ *    before any stream capture.
+ *  - All calls on a device share the one array, which keeps the last call's
+ *    contents; calls that overlap on the GPU (different streams or threads
+ *    without ordering) race on it.  Nothing in it needs clearing: every sum
+ *    a call reads was written earlier in the same call.
+ *  - This entry point has no counterpart in the paper; it computes what
+ *    smr_rhs_plane_waves computes (Eqs. 5, 18, 19). */
+int smr_rhs_plane_waves_static(smr_ctx* ctx, int R, const double* khat, const double* pol,
+                               void* b, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

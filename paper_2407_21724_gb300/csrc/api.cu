@@ -13,10 +13,6 @@
 
 using namespace smr;
 
-struct smr_ctx {
-  Ctx c;
-};
-
 namespace {
 
 const double PI = 3.14159265358979323846;

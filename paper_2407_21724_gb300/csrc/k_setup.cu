@@ -460,6 +460,20 @@ int launch_rhs(Ctx* c, int R, const double* d_khat, const double2* d_pol, double
   return SMR_OK;
 }
 
+// Same two kernels with caller-provided scratch Sv [S][n_psi][2][R] (no allocation).
+int launch_rhs_scratch(Ctx* c, int R, const double* d_khat, const double2* d_pol, double2* Sv,
+                       double2* b, cudaStream_t st) {
+  long long t1 = (long long)c->S * c->npsi * R;
+  k_rhs_shape<<<(unsigned)((t1 + 127) / 128), 128, 0, st>>>(c->S, c->npsi, c->Q, R, c->d_modes, c->d_rq,
+                                                           d_khat, d_pol, c->k, c->zeta, Sv);
+  SMR_LAUNCH(c);
+  long long t2 = (long long)c->p * 2 * c->npsi * R;
+  k_rhs_scatter<<<(unsigned)((t2 + 255) / 256), 256, 0, st>>>(c->p, c->npsi, R, c->d_sid, c->d_centres,
+                                                             d_khat, Sv, c->k, b);
+  SMR_LAUNCH(c);
+  return SMR_OK;
+}
+
 // ------------------------------------------------------------------ far field
 // Rv[s][n][d][3] = sum_q w psi_n(q) exp(+j k rhat_d . r_q)   (radiation vectors)
 __global__ void k_radvec(int S, int npsi, int Q, int nd, const double* __restrict__ modes,

@@ -194,6 +194,8 @@ int build_translations(Ctx* c);   // per level d_T64 / d_T32 on the GPU (FP64)
 int build_near(Ctx* c);           // d_B64 / d_B32 on the GPU (FP64) + self blocks
 int launch_rhs(Ctx* c, int R, const double* d_khat, const double2* d_pol, double2* b,
                cudaStream_t st);
+int launch_rhs_scratch(Ctx* c, int R, const double* d_khat, const double2* d_pol, double2* Sv,
+                       double2* b, cudaStream_t st);
 int launch_far_field(Ctx* c, int R, const double2* x, int nd, const double* d_dirs,
                      double2* F, cudaStream_t st);
 int launch_near_field(Ctx* c, int R, const double2* x, int npt, const double* d_pts,
@@ -223,3 +225,8 @@ int solve(Ctx* c, int R, const double2* b, double2* x, const smr_solve_opts* o,
           smr_solve_stats* stats, cudaStream_t st);
 
 }  // namespace smr
+
+// The C ABI wrapper around a context (defined in api.cu).
+struct smr_ctx {
+  smr::Ctx c;
+};

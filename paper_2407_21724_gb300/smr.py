@@ -69,6 +69,7 @@ _SIGS = {
     "smr_set_scene": (C.c_int, [_P, C.c_int, _D, C.POINTER(C.c_int), _D, _D, _D, _D]),
     "smr_info": (C.c_int, [_P, C.POINTER(smr_info_t)]),
     "smr_rhs_plane_waves": (C.c_int, [_P, C.c_int, _D, _D, _P, _P]),
+    "smr_rhs_plane_waves_static": (C.c_int, [_P, C.c_int, _P, _P, _P, _P]),
     "smr_matvec": (C.c_int, [_P, C.c_int, _P, _P, C.c_int, _P]),
     "smr_matvec_parts": (C.c_int, [_P, C.c_int, _P, _P, _P, C.c_int, _P]),
     "smr_matvec_host": (C.c_int, [_P, C.c_int, _D, _D, C.c_int, _P]),
@@ -197,6 +198,16 @@ def smr_rhs_plane_waves(ctx, khat, pol, b, stream=None):
     pv = pl.view(np.float64)
     _check(ctx, lib().smr_rhs_plane_waves(ctx, kh.shape[0], _dptr(kh), _dptr(pv), _ptr(b),
                                           _stream(stream, b)))
+
+
+def smr_rhs_plane_waves_static(ctx, khat, pol, b, R=None, stream=None):
+    """No-allocation variant: khat (R,3) float64 and pol (R,3) complex128 are
+    device tensors (or raw pointers with R given); b is the device output."""
+    if R is None:
+        R = khat.shape[0]
+    kp = khat if isinstance(khat, int) else khat.data_ptr()
+    pp = pol if isinstance(pol, int) else pol.data_ptr()
+    _check(ctx, lib().smr_rhs_plane_waves_static(ctx, R, kp, pp, _ptr(b), _stream(stream, b)))
 
 
 def smr_matvec(ctx, x, y, precision=SMR_PREC_FP64, R=None, stream=None):
