@@ -339,6 +339,7 @@ def run_ours(a):
                     e2e=dict(value=1.0 / e2e_s, unit="matvecs/s", h2d_bytes_per_step=16 * n,
                              d2h_bytes_per_step=16 * n),
                     gpu_launches=launches * a.steps, roofline=roofline, kernels=breakdown,
+                    launches_ms={k: round(v["ms"], 4) for k, v in launch.items()},
                     clocks=clocks, cpu_baseline=cpu)
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -162,6 +162,7 @@ typedef struct {
   int matvecs_fp64;     /* FP64 products incl. true-residual checks            */
   int matvecs_fp32;     /* FP32 products                                       */
   int outer;            /* refinement steps (SMR_PREC_FP32)                    */
+  int reorth;           /* Arnoldi steps that needed a second Gram-Schmidt pass */
   double resid_true;    /* max over r of ||b - Z_64 x|| / ||b|| at exit        */
   double seconds;       /* wall time of the call                               */
 } smr_solve_stats;

@@ -34,6 +34,9 @@ void free_scene(Ctx* c) {
     dfree(L.d_ch_idx); dfree(L.d_ch_quad); dfree(L.d_th_src); dfree(L.d_th_refl); dfree(L.d_th_w64);
     dfree(L.d_th_w32); dfree(L.d_ph_src); dfree(L.d_ph_w64); dfree(L.d_ph_w32); dfree(L.d_shift64);
     dfree(L.d_shift32); dfree(L.d_ant_ptr); dfree(L.d_ant_idx); dfree(L.d_ant_w64); dfree(L.d_ant_w32);
+    dfree(L.d_tht_ptr); dfree(L.d_tht_tp); dfree(L.d_tht_refl); dfree(L.d_tht_w64); dfree(L.d_tht_w32);
+    dfree(L.d_pht_ptr); dfree(L.d_pht_jp); dfree(L.d_pht_w64); dfree(L.d_pht_w32); dfree(L.d_wthp64);
+    dfree(L.d_wthp32); dfree(L.d_boxmap); dfree(L.d_offid);
     if (L.d_out) cudaFree(L.d_out);
     if (L.d_in) cudaFree(L.d_in);
     L.d_out = L.d_in = nullptr;
@@ -43,6 +46,10 @@ void free_scene(Ctx* c) {
   dfree(c->d_centres); dfree(c->d_dshift); dfree(c->d_nr_ptr); dfree(c->d_nr_col); dfree(c->d_nr_blk);
   dfree(c->d_B64); dfree(c->d_B32); dfree(c->d_Pinv64); dfree(c->d_Pinv32); dfree(c->d_pc_ptr);
   dfree(c->d_pc_col); dfree(c->d_pc_blk); dfree(c->d_tmp);
+  dfree(c->d_tile_shape); dfree(c->d_tile_start); dfree(c->d_tile_count); dfree(c->d_perm);
+  if (c->d_G) cudaFree(c->d_G);
+  c->d_G = nullptr;
+  c->G_bytes = 0;
   c->tmp_elems = 0;
   c->spec_R = 0;
   c->spec_prec = -1;
@@ -136,6 +143,50 @@ int build_interp(Ctx* c, Level& C, const Level& P) {
       (rc = upload(c, &C.d_ph_src, psrc)) || (rc = upload(c, &C.d_ph_w64, pw)) ||
       (rc = upload(c, &C.d_ph_w32, pw32)))
     return rc;
+  // separable transposes: theta taps grouped by child row (sign and 1/w_theta(child)
+  // folded in), phi taps grouped by child column (dphi_p / dphi_c folded in)
+  {
+    std::vector<double> xc, wc, xp, wpth;
+    hm::gauss_legendre(C.nth, xc, wc);
+    hm::gauss_legendre(P.nth, xp, wpth);
+    std::vector<int> tptr(C.nth + 1, 0), ttp, trf;
+    std::vector<double> tww;
+    for (int tp = 0; tp < P.nth; ++tp)
+      for (int a = 0; a < 4; ++a) tptr[tsrc[4 * tp + a] + 1]++;
+    for (int i = 0; i < C.nth; ++i) tptr[i + 1] += tptr[i];
+    ttp.resize(tptr[C.nth]); trf.resize(tptr[C.nth]); tww.resize(tptr[C.nth]);
+    std::vector<int> tf(tptr.begin(), tptr.end() - 1);
+    for (int tp = 0; tp < P.nth; ++tp)
+      for (int a = 0; a < 4; ++a) {
+        int i = tsrc[4 * tp + a], e = tf[i]++;
+        ttp[e] = tp;
+        trf[e] = trefl[4 * tp + a];
+        tww[e] = (trefl[4 * tp + a] ? -1.0 : 1.0) * tw[4 * tp + a] / wc[i];
+      }
+    std::vector<int> pptr(C.nph + 1, 0), pjp;
+    std::vector<double> pww;
+    for (int jp = 0; jp < P.nph; ++jp)
+      for (int b = 0; b < 4; ++b) pptr[psrc[4 * jp + b] + 1]++;
+    for (int j = 0; j < C.nph; ++j) pptr[j + 1] += pptr[j];
+    pjp.resize(pptr[C.nph]); pww.resize(pptr[C.nph]);
+    std::vector<int> pf(pptr.begin(), pptr.end() - 1);
+    double ratio = (double)C.nph / (double)P.nph;   // dphi_p / dphi_c
+    for (int jp = 0; jp < P.nph; ++jp)
+      for (int b = 0; b < 4; ++b) {
+        int j = psrc[4 * jp + b], e = pf[j]++;
+        pjp[e] = jp;
+        pww[e] = pw[4 * jp + b] * ratio;
+      }
+    std::vector<float> tww32(tww.begin(), tww.end()), pww32(pww.begin(), pww.end()),
+        wpth32(wpth.begin(), wpth.end());
+    if ((rc = upload(c, &C.d_tht_ptr, tptr)) || (rc = upload(c, &C.d_tht_tp, ttp)) ||
+        (rc = upload(c, &C.d_tht_refl, trf)) || (rc = upload(c, &C.d_tht_w64, tww)) ||
+        (rc = upload(c, &C.d_tht_w32, tww32)) || (rc = upload(c, &C.d_pht_ptr, pptr)) ||
+        (rc = upload(c, &C.d_pht_jp, pjp)) || (rc = upload(c, &C.d_pht_w64, pww)) ||
+        (rc = upload(c, &C.d_pht_w32, pww32)) || (rc = upload(c, &C.d_wthp64, wpth)) ||
+        (rc = upload(c, &C.d_wthp32, wpth32)))
+      return rc;
+  }
   // weighted adjoint A = W_c^{-1} I^T W_p as CSR over child points
   std::vector<int> cnt(C.K + 1, 0);
   int half = C.nph / 2;
@@ -343,6 +394,35 @@ int set_scene(Ctx* c, int p, const double* centres, const int* shape_ids, const 
   for (int s = 0; s + 1 < c->nlev; ++s) {
     int rc = build_interp(c, c->lev[s], c->lev[s + 1]);
     if (rc) return rc;
+  }
+  // dense lattice maps and offset ids (translation tiles)
+  for (int s = 0; s < c->nlev; ++s) {
+    Level& L = c->lev[s];
+    int x0 = *std::min_element(L.bi.begin(), L.bi.end()), x1 = *std::max_element(L.bi.begin(), L.bi.end());
+    int y0 = *std::min_element(L.bj.begin(), L.bj.end()), y1 = *std::max_element(L.bj.begin(), L.bj.end());
+    L.map_x0 = x0; L.map_y0 = y0; L.map_w = x1 - x0 + 1; L.map_h = y1 - y0 + 1;
+    std::vector<int> bm((size_t)L.map_w * L.map_h, -1), oid(49, -1);
+    for (int b = 0; b < L.nbox; ++b) bm[(size_t)(L.bj[b] - y0) * L.map_w + (L.bi[b] - x0)] = b;
+    for (size_t o = 0; o < L.off_dx.size(); ++o) oid[(L.off_dx[o] + 3) * 7 + (L.off_dy[o] + 3)] = (int)o;
+    int rc;
+    if ((rc = upload(c, &L.d_boxmap, bm)) || (rc = upload(c, &L.d_offid, oid))) return rc;
+  }
+  // particles grouped by shape, tiles of at most 16
+  {
+    std::vector<int> perm(p), tsh, tst, tcn;
+    for (int i = 0; i < p; ++i) perm[i] = i;
+    std::stable_sort(perm.begin(), perm.end(), [&](int a, int b) { return c->sid[a] < c->sid[b]; });
+    for (int i = 0; i < p;) {
+      int s = c->sid[perm[i]], j = i;
+      while (j < p && c->sid[perm[j]] == s && j - i < 16) ++j;
+      tsh.push_back(s); tst.push_back(i); tcn.push_back(j - i);
+      i = j;
+    }
+    c->ntile = (int)tsh.size();
+    int rc;
+    if ((rc = upload(c, &c->d_perm, perm)) || (rc = upload(c, &c->d_tile_shape, tsh)) ||
+        (rc = upload(c, &c->d_tile_start, tst)) || (rc = upload(c, &c->d_tile_count, tcn)))
+      return rc;
   }
   // ---- near lists: self + 8 lattice neighbours; block keys (sm, sn, dx, dy)
   c->blk_sm.clear(); c->blk_sn.clear(); c->blk_dx.clear(); c->blk_dy.clear();

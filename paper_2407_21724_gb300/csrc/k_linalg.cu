@@ -2,9 +2,10 @@
 //
 // Vectors are complex FP64 [n][R] (R right-hand sides innermost).  The R
 // systems advance in lockstep: one R-column product per Arnoldi step, classical
-// Gram-Schmidt applied twice (CGS2) per column, Givens rotations and the small
-// least-squares problems on the host in FP64.  One device->host copy per step
-// carries the Hessenberg column of every right-hand side.
+// Gram-Schmidt with a second pass whenever a column's norm falls below 1/sqrt(2)
+// of its value before projection, Givens rotations and the small least-squares
+// problems on the host in FP64.  One device->host copy per step (two when the
+// second pass runs) carries the Hessenberg column of every right-hand side.
 #include <chrono>
 #include <cmath>
 
@@ -62,12 +63,25 @@ __global__ void k_multi_axpy(int J, long long n, int R, const double2* __restric
   long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= n * R) return;
   int r = (int)(t % R);
-  double2 acc = make_double2(0, 0);
-  for (int j = 0; j < J; ++j) {
+  double2 acc = make_double2(0, 0), acc2 = make_double2(0, 0);
+  int j = 0;
+  for (; j + 4 <= J; j += 4) {
+    double2 v0 = V[(size_t)j * ldv + t], v1 = V[(size_t)(j + 1) * ldv + t];
+    double2 v2 = V[(size_t)(j + 2) * ldv + t], v3 = V[(size_t)(j + 3) * ldv + t];
+    double2 c0 = h[(size_t)j * R + r], c1 = h[(size_t)(j + 1) * R + r];
+    double2 c2 = h[(size_t)(j + 2) * R + r], c3 = h[(size_t)(j + 3) * R + r];
+    acc.x += v0.x * c0.x - v0.y * c0.y + v1.x * c1.x - v1.y * c1.y;
+    acc.y += v0.x * c0.y + v0.y * c0.x + v1.x * c1.y + v1.y * c1.x;
+    acc2.x += v2.x * c2.x - v2.y * c2.y + v3.x * c3.x - v3.y * c3.y;
+    acc2.y += v2.x * c2.y + v2.y * c2.x + v3.x * c3.y + v3.y * c3.x;
+  }
+  for (; j < J; ++j) {
     double2 v = V[(size_t)j * ldv + t], c = h[(size_t)j * R + r];
     acc.x += v.x * c.x - v.y * c.y;
     acc.y += v.x * c.y + v.y * c.x;
   }
+  acc.x += acc2.x;
+  acc.y += acc2.y;
   double2 o = w[t];
   o.x += sign * acc.x;
   o.y += sign * acc.y;
@@ -183,7 +197,8 @@ static int apply_A(Ctx* c, int R, int prec, const double2* x, double2* y, cudaSt
 // preconditioner in precision `prec`.  Returns iterations used in *its.
 static int gmres_core(Ctx* c, int R, int prec, int precond, const double2* rhs, double2* d,
                       bool have_d0, const std::vector<double>& tol_col, int maxit, int restart,
-                      Work& W, int* its, int* nmv, std::vector<double>& rel_out, cudaStream_t st) {
+                      Work& W, int* its, int* nmv, int* n_reorth, std::vector<double>& rel_out,
+                      cudaStream_t st) {
   long long n = 2LL * c->npsi * c->p;
   long long ld = n * R;
   int m = restart;
@@ -213,7 +228,7 @@ static int gmres_core(Ctx* c, int R, int prec, int precond, const double2* rhs, 
   // host Hessenberg storage per column (rotated), rotations, rhs g
   std::vector<std::complex<double>> H((size_t)(m + 1) * m * R), g((size_t)(m + 1) * R);
   std::vector<std::complex<double>> cs((size_t)m * R), sn((size_t)m * R);
-  std::vector<double2> hbuf((size_t)(2 * (m + 1) + 1) * R);
+  std::vector<double2> hbuf((size_t)(2 * (m + 1) + 2) * R);
   while (true) {
     rc = col_norms(c, n, R, r0, beta.data(), st);
     if (rc) return rc;
@@ -250,23 +265,43 @@ static int gmres_core(Ctx* c, int R, int prec, int precond, const double2* rhs, 
       if (rc) return rc;
       ++*nmv;
       ++*its;
-      // CGS2 against V_0..V_j
+      // classical Gram-Schmidt against V_0..V_j, repeated once when the norm
+      // drops below 1/sqrt(2) of its value before the projection ("twice is
+      // enough"); every sum in FP64
       double2* dh1 = W.coef;                       // [j+1][R]
       double2* dh2 = W.coef + (size_t)(m + 1) * R; // [j+1][R]
+      double2* dnr = W.coef + (size_t)2 * (m + 1) * R;          // ||w'||^2  [R]
+      double2* dn0 = W.coef + (size_t)2 * (m + 1) * R + R;      // ||w||^2   [R]
+      rc = multidot_dev(c, 1, n, R, W.w, 0, W.w, dn0, W.part, st);
+      if (rc) return rc;
       rc = multidot_dev(c, j + 1, n, R, W.V, ld, W.w, dh1, W.part, st);
       if (rc) return rc;
       rc = multi_axpy(c, j + 1, n, R, W.V, ld, dh1, W.w, -1.0, st);
       if (rc) return rc;
-      rc = multidot_dev(c, j + 1, n, R, W.V, ld, W.w, dh2, W.part, st);
-      if (rc) return rc;
-      rc = multi_axpy(c, j + 1, n, R, W.V, ld, dh2, W.w, -1.0, st);
-      if (rc) return rc;
-      double2* dnr = W.coef + (size_t)2 * (m + 1) * R;
       rc = multidot_dev(c, 1, n, R, W.w, 0, W.w, dnr, W.part, st);
       if (rc) return rc;
-      SMR_CUDA(c, cudaMemcpyAsync(hbuf.data(), W.coef, (size_t)(2 * (m + 1) + 1) * R * sizeof(double2),
+      SMR_CUDA(c, cudaMemcpyAsync(hbuf.data(), W.coef, (size_t)(2 * (m + 1) + 2) * R * sizeof(double2),
                                   cudaMemcpyDeviceToHost, st));
       SMR_CUDA(c, cudaStreamSynchronize(st));
+      bool reorth = false;
+      for (int r = 0; r < R; ++r) {
+        double a0 = hbuf[(size_t)2 * (m + 1) * R + R + r].x, a1 = hbuf[(size_t)2 * (m + 1) * R + r].x;
+        if (active[r] && a1 < 0.5 * a0) reorth = true;
+      }
+      if (reorth) {
+        ++*n_reorth;
+        rc = multidot_dev(c, j + 1, n, R, W.V, ld, W.w, dh2, W.part, st);
+        if (rc) return rc;
+        rc = multi_axpy(c, j + 1, n, R, W.V, ld, dh2, W.w, -1.0, st);
+        if (rc) return rc;
+        rc = multidot_dev(c, 1, n, R, W.w, 0, W.w, dnr, W.part, st);
+        if (rc) return rc;
+        SMR_CUDA(c, cudaMemcpyAsync(hbuf.data() + (size_t)(m + 1) * R, dh2,
+                                    (size_t)((m + 1) + 1) * R * sizeof(double2), cudaMemcpyDeviceToHost, st));
+        SMR_CUDA(c, cudaStreamSynchronize(st));
+      } else {
+        for (size_t q = 0; q < (size_t)(m + 1) * R; ++q) hbuf[(size_t)(m + 1) * R + q] = make_double2(0, 0);
+      }
       // next basis vector V_{j+1} = w / ||w||
       std::vector<double2> inv(R), zz(R, make_double2(0, 0));
       std::vector<double> hn(R);
@@ -397,13 +432,13 @@ int solve(Ctx* c, int R, const double2* b, double2* x, const smr_solve_opts* o, 
   auto cleanup = [&]() {
     cudaFree(W.V); cudaFree(W.Z); cudaFree(W.w); cudaFree(W.t); cudaFree(W.coef); cudaFree(W.part);
   };
-  int its = 0, mv64 = 0, mv32 = 0, outer = 0, rc = SMR_OK;
+  int its = 0, mv64 = 0, mv32 = 0, outer = 0, nreo = 0, rc = SMR_OK;
   std::vector<double> rel;
   double tol = o->tol > 0 ? o->tol : 1e-4;
   if (o->precision == SMR_PREC_FP64) {
     std::vector<double> tc(R, tol);
     rc = gmres_core(c, R, SMR_PREC_FP64, o->precond, b, x, o->use_x0 != 0, tc, maxit, m, W, &its,
-                    &mv64, rel, st);
+                    &mv64, &nreo, rel, st);
   } else {
     // iterative refinement: outer FP64 residual, inner FGMRES on the FP32 product
     double2 *r = nullptr, *dlt = nullptr;
@@ -444,7 +479,7 @@ int solve(Ctx* c, int R, const double2* b, double2* x, const smr_solve_opts* o, 
       if (outer >= max_outer || its >= maxit) { rc = SMR_E_NOT_CONVERGED; break; }
       std::vector<double> rel_in;
       int rci = gmres_core(c, R, SMR_PREC_FP32, o->precond, r, dlt, false, tc, maxit - its, m, W,
-                           &its, &mv32, rel_in, st);
+                           &its, &mv32, &nreo, rel_in, st);
       if (rci && rci != SMR_E_NOT_CONVERGED) { rc = rci; break; }
       std::vector<double2> one(R, make_double2(1, 0));
       SMR_CUDA(c, cudaMemcpyAsync(W.coef, one.data(), R * sizeof(double2), cudaMemcpyHostToDevice, st));
@@ -461,6 +496,7 @@ int solve(Ctx* c, int R, const double2* b, double2* x, const smr_solve_opts* o, 
     stats->matvecs_fp64 = mv64;
     stats->matvecs_fp32 = mv32;
     stats->outer = outer;
+    stats->reorth = nreo;
     double mx = 0;
     for (double v : rel) mx = std::max(mx, v);
     stats->resid_true = mx;

@@ -57,224 +57,469 @@ template <typename V> __device__ __forceinline__ V cmul(V a, V b) {
 
 // ------------------------------------------------------------------ aggregation
 // out0[mu][k][f][r] = shift * sum_n conj(P[s][n][comp f][k]) x[mu][cur f][n][r]
+// One CTA = a tile of up to 16 particles of one shape (x in shared memory) x a
+// chunk of 64 directions; each pattern value is reused for the tile's columns.
 template <typename T>
-__global__ void k_aggregate(int p, int K0, int npsi, int R, int kc, int nchunk,
+__global__ void k_aggregate(int K0, int npsi, int R, int RC, int nkc,
+                            const int* __restrict__ tile_shape, const int* __restrict__ tile_start,
+                            const int* __restrict__ tile_count, const int* __restrict__ perm,
                             const double2* __restrict__ x, const typename CV<T>::V* __restrict__ P,
-                            const int* __restrict__ sid, const double* __restrict__ dshift,
-                            int any_dshift, const double* __restrict__ khat, double k,
+                            const double* __restrict__ dshift, int any_dshift,
+                            const double* __restrict__ khat, double k,
                             typename CV<T>::V* __restrict__ out) {
   typedef typename CV<T>::V V;
-  int mu = blockIdx.x / nchunk, chunk = blockIdx.x % nchunk;
-  int kl = threadIdx.x / R, r = threadIdx.x % R;
-  if (kl >= kc) return;
-  int kk = chunk * kc + kl;
+  extern __shared__ unsigned char smem_raw[];
+  V* xs = reinterpret_cast<V*>(smem_raw);          // [col][2][npsi]
+  int nrc = (R + RC - 1) / RC;
+  int TP = max(1, 16 / RC);                        // particles per column group
+  int nsub = (16 + TP - 1) / TP;
+  int tile = blockIdx.x / (nsub * nkc * nrc);
+  int rest = blockIdx.x % (nsub * nkc * nrc);
+  int sub = rest / (nkc * nrc);
+  rest %= nkc * nrc;
+  int kc = rest / nrc, r0 = (rest % nrc) * RC;
+  int nr = min(RC, R - r0);
+  int s = tile_shape[tile], tp = tile_count[tile];
+  int t0 = tile_start[tile] + sub * TP;
+  int np_ = min(tp - sub * TP, TP);
+  if (np_ <= 0) return;
+  int ncol = np_ * nr;
+  // stage x for the tile's columns (particle, r)
+  for (int t = threadIdx.x; t < ncol * 2 * npsi; t += blockDim.x) {
+    int n = t % npsi, cc = (t / npsi) % 2, col = t / (2 * npsi);
+    int mu = perm[t0 + col / nr], r = r0 + col % nr;
+    xs[(col * 2 + cc) * npsi + n] = cvt2(x[((size_t)mu * 2 * npsi + cc * npsi + n) * R + r], V());
+  }
+  __syncthreads();
+  int kl = threadIdx.x & 63, g = threadIdx.x >> 6;   // 64 directions x 4 column groups
+  int kk = kc * 64 + kl;
   if (kk >= K0) return;
-  const V* Ps = P + (size_t)sid[mu] * npsi * 2 * K0 + kk;
-  const double2* xe = x + (size_t)mu * 2 * npsi * R + r;
-  const double2* xm = xe + (size_t)npsi * R;
-  V a0 = czero<V>(), a1 = czero<V>(), a2 = czero<V>(), a3 = czero<V>();
+  const V* Ps = P + (size_t)s * npsi * 2 * K0 + kk;
+  V acc[4][4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int f = 0; f < 4; ++f) acc[q][f] = czero<V>();
   for (int n = 0; n < npsi; ++n) {
     V pt = Ps[(size_t)(2 * n) * K0], pp = Ps[(size_t)(2 * n + 1) * K0];
-    V e = cvt2(xe[(size_t)n * R], V()), m = cvt2(xm[(size_t)n * R], V());
-    cfmac(a0, pt, e);
-    cfmac(a1, pp, e);
-    cfmac(a2, pt, m);
-    cfmac(a3, pp, m);
-  }
-  if (any_dshift) {
-    const double* d = dshift + 3 * mu;
-    const double* kh = khat + 3 * kk;
-    double ph = k * (kh[0] * d[0] + kh[1] * d[1] + kh[2] * d[2]);
-    double sn, cs;
-    sincos(ph, &sn, &cs);
-    V sh = mkc((T)cs, (T)sn);
-    a0 = cmul(a0, sh); a1 = cmul(a1, sh); a2 = cmul(a2, sh); a3 = cmul(a3, sh);
-  }
-  V* o = out + ((size_t)mu * K0 + kk) * 4 * R + r;
-  o[0] = a0; o[R] = a1; o[2 * R] = a2; o[3 * R] = a3;
-}
-
-// ------------------------------------------------------------------ interpolation
-// outP[B][kp] = sum_children shift[q][kp] * sum_{4x4 taps} w sgn outC[c][tap]
-template <typename T>
-__global__ void k_interp(int nboxP, int Kp, int nphP, int nphC, int Kc, int R, int kc,
-                         const int* __restrict__ ch_ptr, const int* __restrict__ ch_idx,
-                         const int* __restrict__ ch_quad, const int* __restrict__ th_src,
-                         const int* __restrict__ th_refl, const T* __restrict__ th_w,
-                         const int* __restrict__ ph_src, const T* __restrict__ ph_w,
-                         const typename CV<T>::V* __restrict__ shift,
-                         const typename CV<T>::V* __restrict__ outC,
-                         typename CV<T>::V* __restrict__ outP) {
-  typedef typename CV<T>::V V;
-  int B = blockIdx.x % nboxP, chunk = blockIdx.x / nboxP;
-  int kl = threadIdx.x / R, r = threadIdx.x % R;
-  if (kl >= kc) return;
-  int kp = chunk * kc + kl;
-  if (kp >= Kp) return;
-  int tp = kp / nphP, jp = kp - tp * nphP;
-  int rowoff[4], colA[4], colB[4];
-  T wt[4], wp[4];
-  for (int a = 0; a < 4; ++a) {
-    int refl = th_refl[tp * 4 + a];
-    rowoff[a] = th_src[tp * 4 + a] * nphC;
-    wt[a] = refl ? -th_w[tp * 4 + a] : th_w[tp * 4 + a];
-    colA[a] = refl;  // reuse as flag
-  }
-  int half = nphC / 2;
-  for (int b = 0; b < 4; ++b) {
-    int j = ph_src[jp * 4 + b];
-    wp[b] = ph_w[jp * 4 + b];
-    colB[b] = j;
-  }
-  V acc[4] = {czero<V>(), czero<V>(), czero<V>(), czero<V>()};
-  for (int e = ch_ptr[B]; e < ch_ptr[B + 1]; ++e) {
-    const V* src = outC + (size_t)ch_idx[e] * Kc * 4 * R + r;
-    V t[4] = {czero<V>(), czero<V>(), czero<V>(), czero<V>()};
-    for (int a = 0; a < 4; ++a) {
-      for (int b = 0; b < 4; ++b) {
-        int col = colA[a] ? (colB[b] + half) % nphC : colB[b];
-        T w = wt[a] * wp[b];
-        const V* s = src + (size_t)(rowoff[a] + col) * 4 * R;
-        rfma(t[0], w, s[0]);
-        rfma(t[1], w, s[R]);
-        rfma(t[2], w, s[2 * R]);
-        rfma(t[3], w, s[3 * R]);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      int col = g + 4 * q;
+      if (col < ncol) {
+        V e = xs[(col * 2) * npsi + n], m = xs[(col * 2 + 1) * npsi + n];
+        cfmac(acc[q][0], pt, e);
+        cfmac(acc[q][1], pp, e);
+        cfmac(acc[q][2], pt, m);
+        cfmac(acc[q][3], pp, m);
       }
     }
-    V sh = shift[(size_t)ch_quad[e] * Kp + kp];
-    for (int f = 0; f < 4; ++f) cfma(acc[f], sh, t[f]);
   }
-  V* o = outP + ((size_t)B * Kp + kp) * 4 * R + r;
-  for (int f = 0; f < 4; ++f) o[f * R] = acc[f];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    int col = g + 4 * q;
+    if (col >= ncol) continue;
+    int mu = perm[t0 + col / nr], r = r0 + col % nr;
+    if (any_dshift) {
+      const double* d = dshift + 3 * mu;
+      const double* kh = khat + 3 * kk;
+      double ph = k * (kh[0] * d[0] + kh[1] * d[1] + kh[2] * d[2]);
+      double sn, cs;
+      sincos(ph, &sn, &cs);
+      V sh = mkc((T)cs, (T)sn);
+      for (int f = 0; f < 4; ++f) acc[q][f] = cmul(acc[q][f], sh);
+    }
+    V* o = out + ((size_t)mu * K0 + kk) * 4 * R + r;
+    o[0] = acc[q][0]; o[R] = acc[q][1]; o[2 * R] = acc[q][2]; o[3 * R] = acc[q][3];
+  }
+}
+
+// ------------------------------------------------------------------ interpolation (separable)
+// One warp per row of the output grid; lanes stride over (column, field, r).
+// R1 = (R == 1) lets the compiler turn the column / field split into shifts.
+template <bool R1>
+__device__ __forceinline__ void split_e(int e, int R4, int* j, int* fr) {
+  if (R1) { *j = e >> 2; *fr = e & 3; }
+  else { *j = e / R4; *fr = e - *j * R4; }
+}
+
+// theta pass:  G[c][tp][j][f][r] = sum_a w_a sgn_a F[c][row_a][(j + refl_a N/2) mod N][f][r]
+template <typename T, bool R1>
+__global__ void k_interp_theta(int nrows, int nthP, int nphC, int Kc, int R,
+                               const int* __restrict__ th_src, const int* __restrict__ th_refl,
+                               const T* __restrict__ th_w, const typename CV<T>::V* __restrict__ F,
+                               typename CV<T>::V* __restrict__ G) {
+  typedef typename CV<T>::V V;
+  int row = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (row >= nrows) return;
+  int c = row / nthP, tp = row - c * nthP;
+  int R4 = 4 * R;
+  int srow[4];
+  T w[4];
+  bool rf[4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    rf[a] = th_refl[tp * 4 + a] != 0;
+    w[a] = rf[a] ? -th_w[tp * 4 + a] : th_w[tp * 4 + a];
+    srow[a] = th_src[tp * 4 + a] * nphC;
+  }
+  const V* src = F + (size_t)c * Kc * R4;
+  V* dst = G + (size_t)row * nphC * R4;
+  int half = nphC >> 1, n = nphC * R4;
+  for (int e = lane; e < n; e += 32) {
+    int j, fr;
+    split_e<R1>(e, R4, &j, &fr);
+    int jr = j + half;
+    jr = jr >= nphC ? jr - nphC : jr;
+    V acc = czero<V>();
+#pragma unroll
+    for (int a = 0; a < 4; ++a) rfma(acc, w[a], src[(size_t)(srow[a] + (rf[a] ? jr : j)) * R4 + fr]);
+    dst[e] = acc;
+  }
+}
+
+// phi pass, shift and child sum:
+//   out[B][tp][jp][f][r] = sum_c shift[q_c][tp, jp] sum_b w_b G[c][tp][col_b][f][r]
+template <typename T, bool R1>
+__global__ void k_interp_phi(int nrows, int nthP, int nphP, int nphC, int R,
+                             const int* __restrict__ ch_ptr, const int* __restrict__ ch_idx,
+                             const int* __restrict__ ch_quad, const int* __restrict__ ph_src,
+                             const T* __restrict__ ph_w, const typename CV<T>::V* __restrict__ shift,
+                             const typename CV<T>::V* __restrict__ G,
+                             typename CV<T>::V* __restrict__ out) {
+  typedef typename CV<T>::V V;
+  int row = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (row >= nrows) return;
+  int B = row / nthP, tp = row - B * nthP;
+  int Kp = nthP * nphP, R4 = 4 * R;
+  int e0 = ch_ptr[B], e1 = ch_ptr[B + 1];
+  const V* gch[4];
+  const V* sh[4];
+  int nch = e1 - e0;
+  for (int q = 0; q < nch; ++q) {
+    gch[q] = G + ((size_t)ch_idx[e0 + q] * nthP + tp) * nphC * R4;
+    sh[q] = shift + (size_t)ch_quad[e0 + q] * Kp + (size_t)tp * nphP;
+  }
+  V* dst = out + (size_t)row * nphP * R4;
+  int n = nphP * R4;
+  for (int e = lane; e < n; e += 32) {
+    int jp, fr;
+    split_e<R1>(e, R4, &jp, &fr);
+    int col[4];
+    T w[4];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) { col[b] = ph_src[jp * 4 + b] * R4 + fr; w[b] = ph_w[jp * 4 + b]; }
+    V acc = czero<V>();
+    for (int q = 0; q < nch; ++q) {
+      V tsum = czero<V>();
+#pragma unroll
+      for (int b = 0; b < 4; ++b) rfma(tsum, w[b], gch[q][col[b]]);
+      cfma(acc, sh[q][jp], tsum);
+    }
+    dst[e] = acc;
+  }
 }
 
 // ------------------------------------------------------------------ translation
 // in[b][k] = sum_{(b', o) in IL(b)} T[o][k] out[b'][k]   (Eqs. 22-23)
+// One CTA = 4x4 target boxes of the lattice x a chunk of directions; the 8x8
+// source halo and the table rows of the chunk are staged in shared memory,
+// so each source spectrum is fetched about 4 times instead of 27.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int src_bytes) {
+  unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(src_bytes));
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n" ::);
+  asm volatile("cp.async.wait_group 0;\n" ::);
+}
+
+// 4 consecutive complex values (the 4 fields of one direction) from shared memory
+__device__ __forceinline__ void load4(const float2* p, float2* v) {
+  float4 a = reinterpret_cast<const float4*>(p)[0], b = reinterpret_cast<const float4*>(p)[1];
+  v[0] = make_float2(a.x, a.y); v[1] = make_float2(a.z, a.w);
+  v[2] = make_float2(b.x, b.y); v[3] = make_float2(b.z, b.w);
+}
+__device__ __forceinline__ void load4(const double2* p, double2* v) {
+  v[0] = p[0]; v[1] = p[1]; v[2] = p[2]; v[3] = p[3];
+}
+
 template <typename T>
-__global__ void k_translate(int nbox, int K, int R, int kc, const int* __restrict__ il_ptr,
-                            const int* __restrict__ il_src, const int* __restrict__ il_off,
-                            const typename CV<T>::V* __restrict__ Tt,
+__global__ void k_translate(int K, int R, int RC, int KC, int ntx, int nty, int map_x0, int map_y0,
+                            int map_w, int map_h, int noff, const int* __restrict__ boxmap,
+                            const int* __restrict__ offid, const typename CV<T>::V* __restrict__ Tt,
                             const typename CV<T>::V* __restrict__ out,
                             typename CV<T>::V* __restrict__ in) {
   typedef typename CV<T>::V V;
-  int b = blockIdx.x % nbox, chunk = blockIdx.x / nbox;
-  int kl = threadIdx.x / R, r = threadIdx.x % R;
-  if (kl >= kc) return;
-  int kk = chunk * kc + kl;
-  if (kk >= K) return;
-  V acc[4] = {czero<V>(), czero<V>(), czero<V>(), czero<V>()};
-  for (int e = il_ptr[b]; e < il_ptr[b + 1]; ++e) {
-    V t = Tt[(size_t)il_off[e] * K + kk];
-    const V* s = out + ((size_t)il_src[e] * K + kk) * 4 * R + r;
-    cfma(acc[0], t, s[0]);
-    cfma(acc[1], t, s[R]);
-    cfma(acc[2], t, s[2 * R]);
-    cfma(acc[3], t, s[3 * R]);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  int ntile = ntx * nty;
+  int nrc = (R + RC - 1) / RC;
+  int tile = blockIdx.x % ntile;
+  int rest = blockIdx.x / ntile;
+  int rch = rest % nrc, kch = rest / nrc;
+  int tx = tile % ntx, ty = tile / ntx;
+  // absolute lattice origin of the tile, aligned to multiples of 4
+  int ax0 = ((map_x0 >> 2) + tx) * 4, ay0 = ((map_y0 >> 2) + ty) * 4;
+  int k0 = kch * KC, r0 = rch * RC;
+  int nk = min(KC, K - k0), nr = min(RC, R - r0);
+  int W = KC * 4 * RC;                                // V per source box in the chunk
+  V* S = reinterpret_cast<V*>(smem_raw);              // [64 sources][KC][4][RC]
+  V* Ts = S + 64 * W;                                 // [noff][KC]
+  int* bid = reinterpret_cast<int*>(Ts + max(noff, 1) * KC);   // [64] source box ids
+  int* tgt = bid + 64;                                // [16] target box ids
+  int* cnt = tgt + 16;                                // [16] candidate counts
+  int2* lst = reinterpret_cast<int2*>(cnt + 16);      // [16][27] (source slot, table row)
+  for (int t = threadIdx.x; t < 64; t += blockDim.x) {
+    int sx = ax0 - 2 + (t & 7), sy = ay0 - 2 + (t >> 3);
+    int lx = sx - map_x0, ly = sy - map_y0;
+    bid[t] = (lx >= 0 && ly >= 0 && lx < map_w && ly < map_h) ? boxmap[ly * map_w + lx] : -1;
   }
-  V* o = in + ((size_t)b * K + kk) * 4 * R + r;
-  for (int f = 0; f < 4; ++f) o[f * R] = acc[f];
+  __syncthreads();
+  if (RC == R) {
+    // each source box's chunk is contiguous in global memory: asynchronous
+    // 16-byte copies, zero-filled for missing boxes and past the last direction
+    int per = W * (int)sizeof(V) / 16;
+    int valid = nk * 4 * R * (int)sizeof(V);
+    for (int t = threadIdx.x; t < 64 * per; t += blockDim.x) {
+      int sb = t / per, pc = t - sb * per;
+      int b = bid[sb];
+      const char* g = reinterpret_cast<const char*>(out);
+      int nb = 0;
+      if (b >= 0 && pc * 16 < valid) {
+        g += ((size_t)b * K + k0) * 4 * R * sizeof(V) + (size_t)pc * 16;
+        nb = 16;
+      }
+      cp_async16(reinterpret_cast<char*>(S + (size_t)sb * W) + pc * 16, g, nb);
+    }
+  } else {
+    for (int t = threadIdx.x; t < 64 * W; t += blockDim.x) {
+      int sb = t / W, e = t % W;
+      int rl = e % RC, kl = e / (4 * RC), f = (e / RC) % 4;
+      int b = bid[sb];
+      S[t] = (b >= 0 && kl < nk && rl < nr) ? out[(((size_t)b * K + k0 + kl) * 4 + f) * R + r0 + rl]
+                                           : czero<V>();
+    }
+  }
+  for (int t = threadIdx.x; t < noff * KC; t += blockDim.x) {
+    int o = t / KC, kl = t % KC;
+    Ts[t] = (kl < nk) ? Tt[(size_t)o * K + k0 + kl] : czero<V>();
+  }
+  if (threadIdx.x < 16) {
+    int tg = threadIdx.x;
+    int ix = ax0 + (tg & 3), iy = ay0 + (tg >> 2);
+    int lx = ix - map_x0, ly = iy - map_y0;
+    int b = (lx >= 0 && ly >= 0 && lx < map_w && ly < map_h) ? boxmap[ly * map_w + lx] : -1;
+    tgt[tg] = b;
+    int n = 0;
+    if (b >= 0) {
+      int px = ix >> 1, py = iy >> 1;
+      for (int cy = 2 * py - 2; cy <= 2 * py + 3; ++cy)
+        for (int cx = 2 * px - 2; cx <= 2 * px + 3; ++cx) {
+          int dx = ix - cx, dy = iy - cy;
+          if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1) continue;
+          int sb = (cy - ay0 + 2) * 8 + (cx - ax0 + 2);
+          int o = offid[(dx + 3) * 7 + (dy + 3)];
+          if (bid[sb] < 0 || o < 0 || n >= 27) continue;
+          lst[tg * 27 + n] = make_int2(sb * W, o * KC);
+          ++n;
+        }
+    }
+    cnt[tg] = n;
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  // outputs: 16 targets x nk directions x nr columns, 4 fields each
+  int nout = 16 * nk * nr;
+  for (int t = threadIdx.x; t < nout; t += blockDim.x) {
+    int rl = t % nr, kl = (t / nr) % nk, tg = t / (nr * nk);
+    int b = tgt[tg];
+    if (b < 0) continue;
+    V acc[4] = {czero<V>(), czero<V>(), czero<V>(), czero<V>()};
+    int n = cnt[tg];
+    const int2* L = lst + tg * 27;
+    int kr = kl * 4 * RC + rl;
+    for (int e = 0; e < n; ++e) {
+      int2 so = L[e];
+      V tv = Ts[so.y + kl];
+      const V* sv = S + so.x + kr;
+      V v[4];
+      if (RC == 1) {
+        load4(sv, v);
+      } else {
+        v[0] = sv[0]; v[1] = sv[RC]; v[2] = sv[2 * RC]; v[3] = sv[3 * RC];
+      }
+      cfma(acc[0], tv, v[0]);
+      cfma(acc[1], tv, v[1]);
+      cfma(acc[2], tv, v[2]);
+      cfma(acc[3], tv, v[3]);
+    }
+    V* o = in + ((size_t)b * K + k0 + kl) * 4 * R + r0 + rl;
+    for (int f = 0; f < 4; ++f) o[f * R] = acc[f];
+  }
 }
 
-// ------------------------------------------------------------------ anterpolation
-// inC[c][kc] += sum_{(kp, w) in A(kc)} w conj(shift[q][kp]) inP[parent][kp]
-template <typename T>
-__global__ void k_anterp(int nboxC, int Kc, int Kp, int R, int kc, const int* __restrict__ parent,
-                         const int* __restrict__ quad, const int* __restrict__ ant_ptr,
-                         const int* __restrict__ ant_idx, const T* __restrict__ ant_w,
-                         const typename CV<T>::V* __restrict__ shift,
-                         const typename CV<T>::V* __restrict__ inP,
-                         typename CV<T>::V* __restrict__ inC) {
+// ------------------------------------------------------------------ anterpolation (separable adjoint)
+// phi-transposed pass (one warp per row (c, tp)), child c in quadrant q of parent B:
+//   Gt[c][tp][j][f][r] = w_theta_p[tp] sum_{(jp, w) in Pt(j)} w conj(shift[q][tp, jp]) in[B][tp][jp][f][r]
+template <typename T, bool R1>
+__global__ void k_anterp_phi(int nrows, int nthP, int nphP, int nphC, int R,
+                             const int* __restrict__ parent, const int* __restrict__ quad,
+                             const int* __restrict__ pht_ptr, const int* __restrict__ pht_jp,
+                             const T* __restrict__ pht_w, const T* __restrict__ wthp,
+                             const typename CV<T>::V* __restrict__ shift,
+                             const typename CV<T>::V* __restrict__ inP,
+                             typename CV<T>::V* __restrict__ Gt) {
   typedef typename CV<T>::V V;
-  int c = blockIdx.x % nboxC, chunk = blockIdx.x / nboxC;
-  int kl = threadIdx.x / R, r = threadIdx.x % R;
-  if (kl >= kc) return;
-  int kk = chunk * kc + kl;
-  if (kk >= Kc) return;
-  const V* sh = shift + (size_t)quad[c] * Kp;
-  const V* src = inP + (size_t)parent[c] * Kp * 4 * R + r;
-  V acc[4] = {czero<V>(), czero<V>(), czero<V>(), czero<V>()};
-  for (int e = ant_ptr[kk]; e < ant_ptr[kk + 1]; ++e) {
-    int kp = ant_idx[e];
-    T w = ant_w[e];
-    V s = sh[kp];
-    V cw = mkc(w * s.x, -w * s.y);   // w conj(shift)
-    const V* v = src + (size_t)kp * 4 * R;
-    cfma(acc[0], cw, v[0]);
-    cfma(acc[1], cw, v[R]);
-    cfma(acc[2], cw, v[2 * R]);
-    cfma(acc[3], cw, v[3 * R]);
+  int row = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (row >= nrows) return;
+  int c = row / nthP, tp = row - c * nthP;
+  int Kp = nthP * nphP, R4 = 4 * R;
+  const V* src = inP + ((size_t)parent[c] * Kp + (size_t)tp * nphP) * R4;
+  const V* sh = shift + (size_t)quad[c] * Kp + (size_t)tp * nphP;
+  T wt = wthp[tp];
+  V* dst = Gt + (size_t)row * nphC * R4;
+  int n = nphC * R4;
+  for (int e = lane; e < n; e += 32) {
+    int j, fr;
+    split_e<R1>(e, R4, &j, &fr);
+    V acc = czero<V>();
+    for (int q = pht_ptr[j]; q < pht_ptr[j + 1]; ++q) {
+      int jp = pht_jp[q];
+      V sv = sh[jp];
+      T w = pht_w[q] * wt;
+      cfma(acc, mkc(w * sv.x, -w * sv.y), src[jp * R4 + fr]);
+    }
+    dst[e] = acc;
   }
-  V* o = inC + ((size_t)c * Kc + kk) * 4 * R + r;
-  for (int f = 0; f < 4; ++f) {
-    V cur = o[f * R];
-    cur.x += acc[f].x;
-    cur.y += acc[f].y;
-    o[f * R] = cur;
+}
+
+// theta-transposed pass (one warp per child row (c, i)), sign and 1/w_theta_c folded in:
+//   in[c][i][j][f][r] += sum_{(tp, w, refl) in Tt(i)} w Gt[c][tp][(j + refl N/2) mod N][f][r]
+template <typename T, bool R1>
+__global__ void k_anterp_theta(int nrows, int nthC, int nthP, int nphC, int R,
+                               const int* __restrict__ tht_ptr, const int* __restrict__ tht_tp,
+                               const int* __restrict__ tht_refl, const T* __restrict__ tht_w,
+                               const typename CV<T>::V* __restrict__ Gt,
+                               typename CV<T>::V* __restrict__ inC) {
+  typedef typename CV<T>::V V;
+  int row = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (row >= nrows) return;
+  int c = row / nthC, i = row - c * nthC;
+  int R4 = 4 * R;
+  const V* g = Gt + (size_t)c * nthP * nphC * R4;
+  V* dst = inC + (size_t)row * nphC * R4;
+  int half = nphC >> 1, n = nphC * R4;
+  int q0 = tht_ptr[i], q1 = tht_ptr[i + 1];
+  for (int e = lane; e < n; e += 32) {
+    int j, fr;
+    split_e<R1>(e, R4, &j, &fr);
+    int jr = j + half;
+    jr = jr >= nphC ? jr - nphC : jr;
+    V acc = czero<V>();
+    for (int q = q0; q < q1; ++q)
+      rfma(acc, tht_w[q], g[(size_t)(tht_tp[q] * nphC + (tht_refl[q] ? jr : j)) * R4 + fr]);
+    V cur = dst[e];
+    cur.x += acc.x;
+    cur.y += acc.y;
+    dst[e] = cur;
   }
 }
 
 // ------------------------------------------------------------------ receive
 // y_e[m] += -jk sum_k w conj(sh) [P_th (z B0 + B3) + P_ph (z B1 - B2)]
 // y_m[m] += -jk sum_k w conj(sh) [P_th (-B1 + B2/z) + P_ph (B0 + B3/z)]   (Eqs. 24-25)
+// One CTA = a tile of up to 16 (particle, r) columns of one shape; threads are
+// (mode, column pair); pattern and combined spectra chunks staged in shared memory.
 template <typename T>
-__global__ void k_receive(int p, int K0, int npsi, int R, int rc, int nrc,
-                          const typename CV<T>::V* __restrict__ in0,
-                          const typename CV<T>::V* __restrict__ P, const int* __restrict__ sid,
-                          const double* __restrict__ w0, const double* __restrict__ dshift,
-                          int any_dshift, const double* __restrict__ khat, double k, double zeta,
+__global__ void k_receive(int K0, int npsi, int R, int RC, const int* __restrict__ tile_shape,
+                          const int* __restrict__ tile_start, const int* __restrict__ tile_count,
+                          const int* __restrict__ perm, const typename CV<T>::V* __restrict__ in0,
+                          const typename CV<T>::V* __restrict__ P, const double* __restrict__ w0,
+                          const double* __restrict__ dshift, int any_dshift,
+                          const double* __restrict__ khat, double k, double zeta,
                           double2* __restrict__ y, int accumulate) {
   typedef typename CV<T>::V V;
+  const int KC = 32;
   extern __shared__ unsigned char smem_raw[];
-  V* Bs = reinterpret_cast<V*>(smem_raw);           // [K0][4][rc]
-  int mu = blockIdx.x / nrc, r0 = (blockIdx.x % nrc) * rc;
-  int nr = min(rc, R - r0);
-  const V* src = in0 + (size_t)mu * K0 * 4 * R;
-  for (int t = threadIdx.x; t < K0 * 4 * nr; t += blockDim.x) {
-    int rl = t % nr, f = (t / nr) % 4, kk = t / (4 * nr);
-    V v = src[((size_t)kk * 4 + f) * R + r0 + rl];
-    T wk = (T)w0[kk];
-    v.x *= wk;
-    v.y *= wk;
-    if (any_dshift) {
-      const double* d = dshift + 3 * mu;
-      const double* kh = khat + 3 * kk;
-      double ph = -k * (kh[0] * d[0] + kh[1] * d[1] + kh[2] * d[2]);
-      double sn, cs;
-      sincos(ph, &sn, &cs);
-      v = cmul(v, mkc((T)cs, (T)sn));
-    }
-    Bs[((size_t)kk * 4 + f) * rc + rl] = v;
-  }
-  __syncthreads();
-  int m = threadIdx.x / rc, rl = threadIdx.x % rc;
-  if (m >= npsi || rl >= nr) return;
-  const V* Pm = P + ((size_t)sid[mu] * npsi + m) * 2 * K0;
+  V* Ps = reinterpret_cast<V*>(smem_raw);          // [KC][2][npsi]
+  V* Cs = Ps + KC * 2 * npsi;                      // [KC][16 cols][4]
+  int nrc = (R + RC - 1) / RC;
+  int TP = max(1, 16 / RC);
+  int nsub = (16 + TP - 1) / TP;
+  int tile = blockIdx.x / (nsub * nrc);
+  int sub = (blockIdx.x / nrc) % nsub, r0 = (blockIdx.x % nrc) * RC;
+  int nr = min(RC, R - r0);
+  int s = tile_shape[tile], tp = tile_count[tile];
+  int t0 = tile_start[tile] + sub * TP;
+  int ncol = max(0, min(tp - sub * TP, TP)) * nr;
+  if (ncol == 0) return;                           // uniform per block: no barrier skipped
+  int m = threadIdx.x % npsi, g = threadIdx.x / npsi;   // g in [0, 8): columns g, g + 8
   T z = (T)zeta, iz = (T)(1.0 / zeta);
-  V ye = czero<V>(), ym = czero<V>();
-  for (int kk = 0; kk < K0; ++kk) {
-    V pt = Pm[kk], pp = Pm[K0 + kk];
-    const V* Bk = Bs + (size_t)kk * 4 * rc + rl;
-    V B0 = Bk[0], B1 = Bk[rc], B2 = Bk[2 * rc], B3 = Bk[3 * rc];
-    V e1 = mkc(z * B0.x + B3.x, z * B0.y + B3.y);
-    V e2 = mkc(z * B1.x - B2.x, z * B1.y - B2.y);
-    V m1 = mkc(-B1.x + iz * B2.x, -B1.y + iz * B2.y);
-    V m2 = mkc(B0.x + iz * B3.x, B0.y + iz * B3.y);
-    cfma(ye, pt, e1);
-    cfma(ye, pp, e2);
-    cfma(ym, pt, m1);
-    cfma(ym, pp, m2);
+  V ye[2] = {czero<V>(), czero<V>()}, ym[2] = {czero<V>(), czero<V>()};
+  const V* Pg = P + (size_t)s * npsi * 2 * K0;
+  for (int k0 = 0; k0 < K0; k0 += KC) {
+    int nk = min(KC, K0 - k0);
+    __syncthreads();
+    for (int t = threadIdx.x; t < nk * 2 * npsi; t += blockDim.x) {
+      int kl = t % nk, comp = (t / nk) % 2, mm = t / (2 * nk);
+      Ps[(kl * 2 + comp) * npsi + mm] = Pg[((size_t)mm * 2 + comp) * K0 + k0 + kl];
+    }
+    for (int t = threadIdx.x; t < nk * ncol; t += blockDim.x) {
+      int kl = t % nk, col = t / nk;
+      int mu = perm[t0 + col / nr], r = r0 + col % nr;
+      int kk = k0 + kl;
+      const V* b = in0 + ((size_t)mu * K0 + kk) * 4 * R + r;
+      V B0 = b[0], B1 = b[R], B2 = b[2 * R], B3 = b[3 * R];
+      T wk = (T)w0[kk];
+      V sh = mkc(wk, (T)0);
+      if (any_dshift) {
+        const double* d = dshift + 3 * mu;
+        const double* kh = khat + 3 * kk;
+        double ph = -k * (kh[0] * d[0] + kh[1] * d[1] + kh[2] * d[2]);
+        double sn, cs;
+        sincos(ph, &sn, &cs);
+        sh = mkc((T)(w0[kk] * cs), (T)(w0[kk] * sn));
+      }
+      V* cc = Cs + ((size_t)kl * 16 + col) * 4;
+      cc[0] = cmul(sh, mkc(z * B0.x + B3.x, z * B0.y + B3.y));
+      cc[1] = cmul(sh, mkc(z * B1.x - B2.x, z * B1.y - B2.y));
+      cc[2] = cmul(sh, mkc(-B1.x + iz * B2.x, -B1.y + iz * B2.y));
+      cc[3] = cmul(sh, mkc(B0.x + iz * B3.x, B0.y + iz * B3.y));
+    }
+    __syncthreads();
+    if (g < 8) {
+      for (int kl = 0; kl < nk; ++kl) {
+        V pt = Ps[(kl * 2) * npsi + m], pp = Ps[(kl * 2 + 1) * npsi + m];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          int col = g + 8 * q;
+          if (col < ncol) {
+            const V* cc = Cs + ((size_t)kl * 16 + col) * 4;
+            cfma(ye[q], pt, cc[0]);
+            cfma(ye[q], pp, cc[1]);
+            cfma(ym[q], pt, cc[2]);
+            cfma(ym[q], pp, cc[3]);
+          }
+        }
+      }
+    }
   }
-  // multiply by -j k
-  double2 oe = make_double2(k * (double)ye.y, -k * (double)ye.x);
-  double2 om = make_double2(k * (double)ym.y, -k * (double)ym.x);
-  double2* ye_p = y + ((size_t)mu * 2 * npsi + m) * R + r0 + rl;
-  double2* ym_p = ye_p + (size_t)npsi * R;
-  if (accumulate) {
-    double2 a = *ye_p, b = *ym_p;
-    oe.x += a.x; oe.y += a.y; om.x += b.x; om.y += b.y;
+  if (g >= 8) return;
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    int col = g + 8 * q;
+    if (col >= ncol) continue;
+    int mu = perm[t0 + col / nr], r = r0 + col % nr;
+    double2 oe = make_double2(k * (double)ye[q].y, -k * (double)ye[q].x);   // -j k
+    double2 om = make_double2(k * (double)ym[q].y, -k * (double)ym[q].x);
+    double2* pe = y + ((size_t)mu * 2 * npsi + m) * R + r;
+    double2* pm = pe + (size_t)npsi * R;
+    if (accumulate) {
+      double2 a = *pe, b = *pm;
+      oe.x += a.x; oe.y += a.y; om.x += b.x; om.y += b.y;
+    }
+    *pe = oe;
+    *pm = om;
   }
-  *ye_p = oe;
-  *ym_p = om;
 }
 
 // ------------------------------------------------------------------ block-sparse product
@@ -318,12 +563,12 @@ __global__ void k_blocksparse(int nrow, int n2, int R, int rc, int nrc, const in
 }
 
 // ------------------------------------------------------------------ host drivers
-static inline int kchunk(int R) { return std::max(1, 256 / R); }
-
 int ensure_spectra(Ctx* c, int R, int prec) {
   if (c->spec_R == R && c->spec_prec == prec) return SMR_OK;
   size_t es = (prec == SMR_PREC_FP64) ? sizeof(double2) : sizeof(float2);
-  for (auto& L : c->lev) {
+  size_t gmax = 0;
+  for (int s = 0; s < c->nlev; ++s) {
+    Level& L = c->lev[s];
     if (L.d_out) cudaFree(L.d_out);
     if (L.d_in) cudaFree(L.d_in);
     L.d_out = L.d_in = nullptr;
@@ -335,7 +580,19 @@ int ensure_spectra(Ctx* c, int R, int prec) {
       return SMR_E_OOM;
     }
     L.spec_bytes = bytes;
+    if (s + 1 < c->nlev)
+      gmax = std::max(gmax, (size_t)L.nbox * c->lev[s + 1].nth * L.nph * 4 * R * es);
   }
+  if (c->d_G) cudaFree(c->d_G);
+  c->d_G = nullptr;
+  c->G_bytes = 0;
+  if (gmax && cudaMalloc(&c->d_G, gmax) != cudaSuccess) {
+    c->err = "out of device memory for the separable-pass buffer";
+    c->spec_R = 0;
+    c->spec_prec = -1;
+    return SMR_E_OOM;
+  }
+  c->G_bytes = gmax;
   c->spec_R = R;
   c->spec_prec = prec;
   return SMR_OK;
@@ -345,81 +602,106 @@ template <typename T>
 static int far_impl(Ctx* c, int R, const double2* x, double2* y, bool accumulate, cudaStream_t st) {
   typedef typename CV<T>::V V;
   const bool f64 = sizeof(T) == 8;
-  int kc = kchunk(R);
-  Level& L0 = c->lev[0];
-  // aggregation
   const double es = sizeof(V), R_ = R;
+  Level& L0 = c->lev[0];
+  int RC = std::min(R, 16);
+  int nrc = (R + RC - 1) / RC;
+  // aggregation
   {
-    int nchunk = (L0.K + kc - 1) / kc;
+    int nkc = (L0.K + 63) / 64;
+    size_t sm = (size_t)16 * 2 * c->npsi * sizeof(V);
     pbeg(c, st, "aggregate", 0,
          (double)c->p * 2 * c->npsi * R_ * 16 + (double)c->S * c->npsi * 2 * L0.K * es +
              (double)c->p * L0.K * 4 * R_ * es,
          32.0 * c->npsi * c->p * L0.K * R_);
-    k_aggregate<T><<<(unsigned)(c->p * nchunk), 256, 0, st>>>(
-        c->p, L0.K, c->npsi, R, kc, nchunk, x, (const V*)(f64 ? (void*)c->d_P64 : (void*)c->d_P32),
-        c->d_sid, c->d_dshift, c->any_dshift, L0.d_khat, c->k, (V*)L0.d_out);
+    int nsub = (16 + std::max(1, 16 / RC) - 1) / std::max(1, 16 / RC);
+    k_aggregate<T><<<(unsigned)(c->ntile * nsub * nkc * nrc), 256, sm, st>>>(
+        L0.K, c->npsi, R, RC, nkc, c->d_tile_shape, c->d_tile_start, c->d_tile_count, c->d_perm, x,
+        (const V*)(f64 ? (void*)c->d_P64 : (void*)c->d_P32), c->d_dshift, c->any_dshift, L0.d_khat,
+        c->k, (V*)L0.d_out);
     SMR_LAUNCH(c);
     pend(c, st);
   }
-  // upward
+  // upward: separable interpolation, theta then phi (+ shift + child sum)
   for (int s = 0; s + 1 < c->nlev; ++s) {
     Level &Lc = c->lev[s], &Lp = c->lev[s + 1];
-    int nchunk = (Lp.K + kc - 1) / kc;
     pbeg(c, st, "interpolate", s,
          ((double)Lc.nbox * Lc.K + (double)Lp.nbox * Lp.K) * 4 * R_ * es + 4.0 * Lp.K * es,
-         (double)Lc.nbox * Lp.K * 4 * R_ * 72.0);
-    k_interp<T><<<(unsigned)(Lp.nbox * nchunk), 256, 0, st>>>(
-        Lp.nbox, Lp.K, Lp.nph, Lc.nph, Lc.K, R, kc, Lp.d_ch_ptr, Lp.d_ch_idx, Lp.d_ch_quad,
-        Lc.d_th_src, Lc.d_th_refl, (const T*)(f64 ? (void*)Lc.d_th_w64 : (void*)Lc.d_th_w32),
-        Lc.d_ph_src, (const T*)(f64 ? (void*)Lc.d_ph_w64 : (void*)Lc.d_ph_w32),
-        (const V*)(f64 ? (void*)Lc.d_shift64 : (void*)Lc.d_shift32), (const V*)Lc.d_out,
-        (V*)Lp.d_out);
+         (double)Lc.nbox * Lp.nth * Lc.nph * 4 * R_ * 16.0 + (double)Lc.nbox * Lp.K * 4 * R_ * 24.0);
+    int rows1 = Lc.nbox * Lp.nth;
+    auto kth = (R == 1) ? k_interp_theta<T, true> : k_interp_theta<T, false>;
+    kth<<<(unsigned)((rows1 + 7) / 8), 256, 0, st>>>(
+        rows1, Lp.nth, Lc.nph, Lc.K, R, Lc.d_th_src, Lc.d_th_refl,
+        (const T*)(f64 ? (void*)Lc.d_th_w64 : (void*)Lc.d_th_w32), (const V*)Lc.d_out, (V*)c->d_G);
+    SMR_LAUNCH(c);
+    int rows2 = Lp.nbox * Lp.nth;
+    auto kph = (R == 1) ? k_interp_phi<T, true> : k_interp_phi<T, false>;
+    kph<<<(unsigned)((rows2 + 7) / 8), 256, 0, st>>>(
+        rows2, Lp.nth, Lp.nph, Lc.nph, R, Lp.d_ch_ptr, Lp.d_ch_idx, Lp.d_ch_quad, Lc.d_ph_src,
+        (const T*)(f64 ? (void*)Lc.d_ph_w64 : (void*)Lc.d_ph_w32),
+        (const V*)(f64 ? (void*)Lc.d_shift64 : (void*)Lc.d_shift32), (const V*)c->d_G, (V*)Lp.d_out);
     SMR_LAUNCH(c);
     pend(c, st);
   }
   // translation at every level
   for (int s = 0; s < c->nlev; ++s) {
     Level& L = c->lev[s];
-    int nchunk = (L.K + kc - 1) / kc;
+    int noff = (int)L.off_dx.size();
+    int ntx = ((L.map_x0 + L.map_w - 1) >> 2) - (L.map_x0 >> 2) + 1;
+    int nty = ((L.map_y0 + L.map_h - 1) >> 2) - (L.map_y0 >> 2) + 1;
+    int cap = f64 ? 16 : 32;                 // directions x columns staged per CTA
+    int RCt = std::min(R, cap);
+    int KC = std::max(1, cap / RCt);
+    int nkch = (L.K + KC - 1) / KC;
+    int nrct = (R + RCt - 1) / RCt;
+    size_t sm = ((size_t)64 * KC * 4 * RCt + (size_t)std::max(noff, 1) * KC) * sizeof(V) +
+                (64 + 16 + 16) * sizeof(int) + 16 * 27 * sizeof(int2);
+    cudaFuncSetAttribute(k_translate<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     pbeg(c, st, "translate", s,
-         2.0 * L.nbox * L.K * 4 * R_ * es + (double)L.off_dx.size() * L.K * es,
+         2.0 * L.nbox * L.K * 4 * R_ * es + (double)noff * L.K * es,
          8.0 * L.il_src.size() * L.K * 4 * R_);
-    k_translate<T><<<(unsigned)(L.nbox * nchunk), 256, 0, st>>>(
-        L.nbox, L.K, R, kc, L.d_il_ptr, L.d_il_src, L.d_il_off,
+    k_translate<T><<<(unsigned)(ntx * nty * nkch * nrct), 256, sm, st>>>(
+        L.K, R, RCt, KC, ntx, nty, L.map_x0, L.map_y0, L.map_w, L.map_h, noff, L.d_boxmap, L.d_offid,
         (const V*)(f64 ? (void*)L.d_T64 : (void*)L.d_T32), (const V*)L.d_out, (V*)L.d_in);
     SMR_LAUNCH(c);
     pend(c, st);
   }
-  // downward
+  // downward: separable adjoint, phi-transpose then theta-transpose (accumulates)
   for (int s = c->nlev - 2; s >= 0; --s) {
     Level &Lc = c->lev[s], &Lp = c->lev[s + 1];
-    int nchunk = (Lc.K + kc - 1) / kc;
     pbeg(c, st, "anterpolate", s,
-         ((double)Lp.nbox * Lp.K + 2.0 * Lc.nbox * Lc.K) * 4 * R_ * es +
-             (double)Lc.ant_nnz * (4.0 + es / 2) + 4.0 * Lp.K * es,
-         (double)Lc.nbox * Lc.ant_nnz * (34.0 * R_));
-    k_anterp<T><<<(unsigned)(Lc.nbox * nchunk), 256, 0, st>>>(
-        Lc.nbox, Lc.K, Lp.K, R, kc, Lc.d_parent, Lc.d_quad, Lc.d_ant_ptr, Lc.d_ant_idx,
-        (const T*)(f64 ? (void*)Lc.d_ant_w64 : (void*)Lc.d_ant_w32),
-        (const V*)(f64 ? (void*)Lc.d_shift64 : (void*)Lc.d_shift32), (const V*)Lp.d_in,
-        (V*)Lc.d_in);
+         ((double)Lp.nbox * Lp.K + 2.0 * Lc.nbox * Lc.K) * 4 * R_ * es + 4.0 * Lp.K * es,
+         (double)Lc.nbox * Lp.nth * Lc.nph * 4 * R_ * 8.0 * 2 * (double)Lp.nph / Lc.nph * 4.0 / 4.0 +
+             (double)Lc.nbox * Lc.K * 4 * R_ * 16.0 * (double)Lp.nth / Lc.nth);
+    int rows1 = Lc.nbox * Lp.nth;
+    auto kap = (R == 1) ? k_anterp_phi<T, true> : k_anterp_phi<T, false>;
+    kap<<<(unsigned)((rows1 + 7) / 8), 256, 0, st>>>(
+        rows1, Lp.nth, Lp.nph, Lc.nph, R, Lc.d_parent, Lc.d_quad, Lc.d_pht_ptr, Lc.d_pht_jp,
+        (const T*)(f64 ? (void*)Lc.d_pht_w64 : (void*)Lc.d_pht_w32),
+        (const T*)(f64 ? (void*)Lc.d_wthp64 : (void*)Lc.d_wthp32),
+        (const V*)(f64 ? (void*)Lc.d_shift64 : (void*)Lc.d_shift32), (const V*)Lp.d_in, (V*)c->d_G);
+    SMR_LAUNCH(c);
+    int rows2 = Lc.nbox * Lc.nth;
+    auto kat = (R == 1) ? k_anterp_theta<T, true> : k_anterp_theta<T, false>;
+    kat<<<(unsigned)((rows2 + 7) / 8), 256, 0, st>>>(
+        rows2, Lc.nth, Lp.nth, Lc.nph, R, Lc.d_tht_ptr, Lc.d_tht_tp, Lc.d_tht_refl,
+        (const T*)(f64 ? (void*)Lc.d_tht_w64 : (void*)Lc.d_tht_w32), (const V*)c->d_G, (V*)Lc.d_in);
     SMR_LAUNCH(c);
     pend(c, st);
   }
   // receive
   {
-    int rc = std::min(R, std::max(1, 256 / c->npsi));
-    rc = std::min(rc, 4);
-    int nrc = (R + rc - 1) / rc;
-    size_t sm = (size_t)L0.K * 4 * rc * sizeof(V);
-    cudaFuncSetAttribute(k_receive<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+    int thr = c->npsi * 8;
+    size_t sm = ((size_t)32 * 2 * c->npsi + 32 * 16 * 4) * sizeof(V);
     pbeg(c, st, "receive", 0,
          (double)c->p * L0.K * 4 * R_ * es + (double)c->S * c->npsi * 2 * L0.K * es +
              (accumulate ? 2.0 : 1.0) * c->p * 2 * c->npsi * R_ * 16,
          48.0 * c->p * c->npsi * L0.K * R_);
-    k_receive<T><<<(unsigned)(c->p * nrc), c->npsi * rc, sm, st>>>(
-        c->p, L0.K, c->npsi, R, rc, nrc, (const V*)L0.d_in,
-        (const V*)(f64 ? (void*)c->d_P64 : (void*)c->d_P32), c->d_sid, L0.d_w, c->d_dshift,
+    int nsub = (16 + std::max(1, 16 / RC) - 1) / std::max(1, 16 / RC);
+    cudaFuncSetAttribute(k_receive<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    k_receive<T><<<(unsigned)(c->ntile * nsub * nrc), thr, sm, st>>>(
+        L0.K, c->npsi, R, RC, c->d_tile_shape, c->d_tile_start, c->d_tile_count, c->d_perm,
+        (const V*)L0.d_in, (const V*)(f64 ? (void*)c->d_P64 : (void*)c->d_P32), L0.d_w, c->d_dshift,
         c->any_dshift, L0.d_khat, c->k, c->zeta, y, accumulate ? 1 : 0);
     SMR_LAUNCH(c);
     pend(c, st);

