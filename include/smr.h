@@ -105,9 +105,24 @@ int smr_set_scene(smr_ctx* ctx, int p, const double* centres, const int* shape_i
                   const double eps_in[2], const double mu_in[2],
                   const double eps_out[2], const double mu_out[2]);
 
+/* Several independent arrays in one context (a ragged batch): particle i
+ * belongs to array array_ids[i] (0 .. n_arrays-1, every id used); each array's
+ * host centres are in its own frame and must lie on its own square lattice of
+ * spacing opts.pitch.  The arrays share the shapes, media and every table, and
+ * one smr_matvec covers all of them, but no interaction couples two arrays:
+ * each keeps its own quadtree (levels capped at the top level of the largest
+ * array), its own near pairs and its own interaction lists, so the product
+ * is block diagonal over arrays.  The unknown vector stacks the arrays'
+ * particles in the given order; plane-wave right-hand sides use each
+ * particle's own-frame centre.  smr_solve then solves all arrays together
+ * (the tolerance applies to the stacked residual). */
+int smr_set_scene_arrays(smr_ctx* ctx, int p, const double* centres, const int* shape_ids,
+                         const int* array_ids, const double eps_in[2], const double mu_in[2],
+                         const double eps_out[2], const double mu_out[2]);
+
 /* Sizes of the current scene. */
 typedef struct {
-  int p, n_psi, n_shapes, n_levels;
+  int p, n_psi, n_shapes, n_levels, n_arrays;
   long long n_unknowns;     /* 2 n_psi p                                       */
   int L[16], K[16], n_box[16], n_il[16];  /* per level s < n_levels          */
   long long n_near_pairs;   /* particle pairs in the near SpMV (self included) */
@@ -208,6 +223,48 @@ typedef struct {
 } smr_launch_t;
 int smr_profile_matvec(smr_ctx* ctx, int R, const void* x, void* y, int precision,
                        smr_launch_t* out, int n_max, int* n_out, void* stream);
+
+/* Right-hand sides with one plane wave per array (R = 1): particle mu of
+ * array a sees E = pol_a exp(-j k khat_a . r_mu) with r_mu its own-frame
+ * centre (Eqs. 5, 18, 19).  host khat[n_arrays][3], pol[n_arrays][3] complex;
+ * device b[N]. */
+int smr_rhs_plane_waves_arrays(smr_ctx* ctx, const double* khat, const double* pol, void* b,
+                               void* stream);
+
+/* ---- Learned initial guess (no counterpart in the paper; it feeds the
+ * GMRES of Sec. V a starting point).  A 4-layer MLP (F -> W -> W -> W -> O,
+ * SiLU between layers, BF16 weights with FP32 master copies, FP32
+ * activations and accumulation, Adam) maps the features of one scatterer to
+ * its de-phased coefficients abar = alpha exp(+j k khat . r) / scale, with
+ * F = 448: for each of the 48 lattice neighbours within 2 wavelengths
+ * (pitch 0.5, 0 < dx^2 + dy^2 <= 16 cells, ordered by distance then angle)
+ * a one-hot shape id (8) and a presence flag (1), the scatterer's own shape
+ * one-hot (8), the incidence direction (3) and real polarisation (3), two
+ * zeros; and O = 4 n_psi = [Re | Im] of [electric modes, magnetic modes].
+ * Shape ids must be < 8.  Incidences are one per array (host khat[n_arrays][3],
+ * pol[n_arrays][3] complex).  Parameters are stored layer by layer, W_l
+ * row-major [in][out] then b_l [out]. */
+int smr_nn_init(smr_ctx* ctx, int width, unsigned long long seed);   /* needs a scene */
+long long smr_nn_num_params(smr_ctx* ctx);
+int smr_nn_get_params(smr_ctx* ctx, float* params, long long n);     /* host, FP32 master */
+int smr_nn_set_params(smr_ctx* ctx, const float* params, long long n);  /* resets Adam */
+/* device feat[p][448] (float) for the scene's particles */
+int smr_nn_features(smr_ctx* ctx, const double* khat, const double* pol, float* feat, void* stream);
+/* device tgt[p][O] (float) from device coefficients x[N] (R = 1) */
+int smr_nn_targets(smr_ctx* ctx, const double* khat, const void* x, double scale, float* tgt,
+                   void* stream);
+/* One Adam step on the mean squared error over n rows (rows idx[0..n) of
+ * feat/tgt if idx, a device int array, is not NULL); n <= 8192.  *loss
+ * (host, may be NULL) receives the loss before the step. */
+int smr_nn_train_step(smr_ctx* ctx, int n, const float* feat, const int* idx, const float* tgt,
+                      float lr, double* loss, void* stream);
+/* Loss and its gradient (host grad[num_params], may be NULL) without a step. */
+int smr_nn_loss_grad(smr_ctx* ctx, int n, const float* feat, const int* idx, const float* tgt,
+                     double* loss, float* grad, void* stream);
+/* x0 = scale * (Y_re + j Y_im) exp(-j k khat . r) for every particle: device
+ * x0[N], ready for smr_solve with use_x0 = 1. */
+int smr_nn_predict(smr_ctx* ctx, const double* khat, const double* pol, double scale, void* x0,
+                   void* stream);
 
 /* Debug and parity access (host outputs, layouts as the oracle's):
  *  smr_copy_pattern: receiving patterns of a shape, [n_psi][2][K_0] complex

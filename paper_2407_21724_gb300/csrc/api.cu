@@ -46,6 +46,7 @@ void free_scene(Ctx* c) {
   dfree(c->d_centres); dfree(c->d_dshift); dfree(c->d_nr_ptr); dfree(c->d_nr_col); dfree(c->d_nr_blk);
   dfree(c->d_B64); dfree(c->d_B32); dfree(c->d_Pinv64); dfree(c->d_Pinv32); dfree(c->d_pc_ptr);
   dfree(c->d_pc_col); dfree(c->d_pc_blk); dfree(c->d_tmp);
+  dfree(c->d_arr);
   dfree(c->d_tile_shape); dfree(c->d_tile_start); dfree(c->d_tile_count); dfree(c->d_perm);
   if (c->d_G) cudaFree(c->d_G);
   c->d_G = nullptr;
@@ -236,8 +237,8 @@ int build_interp(Ctx* c, Level& C, const Level& P) {
   return SMR_OK;
 }
 
-int set_scene(Ctx* c, int p, const double* centres, const int* shape_ids, const double* eps_in,
-              const double* mu_in, const double* eps_out, const double* mu_out) {
+int set_scene(Ctx* c, int p, const double* centres, const int* shape_ids, const int* array_ids,
+              const double* eps_in, const double* mu_in, const double* eps_out, const double* mu_out) {
   if (p <= 0 || !centres || !shape_ids) return fail(c, SMR_E_INVALID_ARG, "p > 0 and host arrays required");
   if (c->shapes.empty()) return fail(c, SMR_E_SHAPE, "no shapes registered");
   if (eps_in[1] != 0 || mu_in[1] != 0 || eps_out[1] != 0 || mu_out[1] != 0 || eps_in[0] <= 0 ||
@@ -260,35 +261,81 @@ int set_scene(Ctx* c, int p, const double* centres, const int* shape_ids, const 
   for (int i = 0; i < p; ++i)
     if (c->sid[i] < 0 || c->sid[i] >= c->S) return fail(c, SMR_E_SHAPE, "shape id out of range");
   double pitch = c->opts.pitch;
-  // lattice indices and finest-box offsets
-  double ox = 1e300, oy = 1e300, zs = 0;
+  // lattice indices and finest-box offsets, per array: every array is placed
+  // in its own block of a common lattice, aligned and separated so that at
+  // every level up to the cap no box of one array is adjacent to, or shares a
+  // parent neighbourhood with, a box of another (no near pair, no
+  // interaction-list entry crosses arrays)
+  std::vector<int> arr(p, 0);
+  int na = 1;
+  if (array_ids) {
+    for (int i = 0; i < p; ++i) {
+      if (array_ids[i] < 0) return fail(c, SMR_E_INVALID_ARG, "array ids must be >= 0");
+      arr[i] = array_ids[i];
+      na = std::max(na, arr[i] + 1);
+    }
+  }
+  std::vector<double> ax(na, 1e300), ay(na, 1e300);
+  std::vector<int> acount(na, 0);
+  double zs = 0;
   for (int i = 0; i < p; ++i) {
-    ox = std::min(ox, centres[3 * i]);
-    oy = std::min(oy, centres[3 * i + 1]);
+    ax[arr[i]] = std::min(ax[arr[i]], centres[3 * i]);
+    ay[arr[i]] = std::min(ay[arr[i]], centres[3 * i + 1]);
+    acount[arr[i]]++;
     zs += centres[3 * i + 2];
   }
-  c->origin[0] = ox;
-  c->origin[1] = oy;
+  for (int a = 0; a < na; ++a)
+    if (acount[a] == 0) return fail(c, SMR_E_INVALID_ARG, "array ids must be 0..n_arrays-1 without gaps");
+  c->origin[0] = ax[0];
+  c->origin[1] = ay[0];
   c->z0 = zs / p;
   c->pi.resize(p);
   c->pj.resize(p);
-  std::map<std::pair<int, int>, int> idx0;
+  std::vector<int> lx(p), ly(p), ex(na, 0), ey(na, 0);
   std::vector<double> dsh(3 * (size_t)p);
   int anyd = 0;
   for (int i = 0; i < p; ++i) {
-    double fx = (centres[3 * i] - ox) / pitch, fy = (centres[3 * i + 1] - oy) / pitch;
+    int a = arr[i];
+    double fx = (centres[3 * i] - ax[a]) / pitch, fy = (centres[3 * i + 1] - ay[a]) / pitch;
     int ix = (int)std::lround(fx), iy = (int)std::lround(fy);
     if (std::fabs(fx - ix) > 1e-6 || std::fabs(fy - iy) > 1e-6 ||
         std::fabs(centres[3 * i + 2] - c->z0) > 1e-9 * pitch)
       return fail(c, SMR_E_INVALID_ARG, "centres must lie on a square lattice of spacing opts.pitch in one plane");
-    if (!idx0.emplace(std::make_pair(ix, iy), i).second)
-      return fail(c, SMR_E_INVALID_ARG, "two particles share a lattice cell");
-    c->pi[i] = ix;
-    c->pj[i] = iy;
-    dsh[3 * i] = centres[3 * i] - (ox + ix * pitch);
-    dsh[3 * i + 1] = centres[3 * i + 1] - (oy + iy * pitch);
+    if (ix > (1 << 20) || iy > (1 << 20)) return fail(c, SMR_E_INVALID_ARG, "array too large");
+    lx[i] = ix;
+    ly[i] = iy;
+    ex[a] = std::max(ex[a], ix + 1);
+    ey[a] = std::max(ey[a], iy + 1);
+    dsh[3 * i] = centres[3 * i] - (ax[a] + ix * pitch);
+    dsh[3 * i + 1] = centres[3 * i + 1] - (ay[a] + iy * pitch);
     dsh[3 * i + 2] = centres[3 * i + 2] - c->z0;
     if (dsh[3 * i] != 0 || dsh[3 * i + 1] != 0 || dsh[3 * i + 2] != 0) anyd = 1;
+  }
+  int level_cap = 1 << 20;
+  std::vector<int> offx(na, 0), offy(na, 0);
+  if (na > 1) {
+    // each array's own top level: first s where it spans at most 2 boxes per side
+    int scap = 0, emax = 0;
+    for (int a = 0; a < na; ++a) {
+      int sa = 0;
+      while (std::max((ex[a] - 1) >> sa, (ey[a] - 1) >> sa) > 1) ++sa;
+      scap = std::max(scap, sa);
+      emax = std::max(emax, std::max(ex[a], ey[a]));
+    }
+    int M = 1 << (scap + 2);
+    int stride = ((emax + 4 * (1 << scap) + M - 1) / M) * M;
+    int ncol = (int)std::ceil(std::sqrt((double)na));
+    for (int a = 0; a < na; ++a) { offx[a] = (a % ncol) * stride; offy[a] = (a / ncol) * stride; }
+    level_cap = scap;
+  }
+  c->n_arrays = na;
+  c->arr = arr;
+  std::map<std::pair<int, int>, int> idx0;
+  for (int i = 0; i < p; ++i) {
+    c->pi[i] = lx[i] + offx[arr[i]];
+    c->pj[i] = ly[i] + offy[arr[i]];
+    if (!idx0.emplace(std::make_pair(c->pi[i], c->pj[i]), i).second)
+      return fail(c, SMR_E_INVALID_ARG, "two particles share a lattice cell");
   }
   // check no sphere overlaps its neighbours on the lattice
   for (auto& s : c->shapes)
@@ -316,8 +363,8 @@ int set_scene(Ctx* c, int p, const double* centres, const int* shape_ids, const 
     L.centre.resize(3 * (size_t)L.nbox);
     double half = ((double)(1 << s) - 1.0) / 2.0;
     for (int b = 0; b < L.nbox; ++b) {
-      L.centre[3 * b] = ox + ((double)L.bi[b] * (1 << s) + half) * pitch;
-      L.centre[3 * b + 1] = oy + ((double)L.bj[b] * (1 << s) + half) * pitch;
+      L.centre[3 * b] = c->origin[0] + ((double)L.bi[b] * (1 << s) + half) * pitch;
+      L.centre[3 * b + 1] = c->origin[1] + ((double)L.bj[b] * (1 << s) + half) * pitch;
       L.centre[3 * b + 2] = c->z0;
     }
     // interaction list: parents adjacent (or equal), boxes not adjacent
@@ -351,7 +398,7 @@ int set_scene(Ctx* c, int p, const double* centres, const int* shape_ids, const 
     int minx = *std::min_element(L.bi.begin(), L.bi.end()), maxx = *std::max_element(L.bi.begin(), L.bi.end());
     int miny = *std::min_element(L.bj.begin(), L.bj.end()), maxy = *std::max_element(L.bj.begin(), L.bj.end());
     levs.push_back(std::move(L));
-    if (std::max(maxx - minx, maxy - miny) <= 1) break;
+    if (std::max(maxx - minx, maxy - miny) <= 1 || s >= level_cap) break;
     for (size_t t = 0; t < bi.size(); ++t) { bi[t] >>= 1; bj[t] >>= 1; }
     if (s > 20) return fail(c, SMR_E_INVALID_ARG, "tree too deep");
   }
@@ -464,7 +511,7 @@ int set_scene(Ctx* c, int p, const double* centres, const int* shape_ids, const 
   pcp[p] = p;
   std::vector<double> cen(c->centres);
   int rc;
-  if ((rc = upload(c, &c->d_sid, c->sid)) || (rc = upload(c, &c->d_centres, cen)) ||
+  if ((rc = upload(c, &c->d_arr, c->arr)) || (rc = upload(c, &c->d_sid, c->sid)) || (rc = upload(c, &c->d_centres, cen)) ||
       (rc = upload(c, &c->d_dshift, dsh)) || (rc = upload(c, &c->d_nr_ptr, c->nr_ptr)) ||
       (rc = upload(c, &c->d_nr_col, c->nr_col)) || (rc = upload(c, &c->d_nr_blk, c->nr_blk)) ||
       (rc = upload(c, &c->d_pc_ptr, pcp)) || (rc = upload(c, &c->d_pc_col, pcc)) ||
@@ -547,6 +594,7 @@ int smr_destroy(smr_ctx* h) {
   if (!h) return SMR_OK;
   cudaSetDevice(h->c.device);
   free_scene(&h->c);
+  nn_free(&h->c);
   if (h->c.d_red) cudaFree(h->c.d_red);
   if (h->c.h_red) cudaFreeHost(h->c.h_red);
   delete h;
@@ -570,7 +618,22 @@ int smr_set_scene(smr_ctx* h, int p, const double* centres, const int* shape_ids
   if (!h || !eps_in || !mu_in || !eps_out || !mu_out) return SMR_E_INVALID_ARG;
   Ctx* c = &h->c;
   if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, SMR_E_CUDA, "cudaSetDevice");
-  int rc = set_scene(c, p, centres, shape_ids, eps_in, mu_in, eps_out, mu_out);
+  int rc = set_scene(c, p, centres, shape_ids, nullptr, eps_in, mu_in, eps_out, mu_out);
+  if (rc) {
+    std::string msg = c->err;
+    free_scene(c);
+    c->err = msg;
+  }
+  return rc;
+}
+
+int smr_set_scene_arrays(smr_ctx* h, int p, const double* centres, const int* shape_ids,
+                         const int* array_ids, const double eps_in[2], const double mu_in[2],
+                         const double eps_out[2], const double mu_out[2]) {
+  if (!h || !eps_in || !mu_in || !eps_out || !mu_out || !array_ids) return SMR_E_INVALID_ARG;
+  Ctx* c = &h->c;
+  if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, SMR_E_CUDA, "cudaSetDevice");
+  int rc = set_scene(c, p, centres, shape_ids, array_ids, eps_in, mu_in, eps_out, mu_out);
   if (rc) {
     std::string msg = c->err;
     free_scene(c);
@@ -588,6 +651,7 @@ int smr_info(smr_ctx* h, smr_info_t* info) {
   info->n_psi = c->npsi;
   info->n_shapes = c->S;
   info->n_levels = c->nlev;
+  info->n_arrays = c->n_arrays;
   info->n_unknowns = n_unknowns(c);
   double bytes = 0;
   for (int s = 0; s < c->nlev; ++s) {
@@ -750,6 +814,132 @@ int smr_profile_matvec(smr_ctx* h, int R, const void* x, void* y, int precision,
   if (rc) return rc;
   if (e != cudaSuccess) return fail(c, SMR_E_CUDA, cudaGetErrorString(e));
   return SMR_OK;
+}
+
+// ---------------------------------------------------------------- per-array incidence and the learned guess
+namespace {
+int upload_inc(Ctx* c, int n, const double* khat, const double* pol, double** dk, double** dp) {
+  std::vector<double> kh(khat, khat + 3 * (size_t)n), pl(pol, pol + 6 * (size_t)n);
+  int rc = upload(c, dk, kh);
+  if (rc) return rc;
+  return upload(c, dp, pl);
+}
+}  // namespace
+
+int smr_rhs_plane_waves_arrays(smr_ctx* h, const double* khat, const double* pol, void* b, void* stream) {
+  if (!h || !khat || !pol || !b) return SMR_E_INVALID_ARG;
+  Ctx* c = &h->c;
+  if (!check_scene(c)) return SMR_E_STATE;
+  double *dk = nullptr, *dp = nullptr;
+  int rc = upload_inc(c, c->n_arrays, khat, pol, &dk, &dp);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  rc = launch_rhs_arrays(c, dk, (const double2*)dp, (double2*)b, st);
+  cudaStreamSynchronize(st);
+  cudaFree(dk);
+  cudaFree(dp);
+  return rc;
+}
+
+int smr_nn_init(smr_ctx* h, int width, unsigned long long seed) {
+  if (!h) return SMR_E_INVALID_ARG;
+  Ctx* c = &h->c;
+  if (!check_scene(c)) return SMR_E_STATE;
+  return nn_init(c, width, seed);
+}
+
+long long smr_nn_num_params(smr_ctx* h) { return h ? h->c.nn.np : 0; }
+
+int smr_nn_get_params(smr_ctx* h, float* out, long long n) {
+  if (!h || !out) return SMR_E_INVALID_ARG;
+  Ctx* c = &h->c;
+  if (!c->nn.p32 || n != c->nn.np) return fail(c, SMR_E_INVALID_ARG, "parameter count mismatch");
+  SMR_CUDA(c, cudaMemcpy(out, c->nn.p32, n * sizeof(float), cudaMemcpyDeviceToHost));
+  return SMR_OK;
+}
+
+int smr_nn_set_params(smr_ctx* h, const float* in, long long n) {
+  if (!h || !in) return SMR_E_INVALID_ARG;
+  Ctx* c = &h->c;
+  if (!c->nn.p32 || n != c->nn.np) return fail(c, SMR_E_INVALID_ARG, "parameter count mismatch");
+  SMR_CUDA(c, cudaMemcpy(c->nn.p32, in, n * sizeof(float), cudaMemcpyHostToDevice));
+  std::vector<float> z((size_t)n, 0.f);
+  SMR_CUDA(c, cudaMemcpy(c->nn.m, z.data(), n * sizeof(float), cudaMemcpyHostToDevice));
+  SMR_CUDA(c, cudaMemcpy(c->nn.v, z.data(), n * sizeof(float), cudaMemcpyHostToDevice));
+  c->nn.step = 0;
+  // refresh the BF16 copies through one zero-learning-rate Adam step
+  SMR_CUDA(c, cudaMemset(c->nn.g, 0, n * sizeof(float)));
+  int rc = nn_adam(c, 0.f, 0);
+  c->nn.step = 0;
+  if (rc) return rc;
+  SMR_CUDA(c, cudaDeviceSynchronize());
+  return SMR_OK;
+}
+
+int smr_nn_features(smr_ctx* h, const double* khat, const double* pol, float* feat, void* stream) {
+  if (!h || !khat || !pol || !feat) return SMR_E_INVALID_ARG;
+  Ctx* c = &h->c;
+  if (!check_scene(c)) return SMR_E_STATE;
+  double *dk = nullptr, *dp = nullptr;
+  int rc = upload_inc(c, c->n_arrays, khat, pol, &dk, &dp);
+  if (rc) return rc;
+  rc = nn_features(c, dk, dp, feat, (cudaStream_t)stream);
+  cudaFree(dk);
+  cudaFree(dp);
+  return rc;
+}
+
+int smr_nn_targets(smr_ctx* h, const double* khat, const void* x, double scale, float* tgt, void* stream) {
+  if (!h || !khat || !x || !tgt || !(scale > 0)) return SMR_E_INVALID_ARG;
+  Ctx* c = &h->c;
+  if (!check_scene(c)) return SMR_E_STATE;
+  std::vector<double> kh(khat, khat + 3 * (size_t)c->n_arrays);
+  double* dk = nullptr;
+  int rc = upload(c, &dk, kh);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  rc = nn_targets(c, dk, (const double2*)x, scale, tgt, st);
+  cudaStreamSynchronize(st);
+  cudaFree(dk);
+  return rc;
+}
+
+int smr_nn_train_step(smr_ctx* h, int n, const float* feat, const int* idx, const float* tgt, float lr,
+                      double* loss, void* stream) {
+  if (!h || !feat || !tgt || n <= 0) return SMR_E_INVALID_ARG;
+  Ctx* c = &h->c;
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc = nn_forward_backward(c, n, feat, idx, tgt, true, loss, st);
+  if (rc) return rc;
+  return nn_adam(c, lr, st);
+}
+
+int smr_nn_loss_grad(smr_ctx* h, int n, const float* feat, const int* idx, const float* tgt, double* loss,
+                     float* grad, void* stream) {
+  if (!h || !feat || !tgt || n <= 0) return SMR_E_INVALID_ARG;
+  Ctx* c = &h->c;
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc = nn_forward_backward(c, n, feat, idx, tgt, true, loss, st);
+  if (rc) return rc;
+  if (grad) {
+    SMR_CUDA(c, cudaMemcpyAsync(grad, c->nn.g, c->nn.np * sizeof(float), cudaMemcpyDeviceToHost, st));
+    SMR_CUDA(c, cudaStreamSynchronize(st));
+  }
+  return SMR_OK;
+}
+
+int smr_nn_predict(smr_ctx* h, const double* khat, const double* pol, double scale, void* x0, void* stream) {
+  if (!h || !khat || !pol || !x0 || !(scale > 0)) return SMR_E_INVALID_ARG;
+  Ctx* c = &h->c;
+  if (!check_scene(c)) return SMR_E_STATE;
+  if (!c->nn.p32) return fail(c, SMR_E_STATE, "call smr_nn_init first");
+  double *dk = nullptr, *dp = nullptr;
+  int rc = upload_inc(c, c->n_arrays, khat, pol, &dk, &dp);
+  if (rc) return rc;
+  rc = nn_predict(c, dk, dp, scale, (double2*)x0, (cudaStream_t)stream);
+  cudaFree(dk);
+  cudaFree(dp);
+  return rc;
 }
 
 int smr_copy_pattern(smr_ctx* h, int shape, double* out) {

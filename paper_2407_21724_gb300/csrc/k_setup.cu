@@ -460,6 +460,39 @@ int launch_rhs(Ctx* c, int R, const double* d_khat, const double2* d_pol, double
   return SMR_OK;
 }
 
+// per-array incidence: b[mu][c][n] = exp(-j k khat_a . r_mu) Sv[s_mu][n][c][a], a = arr[mu]
+__global__ void k_rhs_scatter_arrays(int p, int npsi, int na, const int* __restrict__ sid,
+                                     const int* __restrict__ arr, const double* __restrict__ cen,
+                                     const double* __restrict__ khat, const double2* __restrict__ Sv,
+                                     double kw, double2* __restrict__ b) {
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= (long long)p * 2 * npsi) return;
+  int n = (int)(t % npsi), cc = (int)((t / npsi) % 2), mu = (int)(t / (2 * npsi));
+  int a = arr[mu];
+  const double* kh = khat + 3 * a;
+  const double* x = cen + 3 * mu;
+  double sn, cs;
+  sincos(-kw * (kh[0] * x[0] + kh[1] * x[1] + kh[2] * x[2]), &sn, &cs);
+  double2 v = Sv[(((size_t)sid[mu] * npsi + n) * 2 + cc) * na + a];
+  b[t] = make_double2(v.x * cs - v.y * sn, v.x * sn + v.y * cs);
+}
+
+int launch_rhs_arrays(Ctx* c, const double* d_khat, const double2* d_pol, double2* b, cudaStream_t st) {
+  int na = c->n_arrays;
+  double2* Sv = nullptr;
+  SMR_CUDA(c, cudaMallocAsync((void**)&Sv, (size_t)c->S * c->npsi * 2 * na * sizeof(double2), st));
+  long long t1 = (long long)c->S * c->npsi * na;
+  k_rhs_shape<<<(unsigned)((t1 + 127) / 128), 128, 0, st>>>(c->S, c->npsi, c->Q, na, c->d_modes, c->d_rq,
+                                                           d_khat, d_pol, c->k, c->zeta, Sv);
+  SMR_LAUNCH(c);
+  long long t2 = (long long)c->p * 2 * c->npsi;
+  k_rhs_scatter_arrays<<<(unsigned)((t2 + 255) / 256), 256, 0, st>>>(c->p, c->npsi, na, c->d_sid, c->d_arr,
+                                                                    c->d_centres, d_khat, Sv, c->k, b);
+  SMR_LAUNCH(c);
+  SMR_CUDA(c, cudaFreeAsync(Sv, st));
+  return SMR_OK;
+}
+
 // Same two kernels with caller-provided scratch Sv [S][n_psi][2][R] (no allocation).
 int launch_rhs_scratch(Ctx* c, int R, const double* d_khat, const double2* d_pol, double2* Sv,
                        double2* b, cudaStream_t st) {

@@ -1,6 +1,7 @@
 // Internal declarations of libsmr: context, per-level tables, kernel launchers.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <complex>
@@ -99,6 +100,21 @@ struct Level {
   size_t spec_bytes = 0;
 };
 
+struct NN {
+  int F = 448, H = 0, O = 0, nl = 4;
+  int dims[5] = {0, 0, 0, 0, 0};
+  long long np = 0;                     // parameter count
+  float* p32 = nullptr;                 // master parameters (W_l [in][out] then b_l [out], per layer)
+  __nv_bfloat16* w16 = nullptr;         // BF16 copies of the weight matrices (same offsets)
+  float *m = nullptr, *v = nullptr, *g = nullptr;
+  long long step = 0;
+  int cap = 0;                          // rows of the activation buffers
+  float* act = nullptr;                 // activations and pre-activations
+  float* dact = nullptr;
+  double* d_loss = nullptr;
+  int* d_slots = nullptr;               // [48][2] neighbour offsets, sorted
+};
+
 // one profiled launch: algorithmic bytes / flops and CUDA events around it
 struct ProfRec {
   const char* name;
@@ -115,7 +131,7 @@ struct Ctx {
   std::vector<Shape> shapes;
   bool have_scene = false;
   // scene
-  int p = 0, npsi = 0, S = 0, nlev = 0;
+  int p = 0, npsi = 0, S = 0, nlev = 0, n_arrays = 1;
   double k = 0, zeta = 1, k_in = 0, zeta_in = 1;
   std::vector<double> centres;          // [p][3]
   std::vector<int> sid;                 // [p]
@@ -132,6 +148,8 @@ struct Ctx {
   float2* d_P32 = nullptr;
   // particles
   int* d_sid = nullptr;
+  std::vector<int> arr;                 // [p] array id of each particle
+  int* d_arr = nullptr;
   double* d_centres = nullptr;          // [p][3]
   double* d_dshift = nullptr;           // [p][3] r_mu - c_box (finest level)
   int any_dshift = 0;
@@ -156,6 +174,7 @@ struct Ctx {
   int* d_tile_start = nullptr;
   int* d_tile_count = nullptr;
   int* d_perm = nullptr;                // particles sorted by shape
+  NN nn;
   // work buffers
   void* d_G = nullptr;                  // separable-pass intermediate
   size_t G_bytes = 0;
@@ -218,12 +237,25 @@ int build_translations(Ctx* c);   // per level d_T64 / d_T32 on the GPU (FP64)
 int build_near(Ctx* c);           // d_B64 / d_B32 on the GPU (FP64) + self blocks
 int launch_rhs(Ctx* c, int R, const double* d_khat, const double2* d_pol, double2* b,
                cudaStream_t st);
+// R = 1 right-hand side with incidence number arr[mu] for particle mu
+// (host khat/pol hold one plane wave per array)
+int launch_rhs_arrays(Ctx* c, const double* d_khat, const double2* d_pol, double2* b, cudaStream_t st);
 int launch_rhs_scratch(Ctx* c, int R, const double* d_khat, const double2* d_pol, double2* Sv,
                        double2* b, cudaStream_t st);
 int launch_far_field(Ctx* c, int R, const double2* x, int nd, const double* d_dirs,
                      double2* F, cudaStream_t st);
 int launch_near_field(Ctx* c, int R, const double2* x, int npt, const double* d_pts,
                       double2* EH, cudaStream_t st);
+
+// ------------------------------------------------------------------ learned initial guess (k_learned.cu)
+int nn_init(Ctx* c, int width, unsigned long long seed);
+void nn_free(Ctx* c);
+int nn_features(Ctx* c, const double* d_khat, const double* d_pol, float* feat, cudaStream_t st);
+int nn_targets(Ctx* c, const double* d_khat, const double2* x, double scale, float* tgt, cudaStream_t st);
+int nn_forward_backward(Ctx* c, int n, const float* feat, const int* idx, const float* tgt, bool backward,
+                        double* loss_host, cudaStream_t st);
+int nn_adam(Ctx* c, float lr, cudaStream_t st);
+int nn_predict(Ctx* c, const double* d_khat, const double* d_pol, double scale, double2* x0, cudaStream_t st);
 
 // ------------------------------------------------------------------ hot path (k_mlfma.cu)
 int ensure_spectra(Ctx* c, int R, int prec);

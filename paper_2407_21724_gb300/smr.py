@@ -37,6 +37,7 @@ class smr_opts(C.Structure):
 
 class smr_info_t(C.Structure):
     _fields_ = [("p", C.c_int), ("n_psi", C.c_int), ("n_shapes", C.c_int), ("n_levels", C.c_int),
+                ("n_arrays", C.c_int),
                 ("n_unknowns", C.c_longlong), ("L", C.c_int * 16), ("K", C.c_int * 16),
                 ("n_box", C.c_int * 16), ("n_il", C.c_int * 16), ("n_near_pairs", C.c_longlong),
                 ("n_near_blocks", C.c_int), ("device_bytes", C.c_double)]
@@ -68,6 +69,8 @@ _SIGS = {
     "smr_last_error": (C.c_char_p, [_P]),
     "smr_add_sphere": (C.c_int, [_P, C.c_double, C.c_int, C.c_int, C.POINTER(C.c_int)]),
     "smr_set_scene": (C.c_int, [_P, C.c_int, _D, C.POINTER(C.c_int), _D, _D, _D, _D]),
+    "smr_set_scene_arrays": (C.c_int, [_P, C.c_int, _D, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                       _D, _D, _D, _D]),
     "smr_info": (C.c_int, [_P, C.POINTER(smr_info_t)]),
     "smr_rhs_plane_waves": (C.c_int, [_P, C.c_int, _D, _D, _P, _P]),
     "smr_rhs_plane_waves_static": (C.c_int, [_P, C.c_int, _P, _P, _P, _P]),
@@ -81,6 +84,16 @@ _SIGS = {
     "smr_near_field": (C.c_int, [_P, C.c_int, _P, C.c_int, _D, _P, _P]),
     "smr_profile_matvec": (C.c_int, [_P, C.c_int, _P, _P, C.c_int, C.POINTER(smr_launch_t), C.c_int,
                                      C.POINTER(C.c_int), _P]),
+    "smr_rhs_plane_waves_arrays": (C.c_int, [_P, _D, _D, _P, _P]),
+    "smr_nn_init": (C.c_int, [_P, C.c_int, C.c_ulonglong]),
+    "smr_nn_num_params": (C.c_longlong, [_P]),
+    "smr_nn_get_params": (C.c_int, [_P, C.POINTER(C.c_float), C.c_longlong]),
+    "smr_nn_set_params": (C.c_int, [_P, C.POINTER(C.c_float), C.c_longlong]),
+    "smr_nn_features": (C.c_int, [_P, _D, _D, _P, _P]),
+    "smr_nn_targets": (C.c_int, [_P, _D, _P, C.c_double, _P, _P]),
+    "smr_nn_train_step": (C.c_int, [_P, C.c_int, _P, _P, _P, C.c_float, _D, _P]),
+    "smr_nn_loss_grad": (C.c_int, [_P, C.c_int, _P, _P, _P, _D, C.POINTER(C.c_float), _P]),
+    "smr_nn_predict": (C.c_int, [_P, _D, _D, C.c_double, _P, _P]),
     "smr_copy_pattern": (C.c_int, [_P, C.c_int, _D]),
     "smr_copy_translation": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _D]),
     "smr_copy_near_block": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_int, _D]),
@@ -183,11 +196,37 @@ def smr_set_scene(ctx, centres, shape_ids, eps_in, eps_out=1.0, mu_in=1.0, mu_ou
                                     _dptr(ei), _dptr(mi), _dptr(eo), _dptr(mo)))
 
 
+def smr_set_scene_arrays(ctx, centres, shape_ids, array_ids, eps_in, eps_out=1.0, mu_in=1.0, mu_out=1.0):
+    c = np.ascontiguousarray(centres, dtype=np.float64).reshape(-1, 3)
+    s = np.ascontiguousarray(shape_ids, dtype=np.int32).ravel()
+    a = np.ascontiguousarray(array_ids, dtype=np.int32).ravel()
+    cx = lambda v: np.array([np.real(v), np.imag(v)], dtype=np.float64)
+    ei, mi, eo, mo = cx(eps_in), cx(mu_in), cx(eps_out), cx(mu_out)
+    ip = C.POINTER(C.c_int)
+    _check(ctx, lib().smr_set_scene_arrays(ctx, c.shape[0], _dptr(c), s.ctypes.data_as(ip),
+                                           a.ctypes.data_as(ip), _dptr(ei), _dptr(mi), _dptr(eo),
+                                           _dptr(mo)))
+
+
+def scene_from_arrays(ws, **opts):
+    """One context holding several workload dicts as independent arrays."""
+    w0 = ws[0]
+    ctx = smr_create(pitch=w0["pitch"], **opts)
+    for (a, npp, npl) in w0["shapes"]:
+        smr_add_sphere(ctx, a, npp, npl)
+    C_ = np.concatenate([w["centres"] for w in ws])
+    S_ = np.concatenate([w["shape_ids"] for w in ws])
+    A_ = np.concatenate([np.full(len(w["centres"]), i, dtype=np.int32) for i, w in enumerate(ws)])
+    smr_set_scene_arrays(ctx, C_, S_, A_, w0["eps_in"])
+    return ctx
+
+
 def smr_info(ctx):
     i = smr_info_t()
     _check(ctx, lib().smr_info(ctx, C.byref(i)))
     n = i.n_levels
-    return dict(p=i.p, n_psi=i.n_psi, n_shapes=i.n_shapes, n_levels=n, n_unknowns=i.n_unknowns,
+    return dict(p=i.p, n_psi=i.n_psi, n_shapes=i.n_shapes, n_levels=n, n_arrays=i.n_arrays,
+                n_unknowns=i.n_unknowns,
                 L=list(i.L[:n]), K=list(i.K[:n]), n_box=list(i.n_box[:n]), n_il=list(i.n_il[:n]),
                 n_near_pairs=i.n_near_pairs, n_near_blocks=i.n_near_blocks,
                 device_bytes=i.device_bytes)
@@ -280,6 +319,75 @@ def smr_profile_matvec(ctx, x, y, precision=SMR_PREC_FP64, R=None, stream=None):
                                          _stream(stream, x)))
     return [dict(name=arr[i].name.decode(), level=arr[i].level, bytes=arr[i].bytes,
                  flops=arr[i].flops, ms=arr[i].ms) for i in range(min(n.value, 256))]
+
+
+def _inc(khat, pol):
+    kh = np.ascontiguousarray(khat, dtype=np.float64).reshape(-1, 3)
+    pl = np.ascontiguousarray(np.asarray(pol, dtype=np.complex128).reshape(-1, 3))
+    return kh, pl, pl.view(np.float64)
+
+
+def _fptr(t):
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+def smr_rhs_plane_waves_arrays(ctx, khat, pol, b, stream=None):
+    kh, pl, pv = _inc(khat, pol)
+    _check(ctx, lib().smr_rhs_plane_waves_arrays(ctx, _dptr(kh), _dptr(pv), _ptr(b), _stream(stream, b)))
+
+
+def smr_nn_init(ctx, width=256, seed=0):
+    _check(ctx, lib().smr_nn_init(ctx, int(width), int(seed)))
+
+
+def smr_nn_num_params(ctx):
+    return int(lib().smr_nn_num_params(ctx))
+
+
+def smr_nn_get_params(ctx):
+    n = smr_nn_num_params(ctx)
+    out = np.empty(n, dtype=np.float32)
+    _check(ctx, lib().smr_nn_get_params(ctx, out.ctypes.data_as(C.POINTER(C.c_float)), n))
+    return out
+
+
+def smr_nn_set_params(ctx, params):
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    _check(ctx, lib().smr_nn_set_params(ctx, p.ctypes.data_as(C.POINTER(C.c_float)), p.size))
+
+
+def smr_nn_features(ctx, khat, pol, feat, stream=None):
+    kh, pl, pv = _inc(khat, pol)
+    _check(ctx, lib().smr_nn_features(ctx, _dptr(kh), _dptr(pv), _fptr(feat), _stream(stream, feat)))
+
+
+def smr_nn_targets(ctx, khat, x, scale, tgt, stream=None):
+    kh = np.ascontiguousarray(khat, dtype=np.float64).reshape(-1, 3)
+    _check(ctx, lib().smr_nn_targets(ctx, _dptr(kh), _ptr(x), float(scale), _fptr(tgt), _stream(stream, x)))
+
+
+def smr_nn_train_step(ctx, n, feat, tgt, lr, idx=None, stream=None):
+    loss = C.c_double()
+    _check(ctx, lib().smr_nn_train_step(ctx, int(n), _fptr(feat), _fptr(idx), _fptr(tgt), float(lr),
+                                        C.byref(loss), _stream(stream, feat)))
+    return loss.value
+
+
+def smr_nn_loss_grad(ctx, n, feat, tgt, idx=None, stream=None):
+    loss = C.c_double()
+    g = np.empty(smr_nn_num_params(ctx), dtype=np.float32)
+    _check(ctx, lib().smr_nn_loss_grad(ctx, int(n), _fptr(feat), _fptr(idx), _fptr(tgt), C.byref(loss),
+                                       g.ctypes.data_as(C.POINTER(C.c_float)), _stream(stream, feat)))
+    return loss.value, g
+
+
+def smr_nn_predict(ctx, khat, pol, scale, x0, stream=None):
+    kh, pl, pv = _inc(khat, pol)
+    _check(ctx, lib().smr_nn_predict(ctx, _dptr(kh), _dptr(pv), float(scale), _ptr(x0), _stream(stream, x0)))
 
 
 def smr_copy_pattern(ctx, shape):

@@ -95,3 +95,32 @@ def make(name, **kw):
         return [make('random', n=int(round(10 + 50 * i / 15)), seed=21726 + i,
                      modes=kw.get('modes', 16)) for i in range(16)]
     raise KeyError(name)
+
+
+def mlp_params(dims, seed):
+    """Seeded MLP parameters (layer by layer, W [in][out] then b) whose values
+    are exactly representable in bfloat16 (the top 16 bits of a float32)."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for l in range(4):
+        a = np.sqrt(6.0 / (dims[l] + dims[l + 1]))
+        parts.append(rng.uniform(-a, a, size=dims[l] * dims[l + 1]))
+        parts.append(rng.uniform(-0.1, 0.1, size=dims[l + 1]))
+    p = np.concatenate(parts).astype(np.float32)
+    return (p.view(np.uint32) & np.uint32(0xFFFF0000)).view(np.float32)
+
+
+def training_arrays(count, n=20, seed0=100000, modes=16):
+    """Random n x n arrays for the learned initial guess: radius index
+    U{0..7} and one incidence per array (theta ~ U[0, 40 deg), phi ~ U[0,
+    360 deg), x or y polarisation), array i drawn from seed seed0 + i."""
+    out = []
+    for i in range(count):
+        rng = np.random.default_rng(seed0 + i)
+        ids = rng.integers(0, 8, size=n * n).astype(np.int32)
+        th, ph = rng.uniform(0.0, 40.0), rng.uniform(0.0, 360.0)
+        pol = 'x' if rng.integers(0, 2) == 0 else 'y'
+        out.append(dict(label=f'{n}x{n} training array {seed0 + i}', centres=lattice(n, n),
+                        shape_ids=ids, shapes=[(r, modes, modes) for r in RADII8],
+                        eps_in=EPS_IN, pitch=PITCH, incidences=[incidence(th, ph, pol)]))
+    return out

@@ -1,0 +1,166 @@
+"""Ragged batches (several independent arrays in one context) and the
+learned initial guess, through the C ABI, against the FP64 oracle."""
+import math
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from oracle import mlfma as oml
+from oracle import mlp as omlp
+from oracle import pmchwt as opm
+from paper_2407_21724_gb300 import smr, workloads
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+@pytest.fixture(scope="module")
+def ragged():
+    ws = [workloads.make("random", n=n, seed=40 + n, modes=16) for n in (5, 9, 6)]
+    keep = np.ones(81, dtype=bool)
+    keep[[10, 44]] = False                           # holes in the 9x9 array
+    ws[1]["centres"], ws[1]["shape_ids"] = ws[1]["centres"][keep], ws[1]["shape_ids"][keep]
+    for i, w in enumerate(ws):                       # arrays in their own, shifted frames
+        w["centres"] = w["centres"] + np.array([3.0 * i, -1.5 * i, 0.0])
+    ctx = smr.scene_from_arrays(ws)
+    yield ws, ctx
+    smr.smr_destroy(ctx)
+
+
+def test_ragged_batch_is_block_diagonal(ragged):
+    """One product over three arrays equals each array's own oracle product."""
+    ws, ctx = ragged
+    info = smr.smr_info(ctx)
+    assert info["n_arrays"] == 3
+    n = info["n_unknowns"]
+    rng = np.random.default_rng(3)
+    x = (rng.standard_normal(n) + 1j * rng.standard_normal(n)) / math.sqrt(2)
+    xd = torch.from_numpy(x).cuda()
+    yd = torch.empty_like(xd)
+    smr.smr_matvec(ctx, xd, yd, smr.SMR_PREC_FP64)
+    torch.cuda.synchronize()
+    y = yd.cpu().numpy()
+    o = 0
+    for w in ws:
+        sc = opm.Scene(w["centres"], w["shape_ids"], w["shapes"], eps_in=w["eps_in"])
+        m = sc.n_unknowns
+        y0 = oml.MLFMA(sc, w["pitch"]).matvec(x[o:o + m])
+        assert rel(y[o:o + m], y0) < 1e-10
+        o += m
+
+
+def test_per_array_incidence_rhs(ragged):
+    ws, ctx = ragged
+    inc = [workloads.incidence(10.0 * i, 37.0 * i, "xy"[i % 2]) for i in range(3)]
+    n = smr.smr_info(ctx)["n_unknowns"]
+    b = torch.empty(n, dtype=torch.complex128, device="cuda")
+    smr.smr_rhs_plane_waves_arrays(ctx, [k for k, _ in inc], [p for _, p in inc], b)
+    torch.cuda.synchronize()
+    g = b.cpu().numpy()
+    o = 0
+    for w, (kh, pol) in zip(ws, inc):
+        sc = opm.Scene(w["centres"], w["shape_ids"], w["shapes"], eps_in=w["eps_in"])
+        ref = opm.rhs(sc, kh, pol)
+        assert rel(g[o:o + ref.size], ref) < 1e-13
+        o += ref.size
+
+
+def test_features_match_oracle(ragged):
+    ws, ctx = ragged
+    inc = [workloads.incidence(5.0 + i, 100.0 * i, "xy"[i % 2]) for i in range(3)]
+    kh, pol = [k for k, _ in inc], [p for _, p in inc]
+    smr.smr_nn_init(ctx, width=8, seed=1)
+    p = sum(len(w["centres"]) for w in ws)
+    feat = torch.empty((p, 448), dtype=torch.float32, device="cuda")
+    smr.smr_nn_features(ctx, kh, pol, feat)
+    torch.cuda.synchronize()
+    C = np.concatenate([w["centres"] for w in ws])
+    S = np.concatenate([w["shape_ids"] for w in ws])
+    A = np.concatenate([np.full(len(w["centres"]), i) for i, w in enumerate(ws)])
+    F0 = omlp.features(C, S, A, kh, pol).astype(np.float32)
+    assert np.array_equal(feat.cpu().numpy(), F0)
+
+
+def test_mlp_gradient_matches_oracle(ragged):
+    """GPU forward/backward (BF16 weights, FP32 arithmetic) against FP64
+    backpropagation on the same BF16-exact weights: loss to 1e-5 and the
+    gradient to 1e-4 relative."""
+    ws, ctx = ragged
+    smr.smr_nn_init(ctx, width=16, seed=2)
+    dims = [448, 16, 16, 16, 128]
+    params = workloads.mlp_params(dims, 11)
+    assert smr.smr_nn_num_params(ctx) == params.size
+    smr.smr_nn_set_params(ctx, params)
+    rng = np.random.default_rng(5)
+    X = (rng.random((37, 448)) < 0.15).astype(np.float32)
+    T = (0.3 * rng.standard_normal((37, 128))).astype(np.float32)
+    loss, g = smr.smr_nn_loss_grad(ctx, 37, torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda())
+    loss0, g0 = omlp.loss_grad(params.astype(np.float64), dims, X.astype(np.float64), T.astype(np.float64))
+    assert abs(loss / loss0 - 1) < 1e-5
+    assert np.linalg.norm(g - g0) / np.linalg.norm(g0) < 1e-4
+    # an Adam step lowers the loss on the same batch
+    Xd, Td = torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda()
+    l0 = smr.smr_nn_train_step(ctx, 37, Xd, Td, 1e-3)
+    for _ in range(20):
+        l1 = smr.smr_nn_train_step(ctx, 37, Xd, Td, 1e-3)
+    assert l1 < l0
+
+
+def test_learned_initial_guess_gains_over_zero():
+    """Train on 48 solved 16x16 arrays (one batched solve), then on a held-out
+    20x20 array the network's guess must start GMRES well below the zero
+    guess's residual and save iterations to 1e-4."""
+    train = workloads.training_arrays(48, n=16, seed0=100000)
+    ctx = smr.scene_from_arrays(train)
+    n = smr.smr_info(ctx)["n_unknowns"]
+    kh = [w["incidences"][0][0] for w in train]
+    pol = [w["incidences"][0][1] for w in train]
+    b = torch.empty(n, dtype=torch.complex128, device="cuda")
+    smr.smr_rhs_plane_waves_arrays(ctx, kh, pol, b)
+    x = torch.zeros_like(b)
+    rc, st = smr.smr_solve(ctx, b, x, tol=1e-5, precision=smr.SMR_PREC_FP32)
+    assert rc == 0
+    scale = float(torch.sqrt(torch.mean(torch.abs(x) ** 2)))
+    p = smr.smr_info(ctx)["p"]
+    smr.smr_nn_init(ctx, width=128, seed=7)
+    feat = torch.empty((p, 448), dtype=torch.float32, device="cuda")
+    tgt = torch.empty((p, 128), dtype=torch.float32, device="cuda")
+    smr.smr_nn_features(ctx, kh, pol, feat)
+    smr.smr_nn_targets(ctx, kh, x, scale, tgt)
+    rng = np.random.default_rng(0)
+    losses = []
+    for it in range(600):
+        idx = torch.from_numpy(rng.integers(0, p, size=2048).astype(np.int32)).cuda()
+        losses.append(smr.smr_nn_train_step(ctx, 2048, feat, tgt, 2e-3 if it < 400 else 5e-4, idx=idx))
+    params = smr.smr_nn_get_params(ctx)
+    smr.smr_destroy(ctx)
+    assert np.mean(losses[-20:]) < 0.3 * np.mean(losses[:20])
+
+    test = workloads.training_arrays(1, n=20, seed0=555)[0]
+    ctx = smr.scene_from_arrays([test])
+    kh1, pol1 = [test["incidences"][0][0]], [test["incidences"][0][1]]
+    n1 = smr.smr_info(ctx)["n_unknowns"]
+    b1 = torch.empty(n1, dtype=torch.complex128, device="cuda")
+    smr.smr_rhs_plane_waves_arrays(ctx, kh1, pol1, b1)
+    smr.smr_nn_init(ctx, width=128, seed=0)
+    smr.smr_nn_set_params(ctx, params)
+    x0 = torch.empty_like(b1)
+    smr.smr_nn_predict(ctx, kh1, pol1, scale, x0)
+    y = torch.empty_like(b1)
+    smr.smr_matvec(ctx, x0, y, smr.SMR_PREC_FP64)
+    torch.cuda.synchronize()
+    r0 = float(torch.linalg.norm(b1 - y) / torch.linalg.norm(b1))
+    assert r0 < 0.5
+    xz = torch.zeros_like(b1)
+    _, s0 = smr.smr_solve(ctx, b1, xz, tol=1e-4)
+    xl = x0.clone()
+    _, s1 = smr.smr_solve(ctx, b1, xl, tol=1e-4, use_x0=1)
+    assert s1["iters"] < s0["iters"]
+    smr.smr_destroy(ctx)
