@@ -32,7 +32,10 @@ if "reference" in sys.argv:
 
 WORKLOADS = {
     "metalens200": ("metalens", dict(n=200, focal=50.0)),
+    "metalens150": ("metalens", dict(n=150, focal=40.0)),
     "random40": ("random", dict(n=40, seed=21724)),
+    "batched100x64": ("random", dict(n=100, seed=21725)),
+    "ragged16": ("ragged16", {}),
     "spheres8x8": ("spheres8x8", {}),
 }
 METRIC = "MLFMA-SMR matvecs/s and GMRES time to 1e-4 residual, tuned vs plain FP64"
@@ -48,6 +51,8 @@ def parse():
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--sample", type=int, default=20, help="side of the oracle's sample sub-array")
+    ap.add_argument("--train-arrays", type=int, default=400,
+                    help="20x20 arrays solved to train the learned initial guess (0: skip)")
     return ap.parse_args()
 
 
@@ -84,7 +89,7 @@ def central_sample(w, side):
     return C[idx], w["shape_ids"][idx]
 
 
-def oracle_sample_rate(w, side, steps, warmup):
+def oracle_sample_rate(w, side, steps, warmup, full_flops=None):
     """Time the FP64 oracle's MLFMA product on the central sub-array and scale
     to full-workload products/s by the algorithmic flop ratio."""
     import numpy as np
@@ -103,7 +108,8 @@ def oracle_sample_rate(w, side, steps, warmup):
             times.append(time.perf_counter() - t0)
     t = float(np.mean(times))
     n_psi = w["shapes"][0][1] + w["shapes"][0][2]
-    ratio = algorithmic_flops(w["centres"], w["pitch"], n_psi) / algorithmic_flops(Cs, w["pitch"], n_psi)
+    full = full_flops if full_flops is not None else algorithmic_flops(w["centres"], w["pitch"], n_psi)
+    ratio = full / algorithmic_flops(Cs, w["pitch"], n_psi)
     return 1.0 / (t * ratio), t, ratio, len(Cs)
 
 
@@ -114,16 +120,26 @@ def run_reference(a):
         return
     from paper_2407_21724_gb300 import workloads
     name, kw = WORKLOADS[a.workload]
-    w = workloads.make(name, **kw)
-    rate, t, ratio, ps = oracle_sample_rate(w, min(a.sample, int(len(w["centres"]) ** 0.5)),
-                                            a.steps, a.warmup)
-    sample = (f"FP64 NumPy oracle MLFMA product on the central {int(ps ** 0.5)}x{int(ps ** 0.5)} "
-              f"sub-array ({ps} particles), {t:.3f} s per product, scaled by the algorithmic flop "
-              f"ratio {ratio:.1f} to the full workload")
+    R = 64 if a.workload == "batched100x64" else 1
+    if a.workload == "ragged16":
+        ws = workloads.make(name, **kw)
+        w = dict(ws[-1])                   # sample from the largest array
+        n_psi = w["shapes"][0][1] + w["shapes"][0][2]
+        full_fl = sum(algorithmic_flops(v["centres"], v["pitch"], n_psi) for v in ws)
+        label = "ragged batch of 16 random arrays, 10x10 ... 60x60, one product"
+    else:
+        w = workloads.make(name, **kw)
+        full_fl = None
+        label = w["label"]
+    side = min(a.sample, int(round(len(w["centres"]) ** 0.5)))
+    rate, t, ratio, ps = oracle_sample_rate(w, side, a.steps, a.warmup, full_fl)
+    sample = (f"FP64 NumPy oracle MLFMA product on the central {side}x{side} sub-array "
+              f"({ps} particles), {t:.3f} s per product, scaled by the algorithmic flop "
+              f"ratio {ratio:.1f} to the full workload (per right-hand side)")
     line = dict(metric=METRIC, value=rate, unit="matvecs/s", n_gpus=a.gpus, steps=a.steps,
                 warmup=a.warmup, ms_per_step=1e3 / rate, higher_is_better=True, scaling="weak",
                 vs_baseline=None, dtype="f64", data="synthetic", impl="reference",
-                config=dict(workload=w["label"], rhs=1, l2="inputs larger than L2 (CPU run)"),
+                config=dict(workload=label, rhs=R, l2="inputs larger than L2 (CPU run)"),
                 cpu_baseline=dict(value=rate, unit="matvecs/s", cores=1, kind="oracle", sample=sample),
                 e2e=dict(value=rate, unit="matvecs/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     print(json.dumps(line), flush=True)
@@ -183,6 +199,61 @@ def traffic_for(kernel):
     return rec["dram_bytes_per_launch"] if h == rec["sha"] else None
 
 
+def train_learned(smr, workloads, n_arrays, dev, n_side=20, width=256, steps=1500, batch=4096):
+    """Solve n_arrays random n_side x n_side arrays (ragged batches of up to
+    100, one incidence each, FP32-inner refinement to 1e-6), then train the
+    MLP on their de-phased coefficients.  Returns parameters and timings."""
+    import numpy as np
+    import torch
+    t0 = time.perf_counter()
+    feats, tgts, xs = [], [], []
+    arrays = workloads.training_arrays(n_arrays, n=n_side, seed0=100000)
+    chunks = [arrays[i:i + 100] for i in range(0, n_arrays, 100)]
+    sols = []
+    for ch in chunks:
+        ctx = smr.scene_from_arrays(ch)
+        nn_ = smr.smr_info(ctx)["n_unknowns"]
+        kh = [w["incidences"][0][0] for w in ch]
+        pol = [w["incidences"][0][1] for w in ch]
+        b = torch.empty(nn_, dtype=torch.complex128, device=dev)
+        smr.smr_rhs_plane_waves_arrays(ctx, kh, pol, b)
+        x = torch.zeros_like(b)
+        smr.smr_solve(ctx, b, x, tol=1e-6, precision=smr.SMR_PREC_FP32, maxit=3000)
+        sols.append((ctx, kh, pol, x))
+    t_data = time.perf_counter() - t0
+    scale = float(torch.sqrt(torch.mean(torch.cat([torch.abs(s[3]) ** 2 for s in sols]))))
+    for ctx, kh, pol, x in sols:
+        p = smr.smr_info(ctx)["p"]
+        smr.smr_nn_init(ctx, width=8, seed=0)          # features need an initialised network
+        f = torch.empty((p, 448), dtype=torch.float32, device=dev)
+        t = torch.empty((p, 128), dtype=torch.float32, device=dev)
+        smr.smr_nn_features(ctx, kh, pol, f)
+        smr.smr_nn_targets(ctx, kh, x, scale, t)
+        feats.append(f)
+        tgts.append(t)
+    F = torch.cat(feats)
+    T = torch.cat(tgts)
+    for ctx, *_ in sols[1:]:
+        smr.smr_destroy(ctx)
+    ctx = sols[0][0]
+    smr.smr_nn_init(ctx, width=width, seed=1)
+    rng = np.random.default_rng(0)
+    N = F.shape[0]
+    torch.cuda.synchronize(dev)
+    t1 = time.perf_counter()
+    losses = []
+    for it in range(steps):
+        idx = torch.from_numpy(rng.integers(0, N, size=batch).astype(np.int32)).to(dev)
+        lr = 2e-3 if it < steps * 2 // 3 else 5e-4
+        losses.append(smr.smr_nn_train_step(ctx, batch, F, T, lr, idx=idx))
+    t_train = time.perf_counter() - t1
+    params = smr.smr_nn_get_params(ctx)
+    smr.smr_destroy(ctx)
+    return dict(params=params, scale=scale, width=width, arrays=n_arrays, samples=int(N),
+                data_seconds=t_data, train_seconds=t_train, steps=steps, batch=batch,
+                loss_first=float(np.mean(losses[:20])), loss_last=float(np.mean(losses[-20:])))
+
+
 def run_ours(a):
     import numpy as np
     import torch
@@ -197,18 +268,31 @@ def run_ours(a):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local)
     name, kw = WORKLOADS[a.workload]
-    w = workloads.make(name, **kw)
     t0 = time.perf_counter()
-    ctx = smr.scene_from_workload(w, device=local)
+    if a.workload == "ragged16":
+        ws = workloads.make(name, **kw)
+        w = dict(label="ragged batch of 16 random arrays, 10x10 ... 60x60, one product",
+                 pitch=ws[0]["pitch"])
+        ctx = smr.scene_from_arrays(ws, device=local)
+        incs = [(v["incidences"][0][0], v["incidences"][0][1]) for v in ws]
+    else:
+        w = workloads.make(name, **kw)
+        ctx = smr.scene_from_workload(w, device=local)
+        incs = [w["incidences"][0]]
     setup_s = time.perf_counter() - t0
     info = smr.smr_info(ctx)
     n = info["n_unknowns"]
+    R = 64 if a.workload == "batched100x64" else 1
     st = torch.cuda.current_stream(dev)
-    b = torch.empty(n, dtype=torch.complex128, device=dev)
-    kh, pol = w["incidences"][0]
-    smr.smr_rhs_plane_waves(ctx, [kh], [pol], b)
+    if R > 1:
+        grid = workloads.incidence_grid64()
+        b = torch.empty(n * R, dtype=torch.complex128, device=dev)
+        smr.smr_rhs_plane_waves(ctx, [k for k, _ in grid], [q for _, q in grid], b)
+    else:
+        b = torch.empty(n, dtype=torch.complex128, device=dev)
+        smr.smr_rhs_plane_waves_arrays(ctx, [k for k, _ in incs], [q for _, q in incs], b)
     rng = np.random.default_rng(rank)
-    x = torch.from_numpy(rng.standard_normal(n) + 1j * rng.standard_normal(n)).to(dev)
+    x = torch.from_numpy(rng.standard_normal(n * R) + 1j * rng.standard_normal(n * R)).to(dev)
     y = torch.empty_like(x)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # 256 MB > 129 MB L2
     P32 = smr.SMR_PREC_FP32
@@ -244,11 +328,11 @@ def run_ours(a):
         ms_total = float(t.item())
         dist.barrier()
     ms_step = ms_total / a.steps
-    value = world * a.steps / (ms_total / 1e3)
+    value = world * R * a.steps / (ms_total / 1e3)      # right-hand-side products per second
 
     # ---- plain FP64 products (same protocol, fewer steps)
     k64 = max(3, a.steps // 4)
-    ms64 = timed(smr.SMR_PREC_FP64, k64, 2) / k64
+    ms64 = timed(smr.SMR_PREC_FP64, k64, 2) / k64 / R
 
     # ---- per-launch profile of the tuned product (CUDA events around every launch)
     prof_runs = [smr.smr_profile_matvec(ctx, x, y, P32) for _ in range(max(3, a.steps // 4))]
@@ -281,7 +365,7 @@ def run_ours(a):
     launches = len(prof_runs[0])
 
     # ---- end to end through the C ABI with host buffers (copies timed)
-    xh = torch.from_numpy(rng.standard_normal(n) + 1j * rng.standard_normal(n)).pin_memory()
+    xh = torch.from_numpy(rng.standard_normal(n * R) + 1j * rng.standard_normal(n * R)).pin_memory()
     yh = torch.empty_like(xh).pin_memory()
     xa, ya = xh.numpy(), yh.numpy()
     lib = smr.lib()
@@ -289,31 +373,49 @@ def run_ours(a):
     D = C.POINTER(C.c_double)
     px, py = xa.ctypes.data_as(D), ya.ctypes.data_as(D)
     for _ in range(2):
-        lib.smr_matvec_host(ctx, 1, px, py, P32, st.cuda_stream)
+        lib.smr_matvec_host(ctx, R, px, py, P32, st.cuda_stream)
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     ke = max(3, a.steps // 2)
     for _ in range(ke):
-        rc = lib.smr_matvec_host(ctx, 1, px, py, P32, st.cuda_stream)
+        rc = lib.smr_matvec_host(ctx, R, px, py, P32, st.cuda_stream)
         assert rc == 0
-    e2e_s = (time.perf_counter() - t0) / ke
+    e2e_s = (time.perf_counter() - t0) / ke / R
 
-    # ---- GMRES to 1e-4 (tuned and plain), after the timed region
+    # ---- GMRES to 1e-4 (tuned, tuned + learned initial guess, plain FP64)
     gm = None
     if not a.no_solve:
         gm = {}
-        for label, prec in (("tuned_fp32_inner_fp64_outer", P32), ("plain_fp64", smr.SMR_PREC_FP64)):
-            xs = torch.zeros_like(b)
+        learned = None
+        if a.train_arrays > 0 and R == 1:
+            learned = train_learned(smr, workloads, a.train_arrays, dev)
+
+        def solve(label, prec, x0=None):
+            xs = torch.zeros_like(b) if x0 is None else x0.clone()
             torch.cuda.synchronize(dev)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(st)
-            rc, stt = smr.smr_solve(ctx, b, xs, tol=1e-4, precision=prec, maxit=3000)
+            extra = {}
+            if x0 is not None:
+                # the guess is part of the solve: features + network + re-phasing
+                smr.smr_nn_predict(ctx, [k for k, _ in incs], [q for _, q in incs], learned["scale"], xs)
+                extra["use_x0"] = 1
+            rc, stt = smr.smr_solve(ctx, b, xs, R=R, tol=1e-4, precision=prec, maxit=3000, **extra)
             e1.record(st)
             torch.cuda.synchronize(dev)
             stt["solver_seconds"] = stt.pop("seconds")
             gm[label] = dict(seconds=e0.elapsed_time(e1) / 1e3, converged=(rc == 0), **stt)
-        gm["speedup_tuned_vs_plain"] = (gm["plain_fp64"]["seconds"] /
-                                        gm["tuned_fp32_inner_fp64_outer"]["seconds"])
+
+        solve("tuned_fp32_inner_fp64_outer", P32)
+        if learned is not None:
+            smr.smr_nn_init(ctx, width=learned["width"], seed=0)
+            smr.smr_nn_set_params(ctx, learned["params"])
+            solve("tuned_plus_learned_x0", P32, x0=torch.zeros_like(b))
+            gm["learned_training"] = {k: v for k, v in learned.items() if k not in ("params",)}
+        solve("plain_fp64", smr.SMR_PREC_FP64)
+        best = min(v["seconds"] for k, v in gm.items() if k.startswith("tuned") and isinstance(v, dict)
+                   and "seconds" in v)
+        gm["speedup_tuned_vs_plain"] = gm["plain_fp64"]["seconds"] / best
 
     # ---- CPU oracle baseline on a bounded sample (rank 0, N = 1 only)
     cpu = None
@@ -330,7 +432,7 @@ def run_ours(a):
         line = dict(metric=METRIC, value=value, unit="matvecs/s", n_gpus=world, steps=a.steps,
                     warmup=a.warmup, ms_per_step=ms_step, higher_is_better=True, scaling="weak",
                     vs_baseline=None, dtype="f32", data="synthetic",
-                    config=dict(workload=w["label"], rhs=1, precision="FP32 product, FP64 tables/IO",
+                    config=dict(workload=w["label"], rhs=R, precision="FP32 product, FP64 tables/IO",
                                 l2="L2 flushed (256 MB write) before every timed step",
                                 parallelism="replicas" if world > 1 else "single GPU",
                                 levels=info["n_levels"], L=info["L"], unknowns=n),

@@ -36,7 +36,7 @@ void free_scene(Ctx* c) {
     dfree(L.d_shift32); dfree(L.d_ant_ptr); dfree(L.d_ant_idx); dfree(L.d_ant_w64); dfree(L.d_ant_w32);
     dfree(L.d_tht_ptr); dfree(L.d_tht_tp); dfree(L.d_tht_refl); dfree(L.d_tht_w64); dfree(L.d_tht_w32);
     dfree(L.d_pht_ptr); dfree(L.d_pht_jp); dfree(L.d_pht_w64); dfree(L.d_pht_w32); dfree(L.d_wthp64);
-    dfree(L.d_wthp32); dfree(L.d_boxmap); dfree(L.d_offid);
+    dfree(L.d_wthp32); dfree(L.d_boxmap); dfree(L.d_offid); dfree(L.d_tiles); dfree(L.d_tiles8);
     if (L.d_out) cudaFree(L.d_out);
     if (L.d_in) cudaFree(L.d_in);
     L.d_out = L.d_in = nullptr;
@@ -450,9 +450,34 @@ int set_scene(Ctx* c, int p, const double* centres, const int* shape_ids, const 
     L.map_x0 = x0; L.map_y0 = y0; L.map_w = x1 - x0 + 1; L.map_h = y1 - y0 + 1;
     std::vector<int> bm((size_t)L.map_w * L.map_h, -1), oid(49, -1);
     for (int b = 0; b < L.nbox; ++b) bm[(size_t)(L.bj[b] - y0) * L.map_w + (L.bi[b] - x0)] = b;
-    for (size_t o = 0; o < L.off_dx.size(); ++o) oid[(L.off_dx[o] + 3) * 7 + (L.off_dy[o] + 3)] = (int)o;
+    // translation tables are stored by lattice offset: row (dx + 3) * 7 + (dy + 3)
+    for (size_t o = 0; o < L.off_dx.size(); ++o) {
+      int g = (L.off_dx[o] + 3) * 7 + (L.off_dy[o] + 3);
+      oid[g] = g;
+    }
+    L.ntile_x = ((x0 + L.map_w - 1) >> 2) - (x0 >> 2) + 1;
+    L.ntile_y = ((y0 + L.map_h - 1) >> 2) - (y0 >> 2) + 1;
+    std::vector<char> used((size_t)L.ntile_x * L.ntile_y, 0);
+    for (int b = 0; b < L.nbox; ++b)
+      used[(size_t)((L.bj[b] >> 2) - (y0 >> 2)) * L.ntile_x + ((L.bi[b] >> 2) - (x0 >> 2))] = 1;
+    std::vector<int> tiles;
+    for (size_t t = 0; t < used.size(); ++t)
+      if (used[t]) tiles.push_back((int)t);
+    L.ntile_ne = (int)tiles.size();
+    L.ntile8_x = ((x0 + L.map_w - 1) >> 3) - (x0 >> 3) + 1;
+    int nt8y = ((y0 + L.map_h - 1) >> 3) - (y0 >> 3) + 1;
+    std::vector<char> used8((size_t)L.ntile8_x * nt8y, 0);
+    for (int b = 0; b < L.nbox; ++b)
+      used8[(size_t)((L.bj[b] >> 3) - (y0 >> 3)) * L.ntile8_x + ((L.bi[b] >> 3) - (x0 >> 3))] = 1;
+    std::vector<int> tiles8;
+    for (size_t t = 0; t < used8.size(); ++t)
+      if (used8[t]) tiles8.push_back((int)t);
+    L.ntile8_ne = (int)tiles8.size();
     int rc;
-    if ((rc = upload(c, &L.d_boxmap, bm)) || (rc = upload(c, &L.d_offid, oid))) return rc;
+    if ((rc = upload(c, &L.d_tiles8, tiles8))) return rc;
+    if ((rc = upload(c, &L.d_boxmap, bm)) || (rc = upload(c, &L.d_offid, oid)) ||
+        (rc = upload(c, &L.d_tiles, tiles)))
+      return rc;
   }
   // particles grouped by shape, tiles of at most 16
   {
@@ -960,7 +985,8 @@ int smr_copy_translation(smr_ctx* h, int level, int dx, int dy, double* out) {
   Level& L = c->lev[level];
   for (size_t o = 0; o < L.off_dx.size(); ++o)
     if (L.off_dx[o] == dx && L.off_dy[o] == dy) {
-      SMR_CUDA(c, cudaMemcpy(out, L.d_T64 + o * L.K, L.K * sizeof(double2), cudaMemcpyDeviceToHost));
+      size_t row = (size_t)(dx + 3) * 7 + (dy + 3);
+      SMR_CUDA(c, cudaMemcpy(out, L.d_T64 + row * L.K, L.K * sizeof(double2), cudaMemcpyDeviceToHost));
       return SMR_OK;
     }
   return fail(c, SMR_E_INVALID_ARG, "offset not in this level's interaction lists");

@@ -219,6 +219,74 @@ __global__ void k_interp_phi(int nrows, int nthP, int nphP, int nphC, int R,
   }
 }
 
+// Fused interpolation: per parent box and tile of TR parent rows, each child's
+// theta pass goes to shared memory and the phi pass, shift and child sum are
+// accumulated in registers (at most EMAX outputs per thread).
+constexpr int EMAX = 12;
+template <typename T, bool R1>
+__global__ void k_interp_fused(int nthP, int nphP, int nphC, int Kc, int R, int TR, int nrt,
+                               const int* __restrict__ ch_ptr, const int* __restrict__ ch_idx,
+                               const int* __restrict__ ch_quad, const int* __restrict__ th_src,
+                               const int* __restrict__ th_refl, const T* __restrict__ th_w,
+                               const int* __restrict__ ph_src, const T* __restrict__ ph_w,
+                               const typename CV<T>::V* __restrict__ shift,
+                               const typename CV<T>::V* __restrict__ F, typename CV<T>::V* __restrict__ out) {
+  typedef typename CV<T>::V V;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* G = reinterpret_cast<V*>(smem_raw);           // [TR][nphC][4R]
+  int B = blockIdx.x / nrt, rt = blockIdx.x % nrt;
+  int tp0 = rt * TR, ntr = min(TR, nthP - tp0);
+  int R4 = 4 * R, Kp = nthP * nphP;
+  int rowG = nphC * R4, rowP = nphP * R4;
+  int nG = ntr * rowG, nel = ntr * rowP;
+  int half = nphC >> 1;
+  V acc[EMAX];
+#pragma unroll
+  for (int i = 0; i < EMAX; ++i) acc[i] = czero<V>();
+  for (int e = ch_ptr[B]; e < ch_ptr[B + 1]; ++e) {
+    const V* src = F + (size_t)ch_idx[e] * Kc * R4;
+    const V* sh = shift + (size_t)ch_quad[e] * Kp + (size_t)tp0 * nphP;
+    __syncthreads();
+    for (int t = threadIdx.x; t < nG; t += blockDim.x) {
+      int tr = t / rowG, rem = t - tr * rowG;
+      int j, fr;
+      split_e<R1>(rem, R4, &j, &fr);
+      int tp = tp0 + tr;
+      int jr = j + half;
+      jr = jr >= nphC ? jr - nphC : jr;
+      V a = czero<V>();
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        int refl = th_refl[tp * 4 + q];
+        T w = refl ? -th_w[tp * 4 + q] : th_w[tp * 4 + q];
+        rfma(a, w, src[(size_t)(th_src[tp * 4 + q] * nphC + (refl ? jr : j)) * R4 + fr]);
+      }
+      G[t] = a;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < EMAX; ++i) {
+      int t = threadIdx.x + i * blockDim.x;
+      if (t < nel) {
+        int tr = t / rowP, rem = t - tr * rowP;
+        int jp, fr;
+        split_e<R1>(rem, R4, &jp, &fr);
+        const V* g = G + tr * rowG + fr;
+        V sum = czero<V>();
+#pragma unroll
+        for (int b = 0; b < 4; ++b) rfma(sum, ph_w[jp * 4 + b], g[ph_src[jp * 4 + b] * R4]);
+        cfma(acc[i], sh[tr * nphP + jp], sum);
+      }
+    }
+  }
+  V* dst = out + ((size_t)B * Kp + (size_t)tp0 * nphP) * R4;
+#pragma unroll
+  for (int i = 0; i < EMAX; ++i) {
+    int t = threadIdx.x + i * blockDim.x;
+    if (t < nel) dst[t] = acc[i];
+  }
+}
+
 // ------------------------------------------------------------------ translation
 // in[b][k] = sum_{(b', o) in IL(b)} T[o][k] out[b'][k]   (Eqs. 22-23)
 // One CTA = 4x4 target boxes of the lattice x a chunk of directions; the 8x8
@@ -244,16 +312,16 @@ __device__ __forceinline__ void load4(const double2* p, double2* v) {
 }
 
 template <typename T>
-__global__ void k_translate(int K, int R, int RC, int KC, int ntx, int nty, int map_x0, int map_y0,
-                            int map_w, int map_h, int noff, const int* __restrict__ boxmap,
+__global__ void k_translate(int K, int R, int RC, int KC, int ntx, int ntile, const int* __restrict__ tiles,
+                            int map_x0, int map_y0, int map_w, int map_h, int noff,
+                            const int* __restrict__ boxmap,
                             const int* __restrict__ offid, const typename CV<T>::V* __restrict__ Tt,
                             const typename CV<T>::V* __restrict__ out,
                             typename CV<T>::V* __restrict__ in) {
   typedef typename CV<T>::V V;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  int ntile = ntx * nty;
   int nrc = (R + RC - 1) / RC;
-  int tile = blockIdx.x % ntile;
+  int tile = tiles[blockIdx.x % ntile];
   int rest = blockIdx.x / ntile;
   int rch = rest % nrc, kch = rest / nrc;
   int tx = tile % ntx, ty = tile / ntx;
@@ -289,6 +357,26 @@ __global__ void k_translate(int K, int R, int RC, int KC, int ntx, int nty, int 
         nb = 16;
       }
       cp_async16(reinterpret_cast<char*>(S + (size_t)sb * W) + pc * 16, g, nb);
+    }
+  } else if ((R * (int)sizeof(V)) % 16 == 0 && (RC * (int)sizeof(V)) % 16 == 0) {
+    // asynchronous 16-byte copies of each (source, direction, field) run of RC
+    // columns (aligned: R and RC span whole 16-byte pieces), zero-filled for
+    // missing boxes, past the last direction and past the last column
+    int pr = RC * (int)sizeof(V) / 16;               // pieces per run
+    int per = KC * 4 * pr;                           // pieces per source box
+    for (int t = threadIdx.x; t < 64 * per; t += blockDim.x) {
+      int sb = t / per, e = t - sb * per;
+      int run = e / pr, pc = e - run * pr;           // run = kl * 4 + f
+      int kl = run >> 2;
+      int b = bid[sb];
+      const char* g = reinterpret_cast<const char*>(out);
+      int nb = 0;
+      int col = pc * 16 / (int)sizeof(V);            // first column of the piece
+      if (b >= 0 && kl < nk && col < nr) {
+        g += ((((size_t)b * K + k0 + kl) * 4 + (run & 3)) * R + r0) * sizeof(V) + (size_t)pc * 16;
+        nb = 16;
+      }
+      cp_async16(reinterpret_cast<char*>(S + (size_t)sb * W + (size_t)run * RC) + pc * 16, g, nb);
     }
   } else {
     for (int t = threadIdx.x; t < 64 * W; t += blockDim.x) {
@@ -354,6 +442,103 @@ __global__ void k_translate(int K, int R, int RC, int KC, int ntx, int nty, int 
     }
     V* o = in + ((size_t)b * K + k0 + kl) * 4 * R + r0 + rl;
     for (int f = 0; f < 4; ++f) o[f * R] = acc[f];
+  }
+}
+
+// Single right-hand side: each thread owns the 2x2 targets that share one
+// parent, for one direction, and walks the parent's 6x6 source window once;
+// a source spectrum is read from shared memory once for all four targets.
+// CTA = 4x4 targets (2x2 parents) x KC directions; 4 x KC threads.
+template <typename T>
+__global__ void __launch_bounds__(256) k_translate1(int K, int KC, int ntx, int ntile,
+                                                    const int* __restrict__ tiles, int map_x0, int map_y0,
+                                                    int map_w, int map_h, const int* __restrict__ boxmap,
+                                                    const typename CV<T>::V* __restrict__ Tg,
+                                                    const typename CV<T>::V* __restrict__ out,
+                                                    typename CV<T>::V* __restrict__ in) {
+  typedef typename CV<T>::V V;
+  constexpr int TS = 8, HS = TS + 4;                  // targets per side, halo per side
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  int tile = tiles[blockIdx.x % ntile];
+  int kch = blockIdx.x / ntile;
+  int tx = tile % ntx, ty = tile / ntx;
+  int ax0 = ((map_x0 >> 3) + tx) * TS, ay0 = ((map_y0 >> 3) + ty) * TS;
+  int k0 = kch * KC;
+  int nk = min(KC, K - k0);
+  int W = KC * 4;
+  V* S = reinterpret_cast<V*>(smem_raw);              // [HS*HS sources][KC][4]
+  V* Ts = S + HS * HS * W;                            // [49 offsets][KC]
+  int* bid = reinterpret_cast<int*>(Ts + 49 * KC);   // [HS*HS] source box ids
+  int* tb = bid + HS * HS;                            // [TS*TS] target box ids
+  for (int t = threadIdx.x; t < HS * HS + TS * TS; t += blockDim.x) {
+    int sx, sy;
+    if (t < HS * HS) { sx = ax0 - 2 + t % HS; sy = ay0 - 2 + t / HS; }
+    else { int u = t - HS * HS; sx = ax0 + u % TS; sy = ay0 + u / TS; }
+    int lx = sx - map_x0, ly = sy - map_y0;
+    bid[t] = (lx >= 0 && ly >= 0 && lx < map_w && ly < map_h) ? boxmap[ly * map_w + lx] : -1;
+  }
+  __syncthreads();
+  {
+    int per = W * (int)sizeof(V) / 16;
+    int valid = nk * 4 * (int)sizeof(V);
+    for (int t = threadIdx.x; t < HS * HS * per; t += blockDim.x) {
+      int sb = t / per, pc = t - sb * per;
+      int b = bid[sb];
+      const char* g = reinterpret_cast<const char*>(out);
+      int nb = 0;
+      if (b >= 0 && pc * 16 < valid) {
+        g += ((size_t)b * K + k0) * 4 * sizeof(V) + (size_t)pc * 16;
+        nb = 16;
+      }
+      cp_async16(reinterpret_cast<char*>(S + (size_t)sb * W) + pc * 16, g, nb);
+    }
+  }
+  for (int t = threadIdx.x; t < 49 * KC; t += blockDim.x) {
+    int o = t / KC, kl = t - o * KC;
+    Ts[t] = (kl < nk) ? Tg[(size_t)o * K + k0 + kl] : czero<V>();
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  int kl = threadIdx.x % KC, par = threadIdx.x / KC;   // parent 0..15 of the tile
+  if (kl >= nk || par >= (TS / 2) * (TS / 2)) return;
+  int pxo = (par % (TS / 2)) * 2, pyo = (par / (TS / 2)) * 2;
+  bool any = false;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) any |= tb[(pyo + (q >> 1)) * TS + (pxo + (q & 1))] >= 0;
+  if (!any) return;
+  const V* Sp = S + (size_t)(pyo * HS + pxo) * W + kl * 4;   // window origin
+  const V* Tp = Ts + kl;
+  V acc[4][4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int f = 0; f < 4; ++f) acc[q][f] = czero<V>();
+  // the parent's 6x6 source window; target q = (q & 1, q >> 1) inside the
+  // parent; offset (dx, dy) = target - source is known at compile time
+#pragma unroll
+  for (int wy = 0; wy < 6; ++wy) {
+#pragma unroll
+    for (int wx = 0; wx < 6; ++wx) {
+      V v[4];
+      load4(Sp + (wy * HS + wx) * W, v);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int dx = (q & 1) + 2 - wx, dy = (q >> 1) + 2 - wy;
+        if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1) continue;
+        V tv = Tp[((dx + 3) * 7 + (dy + 3)) * KC];
+        cfma(acc[q][0], tv, v[0]);
+        cfma(acc[q][1], tv, v[1]);
+        cfma(acc[q][2], tv, v[2]);
+        cfma(acc[q][3], tv, v[3]);
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    int b = tb[(pyo + (q >> 1)) * TS + (pxo + (q & 1))];
+    if (b < 0) continue;
+    V* o = in + ((size_t)b * K + k0 + kl) * 4;
+    o[0] = acc[q][0]; o[1] = acc[q][1]; o[2] = acc[q][2]; o[3] = acc[q][3];
   }
 }
 
@@ -628,6 +813,22 @@ static int far_impl(Ctx* c, int R, const double2* x, double2* y, bool accumulate
     pbeg(c, st, "interpolate", s,
          ((double)Lc.nbox * Lc.K + (double)Lp.nbox * Lp.K) * 4 * R_ * es + 4.0 * Lp.K * es,
          (double)Lc.nbox * Lp.nth * Lc.nph * 4 * R_ * 16.0 + (double)Lc.nbox * Lp.K * 4 * R_ * 24.0);
+    // fused (shared-memory) version when a tile of parent rows fits
+    int TR = std::max(1, std::min(Lp.nth, (256 * EMAX) / (Lp.nph * 4 * R)));
+    size_t smf = (size_t)TR * Lc.nph * 4 * R * sizeof(V);
+    if (Lp.nph * 4 * R <= 256 * EMAX && smf <= 96 * 1024) {
+      int nrt = (Lp.nth + TR - 1) / TR;
+      auto kf = (R == 1) ? k_interp_fused<T, true> : k_interp_fused<T, false>;
+      cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+      kf<<<(unsigned)(Lp.nbox * nrt), 256, smf, st>>>(
+          Lp.nth, Lp.nph, Lc.nph, Lc.K, R, TR, nrt, Lp.d_ch_ptr, Lp.d_ch_idx, Lp.d_ch_quad, Lc.d_th_src,
+          Lc.d_th_refl, (const T*)(f64 ? (void*)Lc.d_th_w64 : (void*)Lc.d_th_w32), Lc.d_ph_src,
+          (const T*)(f64 ? (void*)Lc.d_ph_w64 : (void*)Lc.d_ph_w32),
+          (const V*)(f64 ? (void*)Lc.d_shift64 : (void*)Lc.d_shift32), (const V*)Lc.d_out, (V*)Lp.d_out);
+      SMR_LAUNCH(c);
+      pend(c, st);
+      continue;
+    }
     int rows1 = Lc.nbox * Lp.nth;
     auto kth = (R == 1) ? k_interp_theta<T, true> : k_interp_theta<T, false>;
     kth<<<(unsigned)((rows1 + 7) / 8), 256, 0, st>>>(
@@ -646,9 +847,11 @@ static int far_impl(Ctx* c, int R, const double2* x, double2* y, bool accumulate
   // translation at every level
   for (int s = 0; s < c->nlev; ++s) {
     Level& L = c->lev[s];
-    int noff = (int)L.off_dx.size();
-    int ntx = ((L.map_x0 + L.map_w - 1) >> 2) - (L.map_x0 >> 2) + 1;
-    int nty = ((L.map_y0 + L.map_h - 1) >> 2) - (L.map_y0 >> 2) + 1;
+    if (L.off_dx.empty()) {                  // no interaction list at this level
+      SMR_CUDA(c, cudaMemsetAsync(L.d_in, 0, L.spec_bytes, st));
+      continue;
+    }
+    int noff = 49;                           // tables by lattice offset (7 x 7 grid)
     int cap = f64 ? 16 : 32;                 // directions x columns staged per CTA
     int RCt = std::min(R, cap);
     int KC = std::max(1, cap / RCt);
@@ -657,12 +860,25 @@ static int far_impl(Ctx* c, int R, const double2* x, double2* y, bool accumulate
     size_t sm = ((size_t)64 * KC * 4 * RCt + (size_t)std::max(noff, 1) * KC) * sizeof(V) +
                 (64 + 16 + 16) * sizeof(int) + 16 * 27 * sizeof(int2);
     cudaFuncSetAttribute(k_translate<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_translate1<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     pbeg(c, st, "translate", s,
-         2.0 * L.nbox * L.K * 4 * R_ * es + (double)noff * L.K * es,
+         2.0 * L.nbox * L.K * 4 * R_ * es + (double)L.off_dx.size() * L.K * es,
          8.0 * L.il_src.size() * L.K * 4 * R_);
-    k_translate<T><<<(unsigned)(ntx * nty * nkch * nrct), 256, sm, st>>>(
-        L.K, R, RCt, KC, ntx, nty, L.map_x0, L.map_y0, L.map_w, L.map_h, noff, L.d_boxmap, L.d_offid,
-        (const V*)(f64 ? (void*)L.d_T64 : (void*)L.d_T32), (const V*)L.d_out, (V*)L.d_in);
+    // single right-hand side: 8x8-tile register-blocked kernel, except on
+    // levels whose few boxes would leave most of one 8x8 tile idle
+    if (R == 1 && !(L.ntile8_ne == 1 && L.nbox < 32)) {
+      int KC1 = f64 ? 8 : 16;
+      int nk1 = (L.K + KC1 - 1) / KC1;
+      size_t sm1 = ((size_t)144 * KC1 * 4 + (size_t)49 * KC1) * sizeof(V) + (144 + 64) * sizeof(int);
+      k_translate1<T><<<(unsigned)(L.ntile8_ne * nk1), 16 * KC1, sm1, st>>>(
+          L.K, KC1, L.ntile8_x, L.ntile8_ne, L.d_tiles8, L.map_x0, L.map_y0, L.map_w, L.map_h, L.d_boxmap,
+          (const V*)(f64 ? (void*)L.d_T64 : (void*)L.d_T32), (const V*)L.d_out, (V*)L.d_in);
+    } else {
+      k_translate<T><<<(unsigned)(L.ntile_ne * nkch * nrct), 256, sm, st>>>(
+          L.K, R, RCt, KC, L.ntile_x, L.ntile_ne, L.d_tiles, L.map_x0, L.map_y0, L.map_w, L.map_h, noff,
+          L.d_boxmap, L.d_offid,
+          (const V*)(f64 ? (void*)L.d_T64 : (void*)L.d_T32), (const V*)L.d_out, (V*)L.d_in);
+    }
     SMR_LAUNCH(c);
     pend(c, st);
   }

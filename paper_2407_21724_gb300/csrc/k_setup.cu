@@ -154,17 +154,22 @@ __global__ void k_ttable(int noff, int K, int L, const double* __restrict__ khat
   T[t] = make_double2(pre * acc.y, -pre * acc.x);
 }
 
+// Tables are stored for the whole 7 x 7 grid of lattice offsets, row
+// (dx + 3) * 7 + (dy + 3); the 9 rows of adjacent offsets (never translated)
+// are zero.
 int build_translations(Ctx* c) {
   for (int s = 0; s < c->nlev; ++s) {
     Level& L = c->lev[s];
-    int noff = (int)L.off_dx.size();
+    const int noff = 49;
     if (L.d_T64) cudaFree(L.d_T64);
     L.d_T64 = nullptr;
-    if (noff == 0) continue;
-    std::vector<double2> coef((size_t)noff * (L.L + 1));
-    std::vector<double> xhat(3 * noff);
+    if (L.off_dx.empty()) continue;
+    std::vector<double2> coef((size_t)noff * (L.L + 1), make_double2(0, 0));
+    std::vector<double> xhat(3 * noff, 0.0);
     for (int o = 0; o < noff; ++o) {
-      double X[2] = {L.off_dx[o] * L.box, L.off_dy[o] * L.box};
+      int dx = o / 7 - 3, dy = o % 7 - 3;
+      if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1) { xhat[3 * o] = 1.0; continue; }
+      double X[2] = {dx * L.box, dy * L.box};
       double r = std::sqrt(X[0] * X[0] + X[1] * X[1]);
       xhat[3 * o] = X[0] / r; xhat[3 * o + 1] = X[1] / r; xhat[3 * o + 2] = 0.0;
       std::vector<double> jl, yl;

@@ -89,6 +89,10 @@ struct Level {
   int map_x0 = 0, map_y0 = 0, map_w = 0, map_h = 0;
   int* d_boxmap = nullptr;               // [map_h][map_w] box index or -1
   int* d_offid = nullptr;                // [7][7] offset (dx+3, dy+3) -> table row or -1
+  int ntile_x = 0, ntile_y = 0, ntile_ne = 0;
+  int* d_tiles = nullptr;                // non-empty 4x4 translation tiles (ty * ntile_x + tx)
+  int ntile8_x = 0, ntile8_ne = 0;
+  int* d_tiles8 = nullptr;               // non-empty 8x8 tiles (single right-hand side kernel)
   int* d_ant_ptr = nullptr;              // [K+1] weighted adjoint CSR (rows = this grid)
   int* d_ant_idx = nullptr;              // parent point index
   double* d_ant_w64 = nullptr;
