@@ -144,6 +144,15 @@ int smr_rhs_plane_waves(smr_ctx* ctx, int R, const double* khat, const double* p
  * FP64-generated tables (x and y stay FP64 complex).  device x, y [N][R]. */
 int smr_matvec(smr_ctx* ctx, int R, const void* x, void* y, int precision, void* stream);
 
+/* Same product replayed from a CUDA graph: the first call for a given
+ * (x, y, R, precision) captures every launch of smr_matvec on an internal
+ * stream (ordered after the work already queued on `stream`) and later calls
+ * launch the graph on `stream`, removing the per-kernel launch cost.  The
+ * graph keeps the device addresses of x, y and of the library's buffers:
+ * reuse it only while x and y stay allocated (smr_set_scene and a change of
+ * R or precision drop all graphs).  At most 16 graphs are kept. */
+int smr_matvec_graph(smr_ctx* ctx, int R, const void* x, void* y, int precision, void* stream);
+
 /* Same, split: y_near = near-field part, y_far = MLFMA far part (either may
  * be NULL).  For per-stage parity checks. */
 int smr_matvec_parts(smr_ctx* ctx, int R, const void* x, void* y_near, void* y_far,

@@ -28,6 +28,7 @@ template <typename T> void dfree(T*& p) {
 }
 
 void free_scene(Ctx* c) {
+  free_graphs(c);
   for (auto& L : c->lev) {
     dfree(L.d_khat); dfree(L.d_w); dfree(L.d_il_ptr); dfree(L.d_il_src); dfree(L.d_il_off);
     dfree(L.d_T64); dfree(L.d_T32); dfree(L.d_parent); dfree(L.d_quad); dfree(L.d_ch_ptr);
@@ -37,8 +38,11 @@ void free_scene(Ctx* c) {
     dfree(L.d_tht_ptr); dfree(L.d_tht_tp); dfree(L.d_tht_refl); dfree(L.d_tht_w64); dfree(L.d_tht_w32);
     dfree(L.d_pht_ptr); dfree(L.d_pht_jp); dfree(L.d_pht_w64); dfree(L.d_pht_w32); dfree(L.d_wthp64);
     dfree(L.d_wthp32); dfree(L.d_boxmap); dfree(L.d_offid); dfree(L.d_tiles); dfree(L.d_tiles8);
-    if (L.d_out) cudaFree(L.d_out);
-    if (L.d_in) cudaFree(L.d_in);
+    for (int q = 0; q < 2; ++q) {
+      if (L.buf_out[q]) cudaFree(L.buf_out[q]);
+      if (L.buf_in[q]) cudaFree(L.buf_in[q]);
+      L.buf_out[q] = L.buf_in[q] = nullptr;
+    }
     L.d_out = L.d_in = nullptr;
   }
   c->lev.clear();
@@ -48,7 +52,12 @@ void free_scene(Ctx* c) {
   dfree(c->d_pc_col); dfree(c->d_pc_blk); dfree(c->d_tmp);
   dfree(c->d_arr);
   dfree(c->d_tile_shape); dfree(c->d_tile_start); dfree(c->d_tile_count); dfree(c->d_perm);
-  if (c->d_G) cudaFree(c->d_G);
+  for (int q = 0; q < 2; ++q) {
+    if (c->G_buf[q]) cudaFree(c->G_buf[q]);
+    c->G_buf[q] = nullptr;
+    c->G_size[q] = 0;
+    c->buf_R[q] = 0;
+  }
   c->d_G = nullptr;
   c->G_bytes = 0;
   c->tmp_elems = 0;
@@ -724,6 +733,15 @@ int smr_matvec(smr_ctx* h, int R, const void* x, void* y, int precision, void* s
   int rc = run_near(c, R, precision, (const double2*)x, (double2*)y, st);
   if (rc) return rc;
   return run_far(c, R, precision, (const double2*)x, (double2*)y, true, st);
+}
+
+int smr_matvec_graph(smr_ctx* h, int R, const void* x, void* y, int precision, void* stream) {
+  if (!h || R <= 0 || R > 256 || !x || !y) return SMR_E_INVALID_ARG;
+  Ctx* c = &h->c;
+  if (!check_scene(c)) return SMR_E_STATE;
+  if (precision != SMR_PREC_FP64 && precision != SMR_PREC_FP32)
+    return fail(c, SMR_E_INVALID_ARG, "precision must be SMR_PREC_FP64 or SMR_PREC_FP32");
+  return run_matvec_graph(c, R, precision, (const double2*)x, (double2*)y, (cudaStream_t)stream);
 }
 
 int smr_matvec_parts(smr_ctx* h, int R, const void* x, void* y_near, void* y_far, int precision,

@@ -254,14 +254,17 @@ static int gmres_core(Ctx* c, int R, int prec, int precond, const double2* rhs, 
     int j = 0;
     for (; j < m && *its < maxit; ++j) {
       double2* Vj = W.V + (size_t)j * ld;
-      double2* zj = W.Z ? W.Z + (size_t)j * ld : W.t;
+      // z_j = M^-1 v_j in W.t (fixed address, so one captured graph serves
+      // every product of the solve); the flexible variant keeps a copy in Z_j
       if (precond == SMR_PRECOND_BLOCKDIAG) {
-        rc = run_precond(c, R, prec, Vj, zj, st);
+        rc = run_precond(c, R, prec, Vj, W.t, st);
       } else {
-        SMR_CUDA(c, cudaMemcpyAsync(zj, Vj, ld * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+        SMR_CUDA(c, cudaMemcpyAsync(W.t, Vj, ld * sizeof(double2), cudaMemcpyDeviceToDevice, st));
       }
       if (rc) return rc;
-      rc = apply_A(c, R, prec, zj, W.w, st);
+      if (W.Z)
+        SMR_CUDA(c, cudaMemcpyAsync(W.Z + (size_t)j * ld, W.t, ld * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+      rc = run_matvec_graph(c, R, prec, W.t, W.w, st);
       if (rc) return rc;
       ++*nmv;
       ++*its;

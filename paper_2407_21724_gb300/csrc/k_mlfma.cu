@@ -749,35 +749,52 @@ __global__ void k_blocksparse(int nrow, int n2, int R, int rc, int nrc, const in
 
 // ------------------------------------------------------------------ host drivers
 int ensure_spectra(Ctx* c, int R, int prec) {
-  if (c->spec_R == R && c->spec_prec == prec) return SMR_OK;
-  size_t es = (prec == SMR_PREC_FP64) ? sizeof(double2) : sizeof(float2);
-  size_t gmax = 0;
-  for (int s = 0; s < c->nlev; ++s) {
-    Level& L = c->lev[s];
-    if (L.d_out) cudaFree(L.d_out);
-    if (L.d_in) cudaFree(L.d_in);
-    L.d_out = L.d_in = nullptr;
-    size_t bytes = (size_t)L.nbox * L.K * 4 * R * es;
-    if (cudaMalloc(&L.d_out, bytes) != cudaSuccess || cudaMalloc(&L.d_in, bytes) != cudaSuccess) {
-      c->err = "out of device memory for level spectra";
-      c->spec_R = 0;
+  int p = (prec == SMR_PREC_FP64) ? 0 : 1;
+  if (c->buf_R[p] != R) {
+    // (re)allocate this precision's spectra; graphs built on them are dropped
+    for (size_t i = 0; i < c->graphs.size();) {
+      if (c->graphs[i].prec == prec) {
+        cudaGraphExecDestroy(c->graphs[i].exec);
+        c->graphs.erase(c->graphs.begin() + i);
+      } else {
+        ++i;
+      }
+    }
+    size_t es = (p == 0) ? sizeof(double2) : sizeof(float2);
+    size_t gmax = 0;
+    c->buf_R[p] = 0;
+    for (int s = 0; s < c->nlev; ++s) {
+      Level& L = c->lev[s];
+      if (L.buf_out[p]) cudaFree(L.buf_out[p]);
+      if (L.buf_in[p]) cudaFree(L.buf_in[p]);
+      L.buf_out[p] = L.buf_in[p] = nullptr;
+      size_t bytes = (size_t)L.nbox * L.K * 4 * R * es;
+      if (cudaMalloc(&L.buf_out[p], bytes) != cudaSuccess || cudaMalloc(&L.buf_in[p], bytes) != cudaSuccess) {
+        c->err = "out of device memory for level spectra";
+        c->spec_prec = -1;
+        return SMR_E_OOM;
+      }
+      L.buf_bytes[p] = bytes;
+      if (s + 1 < c->nlev)
+        gmax = std::max(gmax, (size_t)L.nbox * c->lev[s + 1].nth * L.nph * 4 * R * es);
+    }
+    if (c->G_buf[p]) cudaFree(c->G_buf[p]);
+    c->G_buf[p] = nullptr;
+    if (gmax && cudaMalloc(&c->G_buf[p], gmax) != cudaSuccess) {
+      c->err = "out of device memory for the separable-pass buffer";
       c->spec_prec = -1;
       return SMR_E_OOM;
     }
-    L.spec_bytes = bytes;
-    if (s + 1 < c->nlev)
-      gmax = std::max(gmax, (size_t)L.nbox * c->lev[s + 1].nth * L.nph * 4 * R * es);
+    c->G_size[p] = gmax;
+    c->buf_R[p] = R;
   }
-  if (c->d_G) cudaFree(c->d_G);
-  c->d_G = nullptr;
-  c->G_bytes = 0;
-  if (gmax && cudaMalloc(&c->d_G, gmax) != cudaSuccess) {
-    c->err = "out of device memory for the separable-pass buffer";
-    c->spec_R = 0;
-    c->spec_prec = -1;
-    return SMR_E_OOM;
+  for (auto& L : c->lev) {
+    L.d_out = L.buf_out[p];
+    L.d_in = L.buf_in[p];
+    L.spec_bytes = L.buf_bytes[p];
   }
-  c->G_bytes = gmax;
+  c->d_G = c->G_buf[p];
+  c->G_bytes = c->G_size[p];
   c->spec_R = R;
   c->spec_prec = prec;
   return SMR_OK;
@@ -956,6 +973,62 @@ int run_near(Ctx* c, int R, int prec, const double2* x, double2* y, cudaStream_t
                : bs_impl<float>(c, c->p, R, c->d_nr_ptr, c->d_nr_col, c->d_nr_blk, c->d_B32, x, y, false, st);
   pend(c, st);
   return rc;
+}
+
+void free_graphs(Ctx* c) {
+  for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
+  c->graphs.clear();
+  if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
+  c->capture_stream = nullptr;
+}
+
+int run_matvec_graph(Ctx* c, int R, int prec, const double2* x, double2* y, cudaStream_t st) {
+  for (auto& g : c->graphs)
+    if (g.x == x && g.y == y && g.R == R && g.prec == prec) {
+      SMR_CUDA(c, cudaGraphLaunch(g.exec, st));
+      return SMR_OK;
+    }
+  int rc = ensure_spectra(c, R, prec);            // allocations happen outside the capture
+  if (rc) return rc;
+  if (!c->capture_stream) SMR_CUDA(c, cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking));
+  cudaStream_t cs = c->capture_stream;
+  // order the capture stream after work already queued on the caller's stream
+  cudaEvent_t ev;
+  SMR_CUDA(c, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  SMR_CUDA(c, cudaEventRecord(ev, st));
+  SMR_CUDA(c, cudaStreamWaitEvent(cs, ev, 0));
+  SMR_CUDA(c, cudaStreamSynchronize(cs));
+  cudaEventDestroy(ev);
+  std::vector<ProfRec>* prof = c->prof;
+  c->prof = nullptr;
+  SMR_CUDA(c, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  rc = run_near(c, R, prec, x, y, cs);
+  if (!rc) rc = run_far(c, R, prec, x, y, true, cs);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(cs, &graph);
+  c->prof = prof;
+  if (rc) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  if (e != cudaSuccess) {
+    c->err = std::string("graph capture: ") + cudaGetErrorString(e);
+    return SMR_E_CUDA;
+  }
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    c->err = std::string("graph instantiate: ") + cudaGetErrorString(e);
+    return SMR_E_CUDA;
+  }
+  if (c->graphs.size() >= 16) {                  // keep a handful of recent products
+    cudaGraphExecDestroy(c->graphs.front().exec);
+    c->graphs.erase(c->graphs.begin());
+  }
+  c->graphs.push_back({x, y, R, prec, exec});
+  SMR_CUDA(c, cudaGraphLaunch(exec, st));
+  return SMR_OK;
 }
 
 int run_precond(Ctx* c, int R, int prec, const double2* r, double2* z, cudaStream_t st) {

@@ -99,9 +99,12 @@ struct Level {
   float* d_ant_w32 = nullptr;
   long long ant_nnz = 0;
   // spectra (allocated for the current R and precision)
-  void* d_out = nullptr;
+  void* d_out = nullptr;                 // active spectra (the last product's precision)
   void* d_in = nullptr;
   size_t spec_bytes = 0;
+  void* buf_out[2] = {nullptr, nullptr};   // per precision (SMR_PREC_FP64, SMR_PREC_FP32)
+  void* buf_in[2] = {nullptr, nullptr};
+  size_t buf_bytes[2] = {0, 0};
 };
 
 struct NN {
@@ -179,9 +182,21 @@ struct Ctx {
   int* d_tile_count = nullptr;
   int* d_perm = nullptr;                // particles sorted by shape
   NN nn;
+  // captured products: (x, y, R, precision) -> executable graph
+  struct GraphEntry {
+    const void* x;
+    void* y;
+    int R, prec;
+    cudaGraphExec_t exec;
+  };
+  std::vector<GraphEntry> graphs;
+  cudaStream_t capture_stream = nullptr;
   // work buffers
-  void* d_G = nullptr;                  // separable-pass intermediate
+  void* d_G = nullptr;                  // separable-pass intermediate (active precision)
   size_t G_bytes = 0;
+  void* G_buf[2] = {nullptr, nullptr};
+  size_t G_size[2] = {0, 0};
+  int buf_R[2] = {0, 0};
   int spec_R = 0, spec_prec = -1;
   double2* d_tmp = nullptr;             // [N][R] scratch for split products
   size_t tmp_elems = 0;
@@ -267,6 +282,9 @@ int run_near(Ctx* c, int R, int prec, const double2* x, double2* y, cudaStream_t
 int run_far(Ctx* c, int R, int prec, const double2* x, double2* y, bool accumulate,
             cudaStream_t st);
 int run_precond(Ctx* c, int R, int prec, const double2* r, double2* z, cudaStream_t st);
+// y = Z x through a CUDA graph captured on first use for (x, y, R, prec)
+int run_matvec_graph(Ctx* c, int R, int prec, const double2* x, double2* y, cudaStream_t st);
+void free_graphs(Ctx* c);
 
 // ------------------------------------------------------------------ linear algebra (k_linalg.cu)
 // h[j*R + r] = sum_i conj(V_j[i][r]) w[i][r] for j < J (V_j = V + j*ldv), FP64.

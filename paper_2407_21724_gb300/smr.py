@@ -75,6 +75,7 @@ _SIGS = {
     "smr_rhs_plane_waves": (C.c_int, [_P, C.c_int, _D, _D, _P, _P]),
     "smr_rhs_plane_waves_static": (C.c_int, [_P, C.c_int, _P, _P, _P, _P]),
     "smr_matvec": (C.c_int, [_P, C.c_int, _P, _P, C.c_int, _P]),
+    "smr_matvec_graph": (C.c_int, [_P, C.c_int, _P, _P, C.c_int, _P]),
     "smr_matvec_parts": (C.c_int, [_P, C.c_int, _P, _P, _P, C.c_int, _P]),
     "smr_matvec_host": (C.c_int, [_P, C.c_int, _D, _D, C.c_int, _P]),
     "smr_precond": (C.c_int, [_P, C.c_int, _P, _P, C.c_int, _P]),
@@ -254,6 +255,11 @@ def smr_matvec(ctx, x, y, precision=SMR_PREC_FP64, R=None, stream=None):
     n = smr_info(ctx)["n_unknowns"] if R is None else None
     R = R if R is not None else _R(x, n)
     _check(ctx, lib().smr_matvec(ctx, R, _ptr(x), _ptr(y), precision, _stream(stream, x)))
+
+
+def smr_matvec_graph(ctx, x, y, precision=SMR_PREC_FP64, R=None, stream=None):
+    R = R if R is not None else _R(x, smr_info(ctx)["n_unknowns"])
+    _check(ctx, lib().smr_matvec_graph(ctx, R, _ptr(x), _ptr(y), precision, _stream(stream, x)))
 
 
 def smr_matvec_parts(ctx, x, y_near, y_far, precision=SMR_PREC_FP64, R=None, stream=None):

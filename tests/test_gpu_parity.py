@@ -262,3 +262,21 @@ def test_invalid_arguments(c1):
     with pytest.raises(smr.SmrError):
         smr.smr_matvec(ctx, xd, xd, R=1)                   # no scene
     smr.smr_destroy(ctx)
+
+
+def test_graph_product_matches_direct(c1, rnd):
+    """The CUDA-graph replay launches the same kernels: bit-identical to
+    smr_matvec, also on repeated replays and after a change of R."""
+    for c in (c1, rnd):
+        n = c.info["n_unknowns"]
+        for R in (1, 3):
+            x = np.stack([crandn(n, 70 + r) for r in range(R)], axis=1).reshape(-1)
+            xd = torch.from_numpy(x).cuda()
+            y0, y1 = torch.empty_like(xd), torch.empty_like(xd)
+            for prec in (smr.SMR_PREC_FP64, smr.SMR_PREC_FP32):
+                smr.smr_matvec(c.ctx, xd, y0, prec, R=R)
+                for _ in range(3):
+                    y1.zero_()
+                    smr.smr_matvec_graph(c.ctx, xd, y1, prec, R=R)
+                torch.cuda.synchronize()
+                assert torch.equal(y0, y1)
