@@ -175,8 +175,10 @@ typedef struct {
   int precond;     /* SMR_PRECOND_* [SMR_PRECOND_BLOCKDIAG]                    */
   int precision;   /* SMR_PREC_FP64: plain GMRES on the FP64 product;
                       SMR_PREC_FP32: iterative refinement, outer residual with
-                      the FP64 product, inner flexible GMRES on the FP32
-                      product, FP64 Arnoldi/Givens throughout [FP64]          */
+                      the FP64 product, inner GMRES on the FP32 product and
+                      preconditioner.  With R = 1 the inner Krylov basis is
+                      stored in FP32 (Gram-Schmidt products in FP32, sums
+                      over the vector, Hessenberg and Givens in FP64) [FP64] */
   int max_outer;   /* refinement steps for SMR_PREC_FP32 [8]                   */
   int use_x0;      /* 1: x holds the initial guess on entry; 0: start at 0     */
 } smr_solve_opts;
@@ -189,6 +191,9 @@ typedef struct {
   int reorth;           /* Arnoldi steps that needed a second Gram-Schmidt pass */
   double resid_true;    /* max over r of ||b - Z_64 x|| / ||b|| at exit        */
   double seconds;       /* wall time of the call                               */
+  double seconds_product;  /* device time of the Arnoldi products             */
+  double seconds_precond;  /* ... of the preconditioner applications           */
+  double seconds_orth;     /* ... of Gram-Schmidt (inner products, updates)     */
 } smr_solve_stats;
 
 void smr_default_solve_opts(smr_solve_opts* o);

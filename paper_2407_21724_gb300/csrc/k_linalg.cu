@@ -99,6 +99,16 @@ __global__ void k_axpby(long long n, int R, const double2* __restrict__ a, const
                       ca.x * xa.y + ca.y * xa.x + cb.x * yb.y + cb.y * yb.x);
 }
 
+// y = a[r] x
+__global__ void k_scale(long long n, int R, const double2* __restrict__ a, const double2* __restrict__ x,
+                        double2* __restrict__ y) {
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= n * R) return;
+  int r = R == 1 ? 0 : (int)(t % R);
+  double2 xa = x[t], ca = a[r];
+  y[t] = make_double2(ca.x * xa.x - ca.y * xa.y, ca.x * xa.y + ca.y * xa.x);
+}
+
 static void chunking(long long n, int R, int* rl, int* nchunk, long long* rows_per) {
   *rl = std::max(1, 256 / R);
   long long per = std::max<long long>(1024, (n + 511) / 512);
@@ -118,9 +128,440 @@ static int red_buffer(Ctx* c, size_t bytes) {
   return SMR_OK;
 }
 
-// d_h[J][R] on the device; optional host copy.
+// ---- single right-hand side Gram-Schmidt passes ----------------------------
+// Warp g owns rows [GS_SEG g, GS_SEG (g+1)) and keeps its slice of w in
+// registers; lane l holds rows GS_SEG g + l + 32 q, q < GS_RPL, so every load
+// instruction of the warp is one coalesced 512-byte segment.  Two basis
+// vectors are read per step (16 independent loads in flight per lane).
+// Partial sums go to part[row][g] and a second kernel adds them up in a
+// fixed order, so the results are deterministic.
+constexpr int GS_RPL = 8;
+constexpr int GS_SEG = 32 * GS_RPL;
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// part[j][g] = sum over the warp's rows of conj(V_j) w (j < J); with
+// with_norm, part[J][g] = sum |w|^2.
+__global__ void __launch_bounds__(256) k_gs_dot(int J, long long n, const double2* __restrict__ V,
+                                                long long ldv, const double2* __restrict__ w,
+                                                double2* __restrict__ part, int nseg, int with_norm) {
+  int g = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+  int lane = threadIdx.x & 31;
+  if (g >= nseg) return;
+  long long i0 = (long long)g * GS_SEG + lane;
+  bool full = (long long)(g + 1) * GS_SEG <= n;
+  double2 wr[GS_RPL];
+#pragma unroll
+  for (int q = 0; q < GS_RPL; ++q) {
+    long long i = i0 + 32 * q;
+    wr[q] = (full || i < n) ? w[i] : make_double2(0, 0);
+  }
+  if (with_norm) {
+    double s = 0;
+#pragma unroll
+    for (int q = 0; q < GS_RPL; ++q) s += wr[q].x * wr[q].x + wr[q].y * wr[q].y;
+    s = warp_sum(s);
+    if (lane == 0) part[(size_t)J * nseg + g] = make_double2(s, 0);
+  }
+  int j = 0;
+  for (; j + 2 <= J; j += 2) {
+    const double2* v0 = V + (size_t)j * ldv + i0;
+    const double2* v1 = v0 + ldv;
+    double2 a[GS_RPL], b[GS_RPL];
+    if (full) {
+#pragma unroll
+      for (int q = 0; q < GS_RPL; ++q) {
+        a[q] = v0[32 * q];
+        b[q] = v1[32 * q];
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < GS_RPL; ++q) {
+        bool in = i0 + 32 * q < n;
+        a[q] = in ? v0[32 * q] : make_double2(0, 0);
+        b[q] = in ? v1[32 * q] : make_double2(0, 0);
+      }
+    }
+    double ax = 0, ay = 0, bx = 0, by = 0;
+#pragma unroll
+    for (int q = 0; q < GS_RPL; ++q) {
+      ax += a[q].x * wr[q].x + a[q].y * wr[q].y;
+      ay += a[q].x * wr[q].y - a[q].y * wr[q].x;
+      bx += b[q].x * wr[q].x + b[q].y * wr[q].y;
+      by += b[q].x * wr[q].y - b[q].y * wr[q].x;
+    }
+    ax = warp_sum(ax);
+    ay = warp_sum(ay);
+    bx = warp_sum(bx);
+    by = warp_sum(by);
+    if (lane == 0) {
+      part[(size_t)j * nseg + g] = make_double2(ax, ay);
+      part[(size_t)(j + 1) * nseg + g] = make_double2(bx, by);
+    }
+  }
+  if (j < J) {
+    const double2* v0 = V + (size_t)j * ldv + i0;
+    double ax = 0, ay = 0;
+#pragma unroll
+    for (int q = 0; q < GS_RPL; ++q) {
+      double2 a = (full || i0 + 32 * q < n) ? v0[32 * q] : make_double2(0, 0);
+      ax += a.x * wr[q].x + a.y * wr[q].y;
+      ay += a.x * wr[q].y - a.y * wr[q].x;
+    }
+    ax = warp_sum(ax);
+    ay = warp_sum(ay);
+    if (lane == 0) part[(size_t)j * nseg + g] = make_double2(ax, ay);
+  }
+}
+
+// w += sign * sum_j V_j h[j] on the warp's rows; with part_norm, also
+// part_norm[g] = sum |w_new|^2 over those rows.
+__global__ void __launch_bounds__(256) k_gs_axpy(int J, long long n, const double2* __restrict__ V,
+                                                 long long ldv, const double2* __restrict__ h,
+                                                 double2* __restrict__ w, double sign,
+                                                 double2* __restrict__ part_norm, int nseg) {
+  int g = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+  int lane = threadIdx.x & 31;
+  if (g >= nseg) return;
+  long long i0 = (long long)g * GS_SEG + lane;
+  bool full = (long long)(g + 1) * GS_SEG <= n;
+  double2 acc[GS_RPL];
+#pragma unroll
+  for (int q = 0; q < GS_RPL; ++q) acc[q] = make_double2(0, 0);
+  int j = 0;
+  for (; j + 2 <= J; j += 2) {
+    const double2* v0 = V + (size_t)j * ldv + i0;
+    const double2* v1 = v0 + ldv;
+    double2 a[GS_RPL], b[GS_RPL];
+    if (full) {
+#pragma unroll
+      for (int q = 0; q < GS_RPL; ++q) {
+        a[q] = v0[32 * q];
+        b[q] = v1[32 * q];
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < GS_RPL; ++q) {
+        bool in = i0 + 32 * q < n;
+        a[q] = in ? v0[32 * q] : make_double2(0, 0);
+        b[q] = in ? v1[32 * q] : make_double2(0, 0);
+      }
+    }
+    double2 c0 = h[j], c1 = h[j + 1];
+#pragma unroll
+    for (int q = 0; q < GS_RPL; ++q) {
+      acc[q].x += a[q].x * c0.x - a[q].y * c0.y + b[q].x * c1.x - b[q].y * c1.y;
+      acc[q].y += a[q].x * c0.y + a[q].y * c0.x + b[q].x * c1.y + b[q].y * c1.x;
+    }
+  }
+  if (j < J) {
+    const double2* v0 = V + (size_t)j * ldv + i0;
+    double2 c0 = h[j];
+#pragma unroll
+    for (int q = 0; q < GS_RPL; ++q) {
+      double2 a = (full || i0 + 32 * q < n) ? v0[32 * q] : make_double2(0, 0);
+      acc[q].x += a.x * c0.x - a.y * c0.y;
+      acc[q].y += a.x * c0.y + a.y * c0.x;
+    }
+  }
+  double s = 0;
+#pragma unroll
+  for (int q = 0; q < GS_RPL; ++q) {
+    long long i = i0 + 32 * q;
+    if (full || i < n) {
+      double2 o = w[i];
+      o.x += sign * acc[q].x;
+      o.y += sign * acc[q].y;
+      w[i] = o;
+      s += o.x * o.x + o.y * o.y;
+    }
+  }
+  if (part_norm) {
+    s = warp_sum(s);
+    if (lane == 0) part_norm[g] = make_double2(s, 0);
+  }
+}
+
+// out[r] = sum_g part[r][g] for r < rows (r < na goes to out_a[r], the rest
+// to out_b[r - na]); one CTA per row, fixed summation order.
+__global__ void k_gs_final(int nseg, const double2* __restrict__ part, int na, double2* __restrict__ out_a,
+                           double2* __restrict__ out_b, float2* __restrict__ out_f) {
+  __shared__ double2 red[256];
+  int r = blockIdx.x;
+  double2 s = make_double2(0, 0);
+  for (int c = threadIdx.x; c < nseg; c += blockDim.x) {
+    double2 v = part[(size_t)r * nseg + c];
+    s.x += v.x;
+    s.y += v.y;
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int hh = blockDim.x / 2; hh > 0; hh >>= 1) {
+    if ((int)threadIdx.x < hh) {
+      red[threadIdx.x].x += red[threadIdx.x + hh].x;
+      red[threadIdx.x].y += red[threadIdx.x + hh].y;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    if (r < na) {
+      out_a[r] = red[0];
+      if (out_f) out_f[r] = make_float2((float)red[0].x, (float)red[0].y);
+    } else {
+      out_b[r - na] = red[0];
+    }
+  }
+}
+
+static inline int gs_nseg(long long n) { return (int)((n + GS_SEG - 1) / GS_SEG); }
+static inline unsigned gs_grid(int nseg) { return (unsigned)((nseg + 7) / 8); }
+
+// h[0..J) = V^H w and, when d_norm is given, *d_norm = ||w||^2 (one pass).
+static int gs_dot(Ctx* c, int J, long long n, const double2* V, long long ldv, const double2* w,
+                  double2* d_h, double2* d_norm, double2* d_part, cudaStream_t st) {
+  int nseg = gs_nseg(n);
+  int rows = J + (d_norm ? 1 : 0);
+  if (rows == 0) return SMR_OK;
+  k_gs_dot<<<gs_grid(nseg), 256, 0, st>>>(J, n, V, ldv, w, d_part, nseg, d_norm ? 1 : 0);
+  SMR_LAUNCH(c);
+  k_gs_final<<<rows, 256, 0, st>>>(nseg, d_part, J, d_h, d_norm, nullptr);
+  SMR_LAUNCH(c);
+  return SMR_OK;
+}
+
+// w += sign V h and, when d_norm is given, *d_norm = ||w_new||^2 (one pass).
+static int gs_axpy(Ctx* c, int J, long long n, const double2* V, long long ldv, const double2* d_h,
+                   double2* w, double sign, double2* d_norm, double2* d_part, cudaStream_t st) {
+  int nseg = gs_nseg(n);
+  k_gs_axpy<<<gs_grid(nseg), 256, 0, st>>>(J, n, V, ldv, d_h, w, sign, d_norm ? d_part : nullptr, nseg);
+  SMR_LAUNCH(c);
+  if (d_norm) {
+    k_gs_final<<<1, 256, 0, st>>>(nseg, d_part, 0, nullptr, d_norm, nullptr);
+    SMR_LAUNCH(c);
+  }
+  return SMR_OK;
+}
+
+// ---- single right-hand side with an FP32 Krylov basis ----------------------
+// The FP64 passes above are bound by the FP64 units (four DFMA per complex
+// element, a ~1.2 TFLOP/s rate), not by HBM.  With the basis in FP32 the
+// products run on the FP32 pipes and the bytes halve.  Lane l of warp g holds
+// complex rows G32_SEG g + 2 l + 64 q + {0, 1}, q < G32_RPL, read as one
+// float4 per basis vector (a 512-byte segment per warp instruction); the
+// in-warp sums are FP32, the sums over warps FP64.  The new w stays FP64.
+constexpr int G32_RPL = 8;
+constexpr int G32_SEG = 64 * G32_RPL;
+
+__device__ __forceinline__ float warp_sumf(float v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// float4 holding complex rows i, i + 1 of v (zero beyond n)
+__device__ __forceinline__ float4 ld_pair(const float2* __restrict__ v, long long i, long long n, bool full) {
+  if (full || i + 1 < n) return *reinterpret_cast<const float4*>(v + i);
+  if (i < n) {
+    float2 a = v[i];
+    return make_float4(a.x, a.y, 0.f, 0.f);
+  }
+  return make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+// part[j][g] = conj(V_j) . w over the warp's rows (j < J); with with_norm,
+// part[J][g] = sum |w|^2 (FP64).
+__global__ void __launch_bounds__(256) k_gs32_dot(int J, long long n, const float2* __restrict__ V,
+                                                  long long ldv, const double2* __restrict__ w,
+                                                  double2* __restrict__ part, int nseg, int with_norm) {
+  int g = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+  int lane = threadIdx.x & 31;
+  if (g >= nseg) return;
+  long long i0 = (long long)g * G32_SEG + 2 * lane;
+  bool full = (long long)(g + 1) * G32_SEG <= n;
+  float4 wf[G32_RPL];
+  double s = 0;
+#pragma unroll
+  for (int q = 0; q < G32_RPL; ++q) {
+    long long i = i0 + 64 * q;
+    double2 w0 = (full || i < n) ? w[i] : make_double2(0, 0);
+    double2 w1 = (full || i + 1 < n) ? w[i + 1] : make_double2(0, 0);
+    s += w0.x * w0.x + w0.y * w0.y + w1.x * w1.x + w1.y * w1.y;
+    wf[q] = make_float4((float)w0.x, (float)w0.y, (float)w1.x, (float)w1.y);
+  }
+  if (with_norm) {
+    s = warp_sum(s);
+    if (lane == 0) part[(size_t)J * nseg + g] = make_double2(s, 0);
+  }
+  int j = 0;
+  for (; j + 2 <= J; j += 2) {
+    const float2* v0 = V + (size_t)j * ldv;
+    const float2* v1 = v0 + ldv;
+    float4 a[G32_RPL], b[G32_RPL];
+#pragma unroll
+    for (int q = 0; q < G32_RPL; ++q) {
+      a[q] = ld_pair(v0, i0 + 64 * q, n, full);
+      b[q] = ld_pair(v1, i0 + 64 * q, n, full);
+    }
+    float ax = 0, ay = 0, bx = 0, by = 0;
+#pragma unroll
+    for (int q = 0; q < G32_RPL; ++q) {
+      float4 u = wf[q];
+      ax += a[q].x * u.x + a[q].y * u.y + a[q].z * u.z + a[q].w * u.w;
+      ay += a[q].x * u.y - a[q].y * u.x + a[q].z * u.w - a[q].w * u.z;
+      bx += b[q].x * u.x + b[q].y * u.y + b[q].z * u.z + b[q].w * u.w;
+      by += b[q].x * u.y - b[q].y * u.x + b[q].z * u.w - b[q].w * u.z;
+    }
+    ax = warp_sumf(ax);
+    ay = warp_sumf(ay);
+    bx = warp_sumf(bx);
+    by = warp_sumf(by);
+    if (lane == 0) {
+      part[(size_t)j * nseg + g] = make_double2(ax, ay);
+      part[(size_t)(j + 1) * nseg + g] = make_double2(bx, by);
+    }
+  }
+  if (j < J) {
+    const float2* v0 = V + (size_t)j * ldv;
+    float ax = 0, ay = 0;
+#pragma unroll
+    for (int q = 0; q < G32_RPL; ++q) {
+      float4 a = ld_pair(v0, i0 + 64 * q, n, full), u = wf[q];
+      ax += a.x * u.x + a.y * u.y + a.z * u.z + a.w * u.w;
+      ay += a.x * u.y - a.y * u.x + a.z * u.w - a.w * u.z;
+    }
+    ax = warp_sumf(ax);
+    ay = warp_sumf(ay);
+    if (lane == 0) part[(size_t)j * nseg + g] = make_double2(ax, ay);
+  }
+}
+
+// w += sign * sum_j V_j hf[j] (FP32 products and sums, FP64 update of w);
+// with part_norm, part_norm[g] = sum |w_new|^2 over the warp's rows.
+__global__ void __launch_bounds__(256) k_gs32_axpy(int J, long long n, const float2* __restrict__ V,
+                                                   long long ldv, const float2* __restrict__ hf,
+                                                   double2* __restrict__ w, double sign,
+                                                   double2* __restrict__ part_norm, int nseg) {
+  int g = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+  int lane = threadIdx.x & 31;
+  if (g >= nseg) return;
+  long long i0 = (long long)g * G32_SEG + 2 * lane;
+  bool full = (long long)(g + 1) * G32_SEG <= n;
+  float4 acc[G32_RPL];
+#pragma unroll
+  for (int q = 0; q < G32_RPL; ++q) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+  int j = 0;
+  for (; j + 2 <= J; j += 2) {
+    const float2* v0 = V + (size_t)j * ldv;
+    const float2* v1 = v0 + ldv;
+    float4 a[G32_RPL], b[G32_RPL];
+#pragma unroll
+    for (int q = 0; q < G32_RPL; ++q) {
+      a[q] = ld_pair(v0, i0 + 64 * q, n, full);
+      b[q] = ld_pair(v1, i0 + 64 * q, n, full);
+    }
+    float2 c0 = hf[j], c1 = hf[j + 1];
+#pragma unroll
+    for (int q = 0; q < G32_RPL; ++q) {
+      acc[q].x += a[q].x * c0.x - a[q].y * c0.y + b[q].x * c1.x - b[q].y * c1.y;
+      acc[q].y += a[q].x * c0.y + a[q].y * c0.x + b[q].x * c1.y + b[q].y * c1.x;
+      acc[q].z += a[q].z * c0.x - a[q].w * c0.y + b[q].z * c1.x - b[q].w * c1.y;
+      acc[q].w += a[q].z * c0.y + a[q].w * c0.x + b[q].z * c1.y + b[q].w * c1.x;
+    }
+  }
+  if (j < J) {
+    const float2* v0 = V + (size_t)j * ldv;
+    float2 c0 = hf[j];
+#pragma unroll
+    for (int q = 0; q < G32_RPL; ++q) {
+      float4 a = ld_pair(v0, i0 + 64 * q, n, full);
+      acc[q].x += a.x * c0.x - a.y * c0.y;
+      acc[q].y += a.x * c0.y + a.y * c0.x;
+      acc[q].z += a.z * c0.x - a.w * c0.y;
+      acc[q].w += a.z * c0.y + a.w * c0.x;
+    }
+  }
+  double s = 0;
+#pragma unroll
+  for (int q = 0; q < G32_RPL; ++q) {
+    long long i = i0 + 64 * q;
+    if (full || i < n) {
+      double2 o = w[i];
+      o.x += sign * (double)acc[q].x;
+      o.y += sign * (double)acc[q].y;
+      w[i] = o;
+      s += o.x * o.x + o.y * o.y;
+    }
+    if (full || i + 1 < n) {
+      double2 o = w[i + 1];
+      o.x += sign * (double)acc[q].z;
+      o.y += sign * (double)acc[q].w;
+      w[i + 1] = o;
+      s += o.x * o.x + o.y * o.y;
+    }
+  }
+  if (part_norm) {
+    s = warp_sum(s);
+    if (lane == 0) part_norm[g] = make_double2(s, 0);
+  }
+}
+
+// v = (float) (a[0] w)
+__global__ void k_narrow_scale(long long n, const double2* __restrict__ a, const double2* __restrict__ w,
+                               float2* __restrict__ v) {
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  double2 x = w[t], c = a[0];
+  v[t] = make_float2((float)(c.x * x.x - c.y * x.y), (float)(c.x * x.y + c.y * x.x));
+}
+
+__global__ void k_widen(long long n, const float2* __restrict__ v, double2* __restrict__ u) {
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  float2 x = v[t];
+  u[t] = make_double2(x.x, x.y);
+}
+
+static inline int g32_nseg(long long n) { return (int)((n + G32_SEG - 1) / G32_SEG); }
+
+// h = V^H w (FP64 d_h and FP32 d_hf copies) and optionally ||w||^2
+static int gs32_dot(Ctx* c, int J, long long n, const float2* V, long long ldv, const double2* w,
+                    double2* d_h, float2* d_hf, double2* d_norm, double2* d_part, cudaStream_t st) {
+  int nseg = g32_nseg(n);
+  int rows = J + (d_norm ? 1 : 0);
+  if (rows == 0) return SMR_OK;
+  k_gs32_dot<<<gs_grid(nseg), 256, 0, st>>>(J, n, V, ldv, w, d_part, nseg, d_norm ? 1 : 0);
+  SMR_LAUNCH(c);
+  k_gs_final<<<rows, 256, 0, st>>>(nseg, d_part, J, d_h, d_norm, d_hf);
+  SMR_LAUNCH(c);
+  return SMR_OK;
+}
+
+static int gs32_axpy(Ctx* c, int J, long long n, const float2* V, long long ldv, const float2* d_hf,
+                     double2* w, double sign, double2* d_norm, double2* d_part, cudaStream_t st) {
+  int nseg = g32_nseg(n);
+  k_gs32_axpy<<<gs_grid(nseg), 256, 0, st>>>(J, n, V, ldv, d_hf, w, sign, d_norm ? d_part : nullptr, nseg);
+  SMR_LAUNCH(c);
+  if (d_norm) {
+    k_gs_final<<<1, 256, 0, st>>>(nseg, d_part, 0, nullptr, d_norm, nullptr);
+    SMR_LAUNCH(c);
+  }
+  return SMR_OK;
+}
+
+// partial-sum area (double2 elements) that J inner products need
+static size_t part_elems(long long n, int R, int J) {
+  int rl, nchunk;
+  long long per;
+  chunking(n, R, &rl, &nchunk, &per);
+  return std::max((size_t)J * nchunk * R, (size_t)(J + 1) * gs_nseg(n));
+}
+
+// d_h[J][R] on the device.
 static int multidot_dev(Ctx* c, int J, long long n, int R, const double2* V, long long ldv,
                         const double2* w, double2* d_h, double2* d_part, cudaStream_t st) {
+  if (R == 1) return gs_dot(c, J, n, V, ldv, w, d_h, nullptr, d_part, st);
   int rl, nchunk;
   long long per;
   chunking(n, R, &rl, &nchunk, &per);
@@ -137,11 +578,12 @@ int multidot(Ctx* c, int J, long long n, int R, const double2* V, long long ldv,
   int rl, nchunk;
   long long per;
   chunking(n, R, &rl, &nchunk, &per);
-  size_t need = ((size_t)J * nchunk * R + (size_t)J * R) * sizeof(double2);
+  size_t np = part_elems(n, R, J);
+  size_t need = (np + (size_t)J * R) * sizeof(double2);
   int rc = red_buffer(c, need);
   if (rc) return rc;
   double2* d_part = (double2*)c->d_red;
-  double2* d_h = d_part + (size_t)J * nchunk * R;
+  double2* d_h = d_part + np;
   rc = multidot_dev(c, J, n, R, V, ldv, w, d_h, d_part, st);
   if (rc) return rc;
   SMR_CUDA(c, cudaMemcpyAsync(h_host, d_h, (size_t)J * R * sizeof(double2), cudaMemcpyDeviceToHost, st));
@@ -151,6 +593,7 @@ int multidot(Ctx* c, int J, long long n, int R, const double2* V, long long ldv,
 
 int multi_axpy(Ctx* c, int J, long long n, int R, const double2* V, long long ldv, const double2* d_h,
                double2* w, double sign, cudaStream_t st) {
+  if (R == 1) return gs_axpy(c, J, n, V, ldv, d_h, w, sign, nullptr, nullptr, st);
   long long tot = n * R;
   k_multi_axpy<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(J, n, R, V, ldv, d_h, w, sign);
   SMR_LAUNCH(c);
@@ -176,12 +619,16 @@ int col_axpby(long long n, int R, const double2* d_a, const double2* x, const do
 namespace {
 
 struct Work {
-  double2* V = nullptr;    // [m+1][n][R]
-  double2* Z = nullptr;    // [m][n][R] (flexible only)
+  bool f32 = false;        // Krylov basis in FP32 (one right-hand side, FP32 operator)
+  void* V = nullptr;       // [m+1][n][R] basis, double2 or float2
+  double2* u = nullptr;    // [n][R] residual r0; FP64 copy of v_j for the preconditioner
   double2* w = nullptr;    // [n][R]
   double2* t = nullptr;    // [n][R]
-  double2* coef = nullptr; // device [4][m+1][R] small coefficient area
+  double2* coef = nullptr; // device [4][m+2][R] coefficients
+  float2* coef_f = nullptr;  // device [3][m+2] FP32 coefficient copies
   double2* part = nullptr; // reduction partials
+  cudaEvent_t ev[6] = {};
+  double t_pc = 0, t_mv = 0, t_or = 0;   // seconds in preconditioner, products, Gram-Schmidt
 };
 
 }  // namespace
@@ -192,9 +639,42 @@ static int apply_A(Ctx* c, int R, int prec, const double2* x, double2* y, cudaSt
   return run_far(c, R, prec, x, y, true, st);
 }
 
+static float elapsed_s(cudaEvent_t a, cudaEvent_t b) {
+  float ms = 0;
+  cudaEventElapsedTime(&ms, a, b);
+  return ms * 1e-3f;
+}
+
+// One Gram-Schmidt pass of w against v_0..v_{J-1}: h = V^H w, w -= V h,
+// *d_nr = ||w||^2 after the pass, and (when d_n0 is given) ||w||^2 before it.
+static int gs_pass(Ctx* c, Work& W, int J, long long n, int R, long long ld, double2* d_h, float2* d_hf,
+                   double2* d_n0, double2* d_nr, cudaStream_t st) {
+  int rc;
+  if (W.f32) {
+    rc = gs32_dot(c, J, n, (const float2*)W.V, ld, W.w, d_h, d_hf, d_n0, W.part, st);
+    if (rc) return rc;
+    return gs32_axpy(c, J, n, (const float2*)W.V, ld, d_hf, W.w, -1.0, d_nr, W.part, st);
+  }
+  const double2* V = (const double2*)W.V;
+  if (R == 1) {
+    rc = gs_dot(c, J, n, V, ld, W.w, d_h, d_n0, W.part, st);
+    if (rc) return rc;
+    return gs_axpy(c, J, n, V, ld, d_h, W.w, -1.0, d_nr, W.part, st);
+  }
+  if (d_n0) {
+    rc = multidot_dev(c, 1, n, R, W.w, 0, W.w, d_n0, W.part, st);
+    if (rc) return rc;
+  }
+  rc = multidot_dev(c, J, n, R, V, ld, W.w, d_h, W.part, st);
+  if (rc) return rc;
+  rc = multi_axpy(c, J, n, R, V, ld, d_h, W.w, -1.0, st);
+  if (rc) return rc;
+  return multidot_dev(c, 1, n, R, W.w, 0, W.w, d_nr, W.part, st);
+}
+
 // Solve A d = rhs from d = d0 (in d) to per-column relative residual tol_col[r]
-// (relative to ||rhs_r||) with right preconditioning; A and the
-// preconditioner in precision `prec`.  Returns iterations used in *its.
+// (relative to ||rhs_r||) with right preconditioning, x = d0 + M^-1 V y;
+// A and the preconditioner in precision `prec`.  Iterations add to *its.
 static int gmres_core(Ctx* c, int R, int prec, int precond, const double2* rhs, double2* d,
                       bool have_d0, const std::vector<double>& tol_col, int maxit, int restart,
                       Work& W, int* its, int* nmv, int* n_reorth, std::vector<double>& rel_out,
@@ -202,33 +682,57 @@ static int gmres_core(Ctx* c, int R, int prec, int precond, const double2* rhs, 
   long long n = 2LL * c->npsi * c->p;
   long long ld = n * R;
   int m = restart;
+  size_t eb = W.f32 ? sizeof(float2) : sizeof(double2);
+  auto Vj = [&](int j) { return (void*)((char*)W.V + (size_t)j * ld * eb); };
+  unsigned nb = (unsigned)((ld + 255) / 256);
   std::vector<double> bn(R), beta(R);
   int rc = col_norms(c, n, R, rhs, bn.data(), st);
   if (rc) return rc;
   for (int r = 0; r < R; ++r)
     if (bn[r] == 0.0) bn[r] = 1.0;
-  // r0 = rhs - A d0  (in W.V[0])
-  double2* r0 = W.V;
-  if (have_d0) {
-    rc = apply_A(c, R, prec, d, W.w, st);
-    if (rc) return rc;
+  // r0 = rhs - A d0  (in W.u)
+  double2* r0 = W.u;
+  auto residual = [&]() -> int {
+    int e = apply_A(c, R, prec, d, W.w, st);
+    if (e) return e;
     ++*nmv;
     SMR_CUDA(c, cudaMemcpyAsync(r0, rhs, ld * sizeof(double2), cudaMemcpyDeviceToDevice, st));
-    std::vector<double2> one(R, make_double2(-1, 0)), un(R, make_double2(1, 0));
-    SMR_CUDA(c, cudaMemcpyAsync(W.coef, one.data(), R * sizeof(double2), cudaMemcpyHostToDevice, st));
-    SMR_CUDA(c, cudaMemcpyAsync(W.coef + R, un.data(), R * sizeof(double2), cudaMemcpyHostToDevice, st));
-    rc = col_axpby(n, R, W.coef, W.w, W.coef + R, r0, st);
-    if (rc) { c->err = "axpby launch"; return rc; }
+    std::vector<double2> mone(R, make_double2(-1, 0)), one(R, make_double2(1, 0));
+    SMR_CUDA(c, cudaMemcpyAsync(W.coef, mone.data(), R * sizeof(double2), cudaMemcpyHostToDevice, st));
+    SMR_CUDA(c, cudaMemcpyAsync(W.coef + R, one.data(), R * sizeof(double2), cudaMemcpyHostToDevice, st));
+    e = col_axpby(n, R, W.coef, W.w, W.coef + R, r0, st);
+    if (e) c->err = "axpby launch";
+    return e;
+  };
+  if (have_d0) {
+    rc = residual();
+    if (rc) return rc;
   } else {
     SMR_CUDA(c, cudaMemcpyAsync(r0, rhs, ld * sizeof(double2), cudaMemcpyDeviceToDevice, st));
     SMR_CUDA(c, cudaMemsetAsync(d, 0, ld * sizeof(double2), st));
   }
   std::vector<int> done(R, 0);
   rel_out.assign(R, 1.0);
+  // coefficient areas on the device
+  double2* dh1 = W.coef;                                    // [m+1][R]
+  double2* dh2 = W.coef + (size_t)(m + 1) * R;              // [m+1][R]
+  double2* dnr = W.coef + (size_t)2 * (m + 1) * R;          // ||w'||^2  [R]
+  double2* dn0 = dnr + R;                                   // ||w||^2   [R]
+  double2* dsc = W.coef + (size_t)3 * (m + 1) * R;          // scale     [R]
+  float2* dh1f = W.coef_f;
+  float2* dh2f = W.coef_f + (m + 1);
+  float2* dyf = W.coef_f + 2 * (m + 1);
   // host Hessenberg storage per column (rotated), rotations, rhs g
   std::vector<std::complex<double>> H((size_t)(m + 1) * m * R), g((size_t)(m + 1) * R);
   std::vector<std::complex<double>> cs((size_t)m * R), sn((size_t)m * R);
   std::vector<double2> hbuf((size_t)(2 * (m + 1) + 2) * R);
+  // v_j <- a * src (per column a[r] on the device at dsc)
+  auto store_basis = [&](int j, const double2* src) -> int {
+    if (W.f32) k_narrow_scale<<<nb, 256, 0, st>>>(n, dsc, src, (float2*)Vj(j));
+    else k_scale<<<nb, 256, 0, st>>>(n, R, dsc, src, (double2*)Vj(j));
+    SMR_LAUNCH(c);
+    return SMR_OK;
+  };
   while (true) {
     rc = col_norms(c, n, R, r0, beta.data(), st);
     if (rc) return rc;
@@ -240,52 +744,50 @@ static int gmres_core(Ctx* c, int R, int prec, int precond, const double2* rhs, 
       all = all && done[r];
     }
     if (all || *its >= maxit) return all ? SMR_OK : SMR_E_NOT_CONVERGED;
-    // V0 = r0 / beta
-    std::vector<double2> sc(R), zr(R, make_double2(0, 0));
+    std::vector<double2> sc(R);
     for (int r = 0; r < R; ++r) sc[r] = make_double2(beta[r] > 0 ? 1.0 / beta[r] : 0.0, 0);
-    SMR_CUDA(c, cudaMemcpyAsync(W.coef, sc.data(), R * sizeof(double2), cudaMemcpyHostToDevice, st));
-    SMR_CUDA(c, cudaMemcpyAsync(W.coef + R, zr.data(), R * sizeof(double2), cudaMemcpyHostToDevice, st));
-    rc = col_axpby(n, R, W.coef, r0, W.coef + R, r0, st);
+    SMR_CUDA(c, cudaMemcpyAsync(dsc, sc.data(), R * sizeof(double2), cudaMemcpyHostToDevice, st));
+    rc = store_basis(0, r0);
     if (rc) return rc;
     std::fill(g.begin(), g.end(), std::complex<double>(0, 0));
-    for (int r = 0; r < R; ++r) g[r] = beta[r];
+    for (int r = 0; r < R; ++r) g[(size_t)r * (m + 1)] = beta[r];
     std::vector<int> jend(R, 0), active(R, 0);
     for (int r = 0; r < R; ++r) active[r] = !done[r];
     int j = 0;
     for (; j < m && *its < maxit; ++j) {
-      double2* Vj = W.V + (size_t)j * ld;
-      // z_j = M^-1 v_j in W.t (fixed address, so one captured graph serves
-      // every product of the solve); the flexible variant keeps a copy in Z_j
+      cudaEventRecord(W.ev[0], st);
+      // t = M^-1 v_j (W.t has a fixed address, so one captured graph serves
+      // every product of the solve)
+      const double2* vj = (const double2*)Vj(j);
+      if (W.f32) {
+        k_widen<<<nb, 256, 0, st>>>(n, (const float2*)Vj(j), W.u);
+        SMR_LAUNCH(c);
+        vj = W.u;
+      }
       if (precond == SMR_PRECOND_BLOCKDIAG) {
-        rc = run_precond(c, R, prec, Vj, W.t, st);
+        rc = run_precond(c, R, prec, vj, W.t, st);
       } else {
-        SMR_CUDA(c, cudaMemcpyAsync(W.t, Vj, ld * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+        SMR_CUDA(c, cudaMemcpyAsync(W.t, vj, ld * sizeof(double2), cudaMemcpyDeviceToDevice, st));
       }
       if (rc) return rc;
-      if (W.Z)
-        SMR_CUDA(c, cudaMemcpyAsync(W.Z + (size_t)j * ld, W.t, ld * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+      cudaEventRecord(W.ev[1], st);
       rc = run_matvec_graph(c, R, prec, W.t, W.w, st);
       if (rc) return rc;
+      cudaEventRecord(W.ev[2], st);
       ++*nmv;
       ++*its;
-      // classical Gram-Schmidt against V_0..V_j, repeated once when the norm
+      // classical Gram-Schmidt against v_0..v_j, repeated once when the norm
       // drops below 1/sqrt(2) of its value before the projection ("twice is
-      // enough"); every sum in FP64
-      double2* dh1 = W.coef;                       // [j+1][R]
-      double2* dh2 = W.coef + (size_t)(m + 1) * R; // [j+1][R]
-      double2* dnr = W.coef + (size_t)2 * (m + 1) * R;          // ||w'||^2  [R]
-      double2* dn0 = W.coef + (size_t)2 * (m + 1) * R + R;      // ||w||^2   [R]
-      rc = multidot_dev(c, 1, n, R, W.w, 0, W.w, dn0, W.part, st);
+      // enough"); the coefficients and norms are summed in FP64
+      rc = gs_pass(c, W, j + 1, n, R, ld, dh1, dh1f, dn0, dnr, st);
       if (rc) return rc;
-      rc = multidot_dev(c, j + 1, n, R, W.V, ld, W.w, dh1, W.part, st);
-      if (rc) return rc;
-      rc = multi_axpy(c, j + 1, n, R, W.V, ld, dh1, W.w, -1.0, st);
-      if (rc) return rc;
-      rc = multidot_dev(c, 1, n, R, W.w, 0, W.w, dnr, W.part, st);
-      if (rc) return rc;
+      cudaEventRecord(W.ev[3], st);
       SMR_CUDA(c, cudaMemcpyAsync(hbuf.data(), W.coef, (size_t)(2 * (m + 1) + 2) * R * sizeof(double2),
                                   cudaMemcpyDeviceToHost, st));
       SMR_CUDA(c, cudaStreamSynchronize(st));
+      W.t_pc += elapsed_s(W.ev[0], W.ev[1]);
+      W.t_mv += elapsed_s(W.ev[1], W.ev[2]);
+      W.t_or += elapsed_s(W.ev[2], W.ev[3]);
       bool reorth = false;
       for (int r = 0; r < R; ++r) {
         double a0 = hbuf[(size_t)2 * (m + 1) * R + R + r].x, a1 = hbuf[(size_t)2 * (m + 1) * R + r].x;
@@ -293,33 +795,26 @@ static int gmres_core(Ctx* c, int R, int prec, int precond, const double2* rhs, 
       }
       if (reorth) {
         ++*n_reorth;
-        rc = multidot_dev(c, j + 1, n, R, W.V, ld, W.w, dh2, W.part, st);
+        cudaEventRecord(W.ev[4], st);
+        rc = gs_pass(c, W, j + 1, n, R, ld, dh2, dh2f, nullptr, dnr, st);
         if (rc) return rc;
-        rc = multi_axpy(c, j + 1, n, R, W.V, ld, dh2, W.w, -1.0, st);
-        if (rc) return rc;
-        rc = multidot_dev(c, 1, n, R, W.w, 0, W.w, dnr, W.part, st);
-        if (rc) return rc;
+        cudaEventRecord(W.ev[5], st);
         SMR_CUDA(c, cudaMemcpyAsync(hbuf.data() + (size_t)(m + 1) * R, dh2,
                                     (size_t)((m + 1) + 1) * R * sizeof(double2), cudaMemcpyDeviceToHost, st));
         SMR_CUDA(c, cudaStreamSynchronize(st));
+        W.t_or += elapsed_s(W.ev[4], W.ev[5]);
       } else {
         for (size_t q = 0; q < (size_t)(m + 1) * R; ++q) hbuf[(size_t)(m + 1) * R + q] = make_double2(0, 0);
       }
-      // next basis vector V_{j+1} = w / ||w||
-      std::vector<double2> inv(R), zz(R, make_double2(0, 0));
+      // next basis vector v_{j+1} = w / ||w||
+      std::vector<double2> inv(R);
       std::vector<double> hn(R);
       for (int r = 0; r < R; ++r) {
         hn[r] = std::sqrt(std::max(0.0, hbuf[(size_t)2 * (m + 1) * R + r].x));
         inv[r] = make_double2(hn[r] > 0 ? 1.0 / hn[r] : 0.0, 0);
       }
-      double2* Vn = W.V + (size_t)(j + 1) * ld;
-      SMR_CUDA(c, cudaMemcpyAsync(W.coef + (size_t)3 * (m + 1) * R, inv.data(), R * sizeof(double2),
-                                  cudaMemcpyHostToDevice, st));
-      SMR_CUDA(c, cudaMemcpyAsync(W.coef + (size_t)3 * (m + 1) * R + R, zz.data(), R * sizeof(double2),
-                                  cudaMemcpyHostToDevice, st));
-      SMR_CUDA(c, cudaMemcpyAsync(Vn, W.w, ld * sizeof(double2), cudaMemcpyDeviceToDevice, st));
-      rc = col_axpby(n, R, W.coef + (size_t)3 * (m + 1) * R, W.w, W.coef + (size_t)3 * (m + 1) * R + R,
-                     Vn, st);
+      SMR_CUDA(c, cudaMemcpyAsync(dsc, inv.data(), R * sizeof(double2), cudaMemcpyHostToDevice, st));
+      rc = store_basis(j + 1, W.w);
       if (rc) return rc;
       bool any = false;
       for (int r = 0; r < R; ++r) {
@@ -358,7 +853,7 @@ static int gmres_core(Ctx* c, int R, int prec, int precond, const double2* rhs, 
       }
       if (!any) { ++j; break; }
     }
-    // y per column: back substitution; coefficients [jmax][R] on the device
+    // y per column by back substitution, then d += M^-1 (V y)
     int jmax = 0;
     for (int r = 0; r < R; ++r) jmax = std::max(jmax, jend[r]);
     std::vector<double2> ycoef((size_t)std::max(jmax, 1) * R, make_double2(0, 0));
@@ -374,35 +869,31 @@ static int gmres_core(Ctx* c, int R, int prec, int precond, const double2* rhs, 
       for (int i = 0; i < J; ++i) ycoef[(size_t)i * R + r] = make_double2(y[i].real(), y[i].imag());
     }
     if (jmax > 0) {
-      SMR_CUDA(c, cudaMemcpyAsync(W.coef, ycoef.data(), (size_t)jmax * R * sizeof(double2),
-                                  cudaMemcpyHostToDevice, st));
-      if (W.Z) {
-        rc = multi_axpy(c, jmax, n, R, W.Z, ld, W.coef, d, 1.0, st);
+      SMR_CUDA(c, cudaMemsetAsync(W.w, 0, ld * sizeof(double2), st));
+      if (W.f32) {
+        std::vector<float2> yf(jmax);
+        for (int i = 0; i < jmax; ++i) yf[i] = make_float2((float)ycoef[i].x, (float)ycoef[i].y);
+        SMR_CUDA(c, cudaMemcpyAsync(dyf, yf.data(), jmax * sizeof(float2), cudaMemcpyHostToDevice, st));
+        rc = gs32_axpy(c, jmax, n, (const float2*)W.V, ld, dyf, W.w, 1.0, nullptr, nullptr, st);
       } else {
-        SMR_CUDA(c, cudaMemsetAsync(W.w, 0, ld * sizeof(double2), st));
-        rc = multi_axpy(c, jmax, n, R, W.V, ld, W.coef, W.w, 1.0, st);
-        if (rc) return rc;
-        if (precond == SMR_PRECOND_BLOCKDIAG) {
-          rc = run_precond(c, R, prec, W.w, W.t, st);
-        } else {
-          SMR_CUDA(c, cudaMemcpyAsync(W.t, W.w, ld * sizeof(double2), cudaMemcpyDeviceToDevice, st));
-        }
-        if (rc) return rc;
-        std::vector<double2> one(R, make_double2(1, 0));
-        SMR_CUDA(c, cudaMemcpyAsync(W.coef, one.data(), R * sizeof(double2), cudaMemcpyHostToDevice, st));
-        rc = col_axpby(n, R, W.coef, W.t, W.coef, d, st);
+        SMR_CUDA(c, cudaMemcpyAsync(W.coef, ycoef.data(), (size_t)jmax * R * sizeof(double2),
+                                    cudaMemcpyHostToDevice, st));
+        rc = multi_axpy(c, jmax, n, R, (const double2*)W.V, ld, W.coef, W.w, 1.0, st);
       }
       if (rc) return rc;
+      if (precond == SMR_PRECOND_BLOCKDIAG) {
+        rc = run_precond(c, R, prec, W.w, W.t, st);
+      } else {
+        SMR_CUDA(c, cudaMemcpyAsync(W.t, W.w, ld * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+      }
+      if (rc) return rc;
+      std::vector<double2> one(R, make_double2(1, 0));
+      SMR_CUDA(c, cudaMemcpyAsync(W.coef, one.data(), R * sizeof(double2), cudaMemcpyHostToDevice, st));
+      rc = col_axpby(n, R, W.coef, W.t, W.coef, d, st);
+      if (rc) return rc;
     }
-    // true residual of this operator: r0 = rhs - A d
-    rc = apply_A(c, R, prec, d, W.w, st);
-    if (rc) return rc;
-    ++*nmv;
-    SMR_CUDA(c, cudaMemcpyAsync(r0, rhs, ld * sizeof(double2), cudaMemcpyDeviceToDevice, st));
-    std::vector<double2> mone(R, make_double2(-1, 0)), one(R, make_double2(1, 0));
-    SMR_CUDA(c, cudaMemcpyAsync(W.coef, mone.data(), R * sizeof(double2), cudaMemcpyHostToDevice, st));
-    SMR_CUDA(c, cudaMemcpyAsync(W.coef + R, one.data(), R * sizeof(double2), cudaMemcpyHostToDevice, st));
-    rc = col_axpby(n, R, W.coef, W.w, W.coef + R, r0, st);
+    // true residual of this operator
+    rc = residual();
     if (rc) return rc;
   }
 }
@@ -414,27 +905,36 @@ int solve(Ctx* c, int R, const double2* b, double2* x, const smr_solve_opts* o, 
   long long ld = n * R;
   int maxit = o->maxit > 0 ? o->maxit : 2000;
   int m = (o->restart > 0) ? std::min(o->restart, maxit) : maxit;
-  // cap the Krylov dimension by device memory (60% of what is free)
+  // cap the Krylov dimension by device memory (60% of what is free); the
+  // FP32 operator with one right-hand side keeps its basis in FP32
   size_t freeb = 0, totb = 0;
   cudaMemGetInfo(&freeb, &totb);
-  bool flex = (o->precision == SMR_PREC_FP32);
-  double per = (double)ld * sizeof(double2) * (flex ? 2.0 : 1.0);
+  Work W;
+  W.f32 = (o->precision == SMR_PREC_FP32 && R == 1 && n % 2 == 0);
+  size_t eb = W.f32 ? sizeof(float2) : sizeof(double2);
+  double per = (double)ld * eb;
   int mcap = (int)std::max(2.0, 0.6 * (double)freeb / per - 4);
   m = std::max(1, std::min(m, mcap));
-  Work W;
-  size_t vbytes = (size_t)(m + 1) * ld * sizeof(double2);
-  SMR_CUDA(c, cudaMalloc((void**)&W.V, vbytes));
-  if (flex) SMR_CUDA(c, cudaMalloc((void**)&W.Z, (size_t)m * ld * sizeof(double2)));
-  SMR_CUDA(c, cudaMalloc((void**)&W.w, ld * sizeof(double2)));
-  SMR_CUDA(c, cudaMalloc((void**)&W.t, ld * sizeof(double2)));
-  SMR_CUDA(c, cudaMalloc((void**)&W.coef, (size_t)4 * (m + 2) * R * sizeof(double2)));
-  int rl, nchunk;
-  long long rows;
-  chunking(n, R, &rl, &nchunk, &rows);
-  SMR_CUDA(c, cudaMalloc((void**)&W.part, (size_t)(m + 2) * nchunk * R * sizeof(double2)));
   auto cleanup = [&]() {
-    cudaFree(W.V); cudaFree(W.Z); cudaFree(W.w); cudaFree(W.t); cudaFree(W.coef); cudaFree(W.part);
+    cudaFree(W.V); cudaFree(W.u); cudaFree(W.w); cudaFree(W.t); cudaFree(W.coef); cudaFree(W.coef_f);
+    cudaFree(W.part);
+    for (int q = 0; q < 6; ++q)
+      if (W.ev[q]) cudaEventDestroy(W.ev[q]);
   };
+  bool ok = cudaMalloc(&W.V, (size_t)(m + 1) * ld * eb) == cudaSuccess &&
+            cudaMalloc((void**)&W.u, ld * sizeof(double2)) == cudaSuccess &&
+            cudaMalloc((void**)&W.w, ld * sizeof(double2)) == cudaSuccess &&
+            cudaMalloc((void**)&W.t, ld * sizeof(double2)) == cudaSuccess &&
+            cudaMalloc((void**)&W.coef, (size_t)4 * (m + 2) * R * sizeof(double2)) == cudaSuccess &&
+            cudaMalloc((void**)&W.coef_f, (size_t)3 * (m + 2) * sizeof(float2)) == cudaSuccess &&
+            cudaMalloc((void**)&W.part, part_elems(n, R, m + 2) * sizeof(double2)) == cudaSuccess;
+  for (int q = 0; q < 6 && ok; ++q) ok = cudaEventCreate(&W.ev[q]) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    cleanup();
+    c->err = "solve: device allocation of the Krylov workspace failed";
+    return SMR_E_OOM;
+  }
   int its = 0, mv64 = 0, mv32 = 0, outer = 0, nreo = 0, rc = SMR_OK;
   std::vector<double> rel;
   double tol = o->tol > 0 ? o->tol : 1e-4;
@@ -443,7 +943,7 @@ int solve(Ctx* c, int R, const double2* b, double2* x, const smr_solve_opts* o, 
     rc = gmres_core(c, R, SMR_PREC_FP64, o->precond, b, x, o->use_x0 != 0, tc, maxit, m, W, &its,
                     &mv64, &nreo, rel, st);
   } else {
-    // iterative refinement: outer FP64 residual, inner FGMRES on the FP32 product
+    // iterative refinement: outer FP64 residual, inner GMRES on the FP32 operator
     double2 *r = nullptr, *dlt = nullptr;
     SMR_CUDA(c, cudaMalloc((void**)&r, ld * sizeof(double2)));
     SMR_CUDA(c, cudaMalloc((void**)&dlt, ld * sizeof(double2)));
@@ -475,8 +975,9 @@ int solve(Ctx* c, int R, const double2* b, double2* x, const smr_solve_opts* o, 
         double bq = bn[q] > 0 ? bn[q] : 1.0;
         rel[q] = rn[q] / bq;
         all = all && rel[q] <= tol;
-        // inner target: leave half the budget for the FP32 product error
-        tc[q] = (rn[q] > 0) ? std::max(0.5 * tol * bq / rn[q], 1e-7) : 1.0;
+        // inner target: 90% of the remaining tolerance (the FP32 product error
+        // is ~1e-6 relative, far below the rest)
+        tc[q] = (rn[q] > 0) ? std::max(0.9 * tol * bq / rn[q], 1e-7) : 1.0;
       }
       if (all) break;
       if (outer >= max_outer || its >= maxit) { rc = SMR_E_NOT_CONVERGED; break; }
@@ -500,6 +1001,9 @@ int solve(Ctx* c, int R, const double2* b, double2* x, const smr_solve_opts* o, 
     stats->matvecs_fp32 = mv32;
     stats->outer = outer;
     stats->reorth = nreo;
+    stats->seconds_product = W.t_mv;
+    stats->seconds_precond = W.t_pc;
+    stats->seconds_orth = W.t_or;
     double mx = 0;
     for (double v : rel) mx = std::max(mx, v);
     stats->resid_true = mx;

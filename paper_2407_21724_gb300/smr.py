@@ -51,7 +51,8 @@ class smr_solve_opts(C.Structure):
 class smr_solve_stats(C.Structure):
     _fields_ = [("iters", C.c_int), ("matvecs_fp64", C.c_int), ("matvecs_fp32", C.c_int),
                 ("outer", C.c_int), ("reorth", C.c_int), ("resid_true", C.c_double),
-                ("seconds", C.c_double)]
+                ("seconds", C.c_double), ("seconds_product", C.c_double),
+                ("seconds_precond", C.c_double), ("seconds_orth", C.c_double)]
 
 
 class smr_launch_t(C.Structure):
@@ -301,7 +302,9 @@ def smr_solve(ctx, b, x, R=None, stream=None, **kw):
     if rc not in (0, -5):
         _check(ctx, rc)
     return rc, dict(iters=st.iters, matvecs_fp64=st.matvecs_fp64, matvecs_fp32=st.matvecs_fp32,
-                    outer=st.outer, reorth=st.reorth, resid_true=st.resid_true, seconds=st.seconds)
+                    outer=st.outer, reorth=st.reorth, resid_true=st.resid_true, seconds=st.seconds,
+                    seconds_product=st.seconds_product, seconds_precond=st.seconds_precond,
+                    seconds_orth=st.seconds_orth)
 
 
 def smr_far_field(ctx, x, dirs, F, R=None, stream=None):

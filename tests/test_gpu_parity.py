@@ -221,6 +221,45 @@ def test_solve_fp64_and_mixed(c1):
     assert abs(st["iters"] - info["iters"]) <= 1
 
 
+@pytest.mark.parametrize("prec", [smr.SMR_PREC_FP64, smr.SMR_PREC_FP32])
+def test_solve_batched_columns(rnd, prec):
+    """Three systems in lockstep ([N][R], R = 3): every column meets the
+    tolerance on the oracle operator, and the lockstep run takes about as
+    many Arnoldi steps as the slowest column solved alone."""
+    n = rnd.info["n_unknowns"]
+    incs = [workloads.incidence(0, 0, "x"), workloads.incidence(20, 45, "y"),
+            workloads.incidence(35, 180, "x")]
+    B = np.stack([opm.rhs(rnd.sc, k, e) for k, e in incs], axis=1)
+    bd = torch.from_numpy(np.ascontiguousarray(B).reshape(-1)).cuda()
+    xd = torch.zeros_like(bd)
+    rc, st = smr.smr_solve(rnd.ctx, bd, xd, R=3, tol=1e-4, precision=prec)
+    assert rc == 0, st
+    X = xd.cpu().numpy().reshape(n, 3)
+    singles = []
+    for r in range(3):
+        res = np.linalg.norm(B[:, r] - rnd.M.matvec(X[:, r])) / np.linalg.norm(B[:, r])
+        assert res <= 1.001e-4, (r, res, st)
+        b1 = torch.from_numpy(np.ascontiguousarray(B[:, r])).cuda()
+        x1 = torch.zeros_like(b1)
+        rc1, st1 = smr.smr_solve(rnd.ctx, b1, x1, tol=1e-4, precision=prec)
+        assert rc1 == 0
+        singles.append(st1["iters"])
+    assert max(singles) - 2 <= st["iters"] <= max(singles) + 3, (singles, st)
+
+
+@pytest.mark.parametrize("prec", [smr.SMR_PREC_FP64, smr.SMR_PREC_FP32])
+def test_solve_restarted(rnd, prec):
+    """Restarted GMRES (Krylov dimension 8) still reaches a tight tolerance
+    on the oracle operator."""
+    b = opm.rhs(rnd.sc, *workloads.incidence(10, 30, "x"))
+    bd = torch.from_numpy(b).cuda()
+    xd = torch.zeros_like(bd)
+    rc, st = smr.smr_solve(rnd.ctx, bd, xd, tol=1e-5, restart=8, precision=prec)
+    assert rc == 0, st
+    res = np.linalg.norm(b - rnd.M.matvec(xd.cpu().numpy())) / np.linalg.norm(b)
+    assert res <= 1.001e-5, (res, st)
+
+
 def test_far_field_and_cross_sections(c1):
     b = opm.rhs(c1.sc, [0, 0, 1], [1, 0, 0])
     x, _ = ogm.gmres(c1.M.matvec, b, precond=ogm.block_diag_precond(c1.sc), tol=1e-8)
