@@ -34,7 +34,8 @@ void free_scene(Ctx* c) {
     dfree(L.d_T64); dfree(L.d_T32); dfree(L.d_parent); dfree(L.d_quad); dfree(L.d_ch_ptr);
     dfree(L.d_ch_idx); dfree(L.d_ch_quad); dfree(L.d_th_src); dfree(L.d_th_refl); dfree(L.d_th_w64);
     dfree(L.d_th_w32); dfree(L.d_ph_src); dfree(L.d_ph_w64); dfree(L.d_ph_w32); dfree(L.d_shift64);
-    dfree(L.d_shift32); dfree(L.d_ant_ptr); dfree(L.d_ant_idx); dfree(L.d_ant_w64); dfree(L.d_ant_w32);
+    dfree(L.d_shift32); dfree(L.d_ant_lo); dfree(L.d_ant_pjp); dfree(L.d_ant_pw64); dfree(L.d_ant_pw32);
+    dfree(L.d_ant_ttp); dfree(L.d_ant_tw64); dfree(L.d_ant_tw32);
     dfree(L.d_tht_ptr); dfree(L.d_tht_tp); dfree(L.d_tht_refl); dfree(L.d_tht_w64); dfree(L.d_tht_w32);
     dfree(L.d_pht_ptr); dfree(L.d_pht_jp); dfree(L.d_pht_w64); dfree(L.d_pht_w32); dfree(L.d_wthp64);
     dfree(L.d_wthp32); dfree(L.d_boxmap); dfree(L.d_offid); dfree(L.d_tiles); dfree(L.d_tiles8);
@@ -196,41 +197,66 @@ int build_interp(Ctx* c, Level& C, const Level& P) {
         (rc = upload(c, &C.d_pht_w32, pww32)) || (rc = upload(c, &C.d_wthp64, wpth)) ||
         (rc = upload(c, &C.d_wthp32, wpth32)))
       return rc;
-  }
-  // weighted adjoint A = W_c^{-1} I^T W_p as CSR over child points
-  std::vector<int> cnt(C.K + 1, 0);
-  int half = C.nph / 2;
-  auto child_of = [&](int tp, int jp, int a, int b) {
-    int row = tsrc[4 * tp + a];
-    int col = psrc[4 * jp + b];
-    if (trefl[4 * tp + a]) col = (col + half) % C.nph;
-    return row * C.nph + col;
-  };
-  for (int tp = 0; tp < P.nth; ++tp)
-    for (int jp = 0; jp < P.nph; ++jp)
-      for (int a = 0; a < 4; ++a)
-        for (int b = 0; b < 4; ++b) cnt[child_of(tp, jp, a, b) + 1]++;
-  for (int k = 0; k < C.K; ++k) cnt[k + 1] += cnt[k];
-  long long nnz = cnt[C.K];
-  std::vector<int> idx(nnz), fill(cnt.begin(), cnt.end() - 1);
-  std::vector<double> val(nnz);
-  for (int tp = 0; tp < P.nth; ++tp)
-    for (int jp = 0; jp < P.nph; ++jp) {
-      int kp = tp * P.nph + jp;
-      for (int a = 0; a < 4; ++a)
-        for (int b = 0; b < 4; ++b) {
-          int kc = child_of(tp, jp, a, b);
-          double sg = trefl[4 * tp + a] ? -1.0 : 1.0;
-          int e = fill[kc]++;
-          idx[e] = kp;
-          val[e] = sg * tw[4 * tp + a] * pw[4 * jp + b] * P.w[kp] / C.w[kc];
-        }
+    // tiles of the fused single right-hand-side anterpolation: child theta
+    // rows in tiles of TI, each with the range [lo, hi) of parent rows its
+    // transposed taps read; GR = the widest range
+    C.ant_TI = C.nth <= 24 ? C.nth : 16;
+    C.ant_nit = (C.nth + C.ant_TI - 1) / C.ant_TI;
+    std::vector<int> lohi(2 * C.ant_nit);
+    C.ant_GR = 1;
+    for (int it = 0; it < C.ant_nit; ++it) {
+      int i0 = it * C.ant_TI, i1 = std::min(C.nth, i0 + C.ant_TI);
+      int lo = P.nth, hi = 0;
+      for (int e = tptr[i0]; e < tptr[i1]; ++e) {
+        lo = std::min(lo, ttp[e]);
+        hi = std::max(hi, ttp[e] + 1);
+      }
+      if (hi <= lo) { lo = 0; hi = 1; }            // no taps: one (zero-weighted) row
+      lohi[it] = lo;
+      lohi[C.ant_nit + it] = hi;
+      C.ant_GR = std::max(C.ant_GR, hi - lo);
     }
-  std::vector<float> val32(val.begin(), val.end());
-  C.ant_nnz = nnz;
-  if ((rc = upload(c, &C.d_ant_ptr, cnt)) || (rc = upload(c, &C.d_ant_idx, idx)) ||
-      (rc = upload(c, &C.d_ant_w64, val)) || (rc = upload(c, &C.d_ant_w32, val32)))
-    return rc;
+    // column chunk per precision: GR x 2 JC directions in 48 KB of shared memory
+    for (int q = 0; q < 2; ++q) {
+      int dirb = q == 0 ? 64 : 32;                  // SMR_PREC_FP64, SMR_PREC_FP32
+      int jc = (48 * 1024) / (C.ant_GR * 2 * dirb);
+      C.ant_JC[q] = std::max(1, std::min(C.nph / 2, jc));
+    }
+    if ((rc = upload(c, &C.d_ant_lo, lohi))) return rc;
+    // padded transposed taps
+    int pm = 0, tm = 0;
+    for (int j = 0; j < C.nph; ++j) pm = std::max(pm, pptr[j + 1] - pptr[j]);
+    for (int i = 0; i < C.nth; ++i) tm = std::max(tm, tptr[i + 1] - tptr[i]);
+    C.ant_PM = (pm + 3) / 4 * 4;
+    C.ant_TM = (tm + 3) / 4 * 4;
+    std::vector<int> ppj((size_t)C.nph * C.ant_PM), tpk((size_t)C.nth * C.ant_TM);
+    std::vector<double> ppw((size_t)C.nph * C.ant_PM, 0.0), tpw((size_t)C.nth * C.ant_TM, 0.0);
+    for (int j = 0; j < C.nph; ++j)
+      for (int q = 0; q < C.ant_PM; ++q) {
+        int e = pptr[j] + q;
+        bool real = e < pptr[j + 1];
+        // padding repeats the column's first tap (or column 0) with weight 0
+        ppj[(size_t)j * C.ant_PM + q] = real ? pjp[e] : (pptr[j + 1] > pptr[j] ? pjp[pptr[j]] : 0);
+        ppw[(size_t)j * C.ant_PM + q] = real ? pww[e] : 0.0;
+      }
+    for (int i = 0; i < C.nth; ++i)
+      for (int q = 0; q < C.ant_TM; ++q) {
+        int e = tptr[i] + q;
+        bool real = e < tptr[i + 1];
+        // padding repeats the row's first tap (or the tile's first parent row)
+        // with weight 0, so that it reads a row the tile computed
+        int pk = lohi[i / C.ant_TI];
+        if (real) pk = ttp[e] | (trf[e] << 16);
+        else if (tptr[i + 1] > tptr[i]) pk = ttp[tptr[i]] | (trf[tptr[i]] << 16);
+        tpk[(size_t)i * C.ant_TM + q] = pk;
+        tpw[(size_t)i * C.ant_TM + q] = real ? tww[e] : 0.0;
+      }
+    std::vector<float> ppw32(ppw.begin(), ppw.end()), tpw32(tpw.begin(), tpw.end());
+    if ((rc = upload(c, &C.d_ant_pjp, ppj)) || (rc = upload(c, &C.d_ant_pw64, ppw)) ||
+        (rc = upload(c, &C.d_ant_pw32, ppw32)) || (rc = upload(c, &C.d_ant_ttp, tpk)) ||
+        (rc = upload(c, &C.d_ant_tw64, tpw)) || (rc = upload(c, &C.d_ant_tw32, tpw32)))
+      return rc;
+  }
   // shift tables exp(j k khat_p . (c_child - c_parent)), child offset (+-1/2) x child box
   std::vector<double2> sh(4 * (size_t)P.K);
   std::vector<float2> sh32(4 * (size_t)P.K);
@@ -694,7 +720,7 @@ int smr_info(smr_ctx* h, smr_info_t* info) {
     info->K[s] = L.K;
     info->n_box[s] = L.nbox;
     info->n_il[s] = (int)L.il_src.size();
-    bytes += 2.0 * L.nbox * L.K * 4 * 16 + (double)L.off_dx.size() * L.K * 24 + L.ant_nnz * 16;
+    bytes += 2.0 * L.nbox * L.K * 4 * 16 + (double)L.off_dx.size() * L.K * 24;
   }
   info->n_near_pairs = (long long)c->nr_col.size();
   info->n_near_blocks = c->nblk;

@@ -55,6 +55,74 @@ template <typename V> __device__ __forceinline__ V cmul(V a, V b) {
   return r;
 }
 
+// the 4 fields of one direction (single right-hand side): 32 or 64 bytes
+__device__ __forceinline__ void ld_dir(const float2* p, float2* v) {
+  float4 a = reinterpret_cast<const float4*>(p)[0], b = reinterpret_cast<const float4*>(p)[1];
+  v[0] = make_float2(a.x, a.y); v[1] = make_float2(a.z, a.w);
+  v[2] = make_float2(b.x, b.y); v[3] = make_float2(b.z, b.w);
+}
+__device__ __forceinline__ void ld_dir(const double2* p, double2* v) {
+  v[0] = p[0]; v[1] = p[1]; v[2] = p[2]; v[3] = p[3];
+}
+__device__ __forceinline__ void st_dir(float2* p, const float2* v) {
+  reinterpret_cast<float4*>(p)[0] = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+  reinterpret_cast<float4*>(p)[1] = make_float4(v[2].x, v[2].y, v[3].x, v[3].y);
+}
+__device__ __forceinline__ void st_dir(double2* p, const double2* v) {
+  p[0] = v[0]; p[1] = v[1]; p[2] = v[2]; p[3] = v[3];
+}
+
+
+// ------------------------------------------------------------------ 16-byte direction parts
+// Single right-hand side kernels give each thread one 16-byte part of a
+// direction's 4 fields (FP32: 2 fields as a float4, FP64: 1 field), so that
+// a warp instruction reads or writes one contiguous 512-byte run and shared
+// memory is accessed without bank conflicts.  NT threads share a direction.
+template <typename T> struct Part;
+template <> struct Part<float> {
+  typedef float4 H;
+  static constexpr int NT = 2, FPT = 2;
+  static __device__ __forceinline__ H zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+  static __device__ __forceinline__ void rfma(H& a, float w, H v) {
+    a.x = fmaf(w, v.x, a.x); a.y = fmaf(w, v.y, a.y); a.z = fmaf(w, v.z, a.z); a.w = fmaf(w, v.w, a.w);
+  }
+  // a += s * v for each complex field of v
+  static __device__ __forceinline__ void cfma(H& a, float2 s, H v) {
+    a.x = fmaf(s.x, v.x, a.x); a.x = fmaf(-s.y, v.y, a.x);
+    a.y = fmaf(s.x, v.y, a.y); a.y = fmaf(s.y, v.x, a.y);
+    a.z = fmaf(s.x, v.z, a.z); a.z = fmaf(-s.y, v.w, a.z);
+    a.w = fmaf(s.x, v.w, a.w); a.w = fmaf(s.y, v.z, a.w);
+  }
+  static __device__ __forceinline__ void add(H& a, H v) { a.x += v.x; a.y += v.y; a.z += v.z; a.w += v.w; }
+  static __device__ __forceinline__ void w4(const float* p, float* w) {
+    float4 a = *reinterpret_cast<const float4*>(p);
+    w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w;
+  }
+};
+template <> struct Part<double> {
+  typedef double2 H;
+  static constexpr int NT = 4, FPT = 1;
+  static __device__ __forceinline__ H zero() { return make_double2(0.0, 0.0); }
+  static __device__ __forceinline__ void rfma(H& a, double w, H v) { a.x = fma(w, v.x, a.x); a.y = fma(w, v.y, a.y); }
+  static __device__ __forceinline__ void cfma(H& a, double2 s, H v) {
+    a.x = fma(s.x, v.x, a.x); a.x = fma(-s.y, v.y, a.x);
+    a.y = fma(s.x, v.y, a.y); a.y = fma(s.y, v.x, a.y);
+  }
+  static __device__ __forceinline__ void add(H& a, H v) { a.x += v.x; a.y += v.y; }
+  static __device__ __forceinline__ void w4(const double* p, double* w) {
+    double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
+    w[0] = a.x; w[1] = a.y; w[2] = b.x; w[3] = b.y;
+  }
+};
+template <typename T>
+__device__ __forceinline__ typename Part<T>::H ldp(const typename CV<T>::V* base, size_t dir, int h) {
+  return reinterpret_cast<const typename Part<T>::H*>(base + dir * 4)[h];
+}
+template <typename T>
+__device__ __forceinline__ void stp(typename CV<T>::V* base, size_t dir, int h, typename Part<T>::H v) {
+  reinterpret_cast<typename Part<T>::H*>(base + dir * 4)[h] = v;
+}
+
 // ------------------------------------------------------------------ aggregation
 // out0[mu][k][f][r] = shift * sum_n conj(P[s][n][comp f][k]) x[mu][cur f][n][r]
 // One CTA = a tile of up to 16 particles of one shape (x in shared memory) x a
@@ -287,6 +355,84 @@ __global__ void k_interp_fused(int nthP, int nphP, int nphC, int Kc, int R, int 
   }
 }
 
+
+// Single right-hand side: CTA = (parent box, tile of TR parent theta rows);
+// each thread owns up to EM1 parent direction parts of the tile across the
+// loop over the children.  Per child: theta pass of the tile's rows into
+// shared memory G[TR][nphC][4] (4 taps, tables read as 16-byte vectors), then
+// phi pass, shift and child sum in registers.
+template <typename T> struct EM1 { static constexpr int v = sizeof(T) == 4 ? 8 : 12; };
+template <typename T>
+__global__ void __launch_bounds__(256) k_interp1(int nthP, int nphP, int nphC, int Kc, int TR, int nrt,
+                                                 const int* __restrict__ ch_ptr, const int* __restrict__ ch_idx,
+                                                 const int* __restrict__ ch_quad, const int* __restrict__ th_src,
+                                                 const int* __restrict__ th_refl, const T* __restrict__ th_w,
+                                                 const int* __restrict__ ph_src, const T* __restrict__ ph_w,
+                                                 const typename CV<T>::V* __restrict__ shift,
+                                                 const typename CV<T>::V* __restrict__ F,
+                                                 typename CV<T>::V* __restrict__ out) {
+  typedef typename CV<T>::V V;
+  typedef Part<T> P;
+  typedef typename P::H H;
+  constexpr int NT = P::NT, EM = EM1<T>::v;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* G = reinterpret_cast<V*>(smem_raw);           // [TR][nphC][4]
+  int B = blockIdx.x / nrt, rt = blockIdx.x - (blockIdx.x / nrt) * nrt;
+  int tp0 = rt * TR, ntr = min(TR, nthP - tp0);
+  int Kp = nthP * nphP;
+  int nG = ntr * nphC * NT, nout = ntr * nphP * NT;
+  int half = nphC >> 1;
+  H acc[EM];
+#pragma unroll
+  for (int i = 0; i < EM; ++i) acc[i] = P::zero();
+  for (int e = ch_ptr[B]; e < ch_ptr[B + 1]; ++e) {
+    const V* src = F + (size_t)ch_idx[e] * Kc * 4;
+    const V* sh = shift + (size_t)ch_quad[e] * Kp + (size_t)tp0 * nphP;
+    __syncthreads();
+    for (int t = threadIdx.x; t < nG; t += blockDim.x) {
+      int task = t / NT, h = t - task * NT;
+      int tr = task / nphC, j = task - tr * nphC;
+      int tp = tp0 + tr;
+      int jr = j + half;
+      jr = jr >= nphC ? jr - nphC : jr;
+      int4 sr = *reinterpret_cast<const int4*>(th_src + tp * 4);
+      int4 rf = *reinterpret_cast<const int4*>(th_refl + tp * 4);
+      T w[4];
+      P::w4(th_w + tp * 4, w);
+      H a = P::zero();
+      P::rfma(a, rf.x ? -w[0] : w[0], ldp<T>(src, (size_t)sr.x * nphC + (rf.x ? jr : j), h));
+      P::rfma(a, rf.y ? -w[1] : w[1], ldp<T>(src, (size_t)sr.y * nphC + (rf.y ? jr : j), h));
+      P::rfma(a, rf.z ? -w[2] : w[2], ldp<T>(src, (size_t)sr.z * nphC + (rf.z ? jr : j), h));
+      P::rfma(a, rf.w ? -w[3] : w[3], ldp<T>(src, (size_t)sr.w * nphC + (rf.w ? jr : j), h));
+      stp<T>(G, task, h, a);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < EM; ++i) {
+      int t = threadIdx.x + i * blockDim.x;
+      if (t < nout) {
+        int task = t / NT, h = t - task * NT;
+        int tr = task / nphP, jp = task - tr * nphP;
+        int4 cs = *reinterpret_cast<const int4*>(ph_src + jp * 4);
+        T w[4];
+        P::w4(ph_w + jp * 4, w);
+        size_t rb = (size_t)tr * nphC;
+        H sm = P::zero();
+        P::rfma(sm, w[0], ldp<T>(G, rb + cs.x, h));
+        P::rfma(sm, w[1], ldp<T>(G, rb + cs.y, h));
+        P::rfma(sm, w[2], ldp<T>(G, rb + cs.z, h));
+        P::rfma(sm, w[3], ldp<T>(G, rb + cs.w, h));
+        P::cfma(acc[i], sh[tr * nphP + jp], sm);
+      }
+    }
+  }
+  V* dst = out + ((size_t)B * Kp + (size_t)tp0 * nphP) * 4;
+#pragma unroll
+  for (int i = 0; i < EM; ++i) {
+    int t = threadIdx.x + i * blockDim.x;
+    if (t < nout) stp<T>(dst, t / NT, t % NT, acc[i]);
+  }
+}
 // ------------------------------------------------------------------ translation
 // in[b][k] = sum_{(b', o) in IL(b)} T[o][k] out[b'][k]   (Eqs. 22-23)
 // One CTA = 4x4 target boxes of the lattice x a chunk of directions; the 8x8
@@ -609,6 +755,91 @@ __global__ void k_anterp_theta(int nrows, int nthC, int nthP, int nphC, int R,
   }
 }
 
+
+// Single right-hand side, both adjoint passes fused.  CTA = (child c, tile of
+// child theta rows [i0, i0 + TI), column chunk [j0, j0 + JC) of the first
+// half of the phi grid together with the same chunk shifted by N/2, so that
+// the pole reflection j -> j + N/2 stays inside the CTA).  The parent rows
+// [lo, hi) the tile draws on get the phi-transposed pass (conjugate shift and
+// parent theta weight) into shared memory; then the theta-transposed pass adds
+// into the child's incoming spectrum.  Transposed taps are padded to PM / TM
+// per child column / row (zero weights), packed as (tp | refl << 16).
+template <typename T>
+__global__ void __launch_bounds__(256) k_anterp1(int nthC, int nphC, int nthP, int nphP, int TI, int nit,
+                                                 int JC, int njc, const int* __restrict__ parent,
+                                                 const int* __restrict__ quad, const int* __restrict__ lo_row,
+                                                 int PM, const int* __restrict__ pjp, const T* __restrict__ pw,
+                                                 const T* __restrict__ wthp,
+                                                 const typename CV<T>::V* __restrict__ shift,
+                                                 const typename CV<T>::V* __restrict__ inP, int TM,
+                                                 const int* __restrict__ ttp, const T* __restrict__ tw,
+                                                 typename CV<T>::V* __restrict__ inC) {
+  typedef typename CV<T>::V V;
+  typedef Part<T> P;
+  typedef typename P::H H;
+  constexpr int NT = P::NT;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* Gt = reinterpret_cast<V*>(smem_raw);          // [GR][2 JC][4]
+  int blk = blockIdx.x;
+  int jcb = blk % njc;
+  blk /= njc;
+  int it = blk % nit, c = blk / nit;
+  int i0 = it * TI, ni = min(TI, nthC - i0);
+  int half = nphC >> 1;
+  int j0 = jcb * JC, nj = min(JC, half - j0);
+  int lo = lo_row[it], hi = lo_row[nit + it];
+  int nr = hi - lo, W = 2 * nj;
+  int Kp = nthP * nphP, Kc = nthC * nphC;
+  const V* srcP = inP + (size_t)parent[c] * Kp * 4;
+  const V* sh = shift + (size_t)quad[c] * Kp;
+  for (int t = threadIdx.x; t < nr * W * NT; t += blockDim.x) {
+    int task = t / NT, h = t - task * NT;
+    int r = task / W, u = task - r * W;
+    int j = (u < nj) ? j0 + u : j0 + half + (u - nj);
+    int tp = lo + r;
+    T wt = wthp[tp];
+    const V* prow = srcP + (size_t)tp * nphP * 4;
+    const V* srow = sh + (size_t)tp * nphP;
+    H a = P::zero();
+    for (int q = 0; q < PM; q += 4) {
+      int4 jj = *reinterpret_cast<const int4*>(pjp + (size_t)j * PM + q);
+      T w[4];
+      P::w4(pw + (size_t)j * PM + q, w);
+      int js[4] = {jj.x, jj.y, jj.z, jj.w};
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        V s = srow[js[b]];
+        T ww = w[b] * wt;
+        P::cfma(a, mkc(ww * s.x, -ww * s.y), ldp<T>(prow, js[b], h));
+      }
+    }
+    stp<T>(Gt, task, h, a);
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < ni * W * NT; t += blockDim.x) {
+    int task = t / NT, h = t - task * NT;
+    int il = task / W, u = task - il * W;
+    int ur = u < nj ? u + nj : u - nj;             // column j + N/2 (mod N)
+    int j = (u < nj) ? j0 + u : j0 + half + (u - nj);
+    int i = i0 + il;
+    H a = P::zero();
+    for (int q = 0; q < TM; q += 4) {
+      int4 pk = *reinterpret_cast<const int4*>(ttp + (size_t)i * TM + q);
+      T w[4];
+      P::w4(tw + (size_t)i * TM + q, w);
+      int ps[4] = {pk.x, pk.y, pk.z, pk.w};
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        int r = (ps[b] & 0xffff) - lo;
+        P::rfma(a, w[b], ldp<T>(Gt, (size_t)r * W + ((ps[b] >> 16) ? ur : u), h));
+      }
+    }
+    size_t d = (size_t)c * Kc + (size_t)i * nphC + j;
+    H cur = ldp<T>(inC, d, h);
+    P::add(cur, a);
+    stp<T>(inC, d, h, cur);
+  }
+}
 // ------------------------------------------------------------------ receive
 // y_e[m] += -jk sum_k w conj(sh) [P_th (z B0 + B3) + P_ph (z B1 - B2)]
 // y_m[m] += -jk sum_k w conj(sh) [P_th (-B1 + B2/z) + P_ph (B0 + B3/z)]   (Eqs. 24-25)
@@ -830,6 +1061,20 @@ static int far_impl(Ctx* c, int R, const double2* x, double2* y, bool accumulate
     pbeg(c, st, "interpolate", s,
          ((double)Lc.nbox * Lc.K + (double)Lp.nbox * Lp.K) * 4 * R_ * es + 4.0 * Lp.K * es,
          (double)Lc.nbox * Lp.nth * Lc.nph * 4 * R_ * 16.0 + (double)Lc.nbox * Lp.K * 4 * R_ * 24.0);
+    if (R == 1 && Lp.nph * Part<T>::NT <= 256 * EM1<T>::v) {
+      int TR = std::max(1, std::min(Lp.nth, (256 * EM1<T>::v) / (Lp.nph * Part<T>::NT)));
+      int nrt = (Lp.nth + TR - 1) / TR;
+      size_t sm1 = (size_t)TR * Lc.nph * 4 * sizeof(V);
+      cudaFuncSetAttribute(k_interp1<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+      k_interp1<T><<<(unsigned)(Lp.nbox * nrt), 256, sm1, st>>>(
+          Lp.nth, Lp.nph, Lc.nph, Lc.K, TR, nrt, Lp.d_ch_ptr, Lp.d_ch_idx, Lp.d_ch_quad, Lc.d_th_src,
+          Lc.d_th_refl, (const T*)(f64 ? (void*)Lc.d_th_w64 : (void*)Lc.d_th_w32), Lc.d_ph_src,
+          (const T*)(f64 ? (void*)Lc.d_ph_w64 : (void*)Lc.d_ph_w32),
+          (const V*)(f64 ? (void*)Lc.d_shift64 : (void*)Lc.d_shift32), (const V*)Lc.d_out, (V*)Lp.d_out);
+      SMR_LAUNCH(c);
+      pend(c, st);
+      continue;
+    }
     // fused (shared-memory) version when a tile of parent rows fits
     int TR = std::max(1, std::min(Lp.nth, (256 * EMAX) / (Lp.nph * 4 * R)));
     size_t smf = (size_t)TR * Lc.nph * 4 * R * sizeof(V);
@@ -906,6 +1151,21 @@ static int far_impl(Ctx* c, int R, const double2* x, double2* y, bool accumulate
          ((double)Lp.nbox * Lp.K + 2.0 * Lc.nbox * Lc.K) * 4 * R_ * es + 4.0 * Lp.K * es,
          (double)Lc.nbox * Lp.nth * Lc.nph * 4 * R_ * 8.0 * 2 * (double)Lp.nph / Lc.nph * 4.0 / 4.0 +
              (double)Lc.nbox * Lc.K * 4 * R_ * 16.0 * (double)Lp.nth / Lc.nth);
+    if (R == 1) {
+      int JC = Lc.ant_JC[f64 ? 0 : 1];
+      int njc = (Lc.nph / 2 + JC - 1) / JC;
+      size_t sm1 = (size_t)Lc.ant_GR * 2 * JC * 4 * sizeof(V);
+      int thr = (Lc.ant_GR * 2 * JC * Part<T>::NT >= 2048) ? 256 : 128;
+      k_anterp1<T><<<(unsigned)(Lc.nbox * Lc.ant_nit * njc), thr, sm1, st>>>(
+          Lc.nth, Lc.nph, Lp.nth, Lp.nph, Lc.ant_TI, Lc.ant_nit, JC, njc, Lc.d_parent, Lc.d_quad, Lc.d_ant_lo,
+          Lc.ant_PM, Lc.d_ant_pjp, (const T*)(f64 ? (void*)Lc.d_ant_pw64 : (void*)Lc.d_ant_pw32),
+          (const T*)(f64 ? (void*)Lc.d_wthp64 : (void*)Lc.d_wthp32),
+          (const V*)(f64 ? (void*)Lc.d_shift64 : (void*)Lc.d_shift32), (const V*)Lp.d_in, Lc.ant_TM,
+          Lc.d_ant_ttp, (const T*)(f64 ? (void*)Lc.d_ant_tw64 : (void*)Lc.d_ant_tw32), (V*)Lc.d_in);
+      SMR_LAUNCH(c);
+      pend(c, st);
+      continue;
+    }
     int rows1 = Lc.nbox * Lp.nth;
     auto kap = (R == 1) ? k_anterp_phi<T, true> : k_anterp_phi<T, false>;
     kap<<<(unsigned)((rows1 + 7) / 8), 256, 0, st>>>(

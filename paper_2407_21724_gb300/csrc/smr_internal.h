@@ -93,11 +93,22 @@ struct Level {
   int* d_tiles = nullptr;                // non-empty 4x4 translation tiles (ty * ntile_x + tx)
   int ntile8_x = 0, ntile8_ne = 0;
   int* d_tiles8 = nullptr;               // non-empty 8x8 tiles (single right-hand side kernel)
-  int* d_ant_ptr = nullptr;              // [K+1] weighted adjoint CSR (rows = this grid)
-  int* d_ant_idx = nullptr;              // parent point index
-  double* d_ant_w64 = nullptr;
-  float* d_ant_w32 = nullptr;
-  long long ant_nnz = 0;
+  // fused single right-hand-side anterpolation into this level: child theta
+  // rows in nit tiles of TI, parent rows [lo, hi) per tile ([2][nit]), GR the
+  // widest range, JC the column chunk per precision (FP64, FP32)
+  int ant_TI = 0, ant_nit = 0, ant_GR = 0;
+  int ant_JC[2] = {0, 0};
+  int* d_ant_lo = nullptr;
+  // the transposed taps padded to fixed widths (multiples of 4, zero weights):
+  // phi by child column [nph][PM] (parent column, weight x dphi_p / dphi_c),
+  // theta by child row [nth][TM] (parent row | refl << 16, sign x weight / w_theta)
+  int ant_PM = 0, ant_TM = 0;
+  int* d_ant_pjp = nullptr;
+  double* d_ant_pw64 = nullptr;
+  float* d_ant_pw32 = nullptr;
+  int* d_ant_ttp = nullptr;
+  double* d_ant_tw64 = nullptr;
+  float* d_ant_tw32 = nullptr;
   // spectra (allocated for the current R and precision)
   void* d_out = nullptr;                 // active spectra (the last product's precision)
   void* d_in = nullptr;
