@@ -184,6 +184,10 @@ def clocks_stop(proc, f, path, dev):
     return dict(sm_mhz=statistics.median(sm), sm_max_mhz=mx, reasons=sorted(reasons), samples=len(sm))
 
 
+ALU_BOUND = ("near", "aggregate", "receive")
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
 def traffic_for(kernel):
     """DRAM bytes per launch of a kernel from the committed ncu summary, if
     it was taken on the current source of that kernel (else None)."""
@@ -384,12 +388,20 @@ def run_ours(a):
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
         if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     hbm = peaks.get("hbm_gbs", 6800.0)
-    ach = d["bytes"] / d["ms"] / 1e6
-    roofline = dict(kernel=top, bound="hbm", achieved=ach, peak=hbm, unit="GB/s", frac=ach / hbm,
-                    traffic=traffic_for(top), algorithmic_bytes_per_launch=d["bytes"],
-                    launch_ms=d["ms"], share_of_step=d["ms"] / tot,
-                    peak_source="measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks
-                    else "fallback 6800 GB/s")
+    if top.split(":")[0] in ALU_BOUND:
+        # dense per-particle contractions on the FP32 pipes: against the FP32
+        # CUDA-core peak (152 SMs x 128 lanes x 2 flop x 2.07 GHz)
+        ach = d["flops"] / d["ms"] / 1e9
+        roofline = dict(kernel=top, bound="alu", achieved=ach, peak=FP32_PEAK_TFLOPS, unit="TFLOP/s",
+                        frac=ach / FP32_PEAK_TFLOPS, peak_source="derived: 152 SMs x 128 FP32 lanes x 2 flop "
+                        "x 2070 MHz", hbm_GBps=d["bytes"] / d["ms"] / 1e6)
+    else:
+        ach = d["bytes"] / d["ms"] / 1e6
+        roofline = dict(kernel=top, bound="hbm", achieved=ach, peak=hbm, unit="GB/s", frac=ach / hbm,
+                        peak_source="measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks
+                        else "fallback 6800 GB/s")
+    roofline.update(traffic=traffic_for(top), algorithmic_bytes_per_launch=d["bytes"],
+                    algorithmic_flops_per_launch=d["flops"], launch_ms=d["ms"], share_of_step=d["ms"] / tot)
     breakdown = {k: dict(ms=round(v["ms"], 4), share=round(v["ms"] / tot, 4), launches=round(v["launches"]),
                          GBps=round(v["bytes"] / v["ms"] / 1e6, 1),
                          TFLOPs=round(v["flops"] / v["ms"] / 1e9, 2)) for k, v in names.items()}
@@ -473,8 +485,8 @@ def run_ours(a):
                     fp64_matvecs_per_s=1e3 / ms64, fp64_ms_per_matvec=ms64,
                     ms_per_step_without_graph=ms_direct / R,
                     gmres=gm, setup_s=setup_s,
-                    e2e=dict(value=1.0 / e2e_s, unit="matvecs/s", h2d_bytes_per_step=16 * n,
-                             d2h_bytes_per_step=16 * n),
+                    e2e=dict(value=1.0 / e2e_s, unit="matvecs/s", h2d_bytes_per_step=16 * n * R,
+                             d2h_bytes_per_step=16 * n * R),
                     gpu_launches=launches * a.steps, roofline=roofline, kernels=breakdown,
                     launches_ms={k: round(v["ms"], 4) for k, v in launch.items()},
                     clocks=clocks, cpu_baseline=cpu)
