@@ -163,6 +163,22 @@ int smr_matvec_parts(smr_ctx* ctx, int R, const void* x, void* y_near, void* y_f
 int smr_matvec_host(smr_ctx* ctx, int R, const double* x, double* y, int precision,
                     void* stream);
 
+/* Selects where the FP32 product runs its receive step (Eqs. 24-25) for one
+ * right-hand side: 1 (default) on the tensor cores (tcgen05, split TF32: each
+ * FP32 operand as a sum of two TF32 values, three MMAs per step, FP32
+ * accumulation), 0 on the FP32 CUDA cores.  The paper has no counterpart
+ * (it ran on a CPU); both give the FP32 product to FP32 accuracy.  The
+ * tensor-core path needs 4 n_psi <= 128 and particles centred on their
+ * lattice sites; otherwise the CUDA-core path runs.  Drops captured products
+ * (smr_matvec_graph) so the next call captures the new choice. */
+int smr_set_tensor_cores(smr_ctx* ctx, int enable);
+
+/* Synchronises `stream` and reports errors found on the device since the
+ * last check: SMR_E_CUDA if a tensor-core pipeline wait ran out (that
+ * product's result is invalid; the kernel stopped, freed its tensor memory
+ * and returned).  smr_matvec_host and smr_solve make this check themselves. */
+int smr_sync(smr_ctx* ctx, void* stream);
+
 /* z = blockdiag(Z_s^-1) r over particles: the block-diagonal preconditioner
  * of Sec. V (each block the inverse of the particle's self block).
  * device r, z [N][R]; precision as in smr_matvec. */

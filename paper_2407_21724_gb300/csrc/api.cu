@@ -53,6 +53,8 @@ void free_scene(Ctx* c) {
   dfree(c->d_pc_col); dfree(c->d_pc_blk); dfree(c->d_tmp);
   dfree(c->d_arr);
   dfree(c->d_tile_shape); dfree(c->d_tile_start); dfree(c->d_tile_count); dfree(c->d_perm);
+  dfree(c->d_tc_rec); dfree(c->d_tc_perm); dfree(c->d_tc_shape); dfree(c->d_tc_start); dfree(c->d_tc_count);
+  c->tc_ready = false;
   for (int q = 0; q < 2; ++q) {
     if (c->G_buf[q]) cudaFree(c->G_buf[q]);
     c->G_buf[q] = nullptr;
@@ -578,7 +580,7 @@ int set_scene(Ctx* c, int p, const double* centres, const int* shape_ids, const 
       (rc = upload(c, &c->d_pc_blk, pcb)))
     return rc;
   if ((rc = build_modes(c)) || (rc = build_patterns(c)) || (rc = build_translations(c)) ||
-      (rc = build_near(c)))
+      (rc = build_near(c)) || (rc = build_tc(c)))
     return rc;
   SMR_CUDA(c, cudaDeviceSynchronize());
   c->have_scene = true;
@@ -655,6 +657,7 @@ int smr_destroy(smr_ctx* h) {
   cudaSetDevice(h->c.device);
   free_scene(&h->c);
   nn_free(&h->c);
+  if (h->c.d_tc_err) cudaFree(h->c.d_tc_err);
   if (h->c.d_red) cudaFree(h->c.d_red);
   if (h->c.h_red) cudaFreeHost(h->c.h_red);
   delete h;
@@ -800,7 +803,7 @@ int smr_matvec_host(smr_ctx* h, int R, const double* x, double* y, int precision
   if (rc) return rc;
   SMR_CUDA(c, cudaMemcpyAsync(y, dy, n * sizeof(double2), cudaMemcpyDeviceToHost, st));
   SMR_CUDA(c, cudaStreamSynchronize(st));
-  return SMR_OK;
+  return tc_check(c);
 }
 
 int smr_precond(smr_ctx* h, int R, const void* r, void* z, int precision, void* stream) {
@@ -822,7 +825,26 @@ int smr_solve(smr_ctx* h, int R, const void* b, void* x, const smr_solve_opts* o
     return fail(c, SMR_E_INVALID_ARG, "precision must be SMR_PREC_FP64 or SMR_PREC_FP32");
   if (o.precond != SMR_PRECOND_NONE && o.precond != SMR_PRECOND_BLOCKDIAG)
     return fail(c, SMR_E_INVALID_ARG, "unknown preconditioner");
-  return solve(c, R, (const double2*)b, (double2*)x, &o, stats, (cudaStream_t)stream);
+  int rc = solve(c, R, (const double2*)b, (double2*)x, &o, stats, (cudaStream_t)stream);
+  int rt = tc_check(c);
+  return rc ? rc : rt;
+}
+
+int smr_set_tensor_cores(smr_ctx* h, int enable) {
+  if (!h) return SMR_E_INVALID_ARG;
+  Ctx* c = &h->c;
+  cudaSetDevice(c->device);
+  c->tc_enable = enable != 0;
+  free_graphs(c);                              // captured products used the old setting
+  return SMR_OK;
+}
+
+int smr_sync(smr_ctx* h, void* stream) {
+  if (!h) return SMR_E_INVALID_ARG;
+  Ctx* c = &h->c;
+  cudaSetDevice(c->device);
+  SMR_CUDA(c, cudaStreamSynchronize((cudaStream_t)stream));
+  return tc_check(c);
 }
 
 int smr_far_field(smr_ctx* h, int R, const void* x, int n_dir, const double* dirs, void* F, void* stream) {

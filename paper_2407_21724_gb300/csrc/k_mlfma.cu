@@ -1190,6 +1190,11 @@ static int far_impl(Ctx* c, int R, const double2* x, double2* y, bool accumulate
          (double)c->p * L0.K * 4 * R_ * es + (double)c->S * c->npsi * 2 * L0.K * es +
              (accumulate ? 2.0 : 1.0) * c->p * 2 * c->npsi * R_ * 16,
          48.0 * c->p * c->npsi * L0.K * R_);
+    if (!f64 && tc_receive_ok(c, R)) {
+      int rc = run_receive_tc(c, (const float2*)L0.d_in, y, accumulate, st);
+      pend(c, st);
+      return rc;
+    }
     int nsub = (16 + std::max(1, 16 / RC) - 1) / std::max(1, 16 / RC);
     cudaFuncSetAttribute(k_receive<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     k_receive<T><<<(unsigned)(c->ntile * nsub * nrc), thr, sm, st>>>(

@@ -217,6 +217,15 @@ struct Ctx {
   double* d_red = nullptr;              // reduction partials
   size_t red_bytes = 0;
   double* h_red = nullptr;              // pinned host mirror
+  // tensor-core receive (FP32 product, one right-hand side)
+  bool tc_enable = true, tc_ready = false;
+  int tc_nK = 0, tc_ntile = 0;
+  float* d_tc_rec = nullptr;              // [S][nK][hi | lo][128][32] swizzled coefficient images
+  int* d_tc_perm = nullptr;
+  int* d_tc_shape = nullptr;
+  int* d_tc_start = nullptr;
+  int* d_tc_count = nullptr;
+  int* d_tc_err = nullptr;                // set when a pipeline wait runs out
 };
 
 // ------------------------------------------------------------------ helpers
@@ -296,6 +305,11 @@ int run_precond(Ctx* c, int R, int prec, const double2* r, double2* z, cudaStrea
 // y = Z x through a CUDA graph captured on first use for (x, y, R, prec)
 int run_matvec_graph(Ctx* c, int R, int prec, const double2* x, double2* y, cudaStream_t st);
 void free_graphs(Ctx* c);
+// tensor-core receive (k_tc.cu)
+int build_tc(Ctx* c);
+bool tc_receive_ok(const Ctx* c, int R);
+int run_receive_tc(Ctx* c, const float2* in0, double2* y, bool accumulate, cudaStream_t st);
+int tc_check(Ctx* c);
 
 // ------------------------------------------------------------------ linear algebra (k_linalg.cu)
 // h[j*R + r] = sum_i conj(V_j[i][r]) w[i][r] for j < J (V_j = V + j*ldv), FP64.

@@ -100,6 +100,8 @@ _SIGS = {
     "smr_copy_translation": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _D]),
     "smr_copy_near_block": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_int, _D]),
     "smr_copy_level": (C.c_int, [_P, C.c_int, C.c_int, _D, C.c_size_t]),
+    "smr_set_tensor_cores": (C.c_int, [_P, C.c_int]),
+    "smr_sync": (C.c_int, [_P, _P]),
 }
 
 
@@ -305,6 +307,14 @@ def smr_solve(ctx, b, x, R=None, stream=None, **kw):
                     outer=st.outer, reorth=st.reorth, resid_true=st.resid_true, seconds=st.seconds,
                     seconds_product=st.seconds_product, seconds_precond=st.seconds_precond,
                     seconds_orth=st.seconds_orth)
+
+
+def smr_set_tensor_cores(ctx, enable):
+    _check(ctx, lib().smr_set_tensor_cores(ctx, 1 if enable else 0))
+
+
+def smr_sync(ctx, stream=None):
+    _check(ctx, lib().smr_sync(ctx, _stream(stream, None)))
 
 
 def smr_far_field(ctx, x, dirs, F, R=None, stream=None):

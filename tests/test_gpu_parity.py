@@ -151,6 +151,22 @@ def test_matvec_fp32(c1, rnd):
         assert err < 2e-5
 
 
+
+def test_tensor_core_receive(c1, rnd):
+    """The FP32 product with its receive step on the tensor cores (split TF32)
+    matches the CUDA-core FP32 product to FP32 accuracy and the oracle to the
+    FP32 bar, on 24- and 32-mode scenes; no pipeline wait ran out."""
+    for case, seed in ((c1, 31), (rnd, 32)):
+        x = crandn(case.info["n_unknowns"], seed)
+        ref = case.M.matvec(x)
+        smr.smr_set_tensor_cores(case.ctx, False)
+        y0 = case.gpu_matvec(x, smr.SMR_PREC_FP32)
+        smr.smr_set_tensor_cores(case.ctx, True)
+        y1 = case.gpu_matvec(x, smr.SMR_PREC_FP32)
+        smr.smr_sync(case.ctx)
+        assert rel(y1, ref) < 2e-5, rel(y1, ref)
+        assert rel(y1, y0) < 5e-6, rel(y1, y0)
+
 @pytest.mark.parametrize("R", [5, 17, 64])
 def test_batched_columns_match_single(rnd, R):
     """R right-hand sides in one product: every column equals the single
