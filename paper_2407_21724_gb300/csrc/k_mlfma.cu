@@ -591,18 +591,22 @@ __global__ void k_translate(int K, int R, int RC, int KC, int ntx, int ntile, co
   }
 }
 
-// Single right-hand side: each thread owns the 2x2 targets that share one
-// parent, for one direction, and walks the parent's 6x6 source window once;
-// a source spectrum is read from shared memory once for all four targets.
-// CTA = 4x4 targets (2x2 parents) x KC directions; 4 x KC threads.
+// Single right-hand side: each thread owns one 16-byte part of the 2x2
+// targets that share one parent, for one direction, and walks the parent's
+// 6x6 source window once; a staged source part is read from shared memory
+// once for all four targets (conflict-free: lanes read consecutive 16-byte
+// parts).  CTA = 8x8 targets (4x4 parents) x KC directions; 16 x KC x NT threads.
 template <typename T>
-__global__ void __launch_bounds__(256) k_translate1(int K, int KC, int ntx, int ntile,
+__global__ void __launch_bounds__(512) k_translate1(int K, int KC, int ntx, int ntile,
                                                     const int* __restrict__ tiles, int map_x0, int map_y0,
                                                     int map_w, int map_h, const int* __restrict__ boxmap,
                                                     const typename CV<T>::V* __restrict__ Tg,
                                                     const typename CV<T>::V* __restrict__ out,
                                                     typename CV<T>::V* __restrict__ in) {
   typedef typename CV<T>::V V;
+  typedef Part<T> P;
+  typedef typename P::H H;
+  constexpr int NT = P::NT;
   constexpr int TS = 8, HS = TS + 4;                  // targets per side, halo per side
   extern __shared__ __align__(16) unsigned char smem_raw[];
   int tile = tiles[blockIdx.x % ntile];
@@ -645,7 +649,8 @@ __global__ void __launch_bounds__(256) k_translate1(int K, int KC, int ntx, int 
   }
   cp_async_wait_all();
   __syncthreads();
-  int kl = threadIdx.x % KC, par = threadIdx.x / KC;   // parent 0..15 of the tile
+  const int h = threadIdx.x % NT;
+  const int kl = (threadIdx.x / NT) % KC, par = threadIdx.x / (NT * KC);   // parent 0..15 of the tile
   if (kl >= nk || par >= (TS / 2) * (TS / 2)) return;
   int pxo = (par % (TS / 2)) * 2, pyo = (par / (TS / 2)) * 2;
   bool any = false;
@@ -654,28 +659,21 @@ __global__ void __launch_bounds__(256) k_translate1(int K, int KC, int ntx, int 
   if (!any) return;
   const V* Sp = S + (size_t)(pyo * HS + pxo) * W + kl * 4;   // window origin
   const V* Tp = Ts + kl;
-  V acc[4][4];
+  H acc[4];
 #pragma unroll
-  for (int q = 0; q < 4; ++q)
-#pragma unroll
-    for (int f = 0; f < 4; ++f) acc[q][f] = czero<V>();
+  for (int q = 0; q < 4; ++q) acc[q] = P::zero();
   // the parent's 6x6 source window; target q = (q & 1, q >> 1) inside the
   // parent; offset (dx, dy) = target - source is known at compile time
 #pragma unroll
   for (int wy = 0; wy < 6; ++wy) {
 #pragma unroll
     for (int wx = 0; wx < 6; ++wx) {
-      V v[4];
-      load4(Sp + (wy * HS + wx) * W, v);
+      H v = reinterpret_cast<const H*>(Sp + (wy * HS + wx) * W)[h];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int dx = (q & 1) + 2 - wx, dy = (q >> 1) + 2 - wy;
         if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1) continue;
-        V tv = Tp[((dx + 3) * 7 + (dy + 3)) * KC];
-        cfma(acc[q][0], tv, v[0]);
-        cfma(acc[q][1], tv, v[1]);
-        cfma(acc[q][2], tv, v[2]);
-        cfma(acc[q][3], tv, v[3]);
+        P::cfma(acc[q], Tp[((dx + 3) * 7 + (dy + 3)) * KC], v);
       }
     }
   }
@@ -683,8 +681,7 @@ __global__ void __launch_bounds__(256) k_translate1(int K, int KC, int ntx, int 
   for (int q = 0; q < 4; ++q) {
     int b = tb[(pyo + (q >> 1)) * TS + (pxo + (q & 1))];
     if (b < 0) continue;
-    V* o = in + ((size_t)b * K + k0 + kl) * 4;
-    o[0] = acc[q][0]; o[1] = acc[q][1]; o[2] = acc[q][2]; o[3] = acc[q][3];
+    stp<T>(in, (size_t)b * K + k0 + kl, h, acc[q]);
   }
 }
 
@@ -1132,7 +1129,7 @@ static int far_impl(Ctx* c, int R, const double2* x, double2* y, bool accumulate
       int KC1 = f64 ? 8 : 16;
       int nk1 = (L.K + KC1 - 1) / KC1;
       size_t sm1 = ((size_t)144 * KC1 * 4 + (size_t)49 * KC1) * sizeof(V) + (144 + 64) * sizeof(int);
-      k_translate1<T><<<(unsigned)(L.ntile8_ne * nk1), 16 * KC1, sm1, st>>>(
+      k_translate1<T><<<(unsigned)(L.ntile8_ne * nk1), 16 * KC1 * Part<T>::NT, sm1, st>>>(
           L.K, KC1, L.ntile8_x, L.ntile8_ne, L.d_tiles8, L.map_x0, L.map_y0, L.map_w, L.map_h, L.d_boxmap,
           (const V*)(f64 ? (void*)L.d_T64 : (void*)L.d_T32), (const V*)L.d_out, (V*)L.d_in);
     } else {
