@@ -53,8 +53,9 @@ void free_scene(Ctx* c) {
   dfree(c->d_pc_col); dfree(c->d_pc_blk); dfree(c->d_tmp);
   dfree(c->d_arr);
   dfree(c->d_tile_shape); dfree(c->d_tile_start); dfree(c->d_tile_count); dfree(c->d_perm);
-  dfree(c->d_tc_rec); dfree(c->d_tc_perm); dfree(c->d_tc_shape); dfree(c->d_tc_start); dfree(c->d_tc_count);
+  dfree(c->d_tc_rec); dfree(c->d_tc_agg); dfree(c->d_tc_perm); dfree(c->d_tc_shape); dfree(c->d_tc_start); dfree(c->d_tc_count);
   c->tc_ready = false;
+  c->tc_agg_ready = false;
   for (int q = 0; q < 2; ++q) {
     if (c->G_buf[q]) cudaFree(c->G_buf[q]);
     c->G_buf[q] = nullptr;

@@ -1044,6 +1044,11 @@ static int far_impl(Ctx* c, int R, const double2* x, double2* y, bool accumulate
          (double)c->p * 2 * c->npsi * R_ * 16 + (double)c->S * c->npsi * 2 * L0.K * es +
              (double)c->p * L0.K * 4 * R_ * es,
          32.0 * c->npsi * c->p * L0.K * R_);
+    if (!f64 && tc_aggregate_ok(c, R)) {
+      int rc = run_aggregate_tc(c, x, (float2*)L0.d_out, st);
+      pend(c, st);
+      if (rc) return rc;
+    } else {
     int nsub = (16 + std::max(1, 16 / RC) - 1) / std::max(1, 16 / RC);
     k_aggregate<T><<<(unsigned)(c->ntile * nsub * nkc * nrc), 256, sm, st>>>(
         L0.K, c->npsi, R, RC, nkc, c->d_tile_shape, c->d_tile_start, c->d_tile_count, c->d_perm, x,
@@ -1051,6 +1056,7 @@ static int far_impl(Ctx* c, int R, const double2* x, double2* y, bool accumulate
         c->k, (V*)L0.d_out);
     SMR_LAUNCH(c);
     pend(c, st);
+    }
   }
   // upward: separable interpolation, theta then phi (+ shift + child sum)
   for (int s = 0; s + 1 < c->nlev; ++s) {

@@ -241,10 +241,11 @@ __global__ void __launch_bounds__(288, 1) k_receive_tc(int nK, int K8, int M4, c
             *abort_flag = 1;
           } else {
             st_chunk(sm + st * TC_STAGE, tid, r[b]);
-            if (c + TC_PF < nK) ld_chunk(in0, K8, mus, c + TC_PF, tid, r[b]);
             fence_async_smem();
             __syncwarp();
             if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(fullB(st)) : "memory");
+            // the next loads go out after the fence, so it does not wait for them
+            if (c + TC_PF < nK) ld_chunk(in0, K8, mus, c + TC_PF, tid, r[b]);
           }
         }
       }
@@ -328,6 +329,211 @@ __global__ void __launch_bounds__(288, 1) k_receive_tc(int nK, int K8, int M4, c
   }
 }
 
+// Aggregation on the tensor cores (Eq. 26 patterns times coefficients):
+//   out0[mu][(direction, field, re/im)] = sum_k' A_s[.][k'] x[mu][k'],
+//   k' = (current, mode, re/im) (4 N_psi <= 128: the coefficients of mu).
+// A field belongs to one current, so the rows are taken current by current:
+// M tile t covers current t & 1 and the rows (direction, component, re/im)
+// [128 (t >> 1), 128 (t >> 1) + 128) of it, and reads only that current's
+// K chunks (half of K).  Consecutive tiles write the two halves of the same
+// output sectors.
+// CTA = up to 128 particles of one shape, 288 threads.  The 8 producer
+// warps load the tile's coefficients once (FP64 -> split TF32, swizzled,
+// resident for the whole CTA) and then drain the accumulators; one control
+// thread streams the coefficient images of the M tiles through a bulk-copy
+// ring and issues the MMAs into two alternating tensor-memory accumulators,
+// so the epilogue of one M tile overlaps the MMAs of the next.
+constexpr int AG_NS = 3;                       // coefficient-image stages
+constexpr int AG_KCMAX = 4;                    // K chunks (K' <= 128)
+constexpr size_t AG_SMEM = (size_t)2 * AG_KCMAX * TC_BBYTES + (size_t)AG_NS * 2 * TC_ABYTES + 1024 + 1024;
+
+__global__ void __launch_bounds__(288, 1) k_aggregate_tc(int nMT, int nKc, int K4, int npsi2,
+                                                         const int* __restrict__ tshape,
+                                                         const int* __restrict__ tstart,
+                                                         const int* __restrict__ tcount,
+                                                         const int* __restrict__ perm, const float* __restrict__ A,
+                                                         const double* __restrict__ x, float* __restrict__ out0,
+                                                         int* __restrict__ err) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* sm = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  float* Bh = reinterpret_cast<float*>(sm);                               // [current][nKc][128][32]
+  float* Bl = reinterpret_cast<float*>(sm + AG_KCMAX * TC_BBYTES);
+  unsigned char* Ar = sm + 2 * AG_KCMAX * TC_BBYTES;                      // [AG_NS][hi | lo]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(Ar + AG_NS * 2 * TC_ABYTES);
+  // aFull[NS], aDone[NS], accFull[2], accEmpty[2]
+  uint32_t* slot = reinterpret_cast<uint32_t*>(bars + 2 * AG_NS + 4);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(slot + 1);
+  int* mus = reinterpret_cast<int*>(slot + 4);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tile = blockIdx.x;
+  const int s = tshape[tile], t0 = tstart[tile], cnt = tcount[tile];
+  const uint32_t sm0 = saddr(sm), ar0 = saddr(Ar);
+  auto aFull = [&](int st) { return saddr(bars + st); };
+  auto aDone = [&](int st) { return saddr(bars + AG_NS + st); };
+  auto accFull = [&](int b) { return saddr(bars + 2 * AG_NS + b); };
+  auto accEmpty = [&](int b) { return saddr(bars + 2 * AG_NS + 2 + b); };
+  const size_t tileA = (size_t)nKc * 2 * 128 * TC_KC;                   // floats per M tile image
+  const float* As = A + (size_t)s * nMT * tileA;
+  if (warp == 0) tmem_alloc(saddr(slot), 2 * TC_NP);
+  if (tid == 0) {
+    for (int i = 0; i < AG_NS; ++i) {
+      mbar_init(aFull(i), 1);
+      mbar_init(aDone(i), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(accFull(b), 1);
+      mbar_init(accEmpty(b), 8);
+    }
+    *abort_flag = 0;
+    mbar_fence_init();
+  }
+  if (tid < TC_NP) mus[tid] = tid < cnt ? perm[t0 + tid] : -1;
+  tc_before();
+  __syncthreads();
+  tc_after();
+  const uint32_t tmem = *slot;
+  const int total = nMT * nKc;                        // coefficient chunks in order (M tile, K chunk)
+  if (tid == 288 - 32) {
+    // control thread: first coefficient chunks while the producers load x
+    for (int g = 0; g < AG_NS - 1 && g < total; ++g) {
+      const int t = g / nKc, c = g % nKc, st = g % AG_NS;
+      mbar_expect_tx(aFull(st), 2 * TC_ABYTES);
+      bulk_g2s(ar0 + st * 2 * TC_ABYTES, As + t * tileA + (size_t)c * 2 * 128 * TC_KC, 2 * TC_ABYTES, aFull(st));
+    }
+  }
+  if (warp < 8) {
+    // the tile's coefficients: row = particle; item = 4 consecutive values of
+    // one current's (mode, re/im) run, padded to nKc chunks of 32
+    const int per_cur = nKc * 8;                     // items per current and row
+    const int ngrp = 128 * 2 * per_cur;
+    const int Kx = 2 * npsi2;
+    for (int g = tid; g < ngrp; g += 256) {
+      const int row = g / (2 * per_cur), rem = g - row * (2 * per_cur);
+      const int cur = rem / per_cur, q4 = rem - cur * per_cur;
+      const int mu = mus[row], kl = 4 * q4;
+      double v[4] = {0.0, 0.0, 0.0, 0.0};
+      if (mu >= 0) {
+        const double* xr = x + (size_t)mu * Kx + cur * npsi2;
+        if (kl + 3 < npsi2) {
+          double2 a = *reinterpret_cast<const double2*>(xr + kl), b = *reinterpret_cast<const double2*>(xr + kl + 2);
+          v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+        } else {
+          for (int e = 0; e < 4; ++e)
+            if (kl + e < npsi2) v[e] = xr[kl + e];
+        }
+      }
+      float4 h, l;
+      h.x = tf32r((float)v[0]); l.x = tf32r((float)(v[0] - (double)h.x));
+      h.y = tf32r((float)v[1]); l.y = tf32r((float)(v[1] - (double)h.y));
+      h.z = tf32r((float)v[2]); l.z = tf32r((float)(v[2] - (double)h.z));
+      h.w = tf32r((float)v[3]); l.w = tf32r((float)(v[3] - (double)h.w));
+      const int c = cur * nKc + (q4 >> 3), q = q4 & 7;
+      const int off = (c * 128 + row) * 32 + ((q ^ (row & 7)) << 2);
+      *reinterpret_cast<float4*>(Bh + off) = h;
+      *reinterpret_cast<float4*>(Bl + off) = l;
+    }
+    fence_async_smem();
+  }
+  __syncthreads();
+  bool bad = false;
+  if (warp < 8) {
+    // ---- epilogue warps: drain the accumulator of each M tile
+    const int q4 = warp & 3, half = warp >> 2;
+    for (int t = 0; t < nMT && !bad; ++t) {
+      const int b = t & 1;
+      bool ok = false;
+      if (lane == 0) {
+        for (uint32_t i = 0; i < TC_SPIN && !ok; ++i) {
+          ok = mbar_test(accFull(b), (t >> 1) & 1);
+          if (!ok && *abort_flag) break;
+        }
+      }
+      ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+      if (!ok) {
+        bad = true;
+        *abort_flag = 1;
+        break;
+      }
+      tc_after();
+      const int rc = (t >> 1) * 128 + q4 * 32 + lane;   // (direction, component, re/im) of current t & 1
+      const int oi = (rc >> 2) * 8 + (t & 1) * 4 + (rc & 3);
+#pragma unroll 1
+      for (int g = half * 2; g < half * 2 + 2; ++g) {
+        if (g * 32 >= cnt) break;                      // uniform per warp
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(b * TC_NP + g * 32), v);
+        if (rc < K4) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            int col = g * 32 + j;
+            if (col < cnt) out0[(size_t)mus[col] * (2 * K4) + oi] = v[j];
+          }
+        }
+      }
+      tc_before();
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(accEmpty(b)) : "memory");
+    }
+  } else if (lane == 0) {
+    // ---- control thread
+    const uint32_t idesc = idesc_tf32(128, TC_NP);
+    const uint32_t bh0 = sm0, bl0 = sm0 + AG_KCMAX * TC_BBYTES;
+    int g = 0;
+    for (int t = 0; t < nMT && !bad; ++t) {
+      const int b = t & 1;
+      if (t >= 2 && !mbar_wait(accEmpty(b), ((t >> 1) - 1) & 1)) { bad = true; break; }
+      tc_after();
+      const uint32_t d = tmem + (uint32_t)(b * TC_NP);
+      for (int c = 0; c < nKc; ++c, ++g) {
+        const int st = g % AG_NS;
+        bool ok = false;
+        for (uint32_t i = 0; i < TC_SPIN && !ok; ++i) {
+          ok = mbar_test(aFull(st), (g / AG_NS) & 1);
+          if (!ok && *abort_flag) break;
+        }
+        if (!ok) { bad = true; break; }
+        tc_after();
+        const uint32_t Sa = ar0 + st * 2 * TC_ABYTES;
+#pragma unroll
+        for (int k = 0; k < TC_KC / 8; ++k) {
+          uint64_t ah = sdesc_sw128(Sa + 32 * k), al = sdesc_sw128(Sa + TC_ABYTES + 32 * k);
+          const int cb = (t & 1) * nKc + c;            // this current's K chunk of the coefficients
+          uint64_t bh = sdesc_sw128(bh0 + cb * TC_BBYTES + 32 * k), bl = sdesc_sw128(bl0 + cb * TC_BBYTES + 32 * k);
+          mma_tf32(d, ah, bh, idesc, (c > 0 || k > 0) ? 1u : 0u);
+          mma_tf32(d, ah, bl, idesc, 1u);
+          mma_tf32(d, al, bh, idesc, 1u);
+        }
+        mma_commit(aDone(st));
+        // next coefficient chunk into the stage of chunk g - 1 once its MMAs are done
+        const int gn = g + AG_NS - 1;
+        if (gn < total) {
+          if (g >= 1 && !mbar_wait(aDone((g - 1) % AG_NS), ((g - 1) / AG_NS) & 1)) { bad = true; break; }
+          const int tn = gn / nKc, cn = gn % nKc, sn = gn % AG_NS;
+          mbar_expect_tx(aFull(sn), 2 * TC_ABYTES);
+          bulk_g2s(ar0 + sn * 2 * TC_ABYTES, As + tn * tileA + (size_t)cn * 2 * 128 * TC_KC, 2 * TC_ABYTES,
+                   aFull(sn));
+        }
+      }
+      if (bad) break;
+      mma_commit(accFull(b));
+    }
+    // every MMA is complete once the last M tile's accumulator is full (or on failure, the last chunk)
+    if (!bad && nMT > 0 && !mbar_wait(accFull((nMT - 1) & 1), ((nMT - 1) >> 1) & 1)) bad = true;
+    if (bad) {
+      *abort_flag = 1;
+      if (g > 0) mbar_wait(aDone((g - 1) % AG_NS), ((g - 1) / AG_NS) & 1);
+    }
+  }
+  bad = __syncthreads_or(bad) != 0;
+  if (bad && tid == 0) atomicExch(err, 1);
+  tc_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_after();
+    tmem_dealloc(tmem, 2 * TC_NP);
+  }
+}
+
 // TF32 rounding on the host (round to nearest, ties away), for the split
 float tf32_host(float x) {
   uint32_t u;
@@ -350,7 +556,7 @@ int build_tc(Ctx* c) {
   Level& L0 = c->lev[0];
   int npsi = c->npsi, K0 = L0.K, S = c->S;
   int M4 = 4 * npsi, K8 = 8 * K0;
-  if (M4 > 128) return SMR_OK;                       // more than one M tile: CUDA-core receive
+  if (M4 > 128) return SMR_OK;                       // more than one M tile: CUDA-core paths
   int nK = (K8 + TC_KC - 1) / TC_KC;
   size_t nP = (size_t)S * npsi * 2 * K0;
   std::vector<double2> P(nP);
@@ -380,6 +586,35 @@ int build_tc(Ctx* c) {
         img[base + (size_t)128 * TC_KC + off] = lo;
       }
     }
+  // aggregation images: row m' = (direction, field, re/im), column k' =
+  // (current, mode, re/im); entry = the real form of conj(P(mode, field's
+  // component, direction)) where the field's current matches, else 0
+  int K4 = 4 * K0, npsi2 = 2 * npsi;
+  int nKc = (npsi2 + TC_KC - 1) / TC_KC, nMT = 2 * ((K4 + 127) / 128);
+  std::vector<float> agg;
+  if (2 * nKc <= AG_KCMAX && npsi % 2 == 0) {
+    size_t tileA = (size_t)nKc * 2 * 128 * TC_KC;
+    agg.assign((size_t)S * nMT * tileA, 0.f);
+    for (int s = 0; s < S; ++s)
+      for (int t = 0; t < nMT; ++t)
+        for (int rl = 0; rl < 128; ++rl) {
+          int rc = (t >> 1) * 128 + rl;
+          if (rc >= K4) break;
+          int k = rc / 4, comp = (rc / 2) & 1, ro = rc & 1;
+          for (int kl = 0; kl < npsi2; ++kl) {
+            int n = kl / 2, ri = kl & 1;
+            const double2 pv = P[(((size_t)s * npsi + n) * 2 + comp) * K0 + k];
+            double v = ro == 0 ? (ri == 0 ? pv.x : pv.y) : (ri == 0 ? -pv.y : pv.x);
+            float hi = tf32_host((float)v);
+            float lo = tf32_host((float)(v - (double)hi));
+            int ch = kl / TC_KC, kk = kl % TC_KC, q = kk >> 2, e = kk & 3;
+            size_t base = ((size_t)s * nMT + t) * tileA + (size_t)ch * 2 * 128 * TC_KC;
+            size_t off = (size_t)rl * TC_KC + (((q ^ (rl & 7)) << 2) | e);
+            agg[base + off] = hi;
+            agg[base + (size_t)128 * TC_KC + off] = lo;
+          }
+        }
+  }
   // tiles of up to 128 particles of one shape (particles sorted by shape)
   std::vector<int> perm(c->p), tsh, tst, tcn;
   for (int i = 0; i < c->p; ++i) perm[i] = i;
@@ -391,6 +626,13 @@ int build_tc(Ctx* c) {
     i = j;
   }
   int rc;
+  c->tc_agg_ready = false;
+  if (!agg.empty()) {
+    if ((rc = upload(c, &c->d_tc_agg, agg))) return rc;
+    c->tc_nMT = nMT;
+    c->tc_nKc = nKc;
+    c->tc_agg_ready = true;
+  }
   if ((rc = upload(c, &c->d_tc_rec, img)) || (rc = upload(c, &c->d_tc_perm, perm)) ||
       (rc = upload(c, &c->d_tc_shape, tsh)) || (rc = upload(c, &c->d_tc_start, tst)) ||
       (rc = upload(c, &c->d_tc_count, tcn)))
@@ -415,6 +657,19 @@ int run_receive_tc(Ctx* c, const float2* in0, double2* y, bool accumulate, cudaS
   return SMR_OK;
 }
 
+bool tc_aggregate_ok(const Ctx* c, int R) {
+  return c->tc_enable && c->tc_ready && c->tc_agg_ready && R == 1 && !c->any_dshift;
+}
+
+int run_aggregate_tc(Ctx* c, const double2* x, float2* out0, cudaStream_t st) {
+  cudaFuncSetAttribute(k_aggregate_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)AG_SMEM);
+  k_aggregate_tc<<<(unsigned)c->tc_ntile, 288, AG_SMEM, st>>>(
+      c->tc_nMT, c->tc_nKc, 4 * c->lev[0].K, 2 * c->npsi, c->d_tc_shape, c->d_tc_start, c->d_tc_count,
+      c->d_tc_perm, c->d_tc_agg, reinterpret_cast<const double*>(x), reinterpret_cast<float*>(out0), c->d_tc_err);
+  SMR_LAUNCH(c);
+  return SMR_OK;
+}
+
 // 0 = no failed wait seen since the last check (clears the flag)
 int tc_check(Ctx* c) {
   if (!c->d_tc_err) return SMR_OK;
@@ -422,7 +677,7 @@ int tc_check(Ctx* c) {
   SMR_CUDA(c, cudaMemcpy(&h, c->d_tc_err, sizeof(int), cudaMemcpyDeviceToHost));
   if (h) {
     cudaMemset(c->d_tc_err, 0, sizeof(int));
-    c->err = "tensor-core receive: a pipeline wait ran out (results of that product are invalid)";
+    c->err = "tensor-core product step: a pipeline wait ran out (results of that product are invalid)";
     return SMR_E_CUDA;
   }
   return SMR_OK;

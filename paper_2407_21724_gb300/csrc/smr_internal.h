@@ -217,7 +217,7 @@ struct Ctx {
   double* d_red = nullptr;              // reduction partials
   size_t red_bytes = 0;
   double* h_red = nullptr;              // pinned host mirror
-  // tensor-core receive (FP32 product, one right-hand side)
+  // tensor-core receive and aggregation (FP32 product, one right-hand side)
   bool tc_enable = true, tc_ready = false;
   int tc_nK = 0, tc_ntile = 0;
   float* d_tc_rec = nullptr;              // [S][nK][hi | lo][128][32] swizzled coefficient images
@@ -226,6 +226,9 @@ struct Ctx {
   int* d_tc_start = nullptr;
   int* d_tc_count = nullptr;
   int* d_tc_err = nullptr;                // set when a pipeline wait runs out
+  bool tc_agg_ready = false;
+  int tc_nMT = 0, tc_nKc = 0;
+  float* d_tc_agg = nullptr;              // [S][M tiles][K chunks][hi | lo][128][32] aggregation images
 };
 
 // ------------------------------------------------------------------ helpers
@@ -305,10 +308,12 @@ int run_precond(Ctx* c, int R, int prec, const double2* r, double2* z, cudaStrea
 // y = Z x through a CUDA graph captured on first use for (x, y, R, prec)
 int run_matvec_graph(Ctx* c, int R, int prec, const double2* x, double2* y, cudaStream_t st);
 void free_graphs(Ctx* c);
-// tensor-core receive (k_tc.cu)
+// tensor-core receive and aggregation (k_tc.cu)
 int build_tc(Ctx* c);
 bool tc_receive_ok(const Ctx* c, int R);
 int run_receive_tc(Ctx* c, const float2* in0, double2* y, bool accumulate, cudaStream_t st);
+bool tc_aggregate_ok(const Ctx* c, int R);
+int run_aggregate_tc(Ctx* c, const double2* x, float2* out0, cudaStream_t st);
 int tc_check(Ctx* c);
 
 // ------------------------------------------------------------------ linear algebra (k_linalg.cu)
