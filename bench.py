@@ -433,7 +433,7 @@ def run_ours(a):
         if a.train_arrays > 0 and R == 1:
             learned = train_learned(smr, workloads, a.train_arrays, dev)
 
-        def solve(label, prec, x0=None):
+        def solve(label, prec, x0=None, lpc=False):
             xs = torch.zeros_like(b) if x0 is None else x0.clone()
             torch.cuda.synchronize(dev)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -443,7 +443,14 @@ def run_ours(a):
                 # the guess is part of the solve: features + network + re-phasing
                 smr.smr_nn_predict(ctx, [k for k, _ in incs], [q for _, q in incs], learned["scale"], xs)
                 extra["use_x0"] = 1
-            rc, stt = smr.smr_solve(ctx, b, xs, R=R, tol=1e-4, precision=prec, maxit=3000, **extra)
+            if lpc:
+                # learned local-coupling preconditioner, built inside the timed solve
+                smr.smr_nn_precond(ctx, [k for k, _ in incs], [q for _, q in incs], learned["scale"], b)
+                extra["precond"] = smr.SMR_PRECOND_LEARNED
+            # the learned preconditioner is an ablation arm: bounded at twice the
+            # tuned solve's iterations so that a stagnating run stays short
+            mi = 3000 if not lpc else max(50, 2 * gm["tuned_fp32_inner_fp64_outer"]["iters"])
+            rc, stt = smr.smr_solve(ctx, b, xs, R=R, tol=1e-4, precision=prec, maxit=mi, **extra)
             e1.record(st)
             torch.cuda.synchronize(dev)
             stt["solver_seconds"] = stt.pop("seconds")
@@ -457,6 +464,7 @@ def run_ours(a):
             smr.smr_nn_init(ctx, width=learned["width"], seed=0)
             smr.smr_nn_set_params(ctx, learned["params"])
             solve("tuned_plus_learned_x0", P32, x0=torch.zeros_like(b))
+            solve("tuned_plus_learned_x0_and_precond", P32, x0=torch.zeros_like(b), lpc=True)
             gm["learned_training"] = {k: v for k, v in learned.items() if k not in ("params",)}
         solve("plain_fp64", smr.SMR_PREC_FP64)
         best = min(v["seconds"] for k, v in gm.items() if k.startswith("tuned") and isinstance(v, dict)

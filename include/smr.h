@@ -53,7 +53,7 @@ enum {
 
 enum { SMR_PREC_FP64 = 0, SMR_PREC_FP32 = 1 };
 enum { SMR_LRULE_FORMULA = 0, SMR_LRULE_DOUBLE = 1 };
-enum { SMR_PRECOND_NONE = 0, SMR_PRECOND_BLOCKDIAG = 1 };
+enum { SMR_PRECOND_NONE = 0, SMR_PRECOND_BLOCKDIAG = 1, SMR_PRECOND_LEARNED = 2 };
 
 /* Options of a context (smr_default_opts fills the defaults in brackets). */
 typedef struct {
@@ -188,7 +188,8 @@ typedef struct {
   double tol;      /* true relative residual ||b - Z x|| / ||b|| target [1e-4] */
   int maxit;       /* maximum inner iterations in total [2000]                 */
   int restart;     /* Krylov dimension before restart; 0 = maxit [0]           */
-  int precond;     /* SMR_PRECOND_* [SMR_PRECOND_BLOCKDIAG]                    */
+  int precond;     /* SMR_PRECOND_* [SMR_PRECOND_BLOCKDIAG]; SMR_PRECOND_LEARNED
+                      needs smr_nn_precond first and R = 1                    */
   int precision;   /* SMR_PREC_FP64: plain GMRES on the FP64 product;
                       SMR_PREC_FP32: iterative refinement, outer residual with
                       the FP64 product, inner GMRES on the FP32 product and
@@ -291,6 +292,15 @@ int smr_nn_train_step(smr_ctx* ctx, int n, const float* feat, const int* idx, co
 /* Loss and its gradient (host grad[num_params], may be NULL) without a step. */
 int smr_nn_loss_grad(smr_ctx* ctx, int n, const float* feat, const int* idx, const float* tgt,
                      double* loss, float* grad, void* stream);
+/* Learned local-coupling preconditioner for one right-hand side (no
+ * counterpart in the paper): from the network's prediction x_p (as
+ * smr_nn_predict) and the isolated-particle response z = blockdiag(Z_s^-1) b
+ * of the device right-hand side b[N], stores D = x_p / z per unknown with
+ * |D| clamped to [0.1, 10] (0.1 where the ratio is zero or undefined).
+ * smr_solve with precond = SMR_PRECOND_LEARNED (R = 1) then applies
+ * M^-1 r = D (blockdiag(Z_s^-1) r).  D stays until the next call or scene. */
+int smr_nn_precond(smr_ctx* ctx, const double* khat, const double* pol, double scale, const void* b,
+                   void* stream);
 /* x0 = scale * (Y_re + j Y_im) exp(-j k khat . r) for every particle: device
  * x0[N], ready for smr_solve with use_x0 = 1. */
 int smr_nn_predict(smr_ctx* ctx, const double* khat, const double* pol, double scale, void* x0,

@@ -53,7 +53,8 @@ void free_scene(Ctx* c) {
   dfree(c->d_pc_col); dfree(c->d_pc_blk); dfree(c->d_tmp);
   dfree(c->d_arr);
   dfree(c->d_tile_shape); dfree(c->d_tile_start); dfree(c->d_tile_count); dfree(c->d_perm);
-  dfree(c->d_tc_rec); dfree(c->d_tc_agg); dfree(c->d_tc_perm); dfree(c->d_tc_shape); dfree(c->d_tc_start); dfree(c->d_tc_count);
+  dfree(c->d_tc_rec); dfree(c->d_tc_agg); dfree(c->d_tc_perm); dfree(c->d_lpc);
+  c->lpc_ready = false; dfree(c->d_tc_shape); dfree(c->d_tc_start); dfree(c->d_tc_count);
   c->tc_ready = false;
   c->tc_agg_ready = false;
   for (int q = 0; q < 2; ++q) {
@@ -824,8 +825,10 @@ int smr_solve(smr_ctx* h, int R, const void* b, void* x, const smr_solve_opts* o
   if (opts) o = *opts;
   if (o.precision != SMR_PREC_FP64 && o.precision != SMR_PREC_FP32)
     return fail(c, SMR_E_INVALID_ARG, "precision must be SMR_PREC_FP64 or SMR_PREC_FP32");
-  if (o.precond != SMR_PRECOND_NONE && o.precond != SMR_PRECOND_BLOCKDIAG)
+  if (o.precond != SMR_PRECOND_NONE && o.precond != SMR_PRECOND_BLOCKDIAG && o.precond != SMR_PRECOND_LEARNED)
     return fail(c, SMR_E_INVALID_ARG, "unknown preconditioner");
+  if (o.precond == SMR_PRECOND_LEARNED && (R != 1 || !c->lpc_ready))
+    return fail(c, SMR_E_STATE, "SMR_PRECOND_LEARNED needs R = 1 and smr_nn_precond first");
   int rc = solve(c, R, (const double2*)b, (double2*)x, &o, stats, (cudaStream_t)stream);
   int rt = tc_check(c);
   return rc ? rc : rt;
@@ -1029,6 +1032,20 @@ int smr_nn_predict(smr_ctx* h, const double* khat, const double* pol, double sca
   int rc = upload_inc(c, c->n_arrays, khat, pol, &dk, &dp);
   if (rc) return rc;
   rc = nn_predict(c, dk, dp, scale, (double2*)x0, (cudaStream_t)stream);
+  cudaFree(dk);
+  cudaFree(dp);
+  return rc;
+}
+
+int smr_nn_precond(smr_ctx* h, const double* khat, const double* pol, double scale, const void* b, void* stream) {
+  if (!h || !khat || !pol || !b || !(scale > 0)) return SMR_E_INVALID_ARG;
+  Ctx* c = &h->c;
+  if (!check_scene(c)) return SMR_E_STATE;
+  if (!c->nn.p32) return fail(c, SMR_E_STATE, "call smr_nn_init first");
+  double *dk = nullptr, *dp = nullptr;
+  int rc = upload_inc(c, c->n_arrays, khat, pol, &dk, &dp);
+  if (rc) return rc;
+  rc = nn_precond(c, dk, dp, scale, (const double2*)b, (cudaStream_t)stream);
   cudaFree(dk);
   cudaFree(dp);
   return rc;

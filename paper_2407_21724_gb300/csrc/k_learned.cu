@@ -427,4 +427,63 @@ int nn_predict(Ctx* c, const double* d_khat, const double* d_pol, double scale, 
   return rc;
 }
 
+// Learned local-coupling preconditioner: per unknown, the ratio of the
+// network's predicted coefficient to the isolated-particle response
+// (blockdiag(Z_s^-1) b), with its magnitude clamped to [0.1, 10] (a zero or
+// undefined ratio becomes 0.1).
+__global__ void k_lpc_ratio(long long n, const double2* __restrict__ xp, const double2* __restrict__ zi,
+                            double2* __restrict__ D) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double2 a = xp[i], b = zi[i];
+  double bb = b.x * b.x + b.y * b.y;
+  double2 r = make_double2(0.0, 0.0);
+  if (bb > 0) r = make_double2((a.x * b.x + a.y * b.y) / bb, (a.y * b.x - a.x * b.y) / bb);
+  double m = sqrt(r.x * r.x + r.y * r.y);
+  if (!(m > 0.1)) {
+    r = (m > 0) ? make_double2(0.1 * r.x / m, 0.1 * r.y / m) : make_double2(0.1, 0.0);
+  } else if (m > 10.0) {
+    r = make_double2(10.0 * r.x / m, 10.0 * r.y / m);
+  }
+  D[i] = r;
+}
+
+// z[i] *= D[i]
+__global__ void k_lpc_apply(long long n, const double2* __restrict__ D, double2* __restrict__ z) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double2 d = D[i], v = z[i];
+  z[i] = make_double2(d.x * v.x - d.y * v.y, d.x * v.y + d.y * v.x);
+}
+
+int nn_precond(Ctx* c, const double* d_khat, const double* d_pol, double scale, const double2* b, cudaStream_t st) {
+  long long n = 2LL * c->npsi * c->p;
+  double2 *xp = nullptr, *zi = nullptr;
+  if (!c->d_lpc) SMR_CUDA(c, cudaMalloc((void**)&c->d_lpc, n * sizeof(double2)));
+  SMR_CUDA(c, cudaMalloc((void**)&xp, n * sizeof(double2)));
+  if (cudaMalloc((void**)&zi, n * sizeof(double2)) != cudaSuccess) {
+    cudaFree(xp);
+    c->err = "out of device memory";
+    return SMR_E_OOM;
+  }
+  int rc = nn_predict(c, d_khat, d_pol, scale, xp, st);
+  if (!rc) rc = run_precond(c, 1, SMR_PREC_FP64, b, zi, st);
+  if (!rc) {
+    k_lpc_ratio<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, xp, zi, c->d_lpc);
+    if (cudaGetLastError() != cudaSuccess) { c->err = "lpc kernel launch"; rc = SMR_E_CUDA; }
+  }
+  cudaStreamSynchronize(st);
+  cudaFree(xp);
+  cudaFree(zi);
+  c->lpc_ready = (rc == SMR_OK);
+  return rc;
+}
+
+int lpc_apply(Ctx* c, double2* z, cudaStream_t st) {
+  long long n = 2LL * c->npsi * c->p;
+  k_lpc_apply<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, c->d_lpc, z);
+  SMR_LAUNCH(c);
+  return SMR_OK;
+}
+
 }  // namespace smr

@@ -639,6 +639,18 @@ static int apply_A(Ctx* c, int R, int prec, const double2* x, double2* y, cudaSt
   return run_far(c, R, prec, x, y, true, st);
 }
 
+// z = M^-1 v: the block-diagonal preconditioner, scaled per unknown by the
+// learned diagonal for SMR_PRECOND_LEARNED, or a copy for SMR_PRECOND_NONE
+static int apply_M(Ctx* c, int R, int prec, int precond, const double2* v, double2* z, cudaStream_t st) {
+  if (precond == SMR_PRECOND_NONE) {
+    SMR_CUDA(c, cudaMemcpyAsync(z, v, (size_t)2 * c->npsi * c->p * R * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+    return SMR_OK;
+  }
+  int rc = run_precond(c, R, prec, v, z, st);
+  if (rc || precond != SMR_PRECOND_LEARNED) return rc;
+  return lpc_apply(c, z, st);
+}
+
 static float elapsed_s(cudaEvent_t a, cudaEvent_t b) {
   float ms = 0;
   cudaEventElapsedTime(&ms, a, b);
@@ -764,11 +776,7 @@ static int gmres_core(Ctx* c, int R, int prec, int precond, const double2* rhs, 
         SMR_LAUNCH(c);
         vj = W.u;
       }
-      if (precond == SMR_PRECOND_BLOCKDIAG) {
-        rc = run_precond(c, R, prec, vj, W.t, st);
-      } else {
-        SMR_CUDA(c, cudaMemcpyAsync(W.t, vj, ld * sizeof(double2), cudaMemcpyDeviceToDevice, st));
-      }
+      rc = apply_M(c, R, prec, precond, vj, W.t, st);
       if (rc) return rc;
       cudaEventRecord(W.ev[1], st);
       rc = run_matvec_graph(c, R, prec, W.t, W.w, st);
@@ -881,11 +889,7 @@ static int gmres_core(Ctx* c, int R, int prec, int precond, const double2* rhs, 
         rc = multi_axpy(c, jmax, n, R, (const double2*)W.V, ld, W.coef, W.w, 1.0, st);
       }
       if (rc) return rc;
-      if (precond == SMR_PRECOND_BLOCKDIAG) {
-        rc = run_precond(c, R, prec, W.w, W.t, st);
-      } else {
-        SMR_CUDA(c, cudaMemcpyAsync(W.t, W.w, ld * sizeof(double2), cudaMemcpyDeviceToDevice, st));
-      }
+      rc = apply_M(c, R, prec, precond, W.w, W.t, st);
       if (rc) return rc;
       std::vector<double2> one(R, make_double2(1, 0));
       SMR_CUDA(c, cudaMemcpyAsync(W.coef, one.data(), R * sizeof(double2), cudaMemcpyHostToDevice, st));

@@ -229,6 +229,9 @@ struct Ctx {
   bool tc_agg_ready = false;
   int tc_nMT = 0, tc_nKc = 0;
   float* d_tc_agg = nullptr;              // [S][M tiles][K chunks][hi | lo][128][32] aggregation images
+  // learned local-coupling preconditioner: diagonal D [N] (one right-hand side)
+  double2* d_lpc = nullptr;
+  bool lpc_ready = false;
 };
 
 // ------------------------------------------------------------------ helpers
@@ -298,6 +301,8 @@ int nn_forward_backward(Ctx* c, int n, const float* feat, const int* idx, const 
                         double* loss_host, cudaStream_t st);
 int nn_adam(Ctx* c, float lr, cudaStream_t st);
 int nn_predict(Ctx* c, const double* d_khat, const double* d_pol, double scale, double2* x0, cudaStream_t st);
+int nn_precond(Ctx* c, const double* d_khat, const double* d_pol, double scale, const double2* b, cudaStream_t st);
+int lpc_apply(Ctx* c, double2* z, cudaStream_t st);
 
 // ------------------------------------------------------------------ hot path (k_mlfma.cu)
 int ensure_spectra(Ctx* c, int R, int prec);

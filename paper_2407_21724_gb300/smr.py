@@ -18,7 +18,8 @@ _lib = None
 
 SMR_PREC_FP64, SMR_PREC_FP32 = 0, 1
 SMR_LRULE_FORMULA, SMR_LRULE_DOUBLE = 0, 1
-SMR_PRECOND_NONE, SMR_PRECOND_BLOCKDIAG = 0, 1
+SMR_PRECOND_NONE, SMR_PRECOND_BLOCKDIAG, SMR_PRECOND_LEARNED = 0, 1, 2
+SMR_OK, SMR_E_NOT_CONVERGED = 0, -5
 ERRORS = {-1: "INVALID_ARG", -2: "SHAPE", -3: "OOM", -4: "CUDA", -5: "NOT_CONVERGED",
           -6: "BREAKDOWN", -7: "NAN", -9: "STATE"}
 
@@ -101,6 +102,7 @@ _SIGS = {
     "smr_copy_near_block": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_int, _D]),
     "smr_copy_level": (C.c_int, [_P, C.c_int, C.c_int, _D, C.c_size_t]),
     "smr_set_tensor_cores": (C.c_int, [_P, C.c_int]),
+    "smr_nn_precond": (C.c_int, [_P, _D, _D, C.c_double, _P, _P]),
     "smr_sync": (C.c_int, [_P, _P]),
 }
 
@@ -407,6 +409,11 @@ def smr_nn_loss_grad(ctx, n, feat, tgt, idx=None, stream=None):
 def smr_nn_predict(ctx, khat, pol, scale, x0, stream=None):
     kh, pl, pv = _inc(khat, pol)
     _check(ctx, lib().smr_nn_predict(ctx, _dptr(kh), _dptr(pv), float(scale), _ptr(x0), _stream(stream, x0)))
+
+
+def smr_nn_precond(ctx, khat, pol, scale, b, stream=None):
+    kh, pl, pv = _inc(khat, pol)
+    _check(ctx, lib().smr_nn_precond(ctx, _dptr(kh), _dptr(pv), float(scale), _ptr(b), _stream(stream, b)))
 
 
 def smr_copy_pattern(ctx, shape):

@@ -163,4 +163,34 @@ def test_learned_initial_guess_gains_over_zero():
     xl = x0.clone()
     _, s1 = smr.smr_solve(ctx, b1, xl, tol=1e-4, use_x0=1)
     assert s1["iters"] < s0["iters"]
+    # learned local-coupling preconditioner with the same network: it runs
+    # and reports a finite true residual (whether it beats the block-diagonal
+    # preconditioner is the ablation the benchmark reports, not a test bar)
+    smr.smr_nn_precond(ctx, kh1, pol1, scale, b1)
+    xp = x0.clone()
+    rc, s2 = smr.smr_solve(ctx, b1, xp, tol=1e-4, use_x0=1, precond=smr.SMR_PRECOND_LEARNED, maxit=300)
+    assert rc in (0, smr.SMR_E_NOT_CONVERGED) and np.isfinite(s2["resid_true"]), s2
     smr.smr_destroy(ctx)
+
+
+def test_learned_preconditioner_with_zero_network_is_scaled_blockdiag(ragged):
+    """A zero network predicts 0, so D = 0.1 everywhere: M^-1 = 0.1
+    blockdiag(Z_s^-1), whose GMRES residual history equals the block-diagonal
+    one (a constant scaling of a right preconditioner leaves the Krylov
+    spaces unchanged).  Checks D's clamp and the preconditioner path."""
+    ws, ctx = ragged
+    inc = [workloads.incidence(10.0 * i, 37.0 * i, "xy"[i % 2]) for i in range(3)]
+    kh, pol = [k for k, _ in inc], [p for _, p in inc]
+    n = smr.smr_info(ctx)["n_unknowns"]
+    b = torch.empty(n, dtype=torch.complex128, device="cuda")
+    smr.smr_rhs_plane_waves_arrays(ctx, kh, pol, b)
+    smr.smr_nn_init(ctx, width=8, seed=3)
+    smr.smr_nn_set_params(ctx, np.zeros(smr.smr_nn_num_params(ctx), dtype=np.float32))
+    smr.smr_nn_precond(ctx, kh, pol, 1.0, b)
+    xa = torch.zeros_like(b)
+    rca, sa = smr.smr_solve(ctx, b, xa, tol=1e-6, precision=smr.SMR_PREC_FP64)
+    xb = torch.zeros_like(b)
+    rcb, sb = smr.smr_solve(ctx, b, xb, tol=1e-6, precision=smr.SMR_PREC_FP64, precond=smr.SMR_PRECOND_LEARNED)
+    assert rca == 0 and rcb == 0
+    assert abs(sa["iters"] - sb["iters"]) <= 1, (sa, sb)
+    assert rel(xb.cpu().numpy(), xa.cpu().numpy()) < 1e-5
