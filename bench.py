@@ -285,6 +285,19 @@ def focal_report(smr, ctx, x, w, dev):
                 fwhm_x=float(xs[half].max() - xs[half].min()), points=int(len(pts)), seconds=t)
 
 
+def combine_ranks(ms_total, world, R, steps, device):
+    """Replicas: the slowest rank's time over the units all ranks processed.
+    Returns (max over ranks of ms_total, whole-job products per second)."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([ms_total], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+        dist.barrier()
+    return ms_total, world * R * steps / (ms_total / 1e3)
+
+
 def run_ours(a):
     import numpy as np
     import torch
@@ -354,13 +367,8 @@ def run_ours(a):
     if cf is not None and os.path.exists(os.path.join(ROOT, f".clocks_{rank}.csv")):
         os.remove(os.path.join(ROOT, f".clocks_{rank}.csv"))
     torch.cuda.synchronize(dev)
-    if world > 1:
-        t = torch.tensor([ms_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
-        dist.barrier()
+    ms_total, value = combine_ranks(ms_total, world, R, a.steps, dev)
     ms_step = ms_total / a.steps
-    value = world * R * a.steps / (ms_total / 1e3)      # right-hand-side products per second
 
     # ---- the same products launched kernel by kernel (no graph)
     ms_direct = timed(P32, max(3, a.steps // 4), 2, graph=False) / max(3, a.steps // 4)
