@@ -173,6 +173,17 @@ int smr_matvec_host(smr_ctx* ctx, int R, const double* x, double* y, int precisi
  * (smr_matvec_graph) so the next call captures the new choice. */
 int smr_set_tensor_cores(smr_ctx* ctx, int enable);
 
+/* Times the launch variants of the product for one right-hand side in
+ * `precision` on this scene and keeps the fastest for later products (no
+ * counterpart in the paper).  Per level: translation with 8x8 target tiles
+ * and the full or half direction chunk, or 4x4 tiles; interpolation with the
+ * full or half theta-row tile; for SMR_PREC_FP32 also aggregation and
+ * receive on the tensor cores or the CUDA cores.  Each variant is timed over
+ * three products (CUDA events around every launch, the fastest kept).  Uses
+ * and overwrites the context's scratch buffers; drops captured products.
+ * R must be 1. */
+int smr_autotune(smr_ctx* ctx, int R, int precision, void* stream);
+
 /* Synchronises `stream` and reports errors found on the device since the
  * last check: SMR_E_CUDA if a tensor-core pipeline wait ran out (that
  * product's result is invalid; the kernel stopped, freed its tensor memory

@@ -911,6 +911,88 @@ int smr_profile_matvec(smr_ctx* h, int R, const void* x, void* y, int precision,
   return SMR_OK;
 }
 
+// ---------------------------------------------------------------- autotuning of launch variants
+namespace {
+// per (kernel name, level) the fastest of `reps` profiled products
+int profile_min(smr_ctx* h, int R, const void* x, void* y, int prec, int reps, void* stream,
+                std::map<std::pair<std::string, int>, double>& best) {
+  Ctx* c = &h->c;
+  best.clear();
+  for (int r = 0; r < reps; ++r) {
+    std::vector<ProfRec> recs;
+    c->prof = &recs;
+    int rc = smr_matvec(h, R, x, y, prec, stream);
+    c->prof = nullptr;
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    for (auto& q : recs) {
+      float ms = 0.f;
+      if (rc == SMR_OK && e == cudaSuccess) cudaEventElapsedTime(&ms, q.a, q.b);
+      auto key = std::make_pair(std::string(q.name), q.level);
+      auto it = best.find(key);
+      if (it == best.end() || ms < it->second) best[key] = ms;
+      cudaEventDestroy(q.a);
+      cudaEventDestroy(q.b);
+    }
+    if (rc) return rc;
+    if (e != cudaSuccess) return fail(c, SMR_E_CUDA, cudaGetErrorString(e));
+  }
+  return SMR_OK;
+}
+}  // namespace
+
+int smr_autotune(smr_ctx* h, int R, int precision, void* stream) {
+  if (!h || R != 1) return SMR_E_INVALID_ARG;
+  Ctx* c = &h->c;
+  if (!check_scene(c)) return SMR_E_STATE;
+  if (precision != SMR_PREC_FP64 && precision != SMR_PREC_FP32)
+    return fail(c, SMR_E_INVALID_ARG, "precision must be SMR_PREC_FP64 or SMR_PREC_FP32");
+  const int q = precision == SMR_PREC_FP64 ? 0 : 1;
+  size_t n = (size_t)n_unknowns(c);
+  int rc = tmp_buffer(c, 2 * n);
+  if (rc) return rc;
+  double2* x = c->d_tmp;
+  double2* y = c->d_tmp + n;
+  SMR_CUDA(c, cudaMemsetAsync(x, 0, n * sizeof(double2), (cudaStream_t)stream));
+  std::map<std::pair<std::string, int>, double> t;
+  // translation: 8x8 tiles (full, half direction chunk) and 4x4 tiles
+  std::vector<std::vector<double>> ttr(c->nlev, std::vector<double>(4, 1e30));
+  std::vector<std::vector<double>> tip(c->nlev, std::vector<double>(3, 1e30));
+  double agg[2] = {1e30, 1e30}, rec[2] = {1e30, 1e30};
+  const int agg0 = c->tune_tc_agg, rec0 = c->tune_tc_rec;
+  for (int v = 1; v <= 3; ++v) {
+    for (auto& L : c->lev) { L.tune_tr[q] = v; L.tune_ip[q] = (v == 2) ? 2 : 0; }
+    c->tune_tc_agg = c->tune_tc_rec = (v == 3) ? 0 : 1;
+    if ((rc = profile_min(h, 1, x, y, precision, 3, stream, t))) break;
+    for (int s = 0; s < c->nlev; ++s) {
+      auto it = t.find({"translate", s});
+      if (it != t.end()) ttr[s][v] = it->second;
+      auto ip = t.find({"interpolate", s});
+      if (ip != t.end()) tip[s][v == 2 ? 2 : 0] = std::min(tip[s][v == 2 ? 2 : 0], ip->second);
+    }
+    int tc = (v == 3) ? 0 : 1;
+    auto a = t.find({"aggregate", 0});
+    if (a != t.end()) agg[tc] = std::min(agg[tc], a->second);
+    auto r = t.find({"receive", 0});
+    if (r != t.end()) rec[tc] = std::min(rec[tc], r->second);
+  }
+  for (int s = 0; s < c->nlev; ++s) {
+    Level& L = c->lev[s];
+    int bv = 1;
+    for (int v = 2; v <= 3; ++v)
+      if (ttr[s][v] < ttr[s][bv]) bv = v;
+    L.tune_tr[q] = rc ? 0 : bv;
+    L.tune_ip[q] = (!rc && tip[s][2] < tip[s][0]) ? 2 : 0;
+  }
+  c->tune_tc_agg = agg0;
+  c->tune_tc_rec = rec0;
+  if (q == 1) {                                // the tensor-core steps exist in FP32 only
+    c->tune_tc_agg = rc ? -1 : (agg[1] <= agg[0] ? 1 : 0);
+    c->tune_tc_rec = rc ? -1 : (rec[1] <= rec[0] ? 1 : 0);
+  }
+  free_graphs(c);                              // captured products used the trial variants
+  return rc;
+}
+
 // ---------------------------------------------------------------- per-array incidence and the learned guess
 namespace {
 int upload_inc(Ctx* c, int n, const double* khat, const double* pol, double** dk, double** dp) {

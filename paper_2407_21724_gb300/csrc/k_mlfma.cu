@@ -1044,7 +1044,7 @@ static int far_impl(Ctx* c, int R, const double2* x, double2* y, bool accumulate
          (double)c->p * 2 * c->npsi * R_ * 16 + (double)c->S * c->npsi * 2 * L0.K * es +
              (double)c->p * L0.K * 4 * R_ * es,
          32.0 * c->npsi * c->p * L0.K * R_);
-    if (!f64 && tc_aggregate_ok(c, R)) {
+    if (!f64 && tc_aggregate_ok(c, R) && c->tune_tc_agg != 0) {
       int rc = run_aggregate_tc(c, x, (float2*)L0.d_out, st);
       pend(c, st);
       if (rc) return rc;
@@ -1066,6 +1066,7 @@ static int far_impl(Ctx* c, int R, const double2* x, double2* y, bool accumulate
          (double)Lc.nbox * Lp.nth * Lc.nph * 4 * R_ * 16.0 + (double)Lc.nbox * Lp.K * 4 * R_ * 24.0);
     if (R == 1 && Lp.nph * Part<T>::NT <= 256 * EM1<T>::v) {
       int TR = std::max(1, std::min(Lp.nth, (256 * EM1<T>::v) / (Lp.nph * Part<T>::NT)));
+      if (Lc.tune_ip[f64 ? 0 : 1] == 2) TR = std::max(1, TR / 2);
       int nrt = (Lp.nth + TR - 1) / TR;
       size_t sm1 = (size_t)TR * Lc.nph * 4 * sizeof(V);
       cudaFuncSetAttribute(k_interp1<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
@@ -1130,9 +1131,11 @@ static int far_impl(Ctx* c, int R, const double2* x, double2* y, bool accumulate
          2.0 * L.nbox * L.K * 4 * R_ * es + (double)L.off_dx.size() * L.K * es,
          8.0 * L.il_src.size() * L.K * 4 * R_);
     // single right-hand side: 8x8-tile register-blocked kernel, except on
-    // levels whose few boxes would leave most of one 8x8 tile idle
-    if (R == 1 && !(L.ntile8_ne == 1 && L.nbox < 32)) {
-      int KC1 = f64 ? 8 : 16;
+    // levels whose few boxes would leave most of one 8x8 tile idle (or as tuned)
+    const int tv = (R == 1) ? L.tune_tr[f64 ? 0 : 1] : 0;
+    const bool use8 = (tv == 0) ? (R == 1 && !(L.ntile8_ne == 1 && L.nbox < 32)) : (tv != 3);
+    if (use8) {
+      int KC1 = (f64 ? 8 : 16) / (tv == 2 ? 2 : 1);
       int nk1 = (L.K + KC1 - 1) / KC1;
       size_t sm1 = ((size_t)144 * KC1 * 4 + (size_t)49 * KC1) * sizeof(V) + (144 + 64) * sizeof(int);
       k_translate1<T><<<(unsigned)(L.ntile8_ne * nk1), 16 * KC1 * Part<T>::NT, sm1, st>>>(
@@ -1193,7 +1196,7 @@ static int far_impl(Ctx* c, int R, const double2* x, double2* y, bool accumulate
          (double)c->p * L0.K * 4 * R_ * es + (double)c->S * c->npsi * 2 * L0.K * es +
              (accumulate ? 2.0 : 1.0) * c->p * 2 * c->npsi * R_ * 16,
          48.0 * c->p * c->npsi * L0.K * R_);
-    if (!f64 && tc_receive_ok(c, R)) {
+    if (!f64 && tc_receive_ok(c, R) && c->tune_tc_rec != 0) {
       int rc = run_receive_tc(c, (const float2*)L0.d_in, y, accumulate, st);
       pend(c, st);
       return rc;

@@ -102,6 +102,12 @@ struct Level {
   // the transposed taps padded to fixed widths (multiples of 4, zero weights):
   // phi by child column [nph][PM] (parent column, weight x dphi_p / dphi_c),
   // theta by child row [nth][TM] (parent row | refl << 16, sign x weight / w_theta)
+  // launch variants chosen by smr_autotune per precision (FP64, FP32), one
+  // right-hand side; 0 = the built-in rule.  Translation: 1 / 2 = 8x8 target
+  // tiles with the full / half direction chunk, 3 = 4x4 tiles.  Interpolation
+  // into the parent of this level: 2 = half the theta-row tile.
+  int tune_tr[2] = {0, 0};
+  int tune_ip[2] = {0, 0};
   int ant_PM = 0, ant_TM = 0;
   int* d_ant_pjp = nullptr;
   double* d_ant_pw64 = nullptr;
@@ -229,6 +235,8 @@ struct Ctx {
   bool tc_agg_ready = false;
   int tc_nMT = 0, tc_nKc = 0;
   float* d_tc_agg = nullptr;              // [S][M tiles][K chunks][hi | lo][128][32] aggregation images
+  // tensor cores for aggregation / receive chosen by smr_autotune (-1: not tuned)
+  int tune_tc_agg = -1, tune_tc_rec = -1;
   // learned local-coupling preconditioner: diagonal D [N] (one right-hand side)
   double2* d_lpc = nullptr;
   bool lpc_ready = false;

@@ -103,6 +103,7 @@ _SIGS = {
     "smr_copy_level": (C.c_int, [_P, C.c_int, C.c_int, _D, C.c_size_t]),
     "smr_set_tensor_cores": (C.c_int, [_P, C.c_int]),
     "smr_nn_precond": (C.c_int, [_P, _D, _D, C.c_double, _P, _P]),
+    "smr_autotune": (C.c_int, [_P, C.c_int, C.c_int, _P]),
     "smr_sync": (C.c_int, [_P, _P]),
 }
 
@@ -313,6 +314,10 @@ def smr_solve(ctx, b, x, R=None, stream=None, **kw):
 
 def smr_set_tensor_cores(ctx, enable):
     _check(ctx, lib().smr_set_tensor_cores(ctx, 1 if enable else 0))
+
+
+def smr_autotune(ctx, precision=SMR_PREC_FP32, stream=None):
+    _check(ctx, lib().smr_autotune(ctx, 1, precision, _stream(stream, None)))
 
 
 def smr_sync(ctx, stream=None):

@@ -167,6 +167,17 @@ def test_tensor_core_receive(c1, rnd):
         assert rel(y1, ref) < 2e-5, rel(y1, ref)
         assert rel(y1, y0) < 5e-6, rel(y1, y0)
 
+
+def test_autotuned_product_matches_oracle(rnd):
+    """After smr_autotune picks launch variants, the FP64 and FP32 products
+    still meet their bars against the oracle (every variant computes the
+    same product)."""
+    x = crandn(rnd.info["n_unknowns"], 41)
+    ref = rnd.M.matvec(x)
+    for prec, bar in ((smr.SMR_PREC_FP64, TOL64), (smr.SMR_PREC_FP32, 2e-5)):
+        smr.smr_autotune(rnd.ctx, prec)
+        assert rel(rnd.gpu_matvec(x, prec), ref) < bar
+
 @pytest.mark.parametrize("R", [5, 17, 64])
 def test_batched_columns_match_single(rnd, R):
     """R right-hand sides in one product: every column equals the single
