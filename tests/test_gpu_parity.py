@@ -181,15 +181,17 @@ def test_autotuned_product_matches_oracle(rnd):
 @pytest.mark.parametrize("R", [5, 17, 64])
 def test_batched_columns_match_single(rnd, R):
     """R right-hand sides in one product: every column equals the single
-    product bit for bit, in both precisions, and the FP64 columns match the
+    product to rounding (the single right-hand-side kernels sum in their own
+    order: staged conjugate-shifted parent rows in the anterpolation, tuned
+    translation variants), in both precisions, and the FP64 columns match the
     oracle."""
     n = rnd.info["n_unknowns"]
     X = np.stack([crandn(n, 20 + r) for r in range(R)], axis=1)
-    for prec in (smr.SMR_PREC_FP64, smr.SMR_PREC_FP32):
+    for prec, bar in ((smr.SMR_PREC_FP64, 1e-13), (smr.SMR_PREC_FP32, 1e-6)):
         Y = rnd.gpu_matvec(X, prec).reshape(n, R)
         for r in (0, R // 2, R - 1):
             y1 = rnd.gpu_matvec(np.ascontiguousarray(X[:, r]), prec)
-            assert np.array_equal(Y[:, r], y1), (prec, r)
+            assert rel(Y[:, r], y1) < bar, (prec, r, rel(Y[:, r], y1))
     Y = rnd.gpu_matvec(X).reshape(n, R)
     for r in (1, R - 2):
         assert rel(Y[:, r], rnd.M.matvec(X[:, r])) < TOL64
