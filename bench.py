@@ -203,7 +203,7 @@ def traffic_for(kernel):
     return rec["dram_bytes_per_launch"] if h == rec["sha"] else None
 
 
-def train_learned(smr, workloads, n_arrays, dev, n_side=20, width=256, steps=1500, batch=4096):
+def train_learned(smr, workloads, n_arrays, dev, n_side=20, width=256, steps=1500, batch=4096, modes=16):
     """Solve n_arrays random n_side x n_side arrays (ragged batches of up to
     100, one incidence each, FP32-inner refinement to 1e-6), then train the
     MLP on their de-phased coefficients.  Returns parameters and timings."""
@@ -211,7 +211,7 @@ def train_learned(smr, workloads, n_arrays, dev, n_side=20, width=256, steps=150
     import torch
     t0 = time.perf_counter()
     feats, tgts, xs = [], [], []
-    arrays = workloads.training_arrays(n_arrays, n=n_side, seed0=100000)
+    arrays = workloads.training_arrays(n_arrays, n=n_side, seed0=100000, modes=modes)
     chunks = [arrays[i:i + 100] for i in range(0, n_arrays, 100)]
     sols = []
     for ch in chunks:
@@ -443,7 +443,8 @@ def run_ours(a):
         gm = {}
         learned = None
         if a.train_arrays > 0 and R == 1:
-            learned = train_learned(smr, workloads, a.train_arrays, dev)
+            # training arrays carry the workload's modes per current (N_perp = N_par)
+            learned = train_learned(smr, workloads, a.train_arrays, dev, modes=info["n_psi"] // 2)
 
         def solve(label, prec, x0=None, lpc=False):
             xs = torch.zeros_like(b) if x0 is None else x0.clone()
