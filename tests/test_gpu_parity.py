@@ -223,13 +223,23 @@ def test_precond(c1):
 
 
 def test_single_particle_and_line():
+    """Degenerate scenes: one particle (tensor-core tiles of one column, no
+    interaction lists) and a 7-particle line; 8 + 8 and odd 5 + 4 modes (the
+    odd count takes the CUDA-core aggregation).  FP64 at the parity bar,
+    FP32 (tensor cores on and off) at the FP32 bar."""
     for C in ([[0.0, 0.0, 0.0]], [[0.5 * i, 0.0, 0.0] for i in range(7)]):
-        w = dict(centres=np.array(C), shape_ids=np.zeros(len(C), dtype=np.int32),
-                 shapes=[(0.15, 8, 8)], eps_in=4.0, pitch=0.5)
-        c = Case(w)
-        x = crandn(c.info["n_unknowns"], 8)
-        assert rel(c.gpu_matvec(x), c.M.matvec(x)) < TOL64
-        smr.smr_destroy(c.ctx)
+        for modes in ((8, 8), (5, 4)):
+            w = dict(centres=np.array(C), shape_ids=np.zeros(len(C), dtype=np.int32),
+                     shapes=[(0.15,) + modes], eps_in=4.0, pitch=0.5)
+            c = Case(w)
+            x = crandn(c.info["n_unknowns"], 8)
+            ref = c.M.matvec(x)
+            assert rel(c.gpu_matvec(x), ref) < TOL64
+            for tc in (True, False):
+                smr.smr_set_tensor_cores(c.ctx, tc)
+                assert rel(c.gpu_matvec(x, smr.SMR_PREC_FP32), ref) < 2e-5, (len(C), modes, tc)
+            smr.smr_sync(c.ctx)
+            smr.smr_destroy(c.ctx)
 
 
 def test_solve_fp64_and_mixed(c1):
