@@ -30,7 +30,7 @@ template <typename T> void dfree(T*& p) {
 void free_scene(Ctx* c) {
   free_graphs(c);
   for (auto& L : c->lev) {
-    dfree(L.d_khat); dfree(L.d_w); dfree(L.d_il_ptr); dfree(L.d_il_src); dfree(L.d_il_off);
+    dfree(L.d_khat); dfree(L.d_w); dfree(L.d_il_ptr); dfree(L.d_il_src); dfree(L.d_il_off); dfree(L.d_il_pk);
     dfree(L.d_T64); dfree(L.d_T32); dfree(L.d_parent); dfree(L.d_quad); dfree(L.d_ch_ptr);
     dfree(L.d_ch_idx); dfree(L.d_ch_quad); dfree(L.d_th_src); dfree(L.d_th_refl); dfree(L.d_th_w64);
     dfree(L.d_th_w32); dfree(L.d_ph_src); dfree(L.d_ph_w64); dfree(L.d_ph_w32); dfree(L.d_shift64);
@@ -512,7 +512,12 @@ int set_scene(Ctx* c, int p, const double* centres, const int* shape_ids, const 
     for (size_t t = 0; t < used8.size(); ++t)
       if (used8[t]) tiles8.push_back((int)t);
     L.ntile8_ne = (int)tiles8.size();
+    // interaction list packed for the few-box kernel: source box * 64 + table row
+    std::vector<int> pk(L.il_src.size());
+    for (size_t e = 0; e < L.il_src.size(); ++e)
+      pk[e] = L.il_src[e] * 64 + (L.off_dx[L.il_off[e]] + 3) * 7 + (L.off_dy[L.il_off[e]] + 3);
     int rc;
+    if (!pk.empty() && (rc = upload(c, &L.d_il_pk, pk))) return rc;
     if ((rc = upload(c, &L.d_tiles8, tiles8))) return rc;
     if ((rc = upload(c, &L.d_boxmap, bm)) || (rc = upload(c, &L.d_offid, oid)) ||
         (rc = upload(c, &L.d_tiles, tiles)))
@@ -955,17 +960,18 @@ int smr_autotune(smr_ctx* h, int R, int precision, void* stream) {
   SMR_CUDA(c, cudaMemsetAsync(x, 0, n * sizeof(double2), (cudaStream_t)stream));
   std::map<std::pair<std::string, int>, double> t;
   // translation: 8x8 tiles (full, half direction chunk) and 4x4 tiles
-  std::vector<std::vector<double>> ttr(c->nlev, std::vector<double>(4, 1e30));
+  std::vector<std::vector<double>> ttr(c->nlev, std::vector<double>(5, 1e30));
   std::vector<std::vector<double>> tip(c->nlev, std::vector<double>(3, 1e30));
   double agg[2] = {1e30, 1e30}, rec[2] = {1e30, 1e30};
   const int agg0 = c->tune_tc_agg, rec0 = c->tune_tc_rec;
-  for (int v = 1; v <= 3; ++v) {
-    for (auto& L : c->lev) { L.tune_tr[q] = v; L.tune_ip[q] = (v == 2) ? 2 : 0; }
+  for (int v = 1; v <= 4; ++v) {
+    // variant 4 (few-box kernel) only where a level has at most 1024 boxes
+    for (auto& L : c->lev) { L.tune_tr[q] = (v == 4 && L.nbox > 1024) ? 1 : v; L.tune_ip[q] = (v == 2) ? 2 : 0; }
     c->tune_tc_agg = c->tune_tc_rec = (v == 3) ? 0 : 1;
     if ((rc = profile_min(h, 1, x, y, precision, 3, stream, t))) break;
     for (int s = 0; s < c->nlev; ++s) {
       auto it = t.find({"translate", s});
-      if (it != t.end()) ttr[s][v] = it->second;
+      if (it != t.end() && c->lev[s].tune_tr[q] == v) ttr[s][v] = it->second;
       auto ip = t.find({"interpolate", s});
       if (ip != t.end()) tip[s][v == 2 ? 2 : 0] = std::min(tip[s][v == 2 ? 2 : 0], ip->second);
     }
@@ -978,7 +984,7 @@ int smr_autotune(smr_ctx* h, int R, int precision, void* stream) {
   for (int s = 0; s < c->nlev; ++s) {
     Level& L = c->lev[s];
     int bv = 1;
-    for (int v = 2; v <= 3; ++v)
+    for (int v = 2; v <= 4; ++v)
       if (ttr[s][v] < ttr[s][bv]) bv = v;
     L.tune_tr[q] = rc ? 0 : bv;
     L.tune_ip[q] = (!rc && tip[s][2] < tip[s][0]) ? 2 : 0;

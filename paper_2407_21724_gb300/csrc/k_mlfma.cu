@@ -685,6 +685,34 @@ __global__ void __launch_bounds__(512) k_translate1(int K, int KC, int ntx, int 
   }
 }
 
+// Few boxes, many directions (coarse levels), one right-hand side: threads run
+// along the directions (NT 16-byte parts each, coalesced); a CTA takes TG
+// consecutive target boxes and reads each target's interaction list
+// (source box * 64 + table row) uniformly.
+template <typename T>
+__global__ void __launch_bounds__(256) k_translate_few(int K, int nbox, int TG, const int* __restrict__ il_ptr,
+                                                       const int* __restrict__ il_pk,
+                                                       const typename CV<T>::V* __restrict__ Tg,
+                                                       const typename CV<T>::V* __restrict__ out,
+                                                       typename CV<T>::V* __restrict__ in) {
+  typedef typename CV<T>::V V;
+  typedef Part<T> P;
+  typedef typename P::H H;
+  constexpr int NT = P::NT;
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const int k = (int)(t / NT), h = (int)(t % NT);
+  const bool ok = k < K;
+  const int b0 = blockIdx.y * TG, b1 = min(nbox, b0 + TG);
+  for (int b = b0; b < b1; ++b) {
+    H acc = P::zero();
+    for (int e = il_ptr[b]; e < il_ptr[b + 1]; ++e) {
+      const int pk = il_pk[e];
+      if (ok) P::cfma(acc, Tg[(size_t)(pk & 63) * K + k], ldp<T>(out, (size_t)(pk >> 6) * K + k, h));
+    }
+    if (ok) stp<T>(in, (size_t)b * K + k, h, acc);
+  }
+}
+
 // ------------------------------------------------------------------ anterpolation (separable adjoint)
 // phi-transposed pass (one warp per row (c, tp)), child c in quadrant q of parent B:
 //   Gt[c][tp][j][f][r] = w_theta_p[tp] sum_{(jp, w) in Pt(j)} w conj(shift[q][tp, jp]) in[B][tp][jp][f][r]
@@ -1133,8 +1161,15 @@ static int far_impl(Ctx* c, int R, const double2* x, double2* y, bool accumulate
     // single right-hand side: 8x8-tile register-blocked kernel, except on
     // levels whose few boxes would leave most of one 8x8 tile idle (or as tuned)
     const int tv = (R == 1) ? L.tune_tr[f64 ? 0 : 1] : 0;
+    const bool few = (tv == 4) || (tv == 0 && R == 1 && L.nbox <= 64);
     const bool use8 = (tv == 0) ? (R == 1 && !(L.ntile8_ne == 1 && L.nbox < 32)) : (tv != 3);
-    if (use8) {
+    if (few) {
+      const int TG = 8;
+      dim3 g((unsigned)(((long long)L.K * Part<T>::NT + 255) / 256), (unsigned)((L.nbox + TG - 1) / TG));
+      k_translate_few<T><<<g, 256, 0, st>>>(L.K, L.nbox, TG, L.d_il_ptr, L.d_il_pk,
+                                             (const V*)(f64 ? (void*)L.d_T64 : (void*)L.d_T32), (const V*)L.d_out,
+                                             (V*)L.d_in);
+    } else if (use8) {
       int KC1 = (f64 ? 8 : 16) / (tv == 2 ? 2 : 1);
       int nk1 = (L.K + KC1 - 1) / KC1;
       size_t sm1 = ((size_t)144 * KC1 * 4 + (size_t)49 * KC1) * sizeof(V) + (144 + 64) * sizeof(int);

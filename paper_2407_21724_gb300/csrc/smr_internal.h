@@ -56,6 +56,7 @@ struct Level {
   int* d_il_ptr = nullptr;
   int* d_il_src = nullptr;
   int* d_il_off = nullptr;
+  int* d_il_pk = nullptr;                // [n_il] source box * 64 + table row (few-box kernel)
   double2* d_T64 = nullptr;              // [noff][K]
   float2* d_T32 = nullptr;
   int* d_parent = nullptr;
@@ -104,7 +105,8 @@ struct Level {
   // theta by child row [nth][TM] (parent row | refl << 16, sign x weight / w_theta)
   // launch variants chosen by smr_autotune per precision (FP64, FP32), one
   // right-hand side; 0 = the built-in rule.  Translation: 1 / 2 = 8x8 target
-  // tiles with the full / half direction chunk, 3 = 4x4 tiles.  Interpolation
+  // tiles with the full / half direction chunk, 3 = 4x4 tiles, 4 = the
+  // few-box kernel (threads along the directions).  Interpolation
   // into the parent of this level: 2 = half the theta-row tile.
   int tune_tr[2] = {0, 0};
   int tune_ip[2] = {0, 0};
