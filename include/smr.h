@@ -176,8 +176,10 @@ int smr_set_tensor_cores(smr_ctx* ctx, int enable);
 /* Times the launch variants of the product for one right-hand side in
  * `precision` on this scene and keeps the fastest for later products (no
  * counterpart in the paper).  Per level: translation with 8x8 target tiles
- * and the full or half direction chunk, or 4x4 tiles; interpolation with the
- * full or half theta-row tile; for SMR_PREC_FP32 also aggregation and
+ * and the full or half direction chunk, 4x4 tiles, or threads along the
+ * directions (levels of at most 1024 boxes); interpolation with the full or
+ * half theta-row tile; anterpolation with the full or half column chunk or
+ * 256-thread CTAs; for SMR_PREC_FP32 also aggregation and
  * receive on the tensor cores or the CUDA cores.  Each variant is timed over
  * three products (CUDA events around every launch, the fastest kept).  Uses
  * and overwrites the context's scratch buffers; drops captured products.

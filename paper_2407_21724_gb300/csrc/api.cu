@@ -962,16 +962,24 @@ int smr_autotune(smr_ctx* h, int R, int precision, void* stream) {
   // translation: 8x8 tiles (full, half direction chunk) and 4x4 tiles
   std::vector<std::vector<double>> ttr(c->nlev, std::vector<double>(5, 1e30));
   std::vector<std::vector<double>> tip(c->nlev, std::vector<double>(3, 1e30));
+  std::vector<std::vector<double>> tan_(c->nlev, std::vector<double>(3, 1e30));
+  const int anv[5] = {0, 0, 1, 2, 0};          // anterpolation variant timed in trial v
   double agg[2] = {1e30, 1e30}, rec[2] = {1e30, 1e30};
   const int agg0 = c->tune_tc_agg, rec0 = c->tune_tc_rec;
   for (int v = 1; v <= 4; ++v) {
     // variant 4 (few-box kernel) only where a level has at most 1024 boxes
-    for (auto& L : c->lev) { L.tune_tr[q] = (v == 4 && L.nbox > 1024) ? 1 : v; L.tune_ip[q] = (v == 2) ? 2 : 0; }
+    for (auto& L : c->lev) {
+      L.tune_tr[q] = (v == 4 && L.nbox > 1024) ? 1 : v;
+      L.tune_ip[q] = (v == 2) ? 2 : 0;
+      L.tune_an[q] = anv[v];
+    }
     c->tune_tc_agg = c->tune_tc_rec = (v == 3) ? 0 : 1;
     if ((rc = profile_min(h, 1, x, y, precision, 3, stream, t))) break;
     for (int s = 0; s < c->nlev; ++s) {
       auto it = t.find({"translate", s});
       if (it != t.end() && c->lev[s].tune_tr[q] == v) ttr[s][v] = it->second;
+      auto an = t.find({"anterpolate", s});
+      if (an != t.end()) tan_[s][anv[v]] = std::min(tan_[s][anv[v]], an->second);
       auto ip = t.find({"interpolate", s});
       if (ip != t.end()) tip[s][v == 2 ? 2 : 0] = std::min(tip[s][v == 2 ? 2 : 0], ip->second);
     }
@@ -988,6 +996,10 @@ int smr_autotune(smr_ctx* h, int R, int precision, void* stream) {
       if (ttr[s][v] < ttr[s][bv]) bv = v;
     L.tune_tr[q] = rc ? 0 : bv;
     L.tune_ip[q] = (!rc && tip[s][2] < tip[s][0]) ? 2 : 0;
+    int ba = 0;
+    for (int v = 1; v <= 2; ++v)
+      if (tan_[s][v] < tan_[s][ba]) ba = v;
+    L.tune_an[q] = rc ? 0 : ba;
   }
   c->tune_tc_agg = agg0;
   c->tune_tc_rec = rec0;

@@ -1193,10 +1193,12 @@ static int far_impl(Ctx* c, int R, const double2* x, double2* y, bool accumulate
          (double)Lc.nbox * Lp.nth * Lc.nph * 4 * R_ * 8.0 * 2 * (double)Lp.nph / Lc.nph * 4.0 / 4.0 +
              (double)Lc.nbox * Lc.K * 4 * R_ * 16.0 * (double)Lp.nth / Lc.nth);
     if (R == 1) {
+      const int an = Lc.tune_an[f64 ? 0 : 1];
       int JC = Lc.ant_JC[f64 ? 0 : 1];
+      if (an == 1) JC = std::max(1, JC / 2);
       int njc = (Lc.nph / 2 + JC - 1) / JC;
       size_t sm1 = (size_t)Lc.ant_GR * 2 * JC * 4 * sizeof(V);
-      int thr = (Lc.ant_GR * 2 * JC * Part<T>::NT >= 2048) ? 256 : 128;
+      int thr = (an == 2 || Lc.ant_GR * 2 * JC * Part<T>::NT >= 2048) ? 256 : 128;
       k_anterp1<T><<<(unsigned)(Lc.nbox * Lc.ant_nit * njc), thr, sm1, st>>>(
           Lc.nth, Lc.nph, Lp.nth, Lp.nph, Lc.ant_TI, Lc.ant_nit, JC, njc, Lc.d_parent, Lc.d_quad, Lc.d_ant_lo,
           Lc.ant_PM, Lc.d_ant_pjp, (const T*)(f64 ? (void*)Lc.d_ant_pw64 : (void*)Lc.d_ant_pw32),

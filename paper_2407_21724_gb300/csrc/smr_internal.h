@@ -110,6 +110,8 @@ struct Level {
   // into the parent of this level: 2 = half the theta-row tile.
   int tune_tr[2] = {0, 0};
   int tune_ip[2] = {0, 0};
+  // anterpolation into this level: 1 = half the column chunk, 2 = 256 threads
+  int tune_an[2] = {0, 0};
   int ant_PM = 0, ant_TM = 0;
   int* d_ant_pjp = nullptr;
   double* d_ant_pw64 = nullptr;
