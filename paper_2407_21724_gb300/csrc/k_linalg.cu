@@ -785,8 +785,9 @@ static int gmres_core(Ctx* c, int R, int prec, int precond, const double2* rhs, 
       ++*nmv;
       ++*its;
       // classical Gram-Schmidt against v_0..v_j, repeated once when the norm
-      // drops below 1/sqrt(2) of its value before the projection ("twice is
-      // enough"); the coefficients and norms are summed in FP64
+      // drops below 1/sqrt(10) of its value before the projection (a single
+      // pass then loses at most ~3x the working precision in orthogonality);
+      // the coefficients and norms are summed in FP64
       rc = gs_pass(c, W, j + 1, n, R, ld, dh1, dh1f, dn0, dnr, st);
       if (rc) return rc;
       cudaEventRecord(W.ev[3], st);
@@ -799,7 +800,7 @@ static int gmres_core(Ctx* c, int R, int prec, int precond, const double2* rhs, 
       bool reorth = false;
       for (int r = 0; r < R; ++r) {
         double a0 = hbuf[(size_t)2 * (m + 1) * R + R + r].x, a1 = hbuf[(size_t)2 * (m + 1) * R + r].x;
-        if (active[r] && a1 < 0.5 * a0) reorth = true;
+        if (active[r] && a1 < 0.1 * a0) reorth = true;
       }
       if (reorth) {
         ++*n_reorth;
