@@ -29,7 +29,8 @@ namespace smr {
 
 namespace {
 
-constexpr int TC_NP = 128;                     // particles per CTA (MMA N)
+constexpr int TC_NP = 128;                     // particle rows per CTA (MMA N)
+constexpr int TC_TILE = 96;                    // particles per tile: 3 waves of smaller tiles on 152 SMs
 constexpr int TC_KC = 32;                      // K values per chunk (one swizzle row)
 constexpr int TC_ABYTES = 128 * TC_KC * 4;     // one coefficient chunk, one split: 16 KB
 constexpr int TC_BBYTES = TC_NP * TC_KC * 4;   // one spectrum chunk, one split: 16 KB
@@ -621,7 +622,7 @@ int build_tc(Ctx* c) {
   std::stable_sort(perm.begin(), perm.end(), [&](int a, int b) { return c->sid[a] < c->sid[b]; });
   for (int i = 0; i < c->p;) {
     int s = c->sid[perm[i]], j = i;
-    while (j < c->p && c->sid[perm[j]] == s && j - i < TC_NP) ++j;
+    while (j < c->p && c->sid[perm[j]] == s && j - i < TC_TILE) ++j;
     tsh.push_back(s); tst.push_back(i); tcn.push_back(j - i);
     i = j;
   }
