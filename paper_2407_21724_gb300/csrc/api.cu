@@ -53,7 +53,8 @@ void free_scene(Ctx* c) {
   dfree(c->d_pc_col); dfree(c->d_pc_blk); dfree(c->d_tmp);
   dfree(c->d_arr);
   dfree(c->d_tile_shape); dfree(c->d_tile_start); dfree(c->d_tile_count); dfree(c->d_perm);
-  dfree(c->d_tc_rec); dfree(c->d_tc_agg); dfree(c->d_tc_perm); dfree(c->d_lpc);
+  dfree(c->d_tc_rec); dfree(c->d_tc_agg); dfree(c->d_tc_perm); dfree(c->d_lpc); dfree(c->d_split);
+  c->split_elems = 0;
   c->lpc_ready = false; dfree(c->d_tc_shape); dfree(c->d_tc_start); dfree(c->d_tc_count);
   c->tc_ready = false;
   c->tc_agg_ready = false;
@@ -766,9 +767,7 @@ int smr_matvec(smr_ctx* h, int R, const void* x, void* y, int precision, void* s
   if (precision != SMR_PREC_FP64 && precision != SMR_PREC_FP32)
     return fail(c, SMR_E_INVALID_ARG, "precision must be SMR_PREC_FP64 or SMR_PREC_FP32");
   cudaStream_t st = (cudaStream_t)stream;
-  int rc = run_near(c, R, precision, (const double2*)x, (double2*)y, st);
-  if (rc) return rc;
-  return run_far(c, R, precision, (const double2*)x, (double2*)y, true, st);
+  return run_product(c, R, precision, (const double2*)x, (double2*)y, st);
 }
 
 int smr_matvec_graph(smr_ctx* h, int R, const void* x, void* y, int precision, void* stream) {

@@ -634,9 +634,7 @@ struct Work {
 }  // namespace
 
 static int apply_A(Ctx* c, int R, int prec, const double2* x, double2* y, cudaStream_t st) {
-  int rc = run_near(c, R, prec, x, y, st);
-  if (rc) return rc;
-  return run_far(c, R, prec, x, y, true, st);
+  return run_product(c, R, prec, x, y, st);
 }
 
 // z = M^-1 v: the block-diagonal preconditioner, scaled per unknown by the

@@ -1283,6 +1283,83 @@ int run_near(Ctx* c, int R, int prec, const double2* x, double2* y, cudaStream_t
   return rc;
 }
 
+// out[c][i] = in[i][c] for in [rows][cols] (tiles of 32 x 32 through shared
+// memory); grid x runs over the longer of the two dimensions
+__global__ void k_transpose_c128(long long rows, long long cols, const double2* __restrict__ in,
+                                 double2* __restrict__ out) {
+  __shared__ double2 t[32][33];
+  const bool rx = rows >= cols;
+  const long long i0 = (long long)(rx ? blockIdx.x : blockIdx.y) * 32;
+  const long long c0 = (long long)(rx ? blockIdx.y : blockIdx.x) * 32;
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    long long i = i0 + k, cc = c0 + threadIdx.x;
+    if (i < rows && cc < cols) t[k][threadIdx.x] = in[i * cols + cc];
+  }
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    long long cc = c0 + k, i = i0 + threadIdx.x;
+    if (i < rows && cc < cols) out[cc * rows + i] = t[threadIdx.x][k];
+  }
+}
+
+static int transpose_c128(Ctx* c, long long rows, long long cols, const double2* in, double2* out,
+                          cudaStream_t st) {
+  long long a = (rows + 31) / 32, b = (cols + 31) / 32;
+  dim3 g((unsigned)std::max(a, b), (unsigned)std::min(a, b));
+  k_transpose_c128<<<g, dim3(32, 8), 0, st>>>(rows, cols, in, out);
+  SMR_LAUNCH(c);
+  return SMR_OK;
+}
+
+bool split_columns(const Ctx* c, int R, int prec) { return R > 1 && prec == SMR_PREC_FP32 && c->split_cols; }
+
+// column buffers [R][N] for split products (allocated outside graph capture)
+int ensure_split(Ctx* c, int R) {
+  size_t need = (size_t)2 * R * 2 * c->npsi * c->p;
+  if (c->split_elems >= need) return SMR_OK;
+  if (c->d_split) cudaFree(c->d_split);
+  c->d_split = nullptr;
+  c->split_elems = 0;
+  if (cudaMalloc((void**)&c->d_split, need * sizeof(double2)) != cudaSuccess) {
+    cudaGetLastError();
+    c->err = "out of device memory for the column buffers of a split product";
+    return SMR_E_OOM;
+  }
+  c->split_elems = need;
+  return SMR_OK;
+}
+
+// y = Z x for R right-hand sides [N][R].  FP32 products with several
+// right-hand sides run column by column on the single right-hand-side kernels
+// (16-byte parts, tensor-core aggregation and receive), which are faster per
+// column than the batched kernels: x is transposed to [R][N], each column is
+// multiplied, and y is transposed back.
+int run_product(Ctx* c, int R, int prec, const double2* x, double2* y, cudaStream_t st) {
+  if (!split_columns(c, R, prec)) {
+    int rc = run_near(c, R, prec, x, y, st);
+    if (rc) return rc;
+    return run_far(c, R, prec, x, y, true, st);
+  }
+  int rc = ensure_split(c, R);
+  if (rc) return rc;
+  const long long n = 2LL * c->npsi * c->p;
+  double2* xs = c->d_split;
+  double2* ys = c->d_split + (size_t)R * n;
+  pbeg(c, st, "transpose", -1, 2.0 * n * R * 16, 0.0);
+  rc = transpose_c128(c, n, R, x, xs, st);
+  pend(c, st);
+  if (rc) return rc;
+  for (int r = 0; r < R && !rc; ++r) {
+    rc = run_near(c, 1, prec, xs + (size_t)r * n, ys + (size_t)r * n, st);
+    if (!rc) rc = run_far(c, 1, prec, xs + (size_t)r * n, ys + (size_t)r * n, true, st);
+  }
+  if (rc) return rc;
+  pbeg(c, st, "transpose", -1, 2.0 * n * R * 16, 0.0);
+  rc = transpose_c128(c, R, n, ys, y, st);
+  pend(c, st);
+  return rc;
+}
+
 void free_graphs(Ctx* c) {
   for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
   c->graphs.clear();
@@ -1296,7 +1373,10 @@ int run_matvec_graph(Ctx* c, int R, int prec, const double2* x, double2* y, cuda
       SMR_CUDA(c, cudaGraphLaunch(g.exec, st));
       return SMR_OK;
     }
-  int rc = ensure_spectra(c, R, prec);            // allocations happen outside the capture
+  // allocations happen outside the capture
+  const bool split = split_columns(c, R, prec);
+  int rc = ensure_spectra(c, split ? 1 : R, prec);
+  if (!rc && split) rc = ensure_split(c, R);
   if (rc) return rc;
   if (!c->capture_stream) SMR_CUDA(c, cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking));
   cudaStream_t cs = c->capture_stream;
@@ -1310,8 +1390,7 @@ int run_matvec_graph(Ctx* c, int R, int prec, const double2* x, double2* y, cuda
   std::vector<ProfRec>* prof = c->prof;
   c->prof = nullptr;
   SMR_CUDA(c, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-  rc = run_near(c, R, prec, x, y, cs);
-  if (!rc) rc = run_far(c, R, prec, x, y, true, cs);
+  rc = run_product(c, R, prec, x, y, cs);
   cudaGraph_t graph = nullptr;
   cudaError_t e = cudaStreamEndCapture(cs, &graph);
   c->prof = prof;

@@ -241,6 +241,10 @@ struct Ctx {
   float* d_tc_agg = nullptr;              // [S][M tiles][K chunks][hi | lo][128][32] aggregation images
   // tensor cores for aggregation / receive chosen by smr_autotune (-1: not tuned)
   int tune_tc_agg = -1, tune_tc_rec = -1;
+  // column buffers of split products ([R][N] in, [R][N] out)
+  bool split_cols = true;
+  double2* d_split = nullptr;
+  size_t split_elems = 0;
   // learned local-coupling preconditioner: diagonal D [N] (one right-hand side)
   double2* d_lpc = nullptr;
   bool lpc_ready = false;
@@ -324,6 +328,8 @@ int run_far(Ctx* c, int R, int prec, const double2* x, double2* y, bool accumula
 int run_precond(Ctx* c, int R, int prec, const double2* r, double2* z, cudaStream_t st);
 // y = Z x through a CUDA graph captured on first use for (x, y, R, prec)
 int run_matvec_graph(Ctx* c, int R, int prec, const double2* x, double2* y, cudaStream_t st);
+// y = Z x (near + far); FP32 with R > 1 runs column by column (split products)
+int run_product(Ctx* c, int R, int prec, const double2* x, double2* y, cudaStream_t st);
 void free_graphs(Ctx* c);
 // tensor-core receive and aggregation (k_tc.cu)
 int build_tc(Ctx* c);

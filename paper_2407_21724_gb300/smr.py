@@ -339,12 +339,13 @@ def smr_near_field(ctx, x, pts, EH, R=None, stream=None):
 def smr_profile_matvec(ctx, x, y, precision=SMR_PREC_FP64, R=None, stream=None):
     """One product with per-launch (name, level, bytes, flops, ms) records."""
     R = R if R is not None else _R(x, smr_info(ctx)["n_unknowns"])
-    arr = (smr_launch_t * 256)()
+    cap = 8192
+    arr = (smr_launch_t * cap)()
     n = C.c_int()
-    _check(ctx, lib().smr_profile_matvec(ctx, R, _ptr(x), _ptr(y), precision, arr, 256, C.byref(n),
+    _check(ctx, lib().smr_profile_matvec(ctx, R, _ptr(x), _ptr(y), precision, arr, cap, C.byref(n),
                                          _stream(stream, x)))
     return [dict(name=arr[i].name.decode(), level=arr[i].level, bytes=arr[i].bytes,
-                 flops=arr[i].flops, ms=arr[i].ms) for i in range(min(n.value, 256))]
+                 flops=arr[i].flops, ms=arr[i].ms) for i in range(min(n.value, cap))]
 
 
 def _inc(khat, pol):
