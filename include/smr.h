@@ -206,9 +206,9 @@ typedef struct {
   int precision;   /* SMR_PREC_FP64: plain GMRES on the FP64 product;
                       SMR_PREC_FP32: iterative refinement, outer residual with
                       the FP64 product, inner GMRES on the FP32 product and
-                      preconditioner.  With R = 1 the inner Krylov basis is
-                      stored in FP32 (Gram-Schmidt products in FP32, sums
-                      over the vector, Hessenberg and Givens in FP64) [FP64] */
+                      preconditioner.  The inner Krylov basis is stored in
+                      FP32 (Gram-Schmidt products in FP32, sums over the
+                      vector, Hessenberg and Givens in FP64) [FP64]          */
   int max_outer;   /* refinement steps for SMR_PREC_FP32 [8]                   */
   int use_x0;      /* 1: x holds the initial guess on entry; 0: start at 0     */
 } smr_solve_opts;

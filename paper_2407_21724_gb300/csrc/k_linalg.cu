@@ -2,7 +2,7 @@
 //
 // Vectors are complex FP64 [n][R] (R right-hand sides innermost).  The R
 // systems advance in lockstep: one R-column product per Arnoldi step, classical
-// Gram-Schmidt with a second pass whenever a column's norm falls below 1/sqrt(2)
+// Gram-Schmidt with a second pass whenever a column's norm falls below 1/sqrt(10)
 // of its value before projection, Givens rotations and the small least-squares
 // problems on the host in FP64.  One device->host copy per step (two when the
 // second pass runs) carries the Hessenberg column of every right-hand side.
@@ -523,6 +523,92 @@ __global__ void k_widen(long long n, const float2* __restrict__ v, double2* __re
   u[t] = make_double2(x.x, x.y);
 }
 
+// ---- several right-hand sides with an FP32 Krylov basis (vectors [n][R])
+// part[j][chunk][r] = conj(V_j) . w over the chunk's rows, FP32 products and
+// per-thread sums, FP64 sums across the CTA
+__global__ void k_gsr_dot(int J, long long n, int R, int rl, int nchunk, long long rows_per,
+                          const float2* __restrict__ V, long long ldv, const double2* __restrict__ w,
+                          double2* __restrict__ part) {
+  int j = blockIdx.y, chunk = blockIdx.x;
+  int a = threadIdx.x / R, r = threadIdx.x % R;
+  float ax = 0.f, ay = 0.f;
+  if (a < rl) {
+    const float2* v = V + (size_t)j * ldv;
+    long long i0 = chunk * rows_per, i1 = min(n, i0 + rows_per);
+    for (long long i = i0 + a; i < i1; i += rl) {
+      float2 x = v[i * R + r];
+      double2 yd = w[i * R + r];
+      float2 y = make_float2((float)yd.x, (float)yd.y);
+      ax += x.x * y.x + x.y * y.y;
+      ay += x.x * y.y - x.y * y.x;
+    }
+  }
+  __shared__ double2 red[256];
+  red[threadIdx.x] = make_double2(ax, ay);
+  __syncthreads();
+  if (a == 0 && r < R) {
+    double2 s = make_double2(0, 0);
+    for (int q = 0; q < rl; ++q) {
+      double2 t = red[q * R + r];
+      s.x += t.x;
+      s.y += t.y;
+    }
+    part[((size_t)j * nchunk + chunk) * R + r] = s;
+  }
+}
+
+// h[j][r] (FP64) and hf[j][r] (FP32) = sum over chunks of part[j][chunk][r]
+__global__ void k_gsr_final(int J, int R, int nchunk, const double2* __restrict__ part, double2* __restrict__ h,
+                            float2* __restrict__ hf) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= J * R) return;
+  int j = t / R, r = t % R;
+  double2 s = make_double2(0, 0);
+  for (int c = 0; c < nchunk; ++c) {
+    double2 v = part[((size_t)j * nchunk + c) * R + r];
+    s.x += v.x;
+    s.y += v.y;
+  }
+  h[t] = s;
+  hf[t] = make_float2((float)s.x, (float)s.y);
+}
+
+// w[i][r] += sign * sum_j V_j[i][r] hf[j][r] (FP32 products and sums)
+__global__ void k_gsr_axpy(int J, long long n, int R, const float2* __restrict__ V, long long ldv,
+                           const float2* __restrict__ hf, double2* __restrict__ w, double sign) {
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= n * R) return;
+  int r = (int)(t % R);
+  float ax = 0.f, ay = 0.f, bx = 0.f, by = 0.f;
+  int j = 0;
+  for (; j + 2 <= J; j += 2) {
+    float2 v0 = V[(size_t)j * ldv + t], v1 = V[(size_t)(j + 1) * ldv + t];
+    float2 c0 = hf[(size_t)j * R + r], c1 = hf[(size_t)(j + 1) * R + r];
+    ax += v0.x * c0.x - v0.y * c0.y;
+    ay += v0.x * c0.y + v0.y * c0.x;
+    bx += v1.x * c1.x - v1.y * c1.y;
+    by += v1.x * c1.y + v1.y * c1.x;
+  }
+  if (j < J) {
+    float2 v0 = V[(size_t)j * ldv + t], c0 = hf[(size_t)j * R + r];
+    ax += v0.x * c0.x - v0.y * c0.y;
+    ay += v0.x * c0.y + v0.y * c0.x;
+  }
+  double2 o = w[t];
+  o.x += sign * ((double)ax + (double)bx);
+  o.y += sign * ((double)ay + (double)by);
+  w[t] = o;
+}
+
+// v[i][r] = (float) (a[r] w[i][r])
+__global__ void k_narrow_scale_r(long long n, int R, const double2* __restrict__ a, const double2* __restrict__ w,
+                                 float2* __restrict__ v) {
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= n * R) return;
+  double2 x = w[t], c = a[t % R];
+  v[t] = make_float2((float)(c.x * x.x - c.y * x.y), (float)(c.x * x.y + c.y * x.x));
+}
+
 static inline int g32_nseg(long long n) { return (int)((n + G32_SEG - 1) / G32_SEG); }
 
 // h = V^H w (FP64 d_h and FP32 d_hf copies) and optionally ||w||^2
@@ -660,10 +746,27 @@ static float elapsed_s(cudaEvent_t a, cudaEvent_t b) {
 static int gs_pass(Ctx* c, Work& W, int J, long long n, int R, long long ld, double2* d_h, float2* d_hf,
                    double2* d_n0, double2* d_nr, cudaStream_t st) {
   int rc;
-  if (W.f32) {
+  if (W.f32 && R == 1) {
     rc = gs32_dot(c, J, n, (const float2*)W.V, ld, W.w, d_h, d_hf, d_n0, W.part, st);
     if (rc) return rc;
     return gs32_axpy(c, J, n, (const float2*)W.V, ld, d_hf, W.w, -1.0, d_nr, W.part, st);
+  }
+  if (W.f32) {
+    if (d_n0) {
+      rc = multidot_dev(c, 1, n, R, W.w, 0, W.w, d_n0, W.part, st);
+      if (rc) return rc;
+    }
+    int rl, nchunk;
+    long long per;
+    chunking(n, R, &rl, &nchunk, &per);
+    dim3 g(nchunk, J);
+    k_gsr_dot<<<g, 256, 0, st>>>(J, n, R, rl, nchunk, per, (const float2*)W.V, ld, W.w, W.part);
+    SMR_LAUNCH(c);
+    k_gsr_final<<<(J * R + 127) / 128, 128, 0, st>>>(J, R, nchunk, W.part, d_h, d_hf);
+    SMR_LAUNCH(c);
+    k_gsr_axpy<<<(unsigned)((ld + 255) / 256), 256, 0, st>>>(J, n, R, (const float2*)W.V, ld, d_hf, W.w, -1.0);
+    SMR_LAUNCH(c);
+    return multidot_dev(c, 1, n, R, W.w, 0, W.w, d_nr, W.part, st);
   }
   const double2* V = (const double2*)W.V;
   if (R == 1) {
@@ -730,15 +833,16 @@ static int gmres_core(Ctx* c, int R, int prec, int precond, const double2* rhs, 
   double2* dn0 = dnr + R;                                   // ||w||^2   [R]
   double2* dsc = W.coef + (size_t)3 * (m + 1) * R;          // scale     [R]
   float2* dh1f = W.coef_f;
-  float2* dh2f = W.coef_f + (m + 1);
-  float2* dyf = W.coef_f + 2 * (m + 1);
+  float2* dh2f = W.coef_f + (size_t)(m + 1) * R;
+  float2* dyf = W.coef_f + (size_t)2 * (m + 1) * R;
   // host Hessenberg storage per column (rotated), rotations, rhs g
   std::vector<std::complex<double>> H((size_t)(m + 1) * m * R), g((size_t)(m + 1) * R);
   std::vector<std::complex<double>> cs((size_t)m * R), sn((size_t)m * R);
   std::vector<double2> hbuf((size_t)(2 * (m + 1) + 2) * R);
   // v_j <- a * src (per column a[r] on the device at dsc)
   auto store_basis = [&](int j, const double2* src) -> int {
-    if (W.f32) k_narrow_scale<<<nb, 256, 0, st>>>(n, dsc, src, (float2*)Vj(j));
+    if (W.f32 && R == 1) k_narrow_scale<<<nb, 256, 0, st>>>(n, dsc, src, (float2*)Vj(j));
+    else if (W.f32) k_narrow_scale_r<<<nb, 256, 0, st>>>(n, R, dsc, src, (float2*)Vj(j));
     else k_scale<<<nb, 256, 0, st>>>(n, R, dsc, src, (double2*)Vj(j));
     SMR_LAUNCH(c);
     return SMR_OK;
@@ -770,7 +874,7 @@ static int gmres_core(Ctx* c, int R, int prec, int precond, const double2* rhs, 
       // every product of the solve)
       const double2* vj = (const double2*)Vj(j);
       if (W.f32) {
-        k_widen<<<nb, 256, 0, st>>>(n, (const float2*)Vj(j), W.u);
+        k_widen<<<nb, 256, 0, st>>>(ld, (const float2*)Vj(j), W.u);
         SMR_LAUNCH(c);
         vj = W.u;
       }
@@ -878,10 +982,16 @@ static int gmres_core(Ctx* c, int R, int prec, int precond, const double2* rhs, 
     if (jmax > 0) {
       SMR_CUDA(c, cudaMemsetAsync(W.w, 0, ld * sizeof(double2), st));
       if (W.f32) {
-        std::vector<float2> yf(jmax);
-        for (int i = 0; i < jmax; ++i) yf[i] = make_float2((float)ycoef[i].x, (float)ycoef[i].y);
-        SMR_CUDA(c, cudaMemcpyAsync(dyf, yf.data(), jmax * sizeof(float2), cudaMemcpyHostToDevice, st));
-        rc = gs32_axpy(c, jmax, n, (const float2*)W.V, ld, dyf, W.w, 1.0, nullptr, nullptr, st);
+        std::vector<float2> yf((size_t)jmax * R);
+        for (size_t i = 0; i < yf.size(); ++i) yf[i] = make_float2((float)ycoef[i].x, (float)ycoef[i].y);
+        SMR_CUDA(c, cudaMemcpyAsync(dyf, yf.data(), yf.size() * sizeof(float2), cudaMemcpyHostToDevice, st));
+        if (R == 1) {
+          rc = gs32_axpy(c, jmax, n, (const float2*)W.V, ld, dyf, W.w, 1.0, nullptr, nullptr, st);
+        } else {
+          k_gsr_axpy<<<(unsigned)((ld + 255) / 256), 256, 0, st>>>(jmax, n, R, (const float2*)W.V, ld, dyf, W.w,
+                                                                 1.0);
+          rc = cudaGetLastError() == cudaSuccess ? SMR_OK : SMR_E_CUDA;
+        }
       } else {
         SMR_CUDA(c, cudaMemcpyAsync(W.coef, ycoef.data(), (size_t)jmax * R * sizeof(double2),
                                     cudaMemcpyHostToDevice, st));
@@ -909,11 +1019,11 @@ int solve(Ctx* c, int R, const double2* b, double2* x, const smr_solve_opts* o, 
   int maxit = o->maxit > 0 ? o->maxit : 2000;
   int m = (o->restart > 0) ? std::min(o->restart, maxit) : maxit;
   // cap the Krylov dimension by device memory (60% of what is free); the
-  // FP32 operator with one right-hand side keeps its basis in FP32
+  // FP32 operator keeps its basis in FP32
   size_t freeb = 0, totb = 0;
   cudaMemGetInfo(&freeb, &totb);
   Work W;
-  W.f32 = (o->precision == SMR_PREC_FP32 && R == 1 && n % 2 == 0);
+  W.f32 = (o->precision == SMR_PREC_FP32 && n % 2 == 0);
   size_t eb = W.f32 ? sizeof(float2) : sizeof(double2);
   double per = (double)ld * eb;
   int mcap = (int)std::max(2.0, 0.6 * (double)freeb / per - 4);
@@ -929,7 +1039,7 @@ int solve(Ctx* c, int R, const double2* b, double2* x, const smr_solve_opts* o, 
             cudaMalloc((void**)&W.w, ld * sizeof(double2)) == cudaSuccess &&
             cudaMalloc((void**)&W.t, ld * sizeof(double2)) == cudaSuccess &&
             cudaMalloc((void**)&W.coef, (size_t)4 * (m + 2) * R * sizeof(double2)) == cudaSuccess &&
-            cudaMalloc((void**)&W.coef_f, (size_t)3 * (m + 2) * sizeof(float2)) == cudaSuccess &&
+            cudaMalloc((void**)&W.coef_f, (size_t)3 * (m + 2) * R * sizeof(float2)) == cudaSuccess &&
             cudaMalloc((void**)&W.part, part_elems(n, R, m + 2) * sizeof(double2)) == cudaSuccess;
   for (int q = 0; q < 6 && ok; ++q) ok = cudaEventCreate(&W.ev[q]) == cudaSuccess;
   if (!ok) {
