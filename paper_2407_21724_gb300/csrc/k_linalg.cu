@@ -690,7 +690,8 @@ int col_norms(Ctx* c, long long n, int R, const double2* v, double* norms_host, 
   std::vector<double2> h(R);
   int rc = multidot(c, 1, n, R, v, 0, v, h.data(), st);
   if (rc) return rc;
-  for (int r = 0; r < R; ++r) norms_host[r] = std::sqrt(std::max(0.0, h[r].x));
+  // NaN stays NaN (std::max(0.0, NaN) would hide it)
+  for (int r = 0; r < R; ++r) norms_host[r] = std::isnan(h[r].x) ? h[r].x : std::sqrt(std::max(0.0, h[r].x));
   return SMR_OK;
 }
 
@@ -921,7 +922,8 @@ static int gmres_core(Ctx* c, int R, int prec, int precond, const double2* rhs, 
       std::vector<double2> inv(R);
       std::vector<double> hn(R);
       for (int r = 0; r < R; ++r) {
-        hn[r] = std::sqrt(std::max(0.0, hbuf[(size_t)2 * (m + 1) * R + r].x));
+        const double n2 = hbuf[(size_t)2 * (m + 1) * R + r].x;
+        hn[r] = std::isnan(n2) ? n2 : std::sqrt(std::max(0.0, n2));
         inv[r] = make_double2(hn[r] > 0 ? 1.0 / hn[r] : 0.0, 0);
       }
       SMR_CUDA(c, cudaMemcpyAsync(dsc, inv.data(), R * sizeof(double2), cudaMemcpyHostToDevice, st));
@@ -1081,6 +1083,14 @@ int solve(Ctx* c, int R, const double2* b, double2* x, const smr_solve_opts* o, 
       }
       rc = col_norms(c, n, R, r, rn.data(), st);
       if (rc) break;
+      bool finite = true;
+      for (int q = 0; q < R; ++q) finite = finite && std::isfinite(rn[q]);
+      if (!finite) {
+        c->err = "NaN or Inf in the residual (right-hand side or initial guess)";
+        rel.assign(R, std::nan(""));
+        rc = SMR_E_NAN;
+        break;
+      }
       bool all = true;
       std::vector<double> tc(R);
       rel.assign(R, 0.0);
@@ -1118,7 +1128,7 @@ int solve(Ctx* c, int R, const double2* b, double2* x, const smr_solve_opts* o, 
     stats->seconds_precond = W.t_pc;
     stats->seconds_orth = W.t_or;
     double mx = 0;
-    for (double v : rel) mx = std::max(mx, v);
+    for (double v : rel) mx = (std::isnan(v) || std::isnan(mx)) ? std::nan("") : std::max(mx, v);
     stats->resid_true = mx;
     stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   }
