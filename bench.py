@@ -230,7 +230,7 @@ def train_learned(smr, workloads, n_arrays, dev, n_side=20, width=256, steps=150
         p = smr.smr_info(ctx)["p"]
         smr.smr_nn_init(ctx, width=8, seed=0)          # features need an initialised network
         f = torch.empty((p, 448), dtype=torch.float32, device=dev)
-        t = torch.empty((p, 128), dtype=torch.float32, device=dev)
+        t = torch.empty((p, 4 * smr.smr_info(ctx)["n_psi"]), dtype=torch.float32, device=dev)
         smr.smr_nn_features(ctx, kh, pol, f)
         smr.smr_nn_targets(ctx, kh, x, scale, t)
         feats.append(f)

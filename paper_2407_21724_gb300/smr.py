@@ -102,6 +102,7 @@ _SIGS = {
     "smr_copy_near_block": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_int, _D]),
     "smr_copy_level": (C.c_int, [_P, C.c_int, C.c_int, _D, C.c_size_t]),
     "smr_set_tensor_cores": (C.c_int, [_P, C.c_int]),
+    "smr_add_shape_sampled": (C.c_int, [_P, C.c_int, _D, _D, C.c_int, C.c_int, _D, _D, C.POINTER(C.c_int)]),
     "smr_nn_precond": (C.c_int, [_P, _D, _D, C.c_double, _P, _P]),
     "smr_autotune": (C.c_int, [_P, C.c_int, C.c_int, _P]),
     "smr_sync": (C.c_int, [_P, _P]),
@@ -219,8 +220,7 @@ def scene_from_arrays(ws, **opts):
     """One context holding several workload dicts as independent arrays."""
     w0 = ws[0]
     ctx = smr_create(pitch=w0["pitch"], **opts)
-    for (a, npp, npl) in w0["shapes"]:
-        smr_add_sphere(ctx, a, npp, npl)
+    add_shapes(ctx, w0["shapes"])
     C_ = np.concatenate([w["centres"] for w in ws])
     S_ = np.concatenate([w["shape_ids"] for w in ws])
     A_ = np.concatenate([np.full(len(w["centres"]), i, dtype=np.int32) for i, w in enumerate(ws)])
@@ -387,12 +387,20 @@ def smr_nn_set_params(ctx, params):
     _check(ctx, lib().smr_nn_set_params(ctx, p.ctypes.data_as(C.POINTER(C.c_float)), p.size))
 
 
+def _need(t, n, what):
+    if hasattr(t, "numel") and t.numel() != n:
+        raise ValueError(f"{what}: {t.numel()} elements given, {n} required")
+
+
 def smr_nn_features(ctx, khat, pol, feat, stream=None):
+    _need(feat, smr_info(ctx)["p"] * 448, "features [p][448]")
     kh, pl, pv = _inc(khat, pol)
     _check(ctx, lib().smr_nn_features(ctx, _dptr(kh), _dptr(pv), _fptr(feat), _stream(stream, feat)))
 
 
 def smr_nn_targets(ctx, khat, x, scale, tgt, stream=None):
+    i = smr_info(ctx)
+    _need(tgt, i["p"] * 4 * i["n_psi"], "targets [p][4 n_psi]")
     kh = np.ascontiguousarray(khat, dtype=np.float64).reshape(-1, 3)
     _check(ctx, lib().smr_nn_targets(ctx, _dptr(kh), _ptr(x), float(scale), _fptr(tgt), _stream(stream, x)))
 
@@ -450,10 +458,34 @@ def smr_copy_level(ctx, level, kind, R=1):
     return out
 
 
+def add_shapes(ctx, shapes):
+    """Register shapes: (radius, n_perp, n_par) tuples are closed-form spheres;
+    objects with r, w, psi, div, Zs, n_perp, n_par are shapes given as data."""
+    for sh in shapes:
+        if hasattr(sh, "psi"):
+            smr_add_shape_sampled(ctx, sh.r, sh.w, sh.n_perp, sh.n_par, sh.psi, sh.div, sh.Zs)
+        else:
+            a, npp, npl = sh
+            smr_add_sphere(ctx, a, npp, npl)
+
+
+def smr_add_shape_sampled(ctx, pts, wts, n_perp, n_par, psi, div, self_block):
+    """pts (Q,3), wts (Q,), psi (n_psi,Q,3), div (n_psi,Q), self_block
+    (2 n_psi, 2 n_psi) complex; returns the shape id."""
+    P = np.ascontiguousarray(pts, dtype=np.float64).reshape(-1, 3)
+    W = np.ascontiguousarray(wts, dtype=np.float64).ravel()
+    M = np.ascontiguousarray(np.concatenate([np.asarray(psi, dtype=np.float64),
+                                             np.asarray(div, dtype=np.float64)[..., None]], axis=2))
+    Z = np.ascontiguousarray(self_block, dtype=np.complex128)
+    sid = C.c_int()
+    _check(ctx, lib().smr_add_shape_sampled(ctx, P.shape[0], _dptr(P), _dptr(W), n_perp, n_par, _dptr(M),
+                                            _dptr(Z.view(np.float64)), C.byref(sid)))
+    return sid.value
+
+
 def scene_from_workload(w, **opts):
     """Create a context and set the scene of a workload dict (workloads.make)."""
     ctx = smr_create(pitch=w["pitch"], **opts)
-    for (a, npp, npl) in w["shapes"]:
-        smr_add_sphere(ctx, a, npp, npl)
+    add_shapes(ctx, w["shapes"])
     smr_set_scene(ctx, w["centres"], w["shape_ids"], w["eps_in"])
     return ctx
