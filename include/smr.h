@@ -91,6 +91,28 @@ const char* smr_last_error(const smr_ctx* ctx);
  * *shape_id receives the new id (0, 1, ...).  Must precede smr_set_scene. */
 int smr_add_sphere(smr_ctx* ctx, double radius, int n_perp, int n_par, int* shape_id);
 
+/* Register a shape given as data instead of in closed form: the form in
+ * which the static modes of a meshed particle (Sec. V, stages ii and iv: RWG
+ * star/loop eigenfunctions mapped to the surface) reach the solver.  Host
+ * inputs, copied:
+ *   pts[n_q][3]   surface quadrature points relative to the particle centre
+ *   wts[n_q]      their weights (area elements; >= 0)
+ *   modes[n_psi][n_q][4]  per mode and point the tangential field (x, y, z)
+ *                 and its surface divergence, n_psi = n_perp + n_par, the
+ *                 n_perp transverse modes first
+ *   self_block[2 n_psi][2 n_psi]  complex (re, im interleaved), row-major:
+ *                 Z_s of Eq. 16 with mu = nu for the media that will be
+ *                 passed to smr_set_scene, [electric; magnetic] as in the
+ *                 unknown vector.
+ * Patterns (Eq. 26), neighbour blocks, right-hand sides and fields are then
+ * computed from these samples exactly as for the closed-form spheres.
+ * 1 <= n_q <= 1024; all shapes of a context share n_psi.  The bounding radius
+ * of the points must stay below half the pitch.  Must precede smr_set_scene.
+ * The paper assembles these data from a surface mesh; there is no separate
+ * counterpart call. */
+int smr_add_shape_sampled(smr_ctx* ctx, int n_q, const double* pts, const double* wts, int n_perp, int n_par,
+                          const double* modes, const double* self_block, int* shape_id);
+
 /* Set the scene: p particles with host centres[p][3] and host shape_ids[p],
  * inner medium (eps_in, mu_in) and background (eps_out, mu_out), each a
  * complex relative value {re, im}.  Centres must lie one per cell of a square

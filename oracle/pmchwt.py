@@ -35,6 +35,33 @@ class Medium:
             self.zeta = float(np.real(self.zeta))
 
 
+class SampledShape:
+    """A shape given as data rather than in closed form (the form in which a
+    meshed particle's static modes reach the solver, Sec. V stages ii-iv):
+    surface quadrature points r (Q,3) relative to the particle centre and
+    weights w (Q,), the N_perp + N_par mode fields psi (N_psi,Q,3) and surface
+    divergences div (N_psi,Q) at those points, and the self block Z_s
+    (2 N_psi, 2 N_psi) for the scene's media (Eq. 16 with mu = nu)."""
+
+    def __init__(self, r, w, psi, div, Zs, n_perp, n_par):
+        self.r = np.asarray(r, dtype=float).reshape(-1, 3)
+        self.w = np.asarray(w, dtype=float).ravel()
+        self.psi = np.asarray(psi, dtype=float)
+        self.div = np.asarray(div, dtype=float)
+        self.Zs = np.asarray(Zs, dtype=complex)
+        self.n_perp, self.n_par = int(n_perp), int(n_par)
+        assert self.psi.shape == (self.n_psi, self.w.size, 3) and self.div.shape == (self.n_psi, self.w.size)
+        assert self.Zs.shape == (2 * self.n_psi, 2 * self.n_psi)
+
+    @property
+    def n_psi(self):
+        return self.n_perp + self.n_par
+
+    @property
+    def a(self):
+        return float(np.max(np.linalg.norm(self.r, axis=1)))
+
+
 class Scene:
     """p particles: centres (p,3), shape ids (p,), shapes, inner/outer media,
     and the surface rule (n_theta, n_phi) used for every surface integral."""
@@ -43,7 +70,7 @@ class Scene:
                  mu_in=1.0, mu_out=1.0, lam=1.0, n_theta=16, n_phi=32):
         self.centres = np.asarray(centres, dtype=float).reshape(-1, 3)
         self.shape_ids = np.asarray(shape_ids, dtype=int).ravel()
-        self.shapes = [s if isinstance(s, SphereShape) else SphereShape(*s) for s in shapes]
+        self.shapes = [s if isinstance(s, (SphereShape, SampledShape)) else SphereShape(*s) for s in shapes]
         self.inner = Medium(eps_in, mu_in, lam)
         self.outer = Medium(eps_out, mu_out, lam)
         self.n_theta, self.n_phi = n_theta, n_phi
@@ -64,14 +91,19 @@ class Scene:
         """(rule, psi, div) of shape s on the scene's surface rule."""
         if s not in self._rules:
             sh = self.shapes[s]
-            rule = sphere_rule(sh.a, self.n_theta, self.n_phi)
-            psi, div = eval_modes(sh, rule)
-            self._rules[s] = (rule, psi, div)
+            if isinstance(sh, SampledShape):
+                self._rules[s] = ({'r': sh.r, 'w': sh.w}, sh.psi, sh.div)
+            else:
+                rule = sphere_rule(sh.a, self.n_theta, self.n_phi)
+                psi, div = eval_modes(sh, rule)
+                self._rules[s] = (rule, psi, div)
         return self._rules[s]
 
     def self_block(self, s):
-        return self_block(self.shapes[s], self.outer.k, self.outer.zeta,
-                          self.inner.k, self.inner.zeta)
+        sh = self.shapes[s]
+        if isinstance(sh, SampledShape):
+            return sh.Zs
+        return self_block(sh, self.outer.k, self.outer.zeta, self.inner.k, self.inner.zeta)
 
 
 def exterior_TK(scene, s_m, c_m, s_n, c_n):

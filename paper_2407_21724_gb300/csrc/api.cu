@@ -379,7 +379,7 @@ int set_scene(Ctx* c, int p, const double* centres, const int* shape_ids, const 
   }
   // check no sphere overlaps its neighbours on the lattice
   for (auto& s : c->shapes)
-    if (2 * s.a >= pitch) return fail(c, SMR_E_INVALID_ARG, "sphere diameter must be below the pitch");
+    if (2 * s.a >= pitch) return fail(c, SMR_E_INVALID_ARG, "particle diameter must be below the pitch");
   c->any_dshift = anyd;
   // ---- levels
   std::vector<int> bi(c->pi), bj(c->pj);
@@ -679,7 +679,54 @@ int smr_add_sphere(smr_ctx* h, double radius, int n_perp, int n_par, int* shape_
   Ctx* c = &h->c;
   if (!(radius > 0) || n_perp < 0 || n_par < 0 || n_perp + n_par < 1 || n_perp + n_par > 128)
     return fail(c, SMR_E_INVALID_ARG, "radius > 0 and 1 <= n_perp + n_par <= 128 required");
-  c->shapes.push_back(Shape{radius, n_perp, n_par});
+  Shape sh;
+  sh.a = radius;
+  sh.n_perp = n_perp;
+  sh.n_par = n_par;
+  c->shapes.push_back(sh);
+  if (shape_id) *shape_id = (int)c->shapes.size() - 1;
+  return SMR_OK;
+}
+
+int smr_add_shape_sampled(smr_ctx* h, int n_q, const double* pts, const double* wts, int n_perp, int n_par,
+                          const double* modes, const double* self_block, int* shape_id) {
+  if (!h) return SMR_E_INVALID_ARG;
+  Ctx* c = &h->c;
+  if (!pts || !wts || !modes || !self_block || n_q < 1 || n_q > 1024)
+    return fail(c, SMR_E_INVALID_ARG, "1 <= n_q <= 1024 and non-null points, weights, modes, self block required");
+  if (n_perp < 0 || n_par < 0 || n_perp + n_par < 1 || n_perp + n_par > 128)
+    return fail(c, SMR_E_INVALID_ARG, "1 <= n_perp + n_par <= 128 required");
+  Shape sh;
+  sh.n_perp = n_perp;
+  sh.n_par = n_par;
+  sh.sampled = true;
+  sh.nq = n_q;
+  int n = n_perp + n_par;
+  sh.rq.resize((size_t)n_q * 4);
+  double rmax = 0;
+  for (int q = 0; q < n_q; ++q) {
+    double r2 = 0;
+    for (int d = 0; d < 3; ++d) {
+      double v = pts[3 * q + d];
+      if (!std::isfinite(v)) return fail(c, SMR_E_INVALID_ARG, "non-finite quadrature point");
+      sh.rq[4 * q + d] = v;
+      r2 += v * v;
+    }
+    if (!(wts[q] >= 0) || !std::isfinite(wts[q])) return fail(c, SMR_E_INVALID_ARG, "weights must be finite and >= 0");
+    sh.rq[4 * q + 3] = wts[q];
+    rmax = std::max(rmax, std::sqrt(r2));
+  }
+  sh.a = rmax;
+  sh.modes.assign(modes, modes + (size_t)n * n_q * 4);
+  for (double v : sh.modes)
+    if (!std::isfinite(v)) return fail(c, SMR_E_INVALID_ARG, "non-finite mode sample");
+  sh.Z.resize((size_t)4 * n * n);
+  for (size_t i = 0; i < sh.Z.size(); ++i) {
+    sh.Z[i] = cd(self_block[2 * i], self_block[2 * i + 1]);
+    if (!std::isfinite(sh.Z[i].real()) || !std::isfinite(sh.Z[i].imag()))
+      return fail(c, SMR_E_INVALID_ARG, "non-finite self block");
+  }
+  c->shapes.push_back(std::move(sh));
   if (shape_id) *shape_id = (int)c->shapes.size() - 1;
   return SMR_OK;
 }

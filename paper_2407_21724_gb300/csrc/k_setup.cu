@@ -15,10 +15,19 @@ int build_modes(Ctx* c) {
   std::vector<double> x, w;
   hm::gauss_legendre(c->opts.n_theta, x, w);
   int nt = c->opts.n_theta, np = c->opts.n_phi;
-  c->Q = nt * np;
-  c->rule_th.resize(c->Q);
-  c->rule_ph.resize(c->Q);
-  c->rule_w1.resize(c->Q);
+  // one point count for every shape: the sphere rule's and the largest
+  // sampled shape's (shorter rules are padded with zero-weight points)
+  bool any_sphere = false;
+  int qmax = 0;
+  for (const Shape& sh : c->shapes) {
+    if (sh.sampled) qmax = std::max(qmax, sh.nq);
+    else any_sphere = true;
+  }
+  c->Q = std::max(any_sphere ? nt * np : 0, qmax);
+  const int Qs = nt * np;
+  c->rule_th.resize(Qs);
+  c->rule_ph.resize(Qs);
+  c->rule_w1.resize(Qs);
   for (int i = 0; i < nt; ++i)
     for (int j = 0; j < np; ++j) {
       int q = i * np + j;
@@ -30,11 +39,28 @@ int build_modes(Ctx* c) {
   std::vector<double> modes((size_t)S * n * Q * 4, 0.0), rq((size_t)S * Q * 4);
   for (int s = 0; s < S; ++s) {
     const Shape& sh = c->shapes[s];
+    if (sh.sampled) {
+      for (int q = 0; q < Q; ++q) {                  // padding repeats point 0 with weight 0
+        const int qq = q < sh.nq ? q : 0;
+        double* R = &rq[((size_t)s * Q + q) * 4];
+        for (int d = 0; d < 3; ++d) R[d] = sh.rq[4 * qq + d];
+        R[3] = q < sh.nq ? sh.rq[4 * qq + 3] : 0.0;
+        for (int i = 0; i < n; ++i)
+          for (int d = 0; d < 4; ++d)
+            modes[(((size_t)s * n + i) * Q + q) * 4 + d] = q < sh.nq ? sh.modes[((size_t)i * sh.nq + q) * 4 + d] : 0.0;
+      }
+      continue;
+    }
     double a = sh.a;
     std::vector<int> lp, mp, kp, ll, ml, kl;
     hm::mode_list(sh.n_perp, lp, mp, kp);
     hm::mode_list(sh.n_par, ll, ml, kl);
     for (int q = 0; q < Q; ++q) {
+      if (q >= Qs) {                                 // padding of a longer sampled rule
+        double* R = &rq[((size_t)s * Q + q) * 4];
+        R[0] = a; R[1] = R[2] = R[3] = 0.0;
+        continue;
+      }
       double th = c->rule_th[q], ph = c->rule_ph[q];
       double st = std::sin(th), ct = std::cos(th), sp = std::sin(ph), cp = std::cos(ph);
       double rh[3] = {st * cp, st * sp, ct};
@@ -337,7 +363,8 @@ int build_near(Ctx* c) {
   std::vector<double2> selfT((size_t)S * bsz), invT((size_t)S * bsz);
   for (int s = 0; s < S; ++s) {
     std::vector<cd> Z;
-    sphere_self_block(c->shapes[s], c->k, c->zeta, c->k_in, c->zeta_in, Z);
+    if (c->shapes[s].sampled) Z = c->shapes[s].Z;
+    else sphere_self_block(c->shapes[s], c->k, c->zeta, c->k_in, c->zeta_in, Z);
     std::vector<cd> Zi = Z;
     if (!hm::invert(n2, Zi)) {
       c->err = "singular self block";

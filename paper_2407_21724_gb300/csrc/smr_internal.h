@@ -35,9 +35,15 @@ void mode_list(int n, std::vector<int>& l, std::vector<int>& m, std::vector<int>
 
 // ------------------------------------------------------------------ data
 struct Shape {
-  double a;
+  double a;                               // sphere radius, or bounding radius of a sampled shape
   int n_perp, n_par;
   int n_psi() const { return n_perp + n_par; }
+  // shape given as data (smr_add_shape_sampled): points and weights [nq][4],
+  // mode fields and divergences [n_psi][nq][4], self block [2n][2n]
+  bool sampled = false;
+  int nq = 0;
+  std::vector<double> rq, modes;
+  std::vector<cd> Z;
 };
 
 struct Level {

@@ -178,6 +178,38 @@ def test_autotuned_product_matches_oracle(rnd):
         smr.smr_autotune(rnd.ctx, prec)
         assert rel(rnd.gpu_matvec(x, prec), ref) < bar
 
+
+def test_sampled_shapes_match_oracle():
+    """Shapes given as data (smr_add_shape_sampled): a sphere on a rotated
+    16 x 32 rule, one on a rotated 12 x 24 rule (fewer points: padding) and
+    a closed-form sphere in one 6 x 5 random lattice.  FP64 product, right-
+    hand side and solve against the oracle with the same shape data; FP32
+    (tensor cores) at the FP32 bar."""
+    from tests.sampled import media, rotated_sphere
+    md = media(4.0)
+    shapes = [rotated_sphere(0.12, 8, 8, md, seed=1),
+              rotated_sphere(0.17, 8, 8, md, n_theta=12, n_phi=24, seed=2), (0.15, 8, 8)]
+    rng = np.random.default_rng(12)
+    C = workloads.lattice(6, 5)
+    w = dict(centres=C, shape_ids=rng.integers(0, 3, size=len(C)).astype(np.int32), shapes=shapes,
+             eps_in=4.0, pitch=0.5)
+    c = Case(w)
+    x = crandn(c.info["n_unknowns"], 13)
+    ref = c.M.matvec(x)
+    assert rel(c.gpu_matvec(x), ref) < TOL64
+    assert rel(c.gpu_matvec(x, smr.SMR_PREC_FP32), ref) < 2e-5
+    b = opm.rhs(c.sc, [0, 0, 1], [1, 0, 0])
+    bd = torch.empty_like(torch.from_numpy(b)).cuda()
+    kh, pol = workloads.incidence(0, 0, "x")
+    smr.smr_rhs_plane_waves(c.ctx, [kh], [pol], bd)
+    torch.cuda.synchronize()
+    assert rel(bd.cpu().numpy(), b) < 1e-12
+    xd = torch.zeros_like(bd)
+    rc, st = smr.smr_solve(c.ctx, bd, xd, tol=1e-6)
+    assert rc == 0
+    assert np.linalg.norm(b - c.M.matvec(xd.cpu().numpy())) / np.linalg.norm(b) <= 1.001e-6
+    smr.smr_destroy(c.ctx)
+
 @pytest.mark.parametrize("R", [5, 17, 64])
 def test_batched_columns_match_single(rnd, R):
     """R right-hand sides in one product: every column equals the single
@@ -297,6 +329,16 @@ def test_solve_restarted(rnd, prec):
     assert rc == 0, st
     res = np.linalg.norm(b - rnd.M.matvec(xd.cpu().numpy())) / np.linalg.norm(b)
     assert res <= 1.001e-5, (res, st)
+
+
+def test_solve_rejects_nan_initial_guess(c1):
+    """A NaN initial guess ends the solve with SMR_E_NAN (raised by the
+    binding), in both precisions; it never reports convergence."""
+    b = torch.from_numpy(opm.rhs(c1.sc, [0, 0, 1], [1, 0, 0])).cuda()
+    for prec in (smr.SMR_PREC_FP64, smr.SMR_PREC_FP32):
+        x = torch.full_like(b, float("nan"))
+        with pytest.raises(smr.SmrError):
+            smr.smr_solve(c1.ctx, b, x, tol=1e-4, precision=prec, use_x0=1)
 
 
 def test_far_field_and_cross_sections(c1):
