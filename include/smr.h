@@ -266,6 +266,20 @@ int smr_solve(smr_ctx* ctx, int R, const void* b, void* x, const smr_solve_opts*
 int smr_far_field(smr_ctx* ctx, int R, const void* x, int n_dir, const double* dirs,
                   void* F, void* stream);
 
+/* Scattering and extinction cross sections of each column of device
+ * coefficients x[N][R] (Sec. V outputs).  C_sca is the scattered power
+ * integral of |F|^2 over the unit sphere, taken with an n_theta-point
+ * Gauss-Legendre rule in cos(theta) times a 2 n_theta-point trapezoid rule
+ * in phi (exact for |F|^2 band-limited to degree 2 n_theta - 1).  C_ext
+ * follows the optical theorem at column r's incident direction:
+ * C_ext = -(4 pi / k) Im(conj(pol_r) . F(khat_r)) / |pol_r|^2.  Host inputs
+ * khat[R][3] (normalised here) and pol[R][3] complex (interleaved re, im),
+ * the plane wave column r was excited with; host outputs csca[R], cext[R]
+ * (units of length^2).  1 <= n_theta <= 2048; zero khat or pol gives
+ * SMR_E_INVALID_ARG.  Synchronises `stream`. */
+int smr_cross_sections(smr_ctx* ctx, int R, const void* x, int n_theta, const double* khat,
+                       const double* pol, double* csca, double* cext, void* stream);
+
 /* Scattered E and H at host points pts[n_pt][3] (outside every particle) by
  * direct surface quadrature with the full Green's dyadic:
  * E = -zeta L{J} + K{M}, H = -K{J} - L{M}/zeta.  Writes device

@@ -917,6 +917,74 @@ int smr_far_field(smr_ctx* h, int R, const void* x, int n_dir, const double* dir
   return rc;
 }
 
+int smr_cross_sections(smr_ctx* h, int R, const void* x, int n_theta, const double* khat,
+                       const double* pol, double* csca, double* cext, void* stream) {
+  if (!h || R <= 0 || !x || n_theta < 1 || n_theta > 2048 || !khat || !pol || !csca || !cext)
+    return SMR_E_INVALID_ARG;
+  Ctx* c = &h->c;
+  if (!check_scene(c)) return SMR_E_STATE;
+  cudaSetDevice(c->device);
+  // Gauss-Legendre in cos(theta) times the trapezoid rule in phi: exact for
+  // band-limited |F|^2 up to degree 2 n_theta - 1 in each.
+  std::vector<double> xg, wg;
+  hm::gauss_legendre(n_theta, xg, wg);
+  int n_phi = 2 * n_theta, n_sca = n_theta * n_phi;
+  std::vector<double> dirs(3 * ((size_t)n_sca + R)), W(n_sca);
+  for (int i = 0; i < n_theta; ++i) {
+    double st = std::sqrt(std::max(0.0, 1.0 - xg[i] * xg[i]));
+    for (int j = 0; j < n_phi; ++j) {
+      double ph = 2.0 * M_PI * j / n_phi;
+      size_t d = (size_t)i * n_phi + j;
+      dirs[3 * d] = st * std::cos(ph);
+      dirs[3 * d + 1] = st * std::sin(ph);
+      dirs[3 * d + 2] = xg[i];
+      W[d] = wg[i] * 2.0 * M_PI / n_phi;
+    }
+  }
+  std::vector<double2> pl(3 * (size_t)R);
+  for (int r = 0; r < R; ++r) {
+    const double* kr = khat + 3 * (size_t)r;
+    double nk = std::sqrt(kr[0] * kr[0] + kr[1] * kr[1] + kr[2] * kr[2]);
+    double np = 0;
+    for (int i = 0; i < 3; ++i) {
+      pl[3 * r + i] = make_double2(pol[6 * r + 2 * i], pol[6 * r + 2 * i + 1]);
+      np += pol[6 * r + 2 * i] * pol[6 * r + 2 * i] + pol[6 * r + 2 * i + 1] * pol[6 * r + 2 * i + 1];
+    }
+    if (!(nk > 0) || !(np > 0))
+      return fail(c, SMR_E_INVALID_ARG, "khat and pol must be non-zero for every column");
+    for (int i = 0; i < 3; ++i) dirs[3 * ((size_t)n_sca + r) + i] = kr[i] / nk;
+  }
+  double *d_dirs = nullptr, *d_w = nullptr, *d_cs = nullptr;
+  double2* d_pol = nullptr;
+  int rc;
+  if ((rc = upload(c, &d_dirs, dirs)) || (rc = upload(c, &d_w, W)) || (rc = upload(c, &d_pol, pl))) {
+    cudaFree(d_dirs);
+    cudaFree(d_w);
+    return rc;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<double> cs(2 * (size_t)R);
+  if (cudaMalloc((void**)&d_cs, cs.size() * sizeof(double)) != cudaSuccess) {
+    rc = fail(c, SMR_E_OOM, "cross sections: out of device memory");
+  } else {
+    rc = launch_cross_sections(c, R, (const double2*)x, n_sca, d_dirs, d_w, d_pol, d_cs, st);
+    cudaStreamSynchronize(st);
+    if (rc == SMR_OK &&
+        cudaMemcpy(cs.data(), d_cs, cs.size() * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+      rc = fail(c, SMR_E_CUDA, "cross sections: copy back failed");
+  }
+  cudaFree(d_dirs);
+  cudaFree(d_w);
+  cudaFree(d_pol);
+  cudaFree(d_cs);
+  if (rc == SMR_OK)
+    for (int r = 0; r < R; ++r) {
+      csca[r] = cs[2 * r];
+      cext[r] = cs[2 * r + 1];
+    }
+  return rc;
+}
+
 int smr_near_field(smr_ctx* h, int R, const void* x, int n_pt, const double* pts, void* EH, void* stream) {
   if (!h || R <= 0 || !x || n_pt <= 0 || !pts || !EH) return SMR_E_INVALID_ARG;
   Ctx* c = &h->c;

@@ -640,6 +640,59 @@ int launch_far_field(Ctx* c, int R, const double2* x, int nd, const double* d_di
   return SMR_OK;
 }
 
+// Cross sections from far-field amplitudes F[nd][3][R].  CTA per column r:
+// the first n_sca directions carry quadrature weights W (scattered power
+// over the sphere, Sec. V); direction n_sca + r is column r's own incident
+// direction, where the optical theorem gives the extinction.  cs[2r] = C_sca,
+// cs[2r + 1] = C_ext.
+__global__ void k_cross_sections(int n_sca, int R, const double2* __restrict__ F,
+                                 const double* __restrict__ W, const double2* __restrict__ pol,
+                                 double kw, double* __restrict__ cs) {
+  __shared__ double red[256];
+  int r = blockIdx.x;
+  double acc = 0;
+  for (int d = threadIdx.x; d < n_sca; d += blockDim.x) {
+    double e = 0;
+    for (int i = 0; i < 3; ++i) {
+      double2 f = F[((size_t)d * 3 + i) * R + r];
+      e += f.x * f.x + f.y * f.y;
+    }
+    acc += W[d] * e;
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    // Im(conj(e) . F) / |e|^2 at the forward direction.
+    double im = 0, nn = 0;
+    for (int i = 0; i < 3; ++i) {
+      double2 e = pol[(size_t)r * 3 + i];
+      double2 f = F[((size_t)(n_sca + r) * 3 + i) * R + r];
+      im += e.x * f.y - e.y * f.x;
+      nn += e.x * e.x + e.y * e.y;
+    }
+    cs[2 * r] = red[0];
+    cs[2 * r + 1] = -(4.0 * M_PI / kw) * im / nn;
+  }
+}
+
+int launch_cross_sections(Ctx* c, int R, const double2* x, int n_sca, const double* d_dirs,
+                          const double* d_w, const double2* d_pol, double* d_cs, cudaStream_t st) {
+  int nd = n_sca + R;
+  double2* F = nullptr;
+  SMR_CUDA(c, cudaMallocAsync((void**)&F, (size_t)nd * 3 * R * sizeof(double2), st));
+  int rc = launch_far_field(c, R, x, nd, d_dirs, F, st);
+  if (rc == SMR_OK) {
+    k_cross_sections<<<R, 256, 0, st>>>(n_sca, R, F, d_w, d_pol, c->k, d_cs);
+    SMR_LAUNCH(c);
+  }
+  SMR_CUDA(c, cudaFreeAsync(F, st));
+  return rc;
+}
+
 // ------------------------------------------------------------------ near field
 // CTA per particle mu (and right-hand side r): currents at the quadrature
 // points staged in shared memory; threads stride over field points and add

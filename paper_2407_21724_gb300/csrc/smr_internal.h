@@ -311,6 +311,8 @@ int launch_rhs_scratch(Ctx* c, int R, const double* d_khat, const double2* d_pol
                        double2* b, cudaStream_t st);
 int launch_far_field(Ctx* c, int R, const double2* x, int nd, const double* d_dirs,
                      double2* F, cudaStream_t st);
+int launch_cross_sections(Ctx* c, int R, const double2* x, int n_sca, const double* d_dirs,
+                          const double* d_w, const double2* d_pol, double* d_cs, cudaStream_t st);
 int launch_near_field(Ctx* c, int R, const double2* x, int npt, const double* d_pts,
                       double2* EH, cudaStream_t st);
 

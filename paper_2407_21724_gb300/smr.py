@@ -84,6 +84,7 @@ _SIGS = {
     "smr_solve": (C.c_int, [_P, C.c_int, _P, _P, C.POINTER(smr_solve_opts),
                             C.POINTER(smr_solve_stats), _P]),
     "smr_far_field": (C.c_int, [_P, C.c_int, _P, C.c_int, _D, _P, _P]),
+    "smr_cross_sections": (C.c_int, [_P, C.c_int, _P, C.c_int, _D, _D, _D, _D, _P]),
     "smr_near_field": (C.c_int, [_P, C.c_int, _P, C.c_int, _D, _P, _P]),
     "smr_profile_matvec": (C.c_int, [_P, C.c_int, _P, _P, C.c_int, C.POINTER(smr_launch_t), C.c_int,
                                      C.POINTER(C.c_int), _P]),
@@ -328,6 +329,21 @@ def smr_far_field(ctx, x, dirs, F, R=None, stream=None):
     d = np.ascontiguousarray(dirs, dtype=np.float64).reshape(-1, 3)
     R = R if R is not None else _R(x, smr_info(ctx)["n_unknowns"])
     _check(ctx, lib().smr_far_field(ctx, R, _ptr(x), d.shape[0], _dptr(d), _ptr(F), _stream(stream, x)))
+
+
+def smr_cross_sections(ctx, x, khat, pol, n_theta=48, R=None, stream=None):
+    """(C_sca[R], C_ext[R]) for plane-wave excitations khat[R][3], pol[R][3]."""
+    R = R if R is not None else _R(x, smr_info(ctx)["n_unknowns"])
+    kh = np.ascontiguousarray(khat, dtype=np.float64).reshape(-1, 3)
+    pc = np.ascontiguousarray(pol, dtype=np.complex128).reshape(-1, 3)
+    if kh.shape[0] != R or pc.shape[0] != R:
+        raise ValueError(f"khat and pol need {R} rows, got {kh.shape[0]} and {pc.shape[0]}")
+    pv = np.ascontiguousarray(pc.view(np.float64))
+    csca = np.zeros(R)
+    cext = np.zeros(R)
+    _check(ctx, lib().smr_cross_sections(ctx, R, _ptr(x), int(n_theta), _dptr(kh), _dptr(pv),
+                                         _dptr(csca), _dptr(cext), _stream(stream, x)))
+    return csca, cext
 
 
 def smr_near_field(ctx, x, pts, EH, R=None, stream=None):

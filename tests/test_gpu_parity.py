@@ -352,6 +352,27 @@ def test_far_field_and_cross_sections(c1):
     smr.smr_far_field(c1.ctx, xd, d, F)
     torch.cuda.synchronize()
     assert rel(F.cpu().numpy().reshape(40, 3), opm.far_field(c1.sc, x, d)) < 1e-12
+    # Two columns: the converged scattering solution, and an arbitrary
+    # coefficient vector with its own (unnormalised) direction and complex
+    # polarisation, so both sums and the per-column forward direction count.
+    y = crandn(c1.info["n_unknowns"], 12) * 0.3
+    X = torch.from_numpy(np.ascontiguousarray(np.stack([x, y], axis=1))).cuda()
+    khat = np.array([[0.0, 0.0, 1.0], [1.0, -2.0, 0.5]])
+    pol = np.array([[1.0, 0, 0], [0.3 + 0.2j, 0.1j, -0.4]])
+    for nt in (1, 9, 24):
+        cs, ce = smr.smr_cross_sections(c1.ctx, X, khat, pol, n_theta=nt)
+        for r, v in enumerate((x, y)):
+            ws = opm.scattering_cross_section(c1.sc, v, nt)
+            we = opm.extinction_cross_section(c1.sc, v, khat[r], pol[r])
+            assert abs(cs[r] - ws) <= 1e-12 * abs(ws), (nt, r, cs[r], ws)
+            assert abs(ce[r] - we) <= 1e-12 * max(abs(we), abs(ws)), (nt, r, ce[r], we)
+    # Lossless particles at convergence: extinction equals scattering once
+    # 24 x 48 directions resolve |F|^2.
+    assert abs(cs[0] - ce[0]) < 1e-4 * cs[0]
+    with pytest.raises(smr.SmrError):
+        smr.smr_cross_sections(c1.ctx, X, khat, np.zeros((2, 3)), n_theta=8)
+    with pytest.raises(smr.SmrError):
+        smr.smr_cross_sections(c1.ctx, X, khat, pol, n_theta=0)
 
 
 def test_near_field(c1):
