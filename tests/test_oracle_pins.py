@@ -357,3 +357,45 @@ def test_gmres_matches_direct_solve(mixed5):
     assert np.linalg.norm(x - xd) / np.linalg.norm(xd) < 1e-6
     x2, info2 = gmres(lambda v: Z @ v, b, precond=block_diag_precond(sc), tol=1e-8, restart=7)
     assert info2['resid_true'] <= 1e-8
+
+
+def _reciprocity_gap(M, sc, seed=1):
+    """|u^T A v - (Dv)^T A (Du)| / |u^T A v| for the operator M.matvec."""
+    rng = np.random.default_rng(seed)
+    n = sc.n_unknowns
+    u = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    v = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    D = np.ones(n)
+    D.reshape(sc.p, 2, sc.n_psi)[:, 1, :] = -1
+    a = u @ M.matvec(v)
+    return abs(a - (D * v) @ M.matvec(D * u)) / abs(a)
+
+
+def test_mlfma_is_reciprocal(mixed5):
+    """The MLFMA operator keeps the Galerkin symmetry Z^T = D Z D exactly (to
+    rounding), not only to FMM accuracy: receive patterns mirror the
+    aggregation patterns, each translation is symmetric in the box pair, and
+    anterpolation is the weighted adjoint of interpolation (Sec. IV).  This
+    holds at any array size, so it also checks products too large for the
+    oracle to compute."""
+    sc, _ = mixed5
+    assert _reciprocity_gap(ml.MLFMA(sc, 0.5, L0=10), sc) < 1e-12
+
+
+def test_mlfma_reciprocity_catches_unweighted_anterpolation(mixed5, monkeypatch):
+    """Plant plain transposed interpolation (quadrature weights dropped) in
+    the downward pass: the operator stays accurate to a few digits but loses
+    its symmetry by far more than rounding."""
+    sc, _ = mixed5
+
+    def plain_transpose(self, s, in_parent):
+        lev, par = self.tree.levels[s], self.tree.levels[s + 1]
+        gp = self.grids[s + 1]
+        out = np.zeros((len(lev['ij']), self.grids[s].K, 4), dtype=complex)
+        for c in range(len(lev['ij'])):
+            B = lev['parent'][c]
+            shift = np.exp(-1j * self.k * (gp.khat @ (lev['centre'][c] - par['centre'][B])))
+            out[c] = self.interp[s].T @ (shift[:, None] * in_parent[B])
+        return out
+    monkeypatch.setattr(ml.MLFMA, "downward", plain_transpose)
+    assert _reciprocity_gap(ml.MLFMA(sc, 0.5, L0=10), sc) > 1e-6
