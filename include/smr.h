@@ -185,14 +185,16 @@ int smr_matvec_parts(smr_ctx* ctx, int R, const void* x, void* y_near, void* y_f
 int smr_matvec_host(smr_ctx* ctx, int R, const double* x, double* y, int precision,
                     void* stream);
 
-/* Selects where the FP32 product runs its receive step (Eqs. 24-25) for one
+/* Selects where the FP32 product runs its dense contractions for one
  * right-hand side: 1 (default) on the tensor cores (tcgen05, split TF32: each
  * FP32 operand as a sum of two TF32 values, three MMAs per step, FP32
- * accumulation), 0 on the FP32 CUDA cores.  The paper has no counterpart
- * (it ran on a CPU); both give the FP32 product to FP32 accuracy.  The
- * tensor-core path needs 4 n_psi <= 128 and particles centred on their
- * lattice sites; otherwise the CUDA-core path runs.  Drops captured products
- * (smr_matvec_graph) so the next call captures the new choice. */
+ * accumulation), 0 on the FP32 CUDA cores.  The steps are aggregation and
+ * receive (Eqs. 24-26), which need particles centred on their lattice
+ * sites, and the near-field product (Eq. 16 blocks; pairs sharing a block
+ * form one GEMM, one launch per lattice offset).  All need 4 n_psi <= 128;
+ * otherwise the CUDA-core path runs.  The paper has no counterpart (it ran
+ * on a CPU); both give the FP32 product to FP32 accuracy.  Drops captured
+ * products (smr_matvec_graph) so the next call captures the new choice. */
 int smr_set_tensor_cores(smr_ctx* ctx, int enable);
 
 /* Times the launch variants of the product for one right-hand side in
@@ -201,8 +203,9 @@ int smr_set_tensor_cores(smr_ctx* ctx, int enable);
  * and the full or half direction chunk, 4x4 tiles, or threads along the
  * directions (levels of at most 1024 boxes); interpolation with the full or
  * half theta-row tile; anterpolation with the full or half column chunk or
- * 256-thread CTAs; for SMR_PREC_FP32 also aggregation and
- * receive on the tensor cores or the CUDA cores.  Each variant is timed over
+ * 256-thread CTAs; for SMR_PREC_FP32 also aggregation,
+ * receive and the near-field product on the tensor cores or the CUDA
+ * cores.  Each variant is timed over
  * three products (CUDA events around every launch, the fastest kept).  Uses
  * and overwrites the context's scratch buffers; drops captured products.
  * R must be 1. */

@@ -1273,6 +1273,7 @@ static int bs_impl(Ctx* c, int nrow, int R, const int* ptr, const int* col, cons
 }
 
 int run_near(Ctx* c, int R, int prec, const double2* x, double2* y, cudaStream_t st) {
+  if (prec == SMR_PREC_FP32 && tc_near_ok(c, R) && c->tune_tc_near != 0) return run_near_tc(c, x, y, st);
   double n2 = 2.0 * c->npsi, es = prec == SMR_PREC_FP64 ? 16 : 8;
   pbeg(c, st, "near", -1, 2.0 * c->p * n2 * R * 16 + (double)c->nblk * n2 * n2 * es,
        8.0 * n2 * n2 * c->nr_col.size() * R);

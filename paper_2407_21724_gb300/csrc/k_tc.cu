@@ -12,6 +12,12 @@
 // A B ~ A_hi B_hi + A_hi B_lo + A_lo B_hi (three MMAs per K step, FP32
 // accumulation in tensor memory).
 //
+// The near-field product (block-sparse, Eq. 16 blocks) runs through the same
+// kernel: pairs (mu, nu) that share a block are one GEMM with the block's real
+// form as A (rows (i, re/im) of y_mu, columns (j, re/im) of x_nu) and the
+// gathered x_nu rows as B; one launch per lattice offset, so every y row is
+// written by one CTA per launch.
+//
 // Operands live in shared memory in the K-major 128-byte-swizzled layout:
 // rows of 32 FP32 values (128 bytes), 8-row atoms of 1024 bytes, and the
 // 16-byte chunk q of row r stored at chunk q ^ (r mod 8).  The coefficient
@@ -37,7 +43,7 @@ constexpr int TC_BBYTES = TC_NP * TC_KC * 4;   // one spectrum chunk, one split:
 constexpr int TC_STAGE = 2 * TC_ABYTES + 2 * TC_BBYTES;
 constexpr int TC_NSTAGE = 3;
 constexpr int TC_PF = 3;                       // spectrum chunks of loads in flight per producer
-constexpr size_t TC_SMEM = (size_t)TC_NSTAGE * TC_STAGE + 1024 + 1024;   // + alignment, barriers, ids
+constexpr size_t TC_SMEM = (size_t)TC_NSTAGE * TC_STAGE + 1024 + 2048;   // + alignment, barriers, ids
 constexpr uint32_t TC_SPIN = 1u << 24;         // try_wait rounds before giving up
 
 __device__ __forceinline__ uint32_t saddr(const void* p) {
@@ -137,8 +143,11 @@ __device__ __forceinline__ void tmem_ld32(uint32_t t, float* v) {
 // is loaded two chunks ahead into registers, then split into TF32 hi / lo and
 // stored swizzled.  Thread 0 issues the 12 MMAs of a chunk (4 K steps x 3
 // products) and commits them to the stage's barrier.
-// A = per-shape coefficient images [nK][hi | lo][128 rows][32] (swizzled),
-// in0 = level-0 incoming spectra [p][K8] (FP32), y [p][M4] (FP64).
+// A = coefficient images [nK][hi | lo][128 rows][32] (swizzled), one per
+// tile (tshape); in0 = B rows [.][K8] (FP32), gathered by perm; y [.][M4]
+// (FP64), rows yperm.  Receive: A per shape, in0 the level-0 incoming
+// spectra, perm = yperm = particles.  Near: A per block, in0 = x (FP32),
+// perm = nu, yperm = mu.
 __device__ __forceinline__ void ld_chunk(const float* __restrict__ in0, int K8, const int* mus, int c, int tid,
                                          float4* r) {
 #pragma unroll
@@ -178,7 +187,8 @@ __device__ __forceinline__ void st_chunk(unsigned char* S, int tid, const float4
 __global__ void __launch_bounds__(288, 1) k_receive_tc(int nK, int K8, int M4, const int* __restrict__ tshape,
                                                        const int* __restrict__ tstart,
                                                        const int* __restrict__ tcount,
-                                                       const int* __restrict__ perm, const float* __restrict__ A,
+                                                       const int* __restrict__ perm,
+                                                       const int* __restrict__ yperm, const float* __restrict__ A,
                                                        const float* __restrict__ in0, double* __restrict__ y,
                                                        int accumulate, int* __restrict__ err) {
   extern __shared__ unsigned char smem_raw[];
@@ -187,7 +197,8 @@ __global__ void __launch_bounds__(288, 1) k_receive_tc(int nK, int K8, int M4, c
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm + TC_NSTAGE * TC_STAGE);
   uint32_t* slot = reinterpret_cast<uint32_t*>(bars + 3 * TC_NSTAGE);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(slot + 1);
-  int* mus = reinterpret_cast<int*>(slot + 4);                              // [TC_NP]
+  int* mus = reinterpret_cast<int*>(slot + 4);                              // [TC_NP] B rows
+  int* ys = mus + TC_NP;                                                    // [TC_NP] y rows
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int tile = blockIdx.x;
   const int s = tshape[tile], t0 = tstart[tile], cnt = tcount[tile];
@@ -206,7 +217,10 @@ __global__ void __launch_bounds__(288, 1) k_receive_tc(int nK, int K8, int M4, c
     *abort_flag = 0;
     mbar_fence_init();
   }
-  if (tid < TC_NP) mus[tid] = tid < cnt ? perm[t0 + tid] : -1;
+  if (tid < TC_NP) {
+    mus[tid] = tid < cnt ? perm[t0 + tid] : -1;
+    ys[tid] = tid < cnt ? yperm[t0 + tid] : -1;
+  }
   tc_before();
   __syncthreads();
   tc_after();
@@ -310,12 +324,12 @@ __global__ void __launch_bounds__(288, 1) k_receive_tc(int nK, int K8, int M4, c
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
           int col = g * 32 + j;
-          yo[j] = (accumulate && col < cnt) ? y[(size_t)mus[col] * M4 + row] : 0.0;
+          yo[j] = (accumulate && col < cnt) ? y[(size_t)ys[col] * M4 + row] : 0.0;
         }
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
           int col = g * 32 + j;
-          if (col < cnt) y[(size_t)mus[col] * M4 + row] = yo[j] + (double)v[j];
+          if (col < cnt) y[(size_t)ys[col] * M4 + row] = yo[j] + (double)v[j];
         }
       }
     }
@@ -535,6 +549,11 @@ __global__ void __launch_bounds__(288, 1) k_aggregate_tc(int nMT, int nKc, int K
   }
 }
 
+__global__ void k_x32(long long n, const double2* __restrict__ a, float2* __restrict__ b) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) b[i] = make_float2((float)a[i].x, (float)a[i].y);
+}
+
 // TF32 rounding on the host (round to nearest, ties away), for the split
 float tf32_host(float x) {
   uint32_t u;
@@ -652,7 +671,7 @@ int run_receive_tc(Ctx* c, const float2* in0, double2* y, bool accumulate, cudaS
   cudaFuncSetAttribute(k_receive_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
   k_receive_tc<<<(unsigned)c->tc_ntile, 288, TC_SMEM, st>>>(
       c->tc_nK, 8 * c->lev[0].K, 4 * c->npsi, c->d_tc_shape, c->d_tc_start, c->d_tc_count, c->d_tc_perm,
-      c->d_tc_rec, reinterpret_cast<const float*>(in0), reinterpret_cast<double*>(y), accumulate ? 1 : 0,
+      c->d_tc_perm, c->d_tc_rec, reinterpret_cast<const float*>(in0), reinterpret_cast<double*>(y), accumulate ? 1 : 0,
       c->d_tc_err);
   SMR_LAUNCH(c);
   return SMR_OK;
@@ -668,6 +687,133 @@ int run_aggregate_tc(Ctx* c, const double2* x, float2* out0, cudaStream_t st) {
       c->tc_nMT, c->tc_nKc, 4 * c->lev[0].K, 2 * c->npsi, c->d_tc_shape, c->d_tc_start, c->d_tc_count,
       c->d_tc_perm, c->d_tc_agg, reinterpret_cast<const double*>(x), reinterpret_cast<float*>(out0), c->d_tc_err);
   SMR_LAUNCH(c);
+  return SMR_OK;
+}
+
+// Near product on the tensor cores.  Block b (n2 x n2 complex, stored
+// column-major in d_B64) in real form: row (i, re/im) of y, column (j, re/im)
+// of x, entries [Re, -Im; Im, Re] of B_ij; split into TF32 hi / lo and laid
+// out like the receive images.  Pairs go to phases by lattice offset (self
+// blocks first, so that phase 0 writes every y row and the others add), and
+// within a phase into tiles of up to TC_NP pairs sharing a block.
+int build_near_tc(Ctx* c) {
+  c->tcn_ready = false;
+  const int n2 = 2 * c->npsi, M4 = 2 * n2, S = c->S, nb = c->nblk;
+  if (M4 > 128 || c->p == 0) return SMR_OK;          // more than one M tile: CUDA-core path
+  const int nK = (M4 + TC_KC - 1) / TC_KC;
+  const size_t bsz = (size_t)n2 * n2;
+  std::vector<double2> B((size_t)nb * bsz);
+  SMR_CUDA(c, cudaMemcpy(B.data(), c->d_B64, B.size() * sizeof(double2), cudaMemcpyDeviceToHost));
+  const size_t per = (size_t)nK * 2 * 128 * TC_KC;
+  std::vector<float> img((size_t)nb * per, 0.f);
+  for (int b = 0; b < nb; ++b)
+    for (int j = 0; j < n2; ++j)
+      for (int i = 0; i < n2; ++i) {
+        const double2 z = B[(size_t)b * bsz + (size_t)j * n2 + i];
+        for (int ro = 0; ro < 2; ++ro)
+          for (int ri = 0; ri < 2; ++ri) {
+            const int row = 2 * i + ro, kp = 2 * j + ri;
+            const double v = ro == 0 ? (ri == 0 ? z.x : -z.y) : (ri == 0 ? z.y : z.x);
+            const float hi = tf32_host((float)v), lo = tf32_host((float)(v - (double)hi));
+            const int ch = kp / TC_KC, kk = kp % TC_KC, q = kk >> 2, e = kk & 3;
+            const size_t base = (size_t)b * per + (size_t)ch * 2 * 128 * TC_KC;
+            const size_t off = (size_t)row * TC_KC + (((q ^ (row & 7)) << 2) | e);
+            img[base + off] = hi;
+            img[base + (size_t)128 * TC_KC + off] = lo;
+          }
+      }
+  // phase of a block: 0 for self blocks, 1..8 for the lattice offsets
+  auto phase_of = [&](int b) {
+    if (b < S) return 0;
+    const int o = (c->blk_dy[b] + 1) * 3 + (c->blk_dx[b] + 1);
+    return o < 4 ? o + 1 : o;
+  };
+  const int NPH = 9;
+  std::vector<std::vector<int>> pr(NPH);               // pair indices e per phase
+  std::vector<int> emu(c->nr_col.size());
+  std::vector<unsigned short> seen((size_t)c->p * NPH, 0);
+  for (int mu = 0; mu < c->p; ++mu)
+    for (int e = c->nr_ptr[mu]; e < c->nr_ptr[mu + 1]; ++e) {
+      const int b = c->nr_blk[e];
+      const int dx = b < S ? 0 : c->blk_dx[b], dy = b < S ? 0 : c->blk_dy[b];
+      if (dx < -1 || dx > 1 || dy < -1 || dy > 1) return SMR_OK;   // not a lattice neighbour
+      if (b >= S && dx == 0 && dy == 0) return SMR_OK;
+      const int ph = phase_of(b);
+      seen[(size_t)mu * NPH + ph]++;
+      emu[e] = mu;
+      pr[ph].push_back(e);
+    }
+  // each y row at most once per phase (no two CTAs of a launch write it),
+  // and exactly once in phase 0, which writes instead of adding
+  for (int mu = 0; mu < c->p; ++mu)
+    for (int ph = 0; ph < NPH; ++ph)
+      if (seen[(size_t)mu * NPH + ph] > 1 || (ph == 0 && seen[(size_t)mu * NPH] != 1)) return SMR_OK;
+  std::vector<int> tb, ts, tn, pnu, pmu, phase(1, 0);
+  std::vector<double> bytes, flops;
+  for (int ph = 0; ph < NPH; ++ph) {
+    std::vector<int>& v = pr[ph];
+    std::stable_sort(v.begin(), v.end(), [&](int a, int b) { return c->nr_blk[a] < c->nr_blk[b]; });
+    std::vector<char> used(nb, 0);
+    int nbu = 0;
+    for (size_t i = 0; i < v.size();) {
+      const int b = c->nr_blk[v[i]];
+      size_t j = i;
+      while (j < v.size() && c->nr_blk[v[j]] == b && j - i < (size_t)TC_NP) ++j;
+      tb.push_back(b);
+      ts.push_back((int)pnu.size());
+      tn.push_back((int)(j - i));
+      for (size_t k = i; k < j; ++k) {
+        const int e = v[k];
+        pnu.push_back(c->nr_col[e]);
+        pmu.push_back(emu[e]);
+      }
+      if (!used[b]) { used[b] = 1; ++nbu; }
+      i = j;
+    }
+    phase.push_back((int)tb.size());
+    const double np = (double)v.size();
+    // x row (FP32) read, y row written (and read after phase 0), each block once
+    bytes.push_back(np * M4 * (4.0 + (ph == 0 ? 8.0 : 16.0)) + (double)nbu * bsz * 8.0);
+    flops.push_back(8.0 * (double)bsz * np);
+  }
+  int rc;
+  if ((rc = upload(c, &c->d_tcn_img, img)) || (rc = upload(c, &c->d_tcn_blk, tb)) ||
+      (rc = upload(c, &c->d_tcn_start, ts)) || (rc = upload(c, &c->d_tcn_count, tn)) ||
+      (rc = upload(c, &c->d_tcn_nu, pnu)) || (rc = upload(c, &c->d_tcn_mu, pmu)))
+    return rc;
+  if (c->d_x32) cudaFree(c->d_x32);
+  c->d_x32 = nullptr;
+  SMR_CUDA(c, cudaMalloc((void**)&c->d_x32, (size_t)c->p * n2 * sizeof(float2)));
+  if (!c->d_tc_err) SMR_CUDA(c, cudaMalloc((void**)&c->d_tc_err, sizeof(int)));
+  c->tcn_nK = nK;
+  c->tcn_phase = phase;
+  c->tcn_bytes = bytes;
+  c->tcn_flops = flops;
+  c->tcn_ready = true;
+  return SMR_OK;
+}
+
+bool tc_near_ok(const Ctx* c, int R) { return c->tc_enable && c->tcn_ready && R == 1; }
+
+int run_near_tc(Ctx* c, const double2* x, double2* y, cudaStream_t st) {
+  const int n2 = 2 * c->npsi, M4 = 2 * n2;
+  const long long n = (long long)c->p * n2;
+  pbeg(c, st, "near", -1, (double)n * 24.0, 0.0);
+  k_x32<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, x, c->d_x32);
+  SMR_LAUNCH(c);
+  pend(c, st);
+  cudaFuncSetAttribute(k_receive_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
+  for (size_t ph = 0; ph + 1 < c->tcn_phase.size(); ++ph) {
+    const int t0 = c->tcn_phase[ph], nt = c->tcn_phase[ph + 1] - t0;
+    if (nt == 0) continue;
+    pbeg(c, st, "near", -1, c->tcn_bytes[ph], c->tcn_flops[ph]);
+    k_receive_tc<<<(unsigned)nt, 288, TC_SMEM, st>>>(
+        c->tcn_nK, M4, M4, c->d_tcn_blk + t0, c->d_tcn_start + t0, c->d_tcn_count + t0, c->d_tcn_nu,
+        c->d_tcn_mu, c->d_tcn_img, reinterpret_cast<const float*>(c->d_x32), reinterpret_cast<double*>(y),
+        ph > 0 ? 1 : 0, c->d_tc_err);
+    SMR_LAUNCH(c);
+    pend(c, st);
+  }
   return SMR_OK;
 }
 

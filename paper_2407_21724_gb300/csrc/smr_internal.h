@@ -246,7 +246,20 @@ struct Ctx {
   int tc_nMT = 0, tc_nKc = 0;
   float* d_tc_agg = nullptr;              // [S][M tiles][K chunks][hi | lo][128][32] aggregation images
   // tensor cores for aggregation / receive chosen by smr_autotune (-1: not tuned)
-  int tune_tc_agg = -1, tune_tc_rec = -1;
+  int tune_tc_agg = -1, tune_tc_rec = -1, tune_tc_near = -1;
+  // near product on the tensor cores: block images, and per lattice offset
+  // (phase; self blocks first) tiles of up to 128 pairs sharing a block
+  bool tcn_ready = false;
+  int tcn_nK = 0;
+  std::vector<int> tcn_phase;             // [n phases + 1] tile ranges
+  std::vector<double> tcn_bytes, tcn_flops;   // algorithmic bytes and flops per phase
+  float* d_tcn_img = nullptr;             // [nblk][nK][hi | lo][128][32] swizzled block images
+  int* d_tcn_blk = nullptr;               // per tile: block
+  int* d_tcn_start = nullptr;
+  int* d_tcn_count = nullptr;
+  int* d_tcn_nu = nullptr;                // per pair: source particle (x row)
+  int* d_tcn_mu = nullptr;                // per pair: target particle (y row)
+  float2* d_x32 = nullptr;                // x in FP32 for the gathers
   // column buffers of split products ([R][N] in, [R][N] out)
   bool split_cols = true;
   double2* d_split = nullptr;
@@ -344,6 +357,9 @@ int build_tc(Ctx* c);
 bool tc_receive_ok(const Ctx* c, int R);
 int run_receive_tc(Ctx* c, const float2* in0, double2* y, bool accumulate, cudaStream_t st);
 bool tc_aggregate_ok(const Ctx* c, int R);
+int build_near_tc(Ctx* c);
+bool tc_near_ok(const Ctx* c, int R);
+int run_near_tc(Ctx* c, const double2* x, double2* y, cudaStream_t st);
 int run_aggregate_tc(Ctx* c, const double2* x, float2* out0, cudaStream_t st);
 int tc_check(Ctx* c);
 

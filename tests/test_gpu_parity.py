@@ -168,6 +168,28 @@ def test_tensor_core_receive(c1, rnd):
         assert rel(y1, y0) < 5e-6, rel(y1, y0)
 
 
+def test_tensor_core_near(c1, rnd):
+    """The FP32 near-field product on the tensor cores (pairs sharing a block
+    as one split-TF32 GEMM, one launch per lattice offset) matches the FP64
+    near product to the FP32 bar, and the CUDA-core FP32 near product."""
+    for case, seed in ((c1, 33), (rnd, 34)):
+        n = case.info["n_unknowns"]
+        xd = torch.from_numpy(crandn(n, seed)).cuda()
+        parts = {}
+        for tc, prec in ((True, smr.SMR_PREC_FP32), (False, smr.SMR_PREC_FP32), (True, smr.SMR_PREC_FP64)):
+            smr.smr_set_tensor_cores(case.ctx, tc)
+            yn, yf = torch.empty_like(xd), torch.empty_like(xd)
+            smr.smr_matvec_parts(case.ctx, xd, yn, yf, prec)
+            torch.cuda.synchronize()
+            parts[(tc, prec)] = yn.cpu().numpy()
+        smr.smr_set_tensor_cores(case.ctx, True)
+        smr.smr_sync(case.ctx)
+        ref = parts[(True, smr.SMR_PREC_FP64)]
+        assert rel(parts[(True, smr.SMR_PREC_FP32)], ref) < 2e-6
+        assert rel(parts[(False, smr.SMR_PREC_FP32)], ref) < 2e-6
+        assert rel(parts[(True, smr.SMR_PREC_FP32)], parts[(False, smr.SMR_PREC_FP32)]) < 2e-6
+
+
 def test_autotuned_product_matches_oracle(rnd):
     """After smr_autotune picks launch variants, the FP64 and FP32 products
     still meet their bars against the oracle (every variant computes the
