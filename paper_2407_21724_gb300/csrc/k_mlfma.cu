@@ -363,7 +363,7 @@ __global__ void k_interp_fused(int nthP, int nphP, int nphC, int Kc, int R, int 
 // phi pass, shift and child sum in registers.
 template <typename T> struct EM1 { static constexpr int v = sizeof(T) == 4 ? 8 : 12; };
 template <typename T>
-__global__ void __launch_bounds__(256) k_interp1(int nthP, int nphP, int nphC, int Kc, int TR, int nrt,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_interp1(int nthP, int nphP, unsigned mP, int nphC, int Kc, int TR, int nrt,
                                                  const int* __restrict__ ch_ptr, const int* __restrict__ ch_idx,
                                                  const int* __restrict__ ch_quad, const int* __restrict__ th_src,
                                                  const int* __restrict__ th_refl, const T* __restrict__ th_w,
@@ -380,8 +380,13 @@ __global__ void __launch_bounds__(256) k_interp1(int nthP, int nphP, int nphC, i
   int B = blockIdx.x / nrt, rt = blockIdx.x - (blockIdx.x / nrt) * nrt;
   int tp0 = rt * TR, ntr = min(TR, nthP - tp0);
   int Kp = nthP * nphP;
-  int nG = ntr * nphC * NT, nout = ntr * nphP * NT;
+  int nout = ntr * nphP * NT;
   int half = nphC >> 1;
+  // (row, column) of this thread's tasks, stepped by the NTH tasks of one
+  // sweep of the CTA without dividing per task
+  const int NTH = blockDim.x / NT, task0 = threadIdx.x / NT, h = threadIdx.x % NT;
+  const int trG0 = task0 / nphC, jG0 = task0 - trG0 * nphC;
+  const int dqG = NTH / nphC, drG = NTH - dqG * nphC;
   H acc[EM];
 #pragma unroll
   for (int i = 0; i < EM; ++i) acc[i] = P::zero();
@@ -389,9 +394,7 @@ __global__ void __launch_bounds__(256) k_interp1(int nthP, int nphP, int nphC, i
     const V* src = F + (size_t)ch_idx[e] * Kc * 4;
     const V* sh = shift + (size_t)ch_quad[e] * Kp + (size_t)tp0 * nphP;
     __syncthreads();
-    for (int t = threadIdx.x; t < nG; t += blockDim.x) {
-      int task = t / NT, h = t - task * NT;
-      int tr = task / nphC, j = task - tr * nphC;
+    for (int tr = trG0, j = jG0, task = task0; tr < ntr; task += NTH) {
       int tp = tp0 + tr;
       int jr = j + half;
       jr = jr >= nphC ? jr - nphC : jr;
@@ -405,14 +408,17 @@ __global__ void __launch_bounds__(256) k_interp1(int nthP, int nphP, int nphC, i
       P::rfma(a, rf.z ? -w[2] : w[2], ldp<T>(src, (size_t)sr.z * nphC + (rf.z ? jr : j), h));
       P::rfma(a, rf.w ? -w[3] : w[3], ldp<T>(src, (size_t)sr.w * nphC + (rf.w ? jr : j), h));
       stp<T>(G, task, h, a);
+      j += drG;
+      tr += dqG;
+      if (j >= nphC) { j -= nphC; ++tr; }
     }
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < EM; ++i) {
-      int t = threadIdx.x + i * blockDim.x;
-      if (t < nout) {
-        int task = t / NT, h = t - task * NT;
-        int tr = task / nphP, jp = task - tr * nphP;
+      // task / nphP as a multiply-high by ceil(2^32 / nphP): exact while task * nphP < 2^32
+      const unsigned task = (unsigned)(task0 + i * NTH);
+      const int tr = (int)__umulhi(task, mP), jp = (int)task - tr * nphP;
+      if (tr < ntr) {
         int4 cs = *reinterpret_cast<const int4*>(ph_src + jp * 4);
         T w[4];
         P::w4(ph_w + jp * 4, w);
@@ -596,8 +602,8 @@ __global__ void k_translate(int K, int R, int RC, int KC, int ntx, int ntile, co
 // 6x6 source window once; a staged source part is read from shared memory
 // once for all four targets (conflict-free: lanes read consecutive 16-byte
 // parts).  CTA = 8x8 targets (4x4 parents) x KC directions; 16 x KC x NT threads.
-template <typename T>
-__global__ void __launch_bounds__(512) k_translate1(int K, int KC, int ntx, int ntile,
+template <typename T, int KC>
+__global__ void __launch_bounds__(512) k_translate1(int K, int ntx, int ntile,
                                                     const int* __restrict__ tiles, int map_x0, int map_y0,
                                                     int map_w, int map_h, const int* __restrict__ boxmap,
                                                     const typename CV<T>::V* __restrict__ Tg,
@@ -615,7 +621,7 @@ __global__ void __launch_bounds__(512) k_translate1(int K, int KC, int ntx, int 
   int ax0 = ((map_x0 >> 3) + tx) * TS, ay0 = ((map_y0 >> 3) + ty) * TS;
   int k0 = kch * KC;
   int nk = min(KC, K - k0);
-  int W = KC * 4;
+  constexpr int W = KC * 4;
   V* S = reinterpret_cast<V*>(smem_raw);              // [HS*HS sources][KC][4]
   V* Ts = S + HS * HS * W;                            // [49 offsets][KC]
   int* bid = reinterpret_cast<int*>(Ts + 49 * KC);   // [HS*HS] source box ids
@@ -629,7 +635,7 @@ __global__ void __launch_bounds__(512) k_translate1(int K, int KC, int ntx, int 
   }
   __syncthreads();
   {
-    int per = W * (int)sizeof(V) / 16;
+    constexpr int per = W * (int)sizeof(V) / 16;      // 16-byte pieces per source row
     int valid = nk * 4 * (int)sizeof(V);
     for (int t = threadIdx.x; t < HS * HS * per; t += blockDim.x) {
       int sb = t / per, pc = t - sb * per;
@@ -817,9 +823,12 @@ __global__ void __launch_bounds__(256) k_anterp1(int nthC, int nphC, int nthP, i
   int Kp = nthP * nphP, Kc = nthC * nphC;
   const V* srcP = inP + (size_t)parent[c] * Kp * 4;
   const V* sh = shift + (size_t)quad[c] * Kp;
-  for (int t = threadIdx.x; t < nr * W * NT; t += blockDim.x) {
-    int task = t / NT, h = t - task * NT;
-    int r = task / W, u = task - r * W;
+  // (row, column) of this thread's tasks, stepped by the NTH tasks of one
+  // sweep of the CTA without dividing per task
+  const int NTH = blockDim.x / NT, task0 = threadIdx.x / NT, h = threadIdx.x % NT;
+  const int r0 = task0 / W, u0 = task0 - r0 * W;
+  const int dq = NTH / W, dr = NTH - dq * W;
+  for (int r = r0, u = u0, task = task0; r < nr; task += NTH) {
     int j = (u < nj) ? j0 + u : j0 + half + (u - nj);
     int tp = lo + r;
     T wt = wthp[tp];
@@ -839,11 +848,12 @@ __global__ void __launch_bounds__(256) k_anterp1(int nthC, int nphC, int nthP, i
       }
     }
     stp<T>(Gt, task, h, a);
+    u += dr;
+    r += dq;
+    if (u >= W) { u -= W; ++r; }
   }
   __syncthreads();
-  for (int t = threadIdx.x; t < ni * W * NT; t += blockDim.x) {
-    int task = t / NT, h = t - task * NT;
-    int il = task / W, u = task - il * W;
+  for (int il = r0, u = u0; il < ni;) {
     int ur = u < nj ? u + nj : u - nj;             // column j + N/2 (mod N)
     int j = (u < nj) ? j0 + u : j0 + half + (u - nj);
     int i = i0 + il;
@@ -863,6 +873,9 @@ __global__ void __launch_bounds__(256) k_anterp1(int nthC, int nphC, int nthP, i
     H cur = ldp<T>(inC, d, h);
     P::add(cur, a);
     stp<T>(inC, d, h, cur);
+    u += dr;
+    il += dq;
+    if (u >= W) { u -= W; ++il; }
   }
 }
 // ------------------------------------------------------------------ receive
@@ -1098,8 +1111,9 @@ static int far_impl(Ctx* c, int R, const double2* x, double2* y, bool accumulate
       int nrt = (Lp.nth + TR - 1) / TR;
       size_t sm1 = (size_t)TR * Lc.nph * 4 * sizeof(V);
       cudaFuncSetAttribute(k_interp1<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+      const unsigned mP = (unsigned)(((1ull << 32) + (unsigned)Lp.nph - 1) / (unsigned)Lp.nph);
       k_interp1<T><<<(unsigned)(Lp.nbox * nrt), 256, sm1, st>>>(
-          Lp.nth, Lp.nph, Lc.nph, Lc.K, TR, nrt, Lp.d_ch_ptr, Lp.d_ch_idx, Lp.d_ch_quad, Lc.d_th_src,
+          Lp.nth, Lp.nph, mP, Lc.nph, Lc.K, TR, nrt, Lp.d_ch_ptr, Lp.d_ch_idx, Lp.d_ch_quad, Lc.d_th_src,
           Lc.d_th_refl, (const T*)(f64 ? (void*)Lc.d_th_w64 : (void*)Lc.d_th_w32), Lc.d_ph_src,
           (const T*)(f64 ? (void*)Lc.d_ph_w64 : (void*)Lc.d_ph_w32),
           (const V*)(f64 ? (void*)Lc.d_shift64 : (void*)Lc.d_shift32), (const V*)Lc.d_out, (V*)Lp.d_out);
@@ -1154,7 +1168,6 @@ static int far_impl(Ctx* c, int R, const double2* x, double2* y, bool accumulate
     size_t sm = ((size_t)64 * KC * 4 * RCt + (size_t)std::max(noff, 1) * KC) * sizeof(V) +
                 (64 + 16 + 16) * sizeof(int) + 16 * 27 * sizeof(int2);
     cudaFuncSetAttribute(k_translate<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_translate1<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     pbeg(c, st, "translate", s,
          2.0 * L.nbox * L.K * 4 * R_ * es + (double)L.off_dx.size() * L.K * es,
          8.0 * L.il_src.size() * L.K * 4 * R_);
@@ -1170,11 +1183,15 @@ static int far_impl(Ctx* c, int R, const double2* x, double2* y, bool accumulate
                                              (const V*)(f64 ? (void*)L.d_T64 : (void*)L.d_T32), (const V*)L.d_out,
                                              (V*)L.d_in);
     } else if (use8) {
-      int KC1 = (f64 ? 8 : 16) / (tv == 2 ? 2 : 1);
+      // direction chunk: 16 (FP32) or 8 (FP64) directions, halved by the tuner
+      const bool halfc = (tv == 2);
+      int KC1 = (f64 ? 8 : 16) / (halfc ? 2 : 1);
       int nk1 = (L.K + KC1 - 1) / KC1;
       size_t sm1 = ((size_t)144 * KC1 * 4 + (size_t)49 * KC1) * sizeof(V) + (144 + 64) * sizeof(int);
-      k_translate1<T><<<(unsigned)(L.ntile8_ne * nk1), 16 * KC1 * Part<T>::NT, sm1, st>>>(
-          L.K, KC1, L.ntile8_x, L.ntile8_ne, L.d_tiles8, L.map_x0, L.map_y0, L.map_w, L.map_h, L.d_boxmap,
+      auto kt = halfc ? k_translate1<T, (sizeof(T) == 8 ? 4 : 8)> : k_translate1<T, (sizeof(T) == 8 ? 8 : 16)>;
+      cudaFuncSetAttribute(kt, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      kt<<<(unsigned)(L.ntile8_ne * nk1), 16 * KC1 * Part<T>::NT, sm1, st>>>(
+          L.K, L.ntile8_x, L.ntile8_ne, L.d_tiles8, L.map_x0, L.map_y0, L.map_w, L.map_h, L.d_boxmap,
           (const V*)(f64 ? (void*)L.d_T64 : (void*)L.d_T32), (const V*)L.d_out, (V*)L.d_in);
     } else {
       k_translate<T><<<(unsigned)(L.ntile_ne * nkch * nrct), 256, sm, st>>>(
