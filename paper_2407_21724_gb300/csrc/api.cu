@@ -33,7 +33,7 @@ void free_scene(Ctx* c) {
     dfree(L.d_khat); dfree(L.d_w); dfree(L.d_il_ptr); dfree(L.d_il_src); dfree(L.d_il_off); dfree(L.d_il_pk);
     dfree(L.d_T64); dfree(L.d_T32); dfree(L.d_parent); dfree(L.d_quad); dfree(L.d_ch_ptr);
     dfree(L.d_ch_idx); dfree(L.d_ch_quad); dfree(L.d_th_src); dfree(L.d_th_refl); dfree(L.d_th_w64);
-    dfree(L.d_th_w32); dfree(L.d_ph_src); dfree(L.d_ph_w64); dfree(L.d_ph_w32); dfree(L.d_shift64);
+    dfree(L.d_th_w32); dfree(L.d_th_pk); dfree(L.d_th_ws64); dfree(L.d_th_ws32); dfree(L.d_ph_src); dfree(L.d_ph_w64); dfree(L.d_ph_w32); dfree(L.d_shift64);
     dfree(L.d_shift32); dfree(L.d_ant_lo); dfree(L.d_ant_pjp); dfree(L.d_ant_pw64); dfree(L.d_ant_pw32);
     dfree(L.d_ant_ttp); dfree(L.d_ant_tw64); dfree(L.d_ant_tw32);
     dfree(L.d_tht_ptr); dfree(L.d_tht_tp); dfree(L.d_tht_refl); dfree(L.d_tht_w64); dfree(L.d_tht_w32);
@@ -154,7 +154,19 @@ int build_interp(Ctx* c, Level& C, const Level& P) {
     lagrange4(nodes, f, &pw[4 * jp]);
   }
   std::vector<float> tw32(tw.begin(), tw.end()), pw32(pw.begin(), pw.end());
+  // single right-hand-side kernel: source row | reflected << 16, and the
+  // weights with the reflection's sign folded in
+  std::vector<int> tpk(4 * P.nth);
+  std::vector<double> tws(4 * P.nth);
+  for (int e = 0; e < 4 * P.nth; ++e) {
+    tpk[e] = tsrc[e] | (trefl[e] << 16);
+    tws[e] = trefl[e] ? -tw[e] : tw[e];
+  }
+  std::vector<float> tws32(tws.begin(), tws.end());
   int rc;
+  if ((rc = upload(c, &C.d_th_pk, tpk)) || (rc = upload(c, &C.d_th_ws64, tws)) ||
+      (rc = upload(c, &C.d_th_ws32, tws32)))
+    return rc;
   if ((rc = upload(c, &C.d_th_src, tsrc)) || (rc = upload(c, &C.d_th_refl, trefl)) ||
       (rc = upload(c, &C.d_th_w64, tw)) || (rc = upload(c, &C.d_th_w32, tw32)) ||
       (rc = upload(c, &C.d_ph_src, psrc)) || (rc = upload(c, &C.d_ph_w64, pw)) ||

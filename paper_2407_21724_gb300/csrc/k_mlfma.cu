@@ -365,8 +365,8 @@ template <typename T> struct EM1 { static constexpr int v = sizeof(T) == 4 ? 8 :
 template <typename T>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_interp1(int nthP, int nphP, unsigned mP, int nphC, int Kc, int TR, int nrt,
                                                  const int* __restrict__ ch_ptr, const int* __restrict__ ch_idx,
-                                                 const int* __restrict__ ch_quad, const int* __restrict__ th_src,
-                                                 const int* __restrict__ th_refl, const T* __restrict__ th_w,
+                                                 const int* __restrict__ ch_quad, const int* __restrict__ th_pk,
+                                                 const T* __restrict__ th_w,
                                                  const int* __restrict__ ph_src, const T* __restrict__ ph_w,
                                                  const typename CV<T>::V* __restrict__ shift,
                                                  const typename CV<T>::V* __restrict__ F,
@@ -398,15 +398,14 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_interp1(int nth
       int tp = tp0 + tr;
       int jr = j + half;
       jr = jr >= nphC ? jr - nphC : jr;
-      int4 sr = *reinterpret_cast<const int4*>(th_src + tp * 4);
-      int4 rf = *reinterpret_cast<const int4*>(th_refl + tp * 4);
+      int4 pk = *reinterpret_cast<const int4*>(th_pk + tp * 4);
       T w[4];
       P::w4(th_w + tp * 4, w);
       H a = P::zero();
-      P::rfma(a, rf.x ? -w[0] : w[0], ldp<T>(src, (size_t)sr.x * nphC + (rf.x ? jr : j), h));
-      P::rfma(a, rf.y ? -w[1] : w[1], ldp<T>(src, (size_t)sr.y * nphC + (rf.y ? jr : j), h));
-      P::rfma(a, rf.z ? -w[2] : w[2], ldp<T>(src, (size_t)sr.z * nphC + (rf.z ? jr : j), h));
-      P::rfma(a, rf.w ? -w[3] : w[3], ldp<T>(src, (size_t)sr.w * nphC + (rf.w ? jr : j), h));
+      P::rfma(a, w[0], ldp<T>(src, (size_t)(pk.x & 0xffff) * nphC + ((pk.x >> 16) ? jr : j), h));
+      P::rfma(a, w[1], ldp<T>(src, (size_t)(pk.y & 0xffff) * nphC + ((pk.y >> 16) ? jr : j), h));
+      P::rfma(a, w[2], ldp<T>(src, (size_t)(pk.z & 0xffff) * nphC + ((pk.z >> 16) ? jr : j), h));
+      P::rfma(a, w[3], ldp<T>(src, (size_t)(pk.w & 0xffff) * nphC + ((pk.w >> 16) ? jr : j), h));
       stp<T>(G, task, h, a);
       j += drG;
       tr += dqG;
@@ -795,7 +794,8 @@ __global__ void k_anterp_theta(int nrows, int nthC, int nthP, int nphC, int R,
 // parent theta weight) into shared memory; then the theta-transposed pass adds
 // into the child's incoming spectrum.  Transposed taps are padded to PM / TM
 // per child column / row (zero weights), packed as (tp | refl << 16).
-template <typename T>
+// PMC > 0: PM = TM = PMC known at compile time (tap loops unrolled)
+template <typename T, int PMC>
 __global__ void __launch_bounds__(256) k_anterp1(int nthC, int nphC, int nthP, int nphP, int TI, int nit,
                                                  int JC, int njc, const int* __restrict__ parent,
                                                  const int* __restrict__ quad, const int* __restrict__ lo_row,
@@ -835,10 +835,12 @@ __global__ void __launch_bounds__(256) k_anterp1(int nthC, int nphC, int nthP, i
     const V* prow = srcP + (size_t)tp * nphP * 4;
     const V* srow = sh + (size_t)tp * nphP;
     H a = P::zero();
-    for (int q = 0; q < PM; q += 4) {
-      int4 jj = *reinterpret_cast<const int4*>(pjp + (size_t)j * PM + q);
+    const int pm = PMC > 0 ? PMC : PM;
+#pragma unroll
+    for (int q = 0; q < (PMC > 0 ? PMC : PM); q += 4) {
+      int4 jj = *reinterpret_cast<const int4*>(pjp + (size_t)j * pm + q);
       T w[4];
-      P::w4(pw + (size_t)j * PM + q, w);
+      P::w4(pw + (size_t)j * pm + q, w);
       int js[4] = {jj.x, jj.y, jj.z, jj.w};
 #pragma unroll
       for (int b = 0; b < 4; ++b) {
@@ -858,10 +860,12 @@ __global__ void __launch_bounds__(256) k_anterp1(int nthC, int nphC, int nthP, i
     int j = (u < nj) ? j0 + u : j0 + half + (u - nj);
     int i = i0 + il;
     H a = P::zero();
-    for (int q = 0; q < TM; q += 4) {
-      int4 pk = *reinterpret_cast<const int4*>(ttp + (size_t)i * TM + q);
+    const int tm = PMC > 0 ? PMC : TM;
+#pragma unroll
+    for (int q = 0; q < (PMC > 0 ? PMC : TM); q += 4) {
+      int4 pk = *reinterpret_cast<const int4*>(ttp + (size_t)i * tm + q);
       T w[4];
-      P::w4(tw + (size_t)i * TM + q, w);
+      P::w4(tw + (size_t)i * tm + q, w);
       int ps[4] = {pk.x, pk.y, pk.z, pk.w};
 #pragma unroll
       for (int b = 0; b < 4; ++b) {
@@ -1113,8 +1117,8 @@ static int far_impl(Ctx* c, int R, const double2* x, double2* y, bool accumulate
       cudaFuncSetAttribute(k_interp1<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
       const unsigned mP = (unsigned)(((1ull << 32) + (unsigned)Lp.nph - 1) / (unsigned)Lp.nph);
       k_interp1<T><<<(unsigned)(Lp.nbox * nrt), 256, sm1, st>>>(
-          Lp.nth, Lp.nph, mP, Lc.nph, Lc.K, TR, nrt, Lp.d_ch_ptr, Lp.d_ch_idx, Lp.d_ch_quad, Lc.d_th_src,
-          Lc.d_th_refl, (const T*)(f64 ? (void*)Lc.d_th_w64 : (void*)Lc.d_th_w32), Lc.d_ph_src,
+          Lp.nth, Lp.nph, mP, Lc.nph, Lc.K, TR, nrt, Lp.d_ch_ptr, Lp.d_ch_idx, Lp.d_ch_quad, Lc.d_th_pk,
+          (const T*)(f64 ? (void*)Lc.d_th_ws64 : (void*)Lc.d_th_ws32), Lc.d_ph_src,
           (const T*)(f64 ? (void*)Lc.d_ph_w64 : (void*)Lc.d_ph_w32),
           (const V*)(f64 ? (void*)Lc.d_shift64 : (void*)Lc.d_shift32), (const V*)Lc.d_out, (V*)Lp.d_out);
       SMR_LAUNCH(c);
@@ -1216,7 +1220,8 @@ static int far_impl(Ctx* c, int R, const double2* x, double2* y, bool accumulate
       int njc = (Lc.nph / 2 + JC - 1) / JC;
       size_t sm1 = (size_t)Lc.ant_GR * 2 * JC * 4 * sizeof(V);
       int thr = (an == 2 || Lc.ant_GR * 2 * JC * Part<T>::NT >= 2048) ? 256 : 128;
-      k_anterp1<T><<<(unsigned)(Lc.nbox * Lc.ant_nit * njc), thr, sm1, st>>>(
+      auto ka = (Lc.ant_PM == 8 && Lc.ant_TM == 8) ? k_anterp1<T, 8> : k_anterp1<T, 0>;
+      ka<<<(unsigned)(Lc.nbox * Lc.ant_nit * njc), thr, sm1, st>>>(
           Lc.nth, Lc.nph, Lp.nth, Lp.nph, Lc.ant_TI, Lc.ant_nit, JC, njc, Lc.d_parent, Lc.d_quad, Lc.d_ant_lo,
           Lc.ant_PM, Lc.d_ant_pjp, (const T*)(f64 ? (void*)Lc.d_ant_pw64 : (void*)Lc.d_ant_pw32),
           (const T*)(f64 ? (void*)Lc.d_wthp64 : (void*)Lc.d_wthp32),

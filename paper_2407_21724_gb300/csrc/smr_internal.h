@@ -75,6 +75,9 @@ struct Level {
   int* d_th_refl = nullptr;              // [nth_p][4] 1 if reflected through a pole
   double* d_th_w64 = nullptr;            // [nth_p][4]
   float* d_th_w32 = nullptr;
+  int* d_th_pk = nullptr;                 // [nth_parent][4] source row | reflected << 16
+  double* d_th_ws64 = nullptr;            // [nth_parent][4] weights, reflection sign folded in
+  float* d_th_ws32 = nullptr;
   int* d_ph_src = nullptr;               // [nph_p][4]
   double* d_ph_w64 = nullptr;
   float* d_ph_w32 = nullptr;
