@@ -247,6 +247,8 @@ int build_interp(Ctx* c, Level& C, const Level& P) {
     for (int i = 0; i < C.nth; ++i) tm = std::max(tm, tptr[i + 1] - tptr[i]);
     C.ant_PM = (pm + 3) / 4 * 4;
     C.ant_TM = (tm + 3) / 4 * 4;
+    C.ant_PMx = pm;
+    C.ant_TMx = tm;
     std::vector<int> ppj((size_t)C.nph * C.ant_PM), tpk((size_t)C.nth * C.ant_TM);
     std::vector<double> ppw((size_t)C.nph * C.ant_PM, 0.0), tpw((size_t)C.nth * C.ant_TM, 0.0);
     for (int j = 0; j < C.nph; ++j)

@@ -794,7 +794,8 @@ __global__ void k_anterp_theta(int nrows, int nthC, int nthP, int nphC, int R,
 // parent theta weight) into shared memory; then the theta-transposed pass adds
 // into the child's incoming spectrum.  Transposed taps are padded to PM / TM
 // per child column / row (zero weights), packed as (tp | refl << 16).
-// PMC > 0: PM = TM = PMC known at compile time (tap loops unrolled)
+// PMC > 0: tap tables padded to 8 per row (PM = TM = 8) and at most PMC
+// real taps per row, known at compile time (tap loops unrolled)
 template <typename T, int PMC>
 __global__ void __launch_bounds__(256) k_anterp1(int nthC, int nphC, int nthP, int nphP, int TI, int nit,
                                                  int JC, int njc, const int* __restrict__ parent,
@@ -823,9 +824,12 @@ __global__ void __launch_bounds__(256) k_anterp1(int nthC, int nphC, int nthP, i
   int Kp = nthP * nphP, Kc = nthC * nphC;
   const V* srcP = inP + (size_t)parent[c] * Kp * 4;
   const V* sh = shift + (size_t)quad[c] * Kp;
-  // (row, column) of this thread's tasks, stepped by the NTH tasks of one
-  // sweep of the CTA without dividing per task
-  const int NTH = blockDim.x / NT, task0 = threadIdx.x / NT, h = threadIdx.x % NT;
+  // each thread owns PPT consecutive 16-byte parts of a direction (two in
+  // FP64, where a direction has four; one in FP32, where more threads hide
+  // more latency); (row, column) of its tasks stepped by the NTH tasks of
+  // one sweep of the CTA without dividing per task
+  constexpr int PPT = sizeof(T) == 8 ? 2 : 1, NT2 = NT / PPT;
+  const int NTH = blockDim.x / NT2, task0 = threadIdx.x / NT2, h = PPT * (threadIdx.x % NT2);
   const int r0 = task0 / W, u0 = task0 - r0 * W;
   const int dq = NTH / W, dr = NTH - dq * W;
   for (int r = r0, u = u0, task = task0; r < nr; task += NTH) {
@@ -834,8 +838,8 @@ __global__ void __launch_bounds__(256) k_anterp1(int nthC, int nphC, int nthP, i
     T wt = wthp[tp];
     const V* prow = srcP + (size_t)tp * nphP * 4;
     const V* srow = sh + (size_t)tp * nphP;
-    H a = P::zero();
-    const int pm = PMC > 0 ? PMC : PM;
+    H a = P::zero(), a1 = P::zero();
+    const int pm = PMC > 0 ? 8 : PM;
 #pragma unroll
     for (int q = 0; q < (PMC > 0 ? PMC : PM); q += 4) {
       int4 jj = *reinterpret_cast<const int4*>(pjp + (size_t)j * pm + q);
@@ -844,12 +848,16 @@ __global__ void __launch_bounds__(256) k_anterp1(int nthC, int nphC, int nthP, i
       int js[4] = {jj.x, jj.y, jj.z, jj.w};
 #pragma unroll
       for (int b = 0; b < 4; ++b) {
+        if (PMC > 0 && q + b >= PMC) break;
         V s = srow[js[b]];
         T ww = w[b] * wt;
-        P::cfma(a, mkc(ww * s.x, -ww * s.y), ldp<T>(prow, js[b], h));
+        const V cw = mkc(ww * s.x, -ww * s.y);
+        P::cfma(a, cw, ldp<T>(prow, js[b], h));
+        if (PPT == 2) P::cfma(a1, cw, ldp<T>(prow, js[b], h + 1));
       }
     }
     stp<T>(Gt, task, h, a);
+    if (PPT == 2) stp<T>(Gt, task, h + 1, a1);
     u += dr;
     r += dq;
     if (u >= W) { u -= W; ++r; }
@@ -859,8 +867,8 @@ __global__ void __launch_bounds__(256) k_anterp1(int nthC, int nphC, int nthP, i
     int ur = u < nj ? u + nj : u - nj;             // column j + N/2 (mod N)
     int j = (u < nj) ? j0 + u : j0 + half + (u - nj);
     int i = i0 + il;
-    H a = P::zero();
-    const int tm = PMC > 0 ? PMC : TM;
+    H a = P::zero(), a1 = P::zero();
+    const int tm = PMC > 0 ? 8 : TM;
 #pragma unroll
     for (int q = 0; q < (PMC > 0 ? PMC : TM); q += 4) {
       int4 pk = *reinterpret_cast<const int4*>(ttp + (size_t)i * tm + q);
@@ -869,14 +877,22 @@ __global__ void __launch_bounds__(256) k_anterp1(int nthC, int nphC, int nthP, i
       int ps[4] = {pk.x, pk.y, pk.z, pk.w};
 #pragma unroll
       for (int b = 0; b < 4; ++b) {
+        if (PMC > 0 && q + b >= PMC) break;
         int r = (ps[b] & 0xffff) - lo;
-        P::rfma(a, w[b], ldp<T>(Gt, (size_t)r * W + ((ps[b] >> 16) ? ur : u), h));
+        const size_t g = (size_t)r * W + ((ps[b] >> 16) ? ur : u);
+        P::rfma(a, w[b], ldp<T>(Gt, g, h));
+        if (PPT == 2) P::rfma(a1, w[b], ldp<T>(Gt, g, h + 1));
       }
     }
     size_t d = (size_t)c * Kc + (size_t)i * nphC + j;
     H cur = ldp<T>(inC, d, h);
     P::add(cur, a);
     stp<T>(inC, d, h, cur);
+    if (PPT == 2) {
+      H cur1 = ldp<T>(inC, d, h + 1);
+      P::add(cur1, a1);
+      stp<T>(inC, d, h + 1, cur1);
+    }
     u += dr;
     il += dq;
     if (u >= W) { u -= W; ++il; }
@@ -1219,8 +1235,9 @@ static int far_impl(Ctx* c, int R, const double2* x, double2* y, bool accumulate
       if (an == 1) JC = std::max(1, JC / 2);
       int njc = (Lc.nph / 2 + JC - 1) / JC;
       size_t sm1 = (size_t)Lc.ant_GR * 2 * JC * 4 * sizeof(V);
-      int thr = (an == 2 || Lc.ant_GR * 2 * JC * Part<T>::NT >= 2048) ? 256 : 128;
-      auto ka = (Lc.ant_PM == 8 && Lc.ant_TM == 8) ? k_anterp1<T, 8> : k_anterp1<T, 0>;
+      int thr = (an == 2 || Lc.ant_GR * 2 * JC * (Part<T>::NT / (f64 ? 2 : 1)) >= 2048) ? 256 : 128;
+      auto ka = k_anterp1<T, 0>;
+      if (Lc.ant_PM == 8 && Lc.ant_TM == 8) ka = std::max(Lc.ant_PMx, Lc.ant_TMx) <= 7 ? k_anterp1<T, 7> : k_anterp1<T, 8>;
       ka<<<(unsigned)(Lc.nbox * Lc.ant_nit * njc), thr, sm1, st>>>(
           Lc.nth, Lc.nph, Lp.nth, Lp.nph, Lc.ant_TI, Lc.ant_nit, JC, njc, Lc.d_parent, Lc.d_quad, Lc.d_ant_lo,
           Lc.ant_PM, Lc.d_ant_pjp, (const T*)(f64 ? (void*)Lc.d_ant_pw64 : (void*)Lc.d_ant_pw32),

@@ -121,7 +121,8 @@ struct Level {
   int tune_ip[2] = {0, 0};
   // anterpolation into this level: 1 = half the column chunk, 2 = 256 threads
   int tune_an[2] = {0, 0};
-  int ant_PM = 0, ant_TM = 0;
+  int ant_PM = 0, ant_TM = 0;             // padded transposed taps per child column / row
+  int ant_PMx = 0, ant_TMx = 0;           // real maxima
   int* d_ant_pjp = nullptr;
   double* d_ant_pw64 = nullptr;
   float* d_ant_pw32 = nullptr;
