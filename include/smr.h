@@ -205,7 +205,7 @@ int smr_set_tensor_cores(smr_ctx* ctx, int enable);
  * half theta-row tile; anterpolation with the full or half column chunk or
  * 256-thread CTAs; for SMR_PREC_FP32 also aggregation,
  * receive and the near-field product on the tensor cores or the CUDA
- * cores.  Each variant is timed over
+ * cores (the near product on the tensor cores only if at least 5 % faster).  Each variant is timed over
  * three products (CUDA events around every launch, the fastest kept).  Uses
  * and overwrites the context's scratch buffers; drops captured products.
  * R must be 1. */

@@ -1143,7 +1143,10 @@ int smr_autotune(smr_ctx* h, int R, int precision, void* stream) {
   if (q == 1) {                                // the tensor-core steps exist in FP32 only
     c->tune_tc_agg = rc ? -1 : (agg[1] <= agg[0] ? 1 : 0);
     c->tune_tc_rec = rc ? -1 : (rec[1] <= rec[0] ? 1 : 0);
-    c->tune_tc_near = rc ? -1 : (nea[1] <= nea[0] ? 1 : 0);
+    // the near product on the tensor cores only when clearly faster: the two
+    // paths are close on single right-hand sides, and a stable choice keeps
+    // the launch sequence the same from one tuning to the next
+    c->tune_tc_near = rc ? -1 : (nea[1] < 0.95 * nea[0] ? 1 : 0);
   }
   free_graphs(c);                              // captured products used the trial variants
   return rc;
