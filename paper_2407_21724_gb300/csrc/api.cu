@@ -50,7 +50,8 @@ void free_scene(Ctx* c) {
   dfree(c->d_modes); dfree(c->d_rq); dfree(c->d_P64); dfree(c->d_P32); dfree(c->d_sid);
   dfree(c->d_centres); dfree(c->d_dshift); dfree(c->d_nr_ptr); dfree(c->d_nr_col); dfree(c->d_nr_blk);
   dfree(c->d_B64); dfree(c->d_B32); dfree(c->d_tcn_img); dfree(c->d_tcn_blk); dfree(c->d_tcn_start);
-  dfree(c->d_tcn_count); dfree(c->d_tcn_nu); dfree(c->d_tcn_mu); dfree(c->d_x32); dfree(c->d_Pinv64); dfree(c->d_Pinv32); dfree(c->d_pc_ptr);
+  dfree(c->d_tcn_count); dfree(c->d_tcn_nu); dfree(c->d_tcn_mu); dfree(c->d_x32);
+  dfree(c->d_tcn_mask); dfree(c->d_tcn_part); dfree(c->d_Pinv64); dfree(c->d_Pinv32); dfree(c->d_pc_ptr);
   dfree(c->d_pc_col); dfree(c->d_pc_blk); dfree(c->d_tmp);
   dfree(c->d_arr);
   dfree(c->d_tile_shape); dfree(c->d_tile_start); dfree(c->d_tile_count); dfree(c->d_perm);

@@ -184,12 +184,13 @@ __device__ __forceinline__ void st_chunk(unsigned char* S, int tid, const float4
   }
 }
 
+template <typename YT>
 __global__ void __launch_bounds__(288, 1) k_receive_tc(int nK, int K8, int M4, const int* __restrict__ tshape,
                                                        const int* __restrict__ tstart,
                                                        const int* __restrict__ tcount,
                                                        const int* __restrict__ perm,
                                                        const int* __restrict__ yperm, const float* __restrict__ A,
-                                                       const float* __restrict__ in0, double* __restrict__ y,
+                                                       const float* __restrict__ in0, YT* __restrict__ y,
                                                        int accumulate, int* __restrict__ err) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* sm = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -319,17 +320,25 @@ __global__ void __launch_bounds__(288, 1) k_receive_tc(int nK, int K8, int M4, c
       float v[32];
       tmem_ld32(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(g * 32), v);
       if (row < M4) {
-        // the 32 columns are distinct particles: all loads first, then stores
-        double yo[32];
+        if (accumulate) {
+          // the 32 columns are distinct y rows: all loads first, then stores
+          YT yo[32];
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          int col = g * 32 + j;
-          yo[j] = (accumulate && col < cnt) ? y[(size_t)ys[col] * M4 + row] : 0.0;
-        }
+          for (int j = 0; j < 32; ++j) {
+            int col = g * 32 + j;
+            yo[j] = col < cnt ? y[(size_t)ys[col] * M4 + row] : YT(0);
+          }
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          int col = g * 32 + j;
-          if (col < cnt) y[(size_t)ys[col] * M4 + row] = yo[j] + (double)v[j];
+          for (int j = 0; j < 32; ++j) {
+            int col = g * 32 + j;
+            if (col < cnt) y[(size_t)ys[col] * M4 + row] = yo[j] + (YT)v[j];
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            int col = g * 32 + j;
+            if (col < cnt) y[(size_t)ys[col] * M4 + row] = (YT)v[j];
+          }
         }
       }
     }
@@ -668,8 +677,8 @@ int build_tc(Ctx* c) {
 bool tc_receive_ok(const Ctx* c, int R) { return c->tc_enable && c->tc_ready && R == 1 && !c->any_dshift; }
 
 int run_receive_tc(Ctx* c, const float2* in0, double2* y, bool accumulate, cudaStream_t st) {
-  cudaFuncSetAttribute(k_receive_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
-  k_receive_tc<<<(unsigned)c->tc_ntile, 288, TC_SMEM, st>>>(
+  cudaFuncSetAttribute(k_receive_tc<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
+  k_receive_tc<double><<<(unsigned)c->tc_ntile, 288, TC_SMEM, st>>>(
       c->tc_nK, 8 * c->lev[0].K, 4 * c->npsi, c->d_tc_shape, c->d_tc_start, c->d_tc_count, c->d_tc_perm,
       c->d_tc_perm, c->d_tc_rec, reinterpret_cast<const float*>(in0), reinterpret_cast<double*>(y), accumulate ? 1 : 0,
       c->d_tc_err);
@@ -694,8 +703,11 @@ int run_aggregate_tc(Ctx* c, const double2* x, float2* out0, cudaStream_t st) {
 // column-major in d_B64) in real form: row (i, re/im) of y, column (j, re/im)
 // of x, entries [Re, -Im; Im, Re] of B_ij; split into TF32 hi / lo and laid
 // out like the receive images.  Pairs go to phases by lattice offset (self
-// blocks first, so that phase 0 writes every y row and the others add), and
-// within a phase into tiles of up to TC_NP pairs sharing a block.
+// blocks first), and within a phase into tiles of up to TC_NP pairs sharing
+// a block.  One launch runs every tile: the pair (mu, nu) of phase ph writes
+// its FP32 product to row ph * p + mu of a partials buffer (no two pairs
+// share a row, so no read-modify-write), and k_near_sum adds each particle's
+// rows in phase order in FP64.
 int build_near_tc(Ctx* c) {
   c->tcn_ready = false;
   const int n2 = 2 * c->npsi, M4 = 2 * n2, S = c->S, nb = c->nblk;
@@ -749,6 +761,10 @@ int build_near_tc(Ctx* c) {
     for (int ph = 0; ph < NPH; ++ph)
       if (seen[(size_t)mu * NPH + ph] > 1 || (ph == 0 && seen[(size_t)mu * NPH] != 1)) return SMR_OK;
   std::vector<int> tb, ts, tn, pnu, pmu, phase(1, 0);
+  std::vector<unsigned short> pmask(c->p, 0);             // phases in which each particle has a pair
+  for (int mu = 0; mu < c->p; ++mu)
+    for (int ph = 0; ph < NPH; ++ph)
+      if (seen[(size_t)mu * NPH + ph]) pmask[mu] |= (unsigned short)(1u << ph);
   std::vector<double> bytes, flops;
   for (int ph = 0; ph < NPH; ++ph) {
     std::vector<int>& v = pr[ph];
@@ -765,22 +781,26 @@ int build_near_tc(Ctx* c) {
       for (size_t k = i; k < j; ++k) {
         const int e = v[k];
         pnu.push_back(c->nr_col[e]);
-        pmu.push_back(emu[e]);
+        pmu.push_back(ph * c->p + emu[e]);
       }
       if (!used[b]) { used[b] = 1; ++nbu; }
       i = j;
     }
     phase.push_back((int)tb.size());
     const double np = (double)v.size();
-    // x row (FP32) read, y row written (and read after phase 0), each block once
-    bytes.push_back(np * M4 * (4.0 + (ph == 0 ? 8.0 : 16.0)) + (double)nbu * bsz * 8.0);
+    // x row (FP32) read, partial row (FP32) written, each block once
+    bytes.push_back(np * M4 * (4.0 + 4.0) + (double)nbu * bsz * 8.0);
     flops.push_back(8.0 * (double)bsz * np);
   }
   int rc;
   if ((rc = upload(c, &c->d_tcn_img, img)) || (rc = upload(c, &c->d_tcn_blk, tb)) ||
       (rc = upload(c, &c->d_tcn_start, ts)) || (rc = upload(c, &c->d_tcn_count, tn)) ||
-      (rc = upload(c, &c->d_tcn_nu, pnu)) || (rc = upload(c, &c->d_tcn_mu, pmu)))
+      (rc = upload(c, &c->d_tcn_nu, pnu)) || (rc = upload(c, &c->d_tcn_mu, pmu)) ||
+      (rc = upload(c, &c->d_tcn_mask, pmask)))
     return rc;
+  if (c->d_tcn_part) cudaFree(c->d_tcn_part);
+  c->d_tcn_part = nullptr;
+  SMR_CUDA(c, cudaMalloc((void**)&c->d_tcn_part, (size_t)NPH * c->p * M4 * sizeof(float)));
   if (c->d_x32) cudaFree(c->d_x32);
   c->d_x32 = nullptr;
   SMR_CUDA(c, cudaMalloc((void**)&c->d_x32, (size_t)c->p * n2 * sizeof(float2)));
@@ -795,25 +815,46 @@ int build_near_tc(Ctx* c) {
 
 bool tc_near_ok(const Ctx* c, int R) { return c->tc_enable && c->tcn_ready && R == 1; }
 
+// y[mu][r] = sum over the phases in which mu has a pair, in phase order, of
+// the partial rows (FP64 sums of FP32 products)
+__global__ void k_near_sum(int p, int M4, int nph, const unsigned short* __restrict__ mask,
+                           const float* __restrict__ part, double* __restrict__ y) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= (long long)p * M4) return;
+  const int mu = (int)(t / M4), r = (int)(t - (long long)mu * M4);
+  const unsigned m = mask[mu];
+  double a = 0.0;
+  for (int ph = 0; ph < nph; ++ph)
+    if (m >> ph & 1u) a += (double)part[((size_t)ph * p + mu) * M4 + r];
+  y[t] = a;
+}
+
 int run_near_tc(Ctx* c, const double2* x, double2* y, cudaStream_t st) {
   const int n2 = 2 * c->npsi, M4 = 2 * n2;
   const long long n = (long long)c->p * n2;
+  const int nph = (int)c->tcn_phase.size() - 1, nt = c->tcn_phase.back();
   pbeg(c, st, "near", -1, (double)n * 24.0, 0.0);
   k_x32<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, x, c->d_x32);
   SMR_LAUNCH(c);
   pend(c, st);
-  cudaFuncSetAttribute(k_receive_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
-  for (size_t ph = 0; ph + 1 < c->tcn_phase.size(); ++ph) {
-    const int t0 = c->tcn_phase[ph], nt = c->tcn_phase[ph + 1] - t0;
-    if (nt == 0) continue;
-    pbeg(c, st, "near", -1, c->tcn_bytes[ph], c->tcn_flops[ph]);
-    k_receive_tc<<<(unsigned)nt, 288, TC_SMEM, st>>>(
-        c->tcn_nK, M4, M4, c->d_tcn_blk + t0, c->d_tcn_start + t0, c->d_tcn_count + t0, c->d_tcn_nu,
-        c->d_tcn_mu, c->d_tcn_img, reinterpret_cast<const float*>(c->d_x32), reinterpret_cast<double*>(y),
-        ph > 0 ? 1 : 0, c->d_tc_err);
-    SMR_LAUNCH(c);
-    pend(c, st);
+  double bytes = 0, flops = 0;
+  for (int ph = 0; ph < nph; ++ph) {
+    bytes += c->tcn_bytes[ph];
+    flops += c->tcn_flops[ph];
   }
+  cudaFuncSetAttribute(k_receive_tc<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
+  pbeg(c, st, "near", -1, bytes, flops);
+  k_receive_tc<float><<<(unsigned)nt, 288, TC_SMEM, st>>>(
+      c->tcn_nK, M4, M4, c->d_tcn_blk, c->d_tcn_start, c->d_tcn_count, c->d_tcn_nu, c->d_tcn_mu,
+      c->d_tcn_img, reinterpret_cast<const float*>(c->d_x32), c->d_tcn_part, 0, c->d_tc_err);
+  SMR_LAUNCH(c);
+  pend(c, st);
+  const long long nm = (long long)c->p * M4;
+  pbeg(c, st, "near", -1, (double)nm * 8.0 + (double)c->nr_col.size() * M4 * 4.0 + 2.0 * c->p, 0.0);
+  k_near_sum<<<(unsigned)((nm + 255) / 256), 256, 0, st>>>(c->p, M4, nph, c->d_tcn_mask, c->d_tcn_part,
+                                                          reinterpret_cast<double*>(y));
+  SMR_LAUNCH(c);
+  pend(c, st);
   return SMR_OK;
 }
 

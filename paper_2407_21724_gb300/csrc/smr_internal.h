@@ -262,7 +262,9 @@ struct Ctx {
   int* d_tcn_start = nullptr;
   int* d_tcn_count = nullptr;
   int* d_tcn_nu = nullptr;                // per pair: source particle (x row)
-  int* d_tcn_mu = nullptr;                // per pair: target particle (y row)
+  int* d_tcn_mu = nullptr;                // per pair: partial row, phase * p + target particle
+  unsigned short* d_tcn_mask = nullptr;   // per particle: phases in which it has a pair
+  float* d_tcn_part = nullptr;            // [phase][p][4 n_psi] FP32 partial products
   float2* d_x32 = nullptr;                // x in FP32 for the gathers
   // column buffers of split products ([R][N] in, [R][N] out)
   bool split_cols = true;
