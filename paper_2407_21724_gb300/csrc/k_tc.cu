@@ -45,6 +45,7 @@ constexpr int TC_NSTAGE = 3;
 constexpr int TC_PF = 3;                       // spectrum chunks of loads in flight per producer
 constexpr size_t TC_SMEM = (size_t)TC_NSTAGE * TC_STAGE + 1024 + 2048;   // + alignment, barriers, ids
 constexpr uint32_t TC_SPIN = 1u << 24;         // try_wait rounds before giving up
+constexpr int NEAR_NPH = 9;                    // near-product phases: self blocks + 8 lattice offsets
 
 __device__ __forceinline__ uint32_t saddr(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -707,7 +708,7 @@ int run_aggregate_tc(Ctx* c, const double2* x, float2* out0, cudaStream_t st) {
 // a block.  One launch runs every tile: the pair (mu, nu) of phase ph writes
 // its FP32 product to row ph * p + mu of a partials buffer (no two pairs
 // share a row, so no read-modify-write), and k_near_sum adds each particle's
-// rows in phase order in FP64.
+// rows in phase order.
 int build_near_tc(Ctx* c) {
   c->tcn_ready = false;
   const int n2 = 2 * c->npsi, M4 = 2 * n2, S = c->S, nb = c->nblk;
@@ -740,7 +741,7 @@ int build_near_tc(Ctx* c) {
     const int o = (c->blk_dy[b] + 1) * 3 + (c->blk_dx[b] + 1);
     return o < 4 ? o + 1 : o;
   };
-  const int NPH = 9;
+  const int NPH = NEAR_NPH;
   std::vector<std::vector<int>> pr(NPH);               // pair indices e per phase
   std::vector<int> emu(c->nr_col.size());
   std::vector<unsigned short> seen((size_t)c->p * NPH, 0);
@@ -816,29 +817,43 @@ int build_near_tc(Ctx* c) {
 bool tc_near_ok(const Ctx* c, int R) { return c->tc_enable && c->tcn_ready && R == 1; }
 
 // y[mu][r] = sum over the phases in which mu has a pair, in phase order, of
-// the partial rows (FP64 sums of FP32 products)
-__global__ void k_near_sum(int p, int M4, int nph, const unsigned short* __restrict__ mask,
-                           const float* __restrict__ part, double* __restrict__ y) {
+// the partial rows (FP32).  Thread = 4 consecutive r; the present phases'
+// loads are all issued before the sums.
+__global__ void k_near_sum(int p, int M44, const unsigned short* __restrict__ mask,
+                           const float4* __restrict__ part, double2* __restrict__ y) {
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= (long long)p * M4) return;
-  const int mu = (int)(t / M4), r = (int)(t - (long long)mu * M4);
+  if (t >= (long long)p * M44) return;
+  const int mu = (int)(t / M44), r4 = (int)(t - (long long)mu * M44);
   const unsigned m = mask[mu];
-  double a = 0.0;
-  for (int ph = 0; ph < nph; ++ph)
-    if (m >> ph & 1u) a += (double)part[((size_t)ph * p + mu) * M4 + r];
-  y[t] = a;
+  float4 v[NEAR_NPH];
+#pragma unroll
+  for (int ph = 0; ph < NEAR_NPH; ++ph)
+    v[ph] = (m >> ph & 1u) ? part[((size_t)ph * p + mu) * M44 + r4] : make_float4(0.f, 0.f, 0.f, 0.f);
+  // FP32 sums (FP64 adds and conversions run at 1/64 of the FP32 rate here;
+  // the CUDA-core near kernel accumulates in FP32 too)
+  float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+  for (int ph = 0; ph < NEAR_NPH; ++ph)
+    if (m >> ph & 1u) {
+      a.x += v[ph].x;
+      a.y += v[ph].y;
+      a.z += v[ph].z;
+      a.w += v[ph].w;
+    }
+  y[2 * t] = make_double2(a.x, a.y);
+  y[2 * t + 1] = make_double2(a.z, a.w);
 }
 
 int run_near_tc(Ctx* c, const double2* x, double2* y, cudaStream_t st) {
   const int n2 = 2 * c->npsi, M4 = 2 * n2;
   const long long n = (long long)c->p * n2;
-  const int nph = (int)c->tcn_phase.size() - 1, nt = c->tcn_phase.back();
+  const int nt = c->tcn_phase.back();
   pbeg(c, st, "near", -1, (double)n * 24.0, 0.0);
   k_x32<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, x, c->d_x32);
   SMR_LAUNCH(c);
   pend(c, st);
   double bytes = 0, flops = 0;
-  for (int ph = 0; ph < nph; ++ph) {
+  for (size_t ph = 0; ph < c->tcn_bytes.size(); ++ph) {
     bytes += c->tcn_bytes[ph];
     flops += c->tcn_flops[ph];
   }
@@ -849,10 +864,10 @@ int run_near_tc(Ctx* c, const double2* x, double2* y, cudaStream_t st) {
       c->d_tcn_img, reinterpret_cast<const float*>(c->d_x32), c->d_tcn_part, 0, c->d_tc_err);
   SMR_LAUNCH(c);
   pend(c, st);
-  const long long nm = (long long)c->p * M4;
+  const long long nm = (long long)c->p * M4, nt4 = nm / 4;
   pbeg(c, st, "near", -1, (double)nm * 8.0 + (double)c->nr_col.size() * M4 * 4.0 + 2.0 * c->p, 0.0);
-  k_near_sum<<<(unsigned)((nm + 255) / 256), 256, 0, st>>>(c->p, M4, nph, c->d_tcn_mask, c->d_tcn_part,
-                                                          reinterpret_cast<double*>(y));
+  k_near_sum<<<(unsigned)((nt4 + 255) / 256), 256, 0, st>>>(c->p, M4 / 4, c->d_tcn_mask,
+                                                           reinterpret_cast<const float4*>(c->d_tcn_part), y);
   SMR_LAUNCH(c);
   pend(c, st);
   return SMR_OK;
