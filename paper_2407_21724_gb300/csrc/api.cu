@@ -850,8 +850,8 @@ int smr_matvec_parts(smr_ctx* h, int R, const void* x, void* y_near, void* y_far
   if (precision != SMR_PREC_FP64 && precision != SMR_PREC_FP32)
     return fail(c, SMR_E_INVALID_ARG, "precision must be SMR_PREC_FP64 or SMR_PREC_FP32");
   cudaStream_t st = (cudaStream_t)stream;
-  int rc = SMR_OK;
-  if (y_near) rc = run_near(c, R, precision, (const double2*)x, (double2*)y_near, st);
+  int rc = prep_x32(c, R, precision, (const double2*)x, st);
+  if (!rc && y_near) rc = run_near(c, R, precision, (const double2*)x, (double2*)y_near, st);
   if (rc) return rc;
   if (y_far) rc = run_far(c, R, precision, (const double2*)x, (double2*)y_far, false, st);
   return rc;

@@ -26,6 +26,7 @@ template <> __device__ __forceinline__ double2 czero<double2>() { return make_do
 template <> __device__ __forceinline__ float2 czero<float2>() { return make_float2(0.f, 0.f); }
 __device__ __forceinline__ double2 cvt2(double2 v, double2) { return v; }
 __device__ __forceinline__ float2 cvt2(double2 v, float2) { return make_float2((float)v.x, (float)v.y); }
+__device__ __forceinline__ float2 cvt2(float2 v, float2) { return v; }
 __device__ __forceinline__ double2 to64(double2 v) { return v; }
 __device__ __forceinline__ double2 to64(float2 v) { return make_double2(v.x, v.y); }
 
@@ -998,11 +999,11 @@ __global__ void k_receive(int K0, int npsi, int R, int RC, const int* __restrict
 
 // ------------------------------------------------------------------ block-sparse product
 // y[mu][i][r] (+)= sum_{e in row mu} sum_j B[blk_e][i][j] x[col_e][j][r]
-template <typename T>
+template <typename T, typename XV = double2>
 __global__ void k_blocksparse(int nrow, int n2, int R, int rc, int nrc, const int* __restrict__ ptr,
                               const int* __restrict__ col, const int* __restrict__ blk,
                               const typename CV<T>::V* __restrict__ Bt,
-                              const double2* __restrict__ x, double2* __restrict__ y,
+                              const XV* __restrict__ x, double2* __restrict__ y,
                               int accumulate) {
   typedef typename CV<T>::V V;
   extern __shared__ unsigned char smem_raw[];
@@ -1013,7 +1014,7 @@ __global__ void k_blocksparse(int nrow, int n2, int R, int rc, int nrc, const in
   bool active = (i < n2) && (rl < nr);
   V acc = czero<V>();
   for (int e = ptr[mu]; e < ptr[mu + 1]; ++e) {
-    const double2* xv = x + (size_t)col[e] * n2 * R + r0;
+    const XV* xv = x + (size_t)col[e] * n2 * R + r0;
     __syncthreads();
     for (int t = threadIdx.x; t < n2 * nr; t += blockDim.x) {
       int jl = t / nr, q = t % nr;
@@ -1106,7 +1107,7 @@ static int far_impl(Ctx* c, int R, const double2* x, double2* y, bool accumulate
              (double)c->p * L0.K * 4 * R_ * es,
          32.0 * c->npsi * c->p * L0.K * R_);
     if (!f64 && tc_aggregate_ok(c, R) && c->tune_tc_agg != 0) {
-      int rc = run_aggregate_tc(c, x, (float2*)L0.d_out, st);
+      int rc = run_aggregate_tc(c, x, c->x32_of == x ? c->d_x32 : nullptr, (float2*)L0.d_out, st);
       pend(c, st);
       if (rc) return rc;
     } else {
@@ -1311,14 +1312,51 @@ static int bs_impl(Ctx* c, int nrow, int R, const int* ptr, const int* col, cons
   return SMR_OK;
 }
 
+__global__ void k_x32f(long long n, const double2* __restrict__ a, float2* __restrict__ b) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) b[i] = make_float2((float)a[i].x, (float)a[i].y);
+}
+
+// The FP32 single right-hand-side product converts x to FP32 once (the
+// conversion runs on the FP64 units, 1/64 of the FP32 rate) for the near
+// gathers and the tensor-core aggregation; c->x32_of records which x the
+// copy holds, so a step that finds another x reads the FP64 one.
+int prep_x32(Ctx* c, int R, int prec, const double2* x, cudaStream_t st) {
+  c->x32_of = nullptr;
+  if (prec != SMR_PREC_FP32 || R != 1 || !c->d_x32) return SMR_OK;
+  const long long n = (long long)c->p * 2 * c->npsi;
+  pbeg(c, st, "convert", -1, (double)n * 24.0, 0.0);
+  k_x32f<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, x, c->d_x32);
+  SMR_LAUNCH(c);
+  pend(c, st);
+  c->x32_of = x;
+  return SMR_OK;
+}
+
 int run_near(Ctx* c, int R, int prec, const double2* x, double2* y, cudaStream_t st) {
-  if (prec == SMR_PREC_FP32 && tc_near_ok(c, R) && c->tune_tc_near != 0) return run_near_tc(c, x, y, st);
+  if (prec == SMR_PREC_FP32 && tc_near_ok(c, R) && c->tune_tc_near != 0) {
+    if (c->x32_of != x) {
+      int rc = prep_x32(c, R, prec, x, st);
+      if (rc) return rc;
+    }
+    return run_near_tc(c, y, st);
+  }
   double n2 = 2.0 * c->npsi, es = prec == SMR_PREC_FP64 ? 16 : 8;
-  pbeg(c, st, "near", -1, 2.0 * c->p * n2 * R * 16 + (double)c->nblk * n2 * n2 * es,
+  const bool x32 = prec == SMR_PREC_FP32 && R == 1 && c->x32_of == x;
+  pbeg(c, st, "near", -1, c->p * n2 * R * (x32 ? 8 + 16 : 16 + 16) + (double)c->nblk * n2 * n2 * es,
        8.0 * n2 * n2 * c->nr_col.size() * R);
-  int rc = (prec == SMR_PREC_FP64)
-               ? bs_impl<double>(c, c->p, R, c->d_nr_ptr, c->d_nr_col, c->d_nr_blk, c->d_B64, x, y, false, st)
-               : bs_impl<float>(c, c->p, R, c->d_nr_ptr, c->d_nr_col, c->d_nr_blk, c->d_B32, x, y, false, st);
+  int rc;
+  if (x32) {
+    const int n2i = 2 * c->npsi;
+    k_blocksparse<float, float2><<<(unsigned)c->p, n2i, (size_t)n2i * sizeof(float2), st>>>(
+        c->p, n2i, 1, 1, 1, c->d_nr_ptr, c->d_nr_col, c->d_nr_blk, c->d_B32, c->d_x32, y, 0);
+    SMR_LAUNCH(c);
+    rc = SMR_OK;
+  } else {
+    rc = (prec == SMR_PREC_FP64)
+             ? bs_impl<double>(c, c->p, R, c->d_nr_ptr, c->d_nr_col, c->d_nr_blk, c->d_B64, x, y, false, st)
+             : bs_impl<float>(c, c->p, R, c->d_nr_ptr, c->d_nr_col, c->d_nr_blk, c->d_B32, x, y, false, st);
+  }
   pend(c, st);
   return rc;
 }
@@ -1376,7 +1414,8 @@ int ensure_split(Ctx* c, int R) {
 // multiplied, and y is transposed back.
 int run_product(Ctx* c, int R, int prec, const double2* x, double2* y, cudaStream_t st) {
   if (!split_columns(c, R, prec)) {
-    int rc = run_near(c, R, prec, x, y, st);
+    int rc = prep_x32(c, R, prec, x, st);
+    if (!rc) rc = run_near(c, R, prec, x, y, st);
     if (rc) return rc;
     return run_far(c, R, prec, x, y, true, st);
   }
@@ -1390,7 +1429,8 @@ int run_product(Ctx* c, int R, int prec, const double2* x, double2* y, cudaStrea
   pend(c, st);
   if (rc) return rc;
   for (int r = 0; r < R && !rc; ++r) {
-    rc = run_near(c, 1, prec, xs + (size_t)r * n, ys + (size_t)r * n, st);
+    rc = prep_x32(c, 1, prec, xs + (size_t)r * n, st);
+    if (!rc) rc = run_near(c, 1, prec, xs + (size_t)r * n, ys + (size_t)r * n, st);
     if (!rc) rc = run_far(c, 1, prec, xs + (size_t)r * n, ys + (size_t)r * n, true, st);
   }
   if (rc) return rc;

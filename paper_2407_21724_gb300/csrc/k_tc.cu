@@ -372,12 +372,13 @@ constexpr int AG_NS = 3;                       // coefficient-image stages
 constexpr int AG_KCMAX = 4;                    // K chunks (K' <= 128)
 constexpr size_t AG_SMEM = (size_t)2 * AG_KCMAX * TC_BBYTES + (size_t)AG_NS * 2 * TC_ABYTES + 1024 + 1024;
 
+template <typename XT>
 __global__ void __launch_bounds__(288, 1) k_aggregate_tc(int nMT, int nKc, int K4, int npsi2,
                                                          const int* __restrict__ tshape,
                                                          const int* __restrict__ tstart,
                                                          const int* __restrict__ tcount,
                                                          const int* __restrict__ perm, const float* __restrict__ A,
-                                                         const double* __restrict__ x, float* __restrict__ out0,
+                                                         const XT* __restrict__ x, float* __restrict__ out0,
                                                          int* __restrict__ err) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* sm = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -436,22 +437,39 @@ __global__ void __launch_bounds__(288, 1) k_aggregate_tc(int nMT, int nKc, int K
       const int row = g / (2 * per_cur), rem = g - row * (2 * per_cur);
       const int cur = rem / per_cur, q4 = rem - cur * per_cur;
       const int mu = mus[row], kl = 4 * q4;
-      double v[4] = {0.0, 0.0, 0.0, 0.0};
-      if (mu >= 0) {
-        const double* xr = x + (size_t)mu * Kx + cur * npsi2;
-        if (kl + 3 < npsi2) {
-          double2 a = *reinterpret_cast<const double2*>(xr + kl), b = *reinterpret_cast<const double2*>(xr + kl + 2);
-          v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
-        } else {
-          for (int e = 0; e < 4; ++e)
-            if (kl + e < npsi2) v[e] = xr[kl + e];
-        }
-      }
       float4 h, l;
-      h.x = tf32r((float)v[0]); l.x = tf32r((float)(v[0] - (double)h.x));
-      h.y = tf32r((float)v[1]); l.y = tf32r((float)(v[1] - (double)h.y));
-      h.z = tf32r((float)v[2]); l.z = tf32r((float)(v[2] - (double)h.z));
-      h.w = tf32r((float)v[3]); l.w = tf32r((float)(v[3] - (double)h.w));
+      if constexpr (sizeof(XT) == 4) {
+        // FP32 copy of x: the split stays on the FP32 units
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (mu >= 0) {
+          const float* xr = x + (size_t)mu * Kx + cur * npsi2;
+          if (kl + 3 < npsi2) {
+            v = *reinterpret_cast<const float4*>(xr + kl);
+          } else {
+            if (kl < npsi2) v.x = xr[kl];
+            if (kl + 1 < npsi2) v.y = xr[kl + 1];
+            if (kl + 2 < npsi2) v.z = xr[kl + 2];
+          }
+        }
+        h = make_float4(tf32r(v.x), tf32r(v.y), tf32r(v.z), tf32r(v.w));
+        l = make_float4(tf32r(v.x - h.x), tf32r(v.y - h.y), tf32r(v.z - h.z), tf32r(v.w - h.w));
+      } else {
+        double v[4] = {0.0, 0.0, 0.0, 0.0};
+        if (mu >= 0) {
+          const double* xr = x + (size_t)mu * Kx + cur * npsi2;
+          if (kl + 3 < npsi2) {
+            double2 a = *reinterpret_cast<const double2*>(xr + kl), b = *reinterpret_cast<const double2*>(xr + kl + 2);
+            v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+          } else {
+            for (int e = 0; e < 4; ++e)
+              if (kl + e < npsi2) v[e] = xr[kl + e];
+          }
+        }
+        h.x = tf32r((float)v[0]); l.x = tf32r((float)(v[0] - (double)h.x));
+        h.y = tf32r((float)v[1]); l.y = tf32r((float)(v[1] - (double)h.y));
+        h.z = tf32r((float)v[2]); l.z = tf32r((float)(v[2] - (double)h.z));
+        h.w = tf32r((float)v[3]); l.w = tf32r((float)(v[3] - (double)h.w));
+      }
       const int c = cur * nKc + (q4 >> 3), q = q4 & 7;
       const int off = (c * 128 + row) * 32 + ((q ^ (row & 7)) << 2);
       *reinterpret_cast<float4*>(Bh + off) = h;
@@ -557,11 +575,6 @@ __global__ void __launch_bounds__(288, 1) k_aggregate_tc(int nMT, int nKc, int K
     tc_after();
     tmem_dealloc(tmem, 2 * TC_NP);
   }
-}
-
-__global__ void k_x32(long long n, const double2* __restrict__ a, float2* __restrict__ b) {
-  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (i < n) b[i] = make_float2((float)a[i].x, (float)a[i].y);
 }
 
 // TF32 rounding on the host (round to nearest, ties away), for the split
@@ -691,11 +704,21 @@ bool tc_aggregate_ok(const Ctx* c, int R) {
   return c->tc_enable && c->tc_ready && c->tc_agg_ready && R == 1 && !c->any_dshift;
 }
 
-int run_aggregate_tc(Ctx* c, const double2* x, float2* out0, cudaStream_t st) {
-  cudaFuncSetAttribute(k_aggregate_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)AG_SMEM);
-  k_aggregate_tc<<<(unsigned)c->tc_ntile, 288, AG_SMEM, st>>>(
-      c->tc_nMT, c->tc_nKc, 4 * c->lev[0].K, 2 * c->npsi, c->d_tc_shape, c->d_tc_start, c->d_tc_count,
-      c->d_tc_perm, c->d_tc_agg, reinterpret_cast<const double*>(x), reinterpret_cast<float*>(out0), c->d_tc_err);
+// x32: FP32 copy of x (prep_x32), or null to split the FP64 x
+int run_aggregate_tc(Ctx* c, const double2* x, const float2* x32, float2* out0, cudaStream_t st) {
+  if (x32) {
+    cudaFuncSetAttribute(k_aggregate_tc<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)AG_SMEM);
+    k_aggregate_tc<float><<<(unsigned)c->tc_ntile, 288, AG_SMEM, st>>>(
+        c->tc_nMT, c->tc_nKc, 4 * c->lev[0].K, 2 * c->npsi, c->d_tc_shape, c->d_tc_start, c->d_tc_count,
+        c->d_tc_perm, c->d_tc_agg, reinterpret_cast<const float*>(x32), reinterpret_cast<float*>(out0),
+        c->d_tc_err);
+  } else {
+    cudaFuncSetAttribute(k_aggregate_tc<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)AG_SMEM);
+    k_aggregate_tc<double><<<(unsigned)c->tc_ntile, 288, AG_SMEM, st>>>(
+        c->tc_nMT, c->tc_nKc, 4 * c->lev[0].K, 2 * c->npsi, c->d_tc_shape, c->d_tc_start, c->d_tc_count,
+        c->d_tc_perm, c->d_tc_agg, reinterpret_cast<const double*>(x), reinterpret_cast<float*>(out0),
+        c->d_tc_err);
+  }
   SMR_LAUNCH(c);
   return SMR_OK;
 }
@@ -844,14 +867,10 @@ __global__ void k_near_sum(int p, int M44, const unsigned short* __restrict__ ma
   y[2 * t + 1] = make_double2(a.z, a.w);
 }
 
-int run_near_tc(Ctx* c, const double2* x, double2* y, cudaStream_t st) {
+// x must already be in d_x32 (prep_x32)
+int run_near_tc(Ctx* c, double2* y, cudaStream_t st) {
   const int n2 = 2 * c->npsi, M4 = 2 * n2;
-  const long long n = (long long)c->p * n2;
   const int nt = c->tcn_phase.back();
-  pbeg(c, st, "near", -1, (double)n * 24.0, 0.0);
-  k_x32<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, x, c->d_x32);
-  SMR_LAUNCH(c);
-  pend(c, st);
   double bytes = 0, flops = 0;
   for (size_t ph = 0; ph < c->tcn_bytes.size(); ++ph) {
     bytes += c->tcn_bytes[ph];

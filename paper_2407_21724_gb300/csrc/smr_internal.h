@@ -266,6 +266,7 @@ struct Ctx {
   unsigned short* d_tcn_mask = nullptr;   // per particle: phases in which it has a pair
   float* d_tcn_part = nullptr;            // [phase][p][4 n_psi] FP32 partial products
   float2* d_x32 = nullptr;                // x in FP32 for the gathers
+  const double2* x32_of = nullptr;        // which x d_x32 holds (set by prep_x32)
   // column buffers of split products ([R][N] in, [R][N] out)
   bool split_cols = true;
   double2* d_split = nullptr;
@@ -365,8 +366,9 @@ int run_receive_tc(Ctx* c, const float2* in0, double2* y, bool accumulate, cudaS
 bool tc_aggregate_ok(const Ctx* c, int R);
 int build_near_tc(Ctx* c);
 bool tc_near_ok(const Ctx* c, int R);
-int run_near_tc(Ctx* c, const double2* x, double2* y, cudaStream_t st);
-int run_aggregate_tc(Ctx* c, const double2* x, float2* out0, cudaStream_t st);
+int run_near_tc(Ctx* c, double2* y, cudaStream_t st);
+int prep_x32(Ctx* c, int R, int prec, const double2* x, cudaStream_t st);
+int run_aggregate_tc(Ctx* c, const double2* x, const float2* x32, float2* out0, cudaStream_t st);
 int tc_check(Ctx* c);
 
 // ------------------------------------------------------------------ linear algebra (k_linalg.cu)
