@@ -494,6 +494,12 @@ def run_ours(a):
         for line in r.stdout.splitlines():
             if line.startswith("{"):
                 cpu = json.loads(line)["cpu_baseline"]
+        if cpu and gm and "plain_fp64" in gm and cpu.get("value"):
+            # the oracle cannot run the full solve here: its GMRES time is the
+            # extrapolation (plain GPU iteration count + 1) x oracle time per product
+            it = gm["plain_fp64"]["iters"] + 1
+            cpu["gmres_seconds_extrapolated"] = it * R / cpu["value"]
+            cpu["gmres_extrapolation"] = f"{it} products (the plain FP64 solve's count) x oracle seconds per product"
     smr.smr_destroy(ctx)
     if rank == 0:
         line = dict(metric=METRIC, value=value, unit="matvecs/s", n_gpus=world, steps=a.steps,
