@@ -714,6 +714,7 @@ struct Work {
   double2* coef = nullptr; // device [4][m+2][R] coefficients
   float2* coef_f = nullptr;  // device [3][m+2] FP32 coefficient copies
   double2* part = nullptr; // reduction partials
+  double2* hpin = nullptr; // pinned host copy of the coefficient area read each iteration
   cudaEvent_t ev[6] = {};
   double t_pc = 0, t_mv = 0, t_or = 0;   // seconds in preconditioner, products, Gram-Schmidt
 };
@@ -839,7 +840,10 @@ static int gmres_core(Ctx* c, int R, int prec, int precond, const double2* rhs, 
   // host Hessenberg storage per column (rotated), rotations, rhs g
   std::vector<std::complex<double>> H((size_t)(m + 1) * m * R), g((size_t)(m + 1) * R);
   std::vector<std::complex<double>> cs((size_t)m * R), sn((size_t)m * R);
-  std::vector<double2> hbuf((size_t)(2 * (m + 1) + 2) * R);
+  // pinned host mirror of the coefficient area; each iteration copies only
+  // the live part (j + 1 coefficients per column and the two norms)
+  double2* hbuf = W.hpin;
+  const size_t onrm = (size_t)2 * (m + 1) * R;             // dnr, dn0 in the area
   // v_j <- a * src (per column a[r] on the device at dsc)
   auto store_basis = [&](int j, const double2* src) -> int {
     if (W.f32 && R == 1) k_narrow_scale<<<nb, 256, 0, st>>>(n, dsc, src, (float2*)Vj(j));
@@ -894,7 +898,8 @@ static int gmres_core(Ctx* c, int R, int prec, int precond, const double2* rhs, 
       rc = gs_pass(c, W, j + 1, n, R, ld, dh1, dh1f, dn0, dnr, st);
       if (rc) return rc;
       cudaEventRecord(W.ev[3], st);
-      SMR_CUDA(c, cudaMemcpyAsync(hbuf.data(), W.coef, (size_t)(2 * (m + 1) + 2) * R * sizeof(double2),
+      SMR_CUDA(c, cudaMemcpyAsync(hbuf, W.coef, (size_t)(j + 1) * R * sizeof(double2), cudaMemcpyDeviceToHost, st));
+      SMR_CUDA(c, cudaMemcpyAsync(hbuf + onrm, W.coef + onrm, (size_t)2 * R * sizeof(double2),
                                   cudaMemcpyDeviceToHost, st));
       SMR_CUDA(c, cudaStreamSynchronize(st));
       W.t_pc += elapsed_s(W.ev[0], W.ev[1]);
@@ -911,12 +916,13 @@ static int gmres_core(Ctx* c, int R, int prec, int precond, const double2* rhs, 
         rc = gs_pass(c, W, j + 1, n, R, ld, dh2, dh2f, nullptr, dnr, st);
         if (rc) return rc;
         cudaEventRecord(W.ev[5], st);
-        SMR_CUDA(c, cudaMemcpyAsync(hbuf.data() + (size_t)(m + 1) * R, dh2,
-                                    (size_t)((m + 1) + 1) * R * sizeof(double2), cudaMemcpyDeviceToHost, st));
+        SMR_CUDA(c, cudaMemcpyAsync(hbuf + (size_t)(m + 1) * R, dh2, (size_t)(j + 1) * R * sizeof(double2),
+                                    cudaMemcpyDeviceToHost, st));
+        SMR_CUDA(c, cudaMemcpyAsync(hbuf + onrm, dnr, (size_t)R * sizeof(double2), cudaMemcpyDeviceToHost, st));
         SMR_CUDA(c, cudaStreamSynchronize(st));
         W.t_or += elapsed_s(W.ev[4], W.ev[5]);
       } else {
-        for (size_t q = 0; q < (size_t)(m + 1) * R; ++q) hbuf[(size_t)(m + 1) * R + q] = make_double2(0, 0);
+        for (size_t q = 0; q < (size_t)(j + 1) * R; ++q) hbuf[(size_t)(m + 1) * R + q] = make_double2(0, 0);
       }
       // next basis vector v_{j+1} = w / ||w||
       std::vector<double2> inv(R);
@@ -1033,6 +1039,7 @@ int solve(Ctx* c, int R, const double2* b, double2* x, const smr_solve_opts* o, 
   auto cleanup = [&]() {
     cudaFree(W.V); cudaFree(W.u); cudaFree(W.w); cudaFree(W.t); cudaFree(W.coef); cudaFree(W.coef_f);
     cudaFree(W.part);
+    if (W.hpin) cudaFreeHost(W.hpin);
     for (int q = 0; q < 6; ++q)
       if (W.ev[q]) cudaEventDestroy(W.ev[q]);
   };
@@ -1042,7 +1049,8 @@ int solve(Ctx* c, int R, const double2* b, double2* x, const smr_solve_opts* o, 
             cudaMalloc((void**)&W.t, ld * sizeof(double2)) == cudaSuccess &&
             cudaMalloc((void**)&W.coef, (size_t)4 * (m + 2) * R * sizeof(double2)) == cudaSuccess &&
             cudaMalloc((void**)&W.coef_f, (size_t)3 * (m + 2) * R * sizeof(float2)) == cudaSuccess &&
-            cudaMalloc((void**)&W.part, part_elems(n, R, m + 2) * sizeof(double2)) == cudaSuccess;
+            cudaMalloc((void**)&W.part, part_elems(n, R, m + 2) * sizeof(double2)) == cudaSuccess &&
+            cudaMallocHost((void**)&W.hpin, (size_t)(2 * (m + 1) + 2) * R * sizeof(double2)) == cudaSuccess;
   for (int q = 0; q < 6 && ok; ++q) ok = cudaEventCreate(&W.ev[q]) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
