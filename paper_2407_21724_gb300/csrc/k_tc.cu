@@ -15,8 +15,9 @@
 // The near-field product (block-sparse, Eq. 16 blocks) runs through the same
 // kernel: pairs (mu, nu) that share a block are one GEMM with the block's real
 // form as A (rows (i, re/im) of y_mu, columns (j, re/im) of x_nu) and the
-// gathered x_nu rows as B; one launch per lattice offset, so every y row is
-// written by one CTA per launch.
+// gathered x_nu rows (FP32 copy of x) as B.  Each pair stores its product to
+// its own row of a partials buffer, so all tiles run in one launch, and
+// k_near_sum adds a particle's rows in lattice-offset order.
 //
 // Operands live in shared memory in the K-major 128-byte-swizzled layout:
 // rows of 32 FP32 values (128 bytes), 8-row atoms of 1024 bytes, and the
