@@ -48,6 +48,7 @@ enum {
   SMR_E_NOT_CONVERGED = -5, /* solve hit maxit before the tolerance          */
   SMR_E_BREAKDOWN = -6,     /* Arnoldi breakdown before convergence          */
   SMR_E_NAN = -7,           /* NaN or Inf in a residual                      */
+  SMR_E_TIMEOUT = -8,       /* a bounded device-side wait ran out            */
   SMR_E_STATE = -9          /* call made before smr_set_scene, or similar    */
 };
 
@@ -212,10 +213,21 @@ int smr_set_tensor_cores(smr_ctx* ctx, int enable);
 int smr_autotune(smr_ctx* ctx, int R, int precision, void* stream);
 
 /* Synchronises `stream` and reports errors found on the device since the
- * last check: SMR_E_CUDA if a tensor-core pipeline wait ran out (that
- * product's result is invalid; the kernel stopped, freed its tensor memory
- * and returned).  smr_matvec_host and smr_solve make this check themselves. */
+ * last check: SMR_E_TIMEOUT if a tensor-core pipeline wait ran out (that
+ * product's result is invalid; the kernel stopped issuing, waited for the
+ * copies and MMAs it had already issued, freed its tensor memory and
+ * returned, so the context stays usable).  smr_matvec_host and smr_solve
+ * make this check themselves. */
 int smr_sync(smr_ctx* ctx, void* stream);
+
+/* Polling limit of every bounded wait in the tensor-core kernels (rounds of
+ * mbarrier try_wait before a wait gives up and the product reports
+ * SMR_E_TIMEOUT).  rounds < 0 restores the default (2^24); 0 makes every
+ * wait that has to wait give up at once, which a test uses to exercise the
+ * give-up path without faulting anything.  A CTA that gives up still drains
+ * its in-flight copies and MMAs with the default bound.  Drops captured
+ * products.  No counterpart in the paper. */
+int smr_set_wait_limit(smr_ctx* ctx, long long rounds);
 
 /* z = blockdiag(Z_s^-1) r over particles: the block-diagonal preconditioner
  * of Sec. V (each block the inverse of the particle's self block).
@@ -383,8 +395,9 @@ int smr_copy_level(smr_ctx* ctx, int level, int kind, double* out, size_t n_doub
  *  - The intermediate per-shape sums ([n_shapes][n_psi][2][R] complex128)
  *    live in a fixed 4 MiB array in device global memory that every GPU which
  *    loads libsmr holds until the process exits.  A call needing more
- *    (n_shapes * n_psi * 2 * R * 16 bytes > 4 MiB, e.g. R > 128 with 8 shapes
- *    of 32 modes) fails with SMR_E_INVALID_ARG and a message; split R.
+ *    (n_shapes * n_psi * 2 * R * 16 bytes > 4 MiB, i.e. R > 512 with 8 shapes
+ *    of n_psi = 32 modes per current) fails with SMR_E_INVALID_ARG and a
+ *    message; split R.
  *  - The first call on a device looks up that array's device address (with
  *    the context's device made current) and caches it; make that first call
  *    before any stream capture.
@@ -392,8 +405,10 @@ int smr_copy_level(smr_ctx* ctx, int level, int kind, double* out, size_t n_doub
  *    contents; calls that overlap on the GPU (different streams or threads
  *    without ordering) race on it.  Nothing in it needs clearing: every sum
  *    a call reads was written earlier in the same call.
+ *  - The call makes the context's device current and leaves it current,
+ *    like the other entry points.
  *  - This entry point has no counterpart in the paper; it computes what
- *    smr_rhs_plane_waves computes (Eqs. 5, 18, 19). */
+ *    smr_rhs_plane_waves computes. */
 int smr_rhs_plane_waves_static(smr_ctx* ctx, int R, const double* khat, const double* pol,
                                void* b, void* stream);
 

@@ -21,8 +21,7 @@ against the paper, not to be fast:
 * ``mlfma``    - the MLFMA operator step by step (Sec. IV, Eqs. 22-26): tree,
   k-space sampling, patterns, translation function, Lagrange interpolation and
   its weighted adjoint, aggregation, translation, receive, near SpMV.
-* ``gmres``    - right-preconditioned GMRES (the iterative solve of Sec. V) and
-  flexible GMRES with iterative refinement.
+* ``gmres``    - right-preconditioned GMRES (the iterative solve of Sec. V).
 * ``mlp``      - FP64 forward/backward/Adam for the learned initial guess.
 
 Sign conventions (the paper's equations disagree with one another, so one

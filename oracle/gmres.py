@@ -7,9 +7,7 @@ over the Krylov space of A M^{-1}, x = x0 + M^{-1} u, with modified
 Gram-Schmidt Arnoldi and Givens rotations; the iteration stops when the
 TRUE relative residual ||b - A x|| / ||b|| reaches ``tol`` (checked whenever
 the Givens estimate does).  M^{-1} is the block-diagonal preconditioner built
-from the self blocks Z_s (Sec. V, stage v).  ``fgmres`` is the flexible
-variant (the preconditioner may change per iteration), and ``gmres_ir`` the
-iterative refinement loop with an FP64 outer residual.
+from the self blocks Z_s (Sec. V, stage v).
 """
 import numpy as np
 
@@ -82,50 +80,3 @@ def gmres(matvec, b, precond=None, x0=None, tol=1e-4, restart=None, maxit=2000):
         x = x + M(V[:j_end].T @ y)
         r = b - matvec(x)
         mvs += 1
-
-
-def fgmres(matvec, b, precond_j, x0=None, tol=1e-4, maxit=2000):
-    """Flexible GMRES: z_j = precond_j(j, v_j) may vary with j."""
-    b = np.asarray(b, dtype=complex)
-    n = b.size
-    bn = np.linalg.norm(b)
-    x = np.zeros(n, dtype=complex) if x0 is None else np.array(x0, dtype=complex)
-    r = b - matvec(x) if x0 is not None else b.copy()
-    beta = np.linalg.norm(r)
-    if beta / bn <= tol:
-        return x, dict(iters=0, resid_true=beta / bn)
-    m = maxit
-    V = np.zeros((m + 1, n), dtype=complex)
-    Zs = np.zeros((m, n), dtype=complex)
-    H = np.zeros((m + 1, m), dtype=complex)
-    V[0] = r / beta
-    e = np.zeros(m + 1, dtype=complex)
-    e[0] = beta
-    for j in range(m):
-        Zs[j] = precond_j(j, V[j])
-        w = matvec(Zs[j])
-        for i in range(j + 1):
-            H[i, j] = np.vdot(V[i], w)
-            w = w - H[i, j] * V[i]
-        H[j + 1, j] = np.linalg.norm(w)
-        V[j + 1] = w / H[j + 1, j]
-        y, *_ = np.linalg.lstsq(H[:j + 2, :j + 1], e[:j + 2], rcond=None)
-        res = np.linalg.norm(e[:j + 2] - H[:j + 2, :j + 1] @ y) / bn
-        if res <= tol:
-            break
-    x = x + Zs[:j + 1].T @ y
-    return x, dict(iters=j + 1, resid_true=np.linalg.norm(b - matvec(x)) / bn)
-
-
-def gmres_ir(matvec_hi, inner_solve, b, tol=1e-4, max_outer=10):
-    """Iterative refinement: r = b - A_hi x in FP64; d = inner_solve(r); x += d."""
-    b = np.asarray(b, dtype=complex)
-    bn = np.linalg.norm(b)
-    x = np.zeros_like(b)
-    r = b.copy()
-    outer = 0
-    while np.linalg.norm(r) / bn > tol and outer < max_outer:
-        x = x + inner_solve(r)
-        r = b - matvec_hi(x)
-        outer += 1
-    return x, dict(outer=outer, resid_true=np.linalg.norm(r) / bn)

@@ -238,6 +238,26 @@ def extinction_cross_section(scene, x, khat, pol):
     return float(-(4 * np.pi / scene.outer.k) * np.imag(np.vdot(pol, F)) / np.vdot(pol, pol).real)
 
 
+def _L_op(k, g, dg, cur, dv):
+    """L{X} = -j k int g X - (j/k) grad int g div'X at the field points; g and
+    dg = grad_r g carry the quadrature weights, cur (Q,3) and dv (Q,) are X
+    and div'X at the quadrature points."""
+    return -1j * k * (g @ cur) - (1j / k) * np.einsum('pqc,q->pc', dg, dv)
+
+
+def _K_op(dg, cur):
+    """K{X} = curl int g X = int grad_r g x X."""
+    Kx = np.einsum('pqc,qd->pcd', dg, cur)              # grad g (x) X
+    return np.stack([Kx[:, 1, 2] - Kx[:, 2, 1], Kx[:, 2, 0] - Kx[:, 0, 2],
+                     Kx[:, 0, 1] - Kx[:, 1, 0]], axis=1)
+
+
+def _fields(z, LJ, KJ, LM, KM):
+    """Scattered fields of the equivalent currents J, M (the sign conventions
+    of the package docstring): E = -zeta L{J} + K{M}, H = -K{J} - L{M}/zeta."""
+    return -z * LJ + KM, -KJ - LM / z
+
+
 def near_field(scene, x, points):
     """Scattered E and H at points outside every particle (n,3) by direct
     surface quadrature with the full Green's dyadic:
@@ -261,12 +281,9 @@ def near_field(scene, x, points):
         for c in range(2):
             cur = np.einsum('n,nqc->qc', xx[mu, c], psi)     # (Q,3)
             dv = np.einsum('n,nq->q', xx[mu, c], div)          # (Q,)
-            L = -1j * k * (g @ cur) - (1j / k) * np.einsum('pqc,q->pc', dg, dv)
-            Kx = np.einsum('pqc,qd->pcd', dg, cur)              # grad g (x) X
-            Kc = np.stack([Kx[:, 1, 2] - Kx[:, 2, 1], Kx[:, 2, 0] - Kx[:, 0, 2],
-                           Kx[:, 0, 1] - Kx[:, 1, 0]], axis=1)  # grad g x X
-            out.append((L, Kc))
+            out.append((_L_op(k, g, dg, cur, dv), _K_op(dg, cur)))
         (LJ, KJ), (LM, KM) = out
-        E += -z * LJ + KM
-        H += -KJ - LM / z
+        Eq, Hq = _fields(z, LJ, KJ, LM, KM)
+        E += Eq
+        H += Hq
     return E, H

@@ -910,6 +910,15 @@ int smr_set_tensor_cores(smr_ctx* h, int enable) {
   return SMR_OK;
 }
 
+int smr_set_wait_limit(smr_ctx* h, long long rounds) {
+  if (!h) return SMR_E_INVALID_ARG;
+  Ctx* c = &h->c;
+  if (rounds > 0x7fffffffLL) return fail(c, SMR_E_INVALID_ARG, "wait limit above 2^31 - 1 rounds");
+  c->tc_spin = rounds < 0 ? (1u << 24) : (uint32_t)rounds;
+  free_graphs(c);                              // captured products carry the old limit
+  return SMR_OK;
+}
+
 int smr_sync(smr_ctx* h, void* stream) {
   if (!h) return SMR_E_INVALID_ARG;
   Ctx* c = &h->c;

@@ -827,6 +827,10 @@ static int gmres_core(Ctx* c, int R, int prec, int precond, const double2* rhs, 
     SMR_CUDA(c, cudaMemsetAsync(d, 0, ld * sizeof(double2), st));
   }
   std::vector<int> done(R, 0);
+  // columns whose Krylov space became invariant (Arnoldi breakdown); if the
+  // true residual is still above the tolerance after that cycle's update,
+  // no further iteration can lower it and the solve stops with BREAKDOWN
+  std::vector<int> broke(R, 0);
   rel_out.assign(R, 1.0);
   // coefficient areas on the device
   double2* dh1 = W.coef;                                    // [m+1][R]
@@ -862,6 +866,13 @@ static int gmres_core(Ctx* c, int R, int prec, int precond, const double2* rhs, 
       if (rel_out[r] <= tol_col[r]) done[r] = 1;
       all = all && done[r];
     }
+    for (int r = 0; r < R; ++r)
+      if (broke[r] && !done[r]) {
+        c->err = "Arnoldi breakdown: the Krylov space of right-hand side " + std::to_string(r) +
+                 " became invariant with the true relative residual at " + std::to_string(rel_out[r]) +
+                 " (singular or nearly singular operator)";
+        return SMR_E_BREAKDOWN;
+      }
     if (all || *its >= maxit) return all ? SMR_OK : SMR_E_NOT_CONVERGED;
     std::vector<double2> sc(R);
     for (int r = 0; r < R; ++r) sc[r] = make_double2(beta[r] > 0 ? 1.0 / beta[r] : 0.0, 0);
@@ -967,7 +978,11 @@ static int gmres_core(Ctx* c, int R, int prec, int precond, const double2* rhs, 
         double est = std::abs(gr[j + 1]) / bn[r];
         rel_out[r] = est;
         if (!std::isfinite(est)) { c->err = "NaN in Givens update"; return SMR_E_NAN; }
-        if (est <= tol_col[r] || hn[r] == 0.0) active[r] = 0;
+        // breakdown: the new direction vanishes against the norm of A M^-1 v_j
+        // (exactly, or to 1e-13 of it in FP64, where projection noise is ~1e-16)
+        const double w0 = std::sqrt(std::max(0.0, hbuf[(size_t)2 * (m + 1) * R + R + r].x));
+        if (hn[r] == 0.0 || (!W.f32 && hn[r] <= 1e-13 * w0)) broke[r] = 1;
+        if (est <= tol_col[r] || broke[r]) active[r] = 0;
         any = any || active[r];
       }
       if (!any) { ++j; break; }

@@ -1499,6 +1499,10 @@ int run_matvec_graph(Ctx* c, int R, int prec, const double2* x, double2* y, cuda
 }
 
 int run_precond(Ctx* c, int R, int prec, const double2* r, double2* z, cudaStream_t st) {
+  if (!c->pinv_ok) {
+    c->err = "a self block is singular: the block-diagonal preconditioner is undefined";
+    return SMR_E_INVALID_ARG;
+  }
   if (prec == SMR_PREC_FP64)
     return bs_impl<double>(c, c->p, R, c->d_pc_ptr, c->d_pc_col, c->d_pc_blk, c->d_Pinv64, r, z, false, st);
   return bs_impl<float>(c, c->p, R, c->d_pc_ptr, c->d_pc_col, c->d_pc_blk, c->d_Pinv32, r, z, false, st);

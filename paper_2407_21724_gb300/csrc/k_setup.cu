@@ -361,14 +361,18 @@ int build_near(Ctx* c) {
   int nb_total = c->nblk;   // self blocks first (S), then exterior blocks
   size_t bsz = (size_t)n2 * n2;
   std::vector<double2> selfT((size_t)S * bsz), invT((size_t)S * bsz);
+  c->pinv_ok = true;
   for (int s = 0; s < S; ++s) {
     std::vector<cd> Z;
     if (c->shapes[s].sampled) Z = c->shapes[s].Z;
     else sphere_self_block(c->shapes[s], c->k, c->zeta, c->k_in, c->zeta_in, Z);
     std::vector<cd> Zi = Z;
     if (!hm::invert(n2, Zi)) {
-      c->err = "singular self block";
-      return SMR_E_INVALID_ARG;
+      // a singular self block (possible only for shapes given as data)
+      // leaves the block-diagonal preconditioner undefined; the product and
+      // the unpreconditioned solve still run
+      c->pinv_ok = false;
+      std::fill(Zi.begin(), Zi.end(), cd(0.0, 0.0));
     }
     for (int i = 0; i < n2; ++i)
       for (int j = 0; j < n2; ++j) {

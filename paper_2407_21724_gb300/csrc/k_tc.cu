@@ -24,8 +24,11 @@
 // 16-byte chunk q of row r stored at chunk q ^ (r mod 8).  The coefficient
 // images are built in that layout on the host and copied with one bulk copy
 // per K chunk; the spectra are gathered, split and swizzled by the threads.
-// Every wait is bounded; a wait that runs out sets an error flag, the CTA
-// stops issuing work, frees its tensor memory and returns.
+// Every wait is bounded by a polling limit passed to the kernel (the
+// context's wait limit).  A wait that runs out sets an error flag; the CTA
+// then stops issuing work, waits (with the fixed drain bound TC_SPIN) for
+// every bulk copy and MMA commit it has already issued, frees its tensor
+// memory and returns, so nothing asynchronous outlives it.
 #include <algorithm>
 #include <complex>
 #include <cstring>
@@ -45,7 +48,7 @@ constexpr int TC_STAGE = 2 * TC_ABYTES + 2 * TC_BBYTES;
 constexpr int TC_NSTAGE = 3;
 constexpr int TC_PF = 3;                       // spectrum chunks of loads in flight per producer
 constexpr size_t TC_SMEM = (size_t)TC_NSTAGE * TC_STAGE + 1024 + 2048;   // + alignment, barriers, ids
-constexpr uint32_t TC_SPIN = 1u << 24;         // try_wait rounds before giving up
+constexpr uint32_t TC_SPIN = 1u << 24;         // default polling limit; also the drain bound
 constexpr int NEAR_NPH = 9;                    // near-product phases: self blocks + 8 lattice offsets
 
 __device__ __forceinline__ uint32_t saddr(const void* p) {
@@ -89,10 +92,20 @@ __device__ __forceinline__ bool mbar_test(uint32_t a, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// bounded wait: false if the phase did not complete
-__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity) {
-  for (uint32_t i = 0; i < TC_SPIN; ++i)
+// bounded wait: false if the phase did not complete within `limit` polls
+__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, uint32_t limit) {
+  for (uint32_t i = 0; i < limit; ++i)
     if (mbar_test(a, parity)) return true;
+  return false;
+}
+// bounded wait that also gives up as soon as another warp of the CTA has
+// raised the abort flag
+__device__ __forceinline__ bool mbar_wait_or_abort(uint32_t a, uint32_t parity, uint32_t limit,
+                                                   volatile int* abort_flag) {
+  for (uint32_t i = 0; i < limit; ++i) {
+    if (mbar_test(a, parity)) return true;
+    if (*abort_flag) return false;
+  }
   return false;
 }
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
@@ -193,7 +206,7 @@ __global__ void __launch_bounds__(288, 1) k_receive_tc(int nK, int K8, int M4, c
                                                        const int* __restrict__ perm,
                                                        const int* __restrict__ yperm, const float* __restrict__ A,
                                                        const float* __restrict__ in0, YT* __restrict__ y,
-                                                       int accumulate, int* __restrict__ err) {
+                                                       int accumulate, uint32_t spin, int* __restrict__ err) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* sm = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   // barriers: fullA[NS] (bulk copy bytes), fullB[NS] (8 producer warps), done[NS] (MMA commit)
@@ -247,12 +260,7 @@ __global__ void __launch_bounds__(288, 1) k_receive_tc(int nK, int K8, int M4, c
           // lane 0 waits for the stage; the outcome is shared so the warp
           // takes one path (the arrive below needs all 32 lanes)
           bool ok = c < TC_NSTAGE;
-          if (!ok && lane == 0) {
-            for (uint32_t i = 0; i < TC_SPIN && !ok; ++i) {
-              ok = mbar_test(done(st), (use - 1) & 1);
-              if (!ok && *abort_flag) break;
-            }
-          }
+          if (!ok && lane == 0) ok = mbar_wait_or_abort(done(st), (use - 1) & 1, spin, abort_flag);
           ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
           if (!ok) {
             bad = true;
@@ -276,17 +284,17 @@ __global__ void __launch_bounds__(288, 1) k_receive_tc(int nK, int K8, int M4, c
       mbar_expect_tx(fullA(st), 2 * TC_ABYTES);
       bulk_g2s(sm0 + st * TC_STAGE, As + (size_t)c * (2 * 128 * TC_KC), 2 * TC_ABYTES, fullA(st));
     };
-    for (int c = 0; c < TC_NSTAGE - 1 && c < nK; ++c) copyA(c);
-    int issued = -1;
+    int ncopy = 0;                                   // chunks whose coefficient copy was issued
+    for (int c = 0; c < TC_NSTAGE - 1 && c < nK; ++c, ++ncopy) copyA(c);
+    int issued = -1;                                 // last chunk whose MMAs were committed
     for (int c = 0; c < nK && !bad; ++c) {
       const int st = c % TC_NSTAGE, use = c / TC_NSTAGE;
       const uint32_t Sa = sm0 + st * TC_STAGE;
-      bool ok = false;
-      for (uint32_t i = 0; i < TC_SPIN && !ok; ++i) {
-        ok = mbar_test(fullA(st), use & 1) && mbar_test(fullB(st), use & 1);
-        if (!ok && *abort_flag) break;
+      if (!mbar_wait_or_abort(fullA(st), use & 1, spin, abort_flag) ||
+          !mbar_wait_or_abort(fullB(st), use & 1, spin, abort_flag)) {
+        bad = true;
+        break;
       }
-      if (!ok) { bad = true; break; }
       tc_after();
 #pragma unroll
       for (int k = 0; k < TC_KC / 8; ++k) {
@@ -302,14 +310,21 @@ __global__ void __launch_bounds__(288, 1) k_receive_tc(int nK, int K8, int M4, c
       // coefficients of chunk c + NS - 1 go to the stage of chunk c - 1 once its MMAs are done
       const int cn = c + TC_NSTAGE - 1;
       if (cn < nK) {
-        if (c >= 1 && !mbar_wait(done((c - 1) % TC_NSTAGE), ((c - 1) / TC_NSTAGE) & 1)) { bad = true; break; }
+        if (c >= 1 && !mbar_wait(done((c - 1) % TC_NSTAGE), ((c - 1) / TC_NSTAGE) & 1, spin)) { bad = true; break; }
         copyA(cn);
+        ++ncopy;
       }
     }
     // the last commit covers every MMA issued before it
-    if (issued >= 0 && !mbar_wait(done(issued % TC_NSTAGE), (issued / TC_NSTAGE) & 1)) bad = true;
+    if (issued >= 0 && !mbar_wait(done(issued % TC_NSTAGE), (issued / TC_NSTAGE) & 1, spin)) bad = true;
     if (issued != nK - 1) bad = true;
-    if (bad) *abort_flag = 1;
+    if (bad) {
+      *abort_flag = 1;
+      // drain: the coefficient copies not yet consumed, then the last commit
+      for (int ch = issued + 1; ch < ncopy; ++ch)
+        mbar_wait(fullA(ch % TC_NSTAGE), (ch / TC_NSTAGE) & 1, TC_SPIN);
+      if (issued >= 0) mbar_wait(done(issued % TC_NSTAGE), (issued / TC_NSTAGE) & 1, TC_SPIN);
+    }
   }
   bad = __syncthreads_or(bad) != 0;
   if (!bad && warp < 8) {
@@ -380,7 +395,7 @@ __global__ void __launch_bounds__(288, 1) k_aggregate_tc(int nMT, int nKc, int K
                                                          const int* __restrict__ tcount,
                                                          const int* __restrict__ perm, const float* __restrict__ A,
                                                          const XT* __restrict__ x, float* __restrict__ out0,
-                                                         int* __restrict__ err) {
+                                                         uint32_t spin, int* __restrict__ err) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* sm = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   float* Bh = reinterpret_cast<float*>(sm);                               // [current][nKc][128][32]
@@ -420,13 +435,16 @@ __global__ void __launch_bounds__(288, 1) k_aggregate_tc(int nMT, int nKc, int K
   tc_after();
   const uint32_t tmem = *slot;
   const int total = nMT * nKc;                        // coefficient chunks in order (M tile, K chunk)
+  int ncopy = 0;                                      // chunks whose bulk copy was issued (control thread)
+  auto copy_chunk = [&](int g) {
+    const int t = g / nKc, c = g % nKc, st = g % AG_NS;
+    mbar_expect_tx(aFull(st), 2 * TC_ABYTES);
+    bulk_g2s(ar0 + st * 2 * TC_ABYTES, As + t * tileA + (size_t)c * 2 * 128 * TC_KC, 2 * TC_ABYTES, aFull(st));
+    ++ncopy;
+  };
   if (tid == 288 - 32) {
     // control thread: first coefficient chunks while the producers load x
-    for (int g = 0; g < AG_NS - 1 && g < total; ++g) {
-      const int t = g / nKc, c = g % nKc, st = g % AG_NS;
-      mbar_expect_tx(aFull(st), 2 * TC_ABYTES);
-      bulk_g2s(ar0 + st * 2 * TC_ABYTES, As + t * tileA + (size_t)c * 2 * 128 * TC_KC, 2 * TC_ABYTES, aFull(st));
-    }
+    for (int g = 0; g < AG_NS - 1 && g < total; ++g) copy_chunk(g);
   }
   if (warp < 8) {
     // the tile's coefficients: row = particle; item = 4 consecutive values of
@@ -486,12 +504,7 @@ __global__ void __launch_bounds__(288, 1) k_aggregate_tc(int nMT, int nKc, int K
     for (int t = 0; t < nMT && !bad; ++t) {
       const int b = t & 1;
       bool ok = false;
-      if (lane == 0) {
-        for (uint32_t i = 0; i < TC_SPIN && !ok; ++i) {
-          ok = mbar_test(accFull(b), (t >> 1) & 1);
-          if (!ok && *abort_flag) break;
-        }
-      }
+      if (lane == 0) ok = mbar_wait_or_abort(accFull(b), (t >> 1) & 1, spin, abort_flag);
       ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
       if (!ok) {
         bad = true;
@@ -522,20 +535,17 @@ __global__ void __launch_bounds__(288, 1) k_aggregate_tc(int nMT, int nKc, int K
     // ---- control thread
     const uint32_t idesc = idesc_tf32(128, TC_NP);
     const uint32_t bh0 = sm0, bl0 = sm0 + AG_KCMAX * TC_BBYTES;
-    int g = 0;
+    int g = 0;                                        // next chunk to consume
+    uint32_t last_bar = 0, last_par = 0;              // the latest MMA commit (covers all before it)
+    bool committed = false;
     for (int t = 0; t < nMT && !bad; ++t) {
       const int b = t & 1;
-      if (t >= 2 && !mbar_wait(accEmpty(b), ((t >> 1) - 1) & 1)) { bad = true; break; }
+      if (t >= 2 && !mbar_wait_or_abort(accEmpty(b), ((t >> 1) - 1) & 1, spin, abort_flag)) { bad = true; break; }
       tc_after();
       const uint32_t d = tmem + (uint32_t)(b * TC_NP);
-      for (int c = 0; c < nKc; ++c, ++g) {
+      for (int c = 0; c < nKc; ++c) {
         const int st = g % AG_NS;
-        bool ok = false;
-        for (uint32_t i = 0; i < TC_SPIN && !ok; ++i) {
-          ok = mbar_test(aFull(st), (g / AG_NS) & 1);
-          if (!ok && *abort_flag) break;
-        }
-        if (!ok) { bad = true; break; }
+        if (!mbar_wait_or_abort(aFull(st), (g / AG_NS) & 1, spin, abort_flag)) { bad = true; break; }
         tc_after();
         const uint32_t Sa = ar0 + st * 2 * TC_ABYTES;
 #pragma unroll
@@ -548,24 +558,29 @@ __global__ void __launch_bounds__(288, 1) k_aggregate_tc(int nMT, int nKc, int K
           mma_tf32(d, al, bh, idesc, 1u);
         }
         mma_commit(aDone(st));
-        // next coefficient chunk into the stage of chunk g - 1 once its MMAs are done
-        const int gn = g + AG_NS - 1;
+        last_bar = aDone(st);
+        last_par = (g / AG_NS) & 1;
+        committed = true;
+        ++g;
+        // next coefficient chunk into the stage of chunk g - 2 once its MMAs are done
+        const int gn = g - 1 + AG_NS - 1;
         if (gn < total) {
-          if (g >= 1 && !mbar_wait(aDone((g - 1) % AG_NS), ((g - 1) / AG_NS) & 1)) { bad = true; break; }
-          const int tn = gn / nKc, cn = gn % nKc, sn = gn % AG_NS;
-          mbar_expect_tx(aFull(sn), 2 * TC_ABYTES);
-          bulk_g2s(ar0 + sn * 2 * TC_ABYTES, As + tn * tileA + (size_t)cn * 2 * 128 * TC_KC, 2 * TC_ABYTES,
-                   aFull(sn));
+          if (g >= 2 && !mbar_wait(aDone((g - 2) % AG_NS), ((g - 2) / AG_NS) & 1, spin)) { bad = true; break; }
+          copy_chunk(gn);
         }
       }
       if (bad) break;
       mma_commit(accFull(b));
+      last_bar = accFull(b);
+      last_par = (t >> 1) & 1;
     }
-    // every MMA is complete once the last M tile's accumulator is full (or on failure, the last chunk)
-    if (!bad && nMT > 0 && !mbar_wait(accFull((nMT - 1) & 1), ((nMT - 1) >> 1) & 1)) bad = true;
+    // every MMA is complete once the last M tile's accumulator is full
+    if (!bad && nMT > 0 && !mbar_wait(accFull((nMT - 1) & 1), ((nMT - 1) >> 1) & 1, spin)) bad = true;
     if (bad) {
       *abort_flag = 1;
-      if (g > 0) mbar_wait(aDone((g - 1) % AG_NS), ((g - 1) / AG_NS) & 1);
+      // drain: the coefficient copies not yet consumed, then the latest commit
+      for (int ch = g; ch < ncopy; ++ch) mbar_wait(aFull(ch % AG_NS), (ch / AG_NS) & 1, TC_SPIN);
+      if (committed) mbar_wait(last_bar, last_par, TC_SPIN);
     }
   }
   bad = __syncthreads_or(bad) != 0;
@@ -696,7 +711,7 @@ int run_receive_tc(Ctx* c, const float2* in0, double2* y, bool accumulate, cudaS
   k_receive_tc<double><<<(unsigned)c->tc_ntile, 288, TC_SMEM, st>>>(
       c->tc_nK, 8 * c->lev[0].K, 4 * c->npsi, c->d_tc_shape, c->d_tc_start, c->d_tc_count, c->d_tc_perm,
       c->d_tc_perm, c->d_tc_rec, reinterpret_cast<const float*>(in0), reinterpret_cast<double*>(y), accumulate ? 1 : 0,
-      c->d_tc_err);
+      c->tc_spin, c->d_tc_err);
   SMR_LAUNCH(c);
   return SMR_OK;
 }
@@ -712,13 +727,13 @@ int run_aggregate_tc(Ctx* c, const double2* x, const float2* x32, float2* out0, 
     k_aggregate_tc<float><<<(unsigned)c->tc_ntile, 288, AG_SMEM, st>>>(
         c->tc_nMT, c->tc_nKc, 4 * c->lev[0].K, 2 * c->npsi, c->d_tc_shape, c->d_tc_start, c->d_tc_count,
         c->d_tc_perm, c->d_tc_agg, reinterpret_cast<const float*>(x32), reinterpret_cast<float*>(out0),
-        c->d_tc_err);
+        c->tc_spin, c->d_tc_err);
   } else {
     cudaFuncSetAttribute(k_aggregate_tc<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)AG_SMEM);
     k_aggregate_tc<double><<<(unsigned)c->tc_ntile, 288, AG_SMEM, st>>>(
         c->tc_nMT, c->tc_nKc, 4 * c->lev[0].K, 2 * c->npsi, c->d_tc_shape, c->d_tc_start, c->d_tc_count,
         c->d_tc_perm, c->d_tc_agg, reinterpret_cast<const double*>(x), reinterpret_cast<float*>(out0),
-        c->d_tc_err);
+        c->tc_spin, c->d_tc_err);
   }
   SMR_LAUNCH(c);
   return SMR_OK;
@@ -881,7 +896,7 @@ int run_near_tc(Ctx* c, double2* y, cudaStream_t st) {
   pbeg(c, st, "near", -1, bytes, flops);
   k_receive_tc<float><<<(unsigned)nt, 288, TC_SMEM, st>>>(
       c->tcn_nK, M4, M4, c->d_tcn_blk, c->d_tcn_start, c->d_tcn_count, c->d_tcn_nu, c->d_tcn_mu,
-      c->d_tcn_img, reinterpret_cast<const float*>(c->d_x32), c->d_tcn_part, 0, c->d_tc_err);
+      c->d_tcn_img, reinterpret_cast<const float*>(c->d_x32), c->d_tcn_part, 0, c->tc_spin, c->d_tc_err);
   SMR_LAUNCH(c);
   pend(c, st);
   const long long nm = (long long)c->p * M4, nt4 = nm / 4;
@@ -901,7 +916,7 @@ int tc_check(Ctx* c) {
   if (h) {
     cudaMemset(c->d_tc_err, 0, sizeof(int));
     c->err = "tensor-core product step: a pipeline wait ran out (results of that product are invalid)";
-    return SMR_E_CUDA;
+    return SMR_E_TIMEOUT;
   }
   return SMR_OK;
 }

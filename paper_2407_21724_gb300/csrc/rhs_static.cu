@@ -67,6 +67,9 @@ extern "C" int smr_rhs_plane_waves_static(smr_ctx* h, int R, const double* khat,
   void* scratch = nullptr;
   int rc = scratch_address(c, &scratch);
   if (rc) return rc;
+  // the kernels, the scene tables and the scratch address all belong to the
+  // context's device; like the other entry points, the call leaves it current
+  SMR_CUDA(c, cudaSetDevice(c->device));
   // every element of the scratch that is read is written first by the shape
   // kernel of this call, so nothing needs clearing
   return smr::launch_rhs_scratch(c, R, khat, (const double2*)pol, (double2*)scratch, (double2*)b,

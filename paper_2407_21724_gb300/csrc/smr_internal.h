@@ -201,6 +201,7 @@ struct Ctx {
   double2* d_B64 = nullptr;
   float2* d_B32 = nullptr;
   // preconditioner: inverse self blocks, transposed [S][2n][2n]
+  bool pinv_ok = true;                  // every self block was invertible
   double2* d_Pinv64 = nullptr;
   float2* d_Pinv32 = nullptr;
   int* d_pc_ptr = nullptr;              // identity CSR for the block kernel
@@ -246,6 +247,7 @@ struct Ctx {
   int* d_tc_start = nullptr;
   int* d_tc_count = nullptr;
   int* d_tc_err = nullptr;                // set when a pipeline wait runs out
+  uint32_t tc_spin = 1u << 24;            // polling limit of the pipeline waits (smr_set_wait_limit)
   bool tc_agg_ready = false;
   int tc_nMT = 0, tc_nKc = 0;
   float* d_tc_agg = nullptr;              // [S][M tiles][K chunks][hi | lo][128][32] aggregation images

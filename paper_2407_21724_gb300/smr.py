@@ -20,8 +20,9 @@ SMR_PREC_FP64, SMR_PREC_FP32 = 0, 1
 SMR_LRULE_FORMULA, SMR_LRULE_DOUBLE = 0, 1
 SMR_PRECOND_NONE, SMR_PRECOND_BLOCKDIAG, SMR_PRECOND_LEARNED = 0, 1, 2
 SMR_OK, SMR_E_NOT_CONVERGED = 0, -5
+SMR_E_BREAKDOWN, SMR_E_TIMEOUT = -6, -8
 ERRORS = {-1: "INVALID_ARG", -2: "SHAPE", -3: "OOM", -4: "CUDA", -5: "NOT_CONVERGED",
-          -6: "BREAKDOWN", -7: "NAN", -9: "STATE"}
+          -6: "BREAKDOWN", -7: "NAN", -8: "TIMEOUT", -9: "STATE"}
 
 
 class SmrError(RuntimeError):
@@ -107,6 +108,7 @@ _SIGS = {
     "smr_nn_precond": (C.c_int, [_P, _D, _D, C.c_double, _P, _P]),
     "smr_autotune": (C.c_int, [_P, C.c_int, C.c_int, _P]),
     "smr_sync": (C.c_int, [_P, _P]),
+    "smr_set_wait_limit": (C.c_int, [_P, C.c_longlong]),
 }
 
 
@@ -253,6 +255,15 @@ def smr_rhs_plane_waves_static(ctx, khat, pol, b, R=None, stream=None):
     device tensors (or raw pointers with R given); b is the device output."""
     if R is None:
         R = khat.shape[0]
+    for t, dt, what in ((khat, "float64", "khat"), (pol, "complex128", "pol")):
+        if isinstance(t, int):
+            continue
+        # the library reads these as raw device pointers and cannot check them
+        if not (t.is_cuda and t.is_contiguous() and str(t.dtype) == "torch." + dt
+                and tuple(t.shape) == (R, 3)):
+            raise ValueError(f"{what} must be a contiguous ({R}, 3) {dt} CUDA tensor")
+        if hasattr(b, "device") and t.device != b.device:
+            raise ValueError(f"{what} is on {t.device}, the output on {b.device}")
     kp = khat if isinstance(khat, int) else khat.data_ptr()
     pp = pol if isinstance(pol, int) else pol.data_ptr()
     _check(ctx, lib().smr_rhs_plane_waves_static(ctx, R, kp, pp, _ptr(b), _stream(stream, b)))
@@ -323,6 +334,11 @@ def smr_autotune(ctx, precision=SMR_PREC_FP32, stream=None):
 
 def smr_sync(ctx, stream=None):
     _check(ctx, lib().smr_sync(ctx, _stream(stream, None)))
+
+
+def smr_set_wait_limit(ctx, rounds):
+    """Polling limit of the tensor-core pipeline waits; rounds < 0 restores the default."""
+    _check(ctx, lib().smr_set_wait_limit(ctx, int(rounds)))
 
 
 def smr_far_field(ctx, x, dirs, F, R=None, stream=None):
