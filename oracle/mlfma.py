@@ -35,7 +35,7 @@ import numpy as np
 import scipy.sparse as sps
 
 from .pmchwt import exterior_block
-from .special import gauss_legendre, legendre, sph_h2, sphere_frame
+from .special import gauss_legendre, legendre_upto, sph_h2, sphere_frame
 
 
 # ---------------------------------------------------------------- grouping
@@ -190,8 +190,9 @@ def translation_function(k, L, khat, X):
     r = np.linalg.norm(X)
     c = khat @ (X / r)
     out = np.zeros(khat.shape[0], dtype=complex)
+    P = legendre_upto(L, c)
     for l in range(L + 1):
-        out += (-1j) ** l * (2 * l + 1) * sph_h2(l, k * r) * legendre(l, c)
+        out += (-1j) ** l * (2 * l + 1) * sph_h2(l, k * r) * P[l]
     return (-1j * k / (4 * np.pi) ** 2) * out
 
 

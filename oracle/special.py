@@ -38,9 +38,18 @@ def riccati_xi(l, x):
     return x * h, h + x * dh
 
 
-def legendre(l, x):
-    """Legendre polynomial P_l(x) (Eq. 23)."""
-    return sp.eval_legendre(l, x)
+def legendre_upto(L, x):
+    """Legendre polynomials P_0(x) .. P_L(x) (Eq. 23) by Bonnet's three-term
+    recurrence (l + 1) P_{l+1} = (2l + 1) x P_l - l P_{l-1}, ascending in l;
+    returns an array (L + 1, *x.shape)."""
+    x = np.asarray(x, dtype=float)
+    P = np.empty((L + 1,) + x.shape)
+    P[0] = 1.0
+    if L >= 1:
+        P[1] = x
+    for l in range(1, L):
+        P[l + 1] = ((2 * l + 1) * x * P[l] - l * P[l - 1]) / (l + 1)
+    return P
 
 
 def gauss_legendre(n):

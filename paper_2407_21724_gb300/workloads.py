@@ -90,6 +90,15 @@ def make(name, **kw):
                     centres=C, shape_ids=ids,
                     shapes=[(r, modes, modes) for r in RADII8], eps_in=EPS_IN,
                     pitch=PITCH, incidences=[incidence(0, 0, 'x')], focal=f)
+    if name == 'sparse':
+        # n x n random-radius lattice thinned to a seeded fraction of its
+        # sites: the tree depth and the upper levels' box counts of a full
+        # n x n array with few particles
+        w = make('random', n=kw.get('n', 200), seed=kw.get('seed', 21727), modes=kw.get('modes', 16))
+        keep = np.random.default_rng(kw.get('seed', 21727) + 1).random(len(w['centres'])) < kw.get('fill', 0.02)
+        w['centres'], w['shape_ids'] = w['centres'][keep], w['shape_ids'][keep]
+        w['label'] = f"{w['label']} thinned to {int(keep.sum())} sites"
+        return w
     if name == 'ragged16':
         # 16 arrays of n_i = round(10 + 50 i / 15) pillars per side, seeds 21726 + i
         return [make('random', n=int(round(10 + 50 * i / 15)), seed=21726 + i,

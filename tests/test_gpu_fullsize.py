@@ -199,3 +199,43 @@ def test_batched64_columns_match_single_products(batched):
     b = torch.sum(D * Xv * c.product((D * U).contiguous().view(-1), smr.SMR_PREC_FP64, R=R).view(c.n, R), dim=0)
     gap = (torch.abs(a - b) / torch.abs(a)).max().item()
     assert gap < 1e-11, gap
+
+
+def _oracle_box_out(w, level, bx, by, x):
+    """Outgoing spectrum (K_level, 4) of the lens box (bx, by) at `level`,
+    from the oracle run on that box's particles alone.  One anchor particle
+    two boxes to the right of it (a box of its own, zero coefficients) lets
+    the sub-scene's tree reach `level`; the box's lower-left site is the
+    sub-scene's origin, so its boxes and centres coincide with the lens's."""
+    pitch = w["pitch"]
+    C = w["centres"]
+    lo = C[:, :2].min(axis=0)
+    ij = np.rint((C[:, :2] - lo) / pitch).astype(int)
+    sel = np.nonzero(((ij[:, 0] >> level) == bx) & ((ij[:, 1] >> level) == by))[0]
+    assert len(sel) == 4 ** level                       # a full box of the lens
+    corner = lo + np.array([bx, by]) * (2 ** level) * pitch
+    anchor = np.array([[corner[0] + 2 * (2 ** level) * pitch, corner[1], C[0, 2]]])
+    sc = opm.Scene(np.vstack([C[sel], anchor]), np.concatenate([w["shape_ids"][sel], [0]]),
+                   w["shapes"], eps_in=w["eps_in"])
+    M = oml.MLFMA(sc, pitch)
+    assert M.tree.n_levels == level + 1 and M.tree.levels[level]["index"][(0, 0)] == 0
+    n2 = 2 * sc.n_psi
+    xs = np.concatenate([x.reshape(-1, n2)[sel], np.zeros((1, n2))]).reshape(-1)
+    out = M.aggregate(xs)
+    for s in range(level):
+        out = M.upward(s, out)
+    return out[0]
+
+
+def test_lens_upper_level_spectra_match_oracle_subtrees(lens):
+    """Level-4, 5 and 6 outgoing spectra (L = 87, 162, 309) of sampled lens
+    boxes after the autotuned FP64 product, element-wise against the oracle's
+    aggregation and interpolation over each box's subtree (256, 1,024 and
+    4,096 particles): <= 1e-12."""
+    x = crandn(lens.n, 104)
+    lens.product(torch.from_numpy(x).cuda(), smr.SMR_PREC_FP64)
+    for level, bx, by in ((4, 5, 7), (5, 2, 3), (6, 1, 2)):
+        nbx = ((200 - 1) >> level) + 1
+        got = smr.smr_copy_level(lens.ctx, level, 0)[by * nbx + bx, :, :, 0]
+        want = _oracle_box_out(lens.w, level, bx, by, x)
+        assert rel(got, want) < 1e-12, (level, rel(got, want))

@@ -528,3 +528,19 @@ def test_near_field_pin_catches_planted_mistakes(plant, monkeypatch):
                             -1j * k * (g @ cur) + (1j / k) * np.einsum('pqc,q->pc', dg, dv))
     eE, eH = _near_rel(*_single_sphere_near_case())
     assert max(eE, eH) > 1e-3
+
+
+def test_legendre_recurrence():
+    """legendre_upto (Bonnet's recurrence, used for T_L of Eq. 23) against the
+    library's P_l for l <= 40 and the orthogonality int P_l P_m = 2/(2l+1)
+    delta_lm by a Gauss-Legendre rule exact for the products, l, m <= 320."""
+    import scipy.special as sps
+    from oracle.special import legendre_upto
+    x = np.linspace(-1.0, 1.0, 2001)
+    P = legendre_upto(40, x)
+    for l in range(41):
+        assert np.max(np.abs(P[l] - sps.eval_legendre(l, x))) < 1e-13
+    xg, wg = gauss_legendre(330)
+    Q = legendre_upto(320, xg)
+    G = (Q * wg) @ Q.T
+    assert np.max(np.abs(G - np.diag(2.0 / (2 * np.arange(321) + 1)))) < 1e-12
