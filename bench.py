@@ -11,6 +11,9 @@ timed steps, the GMRES time to a 1e-4 true relative residual for the tuned
 solver (FP64-outer iterative refinement over FP32-inner GMRES) and for plain
 FP64 GMRES.
 
+The reference arm (--impl reference) and the line's cpu_baseline time the
+FP64 oracle's full product of the same workload on all host cores.
+
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
        [--workload metalens200|random40|spheres8x8] [--no-solve]
 For N > 1 launch with torch.distributed.run: every rank runs its own replica
@@ -50,70 +53,42 @@ def parse():
     ap.add_argument("--workload", default="metalens200", choices=sorted(WORKLOADS))
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--sample", type=int, default=20, help="side of the oracle's sample sub-array")
     ap.add_argument("--train-arrays", type=int, default=400,
                     help="20x20 arrays solved to train the learned initial guess (0: skip)")
     return ap.parse_args()
 
 
-# ------------------------------------------------------------------ algorithmic work model
-def algorithmic_flops(centres, pitch, n_psi, L0=10):
-    """FMM work of one product (same per-unit counts as the library's
-    profile records): near 8 (2n)^2 per pair, aggregation 32 n per sample,
-    interpolation 72 x 4 per (child, parent direction), translation 32 per
-    (IL entry, direction), anterpolation 34 x 16 x 4 per (child, parent
-    direction) / 4, receive 48 n per sample."""
-    from oracle.mlfma import Tree, truncation
-    t = Tree(centres, pitch)
-    k = 2 * 3.141592653589793
-    K = [2 * (truncation(k, pitch, s, L0) + 1) ** 2 for s in range(t.n_levels)]
-    n2 = 2 * n_psi
-    p = len(centres)
-    fl = 8.0 * n2 * n2 * len(t.near_pairs())
-    fl += (32.0 + 48.0) * n_psi * p * K[0]
-    for s in range(t.n_levels):
-        fl += 32.0 * len(t.levels[s]["il"]) * K[s]
-    for s in range(t.n_levels - 1):
-        nc = len(t.levels[s]["ij"])
-        fl += nc * K[s + 1] * 4 * 72.0 + nc * 16.0 * K[s + 1] * 34.0
-    return fl
-
-
-def central_sample(w, side):
-    """The central side x side sub-array of a square workload."""
-    import numpy as np
-    C = w["centres"]
-    n = int(round(np.sqrt(len(C))))
-    i0 = (n - side) // 2
-    idx = np.array([(i0 + j) * n + i0 + i for j in range(side) for i in range(side)])
-    return C[idx], w["shape_ids"][idx]
-
-
-def oracle_sample_rate(w, side, steps, warmup, full_flops=None):
-    """Time the FP64 oracle's MLFMA product on the central sub-array and scale
-    to full-workload products/s by the algorithmic flop ratio."""
-    import numpy as np
-    from oracle import mlfma as oml
-    from oracle import pmchwt as opm
-    Cs, ids = central_sample(w, side)
-    sc = opm.Scene(Cs, ids, w["shapes"], eps_in=w["eps_in"])
-    M = oml.MLFMA(sc, w["pitch"])
-    rng = np.random.default_rng(0)
-    x = rng.standard_normal(sc.n_unknowns) + 1j * rng.standard_normal(sc.n_unknowns)
-    times = []
-    for i in range(warmup + steps):
-        t0 = time.perf_counter()
-        M.matvec(x)
-        if i >= warmup:
-            times.append(time.perf_counter() - t0)
-    t = float(np.mean(times))
-    n_psi = w["shapes"][0][1] + w["shapes"][0][2]
-    full = full_flops if full_flops is not None else algorithmic_flops(w["centres"], w["pitch"], n_psi)
-    ratio = full / algorithmic_flops(Cs, w["pitch"], n_psi)
-    return 1.0 / (t * ratio), t, ratio, len(Cs)
-
-
 # ------------------------------------------------------------------ reference arm (the oracle)
+def oracle_rate(ws, steps, warmup):
+    """Time the FP64 oracle's full MLFMA product of every scene in ws on all
+    host cores (oracle.parallel: the oracle's own steps split over disjoint
+    boxes in forked workers, bit-identical to the serial product).  A step is
+    one product of each scene; returns (products per second per right-hand
+    side, seconds per step, set-up seconds, workers)."""
+    import numpy as np
+    from oracle import pmchwt as opm
+    from oracle.parallel import ParallelMLFMA
+    t_step, t_setup, workers = 0.0, 0.0, 0
+    for w in ws:
+        sc = opm.Scene(w["centres"], w["shape_ids"], w["shapes"], eps_in=w["eps_in"])
+        t0 = time.perf_counter()
+        P = ParallelMLFMA(sc, w["pitch"])
+        t_setup += time.perf_counter() - t0
+        workers = P.workers
+        rng = np.random.default_rng(0)
+        x = rng.standard_normal(sc.n_unknowns) + 1j * rng.standard_normal(sc.n_unknowns)
+        try:
+            for _ in range(warmup):
+                P.matvec(x)
+            t0 = time.perf_counter()
+            for _ in range(steps):
+                P.matvec(x)
+            t_step += (time.perf_counter() - t0) / steps
+        finally:
+            P.close()
+    return 1.0 / t_step, t_step, t_setup, workers
+
+
 def run_reference(a):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -123,24 +98,23 @@ def run_reference(a):
     R = 64 if a.workload == "batched100x64" else 1
     if a.workload == "ragged16":
         ws = workloads.make(name, **kw)
-        w = dict(ws[-1])                   # sample from the largest array
-        n_psi = w["shapes"][0][1] + w["shapes"][0][2]
-        full_fl = sum(algorithmic_flops(v["centres"], v["pitch"], n_psi) for v in ws)
         label = "ragged batch of 16 random arrays, 10x10 ... 60x60, one product"
     else:
-        w = workloads.make(name, **kw)
-        full_fl = None
-        label = w["label"]
-    side = min(a.sample, int(round(len(w["centres"]) ** 0.5)))
-    rate, t, ratio, ps = oracle_sample_rate(w, side, a.steps, a.warmup, full_fl)
-    sample = (f"FP64 NumPy oracle MLFMA product on the central {side}x{side} sub-array "
-              f"({ps} particles), {t:.3f} s per product, scaled by the algorithmic flop "
-              f"ratio {ratio:.1f} to the full workload (per right-hand side)")
+        ws = [workloads.make(name, **kw)]
+        label = ws[0]["label"]
+    rate, t, t_setup, workers = oracle_rate(ws, a.steps, max(1, a.warmup))
+    # the oracle applies one right-hand side per product: R columns cost R products
+    sample = (f"the full workload: FP64 NumPy oracle MLFMA product of {sum(len(w['centres']) for w in ws)} "
+              f"particles on {workers} worker processes (all host cores, BLAS single-threaded), "
+              f"{t:.2f} s per product over {a.steps} timed products after {max(1, a.warmup)} warm-ups; "
+              f"set-up (tables, near blocks) {t_setup:.1f} s, not timed"
+              + (f"; {R} right-hand sides = {R} products" if R > 1 else ""))
     line = dict(metric=METRIC, value=rate, unit="matvecs/s", n_gpus=a.gpus, steps=a.steps,
-                warmup=a.warmup, ms_per_step=1e3 / rate, higher_is_better=True, scaling="weak",
+                warmup=a.warmup, ms_per_step=1e3 * t, higher_is_better=True, scaling="weak",
                 vs_baseline=None, dtype="f64", data="synthetic", impl="reference",
                 config=dict(workload=label, rhs=R, l2="inputs larger than L2 (CPU run)"),
-                cpu_baseline=dict(value=rate, unit="matvecs/s", cores=1, kind="oracle", sample=sample),
+                cpu_baseline=dict(value=rate, unit="matvecs/s", cores=workers, kind="oracle", sample=sample,
+                                  setup_seconds=t_setup),
                 e2e=dict(value=rate, unit="matvecs/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     print(json.dumps(line), flush=True)
 
@@ -381,6 +355,22 @@ def run_ours(a):
     k64 = max(3, a.steps // 4)
     ms64 = timed(smr.SMR_PREC_FP64, k64, 2) / k64 / R
 
+    # ---- error of the tuned (FP32) product against the FP64 product, whose
+    # agreement with the FP64 oracle is the tested parity bar (<= 1e-10)
+    def prod(v, prec):
+        out = torch.empty_like(v)
+        smr.smr_matvec(ctx, v, out, prec)
+        torch.cuda.synchronize(dev)
+        return out
+
+    def relerr(u, v):
+        return float(torch.linalg.vector_norm(u - v) / torch.linalg.vector_norm(v))
+
+    errors = dict(reference="the FP64 GPU product / solution (the FP64 product equals the FP64 "
+                            "oracle's to <= 1e-10 in the parity tests)",
+                  product_random_x=relerr(prod(x, P32), prod(x, smr.SMR_PREC_FP64)),
+                  product_x_eq_b=relerr(prod(b, P32), prod(b, smr.SMR_PREC_FP64)))
+
     # ---- per-launch profile of the tuned product (CUDA events around every launch)
     prof_runs = [smr.smr_profile_matvec(ctx, x, y, P32) for _ in range(max(3, a.steps // 4))]
     nr = len(prof_runs)
@@ -471,6 +461,7 @@ def run_ours(a):
             return xs
 
         xt = solve("tuned_fp32_inner_fp64_outer", P32)
+        sols = dict(tuned=xt)
         if "focal" in w and R == 1:
             gm["focal"] = focal_report(smr, ctx, xt, w, dev)
         if learned is not None:
@@ -479,7 +470,21 @@ def run_ours(a):
             solve("tuned_plus_learned_x0", P32, x0=torch.zeros_like(b))
             solve("tuned_plus_learned_x0_and_precond", P32, x0=torch.zeros_like(b), lpc=True)
             gm["learned_training"] = {k: v for k, v in learned.items() if k not in ("params",)}
-        solve("plain_fp64", smr.SMR_PREC_FP64)
+        sols["fp64"] = solve("plain_fp64", smr.SMR_PREC_FP64)
+        # the tuned solution and its far field against the plain FP64 solve
+        errors["solution_tuned_vs_fp64"] = relerr(sols["tuned"], sols["fp64"])
+        th, ph = np.meshgrid(np.radians(np.linspace(5.0, 175.0, 8)), np.radians(np.arange(8) * 45.0),
+                             indexing="ij")
+        dirs = np.stack([np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph), np.cos(th)], -1).reshape(-1, 3)
+        ff = {}
+        for key, v in sols.items():
+            F = torch.empty(len(dirs) * 3 * R, dtype=torch.complex128, device=dev)
+            smr.smr_far_field(ctx, v, dirs, F, R=R)
+            torch.cuda.synchronize(dev)
+            ff[key] = F
+        errors["far_field_tuned_vs_fp64"] = relerr(ff["tuned"], ff["fp64"])
+        errors["far_field_directions"] = "64: theta in linspace(5, 175 deg, 8) x phi in 0, 45, ..., 315 deg"
+        errors["solve_tolerance"] = "both solves stop at a true FP64 relative residual of 1e-4"
         best = min(v["seconds"] for k, v in gm.items() if k.startswith("tuned") and isinstance(v, dict)
                    and "seconds" in v)
         gm["speedup_tuned_vs_plain"] = gm["plain_fp64"]["seconds"] / best
@@ -489,7 +494,7 @@ def run_ours(a):
     if rank == 0 and world == 1 and not a.no_cpu:
         env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
         cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "2",
-               "--warmup", "1", "--workload", a.workload, "--sample", str(a.sample)]
+               "--warmup", "1", "--workload", a.workload]
         r = subprocess.run(cmd, capture_output=True, text=True, env=env)
         for line in r.stdout.splitlines():
             if line.startswith("{"):
@@ -511,7 +516,7 @@ def run_ours(a):
                                 levels=info["n_levels"], L=info["L"], unknowns=n),
                     fp64_matvecs_per_s=1e3 / ms64, fp64_ms_per_matvec=ms64,
                     ms_per_step_without_graph=ms_direct / R,
-                    gmres=gm, setup_s=setup_s, autotune_s=tune_s,
+                    gmres=gm, errors_vs_fp64=errors, setup_s=setup_s, autotune_s=tune_s,
                     e2e=dict(value=1.0 / e2e_s, unit="matvecs/s", h2d_bytes_per_step=16 * n * R,
                              d2h_bytes_per_step=16 * n * R),
                     gpu_launches=launches * a.steps, roofline=roofline, kernels=breakdown,

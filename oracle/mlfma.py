@@ -66,6 +66,9 @@ class Tree:
             cen[:, 2] = self.z0
             self.levels.append(dict(ij=keys, centre=cen, index=index))
             self.levels[-1]['il'] = self._interaction_list(s)
+            # entries of target b are il[il_ptr[b]:il_ptr[b + 1]] (listed by target)
+            tb = np.array([e[0] for e in self.levels[-1]['il']], dtype=np.int64)
+            self.levels[-1]['il_ptr'] = np.searchsorted(tb, np.arange(len(keys) + 1))
             if np.max(keys.max(axis=0) - keys.min(axis=0)) <= 1:
                 break                      # every box adjacent: nothing above
             ij_s = keys // 2
@@ -95,11 +98,13 @@ class Tree:
                                 out.append((b, bb, (int(t[0] - cx), int(t[1] - cy))))
         return out
 
-    def near_pairs(self):
-        """(mu, nu) with lattice distance <= 1 (self included)."""
+    def near_pairs(self, mus=None):
+        """(mu, nu) with lattice distance <= 1 (self included), for the
+        particles mus (default all) in ascending order."""
         idx = self.levels[0]['index']
         out = []
-        for mu, t in enumerate(self.ij0):
+        for mu in (range(len(self.ij0)) if mus is None else mus):
+            t = self.ij0[mu]
             for dy in (-1, 0, 1):
                 for dx in (-1, 0, 1):
                     nu = idx.get((t[0] + dx, t[1] + dy))
@@ -184,6 +189,14 @@ def interpolation_matrix(src, dst):
     return sps.csr_matrix((vals, (rows, cols)), shape=(dst.K, src.K))
 
 
+def _interp_task(args):
+    return interpolation_matrix(*args)
+
+
+def _translation_task(args):
+    return translation_function(*args)
+
+
 def translation_function(k, L, khat, X):
     """T_L(khat, X) of Eq. 23 for all rows of khat (K,3), X a 3-vector."""
     X = np.asarray(X, dtype=float)
@@ -200,7 +213,10 @@ def translation_function(k, L, khat, X):
 class MLFMA:
     """MLFMA operator of a Scene on a square lattice of spacing ``pitch``."""
 
-    def __init__(self, scene, pitch, L0=10, rule='formula', digits=3.0):
+    def __init__(self, scene, pitch, L0=10, rule='formula', digits=3.0, pmap=map):
+        """pmap: a map function (e.g. a process pool's) for the independent
+        interpolation matrices and translation tables; the values are the
+        same whichever map computes them."""
         self.scene = scene
         self.tree = Tree(scene.centres, pitch)
         k = scene.outer.k
@@ -208,16 +224,18 @@ class MLFMA:
         self.zeta = scene.outer.zeta
         self.grids = [Grid(truncation(k, pitch, s, L0, rule, digits))
                       for s in range(self.tree.n_levels)]
-        self.interp = [interpolation_matrix(self.grids[s], self.grids[s + 1])
-                       for s in range(self.tree.n_levels - 1)]
+        self.interp = list(pmap(_interp_task, [(self.grids[s], self.grids[s + 1])
+                                                for s in range(self.tree.n_levels - 1)]))
         self.patterns = [self._pattern(s) for s in range(len(scene.shapes))]
-        self.T = []
+        keys, tasks = [], []
         for s, lev in enumerate(self.tree.levels):
-            offs = sorted({o for (_, _, o) in lev['il']})
             box = pitch * 2 ** s
-            tab = {o: translation_function(k, self.grids[s].L, self.grids[s].khat,
-                                           (o[0] * box, o[1] * box, 0.0)) for o in offs}
-            self.T.append(tab)
+            for o in sorted({o for (_, _, o) in lev['il']}):
+                keys.append((s, o))
+                tasks.append((k, self.grids[s].L, self.grids[s].khat, (o[0] * box, o[1] * box, 0.0)))
+        self.T = [dict() for _ in self.tree.levels]
+        for (s, o), tab in zip(keys, pmap(_translation_task, tasks)):
+            self.T[s][o] = tab
         self._near_cache = {}
 
     # ---- setup
@@ -246,23 +264,30 @@ class MLFMA:
         return self._near_cache[key]
 
     # ---- steps
-    def near(self, x):
+    # Every step takes an optional subset of the boxes (or particles) it
+    # writes and an optional output array: a subset's rows are computed with
+    # exactly the operations, in exactly the order, of the full step, so
+    # disjoint subsets can run in separate processes (oracle.parallel).
+    def near(self, x, mus=None, out=None):
         sc = self.scene
         n2 = 2 * sc.n_psi
         xx = x.reshape(sc.p, n2)
-        y = np.zeros_like(xx)
-        for mu, nu in self.tree.near_pairs():
+        y = np.zeros_like(xx) if out is None else out.reshape(sc.p, n2)
+        if mus is not None:
+            y[mus] = 0.0
+        for mu, nu in self.tree.near_pairs(mus):
             y[mu] += self.near_block(mu, nu) @ xx[nu]
         return y.reshape(-1)
 
-    def aggregate(self, x):
+    def aggregate(self, x, mus=None, out=None):
         """Level-0 outgoing spectra (p, K_0, 4)."""
         sc = self.scene
         xx = x.reshape(sc.p, 2, sc.n_psi)
         g = self.grids[0]
-        out = np.zeros((sc.p, g.K, 4), dtype=complex)
+        if out is None:
+            out = np.zeros((sc.p, g.K, 4), dtype=complex)
         cen = self.tree.levels[0]['centre']
-        for mu in range(sc.p):
+        for mu in (range(sc.p) if mus is None else mus):
             P = self.patterns[sc.shape_ids[mu]]               # (N, 2, K)
             shift = np.exp(1j * self.k * (g.khat @ (sc.centres[mu] - cen[mu])))
             for c in range(2):
@@ -270,45 +295,59 @@ class MLFMA:
                     out[mu, :, 2 * c + comp] = shift * (xx[mu, c] @ np.conj(P[:, comp, :]))
         return out
 
-    def upward(self, s, out_s):
+    def upward(self, s, out_s, parents=None, out=None):
         """Level s+1 outgoing spectra from level s (interpolate, shift, sum)."""
         lev, par = self.tree.levels[s], self.tree.levels[s + 1]
         gp = self.grids[s + 1]
-        out = np.zeros((len(par['ij']), gp.K, 4), dtype=complex)
+        if out is None:
+            out = np.zeros((len(par['ij']), gp.K, 4), dtype=complex)
         I = self.interp[s]
-        for c in range(len(lev['ij'])):
+        children = range(len(lev['ij']))
+        if parents is not None:
+            out[parents] = 0.0
+            keep = np.zeros(len(par['ij']), dtype=bool)
+            keep[parents] = True
+            children = [c for c in children if keep[lev['parent'][c]]]
+        for c in children:
             B = lev['parent'][c]
             shift = np.exp(1j * self.k * (gp.khat @ (lev['centre'][c] - par['centre'][B])))
             out[B] += shift[:, None] * (I @ out_s[c])
         return out
 
-    def translate(self, s, out_s):
+    def translate(self, s, out_s, targets=None, inc=None):
         lev = self.tree.levels[s]
-        inc = np.zeros_like(out_s)
-        for (b, bb, o) in lev['il']:
+        if inc is None:
+            inc = np.zeros_like(out_s)
+        il = lev['il']
+        if targets is not None:
+            inc[targets] = 0.0
+            ptr = lev['il_ptr']
+            il = [e for b in targets for e in il[ptr[b]:ptr[b + 1]]]
+        for (b, bb, o) in il:
             inc[b] += self.T[s][o][:, None] * out_s[bb]
         return inc
 
-    def downward(self, s, in_parent):
+    def downward(self, s, in_parent, children=None, out=None):
         """Contribution to level-s incoming spectra from level s+1."""
         lev, par = self.tree.levels[s], self.tree.levels[s + 1]
         gc, gp = self.grids[s], self.grids[s + 1]
         I = self.interp[s]
-        out = np.zeros((len(lev['ij']), gc.K, 4), dtype=complex)
-        for c in range(len(lev['ij'])):
+        if out is None:
+            out = np.zeros((len(lev['ij']), gc.K, 4), dtype=complex)
+        for c in (range(len(lev['ij'])) if children is None else children):
             B = lev['parent'][c]
             shift = np.exp(-1j * self.k * (gp.khat @ (lev['centre'][c] - par['centre'][B])))
             v = (gp.w * shift)[:, None] * in_parent[B]
             out[c] = (I.T @ v) / gc.w[:, None]
         return out
 
-    def receive(self, inc0):
+    def receive(self, inc0, mus=None, out=None):
         sc = self.scene
         g = self.grids[0]
         k, z = self.k, self.zeta
         cen = self.tree.levels[0]['centre']
-        y = np.zeros((sc.p, 2, sc.n_psi), dtype=complex)
-        for mu in range(sc.p):
+        y = np.zeros((sc.p, 2, sc.n_psi), dtype=complex) if out is None else out.reshape(sc.p, 2, sc.n_psi)
+        for mu in (range(sc.p) if mus is None else mus):
             P = self.patterns[sc.shape_ids[mu]]
             shift = np.exp(-1j * k * (g.khat @ (sc.centres[mu] - cen[mu])))
             B = inc0[mu] * (g.w * shift)[:, None]
