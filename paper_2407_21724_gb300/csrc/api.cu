@@ -34,7 +34,8 @@ void free_scene(Ctx* c) {
     dfree(L.d_T64); dfree(L.d_T32); dfree(L.d_parent); dfree(L.d_quad); dfree(L.d_ch_ptr);
     dfree(L.d_ch_idx); dfree(L.d_ch_quad); dfree(L.d_th_src); dfree(L.d_th_refl); dfree(L.d_th_w64);
     dfree(L.d_th_w32); dfree(L.d_th_pk); dfree(L.d_th_ws64); dfree(L.d_th_ws32); dfree(L.d_ph_src); dfree(L.d_ph_w64); dfree(L.d_ph_w32); dfree(L.d_shift64);
-    dfree(L.d_shift32); dfree(L.d_ant_lo); dfree(L.d_ant_pjp); dfree(L.d_ant_pw64); dfree(L.d_ant_pw32);
+    dfree(L.d_shift32); dfree(L.d_ip2_band); dfree(L.d_an2_lo); dfree(L.d_an2_pst); dfree(L.d_an2_pw);
+    dfree(L.d_an2_tws); dfree(L.d_an2_ttp); dfree(L.d_an2_tw); dfree(L.d_ant_lo); dfree(L.d_ant_pjp); dfree(L.d_ant_pw64); dfree(L.d_ant_pw32);
     dfree(L.d_ant_ttp); dfree(L.d_ant_tw64); dfree(L.d_ant_tw32);
     dfree(L.d_tht_ptr); dfree(L.d_tht_tp); dfree(L.d_tht_refl); dfree(L.d_tht_w64); dfree(L.d_tht_w32);
     dfree(L.d_pht_ptr); dfree(L.d_pht_jp); dfree(L.d_pht_w64); dfree(L.d_pht_w32); dfree(L.d_wthp64);
@@ -168,6 +169,46 @@ int build_interp(Ctx* c, Level& C, const Level& P) {
   if ((rc = upload(c, &C.d_th_pk, tpk)) || (rc = upload(c, &C.d_th_ws64, tws)) ||
       (rc = upload(c, &C.d_th_ws32, tws32)))
     return rc;
+  // staged FP32 interpolation (k_interp2): 256 threads; the phi pass gives a
+  // thread NCP column parts (16 bytes each, 2 per direction) of RPT rows; a
+  // tile of TR parent rows reads the band of child rows its taps name
+  {
+    const int NP = 2 * P.nph;
+    int ng, ncp, rpt;
+    if (NP <= 256) { ncp = 1; ng = 256 / NP; rpt = 6; }
+    else { ncp = (NP + 255) / 256; ng = 1; rpt = std::max(1, 8 / ncp); }
+    int TR = std::min(P.nth, ng * rpt);
+    const size_t rowb = (size_t)C.nph * 32;
+    auto band_of = [&](int t0, int t1, int* r0, int* nr) {
+      int lo = ntc, hi = -1;
+      for (int tp = t0; tp < t1; ++tp)
+        for (int a = 0; a < 4; ++a) { lo = std::min(lo, tsrc[4 * tp + a]); hi = std::max(hi, tsrc[4 * tp + a]); }
+      *r0 = lo;
+      *nr = hi - lo + 1;
+    };
+    // shrink the tile until two bands and the tile's theta-pass rows fit 110 KB
+    for (;;) {
+      int br = 0;
+      for (int t0 = 0; t0 < P.nth; t0 += TR) {
+        int r0, nr;
+        band_of(t0, std::min(P.nth, t0 + TR), &r0, &nr);
+        br = std::max(br, nr);
+      }
+      if (TR == 1 || 2 * (size_t)br * rowb + (size_t)TR * (rowb + 96) <= 110 * 1024) break;
+      TR = std::max(1, TR / 2);
+    }
+    C.ip2_TR = TR;
+    C.ip2_nrt = (P.nth + TR - 1) / TR;
+    C.ip2_NCP = ncp;
+    C.ip2_RPT = (TR + ng - 1) / ng;
+    std::vector<int> band(2 * C.ip2_nrt);
+    C.ip2_BR = 0;
+    for (int t = 0; t < C.ip2_nrt; ++t) {
+      band_of(t * TR, std::min(P.nth, (t + 1) * TR), &band[t], &band[C.ip2_nrt + t]);
+      C.ip2_BR = std::max(C.ip2_BR, band[C.ip2_nrt + t]);
+    }
+    if ((rc = upload(c, &C.d_ip2_band, band))) return rc;
+  }
   if ((rc = upload(c, &C.d_th_src, tsrc)) || (rc = upload(c, &C.d_th_refl, trefl)) ||
       (rc = upload(c, &C.d_th_w64, tw)) || (rc = upload(c, &C.d_th_w32, tw32)) ||
       (rc = upload(c, &C.d_ph_src, psrc)) || (rc = upload(c, &C.d_ph_w64, pw)) ||
@@ -272,6 +313,101 @@ int build_interp(Ctx* c, Level& C, const Level& P) {
         tpk[(size_t)i * C.ant_TM + q] = pk;
         tpw[(size_t)i * C.ant_TM + q] = real ? tww[e] : 0.0;
       }
+    // staged FP32 anterpolation (k_anterp2)
+    {
+      const int PM = pm, TM = tm;
+      // phi: the taps of child column j are consecutive parent columns (mod
+      // nphP); unwrap them around j's position and keep PM slots from the first
+      std::vector<int> pst(C.nph);
+      std::vector<float> pw2((size_t)C.nph * PM, 0.f);
+      int padl = 0, padr = 0;
+      for (int j = 0; j < C.nph; ++j) {
+        const int ref = (int)std::lround((double)j * P.nph / C.nph);
+        int dmin = 1 << 30;
+        std::vector<int> dd;
+        for (int e = pptr[j]; e < pptr[j + 1]; ++e) {
+          int d = ((pjp[e] - ref) % P.nph + P.nph) % P.nph;
+          if (d > P.nph / 2) d -= P.nph;
+          dd.push_back(d);
+          dmin = std::min(dmin, d);
+        }
+        if (dd.empty()) dmin = 0;
+        pst[j] = ref + dmin;
+        for (size_t t = 0; t < dd.size(); ++t) {
+          const int slot = dd[t] - dmin;
+          if (slot >= PM) return fail(c, SMR_E_INVALID_ARG, "anterpolation phi taps are not consecutive");
+          pw2[(size_t)j * PM + slot] += (float)pww[pptr[j] + t];
+        }
+        padl = std::max(padl, -pst[j]);
+        padr = std::max(padr, pst[j] + PM - P.nph);
+      }
+      // theta: consecutive parent rows (no pole reflection) from a window start
+      // kept inside [0, nthP - TM]; otherwise the packed taps
+      std::vector<int> tws(C.nth), ttp2((size_t)C.nth * TM);
+      std::vector<float> tw2((size_t)C.nth * TM, 0.f);
+      for (int i = 0; i < C.nth; ++i) {
+        bool refl = false;
+        int first = P.nth;
+        for (int e = tptr[i]; e < tptr[i + 1]; ++e) { refl = refl || trf[e]; first = std::min(first, ttp[e]); }
+        if (tptr[i + 1] == tptr[i]) first = 0;
+        if (!refl && P.nth >= TM) {
+          const int ws = std::min(first, P.nth - TM);
+          tws[i] = ws;
+          for (int e = tptr[i]; e < tptr[i + 1]; ++e) {
+            const int slot = ttp[e] - ws;
+            if (slot < 0 || slot >= TM) return fail(c, SMR_E_INVALID_ARG, "anterpolation theta taps are not consecutive");
+            tw2[(size_t)i * TM + slot] += (float)tww[e];
+          }
+          for (int k = 0; k < TM; ++k) ttp2[(size_t)i * TM + k] = ws + k;
+        } else {
+          tws[i] = -1;
+          for (int k = 0; k < TM; ++k) {
+            const int e = tptr[i] + k;
+            const bool real = e < tptr[i + 1];
+            const int e0 = tptr[i + 1] > tptr[i] ? tptr[i] : -1;
+            ttp2[(size_t)i * TM + k] = real ? (ttp[e] | (trf[e] << 16)) : (e0 >= 0 ? (ttp[e0] | (trf[e0] << 16)) : 0);
+            tw2[(size_t)i * TM + k] = real ? (float)tww[e] : 0.f;
+          }
+        }
+      }
+      // child-row tiles: the widest tile whose parent band fits 100 KB
+      // (padded conjugate-shifted rows + phi-transposed rows)
+      const size_t per_row = (size_t)(P.nph + padl + padr) * 32 + (size_t)C.nph * 32;
+      auto tile_band = [&](int i0, int i1, int* lo, int* hi) {
+        *lo = P.nth; *hi = 0;
+        for (int i = i0; i < i1; ++i)
+          for (int k = 0; k < TM; ++k) {
+            const int tp = ttp2[(size_t)i * TM + k] & 0xffff;
+            *lo = std::min(*lo, tp);
+            *hi = std::max(*hi, tp + 1);
+          }
+      };
+      int TI = C.nth, br = 0;
+      for (;; TI = std::max(1, TI / 2)) {
+        br = 0;
+        for (int i0 = 0; i0 < C.nth; i0 += TI) {
+          int lo, hi;
+          tile_band(i0, std::min(C.nth, i0 + TI), &lo, &hi);
+          br = std::max(br, hi - lo);
+        }
+        if (TI == 1 || (size_t)br * per_row <= 100 * 1024) break;
+      }
+      C.an2_TI = TI;
+      C.an2_nit = (C.nth + TI - 1) / TI;
+      C.an2_BR = br;
+      C.an2_PM = PM;
+      C.an2_TM = TM;
+      C.an2_PADL = padl;
+      C.an2_PADR = padr;
+      std::vector<int> lohi2(2 * C.an2_nit);
+      for (int it = 0; it < C.an2_nit; ++it)
+        tile_band(it * TI, std::min(C.nth, (it + 1) * TI), &lohi2[it], &lohi2[C.an2_nit + it]);
+      if ((size_t)br * per_row > 100 * 1024) C.an2_TI = 0;     // does not fit: k_anterp1
+      if ((rc = upload(c, &C.d_an2_lo, lohi2)) || (rc = upload(c, &C.d_an2_pst, pst)) ||
+          (rc = upload(c, &C.d_an2_pw, pw2)) || (rc = upload(c, &C.d_an2_tws, tws)) ||
+          (rc = upload(c, &C.d_an2_ttp, ttp2)) || (rc = upload(c, &C.d_an2_tw, tw2)))
+        return rc;
+    }
     std::vector<float> ppw32(ppw.begin(), ppw.end()), tpw32(tpw.begin(), tpw.end());
     if ((rc = upload(c, &C.d_ant_pjp, ppj)) || (rc = upload(c, &C.d_ant_pw64, ppw)) ||
         (rc = upload(c, &C.d_ant_pw32, ppw32)) || (rc = upload(c, &C.d_ant_ttp, tpk)) ||
@@ -606,6 +742,11 @@ int set_scene(Ctx* c, int p, const double* centres, const int* shape_ids, const 
   if ((rc = build_modes(c)) || (rc = build_patterns(c)) || (rc = build_translations(c)) ||
       (rc = build_near(c)) || (rc = build_tc(c)) || (rc = build_near_tc(c)))
     return rc;
+  // device flag that the bounded waits of the staged and tensor-core kernels raise
+  if (!c->d_tc_err) {
+    SMR_CUDA(c, cudaMalloc((void**)&c->d_tc_err, sizeof(int)));
+    SMR_CUDA(c, cudaMemset(c->d_tc_err, 0, sizeof(int)));
+  }
   SMR_CUDA(c, cudaDeviceSynchronize());
   c->have_scene = true;
   return SMR_OK;
@@ -1106,15 +1247,17 @@ int smr_autotune(smr_ctx* h, int R, int precision, void* stream) {
   // translation: 8x8 tiles (full, half direction chunk) and 4x4 tiles
   std::vector<std::vector<double>> ttr(c->nlev, std::vector<double>(5, 1e30));
   std::vector<std::vector<double>> tip(c->nlev, std::vector<double>(3, 1e30));
-  std::vector<std::vector<double>> tan_(c->nlev, std::vector<double>(3, 1e30));
-  const int anv[5] = {0, 0, 1, 2, 0};          // anterpolation variant timed in trial v
+  std::vector<std::vector<double>> tan_(c->nlev, std::vector<double>(4, 1e30));
+  const int anv[5] = {0, 0, 1, 2, 3};          // anterpolation variant timed in trial v
   double agg[2] = {1e30, 1e30}, rec[2] = {1e30, 1e30}, nea[2] = {1e30, 1e30};
   const int agg0 = c->tune_tc_agg, rec0 = c->tune_tc_rec, nea0 = c->tune_tc_near;
   for (int v = 1; v <= 4; ++v) {
     // variant 4 (few-box kernel) only where a level has at most 1024 boxes
     for (auto& L : c->lev) {
       L.tune_tr[q] = (v == 4 && L.nbox > 1024) ? 1 : v;
-      L.tune_ip[q] = (v == 2) ? 2 : 0;
+      // interpolation: the built-in rule (staged kernel in FP32), k_interp1
+      // with the full or the half theta-row tile
+      L.tune_ip[q] = (v == 2) ? 2 : (v == 3 ? 1 : 0);
       L.tune_an[q] = anv[v];
     }
     c->tune_tc_agg = c->tune_tc_rec = c->tune_tc_near = (v == 3) ? 0 : 1;
@@ -1125,7 +1268,8 @@ int smr_autotune(smr_ctx* h, int R, int precision, void* stream) {
       auto an = t.find({"anterpolate", s});
       if (an != t.end()) tan_[s][anv[v]] = std::min(tan_[s][anv[v]], an->second);
       auto ip = t.find({"interpolate", s});
-      if (ip != t.end()) tip[s][v == 2 ? 2 : 0] = std::min(tip[s][v == 2 ? 2 : 0], ip->second);
+      const int iv = c->lev[s].tune_ip[q];
+      if (ip != t.end()) tip[s][iv] = std::min(tip[s][iv], ip->second);
     }
     int tc = (v == 3) ? 0 : 1;
     auto a = t.find({"aggregate", 0});
@@ -1141,9 +1285,12 @@ int smr_autotune(smr_ctx* h, int R, int precision, void* stream) {
     for (int v = 2; v <= 4; ++v)
       if (ttr[s][v] < ttr[s][bv]) bv = v;
     L.tune_tr[q] = rc ? 0 : bv;
-    L.tune_ip[q] = (!rc && tip[s][2] < tip[s][0]) ? 2 : 0;
-    int ba = 0;
+    int bi = 0;
     for (int v = 1; v <= 2; ++v)
+      if (tip[s][v] < tip[s][bi]) bi = v;
+    L.tune_ip[q] = rc ? 0 : bi;
+    int ba = 0;
+    for (int v = 1; v <= 3; ++v)
       if (tan_[s][v] < tan_[s][ba]) ba = v;
     L.tune_an[q] = rc ? 0 : ba;
   }

@@ -603,7 +603,7 @@ __global__ void k_translate(int K, int R, int RC, int KC, int ntx, int ntile, co
 // once for all four targets (conflict-free: lanes read consecutive 16-byte
 // parts).  CTA = 8x8 targets (4x4 parents) x KC directions; 16 x KC x NT threads.
 template <typename T, int KC>
-__global__ void __launch_bounds__(512) k_translate1(int K, int ntx, int ntile,
+__global__ void __launch_bounds__(512, 2) k_translate1(int K, int ntx, int ntile,
                                                     const int* __restrict__ tiles, int map_x0, int map_y0,
                                                     int map_w, int map_h, const int* __restrict__ boxmap,
                                                     const typename CV<T>::V* __restrict__ Tg,
@@ -624,7 +624,12 @@ __global__ void __launch_bounds__(512) k_translate1(int K, int ntx, int ntile,
   constexpr int W = KC * 4;
   V* S = reinterpret_cast<V*>(smem_raw);              // [HS*HS sources][KC][4]
   V* Ts = S + HS * HS * W;                            // [49 offsets][KC]
-  int* bid = reinterpret_cast<int*>(Ts + 49 * KC);   // [HS*HS] source box ids
+  // FP32: the table entries as (t_r, t_r, -t_i, t_i), so that a complex
+  // multiply-add of two fields is four packed FMAs
+  constexpr bool PK = sizeof(T) == 4;
+  float4* Ts4 = reinterpret_cast<float4*>(Ts);
+  int* bid = reinterpret_cast<int*>(PK ? reinterpret_cast<unsigned char*>(Ts4 + 49 * KC)
+                                       : reinterpret_cast<unsigned char*>(Ts + 49 * KC));   // [HS*HS] source box ids
   int* tb = bid + HS * HS;                            // [TS*TS] target box ids
   for (int t = threadIdx.x; t < HS * HS + TS * TS; t += blockDim.x) {
     int sx, sy;
@@ -651,7 +656,9 @@ __global__ void __launch_bounds__(512) k_translate1(int K, int ntx, int ntile,
   }
   for (int t = threadIdx.x; t < 49 * KC; t += blockDim.x) {
     int o = t / KC, kl = t - o * KC;
-    Ts[t] = (kl < nk) ? Tg[(size_t)o * K + k0 + kl] : czero<V>();
+    const V tv = (kl < nk) ? Tg[(size_t)o * K + k0 + kl] : czero<V>();
+    if constexpr (PK) Ts4[t] = make_float4((float)tv.x, (float)tv.x, -(float)tv.y, (float)tv.y);
+    else Ts[t] = tv;
   }
   cp_async_wait_all();
   __syncthreads();
@@ -675,11 +682,31 @@ __global__ void __launch_bounds__(512) k_translate1(int K, int ntx, int ntile,
 #pragma unroll
     for (int wx = 0; wx < 6; ++wx) {
       H v = reinterpret_cast<const H*>(Sp + (wy * HS + wx) * W)[h];
+      if constexpr (PK) {
+        // (re, im) += (t_r, t_r) (v_re, v_im) + (-t_i, t_i) (v_im, v_re), per field
+        const float2 v0 = make_float2(v.x, v.y), v1 = make_float2(v.z, v.w);
+        const float2 s0 = make_float2(v.y, v.x), s1 = make_float2(v.w, v.z);
+        const float4* T4 = Ts4 + kl;
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int dx = (q & 1) + 2 - wx, dy = (q >> 1) + 2 - wy;
-        if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1) continue;
-        P::cfma(acc[q], Tp[((dx + 3) * 7 + (dy + 3)) * KC], v);
+        for (int q = 0; q < 4; ++q) {
+          const int dx = (q & 1) + 2 - wx, dy = (q >> 1) + 2 - wy;
+          if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1) continue;
+          const float4 t = T4[((dx + 3) * 7 + (dy + 3)) * KC];
+          const float2 tr = make_float2(t.x, t.y), tn = make_float2(t.z, t.w);
+          float2 a0 = make_float2(acc[q].x, acc[q].y), a1 = make_float2(acc[q].z, acc[q].w);
+          a0 = __ffma2_rn(tr, v0, a0);
+          a0 = __ffma2_rn(tn, s0, a0);
+          a1 = __ffma2_rn(tr, v1, a1);
+          a1 = __ffma2_rn(tn, s1, a1);
+          acc[q] = make_float4(a0.x, a0.y, a1.x, a1.y);
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int dx = (q & 1) + 2 - wx, dy = (q >> 1) + 2 - wy;
+          if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1) continue;
+          P::cfma(acc[q], Tp[((dx + 3) * 7 + (dy + 3)) * KC], v);
+        }
       }
     }
   }
@@ -1126,6 +1153,12 @@ static int far_impl(Ctx* c, int R, const double2* x, double2* y, bool accumulate
     pbeg(c, st, "interpolate", s,
          ((double)Lc.nbox * Lc.K + (double)Lp.nbox * Lp.K) * 4 * R_ * es + 4.0 * Lp.K * es,
          (double)Lc.nbox * Lp.nth * Lc.nph * 4 * R_ * 16.0 + (double)Lc.nbox * Lp.K * 4 * R_ * 24.0);
+    if (!f64 && R == 1 && Lc.tune_ip[1] == 0 && interp2_ok(c, s)) {
+      int rc = run_interp2(c, s, st);
+      pend(c, st);
+      if (rc) return rc;
+      continue;
+    }
     if (R == 1 && Lp.nph * Part<T>::NT <= 256 * EM1<T>::v) {
       int TR = std::max(1, std::min(Lp.nth, (256 * EM1<T>::v) / (Lp.nph * Part<T>::NT)));
       if (Lc.tune_ip[f64 ? 0 : 1] == 2) TR = std::max(1, TR / 2);
@@ -1208,7 +1241,9 @@ static int far_impl(Ctx* c, int R, const double2* x, double2* y, bool accumulate
       const bool halfc = (tv == 2);
       int KC1 = (f64 ? 8 : 16) / (halfc ? 2 : 1);
       int nk1 = (L.K + KC1 - 1) / KC1;
-      size_t sm1 = ((size_t)144 * KC1 * 4 + (size_t)49 * KC1) * sizeof(V) + (144 + 64) * sizeof(int);
+      // FP32 tables are staged as 16-byte (t_r, t_r, -t_i, t_i) entries
+      size_t sm1 = ((size_t)144 * KC1 * 4) * sizeof(V) + (size_t)49 * KC1 * (f64 ? sizeof(V) : 16) +
+                   (144 + 64) * sizeof(int);
       auto kt = halfc ? k_translate1<T, (sizeof(T) == 8 ? 4 : 8)> : k_translate1<T, (sizeof(T) == 8 ? 8 : 16)>;
       cudaFuncSetAttribute(kt, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
       kt<<<(unsigned)(L.ntile8_ne * nk1), 16 * KC1 * Part<T>::NT, sm1, st>>>(
@@ -1230,6 +1265,12 @@ static int far_impl(Ctx* c, int R, const double2* x, double2* y, bool accumulate
          ((double)Lp.nbox * Lp.K + 2.0 * Lc.nbox * Lc.K) * 4 * R_ * es + 4.0 * Lp.K * es,
          (double)Lc.nbox * Lp.nth * Lc.nph * 4 * R_ * 8.0 * 2 * (double)Lp.nph / Lc.nph * 4.0 / 4.0 +
              (double)Lc.nbox * Lc.K * 4 * R_ * 16.0 * (double)Lp.nth / Lc.nth);
+    if (!f64 && R == 1 && Lc.tune_an[1] == 0 && anterp2_ok(c, s)) {
+      int rc = run_anterp2(c, s, st);
+      pend(c, st);
+      if (rc) return rc;
+      continue;
+    }
     if (R == 1) {
       const int an = Lc.tune_an[f64 ? 0 : 1];
       int JC = Lc.ant_JC[f64 ? 0 : 1];

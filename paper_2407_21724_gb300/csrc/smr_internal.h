@@ -116,11 +116,38 @@ struct Level {
   // right-hand side; 0 = the built-in rule.  Translation: 1 / 2 = 8x8 target
   // tiles with the full / half direction chunk, 3 = 4x4 tiles, 4 = the
   // few-box kernel (threads along the directions).  Interpolation
-  // into the parent of this level: 2 = half the theta-row tile.
+  // into the parent of this level: 0 = the built-in rule (the staged kernel
+  // k_interp2 in FP32 where its tile fits), 1 = k_interp1 with the full, 2 =
+  // with half the theta-row tile.
   int tune_tr[2] = {0, 0};
   int tune_ip[2] = {0, 0};
-  // anterpolation into this level: 1 = half the column chunk, 2 = 256 threads
+  // anterpolation into this level: 0 = the built-in rule (the staged kernel
+  // k_anterp2 in FP32 where its tile fits), 1 = k_anterp1 with half the
+  // column chunk, 2 = with 256 threads, 3 = k_anterp1 as built
   int tune_an[2] = {0, 0};
+  // staged single right-hand-side FP32 interpolation into the parent of this
+  // level (k_interp2): tiles of ip2_TR parent theta rows, each with the band
+  // of child rows [first, first + count) its theta taps read ([2][nrt]);
+  // ip2_BR the widest band; ip2_NCP / ip2_RPT the phi-pass shape (column
+  // parts and rows per thread)
+  int ip2_TR = 0, ip2_nrt = 0, ip2_BR = 0, ip2_NCP = 0, ip2_RPT = 0;
+  int* d_ip2_band = nullptr;
+  // staged single right-hand-side FP32 anterpolation into this level
+  // (k_anterp2): child theta-row tiles of an2_TI rows, each with the parent
+  // rows [lo, hi) it reads ([2][nit], widest an2_BR); phi-transposed taps of
+  // child column j: an2_PM consecutive parent columns from an2_pst[j]
+  // (unwrapped, padded rows extend an2_PADL left and an2_PADR right), weights
+  // [nph][PM]; theta-transposed taps of child row i: an2_TM slots, either the
+  // consecutive parent rows from an2_tws[i] (weights [nth][TM]) or, where a tap
+  // is reflected through a pole (an2_tws[i] = -1), the packed rows an2_ttp
+  // (tp | refl << 16) with the same weight slots
+  int an2_TI = 0, an2_nit = 0, an2_BR = 0, an2_PM = 0, an2_TM = 0, an2_PADL = 0, an2_PADR = 0;
+  int* d_an2_lo = nullptr;
+  int* d_an2_pst = nullptr;
+  float* d_an2_pw = nullptr;
+  int* d_an2_tws = nullptr;
+  int* d_an2_ttp = nullptr;
+  float* d_an2_tw = nullptr;
   int ant_PM = 0, ant_TM = 0;             // padded transposed taps per child column / row
   int ant_PMx = 0, ant_TMx = 0;           // real maxima
   int* d_ant_pjp = nullptr;
@@ -253,6 +280,7 @@ struct Ctx {
   float* d_tc_agg = nullptr;              // [S][M tiles][K chunks][hi | lo][128][32] aggregation images
   // tensor cores for aggregation / receive chosen by smr_autotune (-1: not tuned)
   int tune_tc_agg = -1, tune_tc_rec = -1, tune_tc_near = -1;
+  bool lv2_enable = true;                 // staged level kernels for the FP32 product (smr_set_level_kernels)
   // near product on the tensor cores: block images, and per lattice offset
   // (phase; self blocks first) tiles of up to 128 pairs sharing a block
   bool tcn_ready = false;
@@ -372,6 +400,11 @@ int run_near_tc(Ctx* c, double2* y, cudaStream_t st);
 int prep_x32(Ctx* c, int R, int prec, const double2* x, cudaStream_t st);
 int run_aggregate_tc(Ctx* c, const double2* x, const float2* x32, float2* out0, cudaStream_t st);
 int tc_check(Ctx* c);
+// staged FP32 level kernels (k_levels.cu)
+bool interp2_ok(const Ctx* c, int s);
+int run_interp2(Ctx* c, int s, cudaStream_t st);
+bool anterp2_ok(const Ctx* c, int s);
+int run_anterp2(Ctx* c, int s, cudaStream_t st);
 
 // ------------------------------------------------------------------ linear algebra (k_linalg.cu)
 // h[j*R + r] = sum_i conj(V_j[i][r]) w[i][r] for j < J (V_j = V + j*ldv), FP64.
