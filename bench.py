@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--workload", default="metalens200", choices=sorted(WORKLOADS))
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--train-arrays", type=int, default=400,
+    ap.add_argument("--train-arrays", type=int, default=2000,
                     help="20x20 arrays solved to train the learned initial guess (0: skip)")
     return ap.parse_args()
 
@@ -450,10 +450,10 @@ def run_ours(a):
                 # learned local-coupling preconditioner, built inside the timed solve
                 smr.smr_nn_precond(ctx, [k for k, _ in incs], [q for _, q in incs], learned["scale"], b)
                 extra["precond"] = smr.SMR_PRECOND_LEARNED
-            # the learned preconditioner is an ablation arm: bounded at twice the
-            # tuned solve's iterations so that a stagnating run stays short
-            mi = 3000 if not lpc else max(50, 2 * gm["tuned_fp32_inner_fp64_outer"]["iters"])
-            rc, stt = smr.smr_solve(ctx, b, xs, R=R, tol=1e-4, precision=prec, maxit=mi, **extra)
+            # the learned preconditioner is an ablation arm; if it has not cut
+            # the residual tenfold in 40 iterations the solver falls back to
+            # the block-diagonal one (reported as fallback_precond)
+            rc, stt = smr.smr_solve(ctx, b, xs, R=R, tol=1e-4, precision=prec, maxit=3000, **extra)
             e1.record(st)
             torch.cuda.synchronize(dev)
             stt["solver_seconds"] = stt.pop("seconds")

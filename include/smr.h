@@ -247,7 +247,12 @@ typedef struct {
                       FP32 (Gram-Schmidt products in FP32, sums over the
                       vector, Hessenberg and Givens in FP64) [FP64]          */
   int max_outer;   /* refinement steps for SMR_PREC_FP32 [8]                   */
-  int use_x0;      /* 1: x holds the initial guess on entry; 0: start at 0     */
+  int use_x0;      /* 1: x holds the initial guess on entry; 0: start at 0.
+                      A column whose guess has a true residual above ||b||
+                      (worse than zero) starts at 0 instead                 */
+  int fallback_iters; /* SMR_PRECOND_LEARNED: if the residual has not dropped
+                      10x after this many iterations, the solve switches to
+                      SMR_PRECOND_BLOCKDIAG from the current iterate [40]   */
 } smr_solve_opts;
 
 typedef struct {
@@ -261,6 +266,10 @@ typedef struct {
   double seconds_product;  /* device time of the Arnoldi products             */
   double seconds_precond;  /* ... of the preconditioner applications           */
   double seconds_orth;     /* ... of Gram-Schmidt (inner products, updates)     */
+  int fallback_x0;      /* columns whose initial guess was replaced by zero     */
+  int fallback_precond; /* 1 if the learned preconditioner was replaced by the
+                           block-diagonal one (at iteration iters_learned)      */
+  int iters_learned;    /* iterations run with the learned preconditioner       */
 } smr_solve_stats;
 
 void smr_default_solve_opts(smr_solve_opts* o);

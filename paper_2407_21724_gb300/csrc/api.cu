@@ -796,6 +796,7 @@ void smr_default_solve_opts(smr_solve_opts* o) {
   o->precision = SMR_PREC_FP64;
   o->max_outer = 8;
   o->use_x0 = 0;
+  o->fallback_iters = 40;
 }
 
 int smr_create(smr_ctx** out, const smr_opts* opts) {

@@ -1074,21 +1074,75 @@ int solve(Ctx* c, int R, const double2* b, double2* x, const smr_solve_opts* o, 
     return SMR_E_OOM;
   }
   int its = 0, mv64 = 0, mv32 = 0, outer = 0, nreo = 0, rc = SMR_OK;
+  int fb_x0 = 0, fb_pc = 0, its_learned = 0;
+  int precond = o->precond;
+  const bool learned = precond == SMR_PRECOND_LEARNED && o->fallback_iters > 0;
   std::vector<double> rel;
   double tol = o->tol > 0 ? o->tol : 1e-4;
+  // columns of x set to a * x (a = 0 or 1 per column, host values)
+  auto scale_cols = [&](double2* v, const std::vector<int>& keep) -> int {
+    std::vector<double2> zero(R, make_double2(0, 0)), k(R);
+    for (int q = 0; q < R; ++q) k[q] = make_double2(keep[q] ? 1.0 : 0.0, 0.0);
+    SMR_CUDA(c, cudaMemcpyAsync(W.coef, zero.data(), R * sizeof(double2), cudaMemcpyHostToDevice, st));
+    SMR_CUDA(c, cudaMemcpyAsync(W.coef + R, k.data(), R * sizeof(double2), cudaMemcpyHostToDevice, st));
+    return col_axpby(n, R, W.coef, v, W.coef + R, v, st);
+  };
   if (o->precision == SMR_PREC_FP64) {
-    std::vector<double> tc(R, tol);
-    rc = gmres_core(c, R, SMR_PREC_FP64, o->precond, b, x, o->use_x0 != 0, tc, maxit, m, W, &its,
-                    &mv64, &nreo, rel, st);
+    std::vector<double> tc(R, tol), rel0(R, 1.0);
+    bool have_x0 = o->use_x0 != 0;
+    if (have_x0) {
+      // a guess worse than zero (true residual above ||b||) is dropped
+      std::vector<double> bn(R), rn(R);
+      rc = apply_A(c, R, SMR_PREC_FP64, x, W.w, st);
+      ++mv64;
+      std::vector<double2> mone(R, make_double2(-1, 0)), one(R, make_double2(1, 0));
+      if (!rc) {
+        SMR_CUDA(c, cudaMemcpyAsync(W.u, b, ld * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+        SMR_CUDA(c, cudaMemcpyAsync(W.coef, mone.data(), R * sizeof(double2), cudaMemcpyHostToDevice, st));
+        SMR_CUDA(c, cudaMemcpyAsync(W.coef + R, one.data(), R * sizeof(double2), cudaMemcpyHostToDevice, st));
+        rc = col_axpby(n, R, W.coef, W.w, W.coef + R, W.u, st);
+      }
+      if (!rc) rc = col_norms(c, n, R, b, bn.data(), st);
+      if (!rc) rc = col_norms(c, n, R, W.u, rn.data(), st);
+      std::vector<int> keep(R, 1);
+      for (int q = 0; q < R && !rc; ++q) {
+        const double bq = bn[q] > 0 ? bn[q] : 1.0;
+        if (std::isfinite(rn[q]) && rn[q] > bq) { keep[q] = 0; ++fb_x0; }
+        else rel0[q] = rn[q] / bq;
+      }
+      if (!rc && fb_x0) rc = scale_cols(x, keep);
+    }
+    if (!rc && learned) {
+      // probe: up to fallback_iters iterations with the learned preconditioner
+      rc = gmres_core(c, R, SMR_PREC_FP64, precond, b, x, have_x0, tc, std::min(maxit, o->fallback_iters), m, W,
+                      &its, &mv64, &nreo, rel, st);
+      its_learned = its;
+      if (rc == SMR_E_NOT_CONVERGED) {
+        bool dropped = true;
+        for (int q = 0; q < R; ++q) dropped = dropped && rel[q] <= 0.1 * rel0[q];
+        if (!dropped) { precond = SMR_PRECOND_BLOCKDIAG; fb_pc = 1; }
+        have_x0 = true;
+        rc = SMR_OK;
+      } else if (rc == SMR_OK) {
+        have_x0 = false;               // converged: skip the second call
+        maxit = its;
+      }
+    }
+    if (!rc && its < maxit) {
+      const int its0 = its;
+      rc = gmres_core(c, R, SMR_PREC_FP64, precond, b, x, have_x0, tc, maxit, m, W, &its, &mv64, &nreo, rel, st);
+      if (precond == SMR_PRECOND_LEARNED) its_learned += its - its0;
+    }
   } else {
     // iterative refinement: outer FP64 residual, inner GMRES on the FP32 operator
     double2 *r = nullptr, *dlt = nullptr;
     SMR_CUDA(c, cudaMalloc((void**)&r, ld * sizeof(double2)));
     SMR_CUDA(c, cudaMalloc((void**)&dlt, ld * sizeof(double2)));
-    std::vector<double> bn(R), rn(R);
+    std::vector<double> bn(R), rn(R), rn_probe;
     rc = col_norms(c, n, R, b, bn.data(), st);
     if (!o->use_x0) SMR_CUDA(c, cudaMemsetAsync(x, 0, ld * sizeof(double2), st));
     int max_outer = o->max_outer > 0 ? o->max_outer : 8;
+    bool probe = learned, check = false;
     while (rc == SMR_OK) {
       // r = b - A64 x
       if (outer == 0 && !o->use_x0) {
@@ -1106,6 +1160,35 @@ int solve(Ctx* c, int R, const double2* b, double2* x, const smr_solve_opts* o, 
       }
       rc = col_norms(c, n, R, r, rn.data(), st);
       if (rc) break;
+      if (outer == 0 && o->use_x0) {
+        // a guess worse than zero (true residual above ||b||) is dropped:
+        // x = 0 and r = b in those columns
+        std::vector<int> keep(R, 1);
+        for (int q = 0; q < R; ++q) {
+          const double bq = bn[q] > 0 ? bn[q] : 1.0;
+          if (std::isfinite(rn[q]) && rn[q] > bq) { keep[q] = 0; ++fb_x0; }
+        }
+        if (fb_x0) {
+          if ((rc = scale_cols(x, keep))) break;
+          std::vector<double2> a(R), bb(R);
+          for (int q = 0; q < R; ++q) {
+            a[q] = make_double2(keep[q] ? 0.0 : 1.0, 0.0);
+            bb[q] = make_double2(keep[q] ? 1.0 : 0.0, 0.0);
+            if (!keep[q]) rn[q] = bn[q];
+          }
+          SMR_CUDA(c, cudaMemcpyAsync(W.coef, a.data(), R * sizeof(double2), cudaMemcpyHostToDevice, st));
+          SMR_CUDA(c, cudaMemcpyAsync(W.coef + R, bb.data(), R * sizeof(double2), cudaMemcpyHostToDevice, st));
+          if ((rc = col_axpby(n, R, W.coef, b, W.coef + R, r, st))) break;
+        }
+      }
+      if (check) {
+        // the probe with the learned preconditioner must have cut the true
+        // residual tenfold; otherwise the block-diagonal one takes over
+        bool dropped = true;
+        for (int q = 0; q < R; ++q) dropped = dropped && rn[q] <= 0.1 * rn_probe[q];
+        if (!dropped) { precond = SMR_PRECOND_BLOCKDIAG; fb_pc = 1; }
+        check = false;
+      }
       bool finite = true;
       for (int q = 0; q < R; ++q) finite = finite && std::isfinite(rn[q]);
       if (!finite) {
@@ -1128,8 +1211,17 @@ int solve(Ctx* c, int R, const double2* b, double2* x, const smr_solve_opts* o, 
       if (all) break;
       if (outer >= max_outer || its >= maxit) { rc = SMR_E_NOT_CONVERGED; break; }
       std::vector<double> rel_in;
-      int rci = gmres_core(c, R, SMR_PREC_FP32, o->precond, r, dlt, false, tc, maxit - its, m, W,
+      int lim = maxit - its;
+      if (probe) {
+        lim = std::min(lim, o->fallback_iters);
+        rn_probe = rn;
+        probe = false;
+        check = true;
+      }
+      const int its0 = its;
+      int rci = gmres_core(c, R, SMR_PREC_FP32, precond, r, dlt, false, tc, its + lim, m, W,
                            &its, &mv32, &nreo, rel_in, st);
+      if (precond == SMR_PRECOND_LEARNED) its_learned += its - its0;
       if (rci && rci != SMR_E_NOT_CONVERGED) { rc = rci; break; }
       std::vector<double2> one(R, make_double2(1, 0));
       SMR_CUDA(c, cudaMemcpyAsync(W.coef, one.data(), R * sizeof(double2), cudaMemcpyHostToDevice, st));
@@ -1150,6 +1242,9 @@ int solve(Ctx* c, int R, const double2* b, double2* x, const smr_solve_opts* o, 
     stats->seconds_product = W.t_mv;
     stats->seconds_precond = W.t_pc;
     stats->seconds_orth = W.t_or;
+    stats->fallback_x0 = fb_x0;
+    stats->fallback_precond = fb_pc;
+    stats->iters_learned = its_learned;
     double mx = 0;
     for (double v : rel) mx = (std::isnan(v) || std::isnan(mx)) ? std::nan("") : std::max(mx, v);
     stats->resid_true = mx;

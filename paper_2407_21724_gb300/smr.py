@@ -47,14 +47,16 @@ class smr_info_t(C.Structure):
 
 class smr_solve_opts(C.Structure):
     _fields_ = [("tol", C.c_double), ("maxit", C.c_int), ("restart", C.c_int), ("precond", C.c_int),
-                ("precision", C.c_int), ("max_outer", C.c_int), ("use_x0", C.c_int)]
+                ("precision", C.c_int), ("max_outer", C.c_int), ("use_x0", C.c_int),
+                ("fallback_iters", C.c_int)]
 
 
 class smr_solve_stats(C.Structure):
     _fields_ = [("iters", C.c_int), ("matvecs_fp64", C.c_int), ("matvecs_fp32", C.c_int),
                 ("outer", C.c_int), ("reorth", C.c_int), ("resid_true", C.c_double),
                 ("seconds", C.c_double), ("seconds_product", C.c_double),
-                ("seconds_precond", C.c_double), ("seconds_orth", C.c_double)]
+                ("seconds_precond", C.c_double), ("seconds_orth", C.c_double),
+                ("fallback_x0", C.c_int), ("fallback_precond", C.c_int), ("iters_learned", C.c_int)]
 
 
 class smr_launch_t(C.Structure):
@@ -321,7 +323,8 @@ def smr_solve(ctx, b, x, R=None, stream=None, **kw):
     return rc, dict(iters=st.iters, matvecs_fp64=st.matvecs_fp64, matvecs_fp32=st.matvecs_fp32,
                     outer=st.outer, reorth=st.reorth, resid_true=st.resid_true, seconds=st.seconds,
                     seconds_product=st.seconds_product, seconds_precond=st.seconds_precond,
-                    seconds_orth=st.seconds_orth)
+                    seconds_orth=st.seconds_orth, fallback_x0=st.fallback_x0,
+                    fallback_precond=st.fallback_precond, iters_learned=st.iters_learned)
 
 
 def smr_set_tensor_cores(ctx, enable):

@@ -113,10 +113,10 @@ def test_mlp_gradient_matches_oracle(ragged):
     assert l1 < l0
 
 
-def test_learned_initial_guess_gains_over_zero():
-    """Train on 48 solved 16x16 arrays (one batched solve), then on a held-out
-    20x20 array the network's guess must start GMRES well below the zero
-    guess's residual and save iterations to 1e-4."""
+@pytest.fixture(scope="module")
+def trained():
+    """An MLP (width 128) trained on 48 solved random 16x16 arrays (one
+    batched solve, 600 Adam steps); returns (params, scale, losses)."""
     train = workloads.training_arrays(48, n=16, seed0=100000)
     ctx = smr.scene_from_arrays(train)
     n = smr.smr_info(ctx)["n_unknowns"]
@@ -141,8 +141,16 @@ def test_learned_initial_guess_gains_over_zero():
         losses.append(smr.smr_nn_train_step(ctx, 2048, feat, tgt, 2e-3 if it < 400 else 5e-4, idx=idx))
     params = smr.smr_nn_get_params(ctx)
     smr.smr_destroy(ctx)
-    assert np.mean(losses[-20:]) < 0.3 * np.mean(losses[:20])
+    return params, scale, losses
 
+
+def test_learned_initial_guess_gains_over_zero(trained):
+    """On a held-out 20x20 array the network's guess must start GMRES well
+    below the zero guess's residual and save iterations to 1e-4; with the
+    learned local-coupling preconditioner the solve must still converge
+    (the fallback to the block-diagonal preconditioner guarantees it)."""
+    params, scale, losses = trained
+    assert np.mean(losses[-20:]) < 0.3 * np.mean(losses[:20])
     test = workloads.training_arrays(1, n=20, seed0=555)[0]
     ctx = smr.scene_from_arrays([test])
     kh1, pol1 = [test["incidences"][0][0]], [test["incidences"][0][1]]
@@ -163,14 +171,77 @@ def test_learned_initial_guess_gains_over_zero():
     xl = x0.clone()
     _, s1 = smr.smr_solve(ctx, b1, xl, tol=1e-4, use_x0=1)
     assert s1["iters"] < s0["iters"]
-    # learned local-coupling preconditioner with the same network: it runs
-    # and reports a finite true residual (whether it beats the block-diagonal
-    # preconditioner is the ablation the benchmark reports, not a test bar)
+    # learned local-coupling preconditioner with the same network: the solve
+    # converges whatever the network does (a stagnating probe hands over to
+    # the block-diagonal preconditioner); the gain is the benchmark's ablation
     smr.smr_nn_precond(ctx, kh1, pol1, scale, b1)
-    xp = x0.clone()
-    rc, s2 = smr.smr_solve(ctx, b1, xp, tol=1e-4, use_x0=1, precond=smr.SMR_PRECOND_LEARNED, maxit=300)
-    assert rc in (0, smr.SMR_E_NOT_CONVERGED) and np.isfinite(s2["resid_true"]), s2
+    for prec in (smr.SMR_PREC_FP64, smr.SMR_PREC_FP32):
+        xp = x0.clone()
+        rc, s2 = smr.smr_solve(ctx, b1, xp, tol=1e-4, use_x0=1, precond=smr.SMR_PRECOND_LEARNED,
+                               precision=prec, maxit=600)
+        assert rc == 0 and s2["resid_true"] <= 1e-4, s2
+        assert s2["iters_learned"] >= 1 and s2["fallback_x0"] == 0
     smr.smr_destroy(ctx)
+
+
+def test_learned_guess_beats_blockdiag_on_held_out_40x40(trained):
+    """Held-out 40x40 random array (twice the training side, seed outside the
+    training range): block-diagonal GMRES to 1e-4 from the learned guess takes
+    fewer iterations than from zero, in FP64 and in the mixed solver."""
+    params, scale, _ = trained
+    w = workloads.training_arrays(1, n=40, seed0=777)[0]
+    ctx = smr.scene_from_arrays([w])
+    try:
+        kh, pol = [w["incidences"][0][0]], [w["incidences"][0][1]]
+        n = smr.smr_info(ctx)["n_unknowns"]
+        b = torch.empty(n, dtype=torch.complex128, device="cuda")
+        smr.smr_rhs_plane_waves_arrays(ctx, kh, pol, b)
+        smr.smr_nn_init(ctx, width=128, seed=0)
+        smr.smr_nn_set_params(ctx, params)
+        x0 = torch.empty_like(b)
+        smr.smr_nn_predict(ctx, kh, pol, scale, x0)
+        for prec in (smr.SMR_PREC_FP64, smr.SMR_PREC_FP32):
+            xz = torch.zeros_like(b)
+            rc0, s0 = smr.smr_solve(ctx, b, xz, tol=1e-4, precision=prec)
+            xl = x0.clone()
+            rc1, s1 = smr.smr_solve(ctx, b, xl, tol=1e-4, use_x0=1, precision=prec)
+            assert rc0 == 0 and rc1 == 0 and s1["fallback_x0"] == 0
+            assert s1["iters"] < s0["iters"], (prec, s0["iters"], s1["iters"])
+    finally:
+        smr.smr_destroy(ctx)
+
+
+def test_fallbacks_of_a_bad_guess_and_a_stagnating_preconditioner(ragged):
+    """A guess worse than zero is replaced by zero (same iterations as the
+    zero start); a learned preconditioner that has not cut the residual ten
+    times within fallback_iters iterations hands over to the block-diagonal
+    one, and the solve converges."""
+    ws, ctx = ragged
+    inc = [workloads.incidence(10.0 * i, 37.0 * i, "xy"[i % 2]) for i in range(3)]
+    kh, pol = [k for k, _ in inc], [p for _, p in inc]
+    n = smr.smr_info(ctx)["n_unknowns"]
+    b = torch.empty(n, dtype=torch.complex128, device="cuda")
+    smr.smr_rhs_plane_waves_arrays(ctx, kh, pol, b)
+    for prec in (smr.SMR_PREC_FP64, smr.SMR_PREC_FP32):
+        xz = torch.zeros_like(b)
+        _, s0 = smr.smr_solve(ctx, b, xz, tol=1e-6, precision=prec)
+        rng = np.random.default_rng(4)
+        bad = torch.from_numpy(1e3 * (rng.standard_normal(n) + 1j * rng.standard_normal(n))).cuda()
+        rc, s1 = smr.smr_solve(ctx, b, bad, tol=1e-6, precision=prec, use_x0=1)
+        assert rc == 0 and s1["fallback_x0"] == 1 and s1["iters"] == s0["iters"], (s0, s1)
+    # the zero network makes D = 0.1 (a scaled block-diagonal preconditioner);
+    # one iteration does not cut the residual tenfold, so the probe hands over
+    smr.smr_nn_init(ctx, width=8, seed=3)
+    smr.smr_nn_set_params(ctx, np.zeros(smr.smr_nn_num_params(ctx), dtype=np.float32))
+    smr.smr_nn_precond(ctx, kh, pol, 1.0, b)
+    for prec in (smr.SMR_PREC_FP64, smr.SMR_PREC_FP32):
+        xz = torch.zeros_like(b)
+        _, s0 = smr.smr_solve(ctx, b, xz, tol=1e-6, precision=prec)
+        x = torch.zeros_like(b)
+        rc, s = smr.smr_solve(ctx, b, x, tol=1e-6, precision=prec, precond=smr.SMR_PRECOND_LEARNED,
+                              fallback_iters=1)
+        assert rc == 0 and s["fallback_precond"] == 1 and s["iters_learned"] == 1, s
+        assert s["resid_true"] <= 1e-6 and s["iters"] <= s0["iters"] + 4, (s0, s)
 
 
 def test_learned_preconditioner_with_zero_network_is_scaled_blockdiag(ragged):
