@@ -202,14 +202,18 @@ int smr_set_tensor_cores(smr_ctx* ctx, int enable);
  * `precision` on this scene and keeps the fastest for later products (no
  * counterpart in the paper).  Per level: translation with 8x8 target tiles
  * and the full or half direction chunk, 4x4 tiles, or threads along the
- * directions (levels of at most 1024 boxes); interpolation with the full or
- * half theta-row tile; anterpolation with the full or half column chunk or
- * 256-thread CTAs; for SMR_PREC_FP32 also aggregation,
- * receive and the near-field product on the tensor cores or the CUDA
- * cores (the near product on the tensor cores only if at least 5 % faster).  Each variant is timed over
- * three products (CUDA events around every launch, the fastest kept).  Uses
- * and overwrites the context's scratch buffers; drops captured products.
- * R must be 1. */
+ * directions (levels of at most 1024 boxes); interpolation by the staged
+ * kernel (FP32: child theta-row bands bulk-copied into shared memory) or by
+ * the gather kernel with the full or half theta-row tile; anterpolation by
+ * the staged kernel (FP32, where its tile fits) or by the gather kernel with
+ * the full or half column chunk or 256-thread CTAs; for SMR_PREC_FP32 also
+ * aggregation, receive and the near-field product on the tensor cores or the
+ * CUDA cores (the near product on the tensor cores only if at least 5 %
+ * faster).  Each variant is timed over three products (CUDA events around
+ * every launch, the fastest kept).  Uses and overwrites the context's scratch
+ * buffers; drops captured products.  1 <= R <= 256: the variants are timed on
+ * single-column products, and FP32 products with R > 1 run their columns
+ * through the same single-column kernels. */
 int smr_autotune(smr_ctx* ctx, int R, int precision, void* stream);
 
 /* Synchronises `stream` and reports errors found on the device since the

@@ -19,6 +19,10 @@ namespace smr {
 namespace {
 
 constexpr uint32_t LV_DRAIN = 1u << 24;        // polls of the drain after a give-up
+// one fixed ceiling for the dynamic shared memory of every launch of these
+// kernels: a per-launch value would leave a function's limit below the size
+// an earlier-captured graph node of the same function requests
+constexpr int LV_SMEM_MAX = 200 * 1024;
 
 __device__ __forceinline__ uint32_t lv_saddr(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -256,7 +260,7 @@ int launch_interp2(Ctx* c, const Level& Lc, const Level& Lp, const float2* F, fl
   const size_t rowb = (size_t)Lc.nph * 32;
   const size_t sm = 128 + 2 * (size_t)Lc.ip2_BR * rowb + (size_t)Lc.ip2_TR * (rowb + 96) + (size_t)Lc.ip2_TR * 48;
   auto k = k_interp2<NCP, RPTM>;
-  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, LV_SMEM_MAX);
   k<<<(unsigned)(Lp.nbox * Lc.ip2_nrt), 256, sm, st>>>(
       Lc.nth, Lc.nph, Lp.nth, Lp.nph, Lc.ip2_TR, Lc.ip2_nrt, Lc.ip2_BR, Lc.d_ip2_band, Lp.d_ch_ptr, Lp.d_ch_idx,
       Lp.d_ch_quad, Lc.d_th_pk, Lc.d_th_ws32, Lc.d_ph_src, Lc.d_ph_w32, Lc.d_shift32, F, out, c->tc_spin,
@@ -419,7 +423,7 @@ int launch_anterp2(Ctx* c, const Level& Lc, const Level& Lp, cudaStream_t st) {
   const size_t sm = 128 + (size_t)Lc.an2_BR * ((size_t)YL * 32 + (size_t)Lc.nph * 32) +
                     (size_t)((Lc.an2_TI * TM + 3) & ~3) * 4 + (size_t)Lc.an2_TI * TM * 8 + (size_t)Lc.an2_TI * 4;
   auto k = k_anterp2<PM, TM>;
-  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, LV_SMEM_MAX);
   k<<<(unsigned)(Lc.nbox * Lc.an2_nit), 256, sm, st>>>(
       Lc.nth, Lc.nph, Lp.nth, Lp.nph, Lc.an2_TI, Lc.an2_nit, Lc.an2_BR, Lc.an2_PADL, YL, Lc.d_parent, Lc.d_quad,
       Lc.d_an2_lo, Lc.d_an2_pst, Lc.d_an2_pw, Lc.d_an2_tws, Lc.d_an2_ttp, Lc.d_an2_tw, Lc.d_wthp32, Lc.d_shift32,
@@ -432,7 +436,9 @@ int launch_anterp2(Ctx* c, const Level& Lc, const Level& Lp, cudaStream_t st) {
 
 bool interp2_ok(const Ctx* c, int s) {
   const Level& Lc = c->lev[s];
-  return c->lv2_enable && c->d_tc_err && Lc.ip2_NCP >= 1 && Lc.ip2_NCP <= 5 &&
+  const size_t rowb = (size_t)Lc.nph * 32;
+  const size_t sm = 128 + 2 * (size_t)Lc.ip2_BR * rowb + (size_t)Lc.ip2_TR * (rowb + 96) + (size_t)Lc.ip2_TR * 48;
+  return c->lv2_enable && c->d_tc_err && Lc.ip2_NCP >= 1 && Lc.ip2_NCP <= 5 && sm <= (size_t)LV_SMEM_MAX &&
          Lc.ip2_RPT <= (Lc.ip2_NCP == 1 ? 6 : 8 / Lc.ip2_NCP);
 }
 
