@@ -397,6 +397,23 @@ int smr_copy_translation(smr_ctx* ctx, int level, int dx, int dy, double* out);
 int smr_copy_near_block(smr_ctx* ctx, int shape_m, int shape_n, int dx, int dy, double* out);
 int smr_copy_level(smr_ctx* ctx, int level, int kind, double* out, size_t n_doubles);
 
+/* Parity access to the launch variants (the choices smr_autotune makes),
+ * for one level (0 .. n_levels - 1) or every level (-1), for products in
+ * `precision` with one right-hand side:
+ *  SMR_STEP_TRANSLATE: 0 built-in rule, 1 / 2 8x8 target tiles with the full
+ *    / half direction chunk, 3 4x4 tiles, 4 threads along the directions;
+ *  SMR_STEP_INTERPOLATE (into the parent of `level`): 0 built-in rule (in
+ *    FP32 the staged kernel, child theta-row bands bulk-copied into shared
+ *    memory, where its tile fits), 1 / 2 the gather kernel with the full /
+ *    half theta-row tile;
+ *  SMR_STEP_ANTERPOLATE (into `level`): 0 built-in rule (the gather kernel),
+ *    1 half its column chunk, 2 256-thread CTAs, 4 the staged kernel (FP32,
+ *    parent band bulk-copied, where its tile fits).
+ * A variant that does not apply to a level falls back to the built-in rule.
+ * Drops captured products.  No counterpart in the paper. */
+enum { SMR_STEP_TRANSLATE = 0, SMR_STEP_INTERPOLATE = 1, SMR_STEP_ANTERPOLATE = 2 };
+int smr_set_variant(smr_ctx* ctx, int step, int level, int precision, int variant);
+
 /* Right-hand sides of R plane waves, like smr_rhs_plane_waves, but the call
  * allocates and frees no device memory.  For callers that cannot call
  * cudaMalloc: an application whose device memory is fully reserved by its own

@@ -34,8 +34,9 @@ void free_scene(Ctx* c) {
     dfree(L.d_T64); dfree(L.d_T32); dfree(L.d_parent); dfree(L.d_quad); dfree(L.d_ch_ptr);
     dfree(L.d_ch_idx); dfree(L.d_ch_quad); dfree(L.d_th_src); dfree(L.d_th_refl); dfree(L.d_th_w64);
     dfree(L.d_th_w32); dfree(L.d_th_pk); dfree(L.d_th_ws64); dfree(L.d_th_ws32); dfree(L.d_ph_src); dfree(L.d_ph_w64); dfree(L.d_ph_w32); dfree(L.d_shift64);
-    dfree(L.d_shift32); dfree(L.d_ip2_band); dfree(L.d_an2_lo); dfree(L.d_an2_pst); dfree(L.d_an2_pw);
-    dfree(L.d_an2_tws); dfree(L.d_an2_ttp); dfree(L.d_an2_tw); dfree(L.d_ant_lo); dfree(L.d_ant_pjp); dfree(L.d_ant_pw64); dfree(L.d_ant_pw32);
+    dfree(L.d_shift32); dfree(L.d_ip2_band); dfree(L.d_an2_lo);
+    dfree(L.d_an2_ttp); dfree(L.d_an2_tw); dfree(L.d_an2_pst2); dfree(L.d_an2_pwp);
+    dfree(L.d_an2_tq); dfree(L.d_an2_twq); dfree(L.d_ant_lo); dfree(L.d_ant_pjp); dfree(L.d_ant_pw64); dfree(L.d_ant_pw32);
     dfree(L.d_ant_ttp); dfree(L.d_ant_tw64); dfree(L.d_ant_tw32);
     dfree(L.d_tht_ptr); dfree(L.d_tht_tp); dfree(L.d_tht_refl); dfree(L.d_tht_w64); dfree(L.d_tht_w32);
     dfree(L.d_pht_ptr); dfree(L.d_pht_jp); dfree(L.d_pht_w64); dfree(L.d_pht_w32); dfree(L.d_wthp64);
@@ -370,27 +371,69 @@ int build_interp(Ctx* c, Level& C, const Level& P) {
           }
         }
       }
-      // child-row tiles: the widest tile whose parent band fits 100 KB
-      // (padded conjugate-shifted rows + phi-transposed rows)
-      const size_t per_row = (size_t)(P.nph + padl + padr) * 32 + (size_t)C.nph * 32;
+      // pairs of neighbouring child columns (rows) share one window of loaded
+      // values: dense weights over PM + 2 parent columns (the second column's
+      // taps start 0..2 columns after the first's) and TM + 3 parent rows;
+      // weight rows padded to multiples of 4 for 16-byte loads
+      const int WPM = PM + 2, WTM = TM + 3, WPS = (WPM + 3) & ~3, WTS = (WTM + 3) & ~3;
+      const int npp = C.nph / 2, nqp = (C.nth + 1) / 2;
+      std::vector<int> pst2(npp);
+      std::vector<float> pwp((size_t)npp * 2 * WPS, 0.f);
+      bool pairs_ok = (C.nph % 2) == 0;
+      for (int q = 0; q < npp && pairs_ok; ++q) {
+        const int ja = 2 * q, jb = 2 * q + 1, d = pst[jb] - pst[ja];
+        if (d < 0 || d + PM > WPM) { pairs_ok = false; break; }
+        pst2[q] = pst[ja];
+        for (int k = 0; k < PM; ++k) {
+          pwp[((size_t)q * 2 + 0) * WPS + k] = pw2[(size_t)ja * PM + k];
+          pwp[((size_t)q * 2 + 1) * WPS + d + k] = pw2[(size_t)jb * PM + k];
+        }
+        padl = std::max(padl, -pst2[q]);
+        padr = std::max(padr, pst2[q] + WPM - P.nph);
+      }
+      // row pairs (2q, 2q + 1): window start, or -1 where a row reaches a pole
+      std::vector<int> tq(nqp, -1);
+      std::vector<float> twq((size_t)nqp * 2 * WTS, 0.f);
+      for (int q = 0; q < nqp; ++q) {
+        const int ia = 2 * q, ib = 2 * q + 1;
+        if (tws[ia] < 0 || (ib < C.nth && tws[ib] < 0) || P.nth < WTM) continue;
+        const int ws = std::min(tws[ia], P.nth - WTM);
+        const int da = tws[ia] - ws, db = ib < C.nth ? tws[ib] - ws : 0;
+        if (da < 0 || da + TM > WTM || db < 0 || db + TM > WTM) continue;
+        tq[q] = ws;
+        for (int k = 0; k < TM; ++k) {
+          twq[((size_t)q * 2 + 0) * WTS + da + k] = tw2[(size_t)ia * TM + k];
+          if (ib < C.nth) twq[((size_t)q * 2 + 1) * WTS + db + k] = tw2[(size_t)ib * TM + k];
+        }
+      }
+      // child-row tiles (an even number of rows, so pairs align): the widest
+      // tile whose parent band fits 100 KB (the band as copied, its padded
+      // conjugate-shifted rows, the phi-transposed rows)
+      const size_t per_row = (size_t)P.nph * 32 + (size_t)(P.nph + padl + padr) * 32 + (size_t)C.nph * 32;
       auto tile_band = [&](int i0, int i1, int* lo, int* hi) {
         *lo = P.nth; *hi = 0;
-        for (int i = i0; i < i1; ++i)
-          for (int k = 0; k < TM; ++k) {
-            const int tp = ttp2[(size_t)i * TM + k] & 0xffff;
-            *lo = std::min(*lo, tp);
-            *hi = std::max(*hi, tp + 1);
+        for (int i = i0; i < i1; ++i) {
+          if (tq[i / 2] >= 0) {
+            *lo = std::min(*lo, tq[i / 2]);
+            *hi = std::max(*hi, tq[i / 2] + WTM);
+          } else {
+            for (int k = 0; k < TM; ++k) {
+              const int tp = ttp2[(size_t)i * TM + k] & 0xffff;
+              *lo = std::min(*lo, tp);
+              *hi = std::max(*hi, tp + 1);
+            }
           }
+        }
       };
       int TI = C.nth, br = 0;
-      for (;; TI = std::max(1, TI / 2)) {
+      for (;; TI = std::max(2, (TI / 2) & ~1)) {
         br = 0;
         for (int i0 = 0; i0 < C.nth; i0 += TI) {
           int lo, hi;
           tile_band(i0, std::min(C.nth, i0 + TI), &lo, &hi);
           br = std::max(br, hi - lo);
         }
-        if (TI == 1 || (size_t)br * per_row <= 100 * 1024) break;
+        if (TI == 2 || (size_t)br * per_row <= 100 * 1024) break;
       }
       C.an2_TI = TI;
       C.an2_nit = (C.nth + TI - 1) / TI;
@@ -402,10 +445,11 @@ int build_interp(Ctx* c, Level& C, const Level& P) {
       std::vector<int> lohi2(2 * C.an2_nit);
       for (int it = 0; it < C.an2_nit; ++it)
         tile_band(it * TI, std::min(C.nth, (it + 1) * TI), &lohi2[it], &lohi2[C.an2_nit + it]);
-      if ((size_t)br * per_row > 100 * 1024) C.an2_TI = 0;     // does not fit: k_anterp1
-      if ((rc = upload(c, &C.d_an2_lo, lohi2)) || (rc = upload(c, &C.d_an2_pst, pst)) ||
-          (rc = upload(c, &C.d_an2_pw, pw2)) || (rc = upload(c, &C.d_an2_tws, tws)) ||
-          (rc = upload(c, &C.d_an2_ttp, ttp2)) || (rc = upload(c, &C.d_an2_tw, tw2)))
+      if ((size_t)br * per_row > 100 * 1024 || !pairs_ok) C.an2_TI = 0;   // does not fit: k_anterp1
+      if ((rc = upload(c, &C.d_an2_lo, lohi2)) ||
+          (rc = upload(c, &C.d_an2_ttp, ttp2)) || (rc = upload(c, &C.d_an2_tw, tw2)) ||
+          (rc = upload(c, &C.d_an2_pst2, pst2)) || (rc = upload(c, &C.d_an2_pwp, pwp)) ||
+          (rc = upload(c, &C.d_an2_tq, tq)) || (rc = upload(c, &C.d_an2_twq, twq)))
         return rc;
     }
     std::vector<float> ppw32(ppw.begin(), ppw.end()), tpw32(tpw.begin(), tpw.end());
@@ -1052,6 +1096,28 @@ int smr_set_tensor_cores(smr_ctx* h, int enable) {
   return SMR_OK;
 }
 
+int smr_set_variant(smr_ctx* h, int step, int level, int precision, int variant) {
+  if (!h) return SMR_E_INVALID_ARG;
+  Ctx* c = &h->c;
+  if (!check_scene(c)) return SMR_E_STATE;
+  if (precision != SMR_PREC_FP64 && precision != SMR_PREC_FP32)
+    return fail(c, SMR_E_INVALID_ARG, "precision must be SMR_PREC_FP64 or SMR_PREC_FP32");
+  if (level < -1 || level >= c->nlev) return fail(c, SMR_E_INVALID_ARG, "level out of range");
+  const int q = precision == SMR_PREC_FP64 ? 0 : 1;
+  const bool ok = (step == SMR_STEP_TRANSLATE && variant >= 0 && variant <= 4) ||
+                  (step == SMR_STEP_INTERPOLATE && variant >= 0 && variant <= 2) ||
+                  (step == SMR_STEP_ANTERPOLATE && (variant >= 0 && variant <= 2 || variant == 4));
+  if (!ok) return fail(c, SMR_E_INVALID_ARG, "unknown step or variant");
+  for (int s = (level < 0 ? 0 : level); s < (level < 0 ? c->nlev : level + 1); ++s) {
+    Level& L = c->lev[s];
+    if (step == SMR_STEP_TRANSLATE) L.tune_tr[q] = variant;
+    else if (step == SMR_STEP_INTERPOLATE) L.tune_ip[q] = variant;
+    else L.tune_an[q] = variant;
+  }
+  free_graphs(c);                              // captured products used the old variants
+  return SMR_OK;
+}
+
 int smr_set_wait_limit(smr_ctx* h, long long rounds) {
   if (!h) return SMR_E_INVALID_ARG;
   Ctx* c = &h->c;
@@ -1250,8 +1316,8 @@ int smr_autotune(smr_ctx* h, int R, int precision, void* stream) {
   // translation: 8x8 tiles (full, half direction chunk) and 4x4 tiles
   std::vector<std::vector<double>> ttr(c->nlev, std::vector<double>(5, 1e30));
   std::vector<std::vector<double>> tip(c->nlev, std::vector<double>(3, 1e30));
-  std::vector<std::vector<double>> tan_(c->nlev, std::vector<double>(4, 1e30));
-  const int anv[5] = {0, 0, 1, 2, 3};          // anterpolation variant timed in trial v
+  std::vector<std::vector<double>> tan_(c->nlev, std::vector<double>(5, 1e30));
+  const int anv[5] = {0, 0, 1, 2, 4};          // anterpolation variant timed in trial v
   double agg[2] = {1e30, 1e30}, rec[2] = {1e30, 1e30}, nea[2] = {1e30, 1e30};
   const int agg0 = c->tune_tc_agg, rec0 = c->tune_tc_rec, nea0 = c->tune_tc_near;
   for (int v = 1; v <= 4; ++v) {
@@ -1293,7 +1359,7 @@ int smr_autotune(smr_ctx* h, int R, int precision, void* stream) {
       if (tip[s][v] < tip[s][bi]) bi = v;
     L.tune_ip[q] = rc ? 0 : bi;
     int ba = 0;
-    for (int v = 1; v <= 3; ++v)
+    for (int v = 1; v <= 4; ++v)
       if (tan_[s][v] < tan_[s][ba]) ba = v;
     L.tune_an[q] = rc ? 0 : ba;
   }

@@ -271,166 +271,211 @@ int launch_interp2(Ctx* c, const Level& Lc, const Level& Lp, const float2* F, fl
 
 
 // Anterpolation s + 1 -> s (the weighted adjoint of the interpolation, with
-// the conjugate shift).  CTA = (child box c, tile of TI child theta rows);
+// the conjugate shift).  CTA = (parent box B, tile of TI child theta rows);
 // 256 threads.  The parent rows [lo, hi) the tile's taps read arrive by one
-// bulk copy per row into wrap-padded rows Y (one mbarrier); then, all from
-// shared memory:
-//   Y[tp][jp]  = w_theta,p[tp] conj(shift_q[tp][jp]) in_P[tp][jp]   (in place)
-//   Gt[tp][j]  = sum_k pw[j][k] Y[tp][pst[j] + k]                     (phi-transposed)
-//   in_c[i][j] += sum_k tw[i][k] Gt[tp_k][j, or j + N/2 if reflected] (theta-transposed)
-// PM / TM: the phi / theta slot counts (the widest transposed stencil).
+// bulk copy (one mbarrier) and serve the four children of B in turn; per
+// child c (quadrant q), all from shared memory:
+//   Y[tp][jp]  = w_theta,p[tp] conj(shift_q[tp][jp]) in_P[tp][jp]    (wrap-padded rows)
+//   Gt[tp][j]  = sum_k pw[j][k] Y[tp][pst[j] + k]                      (phi-transposed)
+//   in_c[i][j] += sum_k tw[i][k] Gt[tp_k][j, or j + N/2 if reflected]  (theta-transposed)
+// Both transposed passes give a thread two neighbouring outputs from one
+// window of loaded values.  PM / TM: the widest phi / theta transposed stencil.
 template <int PM, int TM>
 __global__ void __launch_bounds__(256, 3) k_anterp2(int nthC, int nphC, int nthP, int nphP, int TI, int nit, int BR,
-                                                    int PADL, int YL, const int* __restrict__ parent,
-                                                    const int* __restrict__ quad, const int* __restrict__ lohi,
-                                                    const int* __restrict__ pst, const float* __restrict__ pw,
-                                                    const int* __restrict__ tws, const int* __restrict__ ttp,
-                                                    const float* __restrict__ tw, const float* __restrict__ wthp,
+                                                    int PADL, int YL, const int* __restrict__ ch_ptr,
+                                                    const int* __restrict__ ch_idx, const int* __restrict__ ch_quad,
+                                                    const int* __restrict__ lohi, const int* __restrict__ ttp,
+                                                    const float* __restrict__ tw, const int* __restrict__ pst2,
+                                                    const float* __restrict__ pwp, const int* __restrict__ tq,
+                                                    const float* __restrict__ twq, const float* __restrict__ wthp,
                                                     const float2* __restrict__ shift, const float2* __restrict__ inP,
                                                     float2* __restrict__ inC, uint32_t spin, int* __restrict__ err) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int tid = threadIdx.x;
-  const int c = blockIdx.x / nit, it = blockIdx.x - c * nit;
+  const int B = blockIdx.x / nit, it = blockIdx.x - B * nit;
   const int i0 = it * TI, ni = min(TI, nthC - i0);
   const int lo = lohi[it], nb = lohi[nit + it] - lo;
-  const int B = parent[c], q = quad[c];
   const int Kc = nthC * nphC, Kp = nthP * nphP;
   const uint32_t yrowb = (uint32_t)YL * 32u, prowb = (uint32_t)nphP * 32u, growb = (uint32_t)nphC * 32u;
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
-  unsigned char* Y = smem + 128;                                   // [BR][YL]
+  unsigned char* Bd = smem + 128;                                  // [BR][nphP] the parent band
+  unsigned char* Y = Bd + (size_t)BR * prowb;                      // [BR][YL]
   unsigned char* Gt = Y + (size_t)BR * yrowb;                      // [BR][nphC]
   int* tt = reinterpret_cast<int*>(Gt + (size_t)BR * growb);       // [TI][TM] band offset | refl << 31
   float2* twp = reinterpret_cast<float2*>(tt + ((TI * TM + 3) & ~3));  // [TI][TM] (w, w), 16-byte aligned
-  int* tf = reinterpret_cast<int*>(twp + TI * TM);                 // [TI] band offset of the window, or -1
+  const int e0 = ch_ptr[B], nch = ch_ptr[B + 1] - e0;
   if (tid == 0) {
     lv_mbar_init(lv_saddr(&bar[0]), 1);
     lv_fence_init();
   }
   __syncthreads();
   if (tid == 0) {
-    lv_expect(lv_saddr(&bar[0]), (uint32_t)nb * prowb);
-    const float2* src = inP + ((size_t)B * Kp + (size_t)lo * nphP) * 4;
-    for (int r = 0; r < nb; ++r)
-      lv_copy_tx(lv_saddr(Y + r * yrowb + (uint32_t)PADL * 32u), src + (size_t)r * nphP * 4, prowb,
-                 lv_saddr(&bar[0]));
+    // the band's rows are contiguous in in_P: one copy
+    lv_copy(lv_saddr(Bd), inP + ((size_t)B * Kp + (size_t)lo * nphP) * 4, (uint32_t)nb * prowb,
+            lv_saddr(&bar[0]));
   }
+  // packed theta taps of the tile's rows (used by the row pairs at the poles)
   for (int t = tid; t < ni * TM; t += 256) {
-    const int il = t / TM, i = i0 + il;
     const int pk = ttp[(size_t)i0 * TM + t];
     tt[t] = (int)((uint32_t)((pk & 0xffff) - lo) * growb | ((uint32_t)(pk >> 16) << 31));
     const float w = tw[(size_t)i0 * TM + t];
     twp[t] = make_float2(w, w);
-    if (t - il * TM == 0) {
-      const int ws = tws[i];
-      tf[il] = ws >= 0 ? (int)((uint32_t)(ws - lo) * growb) : -1;
-    }
   }
   int ok = 1;
   if (tid == 0) ok = lv_mbar_wait(lv_saddr(&bar[0]), 0u, spin);
   if (__syncthreads_or(!ok)) {
     if (tid == 0) {
-      lv_mbar_wait(lv_saddr(&bar[0]), 0u, LV_DRAIN);                 // the row copies land first
+      lv_mbar_wait(lv_saddr(&bar[0]), 0u, LV_DRAIN);                 // the copy lands first
       atomicExch(err, 1);
     }
     return;
   }
-  // ---- Y = w_theta,p conj(shift) in_P, in place, and the wrap padding
-  {
-    const int NP = 2 * nphP, PADR = YL - PADL - nphP;
-    const int ng = NP <= 256 ? 256 / NP : 1, g = NP <= 256 ? tid / NP : 0;
-    const int cp0 = NP <= 256 ? tid % NP : tid, cst = NP <= 256 ? NP : 256;
-    if (g < ng)
-      for (int cp = cp0; cp < NP; cp += cst) {
-        const int jp = cp >> 1, h = cp & 1;
-        const uint32_t o = (uint32_t)(PADL + jp) * 32u + (uint32_t)h * 16u;
-        const int wr = jp < PADR ? nphP : (jp >= nphP - PADL ? -nphP : 0);   // wrap copy, in columns
-        const float2* shp = shift + (size_t)q * Kp + (size_t)lo * nphP + jp;
-#pragma unroll 2
-        for (int r = g; r < nb; r += ng) {
-          float4* p = reinterpret_cast<float4*>(Y + r * yrowb + o);
-          const float2 sv = shp[(size_t)r * nphP];
-          const float w = wthp[lo + r];
-          const float4 v = *p;
-          const float cr = w * sv.x, ci = w * sv.y;                 // w conj(s) v
-          const float4 y = make_float4(fmaf(cr, v.x, ci * v.y), fmaf(cr, v.y, -ci * v.x),
-                                       fmaf(cr, v.z, ci * v.w), fmaf(cr, v.w, -ci * v.z));
-          *p = y;
-          if (wr) *reinterpret_cast<float4*>(reinterpret_cast<unsigned char*>(p) + wr * 32) = y;
-        }
-      }
-  }
-  __syncthreads();
-  // ---- Gt = phi-transposed taps (PM consecutive padded columns per child column)
+  constexpr int WPM = PM + 2, WPS = (WPM + 3) & ~3, WTM = TM + 3, WTS = (WTM + 3) & ~3;
+  const int NP = 2 * nphP, PADR = YL - PADL - nphP;
   const int NC = 2 * nphC, half = nphC >> 1;
-  const int ngc = NC <= 256 ? 256 / NC : 1, gc = NC <= 256 ? tid / NC : 0;
-  const int cpc = NC <= 256 ? tid % NC : tid, cstc = NC <= 256 ? NC : 256;
-  if (gc < ngc)
-    for (int cp = cpc; cp < NC; cp += cstc) {
-      const int j = cp >> 1, h = cp & 1;
-      float2 w2[PM];
-#pragma unroll
-      for (int k = 0; k < PM; ++k) {
-        const float w = pw[(size_t)j * PM + k];
-        w2[k] = make_float2(w, w);
-      }
-      const unsigned char* y0 = Y + (uint32_t)(pst[j] + PADL) * 32u + (uint32_t)h * 16u;
-      unsigned char* g0 = Gt + (uint32_t)j * 32u + (uint32_t)h * 16u;
-      for (int r = gc; r < nb; r += ngc) {
-        const unsigned char* yr = y0 + r * yrowb;
-        float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-        for (int k = 0; k < PM; ++k) fma4p(a, w2[k], lds4(yr + 32 * k));
-        *reinterpret_cast<float4*>(g0 + r * growb) = a;
-      }
-    }
-  __syncthreads();
-  // ---- in_c += theta-transposed taps
-  if (gc < ngc)
-    for (int cp = cpc; cp < NC; cp += cstc) {
-      const int j = cp >> 1, h = cp & 1;
-      const int jr = j < half ? j + half : j - half;
-      const uint32_t jo = (uint32_t)j * 32u + (uint32_t)h * 16u, jro = (uint32_t)jr * 32u + (uint32_t)h * 16u;
-      float4* dst = reinterpret_cast<float4*>(inC + ((size_t)c * Kc + (size_t)i0 * nphC) * 4) + cp;
-      for (int il = gc; il < ni; il += ngc) {
-        // the incoming value this row adds to is loaded first, so its latency
-        // overlaps the taps
-        float4* d = dst + (size_t)il * NC;
-        float4 cur = *d;
-        const float2* wr = twp + il * TM;
-        float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
-        const int f = tf[il];
-        if (f >= 0) {
-          const unsigned char* p = Gt + (uint32_t)f + jo;
-#pragma unroll
-          for (int k = 0; k < TM; ++k) fma4p(a, wr[k], lds4(p + k * growb));
-        } else {
-          const int* tr = tt + il * TM;
-#pragma unroll
-          for (int k = 0; k < TM; ++k) {
-            const int tk = tr[k];
-            fma4p(a, wr[k], lds4(Gt + ((uint32_t)tk & 0x7fffffffu) + (tk < 0 ? jro : jo)));
+  for (int e = 0; e < nch; ++e) {
+    const int c = ch_idx[e0 + e], q = ch_quad[e0 + e];
+    // ---- Y = w_theta,p conj(shift_q) in_P and the wrap padding
+    {
+      const int ng = NP <= 256 ? 256 / NP : 1, g = NP <= 256 ? tid / NP : 0;
+      const int cp0 = NP <= 256 ? tid % NP : tid, cst = NP <= 256 ? NP : 256;
+      if (g < ng)
+        for (int cp = cp0; cp < NP; cp += cst) {
+          const int jp = cp >> 1, h = cp & 1;
+          const uint32_t ob = (uint32_t)jp * 32u + (uint32_t)h * 16u;
+          const uint32_t oy = (uint32_t)(PADL + jp) * 32u + (uint32_t)h * 16u;
+          const int wr = jp < PADR ? nphP : (jp >= nphP - PADL ? -nphP : 0);   // wrap copy, in columns
+          const float2* shp = shift + (size_t)q * Kp + (size_t)lo * nphP + jp;
+#pragma unroll 2
+          for (int r = g; r < nb; r += ng) {
+            const float2 sv = shp[(size_t)r * nphP];
+            const float w = wthp[lo + r];
+            const float4 v = lds4(Bd + r * prowb + ob);
+            const float cr = w * sv.x, ci = w * sv.y;               // w conj(s) v
+            const float4 y = make_float4(fmaf(cr, v.x, ci * v.y), fmaf(cr, v.y, -ci * v.x),
+                                         fmaf(cr, v.z, ci * v.w), fmaf(cr, v.w, -ci * v.z));
+            unsigned char* p = Y + r * yrowb + oy;
+            *reinterpret_cast<float4*>(p) = y;
+            if (wr) *reinterpret_cast<float4*>(p + wr * 32) = y;
           }
         }
-        cur.x += a.x; cur.y += a.y; cur.z += a.z; cur.w += a.w;
-        *d = cur;
+    }
+    __syncthreads();
+    // ---- Gt = phi-transposed taps.  A thread owns a pair of neighbouring
+    // child columns (2P, 2P + 1) and one 16-byte part: one window of WPM
+    // padded parent columns serves both outputs (dense weights in registers)
+    {
+      const int NC2 = nphC;                                        // (pair, part) tasks per row
+      const int ng2 = NC2 <= 256 ? 256 / NC2 : 1, g2 = NC2 <= 256 ? tid / NC2 : 0;
+      const int cp2 = NC2 <= 256 ? tid % NC2 : tid, cs2 = NC2 <= 256 ? NC2 : 256;
+      if (g2 < ng2)
+        for (int cp = cp2; cp < NC2; cp += cs2) {
+          const int P = cp >> 1, h = cp & 1;
+          float wa[WPM], wb[WPM];
+#pragma unroll
+          for (int k = 0; k < WPM; ++k) {
+            wa[k] = pwp[((size_t)P * 2 + 0) * WPS + k];
+            wb[k] = pwp[((size_t)P * 2 + 1) * WPS + k];
+          }
+          const unsigned char* y0 = Y + (uint32_t)(pst2[P] + PADL) * 32u + (uint32_t)h * 16u;
+          unsigned char* g0 = Gt + (uint32_t)(2 * P) * 32u + (uint32_t)h * 16u;
+          for (int r = g2; r < nb; r += ng2) {
+            const unsigned char* yr = y0 + r * yrowb;
+            float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
+#pragma unroll
+            for (int k = 0; k < WPM; ++k) {
+              const float4 v = lds4(yr + 32 * k);
+              a.x = fmaf(wa[k], v.x, a.x); a.y = fmaf(wa[k], v.y, a.y);
+              a.z = fmaf(wa[k], v.z, a.z); a.w = fmaf(wa[k], v.w, a.w);
+              b.x = fmaf(wb[k], v.x, b.x); b.y = fmaf(wb[k], v.y, b.y);
+              b.z = fmaf(wb[k], v.z, b.z); b.w = fmaf(wb[k], v.w, b.w);
+            }
+            *reinterpret_cast<float4*>(g0 + r * growb) = a;
+            *reinterpret_cast<float4*>(g0 + r * growb + 32) = b;
+          }
+        }
+    }
+    __syncthreads();
+    // ---- in_c += theta-transposed taps.  Task = (pair of child rows, column
+    // part), column parts fastest so a warp shares its row pair: one window of
+    // WTM consecutive parent rows serves both rows; a pair that reaches a pole
+    // takes the packed taps row by row
+    {
+      const int nq = (ni + 1) >> 1, Q0 = i0 >> 1;
+      float4* dst0 = reinterpret_cast<float4*>(inC + ((size_t)c * Kc + (size_t)i0 * nphC) * 4);
+      for (int u = tid; u < nq * NC; u += 256) {
+        const int qq = u / NC, cp = u - qq * NC;
+        const int j = cp >> 1, h = cp & 1;
+        const uint32_t jo = (uint32_t)j * 32u + (uint32_t)h * 16u;
+        const int il0 = 2 * qq, two = il0 + 1 < ni;
+        float4* d0 = dst0 + (size_t)il0 * NC + cp;
+        // the incoming values these rows add to are loaded first
+        float4 cur0 = *d0, cur1 = two ? d0[NC] : make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
+        const int ws = tq[Q0 + qq];
+        if (ws >= 0) {
+          const unsigned char* p = Gt + (uint32_t)(ws - lo) * growb + jo;
+          const float4* w0 = reinterpret_cast<const float4*>(twq + (size_t)(Q0 + qq) * 2 * WTS);
+          const float4* w1 = w0 + WTS / 4;
+          float wa[WTS], wb[WTS];
+#pragma unroll
+          for (int k = 0; k < WTS / 4; ++k) {
+            const float4 x = __ldg(w0 + k), y = __ldg(w1 + k);
+            wa[4 * k] = x.x; wa[4 * k + 1] = x.y; wa[4 * k + 2] = x.z; wa[4 * k + 3] = x.w;
+            wb[4 * k] = y.x; wb[4 * k + 1] = y.y; wb[4 * k + 2] = y.z; wb[4 * k + 3] = y.w;
+          }
+#pragma unroll
+          for (int k = 0; k < WTM; ++k) {
+            const float4 v = lds4(p + k * growb);
+            a.x = fmaf(wa[k], v.x, a.x); a.y = fmaf(wa[k], v.y, a.y);
+            a.z = fmaf(wa[k], v.z, a.z); a.w = fmaf(wa[k], v.w, a.w);
+            b.x = fmaf(wb[k], v.x, b.x); b.y = fmaf(wb[k], v.y, b.y);
+            b.z = fmaf(wb[k], v.z, b.z); b.w = fmaf(wb[k], v.w, b.w);
+          }
+        } else {
+          const int jr = j < half ? j + half : j - half;
+          const uint32_t jro = (uint32_t)jr * 32u + (uint32_t)h * 16u;
+#pragma unroll
+          for (int rr = 0; rr < 2; ++rr) {
+            if (rr == 1 && !two) break;
+            const int* tr = tt + (il0 + rr) * TM;
+            const float2* wr = twp + (il0 + rr) * TM;
+            float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int k = 0; k < TM; ++k) {
+              const int tk = tr[k];
+              fma4p(acc, wr[k], lds4(Gt + ((uint32_t)tk & 0x7fffffffu) + (tk < 0 ? jro : jo)));
+            }
+            if (rr == 0) a = acc; else b = acc;
+          }
+        }
+        cur0.x += a.x; cur0.y += a.y; cur0.z += a.z; cur0.w += a.w;
+        *d0 = cur0;
+        if (two) {
+          cur1.x += b.x; cur1.y += b.y; cur1.z += b.z; cur1.w += b.w;
+          d0[NC] = cur1;
+        }
       }
     }
+    __syncthreads();                                               // Y and Gt free for the next child
+  }
 }
 
 template <int PM, int TM>
 int launch_anterp2(Ctx* c, const Level& Lc, const Level& Lp, cudaStream_t st) {
   const int YL = Lp.nph + Lc.an2_PADL + Lc.an2_PADR;
-  const size_t sm = 128 + (size_t)Lc.an2_BR * ((size_t)YL * 32 + (size_t)Lc.nph * 32) +
-                    (size_t)((Lc.an2_TI * TM + 3) & ~3) * 4 + (size_t)Lc.an2_TI * TM * 8 + (size_t)Lc.an2_TI * 4;
+  const size_t sm = 128 + (size_t)Lc.an2_BR * ((size_t)Lp.nph * 32 + (size_t)YL * 32 + (size_t)Lc.nph * 32) +
+                    (size_t)((Lc.an2_TI * TM + 3) & ~3) * 4 + (size_t)Lc.an2_TI * TM * 8;
   auto k = k_anterp2<PM, TM>;
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, LV_SMEM_MAX);
-  k<<<(unsigned)(Lc.nbox * Lc.an2_nit), 256, sm, st>>>(
-      Lc.nth, Lc.nph, Lp.nth, Lp.nph, Lc.an2_TI, Lc.an2_nit, Lc.an2_BR, Lc.an2_PADL, YL, Lc.d_parent, Lc.d_quad,
-      Lc.d_an2_lo, Lc.d_an2_pst, Lc.d_an2_pw, Lc.d_an2_tws, Lc.d_an2_ttp, Lc.d_an2_tw, Lc.d_wthp32, Lc.d_shift32,
-      (const float2*)Lp.d_in, (float2*)Lc.d_in, c->tc_spin, c->d_tc_err);
+  k<<<(unsigned)(Lp.nbox * Lc.an2_nit), 256, sm, st>>>(
+      Lc.nth, Lc.nph, Lp.nth, Lp.nph, Lc.an2_TI, Lc.an2_nit, Lc.an2_BR, Lc.an2_PADL, YL, Lp.d_ch_ptr, Lp.d_ch_idx,
+      Lp.d_ch_quad, Lc.d_an2_lo, Lc.d_an2_ttp, Lc.d_an2_tw, Lc.d_an2_pst2, Lc.d_an2_pwp, Lc.d_an2_tq, Lc.d_an2_twq,
+      Lc.d_wthp32, Lc.d_shift32, (const float2*)Lp.d_in, (float2*)Lc.d_in, c->tc_spin, c->d_tc_err);
   SMR_LAUNCH(c);
   return SMR_OK;
 }
+
 
 }  // namespace
 

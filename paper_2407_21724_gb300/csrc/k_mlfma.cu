@@ -1265,7 +1265,7 @@ static int far_impl(Ctx* c, int R, const double2* x, double2* y, bool accumulate
          ((double)Lp.nbox * Lp.K + 2.0 * Lc.nbox * Lc.K) * 4 * R_ * es + 4.0 * Lp.K * es,
          (double)Lc.nbox * Lp.nth * Lc.nph * 4 * R_ * 8.0 * 2 * (double)Lp.nph / Lc.nph * 4.0 / 4.0 +
              (double)Lc.nbox * Lc.K * 4 * R_ * 16.0 * (double)Lp.nth / Lc.nth);
-    if (!f64 && R == 1 && Lc.tune_an[1] == 0 && anterp2_ok(c, s)) {
+    if (!f64 && R == 1 && Lc.tune_an[1] == 4 && anterp2_ok(c, s)) {
       int rc = run_anterp2(c, s, st);
       pend(c, st);
       if (rc) return rc;

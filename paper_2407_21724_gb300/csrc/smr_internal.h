@@ -121,9 +121,9 @@ struct Level {
   // with half the theta-row tile.
   int tune_tr[2] = {0, 0};
   int tune_ip[2] = {0, 0};
-  // anterpolation into this level: 0 = the built-in rule (the staged kernel
-  // k_anterp2 in FP32 where its tile fits), 1 = k_anterp1 with half the
-  // column chunk, 2 = with 256 threads, 3 = k_anterp1 as built
+  // anterpolation into this level: 0 = the built-in rule (k_anterp1), 1 =
+  // k_anterp1 with half the column chunk, 2 = with 256 threads, 4 = the
+  // staged kernel k_anterp2 (FP32, where its tile fits)
   int tune_an[2] = {0, 0};
   // staged single right-hand-side FP32 interpolation into the parent of this
   // level (k_interp2): tiles of ip2_TR parent theta rows, each with the band
@@ -133,21 +133,23 @@ struct Level {
   int ip2_TR = 0, ip2_nrt = 0, ip2_BR = 0, ip2_NCP = 0, ip2_RPT = 0;
   int* d_ip2_band = nullptr;
   // staged single right-hand-side FP32 anterpolation into this level
-  // (k_anterp2): child theta-row tiles of an2_TI rows, each with the parent
-  // rows [lo, hi) it reads ([2][nit], widest an2_BR); phi-transposed taps of
-  // child column j: an2_PM consecutive parent columns from an2_pst[j]
-  // (unwrapped, padded rows extend an2_PADL left and an2_PADR right), weights
-  // [nph][PM]; theta-transposed taps of child row i: an2_TM slots, either the
-  // consecutive parent rows from an2_tws[i] (weights [nth][TM]) or, where a tap
-  // is reflected through a pole (an2_tws[i] = -1), the packed rows an2_ttp
-  // (tp | refl << 16) with the same weight slots
+  // (k_anterp2): child theta-row tiles of an2_TI rows (even, so row pairs
+  // align), each with the parent rows [lo, hi) it reads ([2][nit], widest
+  // an2_BR); an2_PM / an2_TM the widest phi- / theta-transposed stencil; wrap
+  // padding of the parent rows an2_PADL left and an2_PADR right; the packed
+  // theta taps of each child row (tp | refl << 16) with their weights, used
+  // where a row pair reaches a pole
   int an2_TI = 0, an2_nit = 0, an2_BR = 0, an2_PM = 0, an2_TM = 0, an2_PADL = 0, an2_PADR = 0;
   int* d_an2_lo = nullptr;
-  int* d_an2_pst = nullptr;
-  float* d_an2_pw = nullptr;
-  int* d_an2_tws = nullptr;
   int* d_an2_ttp = nullptr;
   float* d_an2_tw = nullptr;
+  // pairs of neighbouring child columns / rows (two outputs per thread from one
+  // window): window start and dense weights [pairs][2][(PM + 2) or (TM + 3),
+  // padded to 4]; a row pair's start is -1 where a row reaches a pole
+  int* d_an2_pst2 = nullptr;
+  float* d_an2_pwp = nullptr;
+  int* d_an2_tq = nullptr;
+  float* d_an2_twq = nullptr;
   int ant_PM = 0, ant_TM = 0;             // padded transposed taps per child column / row
   int ant_PMx = 0, ant_TMx = 0;           // real maxima
   int* d_ant_pjp = nullptr;

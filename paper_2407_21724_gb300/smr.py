@@ -111,6 +111,7 @@ _SIGS = {
     "smr_autotune": (C.c_int, [_P, C.c_int, C.c_int, _P]),
     "smr_sync": (C.c_int, [_P, _P]),
     "smr_set_wait_limit": (C.c_int, [_P, C.c_longlong]),
+    "smr_set_variant": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_int]),
 }
 
 
@@ -337,6 +338,14 @@ def smr_autotune(ctx, precision=SMR_PREC_FP32, stream=None):
 
 def smr_sync(ctx, stream=None):
     _check(ctx, lib().smr_sync(ctx, _stream(stream, None)))
+
+
+SMR_STEP_TRANSLATE, SMR_STEP_INTERPOLATE, SMR_STEP_ANTERPOLATE = 0, 1, 2
+
+
+def smr_set_variant(ctx, step, level, precision, variant):
+    """Select a launch variant of a level step (level -1: every level)."""
+    _check(ctx, lib().smr_set_variant(ctx, int(step), int(level), int(precision), int(variant)))
 
 
 def smr_set_wait_limit(ctx, rounds):
