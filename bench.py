@@ -299,14 +299,15 @@ def run_ours(a):
         ctx = smr.scene_from_workload(w, device=local)
         incs = [w["incidences"][0]]
     setup_s = time.perf_counter() - t0
+    R = 64 if a.workload == "batched100x64" else 1
     t1 = time.perf_counter()
     # launch variants for this scene, timed on single-column products (columns
-    # of a batched FP32 product run through the same kernels)
-    smr.smr_autotune(ctx, smr.SMR_PREC_FP32)
+    # of a batched FP32 product run through the same kernels), and for R > 1
+    # the number of columns in flight
+    smr.smr_autotune(ctx, smr.SMR_PREC_FP32, R=R)
     tune_s = time.perf_counter() - t1
     info = smr.smr_info(ctx)
     n = info["n_unknowns"]
-    R = 64 if a.workload == "batched100x64" else 1
     st = torch.cuda.current_stream(dev)
     if R > 1:
         grid = workloads.incidence_grid64()
@@ -515,7 +516,8 @@ def run_ours(a):
                     config=dict(workload=w["label"], rhs=R, precision="FP32 product, FP64 tables/IO",
                                 l2="L2 flushed (256 MB write) before every timed step",
                                 parallelism="replicas" if world > 1 else "single GPU",
-                                levels=info["n_levels"], L=info["L"], unknowns=n),
+                                levels=info["n_levels"], L=info["L"], unknowns=n,
+                                column_lanes=info["column_lanes"] if R > 1 else 1),
                     fp64_matvecs_per_s=1e3 / ms64, fp64_ms_per_matvec=ms64,
                     ms_per_step_without_graph=ms_direct / R,
                     gmres=gm, errors_vs_fp64=errors, setup_s=setup_s, autotune_s=tune_s,

@@ -151,6 +151,7 @@ typedef struct {
   long long n_near_pairs;   /* particle pairs in the near SpMV (self included) */
   int n_near_blocks;        /* distinct near blocks stored                     */
   double device_bytes;      /* tables + one set of level spectra (R = 1)       */
+  int column_lanes;         /* columns in flight in FP32 products with R > 1   */
 } smr_info_t;
 int smr_info(smr_ctx* ctx, smr_info_t* info);
 
@@ -213,7 +214,9 @@ int smr_set_tensor_cores(smr_ctx* ctx, int enable);
  * every launch, the fastest kept).  Uses and overwrites the context's scratch
  * buffers; drops captured products.  1 <= R <= 256: the variants are timed on
  * single-column products, and FP32 products with R > 1 run their columns
- * through the same single-column kernels. */
+ * through the same single-column kernels.  For SMR_PREC_FP32 and R > 1 it
+ * then times R-column graph products with 1, 2, 4 and 8 column lanes (at
+ * most R; smr_set_column_lanes) and keeps the fastest. */
 int smr_autotune(smr_ctx* ctx, int R, int precision, void* stream);
 
 /* Synchronises `stream` and reports errors found on the device since the
@@ -232,6 +235,19 @@ int smr_sync(smr_ctx* ctx, void* stream);
  * its in-flight copies and MMAs with the default bound.  Drops captured
  * products.  No counterpart in the paper. */
 int smr_set_wait_limit(smr_ctx* ctx, long long rounds);
+
+/* Columns in flight in an FP32 product with R > 1 right-hand sides (1..16,
+ * default 4).  Such a product runs its columns through the single-column
+ * kernels; the columns are dealt round-robin to `lanes` lanes, each with its
+ * own FP32 spectra, separable-pass and near-product buffers (about the
+ * memory of one single-column product per lane, allocated on first use and
+ * kept until smr_set_scene or smr_destroy) and its own stream, forked from
+ * the caller's stream and joined before the call's last launch.  The lanes
+ * overlap the launches of the upper levels, which one column leaves mostly
+ * idle.  Every column's result is the same as alone (the same kernels on
+ * the same data).  SMR_E_INVALID_ARG outside 1..16.  Drops captured
+ * products.  No counterpart in the paper. */
+int smr_set_column_lanes(smr_ctx* ctx, int lanes);
 
 /* z = blockdiag(Z_s^-1) r over particles: the block-diagonal preconditioner
  * of Sec. V (each block the inverse of the particle's self block).

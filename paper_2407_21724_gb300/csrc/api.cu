@@ -29,6 +29,7 @@ template <typename T> void dfree(T*& p) {
 
 void free_scene(Ctx* c) {
   free_graphs(c);
+  free_lanes(c);
   for (auto& L : c->lev) {
     dfree(L.d_khat); dfree(L.d_w); dfree(L.d_il_ptr); dfree(L.d_il_src); dfree(L.d_il_off); dfree(L.d_il_pk);
     dfree(L.d_T64); dfree(L.d_T32); dfree(L.d_parent); dfree(L.d_quad); dfree(L.d_ch_ptr);
@@ -814,6 +815,49 @@ int tmp_buffer(Ctx* c, size_t elems) {
   return SMR_OK;
 }
 
+// Column lanes of FP32 products with R > 1: R-column graph products with 1,
+// 2, 4 and 8 lanes (at most R), each timed over three replays after the
+// capture; the fastest is kept (a lane count must win by 2 % over a smaller
+// one, so near-ties keep the smaller memory footprint).
+int tune_lanes(Ctx* c, int R, cudaStream_t st) {
+  const size_t n = (size_t)2 * c->npsi * c->p;
+  int rc = tmp_buffer(c, 2 * n * R);
+  if (rc) return rc;
+  double2* X = c->d_tmp;
+  double2* Y = c->d_tmp + n * R;
+  SMR_CUDA(c, cudaMemsetAsync(X, 0, n * R * sizeof(double2), st));
+  cudaEvent_t e0, e1;
+  SMR_CUDA(c, cudaEventCreate(&e0));
+  SMR_CUDA(c, cudaEventCreate(&e1));
+  const int nl0 = c->n_lanes;
+  int best_nl = nl0;
+  float best = 1e30f;
+  for (int nl = 1; nl <= 8 && nl <= R && !rc; nl *= 2) {
+    c->n_lanes = nl;
+    free_graphs(c);
+    rc = run_matvec_graph(c, R, SMR_PREC_FP32, X, Y, st);
+    float tmin = 1e30f;
+    for (int k = 0; k < 3 && !rc; ++k) {
+      cudaEventRecord(e0, st);
+      rc = run_matvec_graph(c, R, SMR_PREC_FP32, X, Y, st);
+      cudaEventRecord(e1, st);
+      if (!rc && cudaEventSynchronize(e1) != cudaSuccess) rc = fail(c, SMR_E_CUDA, "timing a lane count");
+      float ms = 0;
+      if (!rc) cudaEventElapsedTime(&ms, e0, e1);
+      tmin = std::min(tmin, ms);
+    }
+    if (!rc && tmin < 0.98f * best) {
+      best = tmin;
+      best_nl = nl;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->n_lanes = rc ? nl0 : best_nl;
+  free_graphs(c);
+  return rc;
+}
+
 }  // namespace
 
 // ====================================================================== ABI
@@ -986,6 +1030,7 @@ int smr_info(smr_ctx* h, smr_info_t* info) {
   info->n_near_blocks = c->nblk;
   bytes += (double)c->nblk * 4 * c->npsi * c->npsi * 24;
   info->device_bytes = bytes;
+  info->column_lanes = c->n_lanes;
   return SMR_OK;
 }
 
@@ -1124,6 +1169,16 @@ int smr_set_wait_limit(smr_ctx* h, long long rounds) {
   if (rounds > 0x7fffffffLL) return fail(c, SMR_E_INVALID_ARG, "wait limit above 2^31 - 1 rounds");
   c->tc_spin = rounds < 0 ? (1u << 24) : (uint32_t)rounds;
   free_graphs(c);                              // captured products carry the old limit
+  return SMR_OK;
+}
+
+int smr_set_column_lanes(smr_ctx* h, int lanes) {
+  if (!h) return SMR_E_INVALID_ARG;
+  Ctx* c = &h->c;
+  if (lanes < 1 || lanes > 16) return fail(c, SMR_E_INVALID_ARG, "lanes must be in 1..16");
+  cudaSetDevice(c->device);
+  c->n_lanes = lanes;
+  free_graphs(c);                              // captured products hold the old lane count
   return SMR_OK;
 }
 
@@ -1375,6 +1430,7 @@ int smr_autotune(smr_ctx* h, int R, int precision, void* stream) {
     c->tune_tc_near = rc ? -1 : (nea[1] < 0.95 * nea[0] ? 1 : 0);
   }
   free_graphs(c);                              // captured products used the trial variants
+  if (!rc && q == 1 && R > 1 && c->split_cols) rc = tune_lanes(c, R, (cudaStream_t)stream);
   return rc;
 }
 

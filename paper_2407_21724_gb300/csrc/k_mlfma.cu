@@ -1448,11 +1448,91 @@ int ensure_split(Ctx* c, int R) {
   return SMR_OK;
 }
 
+void free_lanes(Ctx* c) {
+  for (size_t j = 1; j < c->lanes.size(); ++j) {
+    Ctx::Lane& a = c->lanes[j];
+    for (void* q : a.out) if (q) cudaFree(q);
+    for (void* q : a.in) if (q) cudaFree(q);
+    if (a.G) cudaFree(a.G);
+    if (a.x32) cudaFree(a.x32);
+    if (a.tcn_part) cudaFree(a.tcn_part);
+    if (a.s) cudaStreamDestroy(a.s);
+  }
+  for (auto& a : c->lanes)
+    if (a.ev) cudaEventDestroy(a.ev);
+  c->lanes.clear();
+  if (c->lane_fork) cudaEventDestroy(c->lane_fork);
+  c->lane_fork = nullptr;
+}
+
+// Work buffers of nl column lanes for FP32 single-column products (outside
+// graph capture; lanes that exist are kept and grown only).
+int ensure_lanes(Ctx* c, int nl) {
+  int rc = ensure_spectra(c, 1, SMR_PREC_FP32);
+  if (rc) return rc;
+  if ((int)c->lanes.size() < nl) c->lanes.resize(nl);
+  if (!c->lane_fork) SMR_CUDA(c, cudaEventCreateWithFlags(&c->lane_fork, cudaEventDisableTiming));
+  Ctx::Lane& l0 = c->lanes[0];                 // the context's own buffers
+  l0.out.assign(c->nlev, nullptr);
+  l0.in.assign(c->nlev, nullptr);
+  for (int s = 0; s < c->nlev; ++s) {
+    l0.out[s] = c->lev[s].buf_out[1];
+    l0.in[s] = c->lev[s].buf_in[1];
+  }
+  l0.G = c->G_buf[1];
+  l0.x32 = c->d_x32;
+  l0.tcn_part = c->d_tcn_part;
+  for (int j = 0; j < nl; ++j) {
+    Ctx::Lane& a = c->lanes[j];
+    if (!a.ev) SMR_CUDA(c, cudaEventCreateWithFlags(&a.ev, cudaEventDisableTiming));
+    if (j == 0) continue;
+    if (!a.s) SMR_CUDA(c, cudaStreamCreateWithFlags(&a.s, cudaStreamNonBlocking));
+    if ((int)a.out.size() != c->nlev) {
+      a.out.assign(c->nlev, nullptr);
+      a.in.assign(c->nlev, nullptr);
+    }
+    bool ok = true;
+    for (int s = 0; s < c->nlev && ok; ++s) {
+      const size_t b = c->lev[s].buf_bytes[1];
+      ok = (a.out[s] || cudaMalloc(&a.out[s], b) == cudaSuccess) &&
+           (a.in[s] || cudaMalloc(&a.in[s], b) == cudaSuccess);
+    }
+    if (ok && c->G_size[1] && !a.G) ok = cudaMalloc(&a.G, c->G_size[1]) == cudaSuccess;
+    if (ok && c->d_x32 && !a.x32)
+      ok = cudaMalloc((void**)&a.x32, (size_t)c->p * 2 * c->npsi * sizeof(float2)) == cudaSuccess;
+    if (ok && c->d_tcn_part && !a.tcn_part) ok = cudaMalloc((void**)&a.tcn_part, c->tcn_part_bytes) == cudaSuccess;
+    if (!ok) {
+      cudaGetLastError();
+      free_lanes(c);
+      c->err = "out of device memory for the column lanes of a split product";
+      return SMR_E_OOM;
+    }
+  }
+  return SMR_OK;
+}
+
+// Points the FP32 single-column work buffers at lane j's.
+static void use_lane(Ctx* c, int j) {
+  const Ctx::Lane& a = c->lanes[j];
+  for (int s = 0; s < c->nlev; ++s) {
+    c->lev[s].d_out = a.out[s];
+    c->lev[s].d_in = a.in[s];
+  }
+  c->d_G = a.G;
+  c->d_x32 = a.x32;
+  c->d_tcn_part = a.tcn_part;
+}
+
+int lanes_for(const Ctx* c, int R) { return c->prof ? 1 : std::max(1, std::min(R, c->n_lanes)); }
+
 // y = Z x for R right-hand sides [N][R].  FP32 products with several
 // right-hand sides run column by column on the single right-hand-side kernels
 // (16-byte parts, tensor-core aggregation and receive), which are faster per
 // column than the batched kernels: x is transposed to [R][N], each column is
-// multiplied, and y is transposed back.
+// multiplied, and y is transposed back.  The columns are dealt to the lanes
+// round-robin; lane j > 0 runs on its own stream, forked from st after the
+// transpose and joined before the transpose back, so a graph captured on st
+// holds n_lanes independent chains of single-column products.
 int run_product(Ctx* c, int R, int prec, const double2* x, double2* y, cudaStream_t st) {
   if (!split_columns(c, R, prec)) {
     int rc = prep_x32(c, R, prec, x, st);
@@ -1460,7 +1540,9 @@ int run_product(Ctx* c, int R, int prec, const double2* x, double2* y, cudaStrea
     if (rc) return rc;
     return run_far(c, R, prec, x, y, true, st);
   }
+  const int nl = lanes_for(c, R);
   int rc = ensure_split(c, R);
+  if (!rc) rc = ensure_lanes(c, nl);
   if (rc) return rc;
   const long long n = 2LL * c->npsi * c->p;
   double2* xs = c->d_split;
@@ -1469,10 +1551,28 @@ int run_product(Ctx* c, int R, int prec, const double2* x, double2* y, cudaStrea
   rc = transpose_c128(c, n, R, x, xs, st);
   pend(c, st);
   if (rc) return rc;
+  if (nl > 1) {
+    SMR_CUDA(c, cudaEventRecord(c->lane_fork, st));
+    for (int j = 1; j < nl; ++j) SMR_CUDA(c, cudaStreamWaitEvent(c->lanes[j].s, c->lane_fork, 0));
+  }
   for (int r = 0; r < R && !rc; ++r) {
-    rc = prep_x32(c, 1, prec, xs + (size_t)r * n, st);
-    if (!rc) rc = run_near(c, 1, prec, xs + (size_t)r * n, ys + (size_t)r * n, st);
-    if (!rc) rc = run_far(c, 1, prec, xs + (size_t)r * n, ys + (size_t)r * n, true, st);
+    const int j = r % nl;
+    cudaStream_t sj = j ? c->lanes[j].s : st;
+    use_lane(c, j);
+    rc = prep_x32(c, 1, prec, xs + (size_t)r * n, sj);
+    if (!rc) rc = run_near(c, 1, prec, xs + (size_t)r * n, ys + (size_t)r * n, sj);
+    if (!rc) rc = far_impl<float>(c, 1, xs + (size_t)r * n, ys + (size_t)r * n, true, sj);
+  }
+  use_lane(c, 0);
+  c->x32_of = nullptr;
+  // every forked lane is joined, also after an error, so that a capture ends cleanly
+  for (int j = 1; j < nl; ++j) {
+    cudaError_t e = cudaEventRecord(c->lanes[j].ev, c->lanes[j].s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, c->lanes[j].ev, 0);
+    if (e != cudaSuccess && !rc) {
+      c->err = std::string("joining column lanes: ") + cudaGetErrorString(e);
+      rc = SMR_E_CUDA;
+    }
   }
   if (rc) return rc;
   pbeg(c, st, "transpose", -1, 2.0 * n * R * 16, 0.0);
@@ -1498,6 +1598,7 @@ int run_matvec_graph(Ctx* c, int R, int prec, const double2* x, double2* y, cuda
   const bool split = split_columns(c, R, prec);
   int rc = ensure_spectra(c, split ? 1 : R, prec);
   if (!rc && split) rc = ensure_split(c, R);
+  if (!rc && split) rc = ensure_lanes(c, lanes_for(c, R));
   if (rc) return rc;
   if (!c->capture_stream) SMR_CUDA(c, cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking));
   cudaStream_t cs = c->capture_stream;

@@ -840,7 +840,8 @@ int build_near_tc(Ctx* c) {
     return rc;
   if (c->d_tcn_part) cudaFree(c->d_tcn_part);
   c->d_tcn_part = nullptr;
-  SMR_CUDA(c, cudaMalloc((void**)&c->d_tcn_part, (size_t)NPH * c->p * M4 * sizeof(float)));
+  c->tcn_part_bytes = (size_t)NPH * c->p * M4 * sizeof(float);
+  SMR_CUDA(c, cudaMalloc((void**)&c->d_tcn_part, c->tcn_part_bytes));
   if (c->d_x32) cudaFree(c->d_x32);
   c->d_x32 = nullptr;
   SMR_CUDA(c, cudaMalloc((void**)&c->d_x32, (size_t)c->p * n2 * sizeof(float2)));

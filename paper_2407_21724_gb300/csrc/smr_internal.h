@@ -303,6 +303,23 @@ struct Ctx {
   bool split_cols = true;
   double2* d_split = nullptr;
   size_t split_elems = 0;
+  size_t tcn_part_bytes = 0;
+  // Column lanes of split products: the columns are dealt round-robin to
+  // n_lanes lanes, each with its own FP32 work buffers and stream, so that
+  // the small upper-level launches of several columns overlap.  Lane 0 is
+  // the context's own buffers and the caller's stream (copied, not owned);
+  // lanes 1.. own theirs.
+  struct Lane {
+    std::vector<void*> out, in;           // per level FP32 spectra
+    void* G = nullptr;
+    float2* x32 = nullptr;
+    float* tcn_part = nullptr;
+    cudaStream_t s = nullptr;
+    cudaEvent_t ev = nullptr;             // end of the lane's columns
+  };
+  std::vector<Lane> lanes;
+  int n_lanes = 4;                        // columns in flight (smr_set_column_lanes, smr_autotune)
+  cudaEvent_t lane_fork = nullptr;
   // learned local-coupling preconditioner: diagonal D [N] (one right-hand side)
   double2* d_lpc = nullptr;
   bool lpc_ready = false;
@@ -391,6 +408,9 @@ int run_matvec_graph(Ctx* c, int R, int prec, const double2* x, double2* y, cuda
 // y = Z x (near + far); FP32 with R > 1 runs column by column (split products)
 int run_product(Ctx* c, int R, int prec, const double2* x, double2* y, cudaStream_t st);
 void free_graphs(Ctx* c);
+// column lanes of split FP32 products (buffers allocated outside graph capture)
+int ensure_lanes(Ctx* c, int nl);
+void free_lanes(Ctx* c);
 // tensor-core receive and aggregation (k_tc.cu)
 int build_tc(Ctx* c);
 bool tc_receive_ok(const Ctx* c, int R);

@@ -42,7 +42,8 @@ class smr_info_t(C.Structure):
                 ("n_arrays", C.c_int),
                 ("n_unknowns", C.c_longlong), ("L", C.c_int * 16), ("K", C.c_int * 16),
                 ("n_box", C.c_int * 16), ("n_il", C.c_int * 16), ("n_near_pairs", C.c_longlong),
-                ("n_near_blocks", C.c_int), ("device_bytes", C.c_double)]
+                ("n_near_blocks", C.c_int), ("device_bytes", C.c_double),
+                ("column_lanes", C.c_int)]
 
 
 class smr_solve_opts(C.Structure):
@@ -111,6 +112,7 @@ _SIGS = {
     "smr_autotune": (C.c_int, [_P, C.c_int, C.c_int, _P]),
     "smr_sync": (C.c_int, [_P, _P]),
     "smr_set_wait_limit": (C.c_int, [_P, C.c_longlong]),
+    "smr_set_column_lanes": (C.c_int, [_P, C.c_int]),
     "smr_set_variant": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_int]),
 }
 
@@ -242,7 +244,7 @@ def smr_info(ctx):
                 n_unknowns=i.n_unknowns,
                 L=list(i.L[:n]), K=list(i.K[:n]), n_box=list(i.n_box[:n]), n_il=list(i.n_il[:n]),
                 n_near_pairs=i.n_near_pairs, n_near_blocks=i.n_near_blocks,
-                device_bytes=i.device_bytes)
+                device_bytes=i.device_bytes, column_lanes=i.column_lanes)
 
 
 def smr_rhs_plane_waves(ctx, khat, pol, b, stream=None):
@@ -332,8 +334,8 @@ def smr_set_tensor_cores(ctx, enable):
     _check(ctx, lib().smr_set_tensor_cores(ctx, 1 if enable else 0))
 
 
-def smr_autotune(ctx, precision=SMR_PREC_FP32, stream=None):
-    _check(ctx, lib().smr_autotune(ctx, 1, precision, _stream(stream, None)))
+def smr_autotune(ctx, precision=SMR_PREC_FP32, stream=None, R=1):
+    _check(ctx, lib().smr_autotune(ctx, int(R), precision, _stream(stream, None)))
 
 
 def smr_sync(ctx, stream=None):
@@ -351,6 +353,11 @@ def smr_set_variant(ctx, step, level, precision, variant):
 def smr_set_wait_limit(ctx, rounds):
     """Polling limit of the tensor-core pipeline waits; rounds < 0 restores the default."""
     _check(ctx, lib().smr_set_wait_limit(ctx, int(rounds)))
+
+
+def smr_set_column_lanes(ctx, lanes):
+    """Columns in flight in an FP32 product with several right-hand sides (1..16)."""
+    _check(ctx, lib().smr_set_column_lanes(ctx, int(lanes)))
 
 
 def smr_far_field(ctx, x, dirs, F, R=None, stream=None):

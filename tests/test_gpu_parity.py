@@ -427,6 +427,36 @@ def test_invalid_arguments(c1):
     smr.smr_destroy(ctx)
 
 
+def test_column_lanes_are_bit_identical(rnd):
+    """FP32 products with R > 1 deal their columns to lanes with their own
+    buffers and streams: any lane count gives bit for bit the product of one
+    lane (the same kernels on the same data), directly and through a graph,
+    and the lane count is checked."""
+    n = rnd.info["n_unknowns"]
+    R = 7
+    x = np.stack([crandn(n, 90 + r) for r in range(R)], axis=1).reshape(-1)
+    xd = torch.from_numpy(x).cuda()
+    ref, y = torch.empty_like(xd), torch.empty_like(xd)
+    try:
+        smr.smr_set_column_lanes(rnd.ctx, 1)
+        smr.smr_matvec(rnd.ctx, xd, ref, smr.SMR_PREC_FP32, R=R)
+        torch.cuda.synchronize()
+        for nl in (2, 3, 4, 16):
+            smr.smr_set_column_lanes(rnd.ctx, nl)
+            for graph in (False, True):
+                for _ in range(2):
+                    y.fill_(float("nan"))
+                    f = smr.smr_matvec_graph if graph else smr.smr_matvec
+                    f(rnd.ctx, xd, y, smr.SMR_PREC_FP32, R=R)
+                    torch.cuda.synchronize()
+                    assert torch.equal(y, ref), (nl, graph)
+        for bad in (0, 17):
+            with pytest.raises(smr.SmrError):
+                smr.smr_set_column_lanes(rnd.ctx, bad)
+    finally:
+        smr.smr_set_column_lanes(rnd.ctx, 4)
+
+
 def test_graph_product_matches_direct(c1, rnd):
     """The CUDA-graph replay launches the same kernels: bit-identical to
     smr_matvec, also on repeated replays and after a change of R."""
