@@ -107,12 +107,58 @@ int smr_add_sphere(smr_ctx* ctx, double radius, int n_perp, int n_par, int* shap
  *                 unknown vector.
  * Patterns (Eq. 26), neighbour blocks, right-hand sides and fields are then
  * computed from these samples exactly as for the closed-form spheres.
- * 1 <= n_q <= 1024; all shapes of a context share n_psi.  The bounding radius
- * of the points must stay below half the pitch.  Must precede smr_set_scene.
- * The paper assembles these data from a surface mesh; there is no separate
- * counterpart call. */
+ * 1 <= n_q <= 8192; all shapes of a context share n_psi.  The points' largest
+ * distance from the z axis must stay below half the pitch.  Must precede
+ * smr_set_scene.  smr_add_shape_mesh produces these data from a mesh. */
 int smr_add_shape_sampled(smr_ctx* ctx, int n_q, const double* pts, const double* wts, int n_perp, int n_par,
                           const double* modes, const double* self_block, int* shape_id);
+
+/* Register a shape given by a closed triangle mesh (Sec. III and Sec. V,
+ * stages i, ii and iv), host inputs, copied:
+ *   verts[nv][3]   vertex positions relative to the particle centre
+ *   tris[nt][3]    vertex indices, counter-clockwise seen from outside
+ * The mesh must be a closed, consistently oriented, genus-0 surface with
+ * outward normals (else SMR_E_SHAPE), 4 <= nt <= 1800.  RWG functions live
+ * on its edges (edge = vertex pair (i, j), i < j, edges in lexicographic
+ * order; the current flows out of the triangle whose vertex cycle runs
+ * i -> j).  On the host in FP64 the call solves the two static eigenproblems
+ * of Sec. III (Eqs. 21-25) in Galerkin form: the electrostatic one in star
+ * functions, A_par v = gamma G v with A_par = <div s, g0 div' s'>, and the
+ * magnetostatic one in loop functions, A_perp = <l, g0 l'>, G the Gram
+ * matrix, g0 = 1/(4 pi R); inner integrals over each source triangle in
+ * closed form, outer integrals by Radon's 7-point degree-5 rule, symmetric
+ * parts diagonalised.  It keeps the n_perp largest gamma_perp and the n_par
+ * smallest gamma_par (Sec. III), modes normalised to <psi, psi> = 1 with
+ * their largest RWG coefficient positive, transverse modes first.  The
+ * solver sees the modes sampled at a 3-point degree-2 rule on every
+ * triangle (n_q = 3 nt points, as smr_add_shape_sampled).  smr_set_scene
+ * computes the self block for the scene's media on the GPU in FP64: the
+ * PMCHWT operators of both media on the modes, the 1/R and grad(1/R) parts
+ * of the inner integrals in closed form (Sec. IV: Graglia 1993, Hodges 1997),
+ * the remainders and the outer integrals by the 7-point rule, the K
+ * operator as a principal value.  Must precede smr_set_scene.  The particle's
+ * largest distance from the z axis must stay below half the pitch. */
+int smr_add_shape_mesh(smr_ctx* ctx, int nv, const double* verts, int nt, const int* tris, int n_perp,
+                       int n_par, int* shape_id);
+
+/* The static modes of a meshed shape: *n_psi and *n_edges (each if
+ * non-NULL) receive the mode count and the RWG count n_e, M (if non-NULL)
+ * the mode -> RWG matrix of Eq. 20
+ * [n_psi][n_e] (psi_i = sum_e M[i][e] f_e), gamma (if non-NULL) the kept
+ * eigenvalues [n_psi] (transverse first).  SMR_E_INVALID_ARG for a shape
+ * that is not meshed. */
+int smr_shape_modes(smr_ctx* ctx, int shape_id, int* n_psi, int* n_edges, double* M, double* gamma);
+
+/* The self block Z_s (Eq. 16 with mu = nu) that the current scene uses for
+ * a shape: host Z[2 n_psi][2 n_psi] complex (re, im interleaved),
+ * row-major.  Needs smr_set_scene. */
+int smr_self_block(smr_ctx* ctx, int shape_id, double* Z);
+
+/* The static-mode solve of smr_add_shape_mesh alone, on the host (no
+ * context, no GPU): same inputs and outputs as smr_add_shape_mesh followed
+ * by smr_shape_modes.  SMR_E_SHAPE for a mesh it rejects. */
+int smr_mesh_static_modes(int nv, const double* verts, int nt, const int* tris, int n_perp, int n_par,
+                          int* n_edges, double* M, double* gamma);
 
 /* Set the scene: p particles with host centres[p][3] and host shape_ids[p],
  * inner medium (eps_in, mu_in) and background (eps_out, mu_out), each a

@@ -574,9 +574,11 @@ int set_scene(Ctx* c, int p, const double* centres, const int* shape_ids, const 
     if (!idx0.emplace(std::make_pair(c->pi[i], c->pj[i]), i).second)
       return fail(c, SMR_E_INVALID_ARG, "two particles share a lattice cell");
   }
-  // check no sphere overlaps its neighbours on the lattice
+  // check no particle overlaps its neighbours on the lattice (the particles
+  // share one plane, so their extent across the z axis decides)
   for (auto& s : c->shapes)
-    if (2 * s.a >= pitch) return fail(c, SMR_E_INVALID_ARG, "particle diameter must be below the pitch");
+    if (2 * (s.sampled ? s.lateral : s.a) >= pitch)
+      return fail(c, SMR_E_INVALID_ARG, "particle width must be below the pitch");
   c->any_dshift = anyd;
   // ---- levels
   std::vector<int> bi(c->pi), bj(c->pj);
@@ -938,8 +940,8 @@ int smr_add_shape_sampled(smr_ctx* h, int n_q, const double* pts, const double* 
                           const double* modes, const double* self_block, int* shape_id) {
   if (!h) return SMR_E_INVALID_ARG;
   Ctx* c = &h->c;
-  if (!pts || !wts || !modes || !self_block || n_q < 1 || n_q > 1024)
-    return fail(c, SMR_E_INVALID_ARG, "1 <= n_q <= 1024 and non-null points, weights, modes, self block required");
+  if (!pts || !wts || !modes || !self_block || n_q < 1 || n_q > 8192)
+    return fail(c, SMR_E_INVALID_ARG, "1 <= n_q <= 8192 and non-null points, weights, modes, self block required");
   if (n_perp < 0 || n_par < 0 || n_perp + n_par < 1 || n_perp + n_par > 128)
     return fail(c, SMR_E_INVALID_ARG, "1 <= n_perp + n_par <= 128 required");
   Shape sh;
@@ -963,6 +965,8 @@ int smr_add_shape_sampled(smr_ctx* h, int n_q, const double* pts, const double* 
     rmax = std::max(rmax, std::sqrt(r2));
   }
   sh.a = rmax;
+  for (int q = 0; q < n_q; ++q)
+    sh.lateral = std::max(sh.lateral, std::hypot(sh.rq[4 * q], sh.rq[4 * q + 1]));
   sh.modes.assign(modes, modes + (size_t)n * n_q * 4);
   for (double v : sh.modes)
     if (!std::isfinite(v)) return fail(c, SMR_E_INVALID_ARG, "non-finite mode sample");
@@ -974,6 +978,75 @@ int smr_add_shape_sampled(smr_ctx* h, int n_q, const double* pts, const double* 
   }
   c->shapes.push_back(std::move(sh));
   if (shape_id) *shape_id = (int)c->shapes.size() - 1;
+  return SMR_OK;
+}
+
+int smr_add_shape_mesh(smr_ctx* h, int nv, const double* verts, int nt, const int* tris, int n_perp, int n_par,
+                       int* shape_id) {
+  if (!h) return SMR_E_INVALID_ARG;
+  Ctx* c = &h->c;
+  if (!verts || !tris || nv < 4 || nt < 4 || nt > 1800)
+    return fail(c, SMR_E_INVALID_ARG, "non-null vertices and triangles, nv >= 4, 4 <= nt <= 1800 required");
+  if (n_perp < 0 || n_par < 0 || n_perp + n_par < 1 || n_perp + n_par > 128)
+    return fail(c, SMR_E_INVALID_ARG, "1 <= n_perp + n_par <= 128 required");
+  Shape sh;
+  sh.n_perp = n_perp;
+  sh.n_par = n_par;
+  int rc = mesh_static_modes(c, nv, verts, nt, tris, n_perp, n_par, sh.mm);
+  if (rc) return rc;
+  sh.sampled = true;
+  sh.mesh = true;
+  sh.nq = sh.mm.nq;
+  sh.rq = sh.mm.rq;
+  sh.modes = sh.mm.modes;
+  sh.a = 0;
+  for (int v = 0; v < nv; ++v) {
+    const double* x = verts + 3 * v;
+    sh.a = std::max(sh.a, std::sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]));
+    sh.lateral = std::max(sh.lateral, std::hypot(x[0], x[1]));
+  }
+  c->shapes.push_back(std::move(sh));
+  if (shape_id) *shape_id = (int)c->shapes.size() - 1;
+  return SMR_OK;
+}
+
+int smr_shape_modes(smr_ctx* h, int shape_id, int* n_psi, int* n_edges, double* M, double* gamma) {
+  if (!h) return SMR_E_INVALID_ARG;
+  Ctx* c = &h->c;
+  if (shape_id < 0 || shape_id >= (int)c->shapes.size() || !c->shapes[shape_id].mesh)
+    return fail(c, SMR_E_INVALID_ARG, "not the id of a meshed shape");
+  const Shape& sh = c->shapes[shape_id];
+  if (n_psi) *n_psi = sh.n_psi();
+  if (n_edges) *n_edges = sh.mm.ne;
+  if (M) std::copy(sh.mm.M.begin(), sh.mm.M.end(), M);
+  if (gamma) std::copy(sh.mm.gamma.begin(), sh.mm.gamma.end(), gamma);
+  return SMR_OK;
+}
+
+int smr_self_block(smr_ctx* h, int shape_id, double* Z) {
+  if (!h || !Z) return SMR_E_INVALID_ARG;
+  Ctx* c = &h->c;
+  if (!check_scene(c)) return SMR_E_STATE;
+  if (shape_id < 0 || shape_id >= (int)c->shapes.size()) return fail(c, SMR_E_INVALID_ARG, "shape id out of range");
+  const std::vector<cd>& z = c->shapes[shape_id].Z;
+  for (size_t i = 0; i < z.size(); ++i) {
+    Z[2 * i] = z[i].real();
+    Z[2 * i + 1] = z[i].imag();
+  }
+  return SMR_OK;
+}
+
+int smr_mesh_static_modes(int nv, const double* verts, int nt, const int* tris, int n_perp, int n_par,
+                          int* n_edges, double* M, double* gamma) {
+  if (!verts || !tris || nv < 4 || nt < 4 || nt > 1800 || n_perp < 0 || n_par < 0 || n_perp + n_par < 1)
+    return SMR_E_INVALID_ARG;
+  Ctx tmp;
+  MeshModes mm;
+  int rc = mesh_static_modes(&tmp, nv, verts, nt, tris, n_perp, n_par, mm);
+  if (rc) return rc;
+  if (n_edges) *n_edges = mm.ne;
+  if (M) std::copy(mm.M.begin(), mm.M.end(), M);
+  if (gamma) std::copy(mm.gamma.begin(), mm.gamma.end(), gamma);
   return SMR_OK;
 }
 

@@ -364,8 +364,15 @@ int build_near(Ctx* c) {
   c->pinv_ok = true;
   for (int s = 0; s < S; ++s) {
     std::vector<cd> Z;
-    if (c->shapes[s].sampled) Z = c->shapes[s].Z;
-    else sphere_self_block(c->shapes[s], c->k, c->zeta, c->k_in, c->zeta_in, Z);
+    if (c->shapes[s].mesh) {
+      int rc = mesh_self_block(c, c->shapes[s], Z);
+      if (rc) return rc;
+    } else if (c->shapes[s].sampled) {
+      Z = c->shapes[s].Z;
+    } else {
+      sphere_self_block(c->shapes[s], c->k, c->zeta, c->k_in, c->zeta_in, Z);
+    }
+    c->shapes[s].Z = Z;                        // the block in use (smr_self_block)
     std::vector<cd> Zi = Z;
     if (!hm::invert(n2, Zi)) {
       // a singular self block (possible only for shapes given as data)
@@ -701,18 +708,24 @@ int launch_cross_sections(Ctx* c, int R, const double2* x, int n_sca, const doub
 // CTA per particle mu (and right-hand side r): currents at the quadrature
 // points staged in shared memory; threads stride over field points and add
 // their particle's contribution with atomics.
-__global__ void k_nearfield(int p, int npsi, int Q, int npt, int R, const int* __restrict__ sid,
+// One block per (particle, right-hand side, chunk of at most QC surface
+// points): the chunk's currents staged in shared memory, every field point
+// accumulated over them (chunks of one particle add atomically).
+__global__ void k_nearfield(int p, int npsi, int Q, int QC, int npt, int R, const int* __restrict__ sid,
                             const double* __restrict__ cen, const double* __restrict__ modes,
                             const double* __restrict__ rq, const double2* __restrict__ x,
                             const double* __restrict__ pts, double kw, double zeta,
                             double* __restrict__ EH) {
-  extern __shared__ double sm[];   // [Q][8 complex] J xyz, divJ, M xyz, divM  + [Q][4] point
-  int mu = blockIdx.x / R, r = blockIdx.x % R;
+  extern __shared__ double sm[];   // [QC][8 complex] J xyz, divJ, M xyz, divM  + [QC][4] point
+  const int nch = (Q + QC - 1) / QC;
+  const int ch = blockIdx.x % nch, br = blockIdx.x / nch;
+  int mu = br / R, r = br % R;
   int s = sid[mu];
+  const int q0 = ch * QC, nq = min(QC, Q - q0);
   double2* cur = reinterpret_cast<double2*>(sm);
-  double* pq = sm + (size_t)Q * 16;
-  const double* Ms = modes + (size_t)s * npsi * Q * 4;
-  for (int q = threadIdx.x; q < Q; q += blockDim.x) {
+  double* pq = sm + (size_t)QC * 16;
+  const double* Ms = modes + (size_t)s * npsi * Q * 4 + (size_t)q0 * 4;
+  for (int q = threadIdx.x; q < nq; q += blockDim.x) {
     double2 a[8];
     for (int i = 0; i < 8; ++i) a[i] = make_double2(0, 0);
     for (int n = 0; n < npsi; ++n) {
@@ -725,7 +738,7 @@ __global__ void k_nearfield(int p, int npsi, int Q, int npt, int R, const int* _
       }
     }
     for (int i = 0; i < 8; ++i) cur[(size_t)q * 8 + i] = a[i];
-    const double* rr = rq + ((size_t)s * Q + q) * 4;
+    const double* rr = rq + ((size_t)s * Q + q0 + q) * 4;
     pq[4 * q] = rr[0] + cen[3 * mu];
     pq[4 * q + 1] = rr[1] + cen[3 * mu + 1];
     pq[4 * q + 2] = rr[2] + cen[3 * mu + 2];
@@ -736,7 +749,7 @@ __global__ void k_nearfield(int p, int npsi, int Q, int npt, int R, const int* _
     double P[3] = {pts[3 * ip], pts[3 * ip + 1], pts[3 * ip + 2]};
     double2 E[3], H[3];
     for (int i = 0; i < 3; ++i) { E[i] = make_double2(0, 0); H[i] = make_double2(0, 0); }
-    for (int q = 0; q < Q; ++q) {
+    for (int q = 0; q < nq; ++q) {
       double d[3] = {P[0] - pq[4 * q], P[1] - pq[4 * q + 1], P[2] - pq[4 * q + 2]};
       double R2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
       double Rr = sqrt(R2), iR = 1.0 / Rr;
@@ -793,11 +806,13 @@ __global__ void k_nearfield(int p, int npsi, int Q, int npt, int R, const int* _
 int launch_near_field(Ctx* c, int R, const double2* x, int npt, const double* d_pts, double2* EH,
                       cudaStream_t st) {
   SMR_CUDA(c, cudaMemsetAsync(EH, 0, (size_t)npt * 6 * R * sizeof(double2), st));
-  size_t sm = (size_t)c->Q * (16 + 4) * sizeof(double);
+  const int QC = std::min(c->Q, 1024);
+  const int nch = (c->Q + QC - 1) / QC;
+  size_t sm = (size_t)QC * (16 + 4) * sizeof(double);
   SMR_CUDA(c, cudaFuncSetAttribute(k_nearfield, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-  k_nearfield<<<(unsigned)(c->p * R), 256, sm, st>>>(c->p, c->npsi, c->Q, npt, R, c->d_sid, c->d_centres,
-                                                     c->d_modes, c->d_rq, x, d_pts, c->k, c->zeta,
-                                                     (double*)EH);
+  k_nearfield<<<(unsigned)(c->p * R * nch), 256, sm, st>>>(c->p, c->npsi, c->Q, QC, npt, R, c->d_sid,
+                                                           c->d_centres, c->d_modes, c->d_rq, x, d_pts, c->k,
+                                                           c->zeta, (double*)EH);
   SMR_LAUNCH(c);
   return SMR_OK;
 }

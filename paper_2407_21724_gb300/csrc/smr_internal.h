@@ -34,6 +34,19 @@ void mode_list(int n, std::vector<int>& l, std::vector<int>& m, std::vector<int>
 }  // namespace hm
 
 // ------------------------------------------------------------------ data
+// Static modes of a meshed shape (smr_add_shape_mesh): the mode -> RWG
+// matrix of Eq. 20, the kept eigenvalues, the geometry, per triangle and
+// mode the affine field psi = alpha r - beta ([nt][n_psi][alpha, beta xyz]),
+// and the 3-point samples handed to the solver like a sampled shape.
+struct MeshModes {
+  int ne = 0, nt = 0, nq = 0;
+  std::vector<double> M, gamma;
+  std::vector<double> geo_V;
+  std::vector<int> geo_T;
+  std::vector<double> area, nrm, ab;
+  std::vector<double> rq, modes;
+};
+
 struct Shape {
   double a;                               // sphere radius, or bounding radius of a sampled shape
   int n_perp, n_par;
@@ -44,6 +57,10 @@ struct Shape {
   int nq = 0;
   std::vector<double> rq, modes;
   std::vector<cd> Z;
+  // meshed shape: the self block is assembled for the scene's media
+  bool mesh = false;
+  MeshModes mm;
+  double lateral = 0;                     // largest distance of a point from the z axis
 };
 
 struct Level {
@@ -408,6 +425,10 @@ int run_matvec_graph(Ctx* c, int R, int prec, const double2* x, double2* y, cuda
 // y = Z x (near + far); FP32 with R > 1 runs column by column (split products)
 int run_product(Ctx* c, int R, int prec, const double2* x, double2* y, cudaStream_t st);
 void free_graphs(Ctx* c);
+// meshed shapes (mesh.cu)
+int mesh_static_modes(Ctx* c, int nv, const double* verts, int nt, const int* tris, int n_perp, int n_par,
+                      MeshModes& out);
+int mesh_self_block(Ctx* c, const Shape& sh, std::vector<cd>& Z);
 // column lanes of split FP32 products (buffers allocated outside graph capture)
 int ensure_lanes(Ctx* c, int nl);
 void free_lanes(Ctx* c);

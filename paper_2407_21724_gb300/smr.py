@@ -19,7 +19,7 @@ _lib = None
 SMR_PREC_FP64, SMR_PREC_FP32 = 0, 1
 SMR_LRULE_FORMULA, SMR_LRULE_DOUBLE = 0, 1
 SMR_PRECOND_NONE, SMR_PRECOND_BLOCKDIAG, SMR_PRECOND_LEARNED = 0, 1, 2
-SMR_OK, SMR_E_NOT_CONVERGED = 0, -5
+SMR_OK, SMR_E_SHAPE, SMR_E_NOT_CONVERGED = 0, -2, -5
 SMR_E_BREAKDOWN, SMR_E_TIMEOUT = -6, -8
 ERRORS = {-1: "INVALID_ARG", -2: "SHAPE", -3: "OOM", -4: "CUDA", -5: "NOT_CONVERGED",
           -6: "BREAKDOWN", -7: "NAN", -8: "TIMEOUT", -9: "STATE"}
@@ -108,6 +108,12 @@ _SIGS = {
     "smr_copy_level": (C.c_int, [_P, C.c_int, C.c_int, _D, C.c_size_t]),
     "smr_set_tensor_cores": (C.c_int, [_P, C.c_int]),
     "smr_add_shape_sampled": (C.c_int, [_P, C.c_int, _D, _D, C.c_int, C.c_int, _D, _D, C.POINTER(C.c_int)]),
+    "smr_add_shape_mesh": (C.c_int, [_P, C.c_int, _D, C.c_int, C.POINTER(C.c_int), C.c_int, C.c_int,
+                                     C.POINTER(C.c_int)]),
+    "smr_shape_modes": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), _D, _D]),
+    "smr_self_block": (C.c_int, [_P, C.c_int, _D]),
+    "smr_mesh_static_modes": (C.c_int, [C.c_int, _D, C.c_int, C.POINTER(C.c_int), C.c_int, C.c_int,
+                                        C.POINTER(C.c_int), _D, _D]),
     "smr_nn_precond": (C.c_int, [_P, _D, _D, C.c_double, _P, _P]),
     "smr_autotune": (C.c_int, [_P, C.c_int, C.c_int, _P]),
     "smr_sync": (C.c_int, [_P, _P]),
@@ -511,9 +517,12 @@ def smr_copy_level(ctx, level, kind, R=1):
 
 def add_shapes(ctx, shapes):
     """Register shapes: (radius, n_perp, n_par) tuples are closed-form spheres;
+    dicts with kind 'mesh' (verts, tris, n_perp, n_par) are meshed shapes;
     objects with r, w, psi, div, Zs, n_perp, n_par are shapes given as data."""
     for sh in shapes:
-        if hasattr(sh, "psi"):
+        if isinstance(sh, dict) and sh.get("kind") == "mesh":
+            smr_add_shape_mesh(ctx, sh["verts"], sh["tris"], sh["n_perp"], sh["n_par"])
+        elif hasattr(sh, "psi"):
             smr_add_shape_sampled(ctx, sh.r, sh.w, sh.n_perp, sh.n_par, sh.psi, sh.div, sh.Zs)
         else:
             a, npp, npl = sh
@@ -532,6 +541,54 @@ def smr_add_shape_sampled(ctx, pts, wts, n_perp, n_par, psi, div, self_block):
     _check(ctx, lib().smr_add_shape_sampled(ctx, P.shape[0], _dptr(P), _dptr(W), n_perp, n_par, _dptr(M),
                                             _dptr(Z.view(np.float64)), C.byref(sid)))
     return sid.value
+
+
+def _mesh_args(verts, tris):
+    V = np.ascontiguousarray(verts, dtype=np.float64).reshape(-1, 3)
+    T = np.ascontiguousarray(tris, dtype=np.int32).reshape(-1, 3)
+    return V, T, T.ctypes.data_as(C.POINTER(C.c_int))
+
+
+def smr_add_shape_mesh(ctx, verts, tris, n_perp, n_par):
+    """verts (nv,3), tris (nt,3) outward; returns the shape id."""
+    V, T, tp = _mesh_args(verts, tris)
+    sid = C.c_int()
+    _check(ctx, lib().smr_add_shape_mesh(ctx, V.shape[0], _dptr(V), T.shape[0], tp, n_perp, n_par,
+                                         C.byref(sid)))
+    return sid.value
+
+
+def smr_shape_modes(ctx, shape_id):
+    """(M [n_psi][n_edges], gamma [n_psi]) of a meshed shape."""
+    n, ne = C.c_int(), C.c_int()
+    _check(ctx, lib().smr_shape_modes(ctx, shape_id, C.byref(n), C.byref(ne), None, None))
+    M = np.empty((n.value, ne.value))
+    g = np.empty(n.value)
+    _check(ctx, lib().smr_shape_modes(ctx, shape_id, None, None, _dptr(M), _dptr(g)))
+    return M, g
+
+
+def smr_self_block(ctx, shape_id):
+    """The self block (2 n_psi, 2 n_psi) complex the scene uses for a shape."""
+    n2 = 2 * smr_info(ctx)["n_psi"]
+    Z = np.empty((n2, n2), dtype=np.complex128)
+    _check(ctx, lib().smr_self_block(ctx, shape_id, _dptr(Z.view(np.float64))))
+    return Z
+
+
+def smr_mesh_static_modes(verts, tris, n_perp, n_par):
+    """Host static-mode solve of a mesh: (M [n_psi][n_edges], gamma [n_psi])."""
+    V, T, tp = _mesh_args(verts, tris)
+    ne = C.c_int()
+    n = n_perp + n_par
+    # edges of a closed genus-0 mesh: 3 nt / 2
+    M = np.empty((n, 3 * T.shape[0] // 2))
+    g = np.empty(n)
+    rc = lib().smr_mesh_static_modes(V.shape[0], _dptr(V), T.shape[0], tp, n_perp, n_par, C.byref(ne),
+                                     _dptr(M), _dptr(g))
+    if rc != 0:
+        raise SmrError(rc, "smr_mesh_static_modes rejected the mesh or the mode counts")
+    return M[:, :ne.value], g
 
 
 def scene_from_workload(w, **opts):

@@ -106,6 +106,82 @@ def make(name, **kw):
     raise KeyError(name)
 
 
+def _orient_outward(V, T):
+    """Order each triangle's vertices so that its normal points away from the
+    origin (the meshes below are star-shaped about it)."""
+    T = T.copy()
+    p0, p1, p2 = V[T[:, 0]], V[T[:, 1]], V[T[:, 2]]
+    n = np.cross(p1 - p0, p2 - p0)
+    flip = np.sum(n * (p0 + p1 + p2), axis=1) < 0
+    T[flip, 1], T[flip, 2] = T[flip, 2].copy(), T[flip, 1].copy()
+    return T
+
+
+def icosphere(radius, level):
+    """Closed triangle mesh of a sphere: the icosahedron with every triangle
+    split into four `level` times, vertices pushed onto the sphere.  Returns
+    (verts (nv,3) float64, tris (nt,3) int32), nt = 20 * 4**level, outward
+    vertex order."""
+    g = (1.0 + np.sqrt(5.0)) / 2.0
+    V = [(-1, g, 0), (1, g, 0), (-1, -g, 0), (1, -g, 0), (0, -1, g), (0, 1, g),
+         (0, -1, -g), (0, 1, -g), (g, 0, -1), (g, 0, 1), (-g, 0, -1), (-g, 0, 1)]
+    T = [(0, 11, 5), (0, 5, 1), (0, 1, 7), (0, 7, 10), (0, 10, 11), (1, 5, 9), (5, 11, 4),
+         (11, 10, 2), (10, 7, 6), (7, 1, 8), (3, 9, 4), (3, 4, 2), (3, 2, 6), (3, 6, 8),
+         (3, 8, 9), (4, 9, 5), (2, 4, 11), (6, 2, 10), (8, 6, 7), (9, 8, 1)]
+    V = [np.array(v, dtype=float) / np.linalg.norm(v) for v in V]
+    for _ in range(level):
+        mid = {}
+
+        def m(a, b):
+            key = (min(a, b), max(a, b))
+            if key not in mid:
+                v = V[a] + V[b]
+                V.append(v / np.linalg.norm(v))
+                mid[key] = len(V) - 1
+            return mid[key]
+        T = [t for (a, b, c) in T for t in
+             ((a, m(a, b), m(c, a)), (b, m(b, c), m(a, b)), (c, m(c, a), m(b, c)),
+              (m(a, b), m(b, c), m(c, a)))]
+    V = radius * np.array(V)
+    return V, _orient_outward(V, np.array(T, dtype=np.int32))
+
+
+def cylinder_mesh(radius, height, n_phi=20, n_z=10, n_r=3):
+    """Closed triangle mesh of a circular cylinder (a nanopillar) centred at
+    the origin, axis z: n_z rows of n_phi quads (two triangles each) on the
+    side, and on each cap a centre fan inside n_r - 1 rings.  600 triangles,
+    302 vertices and 900 edges at the defaults.  Returns (verts, tris) with
+    outward vertex order."""
+    ang = 2.0 * np.pi * np.arange(n_phi) / n_phi
+    ring = np.stack([np.cos(ang), np.sin(ang)], axis=1)
+    V, T = [], []
+
+    def add_ring(r, z):
+        base = len(V)
+        V.extend(np.column_stack([r * ring, np.full(n_phi, z)]))
+        return base
+
+    side = [add_ring(radius, -height / 2 + height * k / n_z) for k in range(n_z + 1)]
+    for k in range(n_z):
+        a, b = side[k], side[k + 1]
+        for j in range(n_phi):
+            j1 = (j + 1) % n_phi
+            T += [(a + j, a + j1, b + j1), (a + j, b + j1, b + j)]
+    for z, outer in ((height / 2, side[-1]), (-height / 2, side[0])):
+        rings = [add_ring(radius * i / n_r, z) for i in range(1, n_r)] + [outer]
+        centre = len(V)
+        V.append(np.array([0.0, 0.0, z]))
+        for j in range(n_phi):
+            T.append((centre, rings[0] + j, rings[0] + (j + 1) % n_phi))
+        for i in range(n_r - 1):
+            a, b = rings[i], rings[i + 1]
+            for j in range(n_phi):
+                j1 = (j + 1) % n_phi
+                T += [(a + j, b + j, b + j1), (a + j, b + j1, a + j1)]
+    V = np.array(V, dtype=float)
+    return V, _orient_outward(V, np.array(T, dtype=np.int32))
+
+
 def mlp_params(dims, seed):
     """Seeded MLP parameters (layer by layer, W [in][out] then b) whose values
     are exactly representable in bfloat16 (the top 16 bits of a float32)."""
