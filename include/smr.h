@@ -137,7 +137,9 @@ int smr_add_shape_sampled(smr_ctx* ctx, int n_q, const double* pts, const double
  * of the inner integrals in closed form (Sec. IV: Graglia 1993, Hodges 1997),
  * the remainders and the outer integrals by the 7-point rule, the K
  * operator as a principal value.  Must precede smr_set_scene.  The particle's
- * largest distance from the z axis must stay below half the pitch. */
+ * largest distance from the z axis must stay below half the pitch.  The
+ * modes depend on the shape alone: the library keeps the last 32 solves of
+ * the process and reuses one for an identical mesh and mode counts. */
 int smr_add_shape_mesh(smr_ctx* ctx, int nv, const double* verts, int nt, const int* tris, int n_perp,
                        int n_par, int* shape_id);
 

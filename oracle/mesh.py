@@ -360,3 +360,22 @@ class MeshModes:
         psi, div, r = self.fields(TRI3_B)
         w = np.repeat(self.mesh.area, 3) / 3.0
         return SampledShape(r, w, psi, div, self.self_block(outer, inner), self.n_perp, self.n_par)
+
+
+def _sampled_task(args):
+    spec, eps_out, eps_in = args
+    from .pmchwt import Medium
+    mm = MeshModes(Mesh(spec['verts'], spec['tris']), spec['n_perp'], spec['n_par'])
+    return mm.sampled(Medium(eps_out), Medium(eps_in))
+
+
+def sampled_shapes(specs, eps_in, eps_out=1.0, workers=1):
+    """``MeshModes.sampled`` of several mesh specs (dicts with verts, tris,
+    n_perp, n_par) for real media, in a pool of spawned processes when
+    workers > 1 (each shape independent)."""
+    jobs = [(s, eps_out, eps_in) for s in specs]
+    if workers <= 1 or len(jobs) <= 1:
+        return [_sampled_task(j) for j in jobs]
+    import multiprocessing as mp
+    with mp.get_context('spawn').Pool(min(workers, len(jobs))) as pool:
+        return pool.map(_sampled_task, jobs)

@@ -70,14 +70,25 @@ class Scene:
                  mu_in=1.0, mu_out=1.0, lam=1.0, n_theta=16, n_phi=32):
         self.centres = np.asarray(centres, dtype=float).reshape(-1, 3)
         self.shape_ids = np.asarray(shape_ids, dtype=int).ravel()
-        self.shapes = [s if isinstance(s, (SphereShape, SampledShape)) else SphereShape(*s) for s in shapes]
         self.inner = Medium(eps_in, mu_in, lam)
         self.outer = Medium(eps_out, mu_out, lam)
+        self.shapes = [self._shape(s) for s in shapes]
         self.n_theta, self.n_phi = n_theta, n_phi
         npsi = {s.n_psi for s in self.shapes}
         assert len(npsi) == 1, "all shapes share one mode count"
         self.n_psi = npsi.pop()
         self._rules = {}
+
+    def _shape(self, s):
+        """Closed-form spheres from (radius, n_perp, n_par); meshed shapes
+        from dicts with kind 'mesh' (verts, tris, n_perp, n_par), their modes
+        and self block computed here (``oracle.mesh``)."""
+        if isinstance(s, (SphereShape, SampledShape)):
+            return s
+        if isinstance(s, dict) and s.get('kind') == 'mesh':
+            from .mesh import Mesh, MeshModes
+            return MeshModes(Mesh(s['verts'], s['tris']), s['n_perp'], s['n_par']).sampled(self.outer, self.inner)
+        return SphereShape(*s)
 
     @property
     def p(self):

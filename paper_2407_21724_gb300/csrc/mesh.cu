@@ -34,6 +34,7 @@
 #include <algorithm>
 #include <cmath>
 #include <map>
+#include <mutex>
 #include <thread>
 
 #include "smr_internal.h"
@@ -473,8 +474,45 @@ bool sym_gen_eig(int n, std::vector<double> A, std::vector<double> B, std::vecto
 }  // namespace
 
 // ---------------------------------------------------------------- static modes
+namespace {
+// Modes depend on the shape only (Sec. III): the last solves of this process
+// are kept and reused for an identical mesh and mode counts.
+struct ModeCacheEntry {
+  std::vector<double> V;
+  std::vector<int> T;
+  int n_perp, n_par;
+  MeshModes mm;
+};
+std::mutex g_mode_mu;
+std::vector<ModeCacheEntry> g_mode_cache;
+const size_t MODE_CACHE_MAX = 32;
+}  // namespace
+
+static int mesh_static_modes_solve(Ctx* c, int nv, const double* verts, int nt, const int* tris, int n_perp,
+                                   int n_par, MeshModes& out);
+
 int mesh_static_modes(Ctx* c, int nv, const double* verts, int nt, const int* tris, int n_perp, int n_par,
                       MeshModes& out) {
+  {
+    std::lock_guard<std::mutex> lk(g_mode_mu);
+    for (const ModeCacheEntry& e : g_mode_cache)
+      if (e.n_perp == n_perp && e.n_par == n_par && e.V.size() == 3 * (size_t)nv && e.T.size() == 3 * (size_t)nt &&
+          std::equal(e.V.begin(), e.V.end(), verts) && std::equal(e.T.begin(), e.T.end(), tris)) {
+        out = e.mm;
+        return SMR_OK;
+      }
+  }
+  int rc = mesh_static_modes_solve(c, nv, verts, nt, tris, n_perp, n_par, out);
+  if (rc) return rc;
+  std::lock_guard<std::mutex> lk(g_mode_mu);
+  g_mode_cache.push_back({std::vector<double>(verts, verts + 3 * (size_t)nv),
+                          std::vector<int>(tris, tris + 3 * (size_t)nt), n_perp, n_par, out});
+  if (g_mode_cache.size() > MODE_CACHE_MAX) g_mode_cache.erase(g_mode_cache.begin());
+  return SMR_OK;
+}
+
+static int mesh_static_modes_solve(Ctx* c, int nv, const double* verts, int nt, const int* tris, int n_perp,
+                                   int n_par, MeshModes& out) {
   MeshGeo g;
   int rc = build_geo(c, nv, verts, nt, tris, g);
   if (rc) return rc;

@@ -1,22 +1,40 @@
 """Seeded synthetic metasurface workloads (inputs only, no solver arithmetic).
 
 Both the CUDA path and the FP64 oracle take their scenes from here.  The
-module draws lattices, radii and incidences; it computes nothing of the
-MLFMA-SMR method itself.
+module draws lattices, radii and incidences and builds particle meshes
+(geometry only); it computes nothing of the MLFMA-SMR method itself.
 
-All lengths are in vacuum wavelengths.  The particles are dielectric spheres
-(eps_r = 4, mu_r = 1) in vacuum on a square lattice of pitch 0.5; every
-sphere carries N_perp transverse and N_par longitudinal static modes.  The
-paper's own workloads (gold spheres, bricks, TiO2 nanofins meshed with an
-external mesher) need permittivity tables and meshes that are not available
-here; the radius-quantised sphere lattices below stand in for them with the
-same particle counts, the same 8-shape structure and the same unknown counts.
+All lengths are in vacuum wavelengths.  The particles are dielectric
+(eps_r = 4, mu_r = 1) in vacuum on a square lattice of pitch 0.5, either
+spheres (closed-form static modes) or nanopillars: circular cylinders of
+height 0.6 given as closed 600-triangle meshes, whose static modes the
+solver computes (N_perp transverse and N_par longitudinal per shape).  Radii
+are quantised to 8 values in [0.08, 0.20].  The paper's gold spheres, bricks
+and TiO2 nanofins need permittivity tables and meshers that are not
+available here; these lattices stand in for them with the same particle
+counts, the same 8-shape structure and the same unknown counts.
 """
 import numpy as np
 
 PITCH = 0.5
 EPS_IN = 4.0
 RADII8 = np.linspace(0.08, 0.20, 8)
+PILLAR_HEIGHT = 0.6
+
+
+def pillar(radius, modes, height=PILLAR_HEIGHT):
+    """A nanopillar shape: the 600-triangle cylinder mesh of ``cylinder_mesh``
+    with `modes` transverse and `modes` longitudinal static modes."""
+    V, T = cylinder_mesh(radius, height)
+    return dict(kind='mesh', verts=V, tris=T, n_perp=modes, n_par=modes, radius=float(radius),
+                height=height, label=f'cylinder r={radius:.4f} h={height}, {len(T)} triangles')
+
+
+def shapes8(kind, modes):
+    """The 8 radii of RADII8 as spheres (radius, n_perp, n_par) or pillars."""
+    if kind == 'pillar':
+        return [pillar(r, modes) for r in RADII8]
+    return [(r, modes, modes) for r in RADII8]
 
 
 def lattice(nx, ny, pitch=PITCH):
@@ -66,6 +84,8 @@ def make(name, **kw):
                     centres=C, shape_ids=np.zeros(64, dtype=np.int32),
                     shapes=[(0.15, 12, 12)], eps_in=EPS_IN, pitch=PITCH,
                     incidences=[incidence(0, 0, 'x')])
+    shape = kw.get('shape', 'sphere')
+    what = 'pillars (600-triangle cylinder meshes, h=0.6)' if shape == 'pillar' else 'spheres'
     if name == 'random':
         # n x n lattice, radius index uniform over 8 values from a seed
         n = kw.get('n', 40)
@@ -74,10 +94,10 @@ def make(name, **kw):
         rng = np.random.default_rng(seed)
         ids = rng.integers(0, 8, size=n * n).astype(np.int32)
         inc = kw.get('incidences') or [incidence(0, 0, 'x')]
-        return dict(label=f'{n}x{n} random-radius spheres (8 radii), {2*modes} modes/current, '
+        return dict(label=f'{n}x{n} random-radius {what} (8 radii), {2*modes} modes/current, '
                           f'{n*n*4*modes} unknowns',
                     centres=lattice(n, n), shape_ids=ids,
-                    shapes=[(r, modes, modes) for r in RADII8], eps_in=EPS_IN,
+                    shapes=shapes8(shape, modes), eps_in=EPS_IN,
                     pitch=PITCH, incidences=inc)
     if name == 'metalens':
         # n x n hyperbolic-phase lens, focal length f, radii quantised to 8 bins
@@ -86,15 +106,17 @@ def make(name, **kw):
         modes = kw.get('modes', 16)
         C = lattice(n, n)
         ids = metalens_bins(C, f).astype(np.int32)
-        return dict(label=f'{n}x{n} metalens f={f}, {2*modes} modes/current, {n*n*4*modes} unknowns',
+        return dict(label=f'{n}x{n} metalens of {what}, f={f}, {2*modes} modes/current, '
+                          f'{n*n*4*modes} unknowns',
                     centres=C, shape_ids=ids,
-                    shapes=[(r, modes, modes) for r in RADII8], eps_in=EPS_IN,
+                    shapes=shapes8(shape, modes), eps_in=EPS_IN,
                     pitch=PITCH, incidences=[incidence(0, 0, 'x')], focal=f)
     if name == 'sparse':
         # n x n random-radius lattice thinned to a seeded fraction of its
         # sites: the tree depth and the upper levels' box counts of a full
         # n x n array with few particles
-        w = make('random', n=kw.get('n', 200), seed=kw.get('seed', 21727), modes=kw.get('modes', 16))
+        w = make('random', n=kw.get('n', 200), seed=kw.get('seed', 21727), modes=kw.get('modes', 16),
+                 shape=shape)
         keep = np.random.default_rng(kw.get('seed', 21727) + 1).random(len(w['centres'])) < kw.get('fill', 0.02)
         w['centres'], w['shape_ids'] = w['centres'][keep], w['shape_ids'][keep]
         w['label'] = f"{w['label']} thinned to {int(keep.sum())} sites"
@@ -102,7 +124,7 @@ def make(name, **kw):
     if name == 'ragged16':
         # 16 arrays of n_i = round(10 + 50 i / 15) pillars per side, seeds 21726 + i
         return [make('random', n=int(round(10 + 50 * i / 15)), seed=21726 + i,
-                     modes=kw.get('modes', 16)) for i in range(16)]
+                     modes=kw.get('modes', 16), shape=shape) for i in range(16)]
     raise KeyError(name)
 
 
@@ -195,17 +217,18 @@ def mlp_params(dims, seed):
     return (p.view(np.uint32) & np.uint32(0xFFFF0000)).view(np.float32)
 
 
-def training_arrays(count, n=20, seed0=100000, modes=16):
+def training_arrays(count, n=20, seed0=100000, modes=16, shape='sphere'):
     """Random n x n arrays for the learned initial guess: radius index
     U{0..7} and one incidence per array (theta ~ U[0, 40 deg), phi ~ U[0,
     360 deg), x or y polarisation), array i drawn from seed seed0 + i."""
     out = []
+    shapes = shapes8(shape, modes)
     for i in range(count):
         rng = np.random.default_rng(seed0 + i)
         ids = rng.integers(0, 8, size=n * n).astype(np.int32)
         th, ph = rng.uniform(0.0, 40.0), rng.uniform(0.0, 360.0)
         pol = 'x' if rng.integers(0, 2) == 0 else 'y'
         out.append(dict(label=f'{n}x{n} training array {seed0 + i}', centres=lattice(n, n),
-                        shape_ids=ids, shapes=[(r, modes, modes) for r in RADII8],
+                        shape_ids=ids, shapes=shapes,
                         eps_in=EPS_IN, pitch=PITCH, incidences=[incidence(th, ph, pol)]))
     return out
