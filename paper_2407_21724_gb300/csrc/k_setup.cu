@@ -708,9 +708,11 @@ int launch_cross_sections(Ctx* c, int R, const double2* x, int n_sca, const doub
 // CTA per particle mu (and right-hand side r): currents at the quadrature
 // points staged in shared memory; threads stride over field points and add
 // their particle's contribution with atomics.
-// One block per (particle, right-hand side, chunk of at most QC surface
-// points): the chunk's currents staged in shared memory, every field point
-// accumulated over them (chunks of one particle add atomically).
+// Field points in groups of blockDim (one point per thread, blockIdx.z),
+// one right-hand side per blockIdx.y; the blocks of a group stride over the
+// units (particle, chunk of at most QC surface points): each unit's currents
+// are staged in shared memory and every thread adds their field at its point
+// in registers.  One atomic add per block and field component at the end.
 __global__ void k_nearfield(int p, int npsi, int Q, int QC, int npt, int R, const int* __restrict__ sid,
                             const double* __restrict__ cen, const double* __restrict__ modes,
                             const double* __restrict__ rq, const double2* __restrict__ x,
@@ -718,81 +720,90 @@ __global__ void k_nearfield(int p, int npsi, int Q, int QC, int npt, int R, cons
                             double* __restrict__ EH) {
   extern __shared__ double sm[];   // [QC][8 complex] J xyz, divJ, M xyz, divM  + [QC][4] point
   const int nch = (Q + QC - 1) / QC;
-  const int ch = blockIdx.x % nch, br = blockIdx.x / nch;
-  int mu = br / R, r = br % R;
-  int s = sid[mu];
-  const int q0 = ch * QC, nq = min(QC, Q - q0);
+  const int r = blockIdx.y;
+  const int ip = blockIdx.z * blockDim.x + threadIdx.x;
+  const bool act = ip < npt;
   double2* cur = reinterpret_cast<double2*>(sm);
   double* pq = sm + (size_t)QC * 16;
-  const double* Ms = modes + (size_t)s * npsi * Q * 4 + (size_t)q0 * 4;
-  for (int q = threadIdx.x; q < nq; q += blockDim.x) {
-    double2 a[8];
-    for (int i = 0; i < 8; ++i) a[i] = make_double2(0, 0);
-    for (int n = 0; n < npsi; ++n) {
-      double2 ae = x[((size_t)mu * 2 * npsi + n) * R + r];
-      double2 am = x[((size_t)mu * 2 * npsi + npsi + n) * R + r];
-      const double* m = Ms + ((size_t)n * Q + q) * 4;
-      for (int i = 0; i < 4; ++i) {
-        a[i].x += ae.x * m[i]; a[i].y += ae.y * m[i];
-        a[4 + i].x += am.x * m[i]; a[4 + i].y += am.y * m[i];
+  double P[3] = {0, 0, 0};
+  if (act)
+    for (int d = 0; d < 3; ++d) P[d] = pts[3 * ip + d];
+  double2 E[3], H[3];
+  for (int i = 0; i < 3; ++i) { E[i] = make_double2(0, 0); H[i] = make_double2(0, 0); }
+  for (long long u = blockIdx.x; u < (long long)p * nch; u += gridDim.x) {
+    const int mu = (int)(u / nch), ch = (int)(u % nch);
+    const int s = sid[mu];
+    const int q0 = ch * QC, nq = min(QC, Q - q0);
+    const double* Ms = modes + (size_t)s * npsi * Q * 4 + (size_t)q0 * 4;
+    for (int q = threadIdx.x; q < nq; q += blockDim.x) {
+      double2 a[8];
+      for (int i = 0; i < 8; ++i) a[i] = make_double2(0, 0);
+      for (int n = 0; n < npsi; ++n) {
+        double2 ae = x[((size_t)mu * 2 * npsi + n) * R + r];
+        double2 am = x[((size_t)mu * 2 * npsi + npsi + n) * R + r];
+        const double* m = Ms + ((size_t)n * Q + q) * 4;
+        for (int i = 0; i < 4; ++i) {
+          a[i].x += ae.x * m[i]; a[i].y += ae.y * m[i];
+          a[4 + i].x += am.x * m[i]; a[4 + i].y += am.y * m[i];
+        }
+      }
+      for (int i = 0; i < 8; ++i) cur[(size_t)q * 8 + i] = a[i];
+      const double* rr = rq + ((size_t)s * Q + q0 + q) * 4;
+      pq[4 * q] = rr[0] + cen[3 * mu];
+      pq[4 * q + 1] = rr[1] + cen[3 * mu + 1];
+      pq[4 * q + 2] = rr[2] + cen[3 * mu + 2];
+      pq[4 * q + 3] = rr[3];
+    }
+    __syncthreads();
+    if (act) {
+      for (int q = 0; q < nq; ++q) {
+        double d[3] = {P[0] - pq[4 * q], P[1] - pq[4 * q + 1], P[2] - pq[4 * q + 2]};
+        double R2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+        double Rr = sqrt(R2), iR = 1.0 / Rr;
+        double sn, cs;
+        sincos(-kw * Rr, &sn, &cs);
+        double w = pq[4 * q + 3];
+        double g = w * iR / (4.0 * PI);
+        double2 G = make_double2(g * cs, g * sn);
+        // grad_r g = -(d) (1 + jkR) e / (4 pi R^3)   (times w)
+        double g3 = g * iR * iR;
+        double2 D = make_double2(-g3 * (cs - kw * Rr * sn), -g3 * (sn + kw * Rr * cs));
+        const double2* c8 = cur + (size_t)q * 8;
+        for (int which = 0; which < 2; ++which) {
+          const double2* X = c8 + 4 * which;
+          // L{X} = -jk G X - (j/k) grad g (div X)
+          // K{X} = grad g x X
+          double2 Lv[3], Kv[3];
+          double2 DX = make_double2(D.x * X[3].x - D.y * X[3].y, D.x * X[3].y + D.y * X[3].x);
+          for (int i = 0; i < 3; ++i) {
+            double2 GX = make_double2(G.x * X[i].x - G.y * X[i].y, G.x * X[i].y + G.y * X[i].x);
+            // -jk GX - (j/k) d_i DX
+            Lv[i] = make_double2(kw * GX.y + d[i] * DX.y / kw, -kw * GX.x - d[i] * DX.x / kw);
+          }
+          // (d x X) * D
+          double2 cxX[3];
+          cxX[0] = make_double2(d[1] * X[2].x - d[2] * X[1].x, d[1] * X[2].y - d[2] * X[1].y);
+          cxX[1] = make_double2(d[2] * X[0].x - d[0] * X[2].x, d[2] * X[0].y - d[0] * X[2].y);
+          cxX[2] = make_double2(d[0] * X[1].x - d[1] * X[0].x, d[0] * X[1].y - d[1] * X[0].y);
+          for (int i = 0; i < 3; ++i)
+            Kv[i] = make_double2(D.x * cxX[i].x - D.y * cxX[i].y, D.x * cxX[i].y + D.y * cxX[i].x);
+          if (which == 0) {  // J: E += -zeta L{J}, H += -K{J}
+            for (int i = 0; i < 3; ++i) {
+              E[i].x -= zeta * Lv[i].x; E[i].y -= zeta * Lv[i].y;
+              H[i].x -= Kv[i].x; H[i].y -= Kv[i].y;
+            }
+          } else {           // M: E += K{M}, H += -L{M}/zeta
+            for (int i = 0; i < 3; ++i) {
+              E[i].x += Kv[i].x; E[i].y += Kv[i].y;
+              H[i].x -= Lv[i].x / zeta; H[i].y -= Lv[i].y / zeta;
+            }
+          }
+        }
       }
     }
-    for (int i = 0; i < 8; ++i) cur[(size_t)q * 8 + i] = a[i];
-    const double* rr = rq + ((size_t)s * Q + q0 + q) * 4;
-    pq[4 * q] = rr[0] + cen[3 * mu];
-    pq[4 * q + 1] = rr[1] + cen[3 * mu + 1];
-    pq[4 * q + 2] = rr[2] + cen[3 * mu + 2];
-    pq[4 * q + 3] = rr[3];
+    __syncthreads();
   }
-  __syncthreads();
-  for (int ip = threadIdx.x; ip < npt; ip += blockDim.x) {
-    double P[3] = {pts[3 * ip], pts[3 * ip + 1], pts[3 * ip + 2]};
-    double2 E[3], H[3];
-    for (int i = 0; i < 3; ++i) { E[i] = make_double2(0, 0); H[i] = make_double2(0, 0); }
-    for (int q = 0; q < nq; ++q) {
-      double d[3] = {P[0] - pq[4 * q], P[1] - pq[4 * q + 1], P[2] - pq[4 * q + 2]};
-      double R2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-      double Rr = sqrt(R2), iR = 1.0 / Rr;
-      double sn, cs;
-      sincos(-kw * Rr, &sn, &cs);
-      double w = pq[4 * q + 3];
-      double g = w * iR / (4.0 * PI);
-      double2 G = make_double2(g * cs, g * sn);
-      // grad_r g = -(d) (1 + jkR) e / (4 pi R^3)   (times w)
-      double g3 = g * iR * iR;
-      double2 D = make_double2(-g3 * (cs - kw * Rr * sn), -g3 * (sn + kw * Rr * cs));
-      const double2* c8 = cur + (size_t)q * 8;
-      for (int which = 0; which < 2; ++which) {
-        const double2* X = c8 + 4 * which;
-        // L{X} = -jk G X - (j/k) grad g (div X)
-        // K{X} = grad g x X
-        double2 Lv[3], Kv[3];
-        double2 DX = make_double2(D.x * X[3].x - D.y * X[3].y, D.x * X[3].y + D.y * X[3].x);
-        for (int i = 0; i < 3; ++i) {
-          double2 GX = make_double2(G.x * X[i].x - G.y * X[i].y, G.x * X[i].y + G.y * X[i].x);
-          // -jk GX - (j/k) d_i DX
-          Lv[i] = make_double2(kw * GX.y + d[i] * DX.y / kw, -kw * GX.x - d[i] * DX.x / kw);
-        }
-        // (d x X) * D
-        double2 cxX[3];
-        cxX[0] = make_double2(d[1] * X[2].x - d[2] * X[1].x, d[1] * X[2].y - d[2] * X[1].y);
-        cxX[1] = make_double2(d[2] * X[0].x - d[0] * X[2].x, d[2] * X[0].y - d[0] * X[2].y);
-        cxX[2] = make_double2(d[0] * X[1].x - d[1] * X[0].x, d[0] * X[1].y - d[1] * X[0].y);
-        for (int i = 0; i < 3; ++i)
-          Kv[i] = make_double2(D.x * cxX[i].x - D.y * cxX[i].y, D.x * cxX[i].y + D.y * cxX[i].x);
-        if (which == 0) {  // J: E += -zeta L{J}, H += -K{J}
-          for (int i = 0; i < 3; ++i) {
-            E[i].x -= zeta * Lv[i].x; E[i].y -= zeta * Lv[i].y;
-            H[i].x -= Kv[i].x; H[i].y -= Kv[i].y;
-          }
-        } else {           // M: E += K{M}, H += -L{M}/zeta
-          for (int i = 0; i < 3; ++i) {
-            E[i].x += Kv[i].x; E[i].y += Kv[i].y;
-            H[i].x -= Lv[i].x / zeta; H[i].y -= Lv[i].y / zeta;
-          }
-        }
-      }
-    }
+  if (act) {
     double* o = EH + (((size_t)ip * 6) * R + r) * 2;
     for (int i = 0; i < 3; ++i) {
       atomicAdd(o + ((size_t)i * R) * 2, E[i].x);
@@ -810,9 +821,10 @@ int launch_near_field(Ctx* c, int R, const double2* x, int npt, const double* d_
   const int nch = (c->Q + QC - 1) / QC;
   size_t sm = (size_t)QC * (16 + 4) * sizeof(double);
   SMR_CUDA(c, cudaFuncSetAttribute(k_nearfield, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-  k_nearfield<<<(unsigned)(c->p * R * nch), 256, sm, st>>>(c->p, c->npsi, c->Q, QC, npt, R, c->d_sid,
-                                                           c->d_centres, c->d_modes, c->d_rq, x, d_pts, c->k,
-                                                           c->zeta, (double*)EH);
+  const long long units = (long long)c->p * nch;
+  dim3 grid((unsigned)std::min<long long>(units, 1216), (unsigned)R, (unsigned)((npt + 255) / 256));
+  k_nearfield<<<grid, 256, sm, st>>>(c->p, c->npsi, c->Q, QC, npt, R, c->d_sid, c->d_centres, c->d_modes,
+                                     c->d_rq, x, d_pts, c->k, c->zeta, (double*)EH);
   SMR_LAUNCH(c);
   return SMR_OK;
 }
