@@ -453,12 +453,12 @@ def run_ours(a):
             # training arrays carry the workload's modes per current (N_perp = N_par)
             learned = train_learned(smr, workloads, a.train_arrays, dev, modes=info["n_psi"] // 2)
 
-        def solve(label, prec, x0=None, lpc=False):
+        def solve(label, prec, x0=None, lpc=False, extra_opts=None):
             xs = torch.zeros_like(b) if x0 is None else x0.clone()
             torch.cuda.synchronize(dev)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(st)
-            extra = {}
+            extra = dict(extra_opts or {})
             if x0 is not None:
                 # the guess is part of the solve: features + network + re-phasing
                 smr.smr_nn_predict(ctx, [k for k, _ in incs], [q for _, q in incs], learned["scale"], xs)
@@ -479,6 +479,9 @@ def run_ours(a):
 
         xt = solve("tuned_fp32_inner_fp64_outer", P32)
         sols = dict(tuned=xt)
+        # the tuned solver with the 2 x 2 cluster block-Jacobi preconditioner
+        # (SMR_PRECOND_CLUSTER, not in the paper; set-up inside the timed solve)
+        sols["tuned_cluster"] = solve("tuned_cluster_precond", P32, extra_opts=dict(precond=smr.SMR_PRECOND_CLUSTER))
         if "focal" in w and R == 1:
             gm["focal"] = focal_report(smr, ctx, xt, w, dev)
         if learned is not None:
@@ -490,6 +493,7 @@ def run_ours(a):
         sols["fp64"] = solve("plain_fp64", smr.SMR_PREC_FP64)
         # the tuned solution and its far field against the plain FP64 solve
         errors["solution_tuned_vs_fp64"] = relerr(sols["tuned"], sols["fp64"])
+        errors["solution_tuned_cluster_vs_fp64"] = relerr(sols["tuned_cluster"], sols["fp64"])
         th, ph = np.meshgrid(np.radians(np.linspace(5.0, 175.0, 8)), np.radians(np.arange(8) * 45.0),
                              indexing="ij")
         dirs = np.stack([np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph), np.cos(th)], -1).reshape(-1, 3)

@@ -54,7 +54,13 @@ enum {
 
 enum { SMR_PREC_FP64 = 0, SMR_PREC_FP32 = 1 };
 enum { SMR_LRULE_FORMULA = 0, SMR_LRULE_DOUBLE = 1 };
-enum { SMR_PRECOND_NONE = 0, SMR_PRECOND_BLOCKDIAG = 1, SMR_PRECOND_LEARNED = 2 };
+enum {
+  SMR_PRECOND_NONE = 0,
+  SMR_PRECOND_BLOCKDIAG = 1,
+  SMR_PRECOND_LEARNED = 2,
+  SMR_PRECOND_NEAR = 3,
+  SMR_PRECOND_CLUSTER = 4
+};
 
 /* Options of a context (smr_default_opts fills the defaults in brackets). */
 typedef struct {
@@ -302,12 +308,36 @@ int smr_set_column_lanes(smr_ctx* ctx, int lanes);
  * device r, z [N][R]; precision as in smr_matvec. */
 int smr_precond(smr_ctx* ctx, int R, const void* r, void* z, int precision, void* stream);
 
+/* z = C^-1 r with C the cluster block-Jacobi matrix: the particles are
+ * grouped into 2 x 2 clusters of lattice cells (the quadtree's level-1
+ * boxes of each array) and C holds, per cluster, the cluster's part of the
+ * near-field matrix (the members' self blocks, Eq. 16 with delta = 1, and
+ * the near blocks between them, Eq. 16 with delta = 0).  The inverses are
+ * computed on first use on the GPU in FP64 (Gauss-Jordan elimination with
+ * partial pivoting, 16 (2 n_psi)^2 complex values per cluster kept in FP64
+ * and FP32 until smr_set_scene or smr_destroy) and applied in `precision`.
+ * Needs 8 n_psi <= 256; SMR_E_INVALID_ARG if a cluster matrix is singular.
+ * Not in the paper (Sec. V uses the block-diagonal preconditioner of
+ * smr_precond); smr_solve uses it with precond = SMR_PRECOND_CLUSTER.
+ * device r, z [N][R]. */
+int smr_precond_cluster(smr_ctx* ctx, int R, const void* r, void* z, int precision, void* stream);
+
 typedef struct {
   double tol;      /* true relative residual ||b - Z x|| / ||b|| target [1e-4] */
   int maxit;       /* maximum inner iterations in total [2000]                 */
   int restart;     /* Krylov dimension before restart; 0 = maxit [0]           */
-  int precond;     /* SMR_PRECOND_* [SMR_PRECOND_BLOCKDIAG]; SMR_PRECOND_LEARNED
-                      needs smr_nn_precond first and R = 1                    */
+  int precond;     /* SMR_PRECOND_* [SMR_PRECOND_BLOCKDIAG]: BLOCKDIAG is the
+                      paper's (Sec. V), M^-1 = blockdiag(Z_s)^-1 = D^-1;
+                      NEAR adds the neighbour coupling by near_sweeps Jacobi
+                      sweeps over the near-field matrix Z_near = D + N
+                      (z <- z + D^-1 r - D^-1 Z_near z from z = D^-1 r, i.e.
+                      the truncated Neumann series of Z_near^-1; it helps
+                      only while the neighbour coupling is weaker than the
+                      self blocks, rho(D^-1 N) < 1; not in the paper);
+                      CLUSTER applies the inverse of each 2 x 2 lattice
+                      cluster's near-field matrix (smr_precond_cluster; not
+                      in the paper); LEARNED needs smr_nn_precond first and
+                      R = 1                                                  */
   int precision;   /* SMR_PREC_FP64: plain GMRES on the FP64 product;
                       SMR_PREC_FP32: iterative refinement, outer residual with
                       the FP64 product, inner GMRES on the FP32 product and
@@ -321,6 +351,7 @@ typedef struct {
   int fallback_iters; /* SMR_PRECOND_LEARNED: if the residual has not dropped
                       10x after this many iterations, the solve switches to
                       SMR_PRECOND_BLOCKDIAG from the current iterate [40]   */
+  int near_sweeps;  /* SMR_PRECOND_NEAR: Jacobi sweeps, 1..8 [1]             */
 } smr_solve_opts;
 
 typedef struct {

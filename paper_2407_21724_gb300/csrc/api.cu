@@ -59,6 +59,9 @@ void free_scene(Ctx* c) {
   dfree(c->d_arr);
   dfree(c->d_tile_shape); dfree(c->d_tile_start); dfree(c->d_tile_count); dfree(c->d_perm);
   dfree(c->d_tc_rec); dfree(c->d_tc_agg); dfree(c->d_tc_perm); dfree(c->d_lpc); dfree(c->d_split);
+  dfree(c->d_pcw);
+  c->pcw_elems = 0;
+  free_clusters(c);
   c->split_elems = 0;
   c->lpc_ready = false; dfree(c->d_tc_shape); dfree(c->d_tc_start); dfree(c->d_tc_count);
   c->tc_ready = false;
@@ -887,6 +890,7 @@ void smr_default_solve_opts(smr_solve_opts* o) {
   o->max_outer = 8;
   o->use_x0 = 0;
   o->fallback_iters = 40;
+  o->near_sweeps = 1;
 }
 
 int smr_create(smr_ctx** out, const smr_opts* opts) {
@@ -1156,8 +1160,8 @@ int smr_matvec_parts(smr_ctx* h, int R, const void* x, void* y_near, void* y_far
   cudaStream_t st = (cudaStream_t)stream;
   int rc = prep_x32(c, R, precision, (const double2*)x, st);
   if (!rc && y_near) rc = run_near(c, R, precision, (const double2*)x, (double2*)y_near, st);
-  if (rc) return rc;
-  if (y_far) rc = run_far(c, R, precision, (const double2*)x, (double2*)y_far, false, st);
+  if (!rc && y_far) rc = run_far(c, R, precision, (const double2*)x, (double2*)y_far, false, st);
+  c->x32_of = nullptr;
   return rc;
 }
 
@@ -1196,13 +1200,31 @@ int smr_solve(smr_ctx* h, int R, const void* b, void* x, const smr_solve_opts* o
   if (opts) o = *opts;
   if (o.precision != SMR_PREC_FP64 && o.precision != SMR_PREC_FP32)
     return fail(c, SMR_E_INVALID_ARG, "precision must be SMR_PREC_FP64 or SMR_PREC_FP32");
-  if (o.precond != SMR_PRECOND_NONE && o.precond != SMR_PRECOND_BLOCKDIAG && o.precond != SMR_PRECOND_LEARNED)
+  if (o.precond != SMR_PRECOND_NONE && o.precond != SMR_PRECOND_BLOCKDIAG && o.precond != SMR_PRECOND_LEARNED &&
+      o.precond != SMR_PRECOND_NEAR && o.precond != SMR_PRECOND_CLUSTER)
     return fail(c, SMR_E_INVALID_ARG, "unknown preconditioner");
+  if (o.precond == SMR_PRECOND_CLUSTER) {
+    int rb = build_clusters(c);
+    if (rb) return rb;
+  }
+  if (o.precond == SMR_PRECOND_NEAR && (o.near_sweeps < 1 || o.near_sweeps > 8))
+    return fail(c, SMR_E_INVALID_ARG, "near_sweeps must be in 1..8");
   if (o.precond == SMR_PRECOND_LEARNED && (R != 1 || !c->lpc_ready))
     return fail(c, SMR_E_STATE, "SMR_PRECOND_LEARNED needs R = 1 and smr_nn_precond first");
   int rc = solve(c, R, (const double2*)b, (double2*)x, &o, stats, (cudaStream_t)stream);
   int rt = tc_check(c);
   return rc ? rc : rt;
+}
+
+int smr_precond_cluster(smr_ctx* h, int R, const void* r, void* z, int precision, void* stream) {
+  if (!h || R <= 0 || R > 256 || !r || !z) return SMR_E_INVALID_ARG;
+  Ctx* c = &h->c;
+  if (!check_scene(c)) return SMR_E_STATE;
+  if (precision != SMR_PREC_FP64 && precision != SMR_PREC_FP32)
+    return fail(c, SMR_E_INVALID_ARG, "precision must be SMR_PREC_FP64 or SMR_PREC_FP32");
+  int rc = build_clusters(c);
+  if (rc) return rc;
+  return run_cluster(c, R, precision, (const double2*)r, (double2*)z, (cudaStream_t)stream);
 }
 
 int smr_set_tensor_cores(smr_ctx* h, int enable) {

@@ -725,13 +725,49 @@ static int apply_A(Ctx* c, int R, int prec, const double2* x, double2* y, cudaSt
   return run_product(c, R, prec, x, y, st);
 }
 
-// z = M^-1 v: the block-diagonal preconditioner, scaled per unknown by the
-// learned diagonal for SMR_PRECOND_LEARNED, or a copy for SMR_PRECOND_NONE
+__global__ void k_sweep_update(long long n, double2* __restrict__ z, const double2* __restrict__ t,
+                               const double2* __restrict__ u) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) {
+    double2 a = z[i], b = t[i], d = u[i];
+    z[i] = make_double2(a.x + b.x - d.x, a.y + b.y - d.y);
+  }
+}
+
+// z = M^-1 v: the block-diagonal preconditioner D^-1, scaled per unknown by
+// the learned diagonal for SMR_PRECOND_LEARNED, followed for
+// SMR_PRECOND_NEAR by c->pc_sweeps Jacobi sweeps over the near field
+// (z <- z + D^-1 v - D^-1 Z_near z), the cluster block-Jacobi inverse for
+// SMR_PRECOND_CLUSTER, or a copy for SMR_PRECOND_NONE
 static int apply_M(Ctx* c, int R, int prec, int precond, const double2* v, double2* z, cudaStream_t st) {
+  const long long ld = 2LL * c->npsi * c->p * R;
   if (precond == SMR_PRECOND_NONE) {
-    SMR_CUDA(c, cudaMemcpyAsync(z, v, (size_t)2 * c->npsi * c->p * R * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+    SMR_CUDA(c, cudaMemcpyAsync(z, v, (size_t)ld * sizeof(double2), cudaMemcpyDeviceToDevice, st));
     return SMR_OK;
   }
+  if (precond == SMR_PRECOND_NEAR) {
+    if (!c->d_pcw || c->pcw_elems < (size_t)3 * ld) {
+      c->err = "near-field preconditioner work vectors missing";
+      return SMR_E_STATE;
+    }
+    double2* t = c->d_pcw;                    // D^-1 v
+    double2* y = c->d_pcw + ld;               // Z_near z
+    double2* u = c->d_pcw + 2 * ld;           // D^-1 Z_near z
+    int rc = run_precond(c, R, prec, v, t, st);
+    if (rc) return rc;
+    SMR_CUDA(c, cudaMemcpyAsync(z, t, (size_t)ld * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+    for (int k = 0; k < c->pc_sweeps && !rc; ++k) {
+      c->x32_of = nullptr;                    // z changed: the FP32 copy of x is stale
+      rc = run_near(c, R, prec, z, y, st);
+      if (!rc) rc = run_precond(c, R, prec, y, u, st);
+      if (!rc) {
+        k_sweep_update<<<(unsigned)((ld + 255) / 256), 256, 0, st>>>(ld, z, t, u);
+        SMR_CUDA(c, cudaGetLastError());
+      }
+    }
+    return rc;
+  }
+  if (precond == SMR_PRECOND_CLUSTER) return run_cluster(c, R, prec, v, z, st);
   int rc = run_precond(c, R, prec, v, z, st);
   if (rc || precond != SMR_PRECOND_LEARNED) return rc;
   return lpc_apply(c, z, st);
@@ -1077,6 +1113,21 @@ int solve(Ctx* c, int R, const double2* b, double2* x, const smr_solve_opts* o, 
   int fb_x0 = 0, fb_pc = 0, its_learned = 0;
   int precond = o->precond;
   const bool learned = precond == SMR_PRECOND_LEARNED && o->fallback_iters > 0;
+  if (precond == SMR_PRECOND_NEAR) {
+    c->pc_sweeps = o->near_sweeps;
+    if (c->pcw_elems < (size_t)3 * ld) {
+      if (c->d_pcw) cudaFree(c->d_pcw);
+      c->d_pcw = nullptr;
+      c->pcw_elems = 0;
+      if (cudaMalloc((void**)&c->d_pcw, (size_t)3 * ld * sizeof(double2)) != cudaSuccess) {
+        cudaGetLastError();
+        cleanup();
+        c->err = "solve: device allocation of the near-field preconditioner's work vectors failed";
+        return SMR_E_OOM;
+      }
+      c->pcw_elems = (size_t)3 * ld;
+    }
+  }
   std::vector<double> rel;
   double tol = o->tol > 0 ? o->tol : 1e-4;
   // columns of x set to a * x (a = 0 or 1 per column, host values)

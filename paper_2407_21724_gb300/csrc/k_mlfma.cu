@@ -1361,7 +1361,9 @@ __global__ void k_x32f(long long n, const double2* __restrict__ a, float2* __res
 // The FP32 single right-hand-side product converts x to FP32 once (the
 // conversion runs on the FP64 units, 1/64 of the FP32 rate) for the near
 // gathers and the tensor-core aggregation; c->x32_of records which x the
-// copy holds, so a step that finds another x reads the FP64 one.
+// copy holds, so a step that finds another x reads the FP64 one.  The record
+// lives for one product call: the callers clear it before they return, and
+// graph capture clears it (a capture converts nothing).
 int prep_x32(Ctx* c, int R, int prec, const double2* x, cudaStream_t st) {
   c->x32_of = nullptr;
   if (prec != SMR_PREC_FP32 || R != 1 || !c->d_x32) return SMR_OK;
@@ -1537,8 +1539,9 @@ int run_product(Ctx* c, int R, int prec, const double2* x, double2* y, cudaStrea
   if (!split_columns(c, R, prec)) {
     int rc = prep_x32(c, R, prec, x, st);
     if (!rc) rc = run_near(c, R, prec, x, y, st);
-    if (rc) return rc;
-    return run_far(c, R, prec, x, y, true, st);
+    if (!rc) rc = run_far(c, R, prec, x, y, true, st);
+    c->x32_of = nullptr;                        // the FP32 copy lives for one product only
+    return rc;
   }
   const int nl = lanes_for(c, R);
   int rc = ensure_split(c, R);
@@ -1616,6 +1619,7 @@ int run_matvec_graph(Ctx* c, int R, int prec, const double2* x, double2* y, cuda
   cudaGraph_t graph = nullptr;
   cudaError_t e = cudaStreamEndCapture(cs, &graph);
   c->prof = prof;
+  c->x32_of = nullptr;                          // the capture converted nothing
   if (rc) {
     if (graph) cudaGraphDestroy(graph);
     return rc;

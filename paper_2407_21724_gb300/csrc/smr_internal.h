@@ -337,6 +337,17 @@ struct Ctx {
   std::vector<Lane> lanes;
   int n_lanes = 4;                        // columns in flight (smr_set_column_lanes, smr_autotune)
   cudaEvent_t lane_fork = nullptr;
+  // cluster block-Jacobi preconditioner (k_cluster.cu): members [ncl][4]
+  // (-1 for an absent one), inverses [ncl][4m][4m] transposed, m = 2 n_psi
+  bool cl_ready = false;
+  int ncl = 0;
+  int* d_cl_mem = nullptr;
+  double2* d_cl_inv64 = nullptr;
+  float2* d_cl_inv32 = nullptr;
+  // near-field sweeps preconditioner: three [N][R] work vectors, sweep count
+  double2* d_pcw = nullptr;
+  size_t pcw_elems = 0;
+  int pc_sweeps = 1;
   // learned local-coupling preconditioner: diagonal D [N] (one right-hand side)
   double2* d_lpc = nullptr;
   bool lpc_ready = false;
@@ -429,6 +440,11 @@ void free_graphs(Ctx* c);
 int mesh_static_modes(Ctx* c, int nv, const double* verts, int nt, const int* tris, int n_perp, int n_par,
                       MeshModes& out);
 int mesh_self_block(Ctx* c, const Shape& sh, std::vector<cd>& Z);
+// cluster block-Jacobi preconditioner (k_cluster.cu)
+bool cluster_ok(const Ctx* c);
+int build_clusters(Ctx* c);
+int run_cluster(Ctx* c, int R, int prec, const double2* r, double2* z, cudaStream_t st);
+void free_clusters(Ctx* c);
 // column lanes of split FP32 products (buffers allocated outside graph capture)
 int ensure_lanes(Ctx* c, int nl);
 void free_lanes(Ctx* c);

@@ -18,7 +18,7 @@ _lib = None
 
 SMR_PREC_FP64, SMR_PREC_FP32 = 0, 1
 SMR_LRULE_FORMULA, SMR_LRULE_DOUBLE = 0, 1
-SMR_PRECOND_NONE, SMR_PRECOND_BLOCKDIAG, SMR_PRECOND_LEARNED = 0, 1, 2
+SMR_PRECOND_NONE, SMR_PRECOND_BLOCKDIAG, SMR_PRECOND_LEARNED, SMR_PRECOND_NEAR, SMR_PRECOND_CLUSTER = 0, 1, 2, 3, 4
 SMR_OK, SMR_E_SHAPE, SMR_E_NOT_CONVERGED = 0, -2, -5
 SMR_E_BREAKDOWN, SMR_E_TIMEOUT = -6, -8
 ERRORS = {-1: "INVALID_ARG", -2: "SHAPE", -3: "OOM", -4: "CUDA", -5: "NOT_CONVERGED",
@@ -49,7 +49,7 @@ class smr_info_t(C.Structure):
 class smr_solve_opts(C.Structure):
     _fields_ = [("tol", C.c_double), ("maxit", C.c_int), ("restart", C.c_int), ("precond", C.c_int),
                 ("precision", C.c_int), ("max_outer", C.c_int), ("use_x0", C.c_int),
-                ("fallback_iters", C.c_int)]
+                ("fallback_iters", C.c_int), ("near_sweeps", C.c_int)]
 
 
 class smr_solve_stats(C.Structure):
@@ -119,6 +119,7 @@ _SIGS = {
     "smr_sync": (C.c_int, [_P, _P]),
     "smr_set_wait_limit": (C.c_int, [_P, C.c_longlong]),
     "smr_set_column_lanes": (C.c_int, [_P, C.c_int]),
+    "smr_precond_cluster": (C.c_int, [_P, C.c_int, _P, _P, C.c_int, _P]),
     "smr_set_variant": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_int]),
 }
 
@@ -359,6 +360,12 @@ def smr_set_variant(ctx, step, level, precision, variant):
 def smr_set_wait_limit(ctx, rounds):
     """Polling limit of the tensor-core pipeline waits; rounds < 0 restores the default."""
     _check(ctx, lib().smr_set_wait_limit(ctx, int(rounds)))
+
+
+def smr_precond_cluster(ctx, r, z, precision=SMR_PREC_FP64, R=None, stream=None):
+    """z = (2 x 2 cluster block-Jacobi matrix)^-1 r."""
+    R = R if R is not None else _R(r, smr_info(ctx)["n_unknowns"])
+    _check(ctx, lib().smr_precond_cluster(ctx, R, _ptr(r), _ptr(z), precision, _stream(stream, r)))
 
 
 def smr_set_column_lanes(ctx, lanes):
