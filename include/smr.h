@@ -261,7 +261,8 @@ int smr_set_tensor_cores(smr_ctx* ctx, int enable);
  * kernel (FP32: child theta-row bands bulk-copied into shared memory) or by
  * the gather kernel with the full or half theta-row tile; anterpolation by
  * the staged kernel (FP32, where its tile fits) or by the gather kernel with
- * the full or half column chunk or 256-thread CTAs; for SMR_PREC_FP32 also
+ * the full or half column chunk, 256-thread CTAs or one CTA per parent box
+ * (FP32); for SMR_PREC_FP32 also
  * aggregation, receive and the near-field product on the tensor cores or the
  * CUDA cores (the near product on the tensor cores only if at least 5 %
  * faster).  Each variant is timed over three products (CUDA events around
@@ -503,7 +504,9 @@ int smr_copy_level(smr_ctx* ctx, int level, int kind, double* out, size_t n_doub
  *    half theta-row tile;
  *  SMR_STEP_ANTERPOLATE (into `level`): 0 built-in rule (the gather kernel),
  *    1 half its column chunk, 2 256-thread CTAs, 4 the staged kernel (FP32,
- *    parent band bulk-copied, where its tile fits).
+ *    parent band bulk-copied, where its tile fits), 5 the gather kernel with
+ *    one CTA per parent box serving its four children (FP32: each parent tap
+ *    read once for the four quadrants' shifts).
  * A variant that does not apply to a level falls back to the built-in rule.
  * Drops captured products.  No counterpart in the paper. */
 enum { SMR_STEP_TRANSLATE = 0, SMR_STEP_INTERPOLATE = 1, SMR_STEP_ANTERPOLATE = 2 };

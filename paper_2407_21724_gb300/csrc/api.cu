@@ -35,7 +35,7 @@ void free_scene(Ctx* c) {
     dfree(L.d_T64); dfree(L.d_T32); dfree(L.d_parent); dfree(L.d_quad); dfree(L.d_ch_ptr);
     dfree(L.d_ch_idx); dfree(L.d_ch_quad); dfree(L.d_th_src); dfree(L.d_th_refl); dfree(L.d_th_w64);
     dfree(L.d_th_w32); dfree(L.d_th_pk); dfree(L.d_th_ws64); dfree(L.d_th_ws32); dfree(L.d_ph_src); dfree(L.d_ph_w64); dfree(L.d_ph_w32); dfree(L.d_shift64);
-    dfree(L.d_shift32); dfree(L.d_ip2_band); dfree(L.d_an2_lo);
+    dfree(L.d_shift32); dfree(L.d_shift4_32); dfree(L.d_ip2_band); dfree(L.d_an2_lo);
     dfree(L.d_an2_ttp); dfree(L.d_an2_tw); dfree(L.d_an2_pst2); dfree(L.d_an2_pwp);
     dfree(L.d_an2_tq); dfree(L.d_an2_twq); dfree(L.d_ant_lo); dfree(L.d_ant_pjp); dfree(L.d_ant_pw64); dfree(L.d_ant_pw32);
     dfree(L.d_ant_ttp); dfree(L.d_ant_tw64); dfree(L.d_ant_tw32);
@@ -287,6 +287,8 @@ int build_interp(Ctx* c, Level& C, const Level& P) {
       int jc = (48 * 1024) / (C.ant_GR * 2 * dirb);
       C.ant_JC[q] = std::max(1, std::min(C.nph / 2, jc));
     }
+    // the per-parent FP32 kernel holds four quadrants' rows: 52 KB for four CTAs per SM
+    C.ant_JC5 = std::max(1, std::min(C.nph / 2, (52 * 1024) / (4 * C.ant_GR * 2 * 32)));
     if ((rc = upload(c, &C.d_ant_lo, lohi))) return rc;
     // padded transposed taps
     int pm = 0, tm = 0;
@@ -473,7 +475,12 @@ int build_interp(Ctx* c, Level& C, const Level& P) {
       sh32[(size_t)q * P.K + k] = make_float2((float)std::cos(ph), (float)std::sin(ph));
     }
   }
-  if ((rc = upload(c, &C.d_shift64, sh)) || (rc = upload(c, &C.d_shift32, sh32))) return rc;
+  std::vector<float2> sh4((size_t)4 * P.K);      // quadrant-interleaved per direction
+  for (int k = 0; k < P.K; ++k)
+    for (int q = 0; q < 4; ++q) sh4[(size_t)4 * k + q] = sh32[(size_t)q * P.K + k];
+  if ((rc = upload(c, &C.d_shift64, sh)) || (rc = upload(c, &C.d_shift32, sh32)) ||
+      (rc = upload(c, &C.d_shift4_32, sh4)))
+    return rc;
   return SMR_OK;
 }
 
@@ -1246,7 +1253,7 @@ int smr_set_variant(smr_ctx* h, int step, int level, int precision, int variant)
   const int q = precision == SMR_PREC_FP64 ? 0 : 1;
   const bool ok = (step == SMR_STEP_TRANSLATE && variant >= 0 && variant <= 4) ||
                   (step == SMR_STEP_INTERPOLATE && variant >= 0 && variant <= 2) ||
-                  (step == SMR_STEP_ANTERPOLATE && (variant >= 0 && variant <= 2 || variant == 4));
+                  (step == SMR_STEP_ANTERPOLATE && (variant >= 0 && variant <= 2 || variant == 4 || variant == 5));
   if (!ok) return fail(c, SMR_E_INVALID_ARG, "unknown step or variant");
   for (int s = (level < 0 ? 0 : level); s < (level < 0 ? c->nlev : level + 1); ++s) {
     Level& L = c->lev[s];
@@ -1466,14 +1473,16 @@ int smr_autotune(smr_ctx* h, int R, int precision, void* stream) {
   // translation: 8x8 tiles (full, half direction chunk) and 4x4 tiles
   std::vector<std::vector<double>> ttr(c->nlev, std::vector<double>(5, 1e30));
   std::vector<std::vector<double>> tip(c->nlev, std::vector<double>(3, 1e30));
-  std::vector<std::vector<double>> tan_(c->nlev, std::vector<double>(5, 1e30));
-  const int anv[5] = {0, 0, 1, 2, 4};          // anterpolation variant timed in trial v
+  std::vector<std::vector<double>> tan_(c->nlev, std::vector<double>(6, 1e30));
+  const int anv[6] = {0, 0, 1, 2, 4, 5};       // anterpolation variant timed in trial v
   double agg[2] = {1e30, 1e30}, rec[2] = {1e30, 1e30}, nea[2] = {1e30, 1e30};
   const int agg0 = c->tune_tc_agg, rec0 = c->tune_tc_rec, nea0 = c->tune_tc_near;
-  for (int v = 1; v <= 4; ++v) {
+  // trial 5 times the per-parent FP32 anterpolation with the other steps at
+  // their first variants
+  for (int v = 1; v <= (q == 1 ? 5 : 4); ++v) {
     // variant 4 (few-box kernel) only where a level has at most 1024 boxes
     for (auto& L : c->lev) {
-      L.tune_tr[q] = (v == 4 && L.nbox > 1024) ? 1 : v;
+      L.tune_tr[q] = (v == 5 || (v == 4 && L.nbox > 1024)) ? 1 : v;
       // interpolation: the built-in rule (staged kernel in FP32), k_interp1
       // with the full or the half theta-row tile
       L.tune_ip[q] = (v == 2) ? 2 : (v == 3 ? 1 : 0);
@@ -1509,7 +1518,7 @@ int smr_autotune(smr_ctx* h, int R, int precision, void* stream) {
       if (tip[s][v] < tip[s][bi]) bi = v;
     L.tune_ip[q] = rc ? 0 : bi;
     int ba = 0;
-    for (int v = 1; v <= 4; ++v)
+    for (int v = 1; v <= 5; ++v)
       if (tan_[s][v] < tan_[s][ba]) ba = v;
     L.tune_an[q] = rc ? 0 : ba;
   }

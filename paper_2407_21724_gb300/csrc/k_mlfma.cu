@@ -926,6 +926,111 @@ __global__ void __launch_bounds__(256) k_anterp1(int nthC, int nphC, int nthP, i
     if (u >= W) { u -= W; ++il; }
   }
 }
+// FP32, one right-hand side: the anterpolation of k_anterp1 with one CTA per
+// parent box serving all of its children.  Every parent tap of the
+// transposed phi pass is read once and multiplied by the conjugate shifts of
+// the four child quadrants (sh4: per parent direction the four quadrants'
+// shifts, 32 bytes), so four accumulators share one load; the theta pass of
+// each child then reads its quadrant's rows from shared memory.
+template <int PMC>
+__global__ void __launch_bounds__(256, 4) k_anterp4(int nthC, int nphC, int nthP, int nphP, int TI, int nit,
+                                                   int JC, int njc, const int* __restrict__ ch_ptr,
+                                                   const int* __restrict__ ch_idx, const int* __restrict__ ch_quad,
+                                                   const int* __restrict__ lo_row, int PM,
+                                                   const int* __restrict__ pjp, const float* __restrict__ pw,
+                                                   const float* __restrict__ wthp, const float4* __restrict__ sh4,
+                                                   const float2* __restrict__ inP, int TM,
+                                                   const int* __restrict__ ttp, const float* __restrict__ tw,
+                                                   float2* __restrict__ inC) {
+  typedef Part<float> P;
+  typedef P::H H;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* Gt = reinterpret_cast<float2*>(smem_raw);   // [4 quadrants][GR][2 JC][4]
+  int blk = blockIdx.x;
+  const int jcb = blk % njc;
+  blk /= njc;
+  const int it = blk % nit, B = blk / nit;
+  const int i0 = it * TI, ni = min(TI, nthC - i0);
+  const int half = nphC >> 1;
+  const int j0 = jcb * JC, nj = min(JC, half - j0);
+  const int lo = lo_row[it], hi = lo_row[nit + it];
+  const int nr = hi - lo, W = 2 * nj;
+  const int Kp = nthP * nphP, Kc = nthC * nphC;
+  const float2* srcP = inP + (size_t)B * Kp * 4;
+  const int NTH = blockDim.x / 2, task0 = threadIdx.x / 2, h = threadIdx.x % 2;
+  const int r0 = task0 / W, u0 = task0 - r0 * W;
+  const int dq = NTH / W, dr = NTH - dq * W;
+  const size_t qstride = (size_t)nr * W;               // tasks per quadrant
+  for (int r = r0, u = u0, task = task0; r < nr; task += NTH) {
+    const int j = (u < nj) ? j0 + u : j0 + half + (u - nj);
+    const int tp = lo + r;
+    const float wt = wthp[tp];
+    const float2* prow = srcP + (size_t)tp * nphP * 4;
+    const float4* srow = sh4 + (size_t)tp * nphP * 2;
+    H a0 = P::zero(), a1 = P::zero(), a2 = P::zero(), a3 = P::zero();
+    const int pm = PMC > 0 ? 8 : PM;
+#pragma unroll
+    for (int q = 0; q < (PMC > 0 ? PMC : PM); q += 4) {
+      const int4 jj = *reinterpret_cast<const int4*>(pjp + (size_t)j * pm + q);
+      float w[4];
+      P::w4(pw + (size_t)j * pm + q, w);
+      const int js[4] = {jj.x, jj.y, jj.z, jj.w};
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        if (PMC > 0 && q + b >= PMC) break;
+        const H v = ldp<float>(prow, js[b], h);
+        const float4 s01 = srow[2 * js[b]], s23 = srow[2 * js[b] + 1];
+        const float ww = w[b] * wt;
+        P::cfma(a0, make_float2(ww * s01.x, -ww * s01.y), v);
+        P::cfma(a1, make_float2(ww * s01.z, -ww * s01.w), v);
+        P::cfma(a2, make_float2(ww * s23.x, -ww * s23.y), v);
+        P::cfma(a3, make_float2(ww * s23.z, -ww * s23.w), v);
+      }
+    }
+    stp<float>(Gt, task, h, a0);
+    stp<float>(Gt, qstride + task, h, a1);
+    stp<float>(Gt, 2 * qstride + task, h, a2);
+    stp<float>(Gt, 3 * qstride + task, h, a3);
+    u += dr;
+    r += dq;
+    if (u >= W) { u -= W; ++r; }
+  }
+  __syncthreads();
+  const int c0 = ch_ptr[B], nch = ch_ptr[B + 1] - c0;
+  for (int k = 0; k < nch; ++k) {
+    const int cb = ch_idx[c0 + k];
+    const float2* Gq = Gt + (size_t)ch_quad[c0 + k] * qstride * 4;
+    for (int il = r0, u = u0; il < ni;) {
+      const int ur = u < nj ? u + nj : u - nj;           // column j + N/2 (mod N)
+      const int j = (u < nj) ? j0 + u : j0 + half + (u - nj);
+      const int i = i0 + il;
+      H a = P::zero();
+      const int tm = PMC > 0 ? 8 : TM;
+#pragma unroll
+      for (int q = 0; q < (PMC > 0 ? PMC : TM); q += 4) {
+        const int4 pk = *reinterpret_cast<const int4*>(ttp + (size_t)i * tm + q);
+        float w[4];
+        P::w4(tw + (size_t)i * tm + q, w);
+        const int ps[4] = {pk.x, pk.y, pk.z, pk.w};
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          if (PMC > 0 && q + b >= PMC) break;
+          const int rr = (ps[b] & 0xffff) - lo;
+          const size_t g = (size_t)rr * W + ((ps[b] >> 16) ? ur : u);
+          P::rfma(a, w[b], ldp<float>(Gq, g, h));
+        }
+      }
+      const size_t d = (size_t)cb * Kc + (size_t)i * nphC + j;
+      H cur = ldp<float>(inC, d, h);
+      P::add(cur, a);
+      stp<float>(inC, d, h, cur);
+      u += dr;
+      il += dq;
+      if (u >= W) { u -= W; ++il; }
+    }
+  }
+}
+
 // ------------------------------------------------------------------ receive
 // y_e[m] += -jk sum_k w conj(sh) [P_th (z B0 + B3) + P_ph (z B1 - B2)]
 // y_m[m] += -jk sum_k w conj(sh) [P_th (-B1 + B2/z) + P_ph (B0 + B3/z)]   (Eqs. 24-25)
@@ -1117,6 +1222,23 @@ int ensure_spectra(Ctx* c, int R, int prec) {
   return SMR_OK;
 }
 
+// The per-parent FP32 anterpolation needs the 8-tap tables and its four
+// quadrants' phi-pass rows within the fixed shared-memory ceiling.
+bool anterp4_ok(Ctx* c, int s) {
+  const Level& Lc = c->lev[s];
+  if (!Lc.d_shift4_32 || Lc.ant_PM != 8 || Lc.ant_TM != 8 || std::max(Lc.ant_PMx, Lc.ant_TMx) > 8) return false;
+  const size_t sm4 = (size_t)4 * Lc.ant_GR * 2 * Lc.ant_JC5 * 4 * sizeof(float2);
+  if (Lc.ant_JC5 < 1 || sm4 > 200 * 1024) return false;
+  static bool attr = false;
+  if (!attr) {
+    // one fixed ceiling for every launch (graph nodes keep their own size)
+    cudaFuncSetAttribute(k_anterp4<7>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_anterp4<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr = true;
+  }
+  return true;
+}
+
 template <typename T>
 static int far_impl(Ctx* c, int R, const double2* x, double2* y, bool accumulate, cudaStream_t st) {
   typedef typename CV<T>::V V;
@@ -1269,6 +1391,19 @@ static int far_impl(Ctx* c, int R, const double2* x, double2* y, bool accumulate
       int rc = run_anterp2(c, s, st);
       pend(c, st);
       if (rc) return rc;
+      continue;
+    }
+    if (!f64 && R == 1 && Lc.tune_an[1] == 5 && anterp4_ok(c, s)) {
+      const int JC = Lc.ant_JC5;
+      const int njc = (Lc.nph / 2 + JC - 1) / JC;
+      const size_t sm4 = (size_t)4 * Lc.ant_GR * 2 * JC * 4 * sizeof(float2);
+      auto ka = std::max(Lc.ant_PMx, Lc.ant_TMx) <= 7 ? k_anterp4<7> : k_anterp4<8>;
+      ka<<<(unsigned)(Lp.nbox * Lc.ant_nit * njc), 256, sm4, st>>>(
+          Lc.nth, Lc.nph, Lp.nth, Lp.nph, Lc.ant_TI, Lc.ant_nit, JC, njc, Lp.d_ch_ptr, Lp.d_ch_idx, Lp.d_ch_quad,
+          Lc.d_ant_lo, Lc.ant_PM, Lc.d_ant_pjp, Lc.d_ant_pw32, Lc.d_wthp32, (const float4*)Lc.d_shift4_32,
+          (const float2*)Lp.d_in, Lc.ant_TM, Lc.d_ant_ttp, Lc.d_ant_tw32, (float2*)Lc.d_in);
+      SMR_LAUNCH(c);
+      pend(c, st);
       continue;
     }
     if (R == 1) {

@@ -84,6 +84,7 @@ struct Level {
   float2* d_T32 = nullptr;
   int* d_parent = nullptr;
   int* d_quad = nullptr;
+  float2* d_shift4_32 = nullptr;   // [K][4] the four quadrants' shifts per direction (parent level's child tables)
   int* d_ch_ptr = nullptr;
   int* d_ch_idx = nullptr;
   int* d_ch_quad = nullptr;
@@ -125,6 +126,7 @@ struct Level {
   // widest range, JC the column chunk per precision (FP64, FP32)
   int ant_TI = 0, ant_nit = 0, ant_GR = 0;
   int ant_JC[2] = {0, 0};
+  int ant_JC5 = 0;                       // column chunk of the per-parent FP32 kernel (four quadrants' rows)
   int* d_ant_lo = nullptr;
   // the transposed taps padded to fixed widths (multiples of 4, zero weights):
   // phi by child column [nph][PM] (parent column, weight x dphi_p / dphi_c),

@@ -97,23 +97,25 @@ def _direct_product(d, prec):
 
 
 VARIANTS = [(smr.SMR_STEP_INTERPOLATE, v) for v in (0, 1, 2)] + \
-           [(smr.SMR_STEP_ANTERPOLATE, v) for v in (0, 1, 2, 4)] + \
+           [(smr.SMR_STEP_ANTERPOLATE, v) for v in (0, 1, 2, 4, 5)] + \
            [(smr.SMR_STEP_TRANSLATE, v) for v in (1, 2, 3, 4)]
 
 
 @pytest.mark.parametrize("prec", [smr.SMR_PREC_FP64, smr.SMR_PREC_FP32])
 def test_deep_every_launch_variant(deep, prec):
     """Every launch variant the autotuner can choose, forced at every level
-    in turn (staged and gather interpolation and anterpolation, every
-    translation tiling), gives the oracle's product: FP64 <= 1e-10, FP32
-    <= 2e-5; for the staged FP32 kernels every level spectrum <= 1e-5."""
+    in turn (staged and gather interpolation and anterpolation, the
+    per-parent anterpolation, every translation tiling), gives the oracle's
+    product: FP64 <= 1e-10, FP32 <= 2e-5; for the staged and per-parent FP32
+    kernels every level spectrum <= 1e-5."""
     ctx = deep["ctx"]
     try:
         for step, v in VARIANTS:
             smr.smr_set_variant(ctx, step, -1, prec, v)
             y = _direct_product(deep, prec)
             assert rel(y, deep["y"]) < (1e-10 if prec == smr.SMR_PREC_FP64 else 2e-5), (step, v)
-            staged = (step == smr.SMR_STEP_INTERPOLATE and v == 0) or (step == smr.SMR_STEP_ANTERPOLATE and v == 4)
+            staged = (step == smr.SMR_STEP_INTERPOLATE and v == 0) or \
+                (step == smr.SMR_STEP_ANTERPOLATE and v in (4, 5))
             if staged and prec == smr.SMR_PREC_FP32:
                 for s in range(deep["M"].tree.n_levels):
                     go = smr.smr_copy_level(ctx, s, 0)[..., 0]
