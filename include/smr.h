@@ -304,6 +304,17 @@ int smr_set_wait_limit(smr_ctx* ctx, long long rounds);
  * products.  No counterpart in the paper. */
 int smr_set_column_lanes(smr_ctx* ctx, int lanes);
 
+/* Overlap inside one product (1 = default, 0 = every step in order on the
+ * caller's stream).  Overlapped, the near-field product runs on a side
+ * stream next to the far field, and the translation of each level (Eq. 23)
+ * on a second side stream as soon as that level's outgoing spectra exist;
+ * the anterpolation into a level waits for its translation and the receive
+ * for the near product (events; in a captured graph these are its edges).
+ * The small upper-level launches then overlap the upward pass.  The result
+ * is bit for bit that of the ordered product (the same kernels on the same
+ * data).  Drops captured products.  No counterpart in the paper. */
+int smr_set_overlap(smr_ctx* ctx, int enable);
+
 /* z = blockdiag(Z_s^-1) r over particles: the block-diagonal preconditioner
  * of Sec. V (each block the inverse of the particle's self block).
  * device r, z [N][R]; precision as in smr_matvec. */

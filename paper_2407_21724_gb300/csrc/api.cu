@@ -923,6 +923,7 @@ int smr_destroy(smr_ctx* h) {
   if (!h) return SMR_OK;
   cudaSetDevice(h->c.device);
   free_scene(&h->c);
+  free_side(&h->c);
   nn_free(&h->c);
   if (h->c.d_tc_err) cudaFree(h->c.d_tc_err);
   if (h->c.d_red) cudaFree(h->c.d_red);
@@ -1281,6 +1282,15 @@ int smr_set_column_lanes(smr_ctx* h, int lanes) {
   cudaSetDevice(c->device);
   c->n_lanes = lanes;
   free_graphs(c);                              // captured products hold the old lane count
+  return SMR_OK;
+}
+
+int smr_set_overlap(smr_ctx* h, int enable) {
+  if (!h) return SMR_E_INVALID_ARG;
+  Ctx* c = &h->c;
+  cudaSetDevice(c->device);
+  c->overlap = enable != 0;
+  free_graphs(c);                              // captured products hold the old launch order
   return SMR_OK;
 }
 

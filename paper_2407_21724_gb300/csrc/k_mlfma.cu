@@ -1247,6 +1247,73 @@ static int far_impl(Ctx* c, int R, const double2* x, double2* y, bool accumulate
   Level& L0 = c->lev[0];
   int RC = std::min(R, 16);
   int nrc = (R + RC - 1) / RC;
+  // Overlap: the translation of each level runs on a side stream after an
+  // event that marks its outgoing spectra, and the anterpolation into a level
+  // waits for that level's translation; the receive waits for the near
+  // product when run_product put it on a side stream (c->near_ev).
+  Ctx::Side* sd = (c->overlap && !c->prof && c->cur_side < (int)c->side.size()) ? &c->side[c->cur_side] : nullptr;
+  if (sd && (!sd->tr || c->nlev > (int)sd->eout.size())) sd = nullptr;
+  // translation at every level (in the upward loop when it overlaps)
+  auto translate = [&](int s, cudaStream_t ts) -> int {
+    Level& L = c->lev[s];
+    if (L.off_dx.empty()) {                  // no interaction list at this level
+      SMR_CUDA(c, cudaMemsetAsync(L.d_in, 0, L.spec_bytes, ts));
+      return SMR_OK;
+    }
+    int noff = 49;                           // tables by lattice offset (7 x 7 grid)
+    int cap = f64 ? 16 : 32;                 // directions x columns staged per CTA
+    int RCt = std::min(R, cap);
+    int KC = std::max(1, cap / RCt);
+    int nkch = (L.K + KC - 1) / KC;
+    int nrct = (R + RCt - 1) / RCt;
+    size_t sm = ((size_t)64 * KC * 4 * RCt + (size_t)std::max(noff, 1) * KC) * sizeof(V) +
+                (64 + 16 + 16) * sizeof(int) + 16 * 27 * sizeof(int2);
+    cudaFuncSetAttribute(k_translate<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    pbeg(c, ts, "translate", s,
+         2.0 * L.nbox * L.K * 4 * R_ * es + (double)L.off_dx.size() * L.K * es,
+         8.0 * L.il_src.size() * L.K * 4 * R_);
+    // single right-hand side: 8x8-tile register-blocked kernel, except on
+    // levels whose few boxes would leave most of one 8x8 tile idle (or as tuned)
+    const int tv = (R == 1) ? L.tune_tr[f64 ? 0 : 1] : 0;
+    const bool few = (tv == 4) || (tv == 0 && R == 1 && L.nbox <= 64);
+    const bool use8 = (tv == 0) ? (R == 1 && !(L.ntile8_ne == 1 && L.nbox < 32)) : (tv != 3);
+    if (few) {
+      const int TG = 8;
+      dim3 g((unsigned)(((long long)L.K * Part<T>::NT + 255) / 256), (unsigned)((L.nbox + TG - 1) / TG));
+      k_translate_few<T><<<g, 256, 0, ts>>>(L.K, L.nbox, TG, L.d_il_ptr, L.d_il_pk,
+                                             (const V*)(f64 ? (void*)L.d_T64 : (void*)L.d_T32), (const V*)L.d_out,
+                                             (V*)L.d_in);
+    } else if (use8) {
+      // direction chunk: 16 (FP32) or 8 (FP64) directions, halved by the tuner
+      const bool halfc = (tv == 2);
+      int KC1 = (f64 ? 8 : 16) / (halfc ? 2 : 1);
+      int nk1 = (L.K + KC1 - 1) / KC1;
+      // FP32 tables are staged as 16-byte (t_r, t_r, -t_i, t_i) entries
+      size_t sm1 = ((size_t)144 * KC1 * 4) * sizeof(V) + (size_t)49 * KC1 * (f64 ? sizeof(V) : 16) +
+                   (144 + 64) * sizeof(int);
+      auto kt = halfc ? k_translate1<T, (sizeof(T) == 8 ? 4 : 8)> : k_translate1<T, (sizeof(T) == 8 ? 8 : 16)>;
+      cudaFuncSetAttribute(kt, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      kt<<<(unsigned)(L.ntile8_ne * nk1), 16 * KC1 * Part<T>::NT, sm1, ts>>>(
+          L.K, L.ntile8_x, L.ntile8_ne, L.d_tiles8, L.map_x0, L.map_y0, L.map_w, L.map_h, L.d_boxmap,
+          (const V*)(f64 ? (void*)L.d_T64 : (void*)L.d_T32), (const V*)L.d_out, (V*)L.d_in);
+    } else {
+      k_translate<T><<<(unsigned)(L.ntile_ne * nkch * nrct), 256, sm, ts>>>(
+          L.K, R, RCt, KC, L.ntile_x, L.ntile_ne, L.d_tiles, L.map_x0, L.map_y0, L.map_w, L.map_h, noff,
+          L.d_boxmap, L.d_offid,
+          (const V*)(f64 ? (void*)L.d_T64 : (void*)L.d_T32), (const V*)L.d_out, (V*)L.d_in);
+    }
+    SMR_LAUNCH(c);
+    pend(c, ts);
+    return SMR_OK;
+  };
+  auto fork_translate = [&](int s) -> int {
+    SMR_CUDA(c, cudaEventRecord(sd->eout[s], st));
+    SMR_CUDA(c, cudaStreamWaitEvent(sd->tr, sd->eout[s], 0));
+    int rc = translate(s, sd->tr);
+    if (rc) return rc;
+    SMR_CUDA(c, cudaEventRecord(sd->etr[s], sd->tr));
+    return SMR_OK;
+  };
   // aggregation
   {
     int nkc = (L0.K + 63) / 64;
@@ -1271,6 +1338,10 @@ static int far_impl(Ctx* c, int R, const double2* x, double2* y, bool accumulate
   }
   // upward: separable interpolation, theta then phi (+ shift + child sum)
   for (int s = 0; s + 1 < c->nlev; ++s) {
+    if (sd) {
+      int rc = fork_translate(s);              // level s's outgoing spectra are complete
+      if (rc) return rc;
+    }
     Level &Lc = c->lev[s], &Lp = c->lev[s + 1];
     pbeg(c, st, "interpolate", s,
          ((double)Lc.nbox * Lc.K + (double)Lp.nbox * Lp.K) * 4 * R_ * es + 4.0 * Lp.K * es,
@@ -1328,60 +1399,22 @@ static int far_impl(Ctx* c, int R, const double2* x, double2* y, bool accumulate
     SMR_LAUNCH(c);
     pend(c, st);
   }
-  // translation at every level
-  for (int s = 0; s < c->nlev; ++s) {
-    Level& L = c->lev[s];
-    if (L.off_dx.empty()) {                  // no interaction list at this level
-      SMR_CUDA(c, cudaMemsetAsync(L.d_in, 0, L.spec_bytes, st));
-      continue;
+  if (sd) {
+    int rc = fork_translate(c->nlev - 1);      // the top level
+    if (rc) return rc;
+  } else {
+    for (int s = 0; s < c->nlev; ++s) {
+      int rc = translate(s, st);
+      if (rc) return rc;
     }
-    int noff = 49;                           // tables by lattice offset (7 x 7 grid)
-    int cap = f64 ? 16 : 32;                 // directions x columns staged per CTA
-    int RCt = std::min(R, cap);
-    int KC = std::max(1, cap / RCt);
-    int nkch = (L.K + KC - 1) / KC;
-    int nrct = (R + RCt - 1) / RCt;
-    size_t sm = ((size_t)64 * KC * 4 * RCt + (size_t)std::max(noff, 1) * KC) * sizeof(V) +
-                (64 + 16 + 16) * sizeof(int) + 16 * 27 * sizeof(int2);
-    cudaFuncSetAttribute(k_translate<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    pbeg(c, st, "translate", s,
-         2.0 * L.nbox * L.K * 4 * R_ * es + (double)L.off_dx.size() * L.K * es,
-         8.0 * L.il_src.size() * L.K * 4 * R_);
-    // single right-hand side: 8x8-tile register-blocked kernel, except on
-    // levels whose few boxes would leave most of one 8x8 tile idle (or as tuned)
-    const int tv = (R == 1) ? L.tune_tr[f64 ? 0 : 1] : 0;
-    const bool few = (tv == 4) || (tv == 0 && R == 1 && L.nbox <= 64);
-    const bool use8 = (tv == 0) ? (R == 1 && !(L.ntile8_ne == 1 && L.nbox < 32)) : (tv != 3);
-    if (few) {
-      const int TG = 8;
-      dim3 g((unsigned)(((long long)L.K * Part<T>::NT + 255) / 256), (unsigned)((L.nbox + TG - 1) / TG));
-      k_translate_few<T><<<g, 256, 0, st>>>(L.K, L.nbox, TG, L.d_il_ptr, L.d_il_pk,
-                                             (const V*)(f64 ? (void*)L.d_T64 : (void*)L.d_T32), (const V*)L.d_out,
-                                             (V*)L.d_in);
-    } else if (use8) {
-      // direction chunk: 16 (FP32) or 8 (FP64) directions, halved by the tuner
-      const bool halfc = (tv == 2);
-      int KC1 = (f64 ? 8 : 16) / (halfc ? 2 : 1);
-      int nk1 = (L.K + KC1 - 1) / KC1;
-      // FP32 tables are staged as 16-byte (t_r, t_r, -t_i, t_i) entries
-      size_t sm1 = ((size_t)144 * KC1 * 4) * sizeof(V) + (size_t)49 * KC1 * (f64 ? sizeof(V) : 16) +
-                   (144 + 64) * sizeof(int);
-      auto kt = halfc ? k_translate1<T, (sizeof(T) == 8 ? 4 : 8)> : k_translate1<T, (sizeof(T) == 8 ? 8 : 16)>;
-      cudaFuncSetAttribute(kt, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-      kt<<<(unsigned)(L.ntile8_ne * nk1), 16 * KC1 * Part<T>::NT, sm1, st>>>(
-          L.K, L.ntile8_x, L.ntile8_ne, L.d_tiles8, L.map_x0, L.map_y0, L.map_w, L.map_h, L.d_boxmap,
-          (const V*)(f64 ? (void*)L.d_T64 : (void*)L.d_T32), (const V*)L.d_out, (V*)L.d_in);
-    } else {
-      k_translate<T><<<(unsigned)(L.ntile_ne * nkch * nrct), 256, sm, st>>>(
-          L.K, R, RCt, KC, L.ntile_x, L.ntile_ne, L.d_tiles, L.map_x0, L.map_y0, L.map_w, L.map_h, noff,
-          L.d_boxmap, L.d_offid,
-          (const V*)(f64 ? (void*)L.d_T64 : (void*)L.d_T32), (const V*)L.d_out, (V*)L.d_in);
-    }
-    SMR_LAUNCH(c);
-    pend(c, st);
   }
   // downward: separable adjoint, phi-transpose then theta-transpose (accumulates)
   for (int s = c->nlev - 2; s >= 0; --s) {
+    if (sd) {
+      // the parent level's incoming spectra and this level's translation
+      SMR_CUDA(c, cudaStreamWaitEvent(st, sd->etr[s + 1], 0));
+      SMR_CUDA(c, cudaStreamWaitEvent(st, sd->etr[s], 0));
+    }
     Level &Lc = c->lev[s], &Lp = c->lev[s + 1];
     pbeg(c, st, "anterpolate", s,
          ((double)Lp.nbox * Lp.K + 2.0 * Lc.nbox * Lc.K) * 4 * R_ * es + 4.0 * Lp.K * es,
@@ -1442,6 +1475,8 @@ static int far_impl(Ctx* c, int R, const double2* x, double2* y, bool accumulate
     pend(c, st);
   }
   // receive
+  if (sd) SMR_CUDA(c, cudaStreamWaitEvent(st, sd->etr[0], 0));
+  if (c->near_ev) SMR_CUDA(c, cudaStreamWaitEvent(st, c->near_ev, 0));
   {
     int thr = c->npsi * 8;
     size_t sm = ((size_t)32 * 2 * c->npsi + 32 * 16 * 4) * sizeof(V);
@@ -1662,6 +1697,59 @@ static void use_lane(Ctx* c, int j) {
 
 int lanes_for(const Ctx* c, int R) { return c->prof ? 1 : std::max(1, std::min(R, c->n_lanes)); }
 
+// Side streams and events of lanes 0 .. n-1 for the overlapped product
+// (created outside graph capture, kept until the context goes).
+int ensure_side(Ctx* c, int n) {
+  if (!c->overlap) return SMR_OK;
+  if ((int)c->side.size() < n) c->side.resize(n);
+  for (int j = 0; j < n; ++j) {
+    Ctx::Side& d = c->side[j];
+    if (d.tr) continue;
+    SMR_CUDA(c, cudaStreamCreateWithFlags(&d.tr, cudaStreamNonBlocking));
+    SMR_CUDA(c, cudaStreamCreateWithFlags(&d.nr, cudaStreamNonBlocking));
+    SMR_CUDA(c, cudaEventCreateWithFlags(&d.ex, cudaEventDisableTiming));
+    SMR_CUDA(c, cudaEventCreateWithFlags(&d.enear, cudaEventDisableTiming));
+    d.eout.assign(32, nullptr);
+    d.etr.assign(32, nullptr);
+    for (int s = 0; s < 32; ++s) {
+      SMR_CUDA(c, cudaEventCreateWithFlags(&d.eout[s], cudaEventDisableTiming));
+      SMR_CUDA(c, cudaEventCreateWithFlags(&d.etr[s], cudaEventDisableTiming));
+    }
+  }
+  return SMR_OK;
+}
+
+void free_side(Ctx* c) {
+  for (auto& d : c->side) {
+    if (d.tr) cudaStreamDestroy(d.tr);
+    if (d.nr) cudaStreamDestroy(d.nr);
+    if (d.ex) cudaEventDestroy(d.ex);
+    if (d.enear) cudaEventDestroy(d.enear);
+    for (auto e : d.eout) if (e) cudaEventDestroy(e);
+    for (auto e : d.etr) if (e) cudaEventDestroy(e);
+  }
+  c->side.clear();
+}
+
+// The near product of lane j: on the lane's side stream after an event on
+// st (x and its FP32 copy ready), with c->near_ev for the receive to wait on;
+// on st itself when the product does not overlap.
+static int near_step(Ctx* c, int R, int prec, const double2* x, double2* y, cudaStream_t st, int j) {
+  c->near_ev = nullptr;
+  if (!c->overlap || c->prof || j >= (int)c->side.size() || !c->side[j].nr) return run_near(c, R, prec, x, y, st);
+  Ctx::Side& d = c->side[j];
+  SMR_CUDA(c, cudaEventRecord(d.ex, st));
+  SMR_CUDA(c, cudaStreamWaitEvent(d.nr, d.ex, 0));
+  int rc = run_near(c, R, prec, x, y, d.nr);
+  SMR_CUDA(c, cudaEventRecord(d.enear, d.nr));
+  if (rc) {
+    SMR_CUDA(c, cudaStreamWaitEvent(st, d.enear, 0));   // joined even on failure
+    return rc;
+  }
+  c->near_ev = d.enear;
+  return SMR_OK;
+}
+
 // y = Z x for R right-hand sides [N][R].  FP32 products with several
 // right-hand sides run column by column on the single right-hand-side kernels
 // (16-byte parts, tensor-core aggregation and receive), which are faster per
@@ -1672,15 +1760,19 @@ int lanes_for(const Ctx* c, int R) { return c->prof ? 1 : std::max(1, std::min(R
 // holds n_lanes independent chains of single-column products.
 int run_product(Ctx* c, int R, int prec, const double2* x, double2* y, cudaStream_t st) {
   if (!split_columns(c, R, prec)) {
-    int rc = prep_x32(c, R, prec, x, st);
-    if (!rc) rc = run_near(c, R, prec, x, y, st);
+    int rc = ensure_side(c, 1);
+    c->cur_side = 0;
+    if (!rc) rc = prep_x32(c, R, prec, x, st);
+    if (!rc) rc = near_step(c, R, prec, x, y, st, 0);
     if (!rc) rc = run_far(c, R, prec, x, y, true, st);
+    c->near_ev = nullptr;
     c->x32_of = nullptr;                        // the FP32 copy lives for one product only
     return rc;
   }
   const int nl = lanes_for(c, R);
   int rc = ensure_split(c, R);
   if (!rc) rc = ensure_lanes(c, nl);
+  if (!rc) rc = ensure_side(c, nl);
   if (rc) return rc;
   const long long n = 2LL * c->npsi * c->p;
   double2* xs = c->d_split;
@@ -1697,11 +1789,14 @@ int run_product(Ctx* c, int R, int prec, const double2* x, double2* y, cudaStrea
     const int j = r % nl;
     cudaStream_t sj = j ? c->lanes[j].s : st;
     use_lane(c, j);
+    c->cur_side = j;
     rc = prep_x32(c, 1, prec, xs + (size_t)r * n, sj);
-    if (!rc) rc = run_near(c, 1, prec, xs + (size_t)r * n, ys + (size_t)r * n, sj);
+    if (!rc) rc = near_step(c, 1, prec, xs + (size_t)r * n, ys + (size_t)r * n, sj, j);
     if (!rc) rc = far_impl<float>(c, 1, xs + (size_t)r * n, ys + (size_t)r * n, true, sj);
+    c->near_ev = nullptr;
   }
   use_lane(c, 0);
+  c->cur_side = 0;
   c->x32_of = nullptr;
   // every forked lane is joined, also after an error, so that a capture ends cleanly
   for (int j = 1; j < nl; ++j) {
@@ -1737,6 +1832,7 @@ int run_matvec_graph(Ctx* c, int R, int prec, const double2* x, double2* y, cuda
   int rc = ensure_spectra(c, split ? 1 : R, prec);
   if (!rc && split) rc = ensure_split(c, R);
   if (!rc && split) rc = ensure_lanes(c, lanes_for(c, R));
+  if (!rc) rc = ensure_side(c, split ? lanes_for(c, R) : 1);
   if (rc) return rc;
   if (!c->capture_stream) SMR_CUDA(c, cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking));
   cudaStream_t cs = c->capture_stream;

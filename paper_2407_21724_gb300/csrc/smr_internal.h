@@ -337,6 +337,17 @@ struct Ctx {
     cudaEvent_t ev = nullptr;             // end of the lane's columns
   };
   std::vector<Lane> lanes;
+  // Overlapped product (smr_set_overlap): per lane a side stream for the
+  // translations, one for the near product, and the events that order them
+  struct Side {
+    cudaStream_t tr = nullptr, nr = nullptr;
+    cudaEvent_t ex = nullptr, enear = nullptr;
+    std::vector<cudaEvent_t> eout, etr;   // per level: outgoing spectra ready, translation done
+  };
+  std::vector<Side> side;
+  bool overlap = true;
+  int cur_side = 0;                       // the side set far_impl uses
+  cudaEvent_t near_ev = nullptr;          // the receive waits for it when set
   int n_lanes = 4;                        // columns in flight (smr_set_column_lanes, smr_autotune)
   cudaEvent_t lane_fork = nullptr;
   // cluster block-Jacobi preconditioner (k_cluster.cu): members [ncl][4]
@@ -450,6 +461,8 @@ void free_clusters(Ctx* c);
 // column lanes of split FP32 products (buffers allocated outside graph capture)
 int ensure_lanes(Ctx* c, int nl);
 void free_lanes(Ctx* c);
+int ensure_side(Ctx* c, int n);
+void free_side(Ctx* c);
 // tensor-core receive and aggregation (k_tc.cu)
 int build_tc(Ctx* c);
 bool tc_receive_ok(const Ctx* c, int R);

@@ -119,6 +119,7 @@ _SIGS = {
     "smr_sync": (C.c_int, [_P, _P]),
     "smr_set_wait_limit": (C.c_int, [_P, C.c_longlong]),
     "smr_set_column_lanes": (C.c_int, [_P, C.c_int]),
+    "smr_set_overlap": (C.c_int, [_P, C.c_int]),
     "smr_precond_cluster": (C.c_int, [_P, C.c_int, _P, _P, C.c_int, _P]),
     "smr_set_variant": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_int]),
 }
@@ -366,6 +367,11 @@ def smr_precond_cluster(ctx, r, z, precision=SMR_PREC_FP64, R=None, stream=None)
     """z = (2 x 2 cluster block-Jacobi matrix)^-1 r."""
     R = R if R is not None else _R(r, smr_info(ctx)["n_unknowns"])
     _check(ctx, lib().smr_precond_cluster(ctx, R, _ptr(r), _ptr(z), precision, _stream(stream, r)))
+
+
+def smr_set_overlap(ctx, enable):
+    """Overlap the near product and the translations with the rest (1) or not (0)."""
+    _check(ctx, lib().smr_set_overlap(ctx, int(bool(enable))))
 
 
 def smr_set_column_lanes(ctx, lanes):

@@ -483,6 +483,31 @@ def test_cluster_preconditioner(rnd):
     assert its[(smr.SMR_PREC_FP64, smr.SMR_PRECOND_CLUSTER)] < its[(smr.SMR_PREC_FP64, smr.SMR_PRECOND_BLOCKDIAG)]
 
 
+def test_overlap_is_bit_identical(rnd):
+    """The overlapped product (near product and translations on side
+    streams, ordered by events) gives bit for bit the ordered product, in
+    both precisions, directly and through graphs, for one column and for
+    several (column lanes)."""
+    n = rnd.info["n_unknowns"]
+    try:
+        for R in (1, 5):
+            x = np.stack([crandn(n, 60 + r) for r in range(R)], axis=1).reshape(-1)
+            xd = torch.from_numpy(x).cuda()
+            ref, y = torch.empty_like(xd), torch.empty_like(xd)
+            for prec in (smr.SMR_PREC_FP64, smr.SMR_PREC_FP32):
+                smr.smr_set_overlap(rnd.ctx, 0)
+                smr.smr_matvec(rnd.ctx, xd, ref, prec, R=R)
+                torch.cuda.synchronize()
+                smr.smr_set_overlap(rnd.ctx, 1)
+                for graph in (False, True, True):
+                    y.fill_(float("nan"))
+                    (smr.smr_matvec_graph if graph else smr.smr_matvec)(rnd.ctx, xd, y, prec, R=R)
+                    torch.cuda.synchronize()
+                    assert torch.equal(y, ref), (R, prec, graph)
+    finally:
+        smr.smr_set_overlap(rnd.ctx, 1)
+
+
 def test_column_lanes_are_bit_identical(rnd):
     """FP32 products with R > 1 deal their columns to lanes with their own
     buffers and streams: any lane count gives bit for bit the product of one
