@@ -256,8 +256,9 @@ int smr_set_tensor_cores(smr_ctx* ctx, int enable);
 /* Times the launch variants of the product for one right-hand side in
  * `precision` on this scene and keeps the fastest for later products (no
  * counterpart in the paper).  Per level: translation with 8x8 target tiles
- * and the full or half direction chunk, 4x4 tiles, or threads along the
- * directions (levels of at most 1024 boxes); interpolation by the staged
+ * and the full or half direction chunk, 4x4 tiles, threads along the
+ * directions (levels of at most 1024 boxes), or one CTA per direction chunk
+ * over the whole level (at most 256 boxes); interpolation by the staged
  * kernel (FP32: child theta-row bands bulk-copied into shared memory) or by
  * the gather kernel with the full or half theta-row tile; anterpolation by
  * the staged kernel (FP32, where its tile fits) or by the gather kernel with
@@ -508,7 +509,9 @@ int smr_copy_level(smr_ctx* ctx, int level, int kind, double* out, size_t n_doub
  * for one level (0 .. n_levels - 1) or every level (-1), for products in
  * `precision` with one right-hand side:
  *  SMR_STEP_TRANSLATE: 0 built-in rule, 1 / 2 8x8 target tiles with the full
- *    / half direction chunk, 3 4x4 tiles, 4 threads along the directions;
+ *    / half direction chunk, 3 4x4 tiles, 4 threads along the directions, 5
+ *    one CTA per direction chunk over every box of the level (levels of at
+ *    most a few hundred boxes: each source spectrum read once);
  *  SMR_STEP_INTERPOLATE (into the parent of `level`): 0 built-in rule (in
  *    FP32 the staged kernel, child theta-row bands bulk-copied into shared
  *    memory, where its tile fits), 1 / 2 the gather kernel with the full /

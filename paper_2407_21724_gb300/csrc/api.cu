@@ -1252,7 +1252,7 @@ int smr_set_variant(smr_ctx* h, int step, int level, int precision, int variant)
     return fail(c, SMR_E_INVALID_ARG, "precision must be SMR_PREC_FP64 or SMR_PREC_FP32");
   if (level < -1 || level >= c->nlev) return fail(c, SMR_E_INVALID_ARG, "level out of range");
   const int q = precision == SMR_PREC_FP64 ? 0 : 1;
-  const bool ok = (step == SMR_STEP_TRANSLATE && variant >= 0 && variant <= 4) ||
+  const bool ok = (step == SMR_STEP_TRANSLATE && variant >= 0 && variant <= 5) ||
                   (step == SMR_STEP_INTERPOLATE && variant >= 0 && variant <= 2) ||
                   (step == SMR_STEP_ANTERPOLATE && (variant >= 0 && variant <= 2 || variant == 4 || variant == 5));
   if (!ok) return fail(c, SMR_E_INVALID_ARG, "unknown step or variant");
@@ -1481,18 +1481,18 @@ int smr_autotune(smr_ctx* h, int R, int precision, void* stream) {
   SMR_CUDA(c, cudaMemsetAsync(x, 0, n * sizeof(double2), (cudaStream_t)stream));
   std::map<std::pair<std::string, int>, double> t;
   // translation: 8x8 tiles (full, half direction chunk) and 4x4 tiles
-  std::vector<std::vector<double>> ttr(c->nlev, std::vector<double>(5, 1e30));
+  std::vector<std::vector<double>> ttr(c->nlev, std::vector<double>(6, 1e30));
   std::vector<std::vector<double>> tip(c->nlev, std::vector<double>(3, 1e30));
   std::vector<std::vector<double>> tan_(c->nlev, std::vector<double>(6, 1e30));
   const int anv[6] = {0, 0, 1, 2, 4, 5};       // anterpolation variant timed in trial v
   double agg[2] = {1e30, 1e30}, rec[2] = {1e30, 1e30}, nea[2] = {1e30, 1e30};
   const int agg0 = c->tune_tc_agg, rec0 = c->tune_tc_rec, nea0 = c->tune_tc_near;
-  // trial 5 times the per-parent FP32 anterpolation with the other steps at
-  // their first variants
-  for (int v = 1; v <= (q == 1 ? 5 : 4); ++v) {
+  // trial 5 times the per-parent FP32 anterpolation and the whole-level
+  // translation (levels of at most 256 boxes), the rest at their first variants
+  for (int v = 1; v <= 5; ++v) {
     // variant 4 (few-box kernel) only where a level has at most 1024 boxes
     for (auto& L : c->lev) {
-      L.tune_tr[q] = (v == 5 || (v == 4 && L.nbox > 1024)) ? 1 : v;
+      L.tune_tr[q] = (v == 4 && L.nbox > 1024) || (v == 5 && L.nbox > 256) ? 1 : v;
       // interpolation: the built-in rule (staged kernel in FP32), k_interp1
       // with the full or the half theta-row tile
       L.tune_ip[q] = (v == 2) ? 2 : (v == 3 ? 1 : 0);
@@ -1520,7 +1520,7 @@ int smr_autotune(smr_ctx* h, int R, int precision, void* stream) {
   for (int s = 0; s < c->nlev; ++s) {
     Level& L = c->lev[s];
     int bv = 1;
-    for (int v = 2; v <= 4; ++v)
+    for (int v = 2; v <= 5; ++v)
       if (ttr[s][v] < ttr[s][bv]) bv = v;
     L.tune_tr[q] = rc ? 0 : bv;
     int bi = 0;

@@ -746,6 +746,51 @@ __global__ void __launch_bounds__(256) k_translate_few(int K, int nbox, int TG, 
   }
 }
 
+// Whole coarse level per CTA, one right-hand side: a CTA takes a chunk of
+// KCH directions of every box of the level (at most a few hundred boxes),
+// stages their outgoing spectra and the chunk of the 49 offset tables in
+// shared memory, and computes every target's sum from there, so each source
+// spectrum is read from memory once instead of once per target that lists
+// it.  Tasks are (target, direction, 16-byte part), the parts of consecutive
+// directions on consecutive threads.
+template <typename T>
+__global__ void __launch_bounds__(256) k_translate_lvl(int K, int nbox, int KCH, const int* __restrict__ il_ptr,
+                                                       const int* __restrict__ il_pk,
+                                                       const typename CV<T>::V* __restrict__ Tg,
+                                                       const typename CV<T>::V* __restrict__ out,
+                                                       typename CV<T>::V* __restrict__ in) {
+  typedef typename CV<T>::V V;
+  typedef Part<T> P;
+  typedef typename P::H H;
+  constexpr int NT = P::NT;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* S = reinterpret_cast<V*>(smem_raw);                 // [nbox][KCH][4]
+  V* Ts = S + (size_t)nbox * KCH * 4;                    // [49][KCH]
+  const int k0 = blockIdx.x * KCH, kn = min(KCH, K - k0);
+  // stage: every box's 4 fields for the chunk, and the tables
+  for (int i = threadIdx.x; i < nbox * KCH * NT; i += blockDim.x) {
+    const int b = i / (KCH * NT), r = i - b * (KCH * NT), kl = r / NT, h = r - kl * NT;
+    H v = P::zero();
+    if (kl < kn) v = ldp<T>(out, (size_t)b * K + k0 + kl, h);
+    stp<T>(S, (size_t)b * KCH + kl, h, v);
+  }
+  for (int i = threadIdx.x; i < 49 * KCH; i += blockDim.x) {
+    const int row = i / KCH, kl = i - row * KCH;
+    Ts[i] = kl < kn ? Tg[(size_t)row * K + k0 + kl] : czero<V>();
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < nbox * KCH * NT; i += blockDim.x) {
+    const int b = i / (KCH * NT), r = i - b * (KCH * NT), kl = r / NT, h = r - kl * NT;
+    if (kl >= kn) continue;
+    H acc = P::zero();
+    for (int e = il_ptr[b]; e < il_ptr[b + 1]; ++e) {
+      const int pk = il_pk[e];
+      P::cfma(acc, Ts[(pk & 63) * KCH + kl], ldp<T>(S, (size_t)(pk >> 6) * KCH + kl, h));
+    }
+    stp<T>(in, (size_t)b * K + k0 + kl, h, acc);
+  }
+}
+
 // ------------------------------------------------------------------ anterpolation (separable adjoint)
 // phi-transposed pass (one warp per row (c, tp)), child c in quadrant q of parent B:
 //   Gt[c][tp][j][f][r] = w_theta_p[tp] sum_{(jp, w) in Pt(j)} w conj(shift[q][tp, jp]) in[B][tp][jp][f][r]
@@ -1222,6 +1267,26 @@ int ensure_spectra(Ctx* c, int R, int prec) {
   return SMR_OK;
 }
 
+// Direction chunk of the whole-level translation: the largest power of two
+// up to 32 whose staged spectra and tables fit in 96 KB (0: none fits).
+int translate_lvl_chunk(int nbox, size_t vbytes) {
+  for (int kch = 32; kch >= 4; kch /= 2)
+    if (((size_t)nbox * kch * 4 + (size_t)49 * kch) * vbytes <= 96 * 1024) return kch;
+  return 0;
+}
+
+bool translate_lvl_ok(Ctx* c, int s, bool f64) {
+  const Level& L = c->lev[s];
+  if (L.off_dx.empty() || !L.d_il_pk || translate_lvl_chunk(L.nbox, f64 ? 16 : 8) == 0) return false;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_translate_lvl<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_translate_lvl<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr = true;
+  }
+  return true;
+}
+
 // The per-parent FP32 anterpolation needs the 8-tap tables and its four
 // quadrants' phi-pass rows within the fixed shared-memory ceiling.
 bool anterp4_ok(Ctx* c, int s) {
@@ -1275,6 +1340,16 @@ static int far_impl(Ctx* c, int R, const double2* x, double2* y, bool accumulate
     // single right-hand side: 8x8-tile register-blocked kernel, except on
     // levels whose few boxes would leave most of one 8x8 tile idle (or as tuned)
     const int tv = (R == 1) ? L.tune_tr[f64 ? 0 : 1] : 0;
+    if (tv == 5 && translate_lvl_ok(c, s, f64)) {
+      const int KCH = translate_lvl_chunk(L.nbox, sizeof(V));
+      const size_t sml = ((size_t)L.nbox * KCH * 4 + (size_t)49 * KCH) * sizeof(V);
+      k_translate_lvl<T><<<(unsigned)((L.K + KCH - 1) / KCH), 256, sml, ts>>>(
+          L.K, L.nbox, KCH, L.d_il_ptr, L.d_il_pk, (const V*)(f64 ? (void*)L.d_T64 : (void*)L.d_T32),
+          (const V*)L.d_out, (V*)L.d_in);
+      SMR_LAUNCH(c);
+      pend(c, ts);
+      return SMR_OK;
+    }
     const bool few = (tv == 4) || (tv == 0 && R == 1 && L.nbox <= 64);
     const bool use8 = (tv == 0) ? (R == 1 && !(L.ntile8_ne == 1 && L.nbox < 32)) : (tv != 3);
     if (few) {
