@@ -515,7 +515,8 @@ int smr_copy_level(smr_ctx* ctx, int level, int kind, double* out, size_t n_doub
  *  SMR_STEP_INTERPOLATE (into the parent of `level`): 0 built-in rule (in
  *    FP32 the staged kernel, child theta-row bands bulk-copied into shared
  *    memory, where its tile fits), 1 / 2 the gather kernel with the full /
- *    half theta-row tile;
+ *    half theta-row tile, 3 the staged kernel whose threads produce two
+ *    neighbouring parent columns from one window of child columns (FP32);
  *  SMR_STEP_ANTERPOLATE (into `level`): 0 built-in rule (the gather kernel),
  *    1 half its column chunk, 2 256-thread CTAs, 4 the staged kernel (FP32,
  *    parent band bulk-copied, where its tile fits), 5 the gather kernel with

@@ -204,6 +204,13 @@ int build_interp(Ctx* c, Level& C, const Level& P) {
     }
     C.ip2_TR = TR;
     C.ip2_nrt = (P.nth + TR - 1) / TR;
+    // paired phi pass: the windows of columns 2m and 2m + 1 start at most one
+    // column apart and five padded columns from the first stay in the row
+    C.ip2_pair = (P.nph % 2 == 0);
+    for (int m = 0; 2 * m + 1 < P.nph && C.ip2_pair; ++m) {
+      const int ja = psrc[4 * (2 * m) + 1], jb = psrc[4 * (2 * m + 1) + 1];
+      C.ip2_pair = (jb - ja == 0 || jb - ja == 1) && ja <= C.nph - 2;
+    }
     C.ip2_NCP = ncp;
     C.ip2_RPT = (TR + ng - 1) / ng;
     std::vector<int> band(2 * C.ip2_nrt);
@@ -1253,7 +1260,7 @@ int smr_set_variant(smr_ctx* h, int step, int level, int precision, int variant)
   if (level < -1 || level >= c->nlev) return fail(c, SMR_E_INVALID_ARG, "level out of range");
   const int q = precision == SMR_PREC_FP64 ? 0 : 1;
   const bool ok = (step == SMR_STEP_TRANSLATE && variant >= 0 && variant <= 5) ||
-                  (step == SMR_STEP_INTERPOLATE && variant >= 0 && variant <= 2) ||
+                  (step == SMR_STEP_INTERPOLATE && variant >= 0 && variant <= 3) ||
                   (step == SMR_STEP_ANTERPOLATE && (variant >= 0 && variant <= 2 || variant == 4 || variant == 5));
   if (!ok) return fail(c, SMR_E_INVALID_ARG, "unknown step or variant");
   for (int s = (level < 0 ? 0 : level); s < (level < 0 ? c->nlev : level + 1); ++s) {
@@ -1482,7 +1489,7 @@ int smr_autotune(smr_ctx* h, int R, int precision, void* stream) {
   std::map<std::pair<std::string, int>, double> t;
   // translation: 8x8 tiles (full, half direction chunk) and 4x4 tiles
   std::vector<std::vector<double>> ttr(c->nlev, std::vector<double>(6, 1e30));
-  std::vector<std::vector<double>> tip(c->nlev, std::vector<double>(3, 1e30));
+  std::vector<std::vector<double>> tip(c->nlev, std::vector<double>(4, 1e30));
   std::vector<std::vector<double>> tan_(c->nlev, std::vector<double>(6, 1e30));
   const int anv[6] = {0, 0, 1, 2, 4, 5};       // anterpolation variant timed in trial v
   double agg[2] = {1e30, 1e30}, rec[2] = {1e30, 1e30}, nea[2] = {1e30, 1e30};
@@ -1495,7 +1502,7 @@ int smr_autotune(smr_ctx* h, int R, int precision, void* stream) {
       L.tune_tr[q] = (v == 4 && L.nbox > 1024) || (v == 5 && L.nbox > 256) ? 1 : v;
       // interpolation: the built-in rule (staged kernel in FP32), k_interp1
       // with the full or the half theta-row tile
-      L.tune_ip[q] = (v == 2) ? 2 : (v == 3 ? 1 : 0);
+      L.tune_ip[q] = (v == 2) ? 2 : (v == 3 ? 1 : (v == 5 && q == 1 ? 3 : 0));
       L.tune_an[q] = anv[v];
     }
     c->tune_tc_agg = c->tune_tc_rec = c->tune_tc_near = (v == 3) ? 0 : 1;
@@ -1524,7 +1531,7 @@ int smr_autotune(smr_ctx* h, int R, int precision, void* stream) {
       if (ttr[s][v] < ttr[s][bv]) bv = v;
     L.tune_tr[q] = rc ? 0 : bv;
     int bi = 0;
-    for (int v = 1; v <= 2; ++v)
+    for (int v = 1; v <= 3; ++v)
       if (tip[s][v] < tip[s][bi]) bi = v;
     L.tune_ip[q] = rc ? 0 : bi;
     int ba = 0;

@@ -93,7 +93,13 @@ __device__ __forceinline__ float4 lds4(const unsigned char* p) { return *reinter
 // column p - 1 mod N, p = 0 .. N + 2), so the four phi taps of a parent
 // column are four consecutive padded columns.  Rows whose theta taps are not
 // reflected through a pole read four consecutive band rows.
-template <int NCP, int RPTM>
+//
+// PAIR (one column part per thread, NCP = 1): a thread's phi pass produces
+// two neighbouring parent columns 2m, 2m + 1 from one window of five padded
+// columns (their tap windows start at the same column or one apart, the
+// parent grid being the finer one), five loads for two outputs instead of
+// eight.
+template <int NCP, int RPTM, bool PAIR = false>
 __global__ void __launch_bounds__(256, 4) k_interp2(int nthC, int nphC, int nthP, int nphP, int TR, int nrt, int BR,
                                                     const int* __restrict__ band, const int* __restrict__ ch_ptr,
                                                     const int* __restrict__ ch_idx, const int* __restrict__ ch_quad,
@@ -140,14 +146,17 @@ __global__ void __launch_bounds__(256, 4) k_interp2(int nthC, int nphC, int nthP
   const int ngt = NC <= 256 ? 256 / NC : 1;
   const int gt = NC <= 256 ? tid / NC : 0;
   const int cpt = NC <= 256 ? tid % NC : tid, cstept = NC <= 256 ? NC : 256;
-  // phi pass: NCP column parts cp = cpp + k * cstepp, rows gp, gp + ngp, ...
+  // phi pass: NCP column parts cp = cpp + k * cstepp, rows gp, gp + ngp, ...;
+  // with PAIR, (column pair, part) units u = tid % nphP, rows gp, gp + ngp, ...
   const int NP = 2 * nphP;
-  const int ngp = NP <= 256 ? 256 / NP : 1;
-  const int gp = NP <= 256 ? tid / NP : 0;
-  const int cpp = NP <= 256 ? tid % NP : tid, cstepp = NP <= 256 ? NP : 256;
-  float4 acc[NCP][RPTM];
+  const int UN = PAIR ? nphP : NP;
+  const int ngp = UN <= 256 ? 256 / UN : 1;
+  const int gp = UN <= 256 ? tid / UN : 0;
+  const int cpp = UN <= 256 ? tid % UN : tid, cstepp = UN <= 256 ? UN : 256;
+  constexpr int NA = PAIR ? 2 : NCP;
+  float4 acc[NA][RPTM];
 #pragma unroll
-  for (int k = 0; k < NCP; ++k)
+  for (int k = 0; k < NA; ++k)
 #pragma unroll
     for (int r = 0; r < RPTM; ++r) acc[k][r] = make_float4(0.f, 0.f, 0.f, 0.f);
   __syncthreads();
@@ -200,7 +209,38 @@ __global__ void __launch_bounds__(256, 4) k_interp2(int nthC, int nphC, int nthP
       ++issued;
     }
     const float2* sh = shift + (size_t)ch_quad[e0 + e] * Kp + (size_t)tp0 * nphP;
-    if (gp < ngp) {
+    if (PAIR && gp < ngp) {
+      const int m = cpp >> 1, h = cpp & 1;
+      const int jpa = 2 * m, jpb = jpa + 1;
+      const int j0 = ph_src[4 * jpa + 1];
+      const bool d1 = ph_src[4 * jpb + 1] != j0;
+      const float4 wa = *reinterpret_cast<const float4*>(ph_w + 4 * jpa);
+      const float4 wb = *reinterpret_cast<const float4*>(ph_w + 4 * jpb);
+      const float2 a0 = make_float2(wa.x, wa.x), a1 = make_float2(wa.y, wa.y);
+      const float2 a2 = make_float2(wa.z, wa.z), a3 = make_float2(wa.w, wa.w);
+      // column b's four weights over the five-column window
+      const float b0s = d1 ? 0.f : wb.x, b1s = d1 ? wb.x : wb.y, b2s = d1 ? wb.y : wb.z;
+      const float b3s = d1 ? wb.z : wb.w, b4s = d1 ? wb.w : 0.f;
+      const float2 b0 = make_float2(b0s, b0s), b1 = make_float2(b1s, b1s), b2 = make_float2(b2s, b2s);
+      const float2 b3 = make_float2(b3s, b3s), b4 = make_float2(b4s, b4s);
+      const unsigned char* g0 = G + (uint32_t)j0 * 32u + (uint32_t)h * 16u;
+#pragma unroll
+      for (int r = 0; r < RPTM; ++r) {
+        const int tr = gp + r * ngp;
+        if (tr < ntr) {
+          const unsigned char* gr = g0 + (uint32_t)tr * growb;
+          const float4 v0 = lds4(gr), v1 = lds4(gr + 32), v2 = lds4(gr + 64), v3 = lds4(gr + 96),
+                       v4 = lds4(gr + 128);
+          float4 sa = make_float4(0.f, 0.f, 0.f, 0.f), sb = sa;
+          fma4p(sa, a0, v0); fma4p(sa, a1, v1); fma4p(sa, a2, v2); fma4p(sa, a3, v3);
+          fma4p(sb, b0, v0); fma4p(sb, b1, v1); fma4p(sb, b2, v2); fma4p(sb, b3, v3); fma4p(sb, b4, v4);
+          const float4 s2 = *reinterpret_cast<const float4*>(sh + (size_t)tr * nphP + jpa);
+          cfma4(acc[0][r], make_float2(s2.x, s2.y), sa);
+          cfma4(acc[1][r], make_float2(s2.z, s2.w), sb);
+        }
+      }
+    }
+    if (!PAIR && gp < ngp) {
 #pragma unroll
       for (int k = 0; k < NCP; ++k) {
         const int cp = cpp + k * cstepp;
@@ -239,7 +279,19 @@ __global__ void __launch_bounds__(256, 4) k_interp2(int nthC, int nphC, int nthP
     }
     return;
   }
-  if (gp < ngp) {
+  if (PAIR && gp < ngp) {
+    float4* dst = reinterpret_cast<float4*>(out + ((size_t)B * Kp + (size_t)tp0 * nphP) * 4);
+    const int m = cpp >> 1, h = cpp & 1;
+#pragma unroll
+    for (int r = 0; r < RPTM; ++r) {
+      const int tr = gp + r * ngp;
+      if (tr < ntr) {
+        dst[(size_t)tr * NP + 4 * m + h] = acc[0][r];
+        dst[(size_t)tr * NP + 4 * m + 2 + h] = acc[1][r];
+      }
+    }
+  }
+  if (!PAIR && gp < ngp) {
     float4* dst = reinterpret_cast<float4*>(out + ((size_t)B * Kp + (size_t)tp0 * nphP) * 4);
 #pragma unroll
     for (int k = 0; k < NCP; ++k) {
@@ -255,11 +307,11 @@ __global__ void __launch_bounds__(256, 4) k_interp2(int nthC, int nphC, int nthP
   }
 }
 
-template <int NCP, int RPTM>
+template <int NCP, int RPTM, bool PAIR = false>
 int launch_interp2(Ctx* c, const Level& Lc, const Level& Lp, const float2* F, float2* out, cudaStream_t st) {
   const size_t rowb = (size_t)Lc.nph * 32;
   const size_t sm = 128 + 2 * (size_t)Lc.ip2_BR * rowb + (size_t)Lc.ip2_TR * (rowb + 96) + (size_t)Lc.ip2_TR * 48;
-  auto k = k_interp2<NCP, RPTM>;
+  auto k = k_interp2<NCP, RPTM, PAIR>;
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, LV_SMEM_MAX);
   k<<<(unsigned)(Lp.nbox * Lc.ip2_nrt), 256, sm, st>>>(
       Lc.nth, Lc.nph, Lp.nth, Lp.nph, Lc.ip2_TR, Lc.ip2_nrt, Lc.ip2_BR, Lc.d_ip2_band, Lp.d_ch_ptr, Lp.d_ch_idx,
@@ -487,10 +539,21 @@ bool interp2_ok(const Ctx* c, int s) {
          Lc.ip2_RPT <= (Lc.ip2_NCP == 1 ? 6 : 8 / Lc.ip2_NCP);
 }
 
+// The paired phi pass: one column part per thread, at most three rows per
+// thread in the paired layout, and every pair's tap windows one column apart
+// at most (checked when the tables are built).
+bool interp2_pair_ok(const Ctx* c, int s) {
+  const Level &Lc = c->lev[s], &Lp = c->lev[s + 1];
+  if (Lc.ip2_NCP != 1 || !Lc.ip2_pair || Lp.nph > 256 || (Lp.nph & 1)) return false;
+  const int ngq = 256 / Lp.nph;
+  return (Lc.ip2_TR + ngq - 1) / ngq <= 3;
+}
+
 int run_interp2(Ctx* c, int s, cudaStream_t st) {
   const Level &Lc = c->lev[s], &Lp = c->lev[s + 1];
   const float2* F = (const float2*)Lc.d_out;
   float2* out = (float2*)Lp.d_out;
+  if (Lc.tune_ip[1] == 3 && interp2_pair_ok(c, s)) return launch_interp2<1, 3, true>(c, Lc, Lp, F, out, st);
   switch (Lc.ip2_NCP) {
     case 1: return launch_interp2<1, 6>(c, Lc, Lp, F, out, st);
     case 2: return launch_interp2<2, 4>(c, Lc, Lp, F, out, st);

@@ -1421,7 +1421,7 @@ static int far_impl(Ctx* c, int R, const double2* x, double2* y, bool accumulate
     pbeg(c, st, "interpolate", s,
          ((double)Lc.nbox * Lc.K + (double)Lp.nbox * Lp.K) * 4 * R_ * es + 4.0 * Lp.K * es,
          (double)Lc.nbox * Lp.nth * Lc.nph * 4 * R_ * 16.0 + (double)Lc.nbox * Lp.K * 4 * R_ * 24.0);
-    if (!f64 && R == 1 && Lc.tune_ip[1] == 0 && interp2_ok(c, s)) {
+    if (!f64 && R == 1 && (Lc.tune_ip[1] == 0 || Lc.tune_ip[1] == 3) && interp2_ok(c, s)) {
       int rc = run_interp2(c, s, st);
       pend(c, st);
       if (rc) return rc;

@@ -150,6 +150,7 @@ struct Level {
   // ip2_BR the widest band; ip2_NCP / ip2_RPT the phi-pass shape (column
   // parts and rows per thread)
   int ip2_TR = 0, ip2_nrt = 0, ip2_BR = 0, ip2_NCP = 0, ip2_RPT = 0;
+  bool ip2_pair = false;                 // paired phi pass possible (tap windows of column pairs)
   int* d_ip2_band = nullptr;
   // staged single right-hand-side FP32 anterpolation into this level
   // (k_anterp2): child theta-row tiles of an2_TI rows (even, so row pairs
@@ -477,6 +478,7 @@ int tc_check(Ctx* c);
 // staged FP32 level kernels (k_levels.cu)
 bool interp2_ok(const Ctx* c, int s);
 int run_interp2(Ctx* c, int s, cudaStream_t st);
+bool interp2_pair_ok(const Ctx* c, int s);
 bool anterp2_ok(const Ctx* c, int s);
 int run_anterp2(Ctx* c, int s, cudaStream_t st);
 

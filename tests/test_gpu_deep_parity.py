@@ -96,7 +96,7 @@ def _direct_product(d, prec):
     return yd.cpu().numpy()
 
 
-VARIANTS = [(smr.SMR_STEP_INTERPOLATE, v) for v in (0, 1, 2)] + \
+VARIANTS = [(smr.SMR_STEP_INTERPOLATE, v) for v in (0, 1, 2, 3)] + \
            [(smr.SMR_STEP_ANTERPOLATE, v) for v in (0, 1, 2, 4, 5)] + \
            [(smr.SMR_STEP_TRANSLATE, v) for v in (1, 2, 3, 4, 5)]
 
@@ -114,7 +114,7 @@ def test_deep_every_launch_variant(deep, prec):
             smr.smr_set_variant(ctx, step, -1, prec, v)
             y = _direct_product(deep, prec)
             assert rel(y, deep["y"]) < (1e-10 if prec == smr.SMR_PREC_FP64 else 2e-5), (step, v)
-            staged = (step == smr.SMR_STEP_INTERPOLATE and v == 0) or \
+            staged = (step == smr.SMR_STEP_INTERPOLATE and v in (0, 3)) or \
                 (step == smr.SMR_STEP_ANTERPOLATE and v in (4, 5)) or (step == smr.SMR_STEP_TRANSLATE and v == 5)
             if staged and prec == smr.SMR_PREC_FP32:
                 for s in range(deep["M"].tree.n_levels):
