@@ -365,6 +365,16 @@ typedef struct {
                       10x after this many iterations, the solve switches to
                       SMR_PRECOND_BLOCKDIAG from the current iterate [40]   */
   int near_sweeps;  /* SMR_PRECOND_NEAR: Jacobi sweeps, 1..8 [1]             */
+  int poly_degree;  /* 0 off, or 2..16 [0]: a polynomial in B = A M^-1 on top
+                       of `precond`, the iterations run on B p(B).  p comes
+                       from poly_degree Arnoldi steps of B started from b (in
+                       the precision the iterations use): its roots, the
+                       harmonic Ritz values (the roots of the GMRES residual
+                       polynomial, 1 - x p(x) = prod (1 - x / theta_i)), are
+                       applied in Leja order.  Each iteration then costs
+                       poly_degree products and Gram-Schmidt against fewer
+                       basis vectors.  One right-hand side only (ignored for
+                       R > 1).  Not in the paper                             */
 } smr_solve_opts;
 
 typedef struct {

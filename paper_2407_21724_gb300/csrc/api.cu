@@ -61,6 +61,8 @@ void free_scene(Ctx* c) {
   dfree(c->d_tc_rec); dfree(c->d_tc_agg); dfree(c->d_tc_perm); dfree(c->d_lpc); dfree(c->d_split);
   dfree(c->d_pcw);
   c->pcw_elems = 0;
+  dfree(c->d_polyw);
+  c->polyw_elems = 0;
   free_clusters(c);
   c->split_elems = 0;
   c->lpc_ready = false; dfree(c->d_tc_shape); dfree(c->d_tc_start); dfree(c->d_tc_count);
@@ -905,6 +907,7 @@ void smr_default_solve_opts(smr_solve_opts* o) {
   o->use_x0 = 0;
   o->fallback_iters = 40;
   o->near_sweeps = 1;
+  o->poly_degree = 0;
 }
 
 int smr_create(smr_ctx** out, const smr_opts* opts) {
@@ -1224,6 +1227,8 @@ int smr_solve(smr_ctx* h, int R, const void* b, void* x, const smr_solve_opts* o
   }
   if (o.precond == SMR_PRECOND_NEAR && (o.near_sweeps < 1 || o.near_sweeps > 8))
     return fail(c, SMR_E_INVALID_ARG, "near_sweeps must be in 1..8");
+  if (o.poly_degree < 0 || o.poly_degree == 1 || o.poly_degree > 16)
+    return fail(c, SMR_E_INVALID_ARG, "poly_degree must be 0 (off) or in 2..16");
   if (o.precond == SMR_PRECOND_LEARNED && (R != 1 || !c->lpc_ready))
     return fail(c, SMR_E_STATE, "SMR_PRECOND_LEARNED needs R = 1 and smr_nn_precond first");
   int rc = solve(c, R, (const double2*)b, (double2*)x, &o, stats, (cudaStream_t)stream);

@@ -725,6 +725,18 @@ static int apply_A(Ctx* c, int R, int prec, const double2* x, double2* y, cudaSt
   return run_product(c, R, prec, x, y, st);
 }
 
+// y += a x for a complex scalar a
+__global__ void k_caxpy(long long n, double2 a, const double2* __restrict__ x, double2* __restrict__ y) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) {
+    const double2 v = x[i];
+    double2 o = y[i];
+    o.x += a.x * v.x - a.y * v.y;
+    o.y += a.x * v.y + a.y * v.x;
+    y[i] = o;
+  }
+}
+
 __global__ void k_sweep_update(long long n, double2* __restrict__ z, const double2* __restrict__ t,
                                const double2* __restrict__ u) {
   long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -739,8 +751,163 @@ __global__ void k_sweep_update(long long n, double2* __restrict__ z, const doubl
 // SMR_PRECOND_NEAR by c->pc_sweeps Jacobi sweeps over the near field
 // (z <- z + D^-1 v - D^-1 Z_near z), the cluster block-Jacobi inverse for
 // SMR_PRECOND_CLUSTER, or a copy for SMR_PRECOND_NONE
+
+typedef std::complex<double> zc;
+
+// Eigenvalues of an upper Hessenberg complex matrix A (n x n, column-major)
+// by the shifted QR algorithm: Wilkinson shifts from the trailing 2 x 2 of
+// the active block, Givens rotations, deflation at negligible subdiagonals.
+static bool hess_eigvals(int n, std::vector<zc> A, std::vector<zc>& ev) {
+  auto a = [&](int i, int j) -> zc& { return A[(size_t)j * n + i]; };
+  ev.assign(n, zc(0, 0));
+  int hi = n - 1, iter = 0;
+  while (hi >= 0) {
+    if (hi == 0) { ev[0] = a(0, 0); break; }
+    int l = hi;
+    for (; l > 0; --l) {
+      const double sc = std::abs(a(l - 1, l - 1)) + std::abs(a(l, l));
+      if (std::abs(a(l, l - 1)) <= 1e-15 * (sc > 0 ? sc : 1.0)) { a(l, l - 1) = 0; break; }
+    }
+    if (l == hi) { ev[hi] = a(hi, hi); --hi; iter = 0; continue; }
+    if (++iter > 300) return false;
+    const zc p = a(hi - 1, hi - 1), q = a(hi - 1, hi), r = a(hi, hi - 1), t = a(hi, hi);
+    const zc tr = p + t, det = p * t - q * r, disc = std::sqrt(tr * tr / 4.0 - det);
+    const zc m1 = tr / 2.0 + disc, m2 = tr / 2.0 - disc;
+    zc mu = std::abs(m1 - t) < std::abs(m2 - t) ? m1 : m2;
+    if (iter % 11 == 10) mu = t + zc(std::abs(a(hi, hi - 1)), 0.0);   // exceptional shift
+    for (int k = l; k <= hi; ++k) a(k, k) -= mu;
+    std::vector<zc> cs(hi - l), sn(hi - l);
+    for (int k = l; k < hi; ++k) {
+      const zc x = a(k, k), y = a(k + 1, k);
+      const double rr = std::sqrt(std::norm(x) + std::norm(y));
+      const zc cc = rr > 0 ? x / rr : zc(1, 0), ss = rr > 0 ? y / rr : zc(0, 0);
+      for (int j = k; j <= hi; ++j) {                // rows k, k+1 <- G [rows]
+        const zc t1 = a(k, j), t2 = a(k + 1, j);
+        a(k, j) = std::conj(cc) * t1 + std::conj(ss) * t2;
+        a(k + 1, j) = -ss * t1 + cc * t2;
+      }
+      cs[k - l] = cc;
+      sn[k - l] = ss;
+    }
+    for (int k = l; k < hi; ++k) {                    // columns k, k+1 <- [columns] G^H
+      const zc cc = cs[k - l], ss = sn[k - l];
+      for (int i = l; i <= std::min(k + 1, hi); ++i) {
+        const zc t1 = a(i, k), t2 = a(i, k + 1);
+        a(i, k) = t1 * cc + t2 * ss;
+        a(i, k + 1) = -t1 * std::conj(ss) + t2 * std::conj(cc);
+      }
+    }
+    for (int k = l; k <= hi; ++k) a(k, k) += mu;
+  }
+  return true;
+}
+
+// Harmonic Ritz values of the d-step Arnoldi relation with the (d+1) x d
+// Hessenberg Hb (column-major, leading dimension ld): the eigenvalues of
+// H_d + |h_{d+1,d}|^2 f e_d^T with H_d^H f = e_d -- the roots of the GMRES
+// residual polynomial of degree d.
+static bool harmonic_ritz(int d, const std::vector<zc>& Hb, int ldh, std::vector<zc>& th) {
+  std::vector<zc> Hd((size_t)d * d), M((size_t)d * d), f(d, zc(0, 0));
+  for (int j = 0; j < d; ++j)
+    for (int i = 0; i < d; ++i) Hd[(size_t)j * d + i] = Hb[(size_t)j * ldh + i];
+  const zc h = Hb[(size_t)(d - 1) * ldh + d];
+  // solve H_d^H f = e_d by Gaussian elimination with partial pivoting
+  for (int j = 0; j < d; ++j)
+    for (int i = 0; i < d; ++i) M[(size_t)j * d + i] = std::conj(Hd[(size_t)i * d + j]);
+  f[d - 1] = 1.0;
+  for (int k = 0; k < d; ++k) {
+    int piv = k;
+    for (int i = k + 1; i < d; ++i)
+      if (std::abs(M[(size_t)k * d + i]) > std::abs(M[(size_t)k * d + piv])) piv = i;
+    if (std::abs(M[(size_t)k * d + piv]) == 0.0) return false;
+    if (piv != k) {
+      for (int j = 0; j < d; ++j) std::swap(M[(size_t)j * d + k], M[(size_t)j * d + piv]);
+      std::swap(f[k], f[piv]);
+    }
+    for (int i = k + 1; i < d; ++i) {
+      const zc fac = M[(size_t)k * d + i] / M[(size_t)k * d + k];
+      for (int j = k; j < d; ++j) M[(size_t)j * d + i] -= fac * M[(size_t)j * d + k];
+      f[i] -= fac * f[k];
+    }
+  }
+  for (int i = d - 1; i >= 0; --i) {
+    zc sum = f[i];
+    for (int j = i + 1; j < d; ++j) sum -= M[(size_t)j * d + i] * f[j];
+    f[i] = sum / M[(size_t)i * d + i];
+  }
+  for (int i = 0; i < d; ++i) Hd[(size_t)(d - 1) * d + i] += std::norm(h) * f[i];
+  if (!hess_eigvals(d, Hd, th)) return false;
+  for (const zc& z : th)
+    if (!std::isfinite(z.real()) || !std::isfinite(z.imag()) || std::abs(z) == 0.0) return false;
+  return true;
+}
+
+// Leja order: the largest root first, then each next root maximises the
+// product of its distances to the roots already taken.
+static void leja_order(std::vector<zc>& th) {
+  const int n = (int)th.size();
+  std::vector<zc> out;
+  std::vector<char> used(n, 0);
+  for (int k = 0; k < n; ++k) {
+    int best = -1;
+    double bs = -1e300;
+    for (int i = 0; i < n; ++i) {
+      if (used[i]) continue;
+      double sc = 0;
+      if (out.empty()) sc = std::abs(th[i]);
+      else
+        for (const zc& z : out) sc += std::log(std::max(std::abs(th[i] - z), 1e-300));
+      if (sc > bs) { bs = sc; best = i; }
+    }
+    used[best] = 1;
+    out.push_back(th[best]);
+  }
+  th = out;
+}
+
+static int apply_M(Ctx* c, int R, int prec, int precond, const double2* v, double2* z, cudaStream_t st);
+
+// z = M^-1 p(B) v with B = A M^-1 and p the polynomial preconditioner in
+// root form: 1 - x p(x) = prod_i (1 - x / theta_i), the roots in Leja order
+// (prod <- v; for each root but the last: y += prod / theta_i, prod -= B prod
+// / theta_i; y += prod / theta_last; z = M^-1 y)
+static int apply_poly(Ctx* c, int R, int prec, int precond, const double2* v, double2* z, cudaStream_t st) {
+  const long long ld = 2LL * c->npsi * c->p * R;
+  const unsigned nb = (unsigned)((ld + 255) / 256);
+  double2* prod = c->d_polyw;
+  double2* y = c->d_polyw + ld;
+  double2* t = c->d_polyw + 2 * ld;
+  double2* w = c->d_polyw + 3 * ld;
+  const auto& th = c->poly_roots;
+  const int dp = (int)th.size();
+  SMR_CUDA(c, cudaMemcpyAsync(prod, v, (size_t)ld * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+  SMR_CUDA(c, cudaMemsetAsync(y, 0, (size_t)ld * sizeof(double2), st));
+  int rc = SMR_OK;
+  for (int i = 0; i < dp && !rc; ++i) {
+    const std::complex<double> inv = 1.0 / th[i];
+    k_caxpy<<<nb, 256, 0, st>>>(ld, make_double2(inv.real(), inv.imag()), prod, y);
+    SMR_CUDA(c, cudaGetLastError());
+    if (i + 1 == dp) break;
+    rc = apply_M(c, R, prec, precond, prod, t, st);
+    if (!rc) rc = run_matvec_graph(c, R, prec, t, w, st);
+    if (!rc) {
+      k_caxpy<<<nb, 256, 0, st>>>(ld, make_double2(-inv.real(), -inv.imag()), w, prod);
+      SMR_CUDA(c, cudaGetLastError());
+      ++c->poly_mv;
+    }
+  }
+  if (!rc) rc = apply_M(c, R, prec, precond, y, z, st);
+  return rc;
+}
+
 static int apply_M(Ctx* c, int R, int prec, int precond, const double2* v, double2* z, cudaStream_t st) {
   const long long ld = 2LL * c->npsi * c->p * R;
+  if (!c->poly_roots.empty() && !c->poly_busy) {
+    c->poly_busy = true;                      // the base preconditioner inside
+    int rc = apply_poly(c, R, prec, precond, v, z, st);
+    c->poly_busy = false;
+    return rc;
+  }
   if (precond == SMR_PRECOND_NONE) {
     SMR_CUDA(c, cudaMemcpyAsync(z, v, (size_t)ld * sizeof(double2), cudaMemcpyDeviceToDevice, st));
     return SMR_OK;
@@ -829,7 +996,7 @@ static int gs_pass(Ctx* c, Work& W, int J, long long n, int R, long long ld, dou
 static int gmres_core(Ctx* c, int R, int prec, int precond, const double2* rhs, double2* d,
                       bool have_d0, const std::vector<double>& tol_col, int maxit, int restart,
                       Work& W, int* its, int* nmv, int* n_reorth, std::vector<double>& rel_out,
-                      cudaStream_t st) {
+                      cudaStream_t st, std::vector<std::complex<double>>* Hout = nullptr) {
   long long n = 2LL * c->npsi * c->p;
   long long ld = n * R;
   int m = restart;
@@ -991,6 +1158,8 @@ static int gmres_core(Ctx* c, int R, int prec, int precond, const double2* rhs, 
           Hc[i] = std::complex<double>(a.x + b.x, a.y + b.y);
         }
         Hc[j + 1] = hn[r];
+        if (Hout && r == 0 && Hout->size() >= (size_t)(m + 1) * m)   // the unrotated column (first cycle)
+          for (int i = 0; i <= j + 1; ++i) (*Hout)[(size_t)j * (m + 1) + i] = Hc[i];
         for (int i = 0; i < j; ++i) {
           std::complex<double> ci = cs[(size_t)r * m + i], si = sn[(size_t)r * m + i];
           std::complex<double> t = ci * Hc[i] + si * Hc[i + 1];
@@ -1126,6 +1295,43 @@ int solve(Ctx* c, int R, const double2* b, double2* x, const smr_solve_opts* o, 
         return SMR_E_OOM;
       }
       c->pcw_elems = (size_t)3 * ld;
+    }
+  }
+  // polynomial preconditioner: roots from d Arnoldi steps on the operator the
+  // iterations use (the FP32 one for the refinement), started from b
+  c->poly_roots.clear();
+  c->poly_mv = 0;
+  int its_poly = 0;
+  if (o->poly_degree >= 2 && R == 1) {
+    const int dp = std::min(o->poly_degree, m);
+    if (c->polyw_elems < (size_t)4 * ld) {
+      if (c->d_polyw) cudaFree(c->d_polyw);
+      c->d_polyw = nullptr;
+      c->polyw_elems = 0;
+      if (cudaMalloc((void**)&c->d_polyw, (size_t)4 * ld * sizeof(double2)) != cudaSuccess) {
+        cudaGetLastError();
+        cleanup();
+        c->err = "solve: device allocation of the polynomial preconditioner's work vectors failed";
+        return SMR_E_OOM;
+      }
+      c->polyw_elems = (size_t)4 * ld;
+    }
+    const int pprec = o->precision == SMR_PREC_FP64 ? SMR_PREC_FP64 : SMR_PREC_FP32;
+    std::vector<zc> Hb((size_t)(dp + 1) * dp, zc(0, 0));
+    std::vector<double> tnever(R, 0.0), relp(R);
+    int mvp = 0, nrp = 0;
+    double2* xp = c->d_polyw;                 // scratch solution of the Arnoldi run
+    int rp = gmres_core(c, R, pprec, precond, b, xp, false, tnever, dp, dp, W, &its_poly, &mvp, &nrp, relp, st, &Hb);
+    if (rp && rp != SMR_E_NOT_CONVERGED && rp != SMR_E_BREAKDOWN) {
+      cleanup();
+      return rp;
+    }
+    (pprec == SMR_PREC_FP64 ? mv64 : mv32) += mvp;
+    std::vector<zc> th;
+    const int deff = std::min(its_poly, dp);
+    if (deff >= 2 && harmonic_ritz(deff, Hb, dp + 1, th)) {
+      leja_order(th);
+      c->poly_roots = th;
     }
   }
   std::vector<double> rel;
@@ -1285,9 +1491,9 @@ int solve(Ctx* c, int R, const double2* b, double2* x, const smr_solve_opts* o, 
   SMR_CUDA(c, cudaStreamSynchronize(st));
   cleanup();
   if (stats) {
-    stats->iters = its;
-    stats->matvecs_fp64 = mv64;
-    stats->matvecs_fp32 = mv32;
+    stats->iters = its + its_poly;
+    stats->matvecs_fp64 = mv64 + (o->precision == SMR_PREC_FP64 ? c->poly_mv : 0);
+    stats->matvecs_fp32 = mv32 + (o->precision == SMR_PREC_FP64 ? 0 : c->poly_mv);
     stats->outer = outer;
     stats->reorth = nreo;
     stats->seconds_product = W.t_mv;
@@ -1301,6 +1507,7 @@ int solve(Ctx* c, int R, const double2* b, double2* x, const smr_solve_opts* o, 
     stats->resid_true = mx;
     stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   }
+  c->poly_roots.clear();
   return rc;
 }
 

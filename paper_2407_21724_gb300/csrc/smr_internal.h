@@ -358,6 +358,13 @@ struct Ctx {
   int* d_cl_mem = nullptr;
   double2* d_cl_inv64 = nullptr;
   float2* d_cl_inv32 = nullptr;
+  // polynomial preconditioner (smr_solve_opts.poly_degree): roots in Leja
+  // order for the running solve, four [N] work vectors, products it made
+  std::vector<std::complex<double>> poly_roots;
+  bool poly_busy = false;
+  int poly_mv = 0;
+  double2* d_polyw = nullptr;
+  size_t polyw_elems = 0;
   // near-field sweeps preconditioner: three [N][R] work vectors, sweep count
   double2* d_pcw = nullptr;
   size_t pcw_elems = 0;

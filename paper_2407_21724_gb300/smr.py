@@ -49,7 +49,7 @@ class smr_info_t(C.Structure):
 class smr_solve_opts(C.Structure):
     _fields_ = [("tol", C.c_double), ("maxit", C.c_int), ("restart", C.c_int), ("precond", C.c_int),
                 ("precision", C.c_int), ("max_outer", C.c_int), ("use_x0", C.c_int),
-                ("fallback_iters", C.c_int), ("near_sweeps", C.c_int)]
+                ("fallback_iters", C.c_int), ("near_sweeps", C.c_int), ("poly_degree", C.c_int)]
 
 
 class smr_solve_stats(C.Structure):
