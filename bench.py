@@ -41,6 +41,10 @@ WORKLOADS = {
     "random100": ("random", dict(n=100, seed=21725, shape="pillar")),
     "ragged16": ("ragged16", dict(shape="pillar")),
     "spheres8x8": ("spheres8x8", {}),
+    # off-lattice scenes (spheres: one exterior near block per displaced pair)
+    "jittered40": ("jittered", dict(n=40, seed=21728, jitter=0.02)),
+    "lattice40": ("random", dict(n=40, seed=21728)),
+    "spiral1600": ("spiral", dict(n=1600)),
 }
 METRIC = "MLFMA-SMR matvecs/s and GMRES time to 1e-4 residual, tuned vs plain FP64"
 

@@ -170,8 +170,17 @@ int smr_mesh_static_modes(int nv, const double* verts, int nt, const int* tris, 
 
 /* Set the scene: p particles with host centres[p][3] and host shape_ids[p],
  * inner medium (eps_in, mu_in) and background (eps_out, mu_out), each a
- * complex relative value {re, im}.  Centres must lie one per cell of a square
- * lattice of spacing opts.pitch in a plane z = const (the quadtree of Sec. IV).
+ * complex relative value {re, im}.  Centres lie in a plane z = const, at
+ * most one in each cell of a square lattice of spacing opts.pitch whose
+ * origin is the smallest x and y of the centres (the quadtree of Sec. IV):
+ * the cell is the particle's finest group.  A centre off its cell's lattice
+ * point (a jittered lattice, a sparse spiral; Sec. V) keeps its displacement:
+ * aggregation and receive shift its spectra to and from the cell centre, and
+ * its exterior near blocks are computed for the exact centre offsets, one
+ * block per distinct (shape, shape, offset).  Displaced scenes must keep
+ * neighbouring particles apart and every particle within distance opts.pitch
+ * of its cell centre (bounding radius plus displacement), else
+ * SMR_E_INVALID_ARG; they run the near product on the CUDA cores.
  * Builds the quadtree, interaction lists, k-space grids, and on the GPU in
  * FP64: the patterns (Eq. 26), translation tables (Eq. 23) and near blocks
  * (Eq. 16; exterior blocks by surface quadrature, self blocks in closed form),
@@ -507,12 +516,17 @@ int smr_nn_predict(smr_ctx* ctx, const double* khat, const double* pol, double s
  *  smr_copy_translation: T_L(khat, X) of Eq. 23 at level s for the lattice
  *    offset X = (dx, dy) x box size, [K_s] complex (FP64 table);
  *  smr_copy_near_block: the stored near block for (shape_m, shape_n, dx, dy)
- *    (dx = dy = 0: self block), [2 n_psi][2 n_psi] complex row-major;
+ *    (dx = dy = 0: self block), [2 n_psi][2 n_psi] complex row-major; on a
+ *    scene with displaced particles, the first block of that key;
+ *  smr_copy_pair_block: the near block Z^{mu nu} that the product applies to
+ *    x_nu for y_mu (mu = nu: self block), same layout; SMR_E_INVALID_ARG if
+ *    mu and nu are not a near pair;
  *  smr_copy_level: level-s outgoing (kind 0) or incoming (kind 1) spectra of
  *    the last product, [n_box][K_s][4][R] complex, in FP64. */
 int smr_copy_pattern(smr_ctx* ctx, int shape, double* out);
 int smr_copy_translation(smr_ctx* ctx, int level, int dx, int dy, double* out);
 int smr_copy_near_block(smr_ctx* ctx, int shape_m, int shape_n, int dx, int dy, double* out);
+int smr_copy_pair_block(smr_ctx* ctx, int mu, int nu, double* out);
 int smr_copy_level(smr_ctx* ctx, int level, int kind, double* out, size_t n_doubles);
 
 /* Parity access to the launch variants (the choices smr_autotune makes),

@@ -554,17 +554,22 @@ int set_scene(Ctx* c, int p, const double* centres, const int* shape_ids, const 
     int a = arr[i];
     double fx = (centres[3 * i] - ax[a]) / pitch, fy = (centres[3 * i + 1] - ay[a]) / pitch;
     int ix = (int)std::lround(fx), iy = (int)std::lround(fy);
-    if (std::fabs(fx - ix) > 1e-6 || std::fabs(fy - iy) > 1e-6 ||
-        std::fabs(centres[3 * i + 2] - c->z0) > 1e-9 * pitch)
-      return fail(c, SMR_E_INVALID_ARG, "centres must lie on a square lattice of spacing opts.pitch in one plane");
+    // off-lattice centres: each particle belongs to the lattice cell nearest
+    // to it (its finest group) and keeps its displacement from the cell's
+    // centre; within 1e-9 cells of a lattice point (rounding of the input)
+    // it counts as on it
+    if (std::fabs(fx - ix) <= 1e-9) fx = ix;
+    if (std::fabs(fy - iy) <= 1e-9) fy = iy;
+    if (std::fabs(centres[3 * i + 2] - c->z0) > 1e-9 * pitch)
+      return fail(c, SMR_E_INVALID_ARG, "centres must lie in one plane z = const");
     if (ix > (1 << 20) || iy > (1 << 20)) return fail(c, SMR_E_INVALID_ARG, "array too large");
     lx[i] = ix;
     ly[i] = iy;
     ex[a] = std::max(ex[a], ix + 1);
     ey[a] = std::max(ey[a], iy + 1);
-    dsh[3 * i] = centres[3 * i] - (ax[a] + ix * pitch);
-    dsh[3 * i + 1] = centres[3 * i + 1] - (ay[a] + iy * pitch);
-    dsh[3 * i + 2] = centres[3 * i + 2] - c->z0;
+    dsh[3 * i] = (fx - ix) * pitch;
+    dsh[3 * i + 1] = (fy - iy) * pitch;
+    dsh[3 * i + 2] = 0.0;
     if (dsh[3 * i] != 0 || dsh[3 * i + 1] != 0 || dsh[3 * i + 2] != 0) anyd = 1;
   }
   int level_cap = 1 << 20;
@@ -598,6 +603,28 @@ int set_scene(Ctx* c, int p, const double* centres, const int* shape_ids, const 
   for (auto& s : c->shapes)
     if (2 * (s.sampled ? s.lateral : s.a) >= pitch)
       return fail(c, SMR_E_INVALID_ARG, "particle width must be below the pitch");
+  if (anyd) {
+    // displaced particles (Sec. V, non-lattice arrays): neighbours must not
+    // overlap, and every particle must lie inside the sphere of radius pitch
+    // about its cell centre, so that the sources of two groups of an
+    // interaction list (centres at least two cells apart) never meet and the
+    // plane-wave expansion of the translation converges
+    for (int i = 0; i < p; ++i) {
+      const Shape& si = c->shapes[c->sid[i]];
+      if (std::hypot(dsh[3 * i], dsh[3 * i + 1]) + si.a >= pitch)
+        return fail(c, SMR_E_INVALID_ARG, "a displaced particle reaches a pitch or more from its cell centre");
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+          auto it = idx0.find({c->pi[i] + dx, c->pj[i] + dy});
+          if (it == idx0.end() || it->second == i) continue;
+          const int j = it->second;
+          const Shape& sj = c->shapes[c->sid[j]];
+          const double ei = si.sampled ? si.lateral : si.a, ej = sj.sampled ? sj.lateral : sj.a;
+          if (std::hypot(centres[3 * i] - centres[3 * j], centres[3 * i + 1] - centres[3 * j + 1]) <= ei + ej)
+            return fail(c, SMR_E_INVALID_ARG, "two neighbouring particles overlap");
+        }
+    }
+  }
   c->any_dshift = anyd;
   // ---- levels
   std::vector<int> bi(c->pi), bj(c->pj);
@@ -760,11 +787,15 @@ int set_scene(Ctx* c, int p, const double* centres, const int* shape_ids, const 
       return rc;
   }
   // ---- near lists: self + 8 lattice neighbours; block keys (sm, sn, dx, dy)
-  c->blk_sm.clear(); c->blk_sn.clear(); c->blk_dx.clear(); c->blk_dy.clear();
+  // on a lattice; with displaced particles every exterior block is keyed by
+  // the exact centre offset as well (one block per distinct pair geometry)
+  c->blk_sm.clear(); c->blk_sn.clear(); c->blk_dx.clear(); c->blk_dy.clear(); c->blk_off.clear();
   for (int s = 0; s < c->S; ++s) {
     c->blk_sm.push_back(s); c->blk_sn.push_back(s); c->blk_dx.push_back(0); c->blk_dy.push_back(0);
+    c->blk_off.insert(c->blk_off.end(), {0.0, 0.0, 0.0});
   }
-  std::map<std::tuple<int, int, int, int>, int> bkey;
+  std::map<std::tuple<int, int, int, int, unsigned long long, unsigned long long>, int> bkey;
+  auto bits = [](double v) { unsigned long long u; std::memcpy(&u, &v, sizeof u); return u; };
   c->nr_ptr.assign(1, 0);
   c->nr_col.clear();
   c->nr_blk.clear();
@@ -777,13 +808,21 @@ int set_scene(Ctx* c, int p, const double* centres, const int* shape_ids, const 
         if (nu == mu) {
           b = c->sid[mu];
         } else {
-          auto key = std::make_tuple(c->sid[mu], c->sid[nu], -dx, -dy);
+          // r_mu - r_nu: the lattice offset, plus the displacements
+          double ox = -dx * pitch, oy = -dy * pitch;
+          if (anyd) {
+            ox += dsh[3 * mu] - dsh[3 * nu];
+            oy += dsh[3 * mu + 1] - dsh[3 * nu + 1];
+          }
+          auto key = std::make_tuple(c->sid[mu], c->sid[nu], -dx, -dy, anyd ? bits(ox) : 0ull,
+                                     anyd ? bits(oy) : 0ull);
           auto f = bkey.find(key);
           if (f == bkey.end()) {
             b = (int)c->blk_sm.size();
             bkey[key] = b;
             c->blk_sm.push_back(c->sid[mu]); c->blk_sn.push_back(c->sid[nu]);
             c->blk_dx.push_back(-dx); c->blk_dy.push_back(-dy);
+            c->blk_off.insert(c->blk_off.end(), {ox, oy, 0.0});
           } else {
             b = f->second;
           }
@@ -806,8 +845,13 @@ int set_scene(Ctx* c, int p, const double* centres, const int* shape_ids, const 
       (rc = upload(c, &c->d_pc_blk, pcb)))
     return rc;
   if ((rc = build_modes(c)) || (rc = build_patterns(c)) || (rc = build_translations(c)) ||
-      (rc = build_near(c)) || (rc = build_tc(c)) || (rc = build_near_tc(c)))
+      (rc = build_near(c)) || (rc = build_tc(c)))
     return rc;
+  // the tensor-core near product groups pairs that share a block; with one
+  // block per displaced pair it would run one pair per tile, so displaced
+  // scenes keep the CUDA-core block-sparse product
+  c->tcn_ready = false;
+  if (!anyd && (rc = build_near_tc(c))) return rc;
   // device flag that the bounded waits of the staged and tensor-core kernels raise
   if (!c->d_tc_err) {
     SMR_CUDA(c, cudaMalloc((void**)&c->d_tc_err, sizeof(int)));
@@ -1743,6 +1787,27 @@ int smr_copy_near_block(smr_ctx* h, int sm, int sn, int dx, int dy, double* out)
       return SMR_OK;
     }
   return fail(c, SMR_E_INVALID_ARG, "no such near block in this scene");
+}
+
+int smr_copy_pair_block(smr_ctx* h, int mu, int nu, double* out) {
+  if (!h || !out) return SMR_E_INVALID_ARG;
+  Ctx* c = &h->c;
+  if (!check_scene(c)) return SMR_E_STATE;
+  if (mu < 0 || mu >= c->p || nu < 0 || nu >= c->p) return fail(c, SMR_E_INVALID_ARG, "particle index out of range");
+  const int n2 = 2 * c->npsi;
+  for (int e = c->nr_ptr[mu]; e < c->nr_ptr[mu + 1]; ++e) {
+    if (c->nr_col[e] != nu) continue;
+    std::vector<double2> t((size_t)n2 * n2);
+    SMR_CUDA(c, cudaMemcpy(t.data(), c->d_B64 + (size_t)c->nr_blk[e] * n2 * n2, t.size() * sizeof(double2),
+                           cudaMemcpyDeviceToHost));
+    for (int i = 0; i < n2; ++i)
+      for (int j = 0; j < n2; ++j) {
+        out[2 * ((size_t)i * n2 + j)] = t[(size_t)j * n2 + i].x;
+        out[2 * ((size_t)i * n2 + j) + 1] = t[(size_t)j * n2 + i].y;
+      }
+    return SMR_OK;
+  }
+  return fail(c, SMR_E_INVALID_ARG, "the two particles are not a near pair");
 }
 
 int smr_copy_level(smr_ctx* h, int level, int kind, double* out, size_t n_doubles) {

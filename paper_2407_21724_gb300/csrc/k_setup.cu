@@ -401,9 +401,7 @@ int build_near(Ctx* c) {
     for (int b = 0; b < nex; ++b) {
       bsm[b] = c->blk_sm[S + b];
       bsn[b] = c->blk_sn[S + b];
-      bdc[3 * b] = c->blk_dx[S + b] * c->opts.pitch;
-      bdc[3 * b + 1] = c->blk_dy[S + b] * c->opts.pitch;
-      bdc[3 * b + 2] = 0.0;
+      for (int d = 0; d < 3; ++d) bdc[3 * b + d] = c->blk_off[3 * (size_t)(S + b) + d];
     }
     int *d_bsm = nullptr, *d_bsn = nullptr;
     double* d_bdc = nullptr;

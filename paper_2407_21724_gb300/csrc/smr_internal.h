@@ -247,6 +247,7 @@ struct Ctx {
   int* d_nr_blk = nullptr;
   int nblk = 0;
   std::vector<int> blk_sm, blk_sn, blk_dx, blk_dy;  // key of each block
+  std::vector<double> blk_off;            // [nblk][3] r_mu - r_nu of each block
   double2* d_B64 = nullptr;
   float2* d_B32 = nullptr;
   // preconditioner: inverse self blocks, transposed [S][2n][2n]

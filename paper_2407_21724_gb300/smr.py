@@ -19,7 +19,7 @@ _lib = None
 SMR_PREC_FP64, SMR_PREC_FP32 = 0, 1
 SMR_LRULE_FORMULA, SMR_LRULE_DOUBLE = 0, 1
 SMR_PRECOND_NONE, SMR_PRECOND_BLOCKDIAG, SMR_PRECOND_LEARNED, SMR_PRECOND_NEAR, SMR_PRECOND_CLUSTER = 0, 1, 2, 3, 4
-SMR_OK, SMR_E_SHAPE, SMR_E_NOT_CONVERGED = 0, -2, -5
+SMR_OK, SMR_E_INVALID_ARG, SMR_E_SHAPE, SMR_E_NOT_CONVERGED = 0, -1, -2, -5
 SMR_E_BREAKDOWN, SMR_E_TIMEOUT = -6, -8
 ERRORS = {-1: "INVALID_ARG", -2: "SHAPE", -3: "OOM", -4: "CUDA", -5: "NOT_CONVERGED",
           -6: "BREAKDOWN", -7: "NAN", -8: "TIMEOUT", -9: "STATE"}
@@ -105,6 +105,7 @@ _SIGS = {
     "smr_copy_pattern": (C.c_int, [_P, C.c_int, _D]),
     "smr_copy_translation": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _D]),
     "smr_copy_near_block": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_int, _D]),
+    "smr_copy_pair_block": (C.c_int, [_P, C.c_int, C.c_int, _D]),
     "smr_copy_level": (C.c_int, [_P, C.c_int, C.c_int, _D, C.c_size_t]),
     "smr_set_tensor_cores": (C.c_int, [_P, C.c_int]),
     "smr_add_shape_sampled": (C.c_int, [_P, C.c_int, _D, _D, C.c_int, C.c_int, _D, _D, C.POINTER(C.c_int)]),
@@ -518,6 +519,13 @@ def smr_copy_near_block(ctx, sm, sn, dx, dy):
     n2 = 2 * smr_info(ctx)["n_psi"]
     out = np.empty((n2, n2), dtype=np.complex128)
     _check(ctx, lib().smr_copy_near_block(ctx, sm, sn, dx, dy, _dptr(out.view(np.float64))))
+    return out
+
+
+def smr_copy_pair_block(ctx, mu, nu):
+    n2 = 2 * smr_info(ctx)["n_psi"]
+    out = np.empty((n2, n2), dtype=np.complex128)
+    _check(ctx, lib().smr_copy_pair_block(ctx, mu, nu, _dptr(out.view(np.float64))))
     return out
 
 

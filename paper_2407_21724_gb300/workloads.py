@@ -5,7 +5,8 @@ module draws lattices, radii and incidences and builds particle meshes
 (geometry only); it computes nothing of the MLFMA-SMR method itself.
 
 All lengths are in vacuum wavelengths.  The particles are dielectric
-(eps_r = 4, mu_r = 1) in vacuum on a square lattice of pitch 0.5, either
+(eps_r = 4, mu_r = 1) in vacuum on a square lattice of pitch 0.5 (or off it:
+a jittered lattice, a golden-angle spiral), either
 spheres (closed-form static modes) or nanopillars: circular cylinders of
 height 0.6 given as closed 600-triangle meshes, whose static modes the
 solver computes (N_perp transverse and N_par longitudinal per shape).  Radii
@@ -121,6 +122,44 @@ def make(name, **kw):
         w['centres'], w['shape_ids'] = w['centres'][keep], w['shape_ids'][keep]
         w['label'] = f"{w['label']} thinned to {int(keep.sum())} sites"
         return w
+    if name == 'jittered':
+        # n x n random-radius lattice, each centre moved by a seeded uniform
+        # in-plane displacement of at most `jitter` wavelengths per axis
+        w = make('random', n=kw.get('n', 40), seed=kw.get('seed', 21728), modes=kw.get('modes', 16),
+                 shape=shape)
+        j = kw.get('jitter', 0.02)
+        rng = np.random.default_rng(kw.get('seed', 21728) + 1)
+        C = w['centres'].copy()
+        C[:, :2] += rng.uniform(-j, j, size=(len(C), 2))
+        w['centres'] = C
+        w['label'] = f"{w['label']}, centres jittered by up to {j} per axis"
+        return w
+    if name == 'spiral':
+        # golden-angle spiral of n particles, i = 1 .. n at r_i = c sqrt(i) and
+        # angle i * 2 pi / phi^2 (the validation geometry of Sec. V), with c
+        # set so that the closest two centres are `d_min` apart (sparser than
+        # the paper's c = sqrt(3) R); radii from the three smallest of the 8
+        # values, drawn from a seed.  With the pitch below d_min / sqrt(2)
+        # every lattice cell holds at most one centre.
+        n = kw.get('n', 400)
+        d_min = kw.get('d_min', 0.75)
+        modes = kw.get('modes', 16)
+        i = np.arange(1, n + 1, dtype=float)
+        ga = 2 * np.pi / ((1 + np.sqrt(5)) / 2) ** 2
+        P = np.stack([np.sqrt(i) * np.cos(i * ga), np.sqrt(i) * np.sin(i * ga)], axis=1)
+        d2 = np.sum((P[:, None, :] - P[None, :, :]) ** 2, axis=2) if n <= 4000 else None
+        if d2 is None:
+            raise ValueError('spiral: n <= 4000')
+        np.fill_diagonal(d2, np.inf)
+        P *= d_min / np.sqrt(d2.min())
+        C = np.zeros((n, 3))
+        C[:, :2] = P
+        ids = np.random.default_rng(kw.get('seed', 21729)).integers(0, 3, size=n).astype(np.int32)
+        inc = kw.get('incidences') or [incidence(0, 0, 'x')]
+        return dict(label=f'golden-angle spiral of {n} {what} (3 radii), closest centres {d_min} apart, '
+                          f'{2*modes} modes/current, {n*4*modes} unknowns',
+                    centres=C, shape_ids=ids, shapes=shapes8(shape, modes)[:3], eps_in=EPS_IN,
+                    pitch=PITCH, incidences=inc)
     if name == 'ragged16':
         # 16 arrays of n_i = round(10 + 50 i / 15) pillars per side, seeds 21726 + i
         return [make('random', n=int(round(10 + 50 * i / 15)), seed=21726 + i,
