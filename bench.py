@@ -45,6 +45,8 @@ WORKLOADS = {
     "jittered40": ("jittered", dict(n=40, seed=21728, jitter=0.02)),
     "lattice40": ("random", dict(n=40, seed=21728)),
     "spiral1600": ("spiral", dict(n=1600)),
+    # rotated particles: 100 x 100 geometric-phase lens of nanofins, 16 rotations
+    "pbfins100": ("pbfins", dict(n=100, bins=16)),
 }
 METRIC = "MLFMA-SMR matvecs/s and GMRES time to 1e-4 residual, tuned vs plain FP64"
 
@@ -85,11 +87,12 @@ def oracle_rate(ws, steps, warmup):
         # meshed shapes: the oracle's static modes and self blocks, each
         # distinct mesh once, the shapes in parallel (spawned processes)
         key = lambda s: s["verts"].tobytes() + s["tris"].tobytes() + bytes([s["n_perp"], s["n_par"]])
-        todo = {key(s): s for s in w["shapes"] if isinstance(s, dict) and key(s) not in built}
+        mesh = lambda s: isinstance(s, dict) and s.get("kind") == "mesh"
+        todo = {key(s): s for s in w["shapes"] if mesh(s) and key(s) not in built}
         if todo:
             for k, v in zip(todo, sampled_shapes(list(todo.values()), w["eps_in"], workers=os.cpu_count() or 1)):
                 built[k] = v
-        shapes = [built[key(s)] if isinstance(s, dict) else s for s in w["shapes"]]
+        shapes = [built[key(s)] if mesh(s) else s for s in w["shapes"]]
         sc = opm.Scene(w["centres"], w["shape_ids"], shapes, eps_in=w["eps_in"])
         P = ParallelMLFMA(sc, w["pitch"])
         t_setup += time.perf_counter() - t0

@@ -149,6 +149,19 @@ int smr_add_shape_sampled(smr_ctx* ctx, int n_q, const double* pts, const double
 int smr_add_shape_mesh(smr_ctx* ctx, int nv, const double* verts, int nt, const int* tris, int n_perp,
                        int n_par, int* shape_id);
 
+/* A copy of shape `base` rotated by `angle` radians about the z axis through
+ * the particle centre (the in-plane rotations of the brick and nanofin arrays
+ * of Sec. V; the PB-phase lens rotates each fin by its own angle).  The
+ * copy's sample points and mode fields are the base's carried by the
+ * rotation R: psi'(R r) = R psi(r); weights, surface divergences, static
+ * eigenvalues, RWG coefficients (smr_shape_modes) and the self block are the
+ * base's (the PMCHWT operators commute with rotations).  Patterns, near
+ * blocks and right-hand sides are computed for the rotated samples like any
+ * other shape's.  The base must be a meshed or sampled shape (SMR_E_SHAPE for
+ * a closed-form sphere, which rotation leaves unchanged); rotating a rotated
+ * copy composes the angles.  Must precede smr_set_scene. */
+int smr_add_shape_rotated(smr_ctx* ctx, int base, double angle, int* shape_id);
+
 /* The static modes of a meshed shape: *n_psi and *n_edges (each if
  * non-NULL) receive the mode count and the RWG count n_e, M (if non-NULL)
  * the mode -> RWG matrix of Eq. 20

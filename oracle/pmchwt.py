@@ -62,6 +62,17 @@ class SampledShape:
         return float(np.max(np.linalg.norm(self.r, axis=1)))
 
 
+def rotated_about_z(sh, angle):
+    """The sampled shape turned by `angle` about the z axis through its centre
+    (the in-plane rotations of Sec. V's brick and nanofin arrays): with R the
+    rotation, a point r goes to R r and a tangential field to R psi there; the
+    weights and surface divergences stay, and so does the self block (the
+    operators T and K are unchanged by a rotation of both arguments)."""
+    c, s = np.cos(angle), np.sin(angle)
+    R = np.array([[c, -s, 0.0], [s, c, 0.0], [0.0, 0.0, 1.0]])
+    return SampledShape(sh.r @ R.T, sh.w, sh.psi @ R.T, sh.div, sh.Zs, sh.n_perp, sh.n_par)
+
+
 class Scene:
     """p particles: centres (p,3), shape ids (p,), shapes, inner/outer media,
     and the surface rule (n_theta, n_phi) used for every surface integral."""
@@ -72,7 +83,9 @@ class Scene:
         self.shape_ids = np.asarray(shape_ids, dtype=int).ravel()
         self.inner = Medium(eps_in, mu_in, lam)
         self.outer = Medium(eps_out, mu_out, lam)
-        self.shapes = [self._shape(s) for s in shapes]
+        self.shapes = []
+        for s in shapes:
+            self.shapes.append(self._shape(s))
         self.n_theta, self.n_phi = n_theta, n_phi
         npsi = {s.n_psi for s in self.shapes}
         assert len(npsi) == 1, "all shapes share one mode count"
@@ -82,9 +95,12 @@ class Scene:
     def _shape(self, s):
         """Closed-form spheres from (radius, n_perp, n_par); meshed shapes
         from dicts with kind 'mesh' (verts, tris, n_perp, n_par), their modes
-        and self block computed here (``oracle.mesh``)."""
+        and self block computed here (``oracle.mesh``); dicts with kind
+        'rotated' (base, angle) turn an earlier shape about z."""
         if isinstance(s, (SphereShape, SampledShape)):
             return s
+        if isinstance(s, dict) and s.get('kind') == 'rotated':
+            return rotated_about_z(self.shapes[s['base']], s['angle'])
         if isinstance(s, dict) and s.get('kind') == 'mesh':
             from .mesh import Mesh, MeshModes
             return MeshModes(Mesh(s['verts'], s['tris']), s['n_perp'], s['n_par']).sampled(self.outer, self.inner)

@@ -1076,6 +1076,35 @@ int smr_add_shape_mesh(smr_ctx* h, int nv, const double* verts, int nt, const in
   return SMR_OK;
 }
 
+int smr_add_shape_rotated(smr_ctx* h, int base, double angle, int* shape_id) {
+  if (!h) return SMR_E_INVALID_ARG;
+  Ctx* c = &h->c;
+  if (base < 0 || base >= (int)c->shapes.size()) return fail(c, SMR_E_SHAPE, "base shape id out of range");
+  if (!std::isfinite(angle)) return fail(c, SMR_E_INVALID_ARG, "angle must be finite");
+  if (!c->shapes[base].sampled)
+    return fail(c, SMR_E_SHAPE, "closed-form spheres are unchanged by rotation: add the sphere again");
+  // the rotated particle's modes are the base modes carried by the rotation
+  // R about z: psi'(R r) = R psi(r); the surface divergence and the weights
+  // are unchanged, and so is the self block
+  Shape sh = c->shapes[base];
+  const double cs = std::cos(angle), sn = std::sin(angle);
+  auto rot = [&](double* v) {
+    const double x = v[0], y = v[1];
+    v[0] = cs * x - sn * y;
+    v[1] = sn * x + cs * y;
+  };
+  for (int q = 0; q < sh.nq; ++q) rot(&sh.rq[4 * (size_t)q]);
+  for (size_t i = 0; i < sh.modes.size(); i += 4) rot(&sh.modes[i]);
+  // a meshed base keeps its mesh data (sh.mm: RWG coefficients, eigenvalues
+  // and the geometry that assembles self blocks) unrotated: the coefficients
+  // and eigenvalues are the same, and the self block is taken from the base
+  sh.rot_base = c->shapes[base].rot_base >= 0 ? c->shapes[base].rot_base : base;
+  sh.rot_angle = c->shapes[base].rot_angle + angle;
+  c->shapes.push_back(std::move(sh));
+  if (shape_id) *shape_id = (int)c->shapes.size() - 1;
+  return SMR_OK;
+}
+
 int smr_shape_modes(smr_ctx* h, int shape_id, int* n_psi, int* n_edges, double* M, double* gamma) {
   if (!h) return SMR_E_INVALID_ARG;
   Ctx* c = &h->c;

@@ -364,7 +364,9 @@ int build_near(Ctx* c) {
   c->pinv_ok = true;
   for (int s = 0; s < S; ++s) {
     std::vector<cd> Z;
-    if (c->shapes[s].mesh) {
+    if (c->shapes[s].rot_base >= 0) {
+      Z = c->shapes[c->shapes[s].rot_base].Z;  // a rotated copy: the same self block
+    } else if (c->shapes[s].mesh) {
       int rc = mesh_self_block(c, c->shapes[s], Z);
       if (rc) return rc;
     } else if (c->shapes[s].sampled) {

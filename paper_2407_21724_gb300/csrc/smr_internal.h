@@ -61,6 +61,10 @@ struct Shape {
   bool mesh = false;
   MeshModes mm;
   double lateral = 0;                     // largest distance of a point from the z axis
+  // rotated copy of another shape (about the z axis): the shape whose self
+  // block it shares (rotation leaves Z_s unchanged), -1 if none
+  int rot_base = -1;
+  double rot_angle = 0;
 };
 
 struct Level {

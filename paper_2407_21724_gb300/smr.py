@@ -109,6 +109,7 @@ _SIGS = {
     "smr_copy_level": (C.c_int, [_P, C.c_int, C.c_int, _D, C.c_size_t]),
     "smr_set_tensor_cores": (C.c_int, [_P, C.c_int]),
     "smr_add_shape_sampled": (C.c_int, [_P, C.c_int, _D, _D, C.c_int, C.c_int, _D, _D, C.POINTER(C.c_int)]),
+    "smr_add_shape_rotated": (C.c_int, [_P, C.c_int, C.c_double, C.POINTER(C.c_int)]),
     "smr_add_shape_mesh": (C.c_int, [_P, C.c_int, _D, C.c_int, C.POINTER(C.c_int), C.c_int, C.c_int,
                                      C.POINTER(C.c_int)]),
     "smr_shape_modes": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), _D, _D]),
@@ -539,10 +540,13 @@ def smr_copy_level(ctx, level, kind, R=1):
 def add_shapes(ctx, shapes):
     """Register shapes: (radius, n_perp, n_par) tuples are closed-form spheres;
     dicts with kind 'mesh' (verts, tris, n_perp, n_par) are meshed shapes;
-    objects with r, w, psi, div, Zs, n_perp, n_par are shapes given as data."""
+    dicts with kind 'rotated' (base, angle) are an earlier shape rotated about
+    z; objects with r, w, psi, div, Zs, n_perp, n_par are shapes given as data."""
     for sh in shapes:
         if isinstance(sh, dict) and sh.get("kind") == "mesh":
             smr_add_shape_mesh(ctx, sh["verts"], sh["tris"], sh["n_perp"], sh["n_par"])
+        elif isinstance(sh, dict) and sh.get("kind") == "rotated":
+            smr_add_shape_rotated(ctx, sh["base"], sh["angle"])
         elif hasattr(sh, "psi"):
             smr_add_shape_sampled(ctx, sh.r, sh.w, sh.n_perp, sh.n_par, sh.psi, sh.div, sh.Zs)
         else:
@@ -576,6 +580,13 @@ def smr_add_shape_mesh(ctx, verts, tris, n_perp, n_par):
     sid = C.c_int()
     _check(ctx, lib().smr_add_shape_mesh(ctx, V.shape[0], _dptr(V), T.shape[0], tp, n_perp, n_par,
                                          C.byref(sid)))
+    return sid.value
+
+
+def smr_add_shape_rotated(ctx, base, angle):
+    """Shape `base` rotated by `angle` radians about z; returns the shape id."""
+    sid = C.c_int()
+    _check(ctx, lib().smr_add_shape_rotated(ctx, int(base), float(angle), C.byref(sid)))
     return sid.value
 
 

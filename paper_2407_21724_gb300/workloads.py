@@ -160,6 +160,25 @@ def make(name, **kw):
                           f'{2*modes} modes/current, {n*4*modes} unknowns',
                     centres=C, shape_ids=ids, shapes=shapes8(shape, modes)[:3], eps_in=EPS_IN,
                     pitch=PITCH, incidences=inc)
+    if name == 'pbfins':
+        # n x n geometric-phase (PB) metalens of identical nanofins, each
+        # turned about z by its pb_angles value rounded to one of `bins`
+        # angles b pi / bins (the rotated copies of one meshed fin), focal
+        # length for NA 0.8 over the aperture, circularly polarised incidence
+        n = kw.get('n', 100)
+        bins = kw.get('bins', 16)
+        modes = kw.get('modes', 10)
+        C = lattice(n, n)
+        f = kw.get('focal', 0.75 * n * PITCH / 2)
+        ids = (np.rint(pb_angles(C, f) / (np.pi / bins)).astype(np.int64) % bins).astype(np.int32)
+        shapes = [nanofin(modes)] + [dict(kind='rotated', base=0, angle=b * np.pi / bins)
+                                     for b in range(1, bins)]
+        k = np.array([0.0, 0.0, 1.0])
+        pol = np.array([1.0, 1.0j, 0.0]) / np.sqrt(2.0)
+        return dict(label=f'{n}x{n} geometric-phase metalens of nanofins {FIN} ({bins} rotations of one '
+                          f'656-triangle box mesh), f={f}, {2*modes} modes/current, {n*n*4*modes} unknowns',
+                    centres=C, shape_ids=ids, shapes=shapes, eps_in=EPS_IN, pitch=PITCH,
+                    incidences=[(k, pol)], focal=f)
     if name == 'ragged16':
         # 16 arrays of n_i = round(10 + 50 i / 15) pillars per side, seeds 21726 + i
         return [make('random', n=int(round(10 + 50 * i / 15)), seed=21726 + i,
@@ -241,6 +260,54 @@ def cylinder_mesh(radius, height, n_phi=20, n_z=10, n_r=3):
                 T += [(a + j, b + j, b + j1), (a + j, b + j1, a + j1)]
     V = np.array(V, dtype=float)
     return V, _orient_outward(V, np.array(T, dtype=np.int32))
+
+
+def box_mesh(lx, ly, lz, nx, ny, nz):
+    """Closed triangle mesh of a rectangular box (a brick or nanofin) of sides
+    lx, ly, lz centred at the origin: each face an (n x n) grid of quads, two
+    triangles each, 4 (nx ny + ny nz + nx nz) triangles.  Returns (verts,
+    tris) with outward vertex order."""
+    ids, V, T = {}, [], []
+    n = (nx, ny, nz)
+    L = np.array([lx, ly, lz], dtype=float)
+
+    def vid(g):
+        if g not in ids:
+            ids[g] = len(V)
+            V.append((np.array(g, dtype=float) / n - 0.5) * L)
+        return ids[g]
+    for ax in range(3):
+        u, v = (ax + 1) % 3, (ax + 2) % 3
+        for side in (0, n[ax]):
+            for i in range(n[u]):
+                for j in range(n[v]):
+                    q = []
+                    for di, dj in ((0, 0), (1, 0), (1, 1), (0, 1)):
+                        g = [0, 0, 0]
+                        g[ax], g[u], g[v] = side, i + di, j + dj
+                        q.append(vid(tuple(g)))
+                    T += [(q[0], q[1], q[2]), (q[0], q[2], q[3])]
+    V = np.array(V, dtype=float)
+    return V, _orient_outward(V, np.array(T, dtype=np.int32))
+
+
+FIN = (0.31, 0.064, 0.45)        # nanofin sides (x, y, z) in wavelengths
+
+
+def nanofin(modes):
+    """A nanofin shape: the 656-triangle box mesh of FIN with `modes`
+    transverse and `modes` longitudinal static modes."""
+    V, T = box_mesh(*FIN, 10, 2, 12)
+    return dict(kind='mesh', verts=V, tris=T, n_perp=modes, n_par=modes,
+                label=f'nanofin {FIN[0]} x {FIN[1]} x {FIN[2]}, {len(T)} triangles')
+
+
+def pb_angles(centres, focal):
+    """Geometric-phase lens rotation of each fin: theta = pi (f - sqrt(f^2 +
+    x^2 + y^2)) (wavelength 1), taken modulo pi (a fin turned by pi is the
+    same fin)."""
+    r2 = centres[:, 0] ** 2 + centres[:, 1] ** 2
+    return np.mod(np.pi * (focal - np.sqrt(focal ** 2 + r2)), np.pi)
 
 
 def mlp_params(dims, seed):
