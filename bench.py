@@ -47,6 +47,10 @@ WORKLOADS = {
     "spiral1600": ("spiral", dict(n=1600)),
     # rotated particles: 100 x 100 geometric-phase lens of nanofins, 16 rotations
     "pbfins100": ("pbfins", dict(n=100, bins=16)),
+    # several particles per finest box: the paper's spiral spacing, and a
+    # two-layer Moire lattice of meshed nanodisks
+    "spiral_dense2000": ("spiral_dense", dict(n=2000)),
+    "moire2k": ("moire", dict(m=22)),
 }
 METRIC = "MLFMA-SMR matvecs/s and GMRES time to 1e-4 residual, tuned vs plain FP64"
 
@@ -94,7 +98,7 @@ def oracle_rate(ws, steps, warmup):
                 built[k] = v
         shapes = [built[key(s)] if mesh(s) else s for s in w["shapes"]]
         sc = opm.Scene(w["centres"], w["shape_ids"], shapes, eps_in=w["eps_in"])
-        P = ParallelMLFMA(sc, w["pitch"])
+        P = ParallelMLFMA(sc, w["pitch"], L0=w.get("L0", 10))
         t_setup += time.perf_counter() - t0
         workers = P.workers
         rng = np.random.default_rng(0)

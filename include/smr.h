@@ -183,17 +183,25 @@ int smr_mesh_static_modes(int nv, const double* verts, int nt, const int* tris, 
 
 /* Set the scene: p particles with host centres[p][3] and host shape_ids[p],
  * inner medium (eps_in, mu_in) and background (eps_out, mu_out), each a
- * complex relative value {re, im}.  Centres lie in a plane z = const, at
- * most one in each cell of a square lattice of spacing opts.pitch whose
- * origin is the smallest x and y of the centres (the quadtree of Sec. IV):
- * the cell is the particle's finest group.  A centre off its cell's lattice
- * point (a jittered lattice, a sparse spiral; Sec. V) keeps its displacement:
- * aggregation and receive shift its spectra to and from the cell centre, and
- * its exterior near blocks are computed for the exact centre offsets, one
- * block per distinct (shape, shape, offset).  Displaced scenes must keep
- * neighbouring particles apart and every particle within distance opts.pitch
- * of its cell centre (bounding radius plus displacement), else
- * SMR_E_INVALID_ARG; they run the near product on the CUDA cores.
+ * complex relative value {re, im}.  Each particle belongs to the cell of a
+ * square lattice of spacing opts.pitch (origin: the smallest x and y of the
+ * centres) nearest its centre; the quadtree of Sec. IV is built over the
+ * cells in the plane z0 = the mean height of the centres.  On a lattice
+ * (every centre on a lattice point of z0, one per cell) each particle is its
+ * own finest group.  A centre off its cell's lattice point (a jittered
+ * lattice, a spiral, a layer of a 2.5D scene above or below z0; Sec. V)
+ * keeps its 3D displacement: aggregation and receive shift its spectra to
+ * and from the cell centre, and its exterior near blocks are computed for
+ * the exact centre offsets, one block per distinct (shape, shape, offset).
+ * Where a cell holds several particles the finest groups are the occupied
+ * cells: a cell's outgoing spectrum is the sum of its particles', each
+ * particle receives its cell's incoming spectrum, and the near pairs are all
+ * pairs in the same or adjacent cells.  Displaced scenes must keep
+ * neighbouring particles apart (bounding cylinders about z) and every
+ * particle within distance opts.pitch of its cell centre (bounding radius
+ * plus displacement), else SMR_E_INVALID_ARG; they run the near product,
+ * aggregation and receive on the CUDA cores.  The learned parts and the
+ * cluster preconditioner need at most one particle per cell.
  * Builds the quadtree, interaction lists, k-space grids, and on the GPU in
  * FP64: the patterns (Eq. 26), translation tables (Eq. 23) and near blocks
  * (Eq. 16; exterior blocks by surface quadrature, self blocks in closed form),

@@ -8,7 +8,11 @@ Steps, in the order the paper composes them:
    coarser levels are a quadtree over the lattice (parent = 2x2 children by
    integer index).  Near = self + the 8 lattice neighbours; every other pair
    is translated at the finest level where their boxes are not adjacent but
-   their parents are (the interaction list, IL).
+   their parents are (the interaction list, IL).  Off the lattice a particle
+   belongs to the cell nearest its centre; where a cell holds several
+   particles the finest boxes are the occupied cells (their particles'
+   spectra summed), and near pairs are all pairs in the same or adjacent
+   cells.
 2. k-space sampling (Sec. V): L_0 = 10 at the finest level, K = 2(L+1)^2
    points per level: L+1 Gauss-Legendre nodes in cos(theta) times 2L+2
    uniform phi_j = 2 pi j / (2L+2).  Coarser levels take the paper's
@@ -48,13 +52,18 @@ class Tree:
         self.origin = C[:, :2].min(axis=0)
         self.z0 = float(C[:, 2].mean())
         ij = np.rint((C[:, :2] - self.origin) / self.pitch).astype(np.int64)
-        assert len({tuple(t) for t in ij}) == len(ij), "one particle per finest box"
         self.ij0 = ij
+        # one particle per cell: the finest boxes are the particles, in their
+        # order; else the occupied cells, ordered like every coarser level
+        self.one_per_cell = len({tuple(t) for t in ij}) == len(ij)
+        self.members = {}         # cell -> its particles, ascending
+        for mu, t in enumerate(ij):
+            self.members.setdefault(tuple(t), []).append(mu)
         self.levels = []          # per level: dict(ij, centre, index, parent)
         ij_s = ij
         s = 0
         while True:
-            if s == 0:
+            if s == 0 and self.one_per_cell:
                 keys = ij
             else:
                 keys = np.unique(ij_s, axis=0)
@@ -75,6 +84,9 @@ class Tree:
             s += 1
         while len(self.levels) > 1 and not self.levels[-1]['il']:
             self.levels.pop()
+        # the finest box of every particle
+        idx0 = self.levels[0]['index']
+        self.cell = np.array([idx0[tuple(t)] for t in ij], dtype=np.int64)
         # parents / children
         for s in range(len(self.levels) - 1):
             par = self.levels[s + 1]['index']
@@ -99,16 +111,15 @@ class Tree:
         return out
 
     def near_pairs(self, mus=None):
-        """(mu, nu) with lattice distance <= 1 (self included), for the
-        particles mus (default all) in ascending order."""
-        idx = self.levels[0]['index']
+        """(mu, nu) with nu in mu's cell or one of the 8 neighbouring cells
+        (self included), for the particles mus (default all) in ascending
+        order."""
         out = []
         for mu in (range(len(self.ij0)) if mus is None else mus):
             t = self.ij0[mu]
             for dy in (-1, 0, 1):
                 for dx in (-1, 0, 1):
-                    nu = idx.get((t[0] + dx, t[1] + dy))
-                    if nu is not None:
+                    for nu in self.members.get((t[0] + dx, t[1] + dy), ()):
                         out.append((mu, nu))
         return out
 
@@ -280,19 +291,27 @@ class MLFMA:
         return y.reshape(-1)
 
     def aggregate(self, x, mus=None, out=None):
-        """Level-0 outgoing spectra (p, K_0, 4)."""
+        """Level-0 outgoing spectra (n_box_0, K_0, 4): each particle's, shifted
+        from its centre to its cell's, summed over the cell's particles."""
         sc = self.scene
         xx = x.reshape(sc.p, 2, sc.n_psi)
         g = self.grids[0]
+        t = self.tree
+        assert mus is None or t.one_per_cell, "particle subsets need one particle per cell"
         if out is None:
-            out = np.zeros((sc.p, g.K, 4), dtype=complex)
-        cen = self.tree.levels[0]['centre']
+            out = np.zeros((len(t.levels[0]['ij']), g.K, 4), dtype=complex)
+        cen = t.levels[0]['centre']
         for mu in (range(sc.p) if mus is None else mus):
+            b = t.cell[mu]
             P = self.patterns[sc.shape_ids[mu]]               # (N, 2, K)
-            shift = np.exp(1j * self.k * (g.khat @ (sc.centres[mu] - cen[mu])))
+            shift = np.exp(1j * self.k * (g.khat @ (sc.centres[mu] - cen[b])))
             for c in range(2):
                 for comp in range(2):
-                    out[mu, :, 2 * c + comp] = shift * (xx[mu, c] @ np.conj(P[:, comp, :]))
+                    v = shift * (xx[mu, c] @ np.conj(P[:, comp, :]))
+                    if t.one_per_cell:
+                        out[b, :, 2 * c + comp] = v
+                    else:
+                        out[b, :, 2 * c + comp] += v
         return out
 
     def upward(self, s, out_s, parents=None, out=None):
@@ -348,9 +367,10 @@ class MLFMA:
         cen = self.tree.levels[0]['centre']
         y = np.zeros((sc.p, 2, sc.n_psi), dtype=complex) if out is None else out.reshape(sc.p, 2, sc.n_psi)
         for mu in (range(sc.p) if mus is None else mus):
+            b = self.tree.cell[mu]
             P = self.patterns[sc.shape_ids[mu]]
-            shift = np.exp(-1j * k * (g.khat @ (sc.centres[mu] - cen[mu])))
-            B = inc0[mu] * (g.w * shift)[:, None]
+            shift = np.exp(-1j * k * (g.khat @ (sc.centres[mu] - cen[b])))
+            B = inc0[b] * (g.w * shift)[:, None]
             Bet, Bep, Bmt, Bmp = B[:, 0], B[:, 1], B[:, 2], B[:, 3]
             y[mu, 0] = -1j * k * (P[:, 0, :] @ (z * Bet + Bmp) + P[:, 1, :] @ (z * Bep - Bmt))
             y[mu, 1] = -1j * k * (P[:, 0, :] @ (-Bep + Bmt / z) + P[:, 1, :] @ (Bet + Bmp / z))

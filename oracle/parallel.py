@@ -103,7 +103,11 @@ class ParallelMLFMA:
         B["x"][:] = np.asarray(x, dtype=complex).reshape(-1)
         p = self.M.scene.p
         self._run("near", 0, p)
-        self._run("agg", 0, p)
+        if t.one_per_cell:
+            self._run("agg", 0, p)
+        else:
+            # several particles per cell sum into one box: one process
+            B["out"][0][:] = M.aggregate(B["x"])
         for s in range(t.n_levels - 1):
             self._run("up", s, len(t.levels[s + 1]["ij"]))
         for s in range(t.n_levels):

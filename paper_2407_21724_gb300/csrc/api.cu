@@ -52,6 +52,12 @@ void free_scene(Ctx* c) {
   c->lev.clear();
   dfree(c->d_modes); dfree(c->d_rq); dfree(c->d_P64); dfree(c->d_P32); dfree(c->d_sid);
   dfree(c->d_centres); dfree(c->d_dshift); dfree(c->d_nr_ptr); dfree(c->d_nr_col); dfree(c->d_nr_blk);
+  dfree(c->d_cell_of); dfree(c->d_cell_ptr); dfree(c->d_cell_idx);
+  for (int q = 0; q < 2; ++q) {
+    if (c->pspec[q]) cudaFree(c->pspec[q]);
+    c->pspec[q] = nullptr;
+  }
+  c->multi = 0;
   dfree(c->d_B64); dfree(c->d_B32); dfree(c->d_tcn_img); dfree(c->d_tcn_blk); dfree(c->d_tcn_start);
   dfree(c->d_tcn_count); dfree(c->d_tcn_nu); dfree(c->d_tcn_mu); dfree(c->d_x32);
   dfree(c->d_tcn_mask); dfree(c->d_tcn_part); dfree(c->d_Pinv64); dfree(c->d_Pinv32); dfree(c->d_pc_ptr);
@@ -560,8 +566,10 @@ int set_scene(Ctx* c, int p, const double* centres, const int* shape_ids, const 
     // it counts as on it
     if (std::fabs(fx - ix) <= 1e-9) fx = ix;
     if (std::fabs(fy - iy) <= 1e-9) fy = iy;
-    if (std::fabs(centres[3 * i + 2] - c->z0) > 1e-9 * pitch)
-      return fail(c, SMR_E_INVALID_ARG, "centres must lie in one plane z = const");
+    // a centre off the mean plane z0 (a layer of a 2.5D scene) keeps its
+    // height as part of the displacement; the quadtree stays in the plane
+    double dz = centres[3 * i + 2] - c->z0;
+    if (std::fabs(dz) <= 1e-9 * pitch) dz = 0.0;
     if (ix > (1 << 20) || iy > (1 << 20)) return fail(c, SMR_E_INVALID_ARG, "array too large");
     lx[i] = ix;
     ly[i] = iy;
@@ -569,7 +577,7 @@ int set_scene(Ctx* c, int p, const double* centres, const int* shape_ids, const 
     ey[a] = std::max(ey[a], iy + 1);
     dsh[3 * i] = (fx - ix) * pitch;
     dsh[3 * i + 1] = (fy - iy) * pitch;
-    dsh[3 * i + 2] = 0.0;
+    dsh[3 * i + 2] = dz;
     if (dsh[3 * i] != 0 || dsh[3 * i + 1] != 0 || dsh[3 * i + 2] != 0) anyd = 1;
   }
   int level_cap = 1 << 20;
@@ -591,13 +599,18 @@ int set_scene(Ctx* c, int p, const double* centres, const int* shape_ids, const 
   }
   c->n_arrays = na;
   c->arr = arr;
-  std::map<std::pair<int, int>, int> idx0;
+  // the particles of every occupied cell, ascending; a cell holding more
+  // than one makes the occupied cells the finest boxes
+  std::map<std::pair<int, int>, std::vector<int>> cellp;
+  int multi = 0;
   for (int i = 0; i < p; ++i) {
     c->pi[i] = lx[i] + offx[arr[i]];
     c->pj[i] = ly[i] + offy[arr[i]];
-    if (!idx0.emplace(std::make_pair(c->pi[i], c->pj[i]), i).second)
-      return fail(c, SMR_E_INVALID_ARG, "two particles share a lattice cell");
+    std::vector<int>& m = cellp[std::make_pair(c->pi[i], c->pj[i])];
+    m.push_back(i);
+    if (m.size() > 1) multi = 1;
   }
+  if (multi && !anyd) return fail(c, SMR_E_INVALID_ARG, "two particles at one centre");
   // check no particle overlaps its neighbours on the lattice (the particles
   // share one plane, so their extent across the z axis decides)
   for (auto& s : c->shapes)
@@ -609,30 +622,43 @@ int set_scene(Ctx* c, int p, const double* centres, const int* shape_ids, const 
     // about its cell centre, so that the sources of two groups of an
     // interaction list (centres at least two cells apart) never meet and the
     // plane-wave expansion of the translation converges
+    // overlap test on bounding cylinders about z: lateral radius and half
+    // height of each shape
+    std::vector<double> zext(c->S, 0.0);
+    for (int t = 0; t < c->S; ++t) {
+      const Shape& sh = c->shapes[t];
+      if (!sh.sampled) zext[t] = sh.a;
+      for (int q = 0; q < sh.nq; ++q) zext[t] = std::max(zext[t], std::fabs(sh.rq[4 * (size_t)q + 2]));
+    }
     for (int i = 0; i < p; ++i) {
       const Shape& si = c->shapes[c->sid[i]];
-      if (std::hypot(dsh[3 * i], dsh[3 * i + 1]) + si.a >= pitch)
+      if (std::sqrt(dsh[3 * i] * dsh[3 * i] + dsh[3 * i + 1] * dsh[3 * i + 1] + dsh[3 * i + 2] * dsh[3 * i + 2]) +
+              si.a >= pitch)
         return fail(c, SMR_E_INVALID_ARG, "a displaced particle reaches a pitch or more from its cell centre");
       for (int dy = -1; dy <= 1; ++dy)
         for (int dx = -1; dx <= 1; ++dx) {
-          auto it = idx0.find({c->pi[i] + dx, c->pj[i] + dy});
-          if (it == idx0.end() || it->second == i) continue;
-          const int j = it->second;
-          const Shape& sj = c->shapes[c->sid[j]];
-          const double ei = si.sampled ? si.lateral : si.a, ej = sj.sampled ? sj.lateral : sj.a;
-          if (std::hypot(centres[3 * i] - centres[3 * j], centres[3 * i + 1] - centres[3 * j + 1]) <= ei + ej)
-            return fail(c, SMR_E_INVALID_ARG, "two neighbouring particles overlap");
+          auto it = cellp.find({c->pi[i] + dx, c->pj[i] + dy});
+          if (it == cellp.end()) continue;
+          for (int j : it->second) {
+            if (j == i) continue;
+            const Shape& sj = c->shapes[c->sid[j]];
+            const double ei = si.sampled ? si.lateral : si.a, ej = sj.sampled ? sj.lateral : sj.a;
+            if (std::hypot(centres[3 * i] - centres[3 * j], centres[3 * i + 1] - centres[3 * j + 1]) <= ei + ej &&
+                std::fabs(centres[3 * i + 2] - centres[3 * j + 2]) < zext[c->sid[i]] + zext[c->sid[j]])
+              return fail(c, SMR_E_INVALID_ARG, "two neighbouring particles overlap");
+          }
         }
     }
   }
   c->any_dshift = anyd;
+  c->multi = multi;
   // ---- levels
   std::vector<int> bi(c->pi), bj(c->pj);
   std::vector<Level> levs;
   for (int s = 0;; ++s) {
     Level L;
     L.box = pitch * (double)(1 << s);
-    if (s == 0) {
+    if (s == 0 && !multi) {
       L.bi = bi;
       L.bj = bj;
     } else {
@@ -794,7 +820,7 @@ int set_scene(Ctx* c, int p, const double* centres, const int* shape_ids, const 
     c->blk_sm.push_back(s); c->blk_sn.push_back(s); c->blk_dx.push_back(0); c->blk_dy.push_back(0);
     c->blk_off.insert(c->blk_off.end(), {0.0, 0.0, 0.0});
   }
-  std::map<std::tuple<int, int, int, int, unsigned long long, unsigned long long>, int> bkey;
+  std::map<std::tuple<int, int, int, int, unsigned long long, unsigned long long, unsigned long long>, int> bkey;
   auto bits = [](double v) { unsigned long long u; std::memcpy(&u, &v, sizeof u); return u; };
   c->nr_ptr.assign(1, 0);
   c->nr_col.clear();
@@ -802,35 +828,59 @@ int set_scene(Ctx* c, int p, const double* centres, const int* shape_ids, const 
   for (int mu = 0; mu < p; ++mu) {
     for (int dy = -1; dy <= 1; ++dy)
       for (int dx = -1; dx <= 1; ++dx) {
-        auto it = idx0.find({c->pi[mu] + dx, c->pj[mu] + dy});
-        if (it == idx0.end()) continue;
-        int nu = it->second, b;
-        if (nu == mu) {
-          b = c->sid[mu];
-        } else {
-          // r_mu - r_nu: the lattice offset, plus the displacements
-          double ox = -dx * pitch, oy = -dy * pitch;
-          if (anyd) {
-            ox += dsh[3 * mu] - dsh[3 * nu];
-            oy += dsh[3 * mu + 1] - dsh[3 * nu + 1];
-          }
-          auto key = std::make_tuple(c->sid[mu], c->sid[nu], -dx, -dy, anyd ? bits(ox) : 0ull,
-                                     anyd ? bits(oy) : 0ull);
-          auto f = bkey.find(key);
-          if (f == bkey.end()) {
-            b = (int)c->blk_sm.size();
-            bkey[key] = b;
-            c->blk_sm.push_back(c->sid[mu]); c->blk_sn.push_back(c->sid[nu]);
-            c->blk_dx.push_back(-dx); c->blk_dy.push_back(-dy);
-            c->blk_off.insert(c->blk_off.end(), {ox, oy, 0.0});
+        auto it = cellp.find({c->pi[mu] + dx, c->pj[mu] + dy});
+        if (it == cellp.end()) continue;
+        for (int nu : it->second) {
+          int b;
+          if (nu == mu) {
+            b = c->sid[mu];
           } else {
-            b = f->second;
+            // r_mu - r_nu: the lattice offset, plus the displacements
+            double ox = -dx * pitch, oy = -dy * pitch, oz = 0.0;
+            if (anyd) {
+              ox += dsh[3 * mu] - dsh[3 * nu];
+              oy += dsh[3 * mu + 1] - dsh[3 * nu + 1];
+              oz = dsh[3 * mu + 2] - dsh[3 * nu + 2];
+            }
+            auto key = std::make_tuple(c->sid[mu], c->sid[nu], -dx, -dy, anyd ? bits(ox) : 0ull,
+                                       anyd ? bits(oy) : 0ull, anyd ? bits(oz) : 0ull);
+            auto f = bkey.find(key);
+            if (f == bkey.end()) {
+              b = (int)c->blk_sm.size();
+              bkey[key] = b;
+              c->blk_sm.push_back(c->sid[mu]); c->blk_sn.push_back(c->sid[nu]);
+              c->blk_dx.push_back(-dx); c->blk_dy.push_back(-dy);
+              c->blk_off.insert(c->blk_off.end(), {ox, oy, oz});
+            } else {
+              b = f->second;
+            }
           }
+          c->nr_col.push_back(nu);
+          c->nr_blk.push_back(b);
         }
-        c->nr_col.push_back(nu);
-        c->nr_blk.push_back(b);
       }
     c->nr_ptr.push_back((int)c->nr_col.size());
+  }
+  // the finest box of every particle, and each box's particles (CSR)
+  {
+    const Level& L0 = c->lev[0];
+    c->cell_of.assign(p, 0);
+    std::vector<int> cptr(L0.nbox + 1, 0), cidx(p);
+    if (multi) {
+      std::map<std::pair<int, int>, int> bidx;
+      for (int b = 0; b < L0.nbox; ++b) bidx[{L0.bi[b], L0.bj[b]}] = b;
+      for (int i = 0; i < p; ++i) c->cell_of[i] = bidx.at({c->pi[i], c->pj[i]});
+    } else {
+      for (int i = 0; i < p; ++i) c->cell_of[i] = i;
+    }
+    for (int i = 0; i < p; ++i) cptr[c->cell_of[i] + 1]++;
+    for (int b = 0; b < L0.nbox; ++b) cptr[b + 1] += cptr[b];
+    std::vector<int> fill(cptr.begin(), cptr.end() - 1);
+    for (int i = 0; i < p; ++i) cidx[fill[c->cell_of[i]]++] = i;
+    int rc;
+    if ((rc = upload(c, &c->d_cell_of, c->cell_of)) || (rc = upload(c, &c->d_cell_ptr, cptr)) ||
+        (rc = upload(c, &c->d_cell_idx, cidx)))
+      return rc;
   }
   c->nblk = (int)c->blk_sm.size();
   std::vector<int> pcp(p + 1), pcc(p), pcb(p);

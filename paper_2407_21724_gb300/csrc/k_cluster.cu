@@ -210,6 +210,10 @@ bool cluster_ok(const Ctx* c) { return 8 * c->npsi <= 256; }
 
 int build_clusters(Ctx* c) {
   if (c->cl_ready) return SMR_OK;
+  if (c->multi) {
+    c->err = "the cluster preconditioner needs at most one particle per lattice cell";
+    return SMR_E_INVALID_ARG;
+  }
   if (!cluster_ok(c)) {
     c->err = "the cluster preconditioner needs 4 x 2 n_psi <= 256 (n_psi <= 32)";
     return SMR_E_INVALID_ARG;

@@ -300,6 +300,7 @@ int nn_init(Ctx* c, int width, unsigned long long seed) {
 int nn_features(Ctx* c, const double* d_khat, const double* d_pol, float* feat, cudaStream_t st) {
   if (!c->nn.p32) { c->err = "call smr_nn_init first"; return SMR_E_STATE; }
   if (c->S > kShapesMax) { c->err = "learned features support at most 8 shapes"; return SMR_E_INVALID_ARG; }
+  if (c->multi) { c->err = "learned features need at most one particle per lattice cell"; return SMR_E_INVALID_ARG; }
   Level& L0 = c->lev[0];
   // lattice indices of particles (level-0 boxes are the particles)
   int* d_pi = nullptr;

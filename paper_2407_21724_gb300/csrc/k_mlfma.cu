@@ -1245,6 +1245,13 @@ int ensure_spectra(Ctx* c, int R, int prec) {
       if (s + 1 < c->nlev)
         gmax = std::max(gmax, (size_t)L.nbox * c->lev[s + 1].nth * L.nph * 4 * R * es);
     }
+    if (c->pspec[p]) cudaFree(c->pspec[p]);
+    c->pspec[p] = nullptr;
+    if (c->multi && cudaMalloc(&c->pspec[p], (size_t)c->p * c->lev[0].K * 4 * R * es) != cudaSuccess) {
+      c->err = "out of device memory for the per-particle spectra";
+      c->spec_prec = -1;
+      return SMR_E_OOM;
+    }
     if (c->G_buf[p]) cudaFree(c->G_buf[p]);
     c->G_buf[p] = nullptr;
     if (gmax && cudaMalloc(&c->G_buf[p], gmax) != cudaSuccess) {
@@ -1302,6 +1309,35 @@ bool anterp4_ok(Ctx* c, int s) {
     attr = true;
   }
   return true;
+}
+
+// Several particles in one finest box.  Box b's outgoing spectrum is the
+// sum of its particles' (each already shifted to the box centre), and each
+// particle receives its box's incoming spectrum; a row is one box's or one
+// particle's [K0][4][R] spectrum.  Grid: (boxes or particles, row chunks of
+// 256 elements); both kernels guard the row end.
+template <typename V>
+__global__ void k_cell_sum(int nbox, long long row, const int* __restrict__ ptr, const int* __restrict__ idx,
+                           const V* __restrict__ part, V* __restrict__ box) {
+  const int b = blockIdx.x;
+  const long long e = blockIdx.y * (long long)blockDim.x + threadIdx.x;
+  if (b >= nbox || e >= row) return;
+  V acc = part[(size_t)idx[ptr[b]] * row + e];
+  for (int t = ptr[b] + 1; t < ptr[b + 1]; ++t) {
+    const V v = part[(size_t)idx[t] * row + e];
+    acc.x += v.x;
+    acc.y += v.y;
+  }
+  box[(size_t)b * row + e] = acc;
+}
+
+template <typename V>
+__global__ void k_cell_bcast(int p, long long row, const int* __restrict__ cell, const V* __restrict__ box,
+                             V* __restrict__ part) {
+  const int mu = blockIdx.x;
+  const long long e = blockIdx.y * (long long)blockDim.x + threadIdx.x;
+  if (mu >= p || e >= row) return;
+  part[(size_t)mu * row + e] = box[(size_t)cell[mu] * row + e];
 }
 
 template <typename T>
@@ -1403,11 +1439,18 @@ static int far_impl(Ctx* c, int R, const double2* x, double2* y, bool accumulate
       if (rc) return rc;
     } else {
     int nsub = (16 + std::max(1, 16 / RC) - 1) / std::max(1, 16 / RC);
+    V* agg = (V*)(c->multi ? c->pspec[f64 ? 0 : 1] : L0.d_out);
     k_aggregate<T><<<(unsigned)(c->ntile * nsub * nkc * nrc), 256, sm, st>>>(
         L0.K, c->npsi, R, RC, nkc, c->d_tile_shape, c->d_tile_start, c->d_tile_count, c->d_perm, x,
         (const V*)(f64 ? (void*)c->d_P64 : (void*)c->d_P32), c->d_dshift, c->any_dshift, L0.d_khat,
-        c->k, (V*)L0.d_out);
+        c->k, agg);
     SMR_LAUNCH(c);
+    if (c->multi) {
+      const long long row = (long long)L0.K * 4 * R;
+      k_cell_sum<V><<<dim3((unsigned)L0.nbox, (unsigned)((row + 255) / 256)), 256, 0, st>>>(
+          L0.nbox, row, c->d_cell_ptr, c->d_cell_idx, agg, (V*)L0.d_out);
+      SMR_LAUNCH(c);
+    }
     pend(c, st);
     }
   }
@@ -1565,10 +1608,19 @@ static int far_impl(Ctx* c, int R, const double2* x, double2* y, bool accumulate
       return rc;
     }
     int nsub = (16 + std::max(1, 16 / RC) - 1) / std::max(1, 16 / RC);
+    const V* inc = (const V*)L0.d_in;
+    if (c->multi) {
+      const long long row = (long long)L0.K * 4 * R;
+      V* part = (V*)c->pspec[f64 ? 0 : 1];
+      k_cell_bcast<V><<<dim3((unsigned)c->p, (unsigned)((row + 255) / 256)), 256, 0, st>>>(
+          c->p, row, c->d_cell_of, (const V*)L0.d_in, part);
+      SMR_LAUNCH(c);
+      inc = part;
+    }
     cudaFuncSetAttribute(k_receive<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     k_receive<T><<<(unsigned)(c->ntile * nsub * nrc), thr, sm, st>>>(
         L0.K, c->npsi, R, RC, c->d_tile_shape, c->d_tile_start, c->d_tile_count, c->d_perm,
-        (const V*)L0.d_in, (const V*)(f64 ? (void*)c->d_P64 : (void*)c->d_P32), L0.d_w, c->d_dshift,
+        inc, (const V*)(f64 ? (void*)c->d_P64 : (void*)c->d_P32), L0.d_w, c->d_dshift,
         c->any_dshift, L0.d_khat, c->k, c->zeta, y, accumulate ? 1 : 0);
     SMR_LAUNCH(c);
     pend(c, st);
@@ -1770,7 +1822,8 @@ static void use_lane(Ctx* c, int j) {
   c->d_tcn_part = a.tcn_part;
 }
 
-int lanes_for(const Ctx* c, int R) { return c->prof ? 1 : std::max(1, std::min(R, c->n_lanes)); }
+// one lane where the per-particle spectra of several-per-box scenes are shared
+int lanes_for(const Ctx* c, int R) { return (c->prof || c->multi) ? 1 : std::max(1, std::min(R, c->n_lanes)); }
 
 // Side streams and events of lanes 0 .. n-1 for the overlapped product
 // (created outside graph capture, kept until the context goes).

@@ -244,6 +244,14 @@ struct Ctx {
   double* d_centres = nullptr;          // [p][3]
   double* d_dshift = nullptr;           // [p][3] r_mu - c_box (finest level)
   int any_dshift = 0;
+  // several particles in one finest box: the boxes are the occupied cells,
+  // aggregation sums each box's particles and receive reads its box
+  int multi = 0;
+  std::vector<int> cell_of;              // [p] finest box of each particle
+  int* d_cell_of = nullptr;
+  int* d_cell_ptr = nullptr;             // [nbox0 + 1] CSR of each box's particles
+  int* d_cell_idx = nullptr;             // [p]
+  void* pspec[2] = {nullptr, nullptr};   // per-particle level-0 spectra (FP64, FP32)
   // near SpMV: CSR by particle, block ids; blocks stored transposed [nb][2n][2n]
   std::vector<int> nr_ptr, nr_col, nr_blk;
   int* d_nr_ptr = nullptr;

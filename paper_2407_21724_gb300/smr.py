@@ -624,8 +624,11 @@ def smr_mesh_static_modes(verts, tris, n_perp, n_par):
 
 
 def scene_from_workload(w, **opts):
-    """Create a context and set the scene of a workload dict (workloads.make)."""
-    ctx = smr_create(pitch=w["pitch"], **opts)
+    """Create a context and set the scene of a workload dict (workloads.make);
+    the workload's L0, if it names one, unless opts overrides it."""
+    o = {"L0": w["L0"]} if "L0" in w else {}
+    o.update(opts)
+    ctx = smr_create(pitch=w["pitch"], **o)
     add_shapes(ctx, w["shapes"])
     smr_set_scene(ctx, w["centres"], w["shape_ids"], w["eps_in"])
     return ctx

@@ -160,6 +160,62 @@ def make(name, **kw):
                           f'{2*modes} modes/current, {n*4*modes} unknowns',
                     centres=C, shape_ids=ids, shapes=shapes8(shape, modes)[:3], eps_in=EPS_IN,
                     pitch=PITCH, incidences=inc)
+    if name == 'spiral_dense':
+        # the paper's spiral spacing, c = sqrt(3) R, for n identical spheres
+        # of radius R: neighbours about 1.4 diameters apart, so a lattice cell
+        # of 0.5 wavelengths holds up to three centres
+        n = kw.get('n', 2000)
+        R = kw.get('R', 0.1)
+        modes = kw.get('modes', 16)
+        i = np.arange(1, n + 1, dtype=float)
+        ga = 2 * np.pi / ((1 + np.sqrt(5)) / 2) ** 2
+        c = np.sqrt(3.0) * R
+        C = np.zeros((n, 3))
+        C[:, 0], C[:, 1] = c * np.sqrt(i) * np.cos(i * ga), c * np.sqrt(i) * np.sin(i * ga)
+        inc = kw.get('incidences') or [incidence(0, 0, 'x')]
+        return dict(label=f'golden-angle spiral of {n} spheres R={R}, c = sqrt(3) R, {2*modes} modes/current, '
+                          f'{n*4*modes} unknowns',
+                    centres=C, shape_ids=np.zeros(n, dtype=np.int32), shapes=[(R, modes, modes)],
+                    eps_in=EPS_IN, pitch=PITCH, incidences=inc)
+    if name == 'moire':
+        # two-layer Moire superlattice (the 2.5D example of Sec. V): the
+        # vertices of a honeycomb of side `side` (m x m unit cells, two
+        # vertices each) at z = -h/2, and the same honeycomb turned by
+        # `twist` degrees about z at z = +h/2; nanodisks of radius `radius`
+        # and height radius / 2 (cylinder meshes), or spheres.  Lengths in
+        # wavelengths from the paper's 400 / 300 / 100 nm at 600 nm.  Cells of
+        # 0.85 wavelengths keep every disk within a cell size of its cell
+        # centre; L0 = 16 for those cells.
+        m = kw.get('m', 16)
+        side = kw.get('side', 400 / 600)
+        h = kw.get('h', 300 / 600)
+        R = kw.get('radius', 100 / 600)
+        twist = np.radians(kw.get('twist', 5.0))
+        modes = kw.get('modes', 10)
+        a1 = np.array([np.sqrt(3) * side, 0.0])
+        a2 = np.array([np.sqrt(3) * side / 2, 1.5 * side])
+        g = np.arange(m) - (m - 1) / 2.0
+        I, J = np.meshgrid(g, g, indexing='xy')
+        base = I.ravel()[:, None] * a1 + J.ravel()[:, None] * a2
+        layer = np.vstack([base, base + [0.0, side]])
+        layer -= layer.mean(axis=0)
+        rot = np.array([[np.cos(twist), -np.sin(twist)], [np.sin(twist), np.cos(twist)]])
+        C = np.zeros((2 * len(layer), 3))
+        C[:len(layer), :2], C[:len(layer), 2] = layer, -h / 2
+        C[len(layer):, :2], C[len(layer):, 2] = layer @ rot.T, h / 2
+        if kw.get('shape', 'disk') == 'sphere':
+            shapes = [(R, modes, modes)]
+        else:
+            V, T = cylinder_mesh(R, R / 2, n_phi=16, n_z=1, n_r=2)
+            shapes = [dict(kind='mesh', verts=V, tris=T, n_perp=modes, n_par=modes,
+                           label=f'disk r={R:.4f} h={R / 2:.4f}, {len(T)} triangles')]
+        n = len(C)
+        return dict(label=f'two-layer Moire lattice of {n} {"spheres" if kw.get("shape") == "sphere" else "nanodisks"} '
+                          f'(honeycomb side {side:.3f}, layers {h} apart, twist {np.degrees(twist):.1f} deg), '
+                          f'{2*modes} modes/current, {n*4*modes} unknowns',
+                    centres=C, shape_ids=np.zeros(n, dtype=np.int32), shapes=shapes, eps_in=EPS_IN,
+                    pitch=kw.get('pitch', 0.85), L0=kw.get('L0', 16),
+                    incidences=kw.get('incidences') or [incidence(0, 0, 'x')])
     if name == 'pbfins':
         # n x n geometric-phase (PB) metalens of identical nanofins, each
         # turned about z by its pb_angles value rounded to one of `bins`

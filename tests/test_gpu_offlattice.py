@@ -1,8 +1,10 @@
 """Particles off the lattice on the GPU against the FP64 oracle: a jittered
-lattice of random-radius spheres, a sparse golden-angle spiral, and jittered
-meshed cylinders.  Displaced centres keep their shift to the finest-group
-centre in aggregation and receive, and their exterior near blocks are
-computed for the exact offsets (Sec. V, non-lattice arrays).
+lattice of random-radius spheres, a sparse golden-angle spiral, jittered
+meshed cylinders, and scenes with several particles per finest cell (the
+paper's dense spiral spacing, a two-layer Moire lattice).  Displaced centres
+keep their shift to the finest-group centre in aggregation and receive,
+their exterior near blocks are computed for the exact offsets, and a cell's
+particles sum into one box spectrum (Sec. V, non-lattice and 2.5D arrays).
 
 Bars as for the lattice: <= 1e-10 relative per FP64 product, <= 2e-5 per
 FP32 product, near blocks to 1e-12, solutions to their tolerance in the
@@ -38,7 +40,7 @@ class Case:
         self.ctx = smr.scene_from_workload(w)
         self.info = smr.smr_info(self.ctx)
         self.sc = opm.Scene(w["centres"], w["shape_ids"], w["shapes"], eps_in=w["eps_in"])
-        self.M = oml.MLFMA(self.sc, w["pitch"])
+        self.M = oml.MLFMA(self.sc, w["pitch"], L0=w.get("L0", 10))
 
     def gpu_matvec(self, x, prec=smr.SMR_PREC_FP64):
         xd = torch.from_numpy(np.ascontiguousarray(x)).cuda()
@@ -173,8 +175,9 @@ def test_jittered_meshed_cylinders():
 
 def test_displaced_scenes_rejected():
     """Overlapping neighbours, a particle reaching a pitch from its cell
-    centre, two centres in one cell and centres out of the plane are
-    refused with SMR_E_INVALID_ARG, and the context stays usable."""
+    centre (in the plane or, for a centre off the mean plane, in 3D) and two
+    overlapping particles in one cell are refused with SMR_E_INVALID_ARG,
+    and the context stays usable."""
     ctx = smr.smr_create(pitch=0.5)
     smr.smr_add_sphere(ctx, 0.15, 4, 4)
     ids = np.zeros(4, dtype=np.int32)
@@ -184,9 +187,9 @@ def test_displaced_scenes_rejected():
     bad.append(c)
     c = good.copy(); c[0, :2] += 0.249                          # 0.352 + 0.15 >= 0.5
     bad.append(c)
-    c = good.copy(); c[1, :2] = c[0, :2] + [0.1, 0.0]          # same cell
+    c = good.copy(); c[1, :2] = c[0, :2] + [0.1, 0.0]          # overlapping, one cell
     bad.append(c)
-    c = good.copy(); c[2, 2] += 0.01                           # out of the plane
+    c = good.copy(); c[2, 2] += 0.6                             # 0.45 above the mean plane: 0.45 + 0.15
     bad.append(c)
     for cc in bad:
         with pytest.raises(smr.SmrError) as e:
@@ -196,3 +199,62 @@ def test_displaced_scenes_rejected():
     smr.smr_set_scene(ctx, c, ids, 4.0)
     assert smr.smr_info(ctx)["n_near_blocks"] == 1 + 12
     smr.smr_destroy(ctx)
+
+
+@pytest.fixture(scope="module")
+def dense():
+    # the paper's spiral spacing (c = sqrt(3) R): up to 4 centres per cell
+    c = Case(workloads.make("spiral_dense", n=150, R=0.1, modes=8))
+    yield c
+    smr.smr_destroy(c.ctx)
+
+
+@pytest.fixture(scope="module")
+def moire():
+    # two 4 x 4-cell honeycomb layers 0.5 apart, the upper turned by 5 deg
+    c = Case(workloads.make("moire", m=4, shape="sphere", modes=6))
+    yield c
+    smr.smr_destroy(c.ctx)
+
+
+@pytest.mark.parametrize("which", ["dense", "moire"])
+def test_several_particles_per_cell(dense, moire, which):
+    c = dense if which == "dense" else moire
+    t = c.M.tree
+    assert not t.one_per_cell
+    assert c.info["n_box"][0] == len(t.levels[0]["ij"]) < c.sc.p
+    for s in range(t.n_levels):
+        assert c.info["n_box"][s] == len(t.levels[s]["ij"])
+        assert c.info["n_il"][s] == len(t.levels[s]["il"])
+    x = crandn(c.info["n_unknowns"], 8)
+    ref = c.M.matvec(x)
+    assert rel(c.gpu_matvec(x), ref) < 1e-10
+    # the level-0 outgoing spectra of that product: each box the sum of its
+    # particles' spectra, boxes in the oracle's order
+    assert rel(smr.smr_copy_level(c.ctx, 0, 0)[..., 0], c.M.aggregate(x)) < 1e-12
+    assert rel(c.gpu_matvec(x, smr.SMR_PREC_FP32), ref) < 2e-5
+    # pair blocks, including pairs inside one cell
+    same = [(mu, nu) for (mu, nu) in t.near_pairs() if mu != nu and t.cell[mu] == t.cell[nu]]
+    assert same
+    for mu, nu in same[:6]:
+        assert rel(smr.smr_copy_pair_block(c.ctx, int(mu), int(nu)), c.M.near_block(mu, nu)) < 1e-12
+
+
+def test_moire_solve(moire):
+    c = moire
+    kh, pol = workloads.incidence(0, 0, "x")
+    n = c.info["n_unknowns"]
+    b = torch.empty(n, dtype=torch.complex128, device="cuda")
+    smr.smr_rhs_plane_waves(c.ctx, [kh], [pol], b)
+    torch.cuda.synchronize()
+    bo = opm.rhs(c.sc, kh, pol)
+    assert rel(b.cpu().numpy(), bo) < 1e-12
+    for prec, tol in ((smr.SMR_PREC_FP64, 1e-10), (smr.SMR_PREC_FP32, 1e-6)):
+        x = torch.zeros_like(b)
+        rc, st = smr.smr_solve(c.ctx, b, x, tol=tol, maxit=400, precision=prec)
+        assert rc == 0
+        assert np.linalg.norm(bo - c.M.matvec(x.cpu().numpy())) / np.linalg.norm(bo) <= 1.01 * tol
+    # the cluster preconditioner needs one particle per cell
+    z = torch.empty_like(b)
+    with pytest.raises(smr.SmrError):
+        smr.smr_precond_cluster(c.ctx, b, z)
