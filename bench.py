@@ -418,20 +418,36 @@ def run_ours(a):
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
         if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     hbm = peaks.get("hbm_gbs", 6800.0)
-    if top.split(":")[0] in ALU_BOUND:
-        # dense per-particle contractions on the FP32 pipes: against the FP32
-        # CUDA-core peak (152 SMs x 128 lanes x 2 flop x 2.07 GHz)
+    # CUDA-core peaks measured on this device (FP32 scalar and packed FMA, FP64 FMA)
+    alu_peaks = {}
+    for kind, key in ((0, "fp32_fma"), (1, "fp32x2_fma"), (2, "fp64_fma")):
+        try:
+            alu_peaks[key] = round(smr.smr_measure_peak(kind), 2)
+        except smr.SmrError:
+            pass
+    fp32_peak = max(alu_peaks.get("fp32_fma", 0.0), alu_peaks.get("fp32x2_fma", 0.0))
+    # the bound is the roof the launch would hit first: its FP32 flops at the
+    # FP32 peak against its bytes at the HBM peak (the per-pair near blocks
+    # of displaced scenes make the near product HBM-bound)
+    alu_first = (top.split(":")[0] in ALU_BOUND and
+                 d["flops"] / ((fp32_peak or FP32_PEAK_TFLOPS) * 1e12) > d["bytes"] / (hbm * 1e9))
+    if alu_first:
+        # dense per-particle contractions on the FP32 pipes: against the
+        # measured FP32 CUDA-core peak (else 152 SMs x 128 lanes x 2 flop x 2.07 GHz)
         ach = d["flops"] / d["ms"] / 1e9
-        roofline = dict(kernel=top, bound="alu", achieved=ach, peak=FP32_PEAK_TFLOPS, unit="TFLOP/s",
-                        frac=ach / FP32_PEAK_TFLOPS, peak_source="derived: 152 SMs x 128 FP32 lanes x 2 flop "
-                        "x 2070 MHz", hbm_GBps=d["bytes"] / d["ms"] / 1e6)
+        pk = fp32_peak or FP32_PEAK_TFLOPS
+        roofline = dict(kernel=top, bound="alu", achieved=ach, peak=pk, unit="TFLOP/s", frac=ach / pk,
+                        peak_source="measured (smr_measure_peak, FP32 FMA)" if fp32_peak else
+                        "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
+                        hbm_GBps=d["bytes"] / d["ms"] / 1e6)
     else:
         ach = d["bytes"] / d["ms"] / 1e6
         roofline = dict(kernel=top, bound="hbm", achieved=ach, peak=hbm, unit="GB/s", frac=ach / hbm,
                         peak_source="measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks
                         else "fallback 6800 GB/s")
     roofline.update(traffic=traffic_for(top), algorithmic_bytes_per_launch=d["bytes"],
-                    algorithmic_flops_per_launch=d["flops"], launch_ms=d["ms"], share_of_step=d["ms"] / tot)
+                    algorithmic_flops_per_launch=d["flops"], launch_ms=d["ms"], share_of_step=d["ms"] / tot,
+                    alu_peaks_measured_tflops=alu_peaks)
     breakdown = {k: dict(ms=round(v["ms"], 4), share=round(v["ms"] / tot, 4), launches=round(v["launches"]),
                          GBps=round(v["bytes"] / v["ms"] / 1e6, 1),
                          TFLOPs=round(v["flops"] / v["ms"] / 1e9, 2)) for k, v in names.items()}

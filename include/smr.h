@@ -531,6 +531,15 @@ int smr_nn_precond(smr_ctx* ctx, const double* khat, const double* pol, double s
 int smr_nn_predict(smr_ctx* ctx, const double* khat, const double* pol, double scale, void* x0,
                    void* stream);
 
+/* Measured arithmetic peak of the current CUDA device, in TFLOP/s (no
+ * context needed): kind 0 = FP32 fused multiply-add, 1 = packed two-wide
+ * FP32 multiply-add, 2 = FP64 fused multiply-add; 16 independent chains per
+ * thread, 8 CTAs of 256 threads per SM, one warm-up launch, the second timed
+ * with CUDA events (a few ms for FP32, about 20 ms for FP64).  These are the
+ * denominators of the CUDA-core roofline.  SMR_E_INVALID_ARG for another
+ * kind, SMR_E_CUDA if a launch fails. */
+int smr_measure_peak(int kind, double* tflops);
+
 /* Debug and parity access (host outputs, layouts as the oracle's):
  *  smr_copy_pattern: receiving patterns of a shape, [n_psi][2][K_0] complex
  *    (theta and phi components of Eq. 26 on the level-0 grid);

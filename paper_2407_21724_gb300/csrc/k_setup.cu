@@ -3,6 +3,9 @@
 // and near fields.  Everything here runs once per scene (or per output
 // request) in FP64; the hot path reads FP64 or FP32 copies of these tables.
 #include <cmath>
+#include <cstring>
+#include <map>
+#include <tuple>
 
 #include "smr_internal.h"
 
@@ -278,7 +281,7 @@ __global__ void k_near_f(int nb, int npsi, int Q, const int* __restrict__ bsm,
 __global__ void k_near_z(int nb, int npsi, int Q, const int* __restrict__ bsm,
                          const double* __restrict__ modes, const double* __restrict__ rq,
                          const double2* __restrict__ F, double kw, double zeta,
-                         double2* __restrict__ Bt, int blk0) {
+                         double2* __restrict__ Bt, const int* __restrict__ bidx) {
   int b = blockIdx.y;
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= npsi * npsi) return;
@@ -302,12 +305,30 @@ __global__ void k_near_z(int nb, int npsi, int Q, const int* __restrict__ bsm,
   double2 T = make_double2(kw * v.y - d.y / kw, -kw * v.x + d.x / kw);
   double2 K = make_double2(-kk.x, -kk.y);
   int n2 = 2 * npsi;
-  double2* B = Bt + (size_t)(blk0 + b) * n2 * n2;
+  double2* B = Bt + (size_t)bidx[b] * n2 * n2;
   // B stored transposed: B[col * n2 + row]
   B[(size_t)n * n2 + m] = make_double2(zeta * T.x, zeta * T.y);
   B[(size_t)(npsi + n) * n2 + m] = K;
   B[(size_t)n * n2 + npsi + m] = make_double2(-K.x, -K.y);
   B[(size_t)(npsi + n) * n2 + npsi + m] = make_double2(T.x / zeta, T.y / zeta);
+}
+
+// Reciprocity of the exterior blocks: T and K are symmetric bilinear forms
+// (the Green's function and the triple product under the swap of source and
+// test), so Z^{nu mu} = [T_nm^T ...] follows from Z^{mu nu} = [z T, K; -K, T/z]
+// as Z^{nu mu}(r, c) = s_r s_c Z^{mu nu}(c, r), s = +1 on the electric rows
+// and -1 on the magnetic ones.  Grid: (element chunks of 256, pairs); both
+// blocks stored transposed (B[col * n2 + row]).
+__global__ void k_near_mirror(int nd, int npsi, const int* __restrict__ dst, const int* __restrict__ src,
+                              double2* __restrict__ Bt) {
+  const int b = blockIdx.y;
+  const int n2 = 2 * npsi;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nd || t >= n2 * n2) return;
+  const int i = t / n2, j = t % n2;             // A(row j, col i) is A[i * n2 + j]
+  const double2 a = Bt[(size_t)src[b] * n2 * n2 + (size_t)i * n2 + j];
+  const double sg = ((i < npsi) == (j < npsi)) ? 1.0 : -1.0;
+  Bt[(size_t)dst[b] * n2 * n2 + (size_t)j * n2 + i] = make_double2(sg * a.x, sg * a.y);
 }
 
 // Closed-form self block of a sphere (Eq. 16 with delta = 1): per (l, m) the
@@ -395,25 +416,55 @@ int build_near(Ctx* c) {
   SMR_CUDA(c, cudaMemcpy(c->d_B64, selfT.data(), (size_t)S * bsz * sizeof(double2), cudaMemcpyHostToDevice));
   int rc = upload(c, &c->d_Pinv64, invT);
   if (rc) return rc;
-  // exterior blocks, in chunks
+  // exterior blocks: a block whose swapped pair (shapes exchanged, offset
+  // negated) is also stored is computed once and mirrored into the other
   int nex = nb_total - S;
   if (nex > 0) {
-    std::vector<int> bsm(nex), bsn(nex);
-    std::vector<double> bdc(3 * nex);
+    auto bits = [](double v) {
+      if (v == 0.0) v = 0.0;                   // -0 and +0 are one key
+      unsigned long long u;
+      std::memcpy(&u, &v, sizeof u);
+      return u;
+    };
+    typedef std::tuple<int, int, unsigned long long, unsigned long long, unsigned long long> Key;
+    std::map<Key, int> index;
+    auto off = [&](int b, int d) { return c->blk_off[3 * (size_t)(S + b) + d]; };
+    for (int b = 0; b < nex; ++b)
+      index[Key(c->blk_sm[S + b], c->blk_sn[S + b], bits(off(b, 0)), bits(off(b, 1)), bits(off(b, 2)))] = b;
+    std::vector<int> from(nex, -1), prim, mdst, msrc;
+    std::vector<char> done(nex, 0);
     for (int b = 0; b < nex; ++b) {
-      bsm[b] = c->blk_sm[S + b];
-      bsn[b] = c->blk_sn[S + b];
-      for (int d = 0; d < 3; ++d) bdc[3 * b + d] = c->blk_off[3 * (size_t)(S + b) + d];
+      if (done[b]) continue;
+      done[b] = 1;
+      prim.push_back(b);
+      auto it = index.find(Key(c->blk_sn[S + b], c->blk_sm[S + b], bits(-off(b, 0)), bits(-off(b, 1)),
+                               bits(-off(b, 2))));
+      if (it != index.end() && !done[it->second]) {
+        done[it->second] = 1;
+        mdst.push_back(S + it->second);
+        msrc.push_back(S + b);
+      }
     }
-    int *d_bsm = nullptr, *d_bsn = nullptr;
+    const int np = (int)prim.size();
+    std::vector<int> bsm(np), bsn(np), bid(np);
+    std::vector<double> bdc(3 * (size_t)np);
+    for (int i = 0; i < np; ++i) {
+      const int b = prim[i];
+      bsm[i] = c->blk_sm[S + b];
+      bsn[i] = c->blk_sn[S + b];
+      bid[i] = S + b;
+      for (int d = 0; d < 3; ++d) bdc[3 * (size_t)i + d] = off(b, d);
+    }
+    int *d_bsm = nullptr, *d_bsn = nullptr, *d_bid = nullptr, *d_md = nullptr, *d_ms = nullptr;
     double* d_bdc = nullptr;
-    if ((rc = upload(c, &d_bsm, bsm)) || (rc = upload(c, &d_bsn, bsn)) || (rc = upload(c, &d_bdc, bdc)))
+    if ((rc = upload(c, &d_bsm, bsm)) || (rc = upload(c, &d_bsn, bsn)) || (rc = upload(c, &d_bdc, bdc)) ||
+        (rc = upload(c, &d_bid, bid)) || (rc = upload(c, &d_md, mdst)) || (rc = upload(c, &d_ms, msrc)))
       return rc;
     int chunk = 64;
     double2* d_F = nullptr;
     SMR_CUDA(c, cudaMalloc((void**)&d_F, (size_t)chunk * c->Q * n * 7 * sizeof(double2)));
-    for (int b0 = 0; b0 < nex; b0 += chunk) {
-      int nbc = std::min(chunk, nex - b0);
+    for (int b0 = 0; b0 < np; b0 += chunk) {
+      int nbc = std::min(chunk, np - b0);
       int qt = std::max(1, 256 / n);
       dim3 g1((c->Q + qt - 1) / qt, nbc), t1(n, qt);
       k_near_f<<<g1, t1>>>(nbc, n, c->Q, d_bsm + b0, d_bsn + b0, d_bdc + 3 * b0, c->d_modes, c->d_rq,
@@ -421,7 +472,14 @@ int build_near(Ctx* c) {
       SMR_LAUNCH(c);
       dim3 g2((n * n + 127) / 128, nbc);
       k_near_z<<<g2, 128>>>(nbc, n, c->Q, d_bsm + b0, c->d_modes, c->d_rq, d_F, c->k, c->zeta,
-                            c->d_B64, S + b0);
+                            c->d_B64, d_bid + b0);
+      SMR_LAUNCH(c);
+    }
+    const int nm = (int)mdst.size();
+    for (int m0 = 0; m0 < nm; m0 += 65535) {
+      const int nd = std::min(65535, nm - m0);
+      dim3 g3((unsigned)((4 * n * n + 255) / 256), (unsigned)nd);
+      k_near_mirror<<<g3, 256>>>(nd, n, d_md + m0, d_ms + m0, c->d_B64);
       SMR_LAUNCH(c);
     }
     SMR_CUDA(c, cudaDeviceSynchronize());
@@ -429,6 +487,9 @@ int build_near(Ctx* c) {
     cudaFree(d_bsm);
     cudaFree(d_bsn);
     cudaFree(d_bdc);
+    cudaFree(d_bid);
+    cudaFree(d_md);
+    cudaFree(d_ms);
   }
   rc = copy32(c, c->d_B64, &c->d_B32, (long long)nb_total * bsz);
   if (rc) return rc;

@@ -109,6 +109,7 @@ _SIGS = {
     "smr_copy_level": (C.c_int, [_P, C.c_int, C.c_int, _D, C.c_size_t]),
     "smr_set_tensor_cores": (C.c_int, [_P, C.c_int]),
     "smr_add_shape_sampled": (C.c_int, [_P, C.c_int, _D, _D, C.c_int, C.c_int, _D, _D, C.POINTER(C.c_int)]),
+    "smr_measure_peak": (C.c_int, [C.c_int, _D]),
     "smr_add_shape_rotated": (C.c_int, [_P, C.c_int, C.c_double, C.POINTER(C.c_int)]),
     "smr_add_shape_mesh": (C.c_int, [_P, C.c_int, _D, C.c_int, C.POINTER(C.c_int), C.c_int, C.c_int,
                                      C.POINTER(C.c_int)]),
@@ -581,6 +582,16 @@ def smr_add_shape_mesh(ctx, verts, tris, n_perp, n_par):
     _check(ctx, lib().smr_add_shape_mesh(ctx, V.shape[0], _dptr(V), T.shape[0], tp, n_perp, n_par,
                                          C.byref(sid)))
     return sid.value
+
+
+def smr_measure_peak(kind):
+    """Measured TFLOP/s of the current device: 0 FP32 FMA, 1 packed FP32x2
+    FMA, 2 FP64 FMA."""
+    v = C.c_double()
+    rc = lib().smr_measure_peak(int(kind), C.byref(v))
+    if rc:
+        raise SmrError(rc, "smr_measure_peak failed")
+    return v.value
 
 
 def smr_add_shape_rotated(ctx, base, angle):
