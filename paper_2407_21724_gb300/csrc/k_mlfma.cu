@@ -1247,7 +1247,8 @@ int ensure_spectra(Ctx* c, int R, int prec) {
     }
     if (c->pspec[p]) cudaFree(c->pspec[p]);
     c->pspec[p] = nullptr;
-    if (c->multi && cudaMalloc(&c->pspec[p], (size_t)c->p * c->lev[0].K * 4 * R * es) != cudaSuccess) {
+    if ((c->multi || c->any_dshift) &&
+        cudaMalloc(&c->pspec[p], (size_t)c->p * c->lev[0].K * 4 * R * es) != cudaSuccess) {
       c->err = "out of device memory for the per-particle spectra";
       c->spec_prec = -1;
       return SMR_E_OOM;
@@ -1311,33 +1312,64 @@ bool anterp4_ok(Ctx* c, int s) {
   return true;
 }
 
-// Several particles in one finest box.  Box b's outgoing spectrum is the
-// sum of its particles' (each already shifted to the box centre), and each
-// particle receives its box's incoming spectrum; a row is one box's or one
-// particle's [K0][4][R] spectrum.  Grid: (boxes or particles, row chunks of
-// 256 elements); both kernels guard the row end.
-template <typename V>
-__global__ void k_cell_sum(int nbox, long long row, const int* __restrict__ ptr, const int* __restrict__ idx,
-                           const V* __restrict__ part, V* __restrict__ box) {
+// Finest boxes made of cells.  Box b's outgoing spectrum is the sum of its
+// particles' spectra, and each particle receives its box's incoming
+// spectrum; a row is one box's or one particle's [K0][4][R] spectrum.  With
+// `shift` set the kernels also carry each particle's displacement d from
+// its box centre: e^{+jk khat.d} into the sum, e^{-jk khat.d} out of the
+// broadcast (the tensor-core aggregation and receive work on unshifted
+// per-particle spectra).  Grid: (boxes or particles, row chunks of 256
+// elements); both kernels guard the row end.
+template <typename T>
+__device__ __forceinline__ typename CV<T>::V shift_phase(const double* d, const double* kh, double k, double sgn) {
+  const double ph = sgn * k * (kh[0] * d[0] + kh[1] * d[1] + kh[2] * d[2]);
+  T sn, cs;
+  if (sizeof(T) == 8) {
+    double s8, c8;
+    sincos(ph, &s8, &c8);
+    sn = (T)s8;
+    cs = (T)c8;
+  } else {
+    float s4, c4;
+    sincosf((float)ph, &s4, &c4);
+    sn = (T)s4;
+    cs = (T)c4;
+  }
+  return mkc(cs, sn);
+}
+
+template <typename T>
+__global__ void k_cell_sum(int nbox, long long row, int R, const int* __restrict__ ptr,
+                           const int* __restrict__ idx, int shift, const double* __restrict__ dshift,
+                           const double* __restrict__ khat, double k,
+                           const typename CV<T>::V* __restrict__ part, typename CV<T>::V* __restrict__ box) {
+  typedef typename CV<T>::V V;
   const int b = blockIdx.x;
   const long long e = blockIdx.y * (long long)blockDim.x + threadIdx.x;
   if (b >= nbox || e >= row) return;
-  V acc = part[(size_t)idx[ptr[b]] * row + e];
-  for (int t = ptr[b] + 1; t < ptr[b + 1]; ++t) {
-    const V v = part[(size_t)idx[t] * row + e];
+  const int kk = (int)(e / (4LL * R));
+  V acc = mkc((T)0, (T)0);
+  for (int t = ptr[b]; t < ptr[b + 1]; ++t) {
+    const int mu = idx[t];
+    V v = part[(size_t)mu * row + e];
+    if (shift) v = cmul(v, shift_phase<T>(dshift + 3 * mu, khat + 3 * kk, k, 1.0));
     acc.x += v.x;
     acc.y += v.y;
   }
   box[(size_t)b * row + e] = acc;
 }
 
-template <typename V>
-__global__ void k_cell_bcast(int p, long long row, const int* __restrict__ cell, const V* __restrict__ box,
-                             V* __restrict__ part) {
+template <typename T>
+__global__ void k_cell_bcast(int p, long long row, int R, const int* __restrict__ cell, int shift,
+                             const double* __restrict__ dshift, const double* __restrict__ khat, double k,
+                             const typename CV<T>::V* __restrict__ box, typename CV<T>::V* __restrict__ part) {
+  typedef typename CV<T>::V V;
   const int mu = blockIdx.x;
   const long long e = blockIdx.y * (long long)blockDim.x + threadIdx.x;
   if (mu >= p || e >= row) return;
-  part[(size_t)mu * row + e] = box[(size_t)cell[mu] * row + e];
+  V v = box[(size_t)cell[mu] * row + e];
+  if (shift) v = cmul(v, shift_phase<T>(dshift + 3 * mu, khat + 3 * (int)(e / (4LL * R)), k, -1.0));
+  part[(size_t)mu * row + e] = v;
 }
 
 template <typename T>
@@ -1433,26 +1465,34 @@ static int far_impl(Ctx* c, int R, const double2* x, double2* y, bool accumulate
          (double)c->p * 2 * c->npsi * R_ * 16 + (double)c->S * c->npsi * 2 * L0.K * es +
              (double)c->p * L0.K * 4 * R_ * es,
          32.0 * c->npsi * c->p * L0.K * R_);
-    if (!f64 && tc_aggregate_ok(c, R) && c->tune_tc_agg != 0) {
-      int rc = run_aggregate_tc(c, x, c->x32_of == x ? c->d_x32 : nullptr, (float2*)L0.d_out, st);
-      pend(c, st);
-      if (rc) return rc;
+    // per-particle spectra go through the box sum where boxes hold several
+    // particles, or where the tensor cores aggregate displaced particles
+    // (the sum then applies the displacement shifts)
+    const bool tc = !f64 && tc_aggregate_ok(c, R) && c->tune_tc_agg != 0;
+    const bool cells = c->multi || (tc && c->any_dshift);
+    V* agg = (V*)(cells ? c->pspec[f64 ? 0 : 1] : L0.d_out);
+    if (tc) {
+      int rc = run_aggregate_tc(c, x, c->x32_of == x ? c->d_x32 : nullptr, (float2*)agg, st);
+      if (rc) {
+        pend(c, st);
+        return rc;
+      }
     } else {
-    int nsub = (16 + std::max(1, 16 / RC) - 1) / std::max(1, 16 / RC);
-    V* agg = (V*)(c->multi ? c->pspec[f64 ? 0 : 1] : L0.d_out);
-    k_aggregate<T><<<(unsigned)(c->ntile * nsub * nkc * nrc), 256, sm, st>>>(
-        L0.K, c->npsi, R, RC, nkc, c->d_tile_shape, c->d_tile_start, c->d_tile_count, c->d_perm, x,
-        (const V*)(f64 ? (void*)c->d_P64 : (void*)c->d_P32), c->d_dshift, c->any_dshift, L0.d_khat,
-        c->k, agg);
-    SMR_LAUNCH(c);
-    if (c->multi) {
+      int nsub = (16 + std::max(1, 16 / RC) - 1) / std::max(1, 16 / RC);
+      k_aggregate<T><<<(unsigned)(c->ntile * nsub * nkc * nrc), 256, sm, st>>>(
+          L0.K, c->npsi, R, RC, nkc, c->d_tile_shape, c->d_tile_start, c->d_tile_count, c->d_perm, x,
+          (const V*)(f64 ? (void*)c->d_P64 : (void*)c->d_P32), c->d_dshift, c->any_dshift, L0.d_khat,
+          c->k, agg);
+      SMR_LAUNCH(c);
+    }
+    if (cells) {
       const long long row = (long long)L0.K * 4 * R;
-      k_cell_sum<V><<<dim3((unsigned)L0.nbox, (unsigned)((row + 255) / 256)), 256, 0, st>>>(
-          L0.nbox, row, c->d_cell_ptr, c->d_cell_idx, agg, (V*)L0.d_out);
+      k_cell_sum<T><<<dim3((unsigned)L0.nbox, (unsigned)((row + 255) / 256)), 256, 0, st>>>(
+          L0.nbox, row, R, c->d_cell_ptr, c->d_cell_idx, (tc && c->any_dshift) ? 1 : 0, c->d_dshift,
+          L0.d_khat, c->k, agg, (V*)L0.d_out);
       SMR_LAUNCH(c);
     }
     pend(c, st);
-    }
   }
   // upward: separable interpolation, theta then phi (+ shift + child sum)
   for (int s = 0; s + 1 < c->nlev; ++s) {
@@ -1602,21 +1642,27 @@ static int far_impl(Ctx* c, int R, const double2* x, double2* y, bool accumulate
          (double)c->p * L0.K * 4 * R_ * es + (double)c->S * c->npsi * 2 * L0.K * es +
              (accumulate ? 2.0 : 1.0) * c->p * 2 * c->npsi * R_ * 16,
          48.0 * c->p * c->npsi * L0.K * R_);
-    if (!f64 && tc_receive_ok(c, R) && c->tune_tc_rec != 0) {
-      int rc = run_receive_tc(c, (const float2*)L0.d_in, y, accumulate, st);
+    // per-particle incoming spectra where boxes hold several particles, or
+    // where the tensor cores receive for displaced particles (the broadcast
+    // then applies the displacement shifts)
+    const bool tc = !f64 && tc_receive_ok(c, R) && c->tune_tc_rec != 0;
+    const bool cells = c->multi || (tc && c->any_dshift);
+    const V* inc = (const V*)L0.d_in;
+    if (cells) {
+      const long long row = (long long)L0.K * 4 * R;
+      V* part = (V*)c->pspec[f64 ? 0 : 1];
+      k_cell_bcast<T><<<dim3((unsigned)c->p, (unsigned)((row + 255) / 256)), 256, 0, st>>>(
+          c->p, row, R, c->d_cell_of, (tc && c->any_dshift) ? 1 : 0, c->d_dshift, L0.d_khat, c->k,
+          (const V*)L0.d_in, part);
+      SMR_LAUNCH(c);
+      inc = part;
+    }
+    if (tc) {
+      int rc = run_receive_tc(c, (const float2*)inc, y, accumulate, st);
       pend(c, st);
       return rc;
     }
     int nsub = (16 + std::max(1, 16 / RC) - 1) / std::max(1, 16 / RC);
-    const V* inc = (const V*)L0.d_in;
-    if (c->multi) {
-      const long long row = (long long)L0.K * 4 * R;
-      V* part = (V*)c->pspec[f64 ? 0 : 1];
-      k_cell_bcast<V><<<dim3((unsigned)c->p, (unsigned)((row + 255) / 256)), 256, 0, st>>>(
-          c->p, row, c->d_cell_of, (const V*)L0.d_in, part);
-      SMR_LAUNCH(c);
-      inc = part;
-    }
     cudaFuncSetAttribute(k_receive<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     k_receive<T><<<(unsigned)(c->ntile * nsub * nrc), thr, sm, st>>>(
         L0.K, c->npsi, R, RC, c->d_tile_shape, c->d_tile_start, c->d_tile_count, c->d_perm,

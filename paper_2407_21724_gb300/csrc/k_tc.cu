@@ -704,7 +704,9 @@ int build_tc(Ctx* c) {
   return SMR_OK;
 }
 
-bool tc_receive_ok(const Ctx* c, int R) { return c->tc_enable && c->tc_ready && R == 1 && !c->any_dshift; }
+// displaced particles take these paths on unshifted per-particle spectra; the
+// box sum and broadcast around them apply the shifts
+bool tc_receive_ok(const Ctx* c, int R) { return c->tc_enable && c->tc_ready && R == 1; }
 
 int run_receive_tc(Ctx* c, const float2* in0, double2* y, bool accumulate, cudaStream_t st) {
   cudaFuncSetAttribute(k_receive_tc<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
@@ -717,7 +719,7 @@ int run_receive_tc(Ctx* c, const float2* in0, double2* y, bool accumulate, cudaS
 }
 
 bool tc_aggregate_ok(const Ctx* c, int R) {
-  return c->tc_enable && c->tc_ready && c->tc_agg_ready && R == 1 && !c->any_dshift;
+  return c->tc_enable && c->tc_ready && c->tc_agg_ready && R == 1;
 }
 
 // x32: FP32 copy of x (prep_x32), or null to split the FP64 x

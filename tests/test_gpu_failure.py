@@ -10,6 +10,11 @@
   invariant Krylov space with the residual still large and must stop with
   SMR_E_BREAKDOWN instead of running to maxit.  The block-diagonal
   preconditioner is undefined for that scene and is refused.
+* Checkpoint and resume of a solve: restarted GMRES carries nothing across
+  a restart but the iterate x.  A solve stopped at maxit (a multiple of the
+  restart length) saves x to a file; a fresh context on the same scene
+  resumes from it (use_x0) and converges, with the interrupted and resumed
+  iterations adding up to the uninterrupted solve's and the same solution.
 """
 import numpy as np
 import pytest
@@ -84,3 +89,42 @@ def test_breakdown_on_singular_operator():
         assert e.value.code == -1
     finally:
         smr.smr_destroy(ctx)
+
+
+@pytest.mark.parametrize("prec", [smr.SMR_PREC_FP64, smr.SMR_PREC_FP32])
+def test_solve_resumes_from_a_checkpoint(tmp_path, prec):
+    w = workloads.make("random", n=12, seed=8, modes=8)
+    kh, pol = workloads.incidence(0, 0, "x")
+    tol, m = 1e-8, 10
+
+    def start():
+        ctx = smr.scene_from_workload(w)
+        n = smr.smr_info(ctx)["n_unknowns"]
+        b = torch.empty(n, dtype=torch.complex128, device="cuda")
+        smr.smr_rhs_plane_waves(ctx, [kh], [pol], b)
+        return ctx, b
+
+    ctx, b = start()
+    x = torch.zeros_like(b)
+    rc, full = smr.smr_solve(ctx, b, x, tol=tol, restart=m, maxit=2000, precision=prec)
+    assert rc == 0 and full["iters"] > 3 * m
+    x_full = x.cpu().numpy()
+    # interrupted after two restart cycles; the iterate goes to a file
+    x.zero_()
+    rc, part = smr.smr_solve(ctx, b, x, tol=tol, restart=m, maxit=2 * m, precision=prec)
+    assert rc == smr.SMR_E_NOT_CONVERGED and part["iters"] <= 2 * m
+    np.save(tmp_path / "x.npy", x.cpu().numpy())
+    smr.smr_destroy(ctx)
+    # a new context resumes
+    ctx, b = start()
+    x = torch.from_numpy(np.load(tmp_path / "x.npy")).cuda()
+    rc, rest = smr.smr_solve(ctx, b, x, tol=tol, restart=m, maxit=2000, precision=prec, use_x0=1)
+    assert rc == 0 and rest["resid_true"] <= tol
+    if prec == smr.SMR_PREC_FP64:
+        # restarted FP64 GMRES: the two halves add up to the whole
+        assert abs(part["iters"] + rest["iters"] - full["iters"]) <= 2 * m // 5 + 2
+    else:
+        # iterative refinement restarts its inner solves at every outer step
+        assert rest["iters"] < full["iters"]
+    assert _rel(x.cpu().numpy(), x_full) < 100 * tol
+    smr.smr_destroy(ctx)
