@@ -95,7 +95,7 @@ def test_breakdown_on_singular_operator():
 def test_solve_resumes_from_a_checkpoint(tmp_path, prec):
     w = workloads.make("random", n=12, seed=8, modes=8)
     kh, pol = workloads.incidence(0, 0, "x")
-    tol, m = 1e-8, 10
+    tol, m = (1e-8 if prec == smr.SMR_PREC_FP64 else 1e-6), 10
 
     def start():
         ctx = smr.scene_from_workload(w)
@@ -106,19 +106,20 @@ def test_solve_resumes_from_a_checkpoint(tmp_path, prec):
 
     ctx, b = start()
     x = torch.zeros_like(b)
-    rc, full = smr.smr_solve(ctx, b, x, tol=tol, restart=m, maxit=2000, precision=prec)
-    assert rc == 0 and full["iters"] > 3 * m
+    rc, full = smr.smr_solve(ctx, b, x, tol=tol, restart=m, maxit=2000, precision=prec, max_outer=40)
+    assert rc == 0 and full["iters"] > 2 * m
     x_full = x.cpu().numpy()
     # interrupted after two restart cycles; the iterate goes to a file
     x.zero_()
-    rc, part = smr.smr_solve(ctx, b, x, tol=tol, restart=m, maxit=2 * m, precision=prec)
+    rc, part = smr.smr_solve(ctx, b, x, tol=tol, restart=m, maxit=2 * m, precision=prec, max_outer=40)
     assert rc == smr.SMR_E_NOT_CONVERGED and part["iters"] <= 2 * m
     np.save(tmp_path / "x.npy", x.cpu().numpy())
     smr.smr_destroy(ctx)
     # a new context resumes
     ctx, b = start()
     x = torch.from_numpy(np.load(tmp_path / "x.npy")).cuda()
-    rc, rest = smr.smr_solve(ctx, b, x, tol=tol, restart=m, maxit=2000, precision=prec, use_x0=1)
+    rc, rest = smr.smr_solve(ctx, b, x, tol=tol, restart=m, maxit=2000, precision=prec, use_x0=1,
+                             max_outer=40)
     assert rc == 0 and rest["resid_true"] <= tol
     if prec == smr.SMR_PREC_FP64:
         # restarted FP64 GMRES: the two halves add up to the whole
