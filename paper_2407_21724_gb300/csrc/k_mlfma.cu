@@ -1868,8 +1868,11 @@ static void use_lane(Ctx* c, int j) {
   c->d_tcn_part = a.tcn_part;
 }
 
-// one lane where the per-particle spectra of several-per-box scenes are shared
-int lanes_for(const Ctx* c, int R) { return (c->prof || c->multi) ? 1 : std::max(1, std::min(R, c->n_lanes)); }
+// one lane where products use the shared per-particle spectra (several
+// particles per box, or displaced particles)
+int lanes_for(const Ctx* c, int R) {
+  return (c->prof || c->multi || c->any_dshift) ? 1 : std::max(1, std::min(R, c->n_lanes));
+}
 
 // Side streams and events of lanes 0 .. n-1 for the overlapped product
 // (created outside graph capture, kept until the context goes).
