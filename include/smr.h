@@ -214,8 +214,9 @@ int smr_set_scene(smr_ctx* ctx, int p, const double* centres, const int* shape_i
 
 /* Several independent arrays in one context (a ragged batch): particle i
  * belongs to array array_ids[i] (0 .. n_arrays-1, every id used); each array's
- * host centres are in its own frame and must lie on its own square lattice of
- * spacing opts.pitch.  The arrays share the shapes, media and every table, and
+ * host centres are in its own frame and follow the rules of smr_set_scene on
+ * its own square lattice of spacing opts.pitch (cells, displacements, several
+ * particles per cell).  The arrays share the shapes, media and every table, and
  * one smr_matvec covers all of them, but no interaction couples two arrays:
  * each keeps its own quadtree (levels capped at the top level of the largest
  * array), its own near pairs and its own interaction lists, so the product
