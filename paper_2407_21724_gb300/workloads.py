@@ -177,6 +177,34 @@ def make(name, **kw):
                           f'{n*4*modes} unknowns',
                     centres=C, shape_ids=np.zeros(n, dtype=np.int32), shapes=[(R, modes, modes)],
                     eps_in=EPS_IN, pitch=PITCH, incidences=inc)
+    if name == 'spiral_bricks':
+        # the paper's largest spiral (Sec. V): n bricks on the golden-angle
+        # spiral with c = sqrt(3) R, R = 1/6 wavelength (100 nm at 600 nm; 115
+        # wavelengths across at n = 40,000), brick i turned about z by
+        # 2 pi (i - 1) / n, rounded to one of `bins` angles (rotated copies of
+        # one box mesh).  The paper's 200 x 200 x 100 nm superellipsoid bricks
+        # are stood in for by 0.3 x 0.3 x 0.15 wavelength boxes, whose corners
+        # stay clear of the closest neighbours; cells of 0.9 wavelengths keep
+        # every brick within a cell size of its cell centre, L0 = 16.
+        n = kw.get('n', 40000)
+        bins = kw.get('bins', 64)
+        modes = kw.get('modes', 10)
+        R = 1.0 / 6.0
+        i = np.arange(1, n + 1, dtype=float)
+        ga = 2 * np.pi / ((1 + np.sqrt(5)) / 2) ** 2
+        c = np.sqrt(3.0) * R
+        C = np.zeros((n, 3))
+        C[:, 0], C[:, 1] = c * np.sqrt(i) * np.cos(i * ga), c * np.sqrt(i) * np.sin(i * ga)
+        theta = 2 * np.pi * (i - 1) / n
+        ids = (np.rint(theta / (2 * np.pi / bins)).astype(np.int64) % bins).astype(np.int32)
+        V, T = box_mesh(0.3, 0.3, 0.15, 4, 4, 2)
+        shapes = [dict(kind='mesh', verts=V, tris=T, n_perp=modes, n_par=modes,
+                       label=f'brick 0.3 x 0.3 x 0.15, {len(T)} triangles')]
+        shapes += [dict(kind='rotated', base=0, angle=b * 2 * np.pi / bins) for b in range(1, bins)]
+        return dict(label=f'golden-angle spiral of {n} bricks (c = sqrt(3) R, R = 1/6), each turned by '
+                          f'2 pi (i-1)/n in {bins} steps, {2*modes} modes/current, {n*4*modes} unknowns',
+                    centres=C, shape_ids=ids, shapes=shapes, eps_in=EPS_IN, pitch=0.9, L0=16,
+                    incidences=kw.get('incidences') or [incidence(0, 0, 'x')])
     if name == 'moire':
         # two-layer Moire superlattice (the 2.5D example of Sec. V): the
         # vertices of a honeycomb of side `side` (m x m unit cells, two
