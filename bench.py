@@ -51,6 +51,7 @@ WORKLOADS = {
     # two-layer Moire lattice of meshed nanodisks
     "spiral_dense2000": ("spiral_dense", dict(n=2000)),
     "moire2k": ("moire", dict(m=22)),
+    "moire20k": ("moire", dict(m=71)),            # the paper's 20,160-disk bilayer size
     # the paper's 40,000-brick golden-angle spiral, bricks turned in 64 steps
     "spiral_bricks40k": ("spiral_bricks", dict(n=40000, bins=64)),
 }
