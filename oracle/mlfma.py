@@ -290,9 +290,10 @@ class MLFMA:
             y[mu] += self.near_block(mu, nu) @ xx[nu]
         return y.reshape(-1)
 
-    def aggregate(self, x, mus=None, out=None):
+    def aggregate(self, x, mus=None, out=None, boxes=None):
         """Level-0 outgoing spectra (n_box_0, K_0, 4): each particle's, shifted
-        from its centre to its cell's, summed over the cell's particles."""
+        from its centre to its cell's, summed over the cell's particles.
+        `mus` (one particle per cell) or `boxes` restrict the rows written."""
         sc = self.scene
         xx = x.reshape(sc.p, 2, sc.n_psi)
         g = self.grids[0]
@@ -301,6 +302,9 @@ class MLFMA:
         if out is None:
             out = np.zeros((len(t.levels[0]['ij']), g.K, 4), dtype=complex)
         cen = t.levels[0]['centre']
+        if boxes is not None:
+            out[boxes] = 0.0
+            mus = [mu for b in boxes for mu in t.members[tuple(t.levels[0]['ij'][b])]]
         for mu in (range(sc.p) if mus is None else mus):
             b = t.cell[mu]
             P = self.patterns[sc.shape_ids[mu]]               # (N, 2, K)
@@ -308,7 +312,7 @@ class MLFMA:
             for c in range(2):
                 for comp in range(2):
                     v = shift * (xx[mu, c] @ np.conj(P[:, comp, :]))
-                    if t.one_per_cell:
+                    if t.one_per_cell and boxes is None:
                         out[b, :, 2 * c + comp] = v
                     else:
                         out[b, :, 2 * c + comp] += v

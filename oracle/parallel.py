@@ -31,12 +31,12 @@ def _shared(shape, dtype=complex):
     return np.frombuffer(buf, dtype=dtype, count=int(np.prod(shape))).reshape(shape)
 
 
-def _near_block_task(key):
+def _near_block_task(task):
+    key, dc = task
     sc = _G["scene"]
     if key[0] == "self":
         return key, sc.self_block(key[1])
-    sm, sn, dc = key[0], key[1], np.asarray(key[3:], dtype=float)
-    return key, exterior_block(sc, sm, dc, sn, np.zeros(3))
+    return key, exterior_block(sc, key[0], dc, key[1], np.zeros(3))
 
 
 def _step(task):
@@ -46,6 +46,8 @@ def _step(task):
         M.near(B["x"], mus=idx, out=B["yn"])
     elif kind == "agg":
         M.aggregate(B["x"], mus=idx, out=B["out"][0])
+    elif kind == "agg_box":
+        M.aggregate(B["x"], out=B["out"][0], boxes=idx)
     elif kind == "up":
         M.upward(s, B["out"][s], parents=idx, out=B["out"][s + 1])
     elif kind == "tr":
@@ -68,17 +70,20 @@ class ParallelMLFMA:
         _G["scene"] = scene
         with ctx.Pool(self.workers) as pool:
             M = MLFMA(scene, pitch, pmap=pool.map, **kw)
-            # every distinct near block once (the keys MLFMA.near_block uses)
-            keys = set()
+            # every distinct near block once (the keys MLFMA.near_block uses),
+            # each computed for the exact offset of the first pair that
+            # names it, as the serial product does
+            keys = {}
             for mu, nu in M.tree.near_pairs():
                 sm, sn = scene.shape_ids[mu], scene.shape_ids[nu]
                 if mu == nu:
-                    keys.add(("self", sm))
+                    keys.setdefault(("self", sm), None)
                 else:
                     d = tuple(M.tree.ij0[mu] - M.tree.ij0[nu])
                     dc = scene.centres[mu] - scene.centres[nu]
-                    keys.add((sm, sn, d) + tuple(np.round(dc, 12)))
-            for key, blk in pool.map(_near_block_task, sorted(keys, key=str), chunksize=4):
+                    keys.setdefault((sm, sn, d) + tuple(np.round(dc, 12)), dc)
+            tasks = sorted(keys.items(), key=lambda kv: str(kv[0]))
+            for key, blk in pool.map(_near_block_task, tasks, chunksize=4):
                 M._near_cache[key] = blk
         self.M = M
         p, n2 = scene.p, 2 * scene.n_psi
@@ -106,8 +111,8 @@ class ParallelMLFMA:
         if t.one_per_cell:
             self._run("agg", 0, p)
         else:
-            # several particles per cell sum into one box: one process
-            B["out"][0][:] = M.aggregate(B["x"])
+            # several particles per cell sum into one box: split by boxes
+            self._run("agg_box", 0, len(t.levels[0]["ij"]))
         for s in range(t.n_levels - 1):
             self._run("up", s, len(t.levels[s + 1]["ij"]))
         for s in range(t.n_levels):
